@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Throughput of the phaseless-AFQMC walker step (propagate + local energy) on B300.
+
+One "step" is one imaginary-time step of every walker (fields, force bias, VHS,
+Taylor propagator with the one-body halves, overlap ratio and phaseless weight,
+QR every 5th step) followed by the mixed local energy of every walker.  The
+metric is walker-steps per second.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl afq|reference]
+
+With N > 1 (under torch.distributed.run) every rank runs an independent replica
+of the workload with its own seed: the step does not shard, so ranks exchange
+nothing on the data path; value = all ranks' walker-steps / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker-steps/s/B300 (propagate+E_loc), FP64 vs mixed, |ΔE| vs FP64 oracle"
+UNIT = "walker-steps/s"
+WORKLOAD = "c2"
+WORKLOAD_TEXT = ("ph-AFQMC step + E_loc, 100 orbitals, 10a+10b electrons, 400 Cholesky "
+                 "vectors (geometric norm decay), 128 complex128 walkers, dt 0.005, QR every "
+                 "5 steps, Philox fields")
+FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 nominal: 148 SMs x 2032 MHz x ~4.15 flop/clk/SM
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["afq", "reference"], default="afq")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="budget of the oracle CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def exchange_flops(W, X, M, na, nb):
+    """Algorithmic flops of the exchange kernel for W walkers: T = L~ theta
+    (4 n^2 M real flops per g and spin, real x complex) plus sum T_ij T_ji
+    (8 n^2 flops per g and spin)."""
+    return W * X * sum(n * n * (4 * M + 8) for n in (na, nb))
+
+
+def step_flops(W, X, M, na, nb, order=6):
+    """Algorithmic flops of one walker step (all walkers), by part."""
+    N = na + nb
+    Mp = M * (M + 1) // 2
+    return {
+        "force_bias": W * 4 * X * N * M,
+        "vhs": W * 4 * X * Mp,
+        "propagate": W * (order * 8 + 2 * 4) * M * M * N,
+        "overlap_theta": W * sum(4 * M * n * n + 8 * M * n * n for n in (na, nb)),
+        "exchange": exchange_flops(W, X, M, na, nb),
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = list(csv.reader(io.StringIO(open(self.path).read())))
+        os.unlink(self.path)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float, W_sample: int = 8) -> dict:
+    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+    from oracle.afqmc import Oracle
+    from oracle.philox import gaussian_fields
+    from paper_2209_04015_b300.synthetic import make_config, trial_walkers
+    s, c = make_config(WORKLOAD)
+    orc = Oracle(s.h1, s.L, s.e0, s.psi_a, s.psi_b, dt=0.005, qr_period=5)
+    orc.init_walkers(trial_walkers(s, W_sample))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        xi = gaussian_fields(steps, W_sample, s.X, 1)
+        orc.step(xi)
+        if orc.nstep % 5 == 0:
+            orc.orthogonalise()
+        orc.local_energy()
+        steps += 1
+        if time.perf_counter() - t0 > seconds or steps >= 200:
+            break
+    dt = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([p.get("num_threads", 1) for p in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": W_sample * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{W_sample} of the {c['W']} walkers of the {WORKLOAD} workload, "
+                      f"{steps} steps (step + QR cadence + E_loc), {dt:.1f} s of host time"}
+
+
+# ----------------------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    from oracle.afqmc import Oracle
+    from oracle.philox import gaussian_fields
+    from paper_2209_04015_b300.synthetic import make_config, trial_walkers
+    s, c = make_config(WORKLOAD)
+    Ws = 4
+    orc = Oracle(s.h1, s.L, s.e0, s.psi_a, s.psi_b, dt=0.005, qr_period=5)
+    orc.init_walkers(trial_walkers(s, Ws))
+
+    def one(k):
+        orc.step(gaussian_fields(k, Ws, s.X, 1))
+        if orc.nstep % 5 == 0:
+            orc.orthogonalise()
+        orc.local_energy()
+
+    for k in range(args.warmup):
+        one(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        one(args.warmup + k)
+    dt = time.perf_counter() - t0
+    value = Ws * args.steps / dt
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([p.get("num_threads", 1) for p in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT, "name": WORKLOAD, "sample_walkers": Ws},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{Ws} of {c['W']} walkers per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_afq(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2209_04015_b300 import AfqContext
+    from paper_2209_04015_b300.synthetic import make_config
+
+    s, c = make_config(WORKLOAD, seed=1 + rank)
+    W, X, M, na, nb = c["W"], s.X, s.M, s.na, s.nb
+    stream = torch.cuda.current_stream()
+    ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, stream=stream.cuda_stream)
+    ctx.init_hamiltonian(s.h1, s.L, s.e0)
+    ctx.init_trial(s.psi_a, s.psi_b)
+    ctx.init_walkers(W)
+    e_dev = torch.empty((W, 4, 2), dtype=torch.float64, device="cuda")
+    emix_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
+        ctx.propagate_dev(None, 1)
+        ctx.local_energy_dev(e_dev.data_ptr(), emix_dev.data_ptr())
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ctx.profile_enable(True)
+    n0 = ctx.launch_count()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()                      # write 256 MB: evicts L2 between timed steps
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - n0
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * W * args.steps / (total_ms / 1e3)
+
+    # end to end through the public host-buffer API: the step's fields go host -> device
+    # from pinned memory, the energies come back to the host, every step
+    K2 = max(10, min(args.steps, 50))
+    host_fields = torch.empty((K2, W, X), dtype=torch.float64).pin_memory()
+    host_fields.copy_(torch.from_numpy(np.random.default_rng(5 + rank).standard_normal((K2, W, X))))
+    hf = host_fields.numpy()
+    ctx.propagate(hf[0], 1)
+    ctx.local_energy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K2):
+        ctx.propagate(hf[k], 1)
+        ctx.local_energy()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": W * K2 / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": W * X * 8,
+           "d2h_bytes_per_step": W * 4 * 16 + 8, "steps": K2}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    flops = step_flops(W, X, M, na, nb)
+    ex_ms, ex_n = prof["exchange"]
+    ex_avg_s = ex_ms / max(ex_n, 1) / 1e3
+    ex_achieved = exchange_flops(W, X, M, na, nb) / ex_avg_s / 1e12
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1],
+                   "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)}
+               for k, v in prof.items() if v[1]}
+    total_flops = sum(flops.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT, "name": WORKLOAD, "M": M, "na": na, "nb": nb,
+                   "X": X, "W_per_gpu": W, "dt": 0.005, "qr_period": 5, "precision": "fp64",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MB write, outside the step events)"},
+        "roofline": {"bound": "alu", "kernel": "exchange", "achieved": ex_achieved,
+                     "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ex_achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "peak_source": "FP64 nominal (148 SMs x 2032 MHz x 4.15 flop/clk/SM)",
+                     "flops_per_launch": exchange_flops(W, X, M, na, nb),
+                     "avg_launch_ms": ex_avg_s * 1e3},
+        "step_flops": total_flops,
+        "step_tflops": total_flops / (total_ms / args.steps / 1e3) / 1e12,
+        "kernels": kernels,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_afq(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

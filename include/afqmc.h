@@ -1,0 +1,175 @@
+/*
+ * afqmc.h - C ABI of the B300 phaseless-AFQMC walker-step library (libafqmc.so).
+ *
+ * The library runs one imaginary-time step of phaseless auxiliary-field QMC for a
+ * batch of single-determinant walkers under a Cholesky-factorised Hamiltonian
+ * (Malone, Mahajan, Spencer, Lee, arXiv:2209.04015, Sec. "Review of AFQMC" and
+ * Sec. "Implementational details"), entirely in CUDA kernels for sm_103a.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Arrays are row-major C arrays.  Complex numbers are interleaved (re, im)
+ *    pairs of doubles, so a "W x X complex" array holds 2*W*X doubles.
+ *  - Pointers are HOST pointers unless the function name ends in _dev, in which
+ *    case they are DEVICE pointers that the kernels read or write on the
+ *    context's stream (for example torch tensors' data_ptr()).
+ *  - The library copies every host input into device memory that it owns; the
+ *    caller keeps ownership of all its buffers, host or device.  Host outputs are
+ *    complete when the call returns; _dev outputs are complete in stream order.
+ *  - Every function returns an afq_status.  On failure nothing is written to the
+ *    caller's outputs, and afq_last_error() returns a message.
+ *  - Spin blocks: walker matrices hold the alpha columns first, then the beta
+ *    columns (na + nb columns in all).
+ *  - Sizes: 1 <= na, nb <= 64 (na or nb may be 0), M <= 1024, X >= 1, W >= 1.
+ */
+#ifndef AFQMC_H
+#define AFQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afq_ctx afq_ctx;
+
+typedef enum afq_status {
+  AFQ_OK = 0,
+  AFQ_ERR_ARG = 1,      /* bad pointer, size or call order                  */
+  AFQ_ERR_CUDA = 2,     /* a CUDA runtime call failed                        */
+  AFQ_ERR_SINGULAR = 3, /* an overlap matrix Psi^T Phi had a zero pivot      */
+  AFQ_ERR_NAN = 4,      /* a weight, overlap or energy became NaN/Inf        */
+  AFQ_ERR_STATE = 5,    /* hamiltonian / trial / walkers not initialised     */
+  AFQ_ERR_NOMEM = 6     /* device allocation failed                          */
+} afq_status;
+
+typedef enum afq_precision {
+  AFQ_FP64 = 0,       /* every contraction in float64                         */
+  AFQ_SPLIT_BF16 = 1, /* force bias, VHS, propagator and exchange as split-bf16
+                         tensor-core GEMMs with fp32 accumulation; overlaps,
+                         inverses, QR and weights stay float64                */
+  AFQ_SPLIT_TF32 = 2  /* reserved                                              */
+} afq_precision;
+
+typedef struct afq_params {
+  double dt;           /* imaginary time step (the paper's Delta tau)            */
+  int taylor_order;    /* order n of the Taylor series of exp(A); default 6      */
+  int qr_period;       /* QR re-orthogonalisation after every qr_period-th step;
+                          0 disables it                                           */
+  uint64_t seed;       /* Philox key for device-drawn fields                     */
+  int precision;       /* an afq_precision                                       */
+  int has_e_shift;     /* 0: E_shift = trial energy, 1: use e_shift              */
+  double e_shift;      /* energy shift in exp(-dt (H - E_shift))                 */
+  double fb_cap;       /* |xbar_g| cap; 0 = off                                  */
+  int free_projection; /* 1: complex weights w <- w I (no phaseless cut)         */
+} afq_params;
+
+/* Fill *p with the defaults: dt 0.005, Taylor order 6, QR every 5 steps, seed 1,
+   FP64, E_shift = trial energy, no cap, phaseless. */
+void afq_default_params(afq_params* p);
+
+/* Create a context bound to cuda_stream (a cudaStream_t, or NULL for the legacy
+   default stream) on the current CUDA device.  *ctx receives the handle; the
+   caller releases it with afq_destroy. */
+int afq_create(afq_ctx** ctx, const afq_params* params, void* cuda_stream);
+int afq_destroy(afq_ctx* ctx);
+/* Message of the last failed call on ctx (never NULL; "" when none). */
+const char* afq_last_error(const afq_ctx* ctx);
+
+/* Hamiltonian of Eq. Habinitio with the Cholesky factorisation (pr|qs) =
+   sum_g L_g,pr L_g,qs (Sec. "Review of AFQMC").
+   h1: M x M, symmetric.  L: X x M x M, each L_g symmetric.  e0: constant energy.
+   Symmetry is checked to 1e-12 relative (AFQ_ERR_ARG otherwise). */
+int afq_init_hamiltonian(afq_ctx* ctx, int M, int X, const double* h1, const double* L,
+                         double e0);
+
+/* Single-determinant trial Psi_T (Sec. "Overlap"): psi_a M x na, psi_b M x nb, real,
+   with orthonormal columns.  Builds the half-rotated vectors L~_g = Psi^T L_g
+   (Sec. "One-body Green's function and force bias"), the rotated h~ = Psi^T h1, the
+   mean field vbar_g, h'' = h1 - 1/2 sum_g L_g L_g + sum_g vbar_g L_g and the
+   half-step propagator exp(-dt h''/2).  Needs afq_init_hamiltonian first. */
+int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a,
+                   const double* psi_b);
+/* Local energy of the trial determinant itself (its Hartree-Fock energy). */
+int afq_trial_energy(afq_ctx* ctx, double* e_out);
+
+/* Walker ensemble of Eq. stat_wfs.  phi: W x M x (na+nb) complex, or NULL for W
+   copies of the trial.  w: W real weights, or NULL for all ones.  Computes the
+   stored overlaps <Psi_T|phi_z> and the Green's-function intermediates, and resets
+   the step counter to 0. */
+int afq_init_walkers(afq_ctx* ctx, int W, const double* phi, const double* w);
+
+/* nsteps hybrid-propagation steps (Sec. "Review of AFQMC": force bias, shifted
+   fields, B(x - xbar), overlap ratio Eq. ovl, importance function Eq. import,
+   phaseless weight Eqs. ph and theta, walker update), with QR after every
+   qr_period-th step.  fields: nsteps x W x X N(0,1) auxiliary fields, or NULL to
+   draw them on the device from Philox4x32-10 at the current step counter.
+   AFQ_ERR_SINGULAR / AFQ_ERR_NAN are reported after the last step. */
+int afq_propagate(afq_ctx* ctx, const double* fields, int nsteps);
+/* Same with device-resident fields (nsteps x W x X doubles) or NULL. */
+int afq_propagate_dev(afq_ctx* ctx, const double* fields_dev, int nsteps);
+
+/* Mixed local energy (Sec. "Local energy"): per walker E1, EJ, EK and
+   E_L = e0 + E1 + EJ + EK as complex numbers (e_out: W x 4 complex, may be NULL),
+   and the weighted estimate sum_z w_z Re E_L,z / sum_z w_z (e_mix, may be NULL). */
+int afq_local_energy(afq_ctx* ctx, double* e_out, double* e_mix);
+/* Same with device outputs; no host synchronisation. */
+int afq_local_energy_dev(afq_ctx* ctx, double* e_out_dev, double* e_mix_dev);
+
+/* QR re-orthogonalisation of every walker's spin blocks, Phi_s = Q R with diag(R)
+   real and positive; Phi_s <- Q and the stored overlap is divided by
+   prod_s det R_s. */
+int afq_orthogonalise(afq_ctx* ctx);
+
+/* Getters (host outputs): walkers W x M x (na+nb) complex; weights W complex
+   (imaginary parts are zero in phaseless mode); stored overlaps W complex; the
+   force bias xbar of the last step, W x X complex. */
+int afq_get_walkers(afq_ctx* ctx, double* phi);
+int afq_get_weights(afq_ctx* ctx, double* w);
+int afq_get_overlaps(afq_ctx* ctx, double* ovlp);
+int afq_get_force_bias(afq_ctx* ctx, double* xbar);
+int afq_get_step(afq_ctx* ctx, uint64_t* step);
+/* Restore a saved state (checkpoint/resume): walkers, weights (W complex),
+   overlaps (W complex, or NULL to recompute) and the step counter. */
+int afq_set_state(afq_ctx* ctx, const double* phi, const double* w, const double* ovlp,
+                  uint64_t step);
+
+/* The device Philox4x32-10 field stream of one step: out is W x X doubles.  Counter
+   (step mod 2^32, walker, g/2, step >> 32), key (seed mod 2^32, seed >> 32);
+   Box-Muller of two 53-bit uniforms gives the fields for g = 2m and 2m+1. */
+int afq_philox_fields(afq_ctx* ctx, uint64_t step, double* out);
+/* The raw Philox words of the same stream: out is W x ceil(X/2) x 4 uint32. */
+int afq_philox_words(afq_ctx* ctx, uint64_t step, uint32_t* out);
+
+/* Number of kernel launches this context has issued since creation. */
+int afq_launch_count(afq_ctx* ctx, uint64_t* count);
+
+/* Kernel classes timed by the built-in profiler (CUDA events recorded on the
+   context's stream around each launch of that class). */
+typedef enum afq_kernel {
+  AFQ_K_FIELDS = 0,   /* fields, force bias, shifted fields, cfb, cmf          */
+  AFQ_K_VHS = 1,      /* VHS build A = i sqrt(dt) sum_g y_g L_g                */
+  AFQ_K_PROPAGATE = 2,/* P T_n(A) P applied to every walker                    */
+  AFQ_K_OVERLAP = 3,  /* overlap, determinant, theta, one-body energy          */
+  AFQ_K_FORCE_BIAS = 4,/* c = L~ theta (force bias and Coulomb vector)         */
+  AFQ_K_WEIGHTS = 5,  /* overlap ratio and phaseless weight                    */
+  AFQ_K_QR = 6,       /* QR re-orthogonalisation                               */
+  AFQ_K_EXCHANGE = 7, /* fused exchange energy                                 */
+  AFQ_K_ENERGY = 8,   /* energy assembly and weighted estimate                 */
+  AFQ_K_COUNT = 9
+} afq_kernel;
+
+/* on != 0 starts recording event pairs around every launch (and clears earlier
+   records); on == 0 stops.  Recording adds two event records per launch. */
+int afq_profile_enable(afq_ctx* ctx, int on);
+/* Total device time in ms and launch count of one kernel class over the records
+   taken since afq_profile_enable(ctx, 1); synchronises the stream. */
+int afq_profile_read(afq_ctx* ctx, int kernel, double* total_ms, uint64_t* launches);
+/* Name of a kernel class, or NULL when kernel is out of range. */
+const char* afq_kernel_name(int kernel);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFQMC_H */

@@ -1,0 +1,251 @@
+"""ctypes binding of libafqmc (include/afqmc.h): argument marshalling only.
+
+Every entry point keeps the C name without its ``afq_`` prefix.  Host arrays are
+numpy arrays (complex arrays as complex128, which matches the interleaved
+(re, im) doubles of the C ABI); the ``*_dev`` methods take raw device pointers
+(for example ``tensor.data_ptr()``).  There is no fallback: if the library
+cannot be loaded, ``load_library`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libafqmc.so")
+
+AFQ_OK, AFQ_ERR_ARG, AFQ_ERR_CUDA, AFQ_ERR_SINGULAR, AFQ_ERR_NAN, AFQ_ERR_STATE, AFQ_ERR_NOMEM = range(7)
+PRECISIONS = {"fp64": 0, "split_bf16": 1, "split_tf32": 2}
+STATUS_NAMES = {0: "AFQ_OK", 1: "AFQ_ERR_ARG", 2: "AFQ_ERR_CUDA", 3: "AFQ_ERR_SINGULAR",
+                4: "AFQ_ERR_NAN", 5: "AFQ_ERR_STATE", 6: "AFQ_ERR_NOMEM"}
+
+
+class AfqParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("taylor_order", ctypes.c_int),
+                ("qr_period", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int), ("has_e_shift", ctypes.c_int),
+                ("e_shift", ctypes.c_double), ("fb_cap", ctypes.c_double),
+                ("free_projection", ctypes.c_int)]
+
+
+class AfqError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "afq_default_params": (None, [ctypes.POINTER(AfqParams)]),
+    "afq_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(AfqParams), _P]),
+    "afq_destroy": (ctypes.c_int, [_P]),
+    "afq_last_error": (ctypes.c_char_p, [_P]),
+    "afq_init_hamiltonian": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_double]),
+    "afq_init_trial": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "afq_trial_energy": (ctypes.c_int, [_P, _D]),
+    "afq_init_walkers": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "afq_propagate": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "afq_propagate_dev": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "afq_local_energy": (ctypes.c_int, [_P, _P, _D]),
+    "afq_local_energy_dev": (ctypes.c_int, [_P, _P, _P]),
+    "afq_orthogonalise": (ctypes.c_int, [_P]),
+    "afq_get_walkers": (ctypes.c_int, [_P, _P]),
+    "afq_get_weights": (ctypes.c_int, [_P, _P]),
+    "afq_get_overlaps": (ctypes.c_int, [_P, _P]),
+    "afq_get_force_bias": (ctypes.c_int, [_P, _P]),
+    "afq_get_step": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "afq_set_state": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_uint64]),
+    "afq_philox_fields": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
+    "afq_philox_words": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
+    "afq_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "afq_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afq_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_uint64)]),
+    "afq_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libafqmc.so and declare its signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libafqmc.so not built ({path}); run "
+                           "`python -m paper_2209_04015_b300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(_P)
+
+
+def _c(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class AfqContext:
+    """One walker ensemble on the current CUDA device (wraps afq_ctx*)."""
+
+    def __init__(self, dt: float = 0.005, taylor_order: int = 6, qr_period: int = 5,
+                 seed: int = 1, precision: str = "fp64", e_shift: float | None = None,
+                 fb_cap: float = 0.0, free_projection: bool = False, stream: int | None = None):
+        self.lib = load_library()
+        p = AfqParams()
+        self.lib.afq_default_params(ctypes.byref(p))
+        p.dt, p.taylor_order, p.qr_period, p.seed = dt, taylor_order, qr_period, seed
+        p.precision = PRECISIONS[precision]
+        p.has_e_shift = 0 if e_shift is None else 1
+        p.e_shift = 0.0 if e_shift is None else float(e_shift)
+        p.fb_cap = fb_cap
+        p.free_projection = 1 if free_projection else 0
+        self.params = p
+        h = _P()
+        rc = self.lib.afq_create(ctypes.byref(h), ctypes.byref(p), _P(stream or 0))
+        if rc != AFQ_OK:
+            raise AfqError(rc, "afq_create failed")
+        self.h = h
+        self.M = self.X = self.na = self.nb = self.W = 0
+
+    # -- plumbing ---------------------------------------------------------------
+    def _check(self, rc: int) -> None:
+        if rc != AFQ_OK:
+            raise AfqError(rc, self.lib.afq_last_error(self.h).decode())
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.afq_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def N(self) -> int:
+        return self.na + self.nb
+
+    # -- entry points -------------------------------------------------------------
+    def init_hamiltonian(self, h1: np.ndarray, L: np.ndarray, e0: float = 0.0) -> None:
+        h1 = _c(h1, np.float64)
+        L = _c(L, np.float64)
+        self.M, self.X = h1.shape[0], L.shape[0]
+        self._check(self.lib.afq_init_hamiltonian(self.h, self.M, self.X, _ptr(h1), _ptr(L),
+                                                  float(e0)))
+
+    def init_trial(self, psi_a: np.ndarray, psi_b: np.ndarray) -> None:
+        a = _c(psi_a, np.float64)
+        b = _c(psi_b, np.float64)
+        self.na, self.nb = a.shape[1], b.shape[1]
+        self._check(self.lib.afq_init_trial(self.h, self.na, self.nb, _ptr(a), _ptr(b)))
+
+    def trial_energy(self) -> float:
+        e = ctypes.c_double()
+        self._check(self.lib.afq_trial_energy(self.h, ctypes.byref(e)))
+        return e.value
+
+    def init_walkers(self, W: int, phi: np.ndarray | None = None,
+                     w: np.ndarray | None = None) -> None:
+        ph = None if phi is None else _c(phi, np.complex128)
+        ww = None if w is None else _c(w, np.float64)
+        self.W = W
+        self._check(self.lib.afq_init_walkers(self.h, W, _ptr(ph), _ptr(ww)))
+
+    def propagate(self, fields: np.ndarray | None = None, nsteps: int = 1) -> None:
+        f = None if fields is None else _c(fields, np.float64)
+        if f is not None and f.size != nsteps * self.W * self.X:
+            raise ValueError("fields must hold nsteps x W x X values")
+        self._check(self.lib.afq_propagate(self.h, _ptr(f), nsteps))
+
+    def propagate_dev(self, fields_ptr: int | None, nsteps: int = 1) -> None:
+        self._check(self.lib.afq_propagate_dev(self.h, _P(fields_ptr or 0) if fields_ptr else None,
+                                               nsteps))
+
+    def local_energy(self) -> tuple[np.ndarray, float]:
+        e = np.empty((self.W, 4), dtype=np.complex128)
+        emix = ctypes.c_double()
+        self._check(self.lib.afq_local_energy(self.h, _ptr(e), ctypes.byref(emix)))
+        return e, emix.value
+
+    def local_energy_dev(self, e_ptr: int | None, emix_ptr: int | None) -> None:
+        self._check(self.lib.afq_local_energy_dev(self.h, _P(e_ptr) if e_ptr else None,
+                                                  _P(emix_ptr) if emix_ptr else None))
+
+    def orthogonalise(self) -> None:
+        self._check(self.lib.afq_orthogonalise(self.h))
+
+    def get_walkers(self) -> np.ndarray:
+        out = np.empty((self.W, self.M, self.N), dtype=np.complex128)
+        self._check(self.lib.afq_get_walkers(self.h, _ptr(out)))
+        return out
+
+    def get_weights(self) -> np.ndarray:
+        out = np.empty(self.W, dtype=np.complex128)
+        self._check(self.lib.afq_get_weights(self.h, _ptr(out)))
+        return out
+
+    def get_overlaps(self) -> np.ndarray:
+        out = np.empty(self.W, dtype=np.complex128)
+        self._check(self.lib.afq_get_overlaps(self.h, _ptr(out)))
+        return out
+
+    def get_force_bias(self) -> np.ndarray:
+        out = np.empty((self.W, self.X), dtype=np.complex128)
+        self._check(self.lib.afq_get_force_bias(self.h, _ptr(out)))
+        return out
+
+    def get_step(self) -> int:
+        s = ctypes.c_uint64()
+        self._check(self.lib.afq_get_step(self.h, ctypes.byref(s)))
+        return s.value
+
+    def set_state(self, phi: np.ndarray, w: np.ndarray, ovlp: np.ndarray | None = None,
+                  step: int = 0) -> None:
+        ph = _c(phi, np.complex128)
+        ww = _c(w, np.complex128)
+        ov = None if ovlp is None else _c(ovlp, np.complex128)
+        self._check(self.lib.afq_set_state(self.h, _ptr(ph), _ptr(ww), _ptr(ov), step))
+
+    def philox_fields(self, step: int) -> np.ndarray:
+        out = np.empty((self.W, self.X), dtype=np.float64)
+        self._check(self.lib.afq_philox_fields(self.h, step, _ptr(out)))
+        return out
+
+    def philox_words(self, step: int) -> np.ndarray:
+        out = np.empty((self.W, (self.X + 1) // 2, 4), dtype=np.uint32)
+        self._check(self.lib.afq_philox_words(self.h, step, _ptr(out)))
+        return out
+
+    def profile_enable(self, on: bool = True) -> None:
+        self._check(self.lib.afq_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self) -> dict[str, tuple[float, int]]:
+        """{kernel class: (total ms, launches)} since profile_enable(True)."""
+        out = {}
+        k = 0
+        while True:
+            name = self.lib.afq_kernel_name(k)
+            if name is None:
+                break
+            ms = ctypes.c_double()
+            n = ctypes.c_uint64()
+            self._check(self.lib.afq_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)))
+            out[name.decode()] = (ms.value, n.value)
+            k += 1
+        return out
+
+    def launch_count(self) -> int:
+        c = ctypes.c_uint64()
+        self._check(self.lib.afq_launch_count(self.h, ctypes.byref(c)))
+        return c.value

@@ -1,0 +1,641 @@
+// C ABI of libafqmc (declared in include/afqmc.h): context, input validation,
+// set-up sequence and the per-step launch sequence on the context's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "afq_internal.cuh"
+
+int afq_fail(afq_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+namespace {
+
+template <class T>
+int dalloc(afq_ctx* ctx, T** p, size_t n) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return afq_fail(ctx, AFQ_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return AFQ_OK;
+}
+
+template <class T>
+void dfree(T** p) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+}
+
+#define AFQ_TRY(x)            \
+  do {                        \
+    int rc_ = (x);            \
+    if (rc_ != AFQ_OK) return rc_; \
+  } while (0)
+
+int free_walker_set(WalkerSet& s) {
+  dfree(&s.phi);
+  dfree(&s.thetaT);
+  dfree(&s.det);
+  dfree(&s.e1);
+  dfree(&s.c);
+  dfree(&s.ekp);
+  dfree(&s.energy);
+  dfree(&s.w);
+  dfree(&s.ovlp);
+  s.W = 0;
+  return AFQ_OK;
+}
+
+int alloc_walker_set(afq_ctx* ctx, WalkerSet& s, int W) {
+  free_walker_set(s);
+  const size_t M = ctx->M, N = ctx->N, X = ctx->X;
+  AFQ_TRY(dalloc(ctx, &s.phi, W * M * N));
+  AFQ_TRY(dalloc(ctx, &s.thetaT, W * N * M));
+  AFQ_TRY(dalloc(ctx, &s.det, 2 * (size_t)W));
+  AFQ_TRY(dalloc(ctx, &s.e1, 2 * (size_t)W));
+  AFQ_TRY(dalloc(ctx, &s.c, W * X));
+  AFQ_TRY(dalloc(ctx, &s.ekp, (size_t)W * 2 * ctx->ex_groups));
+  AFQ_TRY(dalloc(ctx, &s.energy, 4 * (size_t)W));
+  AFQ_TRY(dalloc(ctx, &s.w, W));
+  AFQ_TRY(dalloc(ctx, &s.ovlp, W));
+  s.W = W;
+  return AFQ_OK;
+}
+
+int sync(afq_ctx* ctx) {
+  AFQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return AFQ_OK;
+}
+
+// Reads and clears the device flags; maps them to a status.
+int check_flags(afq_ctx* ctx) {
+  int h[2] = {0, 0};
+  AFQ_CUDA(ctx, cudaMemcpyAsync(h, ctx->flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  AFQ_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(h), ctx->stream));
+  AFQ_TRY(sync(ctx));
+  if (h[0]) return afq_fail(ctx, AFQ_ERR_SINGULAR, std::to_string(h[0]) + " singular pivot(s)");
+  if (h[1]) return afq_fail(ctx, AFQ_ERR_NAN, std::to_string(h[1]) + " non-finite weight(s)");
+  return AFQ_OK;
+}
+
+cudaEvent_t take_event(afq_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Runs one launch wrapper, bracketed by an event pair when profiling is on.
+template <class F>
+int timed(afq_ctx* ctx, int kid, F&& launch) {
+  if (!ctx->profiling) return launch();
+  afq_ctx::ProfRec r{kid, take_event(ctx), take_event(ctx)};
+  AFQ_CUDA(ctx, cudaEventRecord(r.a, ctx->stream));
+  int rc = launch();
+  AFQ_CUDA(ctx, cudaEventRecord(r.b, ctx->stream));
+  ctx->prof.push_back(r);
+  return rc;
+}
+
+// Folds finished event pairs into the per-class totals.
+int drain_profile(afq_ctx* ctx) {
+  if (ctx->prof.empty()) return AFQ_OK;
+  AFQ_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (auto& r : ctx->prof) {
+    float ms = 0.f;
+    AFQ_CUDA(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
+    ctx->prof_ms[r.kid] += ms;
+    ctx->prof_n[r.kid] += 1;
+    ctx->event_pool.push_back(r.a);
+    ctx->event_pool.push_back(r.b);
+  }
+  ctx->prof.clear();
+  return AFQ_OK;
+}
+
+// Green's-function intermediates of a walker set: theta, det, E1 and c.
+int green_and_bias(afq_ctx* ctx, WalkerSet& s) {
+  AFQ_TRY(timed(ctx, AFQ_K_OVERLAP, [&] { return launch_overlap_theta(ctx, s); }));
+  AFQ_TRY(timed(ctx, AFQ_K_FORCE_BIAS, [&] { return launch_force_bias_fp64(ctx, s); }));
+  return AFQ_OK;
+}
+
+int energy_kernels(afq_ctx* ctx, WalkerSet& s) {
+  AFQ_TRY(timed(ctx, AFQ_K_EXCHANGE, [&] { return launch_exchange_fp64(ctx, s); }));
+  AFQ_TRY(timed(ctx, AFQ_K_ENERGY, [&] { return launch_energy_assemble(ctx, s); }));
+  return AFQ_OK;
+}
+
+int free_walkers(afq_ctx* ctx) {
+  free_walker_set(ctx->ws);
+  dfree(&ctx->xi);
+  dfree(&ctx->xbar);
+  dfree(&ctx->y);
+  dfree(&ctx->cfb);
+  dfree(&ctx->cmf);
+  dfree(&ctx->A);
+  dfree(&ctx->detR);
+  ctx->have_walkers = false;
+  return AFQ_OK;
+}
+
+int free_trial(afq_ctx* ctx) {
+  dfree(&ctx->psiT);
+  dfree(&ctx->Lt);
+  dfree(&ctx->ht);
+  dfree(&ctx->vbar);
+  dfree(&ctx->hpp);
+  dfree(&ctx->P);
+  ctx->have_trial = false;
+  return free_walkers(ctx);
+}
+
+bool symmetric(const double* a, int M, double* dev_out) {
+  double mx = 0.0, dv = 0.0;
+  for (int p = 0; p < M; ++p)
+    for (int q = 0; q < M; ++q) {
+      mx = std::fmax(mx, std::fabs(a[(size_t)p * M + q]));
+      if (q > p) dv = std::fmax(dv, std::fabs(a[(size_t)p * M + q] - a[(size_t)q * M + p]));
+    }
+  *dev_out = dv;
+  return dv <= 1e-12 * (mx > 0.0 ? mx : 1.0) && std::isfinite(mx);
+}
+
+// One hybrid-propagation step (Sec. "Review of AFQMC") on the context's stream.
+int one_step(afq_ctx* ctx, const double* xi_dev) {
+  const double log_const = -ctx->p.dt * (ctx->e0 - 0.5 * ctx->sum_vbar2 - ctx->e_shift);
+  const uint64_t step = ctx->step;
+  AFQ_TRY(timed(ctx, AFQ_K_FIELDS, [&] { return launch_fields(ctx, xi_dev, step); }));
+  AFQ_TRY(timed(ctx, AFQ_K_VHS, [&] { return launch_vhs_fp64(ctx); }));
+  AFQ_TRY(timed(ctx, AFQ_K_PROPAGATE, [&] { return launch_propagate_fp64(ctx); }));
+  AFQ_TRY(green_and_bias(ctx, ctx->ws));
+  AFQ_TRY(timed(ctx, AFQ_K_WEIGHTS, [&] { return launch_weights(ctx, log_const); }));
+  ctx->step++;
+  if (ctx->p.qr_period > 0 && ctx->step % (uint64_t)ctx->p.qr_period == 0)
+    AFQ_TRY(timed(ctx, AFQ_K_QR, [&] { return launch_qr(ctx, ctx->ws, ctx->A); }));
+  return AFQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void afq_default_params(afq_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dt = 0.005;
+  p->taylor_order = 6;
+  p->qr_period = 5;
+  p->seed = 1;
+  p->precision = AFQ_FP64;
+  p->has_e_shift = 0;
+  p->e_shift = 0.0;
+  p->fb_cap = 0.0;
+  p->free_projection = 0;
+}
+
+int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
+  if (!out) return AFQ_ERR_ARG;
+  *out = nullptr;
+  afq_ctx* ctx = new (std::nothrow) afq_ctx();
+  if (!ctx) return AFQ_ERR_NOMEM;
+  if (params) {
+    ctx->p = *params;
+  } else {
+    afq_default_params(&ctx->p);
+  }
+  if (!(ctx->p.dt > 0.0) || ctx->p.taylor_order < 1 || ctx->p.taylor_order > 32 ||
+      ctx->p.qr_period < 0 || ctx->p.precision != AFQ_FP64) {
+    delete ctx;
+    return AFQ_ERR_ARG;
+  }
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    delete ctx;
+    return AFQ_ERR_CUDA;
+  }
+  if (cudaMalloc((void**)&ctx->flags, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->flags, 0, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&ctx->emix, sizeof(double)) != cudaSuccess) {
+    cudaFree(ctx->flags);
+    delete ctx;
+    return AFQ_ERR_CUDA;
+  }
+  *out = ctx;
+  return AFQ_OK;
+}
+
+int afq_destroy(afq_ctx* ctx) {
+  if (!ctx) return AFQ_ERR_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  free_trial(ctx);
+  dfree(&ctx->h1);
+  dfree(&ctx->L);
+  dfree(&ctx->Lpk);
+  dfree(&ctx->tpq);
+  dfree(&ctx->flags);
+  dfree(&ctx->emix);
+  dfree(&ctx->scratch);
+  for (auto& r : ctx->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  delete ctx;
+  return AFQ_OK;
+}
+
+const char* afq_last_error(const afq_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int afq_init_hamiltonian(afq_ctx* ctx, int M, int X, const double* h1, const double* L, double e0) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!h1 || !L) return afq_fail(ctx, AFQ_ERR_ARG, "h1 and L must not be NULL");
+  if (M < 1 || M > AFQ_MMAX) return afq_fail(ctx, AFQ_ERR_ARG, "M out of range [1, 1024]");
+  if (X < 1) return afq_fail(ctx, AFQ_ERR_ARG, "X must be >= 1");
+  if (!std::isfinite(e0)) return afq_fail(ctx, AFQ_ERR_ARG, "e0 not finite");
+  double dv;
+  if (!symmetric(h1, M, &dv))
+    return afq_fail(ctx, AFQ_ERR_ARG, "h1 not symmetric (max |h - h^T| = " + std::to_string(dv) + ")");
+  for (int g = 0; g < X; ++g)
+    if (!symmetric(L + (size_t)g * M * M, M, &dv))
+      return afq_fail(ctx, AFQ_ERR_ARG, "L_" + std::to_string(g) + " not symmetric");
+  free_trial(ctx);
+  ctx->M = M;
+  ctx->X = X;
+  ctx->Mp = M * (M + 1) / 2;
+  ctx->e0 = e0;
+  const size_t MM = (size_t)M * M;
+  AFQ_TRY(dalloc(ctx, &ctx->h1, MM));
+  AFQ_TRY(dalloc(ctx, &ctx->L, (size_t)X * MM));
+  AFQ_TRY(dalloc(ctx, &ctx->Lpk, (size_t)X * ctx->Mp));
+  AFQ_TRY(dalloc(ctx, &ctx->tpq, (size_t)ctx->Mp));
+  std::vector<int2> tpq(ctx->Mp);
+  for (int p = 0, t = 0; p < M; ++p)
+    for (int q = p; q < M; ++q) tpq[t++] = make_int2(p, q);
+  AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->h1, h1, MM * 8, cudaMemcpyHostToDevice, ctx->stream));
+  AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->L, L, (size_t)X * MM * 8, cudaMemcpyHostToDevice, ctx->stream));
+  AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->tpq, tpq.data(), tpq.size() * sizeof(int2),
+                                cudaMemcpyHostToDevice, ctx->stream));
+  AFQ_TRY(launch_pack_L(ctx));
+  AFQ_TRY(sync(ctx));
+  ctx->have_ham = true;
+  return AFQ_OK;
+}
+
+int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a, const double* psi_b) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_ham) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_hamiltonian first");
+  if (na < 0 || nb < 0 || na > AFQ_NMAX || nb > AFQ_NMAX || na + nb < 1)
+    return afq_fail(ctx, AFQ_ERR_ARG, "need 0 <= na, nb <= 64 and na + nb >= 1");
+  if (na > ctx->M || nb > ctx->M) return afq_fail(ctx, AFQ_ERR_ARG, "more electrons than orbitals");
+  if ((na && !psi_a) || (nb && !psi_b)) return afq_fail(ctx, AFQ_ERR_ARG, "trial pointer NULL");
+  free_trial(ctx);
+  const int M = ctx->M, X = ctx->X, N = na + nb;
+  ctx->na = na;
+  ctx->nb = nb;
+  ctx->N = N;
+  ctx->ex_groups = (X + exchange_group_size(na > nb ? na : nb) - 1) / exchange_group_size(na > nb ? na : nb);
+  const size_t MM = (size_t)M * M;
+  std::vector<double> psiT((size_t)N * M);
+  for (int p = 0; p < M; ++p) {
+    for (int i = 0; i < na; ++i) psiT[(size_t)i * M + p] = psi_a[(size_t)p * na + i];
+    for (int i = 0; i < nb; ++i) psiT[(size_t)(na + i) * M + p] = psi_b[(size_t)p * nb + i];
+  }
+  for (double v : psiT)
+    if (!std::isfinite(v)) return afq_fail(ctx, AFQ_ERR_ARG, "trial not finite");
+  AFQ_TRY(dalloc(ctx, &ctx->psiT, (size_t)N * M));
+  AFQ_TRY(dalloc(ctx, &ctx->Lt, (size_t)X * N * M));
+  AFQ_TRY(dalloc(ctx, &ctx->ht, (size_t)N * M));
+  AFQ_TRY(dalloc(ctx, &ctx->vbar, (size_t)X));
+  AFQ_TRY(dalloc(ctx, &ctx->hpp, MM));
+  AFQ_TRY(dalloc(ctx, &ctx->P, MM));
+  AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->psiT, psiT.data(), psiT.size() * 8, cudaMemcpyHostToDevice,
+                                ctx->stream));
+  // L~_g = Psi^T L_g (N x M per g) and h~ = Psi^T h1
+  AFQ_TRY(launch_dgemm(ctx, N, M, M, 1.0, ctx->psiT, M, 1, 0, ctx->L, M, 1, (long)MM, 0.0, ctx->Lt,
+                       M, 1, (long)N * M, X, 1));
+  AFQ_TRY(launch_dgemm(ctx, N, M, M, 1.0, ctx->psiT, M, 1, 0, ctx->h1, M, 1, 0, 0.0, ctx->ht, M,
+                       1, 0, 1, 1));
+  AFQ_TRY(launch_vbar(ctx));
+  // sum_g L_g L_g as one GEMM over k = (g, r): A(p, k) = L[k M + p] (L_g symmetric)
+  const int tiles = ((M + 31) / 32) * ((M + 31) / 32);
+  int ksplit = (600 + tiles - 1) / tiles;
+  if (ksplit > X * M / 64) ksplit = X * M / 64 > 0 ? X * M / 64 : 1;
+  if (ksplit > 256) ksplit = 256;
+  double* s2part = nullptr;
+  AFQ_TRY(dalloc(ctx, &s2part, (size_t)ksplit * MM));
+  int rc = launch_dgemm(ctx, M, M, X * M, 1.0, ctx->L, 1, M, 0, ctx->L, M, 1, 0, 0.0, s2part, M, 1,
+                        (long)MM, 1, ksplit);
+  if (rc == AFQ_OK) rc = launch_hpp(ctx, s2part, ksplit);
+  if (rc == AFQ_OK) rc = sync(ctx);
+  dfree(&s2part);
+  AFQ_TRY(rc);
+  // P = exp(-dt h''/2) by scaling and squaring of a degree-18 Taylor polynomial
+  std::vector<double> hpp(MM), vbar(X);
+  AFQ_CUDA(ctx, cudaMemcpy(hpp.data(), ctx->hpp, MM * 8, cudaMemcpyDeviceToHost));
+  AFQ_CUDA(ctx, cudaMemcpy(vbar.data(), ctx->vbar, (size_t)X * 8, cudaMemcpyDeviceToHost));
+  ctx->sum_vbar2 = 0.0;
+  for (double v : vbar) ctx->sum_vbar2 += v * v;
+  double norm1 = 0.0;
+  for (int q = 0; q < M; ++q) {
+    double s = 0.0;
+    for (int p = 0; p < M; ++p) s += std::fabs(hpp[(size_t)p * M + q]);
+    norm1 = std::fmax(norm1, s);
+  }
+  norm1 *= 0.5 * ctx->p.dt;
+  if (!std::isfinite(norm1)) return afq_fail(ctx, AFQ_ERR_NAN, "h'' not finite");
+  int sq = 0;
+  while (norm1 / std::ldexp(1.0, sq) > 0.5) ++sq;
+  double *Bm = nullptr, *E = nullptr, *T = nullptr;
+  rc = dalloc(ctx, &Bm, MM);
+  if (rc == AFQ_OK) rc = dalloc(ctx, &E, MM);
+  if (rc == AFQ_OK) rc = dalloc(ctx, &T, MM);
+  if (rc == AFQ_OK) rc = launch_axpby(ctx, (int)MM, -0.5 * ctx->p.dt / std::ldexp(1.0, sq), ctx->hpp, 0.0, Bm);
+  if (rc == AFQ_OK) rc = launch_set_identity(ctx, M, E);
+  for (int k = 18; k >= 1 && rc == AFQ_OK; --k) {
+    rc = launch_set_identity(ctx, M, T);
+    if (rc == AFQ_OK)
+      rc = launch_dgemm(ctx, M, M, M, 1.0 / k, Bm, M, 1, 0, E, M, 1, 0, 1.0, T, M, 1, 0, 1, 1);
+    std::swap(E, T);
+  }
+  for (int k = 0; k < sq && rc == AFQ_OK; ++k) {
+    rc = launch_dgemm(ctx, M, M, M, 1.0, E, M, 1, 0, E, M, 1, 0, 0.0, T, M, 1, 0, 1, 1);
+    std::swap(E, T);
+  }
+  if (rc == AFQ_OK)
+    rc = cudaMemcpyAsync(ctx->P, E, MM * 8, cudaMemcpyDeviceToDevice, ctx->stream) == cudaSuccess
+             ? AFQ_OK
+             : afq_fail(ctx, AFQ_ERR_CUDA, "copy P");
+  if (rc == AFQ_OK) rc = sync(ctx);
+  dfree(&Bm);
+  dfree(&E);
+  dfree(&T);
+  AFQ_TRY(rc);
+  ctx->have_trial = true;
+  // trial energy: the energy kernels on a one-walker set equal to the trial
+  WalkerSet t;
+  rc = alloc_walker_set(ctx, t, 1);
+  std::vector<double2> phi((size_t)M * N);
+  for (int p = 0; p < M; ++p)
+    for (int j = 0; j < N; ++j) phi[(size_t)p * N + j] = make_double2(psiT[(size_t)j * M + p], 0.0);
+  if (rc == AFQ_OK)
+    rc = cudaMemcpyAsync(t.phi, phi.data(), phi.size() * 16, cudaMemcpyHostToDevice, ctx->stream) ==
+                 cudaSuccess
+             ? AFQ_OK
+             : afq_fail(ctx, AFQ_ERR_CUDA, "copy trial");
+  if (rc == AFQ_OK) rc = green_and_bias(ctx, t);
+  if (rc == AFQ_OK) rc = energy_kernels(ctx, t);
+  double2 e[4];
+  if (rc == AFQ_OK)
+    rc = cudaMemcpyAsync(e, t.energy, sizeof(e), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess
+             ? AFQ_OK
+             : afq_fail(ctx, AFQ_ERR_CUDA, "copy energy");
+  if (rc == AFQ_OK) rc = sync(ctx);
+  free_walker_set(t);
+  AFQ_TRY(rc);
+  AFQ_TRY(check_flags(ctx));
+  ctx->e_trial = e[3].x;
+  ctx->e_shift = ctx->p.has_e_shift ? ctx->p.e_shift : ctx->e_trial;
+  return AFQ_OK;
+}
+
+int afq_trial_energy(afq_ctx* ctx, double* e_out) {
+  if (!ctx || !e_out) return AFQ_ERR_ARG;
+  if (!ctx->have_trial) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_trial first");
+  *e_out = ctx->e_trial;
+  return AFQ_OK;
+}
+
+int afq_init_walkers(afq_ctx* ctx, int W, const double* phi, const double* w) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_trial) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_trial first");
+  if (W < 1 || W > (1 << 24)) return afq_fail(ctx, AFQ_ERR_ARG, "W out of range");
+  free_walkers(ctx);
+  const size_t M = ctx->M, N = ctx->N, X = ctx->X;
+  AFQ_TRY(alloc_walker_set(ctx, ctx->ws, W));
+  AFQ_TRY(dalloc(ctx, &ctx->xi, W * X));
+  AFQ_TRY(dalloc(ctx, &ctx->xbar, W * X));
+  AFQ_TRY(dalloc(ctx, &ctx->y, W * X));
+  AFQ_TRY(dalloc(ctx, &ctx->cfb, (size_t)W));
+  AFQ_TRY(dalloc(ctx, &ctx->cmf, (size_t)W));
+  // A holds i sqrt(dt) V per walker during a step and is the QR workspace after it
+  AFQ_TRY(dalloc(ctx, &ctx->A, (size_t)W * M * (M > N ? M : N)));
+  AFQ_TRY(dalloc(ctx, &ctx->detR, 2 * (size_t)W));
+  AFQ_CUDA(ctx, cudaMemsetAsync(ctx->xbar, 0, W * X * 16, ctx->stream));
+  std::vector<double2> h;
+  if (phi) {
+    AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->ws.phi, phi, W * M * N * 16, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+  } else {
+    std::vector<double> psiT(N * M);
+    AFQ_CUDA(ctx, cudaMemcpy(psiT.data(), ctx->psiT, N * M * 8, cudaMemcpyDeviceToHost));
+    h.resize(W * M * N);
+    for (int z = 0; z < W; ++z)
+      for (size_t p = 0; p < M; ++p)
+        for (size_t j = 0; j < N; ++j) h[(z * M + p) * N + j] = make_double2(psiT[j * M + p], 0.0);
+    AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->ws.phi, h.data(), h.size() * 16, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+  }
+  std::vector<double2> wv(W);
+  for (int z = 0; z < W; ++z) wv[z] = make_double2(w ? w[z] : 1.0, 0.0);
+  AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->ws.w, wv.data(), W * 16, cudaMemcpyHostToDevice, ctx->stream));
+  AFQ_TRY(green_and_bias(ctx, ctx->ws));
+  AFQ_TRY(launch_init_overlap(ctx, ctx->ws));
+  AFQ_TRY(sync(ctx));
+  ctx->step = 0;
+  ctx->have_walkers = true;
+  return check_flags(ctx);
+}
+
+static int propagate_impl(afq_ctx* ctx, const double* fields, int nsteps, bool dev) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  if (nsteps < 0) return afq_fail(ctx, AFQ_ERR_ARG, "nsteps < 0");
+  const size_t WX = (size_t)ctx->ws.W * ctx->X;
+  for (int k = 0; k < nsteps; ++k) {
+    const double* xi = nullptr;
+    if (fields && dev) {
+      xi = fields + k * WX;
+    } else if (fields) {
+      AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->xi, fields + k * WX, WX * 8, cudaMemcpyHostToDevice,
+                                    ctx->stream));
+      xi = ctx->xi;
+    }
+    AFQ_TRY(one_step(ctx, xi));
+  }
+  if (dev) return AFQ_OK;
+  return check_flags(ctx);
+}
+
+int afq_propagate(afq_ctx* ctx, const double* fields, int nsteps) {
+  return propagate_impl(ctx, fields, nsteps, false);
+}
+
+int afq_propagate_dev(afq_ctx* ctx, const double* fields_dev, int nsteps) {
+  return propagate_impl(ctx, fields_dev, nsteps, true);
+}
+
+static int energy_impl(afq_ctx* ctx) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  AFQ_TRY(energy_kernels(ctx, ctx->ws));
+  AFQ_TRY(timed(ctx, AFQ_K_ENERGY, [&] { return launch_emix(ctx, ctx->ws, ctx->emix); }));
+  return AFQ_OK;
+}
+
+int afq_local_energy(afq_ctx* ctx, double* e_out, double* e_mix) {
+  AFQ_TRY(energy_impl(ctx));
+  if (e_out)
+    AFQ_CUDA(ctx, cudaMemcpyAsync(e_out, ctx->ws.energy, (size_t)ctx->ws.W * 4 * 16,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  if (e_mix)
+    AFQ_CUDA(ctx, cudaMemcpyAsync(e_mix, ctx->emix, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  AFQ_TRY(sync(ctx));
+  return check_flags(ctx);
+}
+
+int afq_local_energy_dev(afq_ctx* ctx, double* e_out_dev, double* e_mix_dev) {
+  AFQ_TRY(energy_impl(ctx));
+  if (e_out_dev)
+    AFQ_CUDA(ctx, cudaMemcpyAsync(e_out_dev, ctx->ws.energy, (size_t)ctx->ws.W * 4 * 16,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  if (e_mix_dev)
+    AFQ_CUDA(ctx, cudaMemcpyAsync(e_mix_dev, ctx->emix, 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  return AFQ_OK;
+}
+
+int afq_orthogonalise(afq_ctx* ctx) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  AFQ_TRY(timed(ctx, AFQ_K_QR, [&] { return launch_qr(ctx, ctx->ws, ctx->A); }));
+  AFQ_TRY(sync(ctx));
+  return check_flags(ctx);
+}
+
+static int get_impl(afq_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (!ctx || !dst) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  AFQ_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  return sync(ctx);
+}
+
+int afq_get_walkers(afq_ctx* ctx, double* phi) {
+  if (!ctx) return AFQ_ERR_ARG;
+  return get_impl(ctx, phi, ctx->ws.phi, (size_t)ctx->ws.W * ctx->M * ctx->N * 16);
+}
+int afq_get_weights(afq_ctx* ctx, double* w) {
+  if (!ctx) return AFQ_ERR_ARG;
+  return get_impl(ctx, w, ctx->ws.w, (size_t)ctx->ws.W * 16);
+}
+int afq_get_overlaps(afq_ctx* ctx, double* o) {
+  if (!ctx) return AFQ_ERR_ARG;
+  return get_impl(ctx, o, ctx->ws.ovlp, (size_t)ctx->ws.W * 16);
+}
+int afq_get_force_bias(afq_ctx* ctx, double* xbar) {
+  if (!ctx) return AFQ_ERR_ARG;
+  return get_impl(ctx, xbar, ctx->xbar, (size_t)ctx->ws.W * ctx->X * 16);
+}
+int afq_get_step(afq_ctx* ctx, uint64_t* step) {
+  if (!ctx || !step) return AFQ_ERR_ARG;
+  *step = ctx->step;
+  return AFQ_OK;
+}
+
+int afq_set_state(afq_ctx* ctx, const double* phi, const double* w, const double* ovlp,
+                  uint64_t step) {
+  if (!ctx || !phi || !w) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  const size_t W = ctx->ws.W;
+  AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->ws.phi, phi, W * ctx->M * ctx->N * 16, cudaMemcpyHostToDevice,
+                                ctx->stream));
+  AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->ws.w, w, W * 16, cudaMemcpyHostToDevice, ctx->stream));
+  AFQ_TRY(green_and_bias(ctx, ctx->ws));
+  if (ovlp) {
+    AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->ws.ovlp, ovlp, W * 16, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    AFQ_TRY(launch_init_overlap(ctx, ctx->ws));
+  }
+  ctx->step = step;
+  AFQ_TRY(sync(ctx));
+  return check_flags(ctx);
+}
+
+int afq_philox_fields(afq_ctx* ctx, uint64_t step, double* out) {
+  if (!ctx || !out) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  double* d = nullptr;
+  AFQ_TRY(dalloc(ctx, &d, (size_t)ctx->ws.W * ctx->X));
+  int rc = launch_philox_fields(ctx, step, d, nullptr);
+  if (rc == AFQ_OK)
+    rc = cudaMemcpyAsync(out, d, (size_t)ctx->ws.W * ctx->X * 8, cudaMemcpyDeviceToHost,
+                         ctx->stream) == cudaSuccess
+             ? AFQ_OK
+             : afq_fail(ctx, AFQ_ERR_CUDA, "copy fields");
+  if (rc == AFQ_OK) rc = sync(ctx);
+  dfree(&d);
+  return rc;
+}
+
+int afq_philox_words(afq_ctx* ctx, uint64_t step, uint32_t* out) {
+  if (!ctx || !out) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  const size_t n = (size_t)ctx->ws.W * ((ctx->X + 1) / 2) * 4;
+  uint32_t* d = nullptr;
+  AFQ_TRY(dalloc(ctx, &d, n));
+  int rc = launch_philox_fields(ctx, step, nullptr, d);
+  if (rc == AFQ_OK)
+    rc = cudaMemcpyAsync(out, d, n * 4, cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess
+             ? AFQ_OK
+             : afq_fail(ctx, AFQ_ERR_CUDA, "copy words");
+  if (rc == AFQ_OK) rc = sync(ctx);
+  dfree(&d);
+  return rc;
+}
+
+int afq_profile_enable(afq_ctx* ctx, int on) {
+  if (!ctx) return AFQ_ERR_ARG;
+  AFQ_TRY(drain_profile(ctx));
+  if (on)
+    for (int k = 0; k < AFQ_K_COUNT; ++k) {
+      ctx->prof_ms[k] = 0.0;
+      ctx->prof_n[k] = 0;
+    }
+  ctx->profiling = on != 0;
+  return AFQ_OK;
+}
+
+int afq_profile_read(afq_ctx* ctx, int kernel, double* total_ms, uint64_t* launches) {
+  if (!ctx || kernel < 0 || kernel >= AFQ_K_COUNT) return AFQ_ERR_ARG;
+  AFQ_TRY(drain_profile(ctx));
+  if (total_ms) *total_ms = ctx->prof_ms[kernel];
+  if (launches) *launches = ctx->prof_n[kernel];
+  return AFQ_OK;
+}
+
+const char* afq_kernel_name(int kernel) {
+  static const char* names[AFQ_K_COUNT] = {"fields", "vhs", "propagate", "overlap_theta",
+                                           "force_bias", "weights", "qr", "exchange", "energy"};
+  return kernel >= 0 && kernel < AFQ_K_COUNT ? names[kernel] : nullptr;
+}
+
+int afq_launch_count(afq_ctx* ctx, uint64_t* count) {
+  if (!ctx || !count) return AFQ_ERR_ARG;
+  *count = ctx->launches;
+  return AFQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Internal declarations of libafqmc: the context, device buffers, complex helpers
+// and the host-side launch wrappers of every kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "afqmc.h"
+
+#define AFQ_NMAX 64    // electrons per spin
+#define AFQ_MMAX 1024  // orbitals
+
+// ----------------------------------------------------------------------------
+// complex helpers (double2 = re, im)
+// ----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return cmk(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return cmk(a.x, -a.y); }
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double cabs(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  // a / b with scaling by the larger component of b
+  double s = fabs(b.x) > fabs(b.y) ? fabs(b.x) : fabs(b.y);
+  double2 bs = cmk(b.x / s, b.y / s);
+  double d = bs.x * bs.x + bs.y * bs.y;
+  double2 n = cmul(a, cconj(bs));
+  return cmk(n.x / (d * s), n.y / (d * s));
+}
+__device__ __forceinline__ double2 cexp(double2 a) {
+  double e = exp(a.x), s, c;
+  sincos(a.y, &s, &c);
+  return cmk(e * c, e * s);
+}
+
+// ----------------------------------------------------------------------------
+// walker-set buffers: everything the overlap / force-bias / energy kernels need
+// ----------------------------------------------------------------------------
+struct WalkerSet {
+  int W = 0;
+  double2* phi = nullptr;     // W x M x N   walker matrices, alpha columns first
+  double2* thetaT = nullptr;  // W x N x M   theta^T = (Phi S^-1)^T per spin block
+  double2* det = nullptr;     // W x 2       det(Psi_s^T Phi_s)
+  double2* e1 = nullptr;      // W x 2       one-body energy per spin
+  double2* c = nullptr;       // W x X       Coulomb vector / mixed <v_g>
+  double2* ekp = nullptr;     // W x 2 x G   exchange partial sums per g-group
+  double2* energy = nullptr;  // W x 4       E1, EJ, EK, E_L
+  double2* w = nullptr;       // W           weights
+  double2* ovlp = nullptr;    // W           stored overlaps
+};
+
+struct afq_ctx {
+  afq_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  uint64_t launches = 0;
+
+  int M = 0, X = 0, na = 0, nb = 0, N = 0, Mp = 0;
+  double e0 = 0.0, e_trial = 0.0, e_shift = 0.0, sum_vbar2 = 0.0;
+  bool have_ham = false, have_trial = false, have_walkers = false;
+  uint64_t step = 0;
+  int ex_groups = 0;  // number of g-groups of the exchange kernel
+
+  // Hamiltonian
+  double* h1 = nullptr;   // M x M
+  double* L = nullptr;    // X x M x M (kept for the trial set-up and gradients)
+  double* Lpk = nullptr;  // X x Mp packed upper triangles, Mp = M (M + 1) / 2
+  int2* tpq = nullptr;    // Mp packed index -> (p, q), p <= q
+  // trial
+  double* psiT = nullptr;  // N x M   rows: alpha orbitals then beta orbitals
+  double* Lt = nullptr;    // X x N x M half-rotated Cholesky vectors
+  double* ht = nullptr;    // N x M   Psi^T h1
+  double* vbar = nullptr;  // X
+  double* hpp = nullptr;   // M x M   h''
+  double* P = nullptr;     // M x M   exp(-dt h''/2)
+  // walkers
+  WalkerSet ws;
+  double* xi = nullptr;      // W x X fields of the current step
+  double2* xbar = nullptr;   // W x X
+  double2* y = nullptr;      // W x X shifted fields
+  double2* cfb = nullptr;    // W
+  double2* cmf = nullptr;    // W
+  double2* A = nullptr;      // W x M x M  i sqrt(dt) V, symmetric
+  double* detR = nullptr;    // W x 2
+  double* emix = nullptr;    // 1
+  int* flags = nullptr;      // [0] singular pivots, [1] non-finite values
+  double* scratch = nullptr; // set-up workspace
+  size_t scratch_bytes = 0;
+
+  // built-in profiler: event pairs around launches of each kernel class
+  bool profiling = false;
+  struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> event_pool;
+  double prof_ms[AFQ_K_COUNT] = {};
+  uint64_t prof_n[AFQ_K_COUNT] = {};
+};
+
+// status helpers -------------------------------------------------------------
+int afq_fail(afq_ctx* ctx, int code, const std::string& msg);
+#define AFQ_CUDA(ctx, call)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return afq_fail(ctx, AFQ_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define AFQ_LAUNCHED(ctx)                                                                \
+  do {                                                                                   \
+    (ctx)->launches++;                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess)                                                               \
+      return afq_fail(ctx, AFQ_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ----------------------------------------------------------------------------
+// launch wrappers (each returns AFQ_OK or an error code via afq_fail)
+// ----------------------------------------------------------------------------
+// set-up (k_setup.cu)
+int launch_dgemm(afq_ctx* ctx, int m, int n, int k, double alpha, const double* A, long sam,
+                 long sak, long sab, const double* B, long sbk, long sbn, long sbb, double beta,
+                 double* C, long scm, long scn, long scb, int batch, int ksplit);
+int launch_pack_L(afq_ctx* ctx);
+int launch_vbar(afq_ctx* ctx);
+int launch_hpp(afq_ctx* ctx, const double* s2part, int ksplit);
+int launch_axpby(afq_ctx* ctx, int n, double a, const double* x, double b, double* y);
+int launch_set_identity(afq_ctx* ctx, int M, double* out);
+
+// walker kernels (k_walkers.cu)
+int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s);
+int launch_force_bias_fp64(afq_ctx* ctx, WalkerSet& s);
+int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s);
+int launch_energy_assemble(afq_ctx* ctx, WalkerSet& s);
+int launch_qr(afq_ctx* ctx, WalkerSet& s, double2* Qw);  // Qw: W x N x M workspace
+int exchange_group_size(int nmax);
+int launch_init_overlap(afq_ctx* ctx, WalkerSet& s);
+
+// step kernels (k_step.cu)
+int launch_fields(afq_ctx* ctx, const double* xi_dev, uint64_t step);
+int launch_philox_fields(afq_ctx* ctx, uint64_t step, double* out, uint32_t* words);
+int launch_vhs_fp64(afq_ctx* ctx);
+int launch_propagate_fp64(afq_ctx* ctx);
+int launch_weights(afq_ctx* ctx, double log_const);
+int launch_emix(afq_ctx* ctx, WalkerSet& s, double* out);

@@ -1,0 +1,423 @@
+// Step kernels of libafqmc: auxiliary fields and force bias, the VHS build, the
+// Taylor propagator with the one-body halves, and the phaseless weight update
+// (Sec. "Review of AFQMC": hybrid propagation, Eqs. import, ovl, ph and theta).
+#include "afq_internal.cuh"
+
+namespace {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): multipliers M0, M1, Weyl key
+// increments W0, W1, ten rounds; written here from that definition.
+constexpr uint32_t PH_M0 = 0xD2511F53u, PH_M1 = 0xCD9E8D57u;
+constexpr uint32_t PH_W0 = 0x9E3779B9u, PH_W1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox_block(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += PH_W0;
+      k1 += PH_W1;
+    }
+    const uint32_t lo0 = PH_M0 * c.x, hi0 = __umulhi(PH_M0, c.x);
+    const uint32_t lo1 = PH_M1 * c.z, hi1 = __umulhi(PH_M1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// counter (step mod 2^32, walker, pair, step >> 32), key (seed mod 2^32, seed >> 32)
+__device__ __forceinline__ uint4 field_words(uint64_t step, uint32_t z, uint32_t m, uint64_t seed) {
+  return philox_block(make_uint4((uint32_t)step, z, m, (uint32_t)(step >> 32)), (uint32_t)seed,
+                      (uint32_t)(seed >> 32));
+}
+
+// 53-bit uniform in (0, 1] from two words: ((a >> 5) 2^26 + (b >> 6) + 1) 2^-53
+__device__ __forceinline__ double uniform53(uint32_t a, uint32_t b) {
+  const uint64_t k = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+  return (double)(k + 1) * 0x1p-53;
+}
+
+// Box-Muller: the two N(0,1) fields of one (walker, pair)
+__device__ __forceinline__ void field_pair(uint64_t step, uint32_t z, uint32_t m, uint64_t seed,
+                                           double* g0, double* g1) {
+  const uint4 w = field_words(step, z, m, seed);
+  const double u1 = uniform53(w.x, w.y), u2 = uniform53(w.z, w.w);
+  const double r = sqrt(-2.0 * log(u1));
+  const double ang = 6.283185307179586 * u2;
+  double sn, cs;
+  sincos(ang, &sn, &cs);
+  *g0 = r * cs;
+  *g1 = r * sn;
+}
+
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+__device__ double2 block_sum2(double2 v, double2* red) {
+  v = warp_sum2(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double2 s = cmk(0.0, 0.0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s = cadd(s, red[i]);
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// K3: fields xi (given or Philox), force bias xbar = -i sqrt(dt) (c - vbar) with
+// optional cap, shifted fields y = xi - xbar, cfb = sum (xi xbar - xbar^2/2) and
+// cmf = -i sqrt(dt) sum y vbar.  One CTA per walker.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fields(int X, double sdt, double cap,
+                                                const double* __restrict__ xi_in, uint64_t seed,
+                                                uint64_t step, const double2* __restrict__ c,
+                                                const double* __restrict__ vbar,
+                                                double2* __restrict__ xbar, double2* __restrict__ y,
+                                                double2* __restrict__ cfb,
+                                                double2* __restrict__ cmf) {
+  __shared__ double2 red[8];
+  const int z = blockIdx.x;
+  const int npair = (X + 1) / 2;
+  double2 sfb = cmk(0.0, 0.0), smf = cmk(0.0, 0.0);
+  for (int m = threadIdx.x; m < npair; m += 256) {
+    double xi2[2];
+    if (xi_in) {
+      xi2[0] = xi_in[(long)z * X + 2 * m];
+      xi2[1] = 2 * m + 1 < X ? xi_in[(long)z * X + 2 * m + 1] : 0.0;
+    } else {
+      field_pair(step, (uint32_t)z, (uint32_t)m, seed, &xi2[0], &xi2[1]);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = 2 * m + h;
+      if (g < X) {
+        const double2 cz = c[(long)z * X + g];
+        const double vb = vbar[g];
+        double2 xb = cmk(sdt * cz.y, -sdt * (cz.x - vb));
+        if (cap > 0.0) {
+          const double mag = hypot(xb.x, xb.y);
+          if (mag > cap) xb = cscale(xb, cap / mag);
+        }
+        const double x = xi2[h];
+        const double2 yy = cmk(x - xb.x, -xb.y);
+        const double2 xb2 = cmul(xb, xb);
+        sfb = cadd(sfb, cmk(x * xb.x - 0.5 * xb2.x, x * xb.y - 0.5 * xb2.y));
+        smf = cadd(smf, cscale(yy, vb));
+        xbar[(long)z * X + g] = xb;
+        y[(long)z * X + g] = yy;
+      }
+    }
+  }
+  sfb = block_sum2(sfb, red);
+  smf = block_sum2(smf, red);
+  if (threadIdx.x == 0) {
+    cfb[z] = sfb;
+    cmf[z] = cmk(sdt * smf.y, -sdt * smf.x);
+  }
+}
+
+__global__ void k_philox_fields(int W, int X, uint64_t seed, uint64_t step, double* out,
+                                uint32_t* words) {
+  const int npair = (X + 1) / 2;
+  const long total = (long)W * npair;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int z = (int)(e / npair), m = (int)(e % npair);
+    if (words) {
+      const uint4 w = field_words(step, z, m, seed);
+      words[4 * e + 0] = w.x;
+      words[4 * e + 1] = w.y;
+      words[4 * e + 2] = w.z;
+      words[4 * e + 3] = w.w;
+    }
+    if (out) {
+      double g0, g1;
+      field_pair(step, z, m, seed, &g0, &g1);
+      out[(long)z * X + 2 * m] = g0;
+      if (2 * m + 1 < X) out[(long)z * X + 2 * m + 1] = g1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4 (FP64): A_z = i sqrt(dt) sum_g y_zg L_g over the packed upper triangle,
+// written to both triangles of the dense symmetric W x M x M output.
+// ---------------------------------------------------------------------------
+constexpr int VZ = 8, VT = 64, VK = 32;
+__global__ void __launch_bounds__(256) k_vhs_fp64(int W, int X, int M, int Mp, double sdt,
+                                                  const double2* __restrict__ y,
+                                                  const double* __restrict__ Lpk,
+                                                  const int2* __restrict__ tpq,
+                                                  double2* __restrict__ A) {
+  __shared__ double2 Ys[VZ][VK];
+  __shared__ double Ls[VK][VT];
+  const int t0 = blockIdx.x * VT, z0 = blockIdx.y * VZ;
+  const int tz = threadIdx.x / 32, tt = threadIdx.x % 32;
+  double2 a0 = cmk(0.0, 0.0), a1 = cmk(0.0, 0.0);
+  for (int k0 = 0; k0 < X; k0 += VK) {
+    {
+      const int r = threadIdx.x / VK, kk = threadIdx.x % VK;
+      Ys[r][kk] = (z0 + r < W && k0 + kk < X) ? y[(long)(z0 + r) * X + k0 + kk] : cmk(0.0, 0.0);
+    }
+    for (int e = threadIdx.x; e < VK * VT; e += 256) {
+      const int kk = e / VT, cc = e % VT;
+      Ls[kk][cc] = (k0 + kk < X && t0 + cc < Mp) ? Lpk[(long)(k0 + kk) * Mp + t0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < VK; ++kk) {
+      const double2 yv = Ys[tz][kk];
+      const double l0 = Ls[kk][tt], l1 = Ls[kk][tt + 32];
+      a0.x = fma(yv.x, l0, a0.x);
+      a0.y = fma(yv.y, l0, a0.y);
+      a1.x = fma(yv.x, l1, a1.x);
+      a1.y = fma(yv.y, l1, a1.y);
+    }
+    __syncthreads();
+  }
+  const int z = z0 + tz;
+  if (z >= W) return;
+  double2* Az = A + (long)z * M * M;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int t = t0 + tt + 32 * h;
+    if (t < Mp) {
+      const double2 a = h ? a1 : a0;
+      const double2 v = cmk(-sdt * a.y, sdt * a.x);  // i sqrt(dt) a
+      const int2 pq = tpq[t];
+      Az[(long)pq.x * M + pq.y] = v;
+      if (pq.x != pq.y) Az[(long)pq.y * M + pq.x] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K5 (FP64): Phi_z[:, cols] <- P T_n(A_z) P Phi_z[:, cols] for a chunk of NC
+// columns.  One thread per orbital row p; P and A_z are symmetric, so row q of
+// each is read with the lanes running over p (coalesced), and the column chunk
+// of the current Taylor term is broadcast from shared memory.
+// ---------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ void sym_apply_real(int M, int p, const double* __restrict__ S,
+                                               const double2* __restrict__ in, double2 out[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c] = cmk(0.0, 0.0);
+  int q = 0;
+  for (; q + 4 <= M; q += 4) {
+    double s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] = S[(long)(q + u) * M + p];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double2 b = in[(q + u) * NC + c];
+        out[c].x = fma(s[u], b.x, out[c].x);
+        out[c].y = fma(s[u], b.y, out[c].y);
+      }
+  }
+  for (; q < M; ++q) {
+    const double sv = S[(long)q * M + p];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double2 b = in[q * NC + c];
+      out[c].x = fma(sv, b.x, out[c].x);
+      out[c].y = fma(sv, b.y, out[c].y);
+    }
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void sym_apply_cplx(int M, int p, const double2* __restrict__ S,
+                                               const double2* __restrict__ in, double2 out[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c] = cmk(0.0, 0.0);
+  int q = 0;
+  for (; q + 4 <= M; q += 4) {
+    double2 s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] = S[(long)(q + u) * M + p];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double2 b = in[(q + u) * NC + c];
+        out[c].x = fma(s[u].x, b.x, fma(-s[u].y, b.y, out[c].x));
+        out[c].y = fma(s[u].x, b.y, fma(s[u].y, b.x, out[c].y));
+      }
+  }
+  for (; q < M; ++q) {
+    const double2 sv = S[(long)q * M + p];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double2 b = in[q * NC + c];
+      out[c].x = fma(sv.x, b.x, fma(-sv.y, b.y, out[c].x));
+      out[c].y = fma(sv.x, b.y, fma(sv.y, b.x, out[c].y));
+    }
+  }
+}
+
+template <int NC>
+__global__ void k_propagate_fp64(int M, int N, int order, const double* __restrict__ P,
+                                 const double2* __restrict__ A, double2* __restrict__ phi) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* cur = reinterpret_cast<double2*>(smraw);  // M x NC
+  double2* nxt = cur + M * NC;
+  double2* acc = nxt + M * NC;
+  const int z = blockIdx.y, c0 = blockIdx.x * NC, p = threadIdx.x;
+  const double2* Az = A + (long)z * M * M;
+  double2* phz = phi + (long)z * M * N;
+  if (p < M)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      cur[p * NC + c] = c0 + c < N ? phz[(long)p * N + c0 + c] : cmk(0.0, 0.0);
+  __syncthreads();
+  double2 r[NC];
+  if (p < M) {
+    sym_apply_real<NC>(M, p, P, cur, r);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      acc[p * NC + c] = r[c];
+      nxt[p * NC + c] = r[c];
+    }
+  }
+  __syncthreads();
+  {
+    double2* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  for (int k = 1; k <= order; ++k) {
+    const double inv = 1.0 / k;
+    if (p < M) {
+      sym_apply_cplx<NC>(M, p, Az, cur, r);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const double2 t = cscale(r[c], inv);
+        nxt[p * NC + c] = t;
+        acc[p * NC + c] = cadd(acc[p * NC + c], t);
+      }
+    }
+    __syncthreads();
+    double2* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  if (p < M) {
+    sym_apply_real<NC>(M, p, P, acc, r);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (c0 + c < N) phz[(long)p * N + c0 + c] = r[c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K8: overlap ratio R = (O'/O) e^{cmf}, importance I = R e^{cfb} e^{log_const},
+// phaseless weight w <- w |I| max(0, cos arg R) (or w <- w I in free projection).
+// ---------------------------------------------------------------------------
+__global__ void k_weights(int W, double log_const, int free_proj, const double2* __restrict__ det,
+                          const double2* __restrict__ cfb, const double2* __restrict__ cmf,
+                          double2* __restrict__ ovlp, double2* __restrict__ w, int* flags) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= W) return;
+  const double2 onew = cmul(det[2 * z], det[2 * z + 1]);
+  const double2 ratio = cmul(cdiv(onew, ovlp[z]), cexp(cmf[z]));
+  const double2 imp = cmul(cmul(ratio, cexp(cfb[z])), cmk(exp(log_const), 0.0));
+  double2 wn;
+  if (free_proj) {
+    wn = cmul(w[z], imp);
+  } else {
+    const double cth = cos(atan2(ratio.y, ratio.x));
+    wn = cmk(w[z].x * cabs(imp) * (cth > 0.0 ? cth : 0.0), 0.0);
+  }
+  if (!isfinite(wn.x) || !isfinite(wn.y) || !isfinite(onew.x) || !isfinite(onew.y))
+    atomicAdd(&flags[1], 1);
+  w[z] = wn;
+  ovlp[z] = onew;
+}
+
+// sum_z w_z Re E_L,z / sum_z w_z (complex ratio, real part, in free projection)
+__global__ void __launch_bounds__(256) k_emix(int W, int free_proj, const double2* __restrict__ w,
+                                              const double2* __restrict__ energy,
+                                              double* __restrict__ out) {
+  __shared__ double2 red[8];
+  double2 num = cmk(0.0, 0.0), den = cmk(0.0, 0.0);
+  for (int z = threadIdx.x; z < W; z += 256) {
+    const double2 el = energy[4 * z + 3];
+    if (free_proj) {
+      num = cadd(num, cmul(w[z], el));
+      den = cadd(den, w[z]);
+    } else {
+      num.x += w[z].x * el.x;
+      den.x += w[z].x;
+    }
+  }
+  num = block_sum2(num, red);
+  den = block_sum2(den, red);
+  if (threadIdx.x == 0) out[0] = free_proj ? cdiv(num, den).x : num.x / den.x;
+}
+
+}  // namespace
+
+int launch_fields(afq_ctx* ctx, const double* xi_dev, uint64_t step) {
+  k_fields<<<ctx->ws.W, 256, 0, ctx->stream>>>(ctx->X, sqrt(ctx->p.dt), ctx->p.fb_cap, xi_dev,
+                                               ctx->p.seed, step, ctx->ws.c, ctx->vbar,
+                                               ctx->xbar, ctx->y, ctx->cfb, ctx->cmf);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_philox_fields(afq_ctx* ctx, uint64_t step, double* out, uint32_t* words) {
+  const long total = (long)ctx->ws.W * ((ctx->X + 1) / 2);
+  int grid = (int)((total + 255) / 256);
+  if (grid > 148 * 16) grid = 148 * 16;
+  k_philox_fields<<<grid, 256, 0, ctx->stream>>>(ctx->ws.W, ctx->X, ctx->p.seed, step, out,
+                                                 words);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_vhs_fp64(afq_ctx* ctx) {
+  dim3 grid((ctx->Mp + VT - 1) / VT, (ctx->ws.W + VZ - 1) / VZ);
+  k_vhs_fp64<<<grid, 256, 0, ctx->stream>>>(ctx->ws.W, ctx->X, ctx->M, ctx->Mp, sqrt(ctx->p.dt),
+                                            ctx->y, ctx->Lpk, ctx->tpq, ctx->A);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_propagate_fp64(afq_ctx* ctx) {
+  constexpr int NC = 4;
+  const int threads = 32 * ((ctx->M + 31) / 32);
+  const size_t smem = (size_t)3 * ctx->M * NC * sizeof(double2);
+  static size_t configured = 0;
+  if (smem > configured) {
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_propagate_fp64<NC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  dim3 grid((ctx->N + NC - 1) / NC, ctx->ws.W);
+  k_propagate_fp64<NC><<<grid, threads, smem, ctx->stream>>>(ctx->M, ctx->N, ctx->p.taylor_order,
+                                                             ctx->P, ctx->A, ctx->ws.phi);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_weights(afq_ctx* ctx, double log_const) {
+  k_weights<<<(ctx->ws.W + 127) / 128, 128, 0, ctx->stream>>>(
+      ctx->ws.W, log_const, ctx->p.free_projection, ctx->ws.det, ctx->cfb, ctx->cmf,
+      ctx->ws.ovlp, ctx->ws.w, ctx->flags);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_emix(afq_ctx* ctx, WalkerSet& s, double* out) {
+  k_emix<<<1, 256, 0, ctx->stream>>>(s.W, ctx->p.free_projection, s.w, s.energy, out);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}

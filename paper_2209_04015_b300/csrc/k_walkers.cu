@@ -1,0 +1,478 @@
+// Per-walker kernels of libafqmc: overlap, theta and determinant (Sec. "Overlap",
+// Eq. halfgf), the force-bias / Coulomb contraction (Eq. rfb), the fused exchange
+// energy (Sec. "Local energy"), energy assembly and the QR re-orthogonalisation.
+//
+// FP64 on B300 runs on the FP64 pipe at about 1 TFLOP/s, so these kernels are
+// bound by the number of DFMA instructions: they stage operands in shared memory
+// so every DFMA is fed without global-memory waits, and size grids in the
+// thousands of CTAs so all 148 SMs keep their FP64 pipes busy.
+#include "afq_internal.cuh"
+
+namespace {
+
+constexpr int OT = 256;                                     // threads, overlap kernel
+constexpr int PC = 32;                                      // Phi rows per chunk
+constexpr int MAXO1 = (AFQ_NMAX * AFQ_NMAX + OT - 1) / OT;  // S entries per thread
+
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// Deterministic block sum of a complex value; result valid in thread 0.
+__device__ double2 block_sum2(double2 v, double2* red) {
+  v = warp_sum2(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double2 s = cmk(0.0, 0.0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s = cadd(s, red[i]);
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// K1: S_s = Psi_s^T Phi_s, Gauss-Jordan inverse with partial pivoting giving
+// det S_s and S_s^-1, theta_s^T = S_s^-T Phi_s^T, and E1_s = sum h~ . theta.
+// One CTA per (walker, spin).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int nb,
+                                                      const double* __restrict__ psiT,
+                                                      const double* __restrict__ ht,
+                                                      const double2* __restrict__ phi,
+                                                      double2* __restrict__ thetaT,
+                                                      double2* __restrict__ det,
+                                                      double2* __restrict__ e1, int* flags) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double2 red[OT / 32];
+  __shared__ int s_piv;
+  __shared__ double2 s_det;
+  const int z = blockIdx.x, s = blockIdx.y, tid = threadIdx.x;
+  const int n = s ? nb : na, off = s ? na : 0;
+  if (n == 0) {
+    if (tid == 0) {
+      det[2 * z + s] = cmk(1.0, 0.0);
+      e1[2 * z + s] = cmk(0.0, 0.0);
+    }
+    return;
+  }
+  const int n2 = 2 * n, ldn = n | 1;
+  double2* aug = reinterpret_cast<double2*>(smraw);  // n x 2n  [S | I] -> [I | S^-1]
+  double2* cphi = aug + n * n2;                      // PC x ldn
+  double* cpsi = reinterpret_cast<double*>(cphi + PC * ldn);  // PC x ldn
+  double2* fac = reinterpret_cast<double2*>(cpsi + PC * ldn + (PC * ldn & 1));  // n
+  const double2* phiz = phi + (long)z * M * N;
+
+  // 1. S_ij = sum_p Psi_pi Phi_pj
+  double2 acc[MAXO1];
+#pragma unroll
+  for (int k = 0; k < MAXO1; ++k) acc[k] = cmk(0.0, 0.0);
+  for (int p0 = 0; p0 < M; p0 += PC) {
+    const int pc = min(PC, M - p0);
+    for (int e = tid; e < PC * n; e += OT) {
+      const int pp = e / n, j = e % n;
+      cphi[pp * ldn + j] = pp < pc ? phiz[(long)(p0 + pp) * N + off + j] : cmk(0.0, 0.0);
+      cpsi[pp * ldn + j] = pp < pc ? psiT[(long)(off + j) * M + p0 + pp] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < MAXO1; ++k) {
+      const int o = tid + k * OT;
+      if (o < n * n) {
+        const int i = o / n, j = o % n;
+        double2 a = acc[k];
+        for (int pp = 0; pp < pc; ++pp) {
+          const double ps = cpsi[pp * ldn + i];
+          const double2 ph = cphi[pp * ldn + j];
+          a.x = fma(ps, ph.x, a.x);
+          a.y = fma(ps, ph.y, a.y);
+        }
+        acc[k] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < MAXO1; ++k) {
+    const int o = tid + k * OT;
+    if (o < n * n) {
+      const int i = o / n, j = o % n;
+      aug[i * n2 + j] = acc[k];
+      aug[i * n2 + n + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
+    }
+  }
+  if (tid == 0) s_det = cmk(1.0, 0.0);
+  __syncthreads();
+
+  // 2. Gauss-Jordan elimination with partial pivoting (ties -> lowest row)
+  for (int kc = 0; kc < n; ++kc) {
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = kc;
+      for (int r = kc + tid; r < n; r += 32) {
+        const double v = cabs2(aug[r * n2 + kc]);
+        if (v > best) { best = v; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) s_piv = bi;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != kc)
+      for (int c = tid; c < n2; c += OT) {
+        const double2 t = aug[kc * n2 + c];
+        aug[kc * n2 + c] = aug[piv * n2 + c];
+        aug[piv * n2 + c] = t;
+      }
+    __syncthreads();
+    double2 pv = aug[kc * n2 + kc];
+    const bool bad = !(cabs2(pv) >= 1e-300);
+    if (tid == 0) {
+      if (bad) atomicAdd(&flags[0], 1);
+      double2 d = cmul(s_det, pv);
+      s_det = piv != kc ? cmk(-d.x, -d.y) : d;
+    }
+    if (bad) pv = cmk(1.0, 0.0);
+    const double2 inv = cdiv(cmk(1.0, 0.0), pv);
+    for (int r = tid; r < n; r += OT) fac[r] = aug[r * n2 + kc];
+    __syncthreads();
+    for (int c = tid; c < n2; c += OT) aug[kc * n2 + c] = cmul(aug[kc * n2 + c], inv);
+    __syncthreads();
+    for (int e = tid; e < n * n2; e += OT) {
+      const int r = e / n2, c = e % n2;
+      if (r != kc) aug[e] = csub(aug[e], cmul(fac[r], aug[kc * n2 + c]));
+    }
+    __syncthreads();
+  }
+
+  // 3. theta^T_jp = sum_k (S^-1)_kj Phi_pk and E1 = sum_jp h~_jp theta^T_jp
+  double2 e1acc = cmk(0.0, 0.0);
+  for (int p0 = 0; p0 < M; p0 += PC) {
+    const int pc = min(PC, M - p0);
+    for (int e = tid; e < PC * n; e += OT) {
+      const int pp = e / n, j = e % n;
+      cphi[pp * ldn + j] = pp < pc ? phiz[(long)(p0 + pp) * N + off + j] : cmk(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int e = tid; e < n * PC; e += OT) {
+      const int j = e / PC, pp = e % PC;
+      if (pp < pc) {
+        double2 t = cmk(0.0, 0.0);
+        for (int k = 0; k < n; ++k) {
+          const double2 sv = aug[k * n2 + n + j];
+          const double2 ph = cphi[pp * ldn + k];
+          t.x = fma(sv.x, ph.x, fma(-sv.y, ph.y, t.x));
+          t.y = fma(sv.x, ph.y, fma(sv.y, ph.x, t.y));
+        }
+        const long idx = ((long)z * N + off + j) * M + p0 + pp;
+        thetaT[idx] = t;
+        const double hv = ht[(long)(off + j) * M + p0 + pp];
+        e1acc.x = fma(hv, t.x, e1acc.x);
+        e1acc.y = fma(hv, t.y, e1acc.y);
+      }
+    }
+    __syncthreads();
+  }
+  const double2 tot = block_sum2(e1acc, red);
+  if (tid == 0) {
+    e1[2 * z + s] = tot;
+    det[2 * z + s] = s_det;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2 (FP64): c_zg = sum_k L~_g,k theta^T_z,k over k = (sigma, j, p), K = N M.
+// 32 g x 8 walkers per CTA, one complex output per thread.
+// ---------------------------------------------------------------------------
+constexpr int FG = 32, FZ = 8, FK = 64;
+__global__ void __launch_bounds__(256) k_force_bias_fp64(int X, int W, int K,
+                                                         const double* __restrict__ Lt,
+                                                         const double2* __restrict__ thetaT,
+                                                         double2* __restrict__ c) {
+  __shared__ double As[FG][FK + 1];
+  __shared__ double2 Bs[FZ][FK];
+  const int g0 = blockIdx.x * FG, z0 = blockIdx.y * FZ;
+  const int tg = threadIdx.x % 32, tz = threadIdx.x / 32;
+  double2 acc = cmk(0.0, 0.0);
+  for (int k0 = 0; k0 < K; k0 += FK) {
+    for (int e = threadIdx.x; e < FG * FK; e += 256) {
+      const int r = e / FK, kk = e % FK;
+      As[r][kk] = (g0 + r < X && k0 + kk < K) ? Lt[(long)(g0 + r) * K + k0 + kk] : 0.0;
+    }
+    for (int e = threadIdx.x; e < FZ * FK; e += 256) {
+      const int r = e / FK, kk = e % FK;
+      Bs[r][kk] = (z0 + r < W && k0 + kk < K) ? thetaT[(long)(z0 + r) * K + k0 + kk]
+                                              : cmk(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 16
+    for (int kk = 0; kk < FK; ++kk) {
+      const double a = As[tg][kk];
+      const double2 b = Bs[tz][kk];
+      acc.x = fma(a, b.x, acc.x);
+      acc.y = fma(a, b.y, acc.y);
+    }
+    __syncthreads();
+  }
+  if (g0 + tg < X && z0 + tz < W) c[(long)(z0 + tz) * X + g0 + tg] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// K6 (FP64): exchange.  For walker z, spin s and a group of G Cholesky indices,
+// T^g = L~_g,s theta_s (n x n, K = M) is formed in registers, staged in shared
+// memory, and consumed at once as sum_ij T_ij T_ji; T never reaches HBM.
+// ---------------------------------------------------------------------------
+constexpr int ET = 256, EKC = 32;
+constexpr int MAXO6 = (64 * AFQ_NMAX + ET - 1) / ET;
+__global__ void __launch_bounds__(ET) k_exchange_fp64(int M, int N, int na, int nb, int X,
+                                                      int G, int ngroups,
+                                                      const double* __restrict__ Lt,
+                                                      const double2* __restrict__ thetaT,
+                                                      double2* __restrict__ ekp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double2 red[ET / 32];
+  const int grp = blockIdx.x, z = blockIdx.y, s = blockIdx.z, tid = threadIdx.x;
+  const int n = s ? nb : na, off = s ? na : 0;
+  const long oidx = ((long)z * 2 + s) * ngroups + grp;
+  if (n == 0) {
+    if (tid == 0) ekp[oidx] = cmk(0.0, 0.0);
+    return;
+  }
+  const int g0 = grp * G, gc = min(G, X - g0), R = gc * n, total = R * n;
+  const int lda = EKC + 1;
+  double* As = reinterpret_cast<double*>(smraw);                       // R x lda
+  double2* Bs = reinterpret_cast<double2*>(As + G * n * lda + ((G * n * lda) & 1));  // n x lda
+  double2* Ts = Bs + n * lda;                                          // R x n
+  double2 acc[MAXO6];
+#pragma unroll
+  for (int k = 0; k < MAXO6; ++k) acc[k] = cmk(0.0, 0.0);
+  const double2* thz = thetaT + ((long)z * N + off) * M;
+  for (int p0 = 0; p0 < M; p0 += EKC) {
+    for (int e = tid; e < R * EKC; e += ET) {
+      const int r = e / EKC, kk = e % EKC;
+      const int g = g0 + r / n, i = r % n;
+      As[r * lda + kk] = p0 + kk < M ? Lt[((long)g * N + off + i) * M + p0 + kk] : 0.0;
+    }
+    for (int e = tid; e < n * EKC; e += ET) {
+      const int j = e / EKC, kk = e % EKC;
+      Bs[j * lda + kk] = p0 + kk < M ? thz[(long)j * M + p0 + kk] : cmk(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < MAXO6; ++k) {
+      const int o = tid + k * ET;
+      if (o < total) {
+        const int r = o / n, j = o % n;
+        double2 a = acc[k];
+#pragma unroll 8
+        for (int kk = 0; kk < EKC; ++kk) {
+          const double l = As[r * lda + kk];
+          const double2 t = Bs[j * lda + kk];
+          a.x = fma(l, t.x, a.x);
+          a.y = fma(l, t.y, a.y);
+        }
+        acc[k] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < MAXO6; ++k) {
+    const int o = tid + k * ET;
+    if (o < total) Ts[o] = acc[k];
+  }
+  __syncthreads();
+  double2 part = cmk(0.0, 0.0);
+  const int nn = n * n;
+  for (int e = tid; e < gc * nn; e += ET) {
+    const int g = e / nn, ij = e % nn, i = ij / n, j = ij % n;
+    part = cadd(part, cmul(Ts[(g * n + i) * n + j], Ts[(g * n + j) * n + i]));
+  }
+  const double2 tot = block_sum2(part, red);
+  if (tid == 0) ekp[oidx] = cscale(tot, -0.5);
+}
+
+// E1, EJ = 1/2 sum_g c_g^2, EK and E_L = e0 + E1 + EJ + EK per walker.
+__global__ void __launch_bounds__(256) k_energy_assemble(int X, int ngroups, double e0,
+                                                         const double2* __restrict__ e1,
+                                                         const double2* __restrict__ c,
+                                                         const double2* __restrict__ ekp,
+                                                         double2* __restrict__ energy) {
+  __shared__ double2 red[8];
+  const int z = blockIdx.x;
+  double2 ej = cmk(0.0, 0.0);
+  for (int g = threadIdx.x; g < X; g += 256) {
+    const double2 v = c[(long)z * X + g];
+    ej = cadd(ej, cmul(v, v));
+  }
+  ej = block_sum2(ej, red);
+  double2 ek = cmk(0.0, 0.0);
+  for (int e = threadIdx.x; e < 2 * ngroups; e += 256) ek = cadd(ek, ekp[(long)z * 2 * ngroups + e]);
+  ek = block_sum2(ek, red);
+  if (threadIdx.x == 0) {
+    const double2 one = cadd(e1[2 * z], e1[2 * z + 1]);
+    const double2 coul = cscale(ej, 0.5);
+    energy[4 * z + 0] = one;
+    energy[4 * z + 1] = coul;
+    energy[4 * z + 2] = ek;
+    energy[4 * z + 3] = cadd(cmk(e0, 0.0), cadd(one, cadd(coul, ek)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K7: QR of each spin block by classical Gram-Schmidt applied twice (CGS2), which
+// yields diag(R) real and positive.  Works on a column-major copy Qw of the block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
+                                            double2* __restrict__ phi, double2* __restrict__ Qw,
+                                            double* __restrict__ detR, int* flags) {
+  __shared__ double2 rs[AFQ_NMAX];
+  __shared__ double2 red[8];
+  __shared__ double s_norm;
+  const int z = blockIdx.x, s = blockIdx.y, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const int n = s ? nb : na, off = s ? na : 0;
+  if (n == 0) {
+    if (tid == 0) detR[2 * z + s] = 1.0;
+    return;
+  }
+  double2* phz = phi + (long)z * M * N;
+  double2* Q = Qw + ((long)z * N + off) * M;  // column j at Q + j * M
+  for (int e = tid; e < M * n; e += 256) {
+    const int p = e / n, j = e % n;
+    Q[(long)j * M + p] = phz[(long)p * N + off + j];
+  }
+  __syncthreads();
+  double logdet = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double2* v = Q + (long)j * M;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = wid; i < j; i += 8) {
+        const double2* qi = Q + (long)i * M;
+        double2 d = cmk(0.0, 0.0);
+        for (int p = lane; p < M; p += 32) d = cadd(d, cmul(cconj(qi[p]), v[p]));
+        d = warp_sum2(d);
+        if (lane == 0) rs[i] = d;
+      }
+      __syncthreads();
+      for (int p = tid; p < M; p += 256) {
+        double2 t = v[p];
+        for (int i = 0; i < j; ++i) t = csub(t, cmul(Q[(long)i * M + p], rs[i]));
+        v[p] = t;
+      }
+      __syncthreads();
+    }
+    double2 nr = cmk(0.0, 0.0);
+    for (int p = tid; p < M; p += 256) nr.x += cabs2(v[p]);
+    nr = block_sum2(nr, red);
+    if (tid == 0) s_norm = sqrt(nr.x);
+    __syncthreads();
+    const double rjj = s_norm;
+    if (!(rjj > 0.0) && tid == 0) atomicAdd(&flags[0], 1);
+    const double inv = rjj > 0.0 ? 1.0 / rjj : 1.0;
+    for (int p = tid; p < M; p += 256) v[p] = cscale(v[p], inv);
+    logdet += log(rjj > 0.0 ? rjj : 1.0);
+    __syncthreads();
+  }
+  for (int e = tid; e < M * n; e += 256) {
+    const int p = e / n, j = e % n;
+    phz[(long)p * N + off + j] = Q[(long)j * M + p];
+  }
+  if (tid == 0) detR[2 * z + s] = exp(logdet);
+}
+
+__global__ void k_qr_finish(int W, const double* __restrict__ detR, double2* __restrict__ ovlp) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < W) ovlp[z] = cscale(ovlp[z], 1.0 / (detR[2 * z] * detR[2 * z + 1]));
+}
+
+__global__ void k_init_overlap(int W, const double2* __restrict__ det, double2* __restrict__ ovlp) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < W) ovlp[z] = cmul(det[2 * z], det[2 * z + 1]);
+}
+
+size_t overlap_smem(int n) {
+  const int ldn = n | 1;
+  return (size_t)n * 2 * n * 16 + (size_t)PC * ldn * 16 + (size_t)PC * ldn * 8 + 8 + (size_t)n * 16;
+}
+
+size_t exchange_smem(int G, int n) {
+  const int lda = EKC + 1;
+  return (size_t)G * n * lda * 8 + 8 + (size_t)n * lda * 16 + (size_t)G * n * n * 16;
+}
+
+}  // namespace
+
+int exchange_group_size(int nmax) { return nmax > 0 ? (64 / nmax > 1 ? 64 / nmax : 1) : 1; }
+
+int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s) {
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  const size_t smem = overlap_smem(nmax);
+  static size_t configured = 0;
+  if (smem > configured) {
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_overlap_theta,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  k_overlap_theta<<<dim3(s.W, 2), OT, smem, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb,
+                                                          ctx->psiT, ctx->ht, s.phi, s.thetaT,
+                                                          s.det, s.e1, ctx->flags);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_force_bias_fp64(afq_ctx* ctx, WalkerSet& s) {
+  dim3 grid((ctx->X + FG - 1) / FG, (s.W + FZ - 1) / FZ);
+  k_force_bias_fp64<<<grid, 256, 0, ctx->stream>>>(ctx->X, s.W, ctx->N * ctx->M, ctx->Lt,
+                                                   s.thetaT, s.c);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s) {
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  const int G = exchange_group_size(nmax);
+  const int ngroups = (ctx->X + G - 1) / G;
+  if (ngroups != ctx->ex_groups) return afq_fail(ctx, AFQ_ERR_STATE, "exchange groups changed");
+  const size_t smem = exchange_smem(G, nmax);
+  static size_t configured = 0;
+  if (smem > configured) {
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_exchange_fp64,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  k_exchange_fp64<<<dim3(ngroups, s.W, 2), ET, smem, ctx->stream>>>(
+      ctx->M, ctx->N, ctx->na, ctx->nb, ctx->X, G, ngroups, ctx->Lt, s.thetaT, s.ekp);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_energy_assemble(afq_ctx* ctx, WalkerSet& s) {
+  k_energy_assemble<<<s.W, 256, 0, ctx->stream>>>(ctx->X, ctx->ex_groups, ctx->e0, s.e1, s.c,
+                                                  s.ekp, s.energy);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_qr(afq_ctx* ctx, WalkerSet& s, double2* Qw) {
+  k_qr<<<dim3(s.W, 2), 256, 0, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb, s.phi, Qw,
+                                              ctx->detR, ctx->flags);
+  AFQ_LAUNCHED(ctx);
+  k_qr_finish<<<(s.W + 127) / 128, 128, 0, ctx->stream>>>(s.W, ctx->detR, s.ovlp);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_init_overlap(afq_ctx* ctx, WalkerSet& s) {
+  k_init_overlap<<<(s.W + 127) / 128, 128, 0, ctx->stream>>>(s.W, s.det, s.ovlp);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
