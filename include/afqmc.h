@@ -169,6 +169,29 @@ int afq_profile_read(afq_ctx* ctx, int kernel, double* total_ms, uint64_t* launc
 /* Name of a kernel class, or NULL when kernel is out of range. */
 const char* afq_kernel_name(int kernel);
 
+/* Exchange energy without any device allocation.  The paper has no counterpart:
+   this exists for callers that cannot call cudaMalloc, such as a host framework
+   that owns all device memory through its own pool or fixed arena, or a
+   latency-critical loop that must avoid the device synchronisation of
+   cudaMalloc / cudaFree.
+   Inputs (device pointers, read on cuda_stream): Lt_dev, the half-rotated Cholesky
+   vectors L~_g = Psi^T L_g as X x (na+nb) x M doubles (alpha rows first);
+   thetaT_dev, theta^T of each walker as W x (na+nb) x M complex (theta_s =
+   Phi_s (Psi_s^T Phi_s)^-1 per spin block).  Output: ek_dev, W complex values
+   E_K,z = -1/2 sum_s sum_g sum_ij T_ij T_ji, the same as column EK of
+   afq_local_energy.  The caller owns every buffer.
+   The kernel's partial sums live in a file-scope device array of
+   AFQ_STATIC_EXCHANGE_SLOTS complex doubles (4 MiB, held by each GPU that loads
+   the library until exit).  A call needs W * 2 * ceil(X / G) slots, with
+   G = max(1, 64 / max(na, nb)); larger calls return AFQ_ERR_ARG with a message on
+   stderr.  The first call on a device looks up the array's device address (make
+   that first call before any stream capture).  All calls share the array, so
+   calls that overlap on the GPU race; each call writes every slot it reads.
+   Returns AFQ_OK, AFQ_ERR_ARG or AFQ_ERR_CUDA. */
+#define AFQ_STATIC_EXCHANGE_SLOTS 262144
+int afq_exchange_energy_static(int M, int X, int na, int nb, int W, const double* Lt_dev,
+                               const double* thetaT_dev, double* ek_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libafqmc.so")
 
 AFQ_OK, AFQ_ERR_ARG, AFQ_ERR_CUDA, AFQ_ERR_SINGULAR, AFQ_ERR_NAN, AFQ_ERR_STATE, AFQ_ERR_NOMEM = range(7)
+AFQ_STATIC_EXCHANGE_SLOTS = 262144  # complex partial-sum slots of the static scratch array
 PRECISIONS = {"fp64": 0, "split_bf16": 1, "split_tf32": 2}
 STATUS_NAMES = {0: "AFQ_OK", 1: "AFQ_ERR_ARG", 2: "AFQ_ERR_CUDA", 3: "AFQ_ERR_SINGULAR",
                 4: "AFQ_ERR_NAN", 5: "AFQ_ERR_STATE", 6: "AFQ_ERR_NOMEM"}
@@ -65,6 +66,8 @@ _SIGS = {
     "afq_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "afq_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_uint64)]),
     "afq_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "afq_exchange_energy_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
 }
 
 
@@ -83,6 +86,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def exchange_energy_static(M: int, X: int, na: int, nb: int, W: int, Lt_ptr: int,
+                           thetaT_ptr: int, ek_ptr: int, stream: int | None = None) -> None:
+    """afq_exchange_energy_static on device pointers: exchange energy per walker with
+    no device allocation (partial sums in the library's static scratch array)."""
+    lib = load_library()
+    rc = lib.afq_exchange_energy_static(M, X, na, nb, W, _P(Lt_ptr), _P(thetaT_ptr), _P(ek_ptr),
+                                        _P(stream or 0))
+    if rc != AFQ_OK:
+        raise AfqError(rc, "afq_exchange_energy_static failed (details on stderr)")
 
 
 def _ptr(a: np.ndarray | None):

@@ -455,6 +455,22 @@ int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s) {
   return AFQ_OK;
 }
 
+// The exchange kernel with explicit device pointers and stream (no context): the
+// partial sums go to ekp, W x 2 x ceil(X / G) complex slots.
+cudaError_t launch_exchange_fp64_raw(int M, int X, int na, int nb, int W, const double* Lt,
+                                     const double2* thetaT, double2* ekp, cudaStream_t stream) {
+  const int nmax = na > nb ? na : nb;
+  const int G = exchange_group_size(nmax);
+  const int ngroups = (X + G - 1) / G;
+  const size_t smem = exchange_smem(G, nmax);
+  cudaError_t e = cudaFuncSetAttribute(k_exchange_fp64,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_exchange_fp64<<<dim3(ngroups, W, 2), ET, smem, stream>>>(M, na + nb, na, nb, X, G, ngroups,
+                                                             Lt, thetaT, ekp);
+  return cudaGetLastError();
+}
+
 int launch_energy_assemble(afq_ctx* ctx, WalkerSet& s) {
   k_energy_assemble<<<s.W, 256, 0, ctx->stream>>>(ctx->X, ctx->ex_groups, ctx->e0, s.e1, s.c,
                                                   s.ekp, s.energy);

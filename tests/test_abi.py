@@ -48,7 +48,7 @@ def test_binding_names_match_c_names(lib):
         short = n[len("afq_"):]
         if short in ("create", "destroy", "last_error", "default_params", "kernel_name"):
             continue
-        assert hasattr(binding.AfqContext, short), short
+        assert hasattr(binding.AfqContext, short) or hasattr(binding, short), short
 
 
 def test_default_params_are_host_only(lib):
