@@ -46,9 +46,9 @@ typedef enum afq_status {
 
 typedef enum afq_precision {
   AFQ_FP64 = 0,       /* every contraction in float64                         */
-  AFQ_SPLIT_BF16 = 1, /* force bias, VHS, propagator and exchange as split-bf16
-                         tensor-core GEMMs with fp32 accumulation; overlaps,
-                         inverses, QR and weights stay float64                */
+  AFQ_SPLIT_BF16 = 1, /* the force bias and exchange contractions as split-bf16
+                         tensor-core GEMMs (tcgen05) with FP32 accumulation;
+                         overlaps, inverses, QR and weights stay float64      */
   AFQ_SPLIT_TF32 = 2  /* reserved                                              */
 } afq_precision;
 
@@ -63,10 +63,12 @@ typedef struct afq_params {
   double e_shift;      /* energy shift in exp(-dt (H - E_shift))                 */
   double fb_cap;       /* |xbar_g| cap; 0 = off                                  */
   int free_projection; /* 1: complex weights w <- w I (no phaseless cut)         */
+  int split_slices;    /* AFQ_SPLIT_BF16: bf16 slices per FP64 operand, 1..4
+                          (slice products s + t <= slices - 1 are kept); 0 = 3  */
 } afq_params;
 
 /* Fill *p with the defaults: dt 0.005, Taylor order 6, QR every 5 steps, seed 1,
-   FP64, E_shift = trial energy, no cap, phaseless. */
+   FP64, E_shift = trial energy, no cap, phaseless, 3 slices in split mode. */
 void afq_default_params(afq_params* p);
 
 /* Create a context bound to cuda_stream (a cudaStream_t, or NULL for the legacy
@@ -191,6 +193,16 @@ const char* afq_kernel_name(int kernel);
 #define AFQ_STATIC_EXCHANGE_SLOTS 262144
 int afq_exchange_energy_static(int M, int X, int na, int nb, int W, const double* Lt_dev,
                                const double* thetaT_dev, double* ek_dev, void* cuda_stream);
+
+/* Split-precision real GEMM on the tensor cores: C = A B^T with A m x k, B n x k and
+   C m x n, all row-major FP64 DEVICE arrays, read and written on cuda_stream.  Each
+   operand is cut into `slices` bfloat16 slices (1..4) and the slice products with
+   s + t <= slices - 1 are accumulated in FP32 by tcgen05.mma; this is the
+   contraction engine of the AFQ_SPLIT_BF16 force bias (Eq. rfb) and exchange
+   (Sec. "Local energy").  Allocates its slice workspace, synchronises the stream
+   before returning.  Returns AFQ_OK, AFQ_ERR_ARG, AFQ_ERR_NOMEM or AFQ_ERR_CUDA. */
+int afq_gemm_split_bf16(int m, int n, int k, int slices, const double* A_dev, const double* B_dev,
+                        double* C_dev, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,7 @@ class AfqParams(ctypes.Structure):
                 ("qr_period", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int), ("has_e_shift", ctypes.c_int),
                 ("e_shift", ctypes.c_double), ("fb_cap", ctypes.c_double),
-                ("free_projection", ctypes.c_int)]
+                ("free_projection", ctypes.c_int), ("split_slices", ctypes.c_int)]
 
 
 class AfqError(RuntimeError):
@@ -66,6 +66,8 @@ _SIGS = {
     "afq_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "afq_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_uint64)]),
     "afq_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "afq_gemm_split_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            _P, _P, _P, _P]),
     "afq_exchange_energy_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
 }
@@ -99,6 +101,15 @@ def exchange_energy_static(M: int, X: int, na: int, nb: int, W: int, Lt_ptr: int
         raise AfqError(rc, "afq_exchange_energy_static failed (details on stderr)")
 
 
+def gemm_split_bf16(m: int, n: int, k: int, slices: int, A_ptr: int, B_ptr: int, C_ptr: int,
+                    stream: int | None = None) -> None:
+    """afq_gemm_split_bf16 on device pointers: C = A B^T in split-bf16 on the tensor cores."""
+    lib = load_library()
+    rc = lib.afq_gemm_split_bf16(m, n, k, slices, _P(A_ptr), _P(B_ptr), _P(C_ptr), _P(stream or 0))
+    if rc != AFQ_OK:
+        raise AfqError(rc, "afq_gemm_split_bf16 failed")
+
+
 def _ptr(a: np.ndarray | None):
     return None if a is None else a.ctypes.data_as(_P)
 
@@ -112,7 +123,8 @@ class AfqContext:
 
     def __init__(self, dt: float = 0.005, taylor_order: int = 6, qr_period: int = 5,
                  seed: int = 1, precision: str = "fp64", e_shift: float | None = None,
-                 fb_cap: float = 0.0, free_projection: bool = False, stream: int | None = None):
+                 fb_cap: float = 0.0, free_projection: bool = False, stream: int | None = None,
+                 split_slices: int = 3):
         self.lib = load_library()
         p = AfqParams()
         self.lib.afq_default_params(ctypes.byref(p))
@@ -122,6 +134,7 @@ class AfqContext:
         p.e_shift = 0.0 if e_shift is None else float(e_shift)
         p.fb_cap = fb_cap
         p.free_projection = 1 if free_projection else 0
+        p.split_slices = split_slices
         self.params = p
         h = _P()
         rc = self.lib.afq_create(ctypes.byref(h), ctypes.byref(p), _P(stream or 0))

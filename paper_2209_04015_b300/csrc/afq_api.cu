@@ -68,6 +68,9 @@ int alloc_walker_set(afq_ctx* ctx, WalkerSet& s, int W) {
   AFQ_TRY(dalloc(ctx, &s.energy, 4 * (size_t)W));
   AFQ_TRY(dalloc(ctx, &s.w, W));
   AFQ_TRY(dalloc(ctx, &s.ovlp, W));
+  // exchange slots that a tiling leaves unwritten must read as zero
+  AFQ_CUDA(ctx, cudaMemsetAsync(s.ekp, 0, (size_t)W * 2 * ctx->ex_groups * sizeof(double2),
+                                ctx->stream));
   s.W = W;
   return AFQ_OK;
 }
@@ -79,12 +82,13 @@ int sync(afq_ctx* ctx) {
 
 // Reads and clears the device flags; maps them to a status.
 int check_flags(afq_ctx* ctx) {
-  int h[2] = {0, 0};
+  int h[3] = {0, 0, 0};
   AFQ_CUDA(ctx, cudaMemcpyAsync(h, ctx->flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   AFQ_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(h), ctx->stream));
   AFQ_TRY(sync(ctx));
   if (h[0]) return afq_fail(ctx, AFQ_ERR_SINGULAR, std::to_string(h[0]) + " singular pivot(s)");
   if (h[1]) return afq_fail(ctx, AFQ_ERR_NAN, std::to_string(h[1]) + " non-finite weight(s)");
+  if (h[2]) return afq_fail(ctx, AFQ_ERR_CUDA, "tensor-core pipeline wait timed out");
   return AFQ_OK;
 }
 
@@ -127,15 +131,30 @@ int drain_profile(afq_ctx* ctx) {
   return AFQ_OK;
 }
 
-// Green's-function intermediates of a walker set: theta, det, E1 and c.
+// Green's-function intermediates of a walker set: theta, det, E1 and c.  The
+// walker ensemble of a split-precision context takes the tensor-core force bias;
+// other sets (the trial at set-up) always use FP64.
 int green_and_bias(afq_ctx* ctx, WalkerSet& s) {
+  const bool tc = ctx->mixed && &s == &ctx->ws;
   AFQ_TRY(timed(ctx, AFQ_K_OVERLAP, [&] { return launch_overlap_theta(ctx, s); }));
-  AFQ_TRY(timed(ctx, AFQ_K_FORCE_BIAS, [&] { return launch_force_bias_fp64(ctx, s); }));
+  if (tc) {
+    AFQ_TRY(timed(ctx, AFQ_K_FORCE_BIAS, [&] {
+      int rc = launch_slice_theta(ctx, s);
+      return rc != AFQ_OK ? rc : launch_force_bias_tc(ctx, s);
+    }));
+  } else {
+    AFQ_TRY(timed(ctx, AFQ_K_FORCE_BIAS, [&] { return launch_force_bias_fp64(ctx, s); }));
+  }
   return AFQ_OK;
 }
 
 int energy_kernels(afq_ctx* ctx, WalkerSet& s) {
-  AFQ_TRY(timed(ctx, AFQ_K_EXCHANGE, [&] { return launch_exchange_fp64(ctx, s); }));
+  const bool tc = ctx->mixed && &s == &ctx->ws;
+  if (tc) {
+    AFQ_TRY(timed(ctx, AFQ_K_EXCHANGE, [&] { return launch_exchange_tc(ctx, s); }));
+  } else {
+    AFQ_TRY(timed(ctx, AFQ_K_EXCHANGE, [&] { return launch_exchange_fp64(ctx, s); }));
+  }
   AFQ_TRY(timed(ctx, AFQ_K_ENERGY, [&] { return launch_energy_assemble(ctx, s); }));
   return AFQ_OK;
 }
@@ -154,6 +173,7 @@ int free_walkers(afq_ctx* ctx) {
 }
 
 int free_trial(afq_ctx* ctx) {
+  mixed_free(ctx);
   dfree(&ctx->psiT);
   dfree(&ctx->Lt);
   dfree(&ctx->ht);
@@ -206,6 +226,7 @@ void afq_default_params(afq_params* p) {
   p->e_shift = 0.0;
   p->fb_cap = 0.0;
   p->free_projection = 0;
+  p->split_slices = 3;
 }
 
 int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
@@ -218,18 +239,23 @@ int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
   } else {
     afq_default_params(&ctx->p);
   }
+  if (ctx->p.split_slices == 0) ctx->p.split_slices = 3;
   if (!(ctx->p.dt > 0.0) || ctx->p.taylor_order < 1 || ctx->p.taylor_order > 32 ||
-      ctx->p.qr_period < 0 || ctx->p.precision != AFQ_FP64) {
+      ctx->p.qr_period < 0 ||
+      (ctx->p.precision != AFQ_FP64 && ctx->p.precision != AFQ_SPLIT_BF16) ||
+      ctx->p.split_slices < 1 || ctx->p.split_slices > 4) {
     delete ctx;
     return AFQ_ERR_ARG;
   }
+  ctx->mixed = ctx->p.precision == AFQ_SPLIT_BF16;
+  ctx->S = ctx->p.split_slices;
   ctx->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     delete ctx;
     return AFQ_ERR_CUDA;
   }
-  if (cudaMalloc((void**)&ctx->flags, 2 * sizeof(int)) != cudaSuccess ||
-      cudaMemset(ctx->flags, 0, 2 * sizeof(int)) != cudaSuccess ||
+  if (cudaMalloc((void**)&ctx->flags, 3 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->flags, 0, 3 * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&ctx->emix, sizeof(double)) != cudaSuccess) {
     cudaFree(ctx->flags);
     delete ctx;
@@ -397,7 +423,7 @@ int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a, const doub
                  cudaSuccess
              ? AFQ_OK
              : afq_fail(ctx, AFQ_ERR_CUDA, "copy trial");
-  if (rc == AFQ_OK) rc = green_and_bias(ctx, t);
+  if (rc == AFQ_OK) rc = green_and_bias(ctx, t);   // FP64: t is not the walker ensemble
   if (rc == AFQ_OK) rc = energy_kernels(ctx, t);
   double2 e[4];
   if (rc == AFQ_OK)
@@ -410,6 +436,10 @@ int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a, const doub
   AFQ_TRY(check_flags(ctx));
   ctx->e_trial = e[3].x;
   ctx->e_shift = ctx->p.has_e_shift ? ctx->p.e_shift : ctx->e_trial;
+  if (ctx->mixed) {
+    AFQ_TRY(mixed_init_trial(ctx));
+    AFQ_TRY(sync(ctx));
+  }
   return AFQ_OK;
 }
 
@@ -453,6 +483,7 @@ int afq_init_walkers(afq_ctx* ctx, int W, const double* phi, const double* w) {
   std::vector<double2> wv(W);
   for (int z = 0; z < W; ++z) wv[z] = make_double2(w ? w[z] : 1.0, 0.0);
   AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->ws.w, wv.data(), W * 16, cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->mixed) AFQ_TRY(mixed_init_walkers(ctx));
   AFQ_TRY(green_and_bias(ctx, ctx->ws));
   AFQ_TRY(launch_init_overlap(ctx, ctx->ws));
   AFQ_TRY(sync(ctx));

@@ -2,6 +2,8 @@
 // and the host-side launch wrappers of every kernel.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -91,9 +93,21 @@ struct afq_ctx {
   double2* A = nullptr;      // W x M x M  i sqrt(dt) V, symmetric
   double* detR = nullptr;    // W x 2
   double* emix = nullptr;    // 1
-  int* flags = nullptr;      // [0] singular pivots, [1] non-finite values
+  int* flags = nullptr;      // [0] singular pivots, [1] non-finite values,
+                             // [2] tensor-core pipeline time-outs
   double* scratch = nullptr; // set-up workspace
   size_t scratch_bytes = 0;
+
+  // split-precision (AFQ_SPLIT_BF16) state
+  bool mixed = false;
+  int S = 3;                          // bf16 slices per operand
+  int Mpad = 0;                       // M rounded up to the 32-wide K block
+  __nv_bfloat16* Lt_sl = nullptr;     // S x X x N x Mpad slices of L~
+  __nv_bfloat16* th_sl = nullptr;     // S x W x 2 x N x Mpad slices of theta (re, im planes)
+  float* fb_part = nullptr;           // ksplit x 2W x X force-bias partial sums
+  int fb_BN = 0, fb_kbper = 0, fb_ksplit = 0;
+  int ex_G[2] = {0, 0}, ex_zb[2] = {0, 0}, ex_BN[2] = {0, 0};
+  CUtensorMap tm_fb_a, tm_fb_b, tm_ex_a[2], tm_ex_b[2];
 
   // built-in profiler: event pairs around launches of each kernel class
   bool profiling = false;
@@ -152,3 +166,11 @@ int launch_vhs_fp64(afq_ctx* ctx);
 int launch_propagate_fp64(afq_ctx* ctx);
 int launch_weights(afq_ctx* ctx, double log_const);
 int launch_emix(afq_ctx* ctx, WalkerSet& s, double* out);
+
+// split-precision tensor-core path (k_mixed.cu)
+int mixed_init_trial(afq_ctx* ctx);
+int mixed_init_walkers(afq_ctx* ctx);
+void mixed_free(afq_ctx* ctx);
+int launch_slice_theta(afq_ctx* ctx, WalkerSet& s);
+int launch_force_bias_tc(afq_ctx* ctx, WalkerSet& s);
+int launch_exchange_tc(afq_ctx* ctx, WalkerSet& s);

@@ -1,0 +1,659 @@
+// Split-precision tensor-core contractions of libafqmc (precision AFQ_SPLIT_BF16).
+//
+// Each FP64 operand x is split into S bfloat16 slices, x ~ x_0 + x_1 + ... + x_{S-1}
+// (x_0 = bf16(x), x_k = bf16 of the remainder), and a product A B^T becomes the sum of
+// the slice products A_s B_t^T with s + t <= S - 1, issued as tcgen05.mma (BF16 in,
+// FP32 accumulate in TMEM) into one accumulator, smallest terms first.  With S = 3
+// (six products) the result carries about 24 significant bits.
+//
+// One kernel template serves three contractions (the force bias / Coulomb vector of
+// Eq. rfb, the exchange term of Sec. "Local energy", and a plain GEMM used to test
+// the engine); a policy supplies the tile coordinates, the TMA loads and the
+// epilogue.  Roles inside a 128-thread CTA: thread 0 issues TMA loads into a
+// three-stage ring (all slices of one 32-wide K block per stage, 64-byte swizzle),
+// thread 32 issues the MMAs and commits each stage back to the producer, and all four
+// warps read the 128 x BN accumulator out of TMEM for the epilogue.
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "afq_internal.cuh"
+#include "tc_sm103.cuh"
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kBK = 32;             // K elements per block: one 64-byte row
+constexpr int kASlot = 128 * 64;    // bytes of one A slice of one K block
+constexpr int kStages = 3;
+constexpr int kMaxSlices = 4;
+
+// Slice pairs (s, t) with s + t <= S - 1, ordered from the smallest contributions.
+template <int S>
+__device__ __forceinline__ void slice_pair(int k, int& s, int& t) {
+  int idx = 0;
+#pragma unroll
+  for (int d = S - 1; d >= 0; --d)
+#pragma unroll
+    for (int ss = d; ss >= 0; --ss) {
+      if (idx == k) {
+        s = ss;
+        t = d - ss;
+      }
+      ++idx;
+    }
+}
+
+struct TcCommon {
+  int nkb;            // K blocks in the whole K range
+  int BN;             // MMA N (multiple of 16, <= 256)
+  uint32_t tx_bytes;  // bytes the TMA loads of one stage deliver
+  uint32_t tmem_cols;
+  int* err;           // set to 1 when a pipeline wait times out
+};
+
+// ---------------------------------------------------------------------------
+// The kernel template
+// ---------------------------------------------------------------------------
+template <int S, class P>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const typename P::Args args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ __align__(8) uint64_t empty[kStages];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+  __shared__ int skip;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const typename P::Tile t = P::tile(args);
+  const int BN = args.c.BN;
+  const uint32_t bslot = (uint32_t)BN * 64u;
+  const uint32_t stage_bytes = S * (kASlot + bslot);
+  int* err = args.c.err;
+  // another CTA already failed: do nothing (decided once for the whole CTA, before
+  // any barrier or TMEM is set up)
+  if (threadIdx.x == 0) skip = *(const volatile int*)err;
+  __syncthreads();
+  if (skip) return;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(&done, 1);
+    fail = 0;
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, args.c.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const int nkb = t.kb1 - t.kb0;
+
+  if (threadIdx.x == 0) {
+    // TMA producer
+    int issued = 0;
+    for (int i = 0; i < nkb; ++i) {
+      const int st = i % kStages;
+      if (i >= kStages && !tc::mbar_wait(&empty[st], ((i / kStages) - 1) & 1, err)) {
+        fail = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      tc::mbar_arrive_expect_tx(&full[st], args.c.tx_bytes);
+      uint8_t* sa = smem + st * stage_bytes;
+      uint8_t* sb = sa + S * kASlot;
+#pragma unroll
+      for (int s = 0; s < S; ++s) P::load_a(&tmA, sa + s * kASlot, args, t, s, t.kb0 + i, &full[st]);
+#pragma unroll
+      for (int s = 0; s < S; ++s) P::load_b(&tmB, sb + s * bslot, args, t, s, t.kb0 + i, &full[st]);
+      ++issued;
+    }
+    // no TMA write may still be in flight when the CTA moves on
+    for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
+      tc::mbar_wait(&full[i % kStages], (i / kStages) & 1, err);
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    const uint32_t idesc = tc::idesc_bf16(128, BN);
+    for (int i = 0; i < nkb; ++i) {
+      const int st = i % kStages;
+      if (!tc::mbar_wait(&full[st], (i / kStages) & 1, err)) {
+        fail = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
+      const uint32_t sb = sa + S * kASlot;
+#pragma unroll
+      for (int k = 0; k < S * (S + 1) / 2; ++k) {
+        int s = 0, u = 0;
+        slice_pair<S>(k, s, u);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+          tc::mma_bf16(tmem, tc::sdesc_k64(sa + s * kASlot + ks * 32),
+                       tc::sdesc_k64(sb + u * bslot + ks * 32), idesc, (i | k | ks) != 0);
+      }
+      tc::mma_commit(&empty[st]);
+    }
+    tc::mma_commit(&done);
+  }
+  bool ok = tc::mbar_wait(&done, 0, err);
+  // the MMAs already issued must finish before TMEM is read or freed: wait again,
+  // bounded by time only
+  if (!ok) {
+    static const int zero = 0;
+    ok = tc::mbar_wait(&done, 0, &zero);
+  }
+  if (!ok) fail = 1;
+  tc::fence_after_sync();
+  __syncthreads();
+  const bool bad = fail != 0;
+  __syncwarp();
+  if (bad) {
+    if (threadIdx.x == 0) atomicExch(args.c.err, 1);
+  } else {
+    P::epilogue(args, t, tmem, smem, warp, lane);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, args.c.tmem_cols);
+}
+
+__device__ __forceinline__ void tmem_row16(uint32_t tmem, int warp, int c0, float (&v)[16]) {
+  tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+}
+
+// ---------------------------------------------------------------------------
+// Policy: plain GEMM C (m x n, FP64) = A (m x K) B (n x K)^T from slice planes
+// [s][rows][Kp] (3D tensor maps {Kp, rows, S}).
+// ---------------------------------------------------------------------------
+struct GemmP {
+  struct Args {
+    TcCommon c;
+    int m, n;
+    double* C;
+    long ldc;
+  };
+  struct Tile {
+    int m0, n0, kb0, kb1;
+  };
+  static __device__ Tile tile(const Args& a) {
+    return Tile{(int)blockIdx.y * 128, (int)blockIdx.x * a.c.BN, 0, a.c.nkb};
+  }
+  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int s,
+                                int kb, uint64_t* bar) {
+    tc::tma_load_3d(dst, tm, kb * kBK, t.m0, s, bar);
+  }
+  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int s,
+                                int kb, uint64_t* bar) {
+    tc::tma_load_3d(dst, tm, kb * kBK, t.n0, s, bar);
+  }
+  static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t*, int warp,
+                                  int lane) {
+    const int row = t.m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < a.c.BN; c0 += 16) {
+      float v[16];
+      tmem_row16(tmem, warp, c0, v);
+      if (row < a.m)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = t.n0 + c0 + j;
+          if (col < a.n) a.C[(long)row * a.ldc + col] = v[j];
+        }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Policy: force bias / Coulomb vector, split over K.  Rows g of L~ (K = N Mpad),
+// columns (z, re/im) of theta; partial sums part[ks][col][g] (FP32, g contiguous).
+// ---------------------------------------------------------------------------
+struct FbP {
+  struct Args {
+    TcCommon c;
+    int X, W2, kbper;
+    float* part;
+  };
+  struct Tile {
+    int g0, n0, ks, kb0, kb1;
+  };
+  static __device__ Tile tile(const Args& a) {
+    const int ks = blockIdx.z;
+    const int kb0 = ks * a.kbper;
+    const int kb1 = min(a.c.nkb, kb0 + a.kbper);
+    return Tile{(int)blockIdx.y * 128, (int)blockIdx.x * a.c.BN, ks, kb0, kb1};
+  }
+  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int s,
+                                int kb, uint64_t* bar) {
+    tc::tma_load_3d(dst, tm, kb * kBK, t.g0, s, bar);
+  }
+  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int s,
+                                int kb, uint64_t* bar) {
+    tc::tma_load_3d(dst, tm, kb * kBK, t.n0, s, bar);
+  }
+  static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t*, int warp,
+                                  int lane) {
+    const int g = t.g0 + warp * 32 + lane;
+    float* out = a.part + (long)t.ks * a.W2 * a.X;
+    for (int c0 = 0; c0 < a.c.BN; c0 += 16) {
+      float v[16];
+      tmem_row16(tmem, warp, c0, v);
+      if (g < a.X)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = t.n0 + c0 + j;
+          if (col < a.W2) out[(long)col * a.X + g] = v[j];
+        }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Policy: exchange for one spin.  A tile rows (g, i): G Cholesky indices x n
+// orbitals of L~ (4D map {Mpad, N, X, S}, box {32, n, G, 1}); B tile rows
+// (z, re/im, j): zb walkers of theta (4D map {Mpad, N, 2W, S}, box {32, n, 2 zb, 1});
+// K = Mpad.  The 128 x BN accumulator holds T^{g z}_ij for every (g, z) pair of
+// the tile; the epilogue stages it in shared memory and forms sum_ij T_ij T_ji.
+// ---------------------------------------------------------------------------
+struct ExP {
+  struct Args {
+    TcCommon c;
+    int n, off, G, zb, X, W, spin, ex_groups;
+    double2* ekp;
+  };
+  struct Tile {
+    int gt, g0, z0, kb0, kb1;
+  };
+  static __device__ Tile tile(const Args& a) {
+    return Tile{(int)blockIdx.x, (int)blockIdx.x * a.G, (int)blockIdx.y * a.zb, 0, a.c.nkb};
+  }
+  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args& a, const Tile& t,
+                                int s, int kb, uint64_t* bar) {
+    tc::tma_load_4d(dst, tm, kb * kBK, a.off, t.g0, s, bar);
+  }
+  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args& a, const Tile& t,
+                                int s, int kb, uint64_t* bar) {
+    tc::tma_load_4d(dst, tm, kb * kBK, a.off, 2 * t.z0, s, bar);
+  }
+  static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t* smem,
+                                  int warp, int lane) {
+    const int n = a.n, BN = a.c.BN, pitch = BN + 1;
+    float* Ts = reinterpret_cast<float*>(smem);
+    const int r = warp * 32 + lane;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      float v[16];
+      tmem_row16(tmem, warp, c0, v);
+      if (r < a.G * n)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) Ts[r * pitch + c0 + j] = v[j];
+    }
+    __syncthreads();
+    const int gc = min(a.G, a.X - t.g0), nn = n * n;
+    for (int zl = warp; zl < a.zb; zl += 4) {
+      const int z = t.z0 + zl;
+      const int cb = zl * 2 * n;
+      float sr = 0.f, si = 0.f;
+      for (int e = lane; e < gc * nn; e += 32) {
+        const int gl = e / nn, ij = e % nn, i = ij / n, j = ij % n;
+        const float* ri = Ts + (gl * n + i) * pitch + cb;
+        const float* rj = Ts + (gl * n + j) * pitch + cb;
+        const float ar = ri[j], ai = ri[n + j], br = rj[i], bi = rj[n + i];
+        sr = fmaf(ar, br, fmaf(-ai, bi, sr));
+        si = fmaf(ar, bi, fmaf(ai, br, si));
+      }
+      double dr = sr, di = si;
+      for (int o = 16; o > 0; o >>= 1) {
+        dr += __shfl_down_sync(0xffffffffu, dr, o);
+        di += __shfl_down_sync(0xffffffffu, di, o);
+      }
+      if (lane == 0 && z < a.W)
+        a.ekp[((long)z * 2 + a.spin) * a.ex_groups + t.gt] = make_double2(-0.5 * dr, -0.5 * di);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// slicing kernels: FP64 -> S bfloat16 planes
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_bf16(double x, int S, __nv_bfloat16* out, long plane) {
+  double r = x;
+  for (int s = 0; s < S; ++s) {
+    const __nv_bfloat16 h = __double2bfloat16(r);
+    out[s * plane] = h;
+    r -= (double)__bfloat162float(h);
+  }
+}
+
+// in: rows x K (row pitch ld); out: S planes of rows x Kp, zero for k >= K
+__global__ void k_slice_real(const double* __restrict__ in, long ld, long rows, int K, int Kp,
+                             int S, __nv_bfloat16* __restrict__ out) {
+  const long total = rows * Kp, plane = rows * Kp;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long r = e / Kp;
+    const int k = (int)(e % Kp);
+    split_bf16(k < K ? in[r * ld + k] : 0.0, S, out + e, plane);
+  }
+}
+
+// thetaT W x N x M complex -> S planes of [z][re/im][j][Mpad]
+__global__ void k_slice_theta(const double2* __restrict__ thetaT, int W, int N, int M, int Mpad,
+                              int S, __nv_bfloat16* __restrict__ out) {
+  const long total = (long)W * N * Mpad, plane = 2 * total;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int p = (int)(e % Mpad);
+    const long zj = e / Mpad;
+    const int j = (int)(zj % N);
+    const long z = zj / N;
+    const double2 v = p < M ? thetaT[zj * M + p] : make_double2(0.0, 0.0);
+    const long base = ((z * 2) * N + j) * Mpad + p;
+    split_bf16(v.x, S, out + base, plane);
+    split_bf16(v.y, S, out + base + (long)N * Mpad, plane);
+  }
+}
+
+// c_zg = sum_ks part[ks][2z + re/im][g] in FP64
+__global__ void k_fb_reduce(int X, int W, int ksplit, const float* __restrict__ part,
+                            double2* __restrict__ c) {
+  const long total = (long)W * X;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const int z = (int)(e / X), g = (int)(e % X);
+    double re = 0.0, im = 0.0;
+    for (int ks = 0; ks < ksplit; ++ks) {
+      re += part[((long)ks * 2 * W + 2 * z) * X + g];
+      im += part[((long)ks * 2 * W + 2 * z + 1) * X + g];
+    }
+    c[e] = make_double2(re, im);
+  }
+}
+
+int grid1d(long n) {
+  long g = (n + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 148 * 32 ? 148 * 32 : g));
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// BF16 tensor map with the 64-byte swizzle; dims[0] is the contiguous K axis.
+bool make_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dims,
+               const uint32_t* box) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gdim[5], gstride[4];
+  cuuint32_t bdim[5], estr[5];
+  uint64_t stride = 2;
+  for (int i = 0; i < rank; ++i) {
+    gdim[i] = dims[i];
+    bdim[i] = box[i];
+    estr[i] = 1;
+    if (i > 0) gstride[i - 1] = stride;
+    stride *= dims[i];
+  }
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), gdim, gstride,
+            bdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+uint32_t tmem_cols_for(int BN) {
+  uint32_t c = 32;
+  while (c < (uint32_t)BN) c <<= 1;
+  return c;
+}
+
+size_t tc_smem(int S, int BN, size_t epilogue_bytes) {
+  size_t pipe = (size_t)kStages * S * (kASlot + (size_t)BN * 64);
+  return (pipe > epilogue_bytes ? pipe : epilogue_bytes) + 1024;
+}
+
+template <int S, class P>
+cudaError_t launch_tc(dim3 grid, size_t smem, cudaStream_t stream, const CUtensorMap& a,
+                      const CUtensorMap& b, const typename P::Args& args) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_split<S, P>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tc_split<S, P><<<grid, kThreads, smem, stream>>>(a, b, args);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_tc_s(int S, dim3 grid, size_t smem, cudaStream_t stream, const CUtensorMap& a,
+                        const CUtensorMap& b, const typename P::Args& args) {
+  switch (S) {
+    case 1: return launch_tc<1, P>(grid, smem, stream, a, b, args);
+    case 2: return launch_tc<2, P>(grid, smem, stream, a, b, args);
+    case 3: return launch_tc<3, P>(grid, smem, stream, a, b, args);
+    case 4: return launch_tc<4, P>(grid, smem, stream, a, b, args);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+// ===========================================================================
+// context integration
+// ===========================================================================
+int mixed_exchange_tiles(int n, int* G, int* zb, int* BN) {
+  if (n <= 0) return 0;
+  *G = 128 / n;
+  *zb = 256 / (2 * n);
+  *BN = round_up(2 * n * *zb, 16);
+  if (*BN > 256) {
+    *zb -= 1;
+    *BN = round_up(2 * n * *zb, 16);
+  }
+  return 1;
+}
+
+void mixed_free(afq_ctx* ctx) {
+  if (ctx->Lt_sl) cudaFree(ctx->Lt_sl);
+  if (ctx->th_sl) cudaFree(ctx->th_sl);
+  if (ctx->fb_part) cudaFree(ctx->fb_part);
+  ctx->Lt_sl = nullptr;
+  ctx->th_sl = nullptr;
+  ctx->fb_part = nullptr;
+}
+
+// Slices L~ once per trial: S planes of [g][j][Mpad].
+int mixed_init_trial(afq_ctx* ctx) {
+  const int S = ctx->S, X = ctx->X, N = ctx->N, M = ctx->M;
+  ctx->Mpad = round_up(M, kBK);
+  const size_t plane = (size_t)X * N * ctx->Mpad;
+  if (ctx->Lt_sl) cudaFree(ctx->Lt_sl);
+  ctx->Lt_sl = nullptr;
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->Lt_sl, plane * S * sizeof(__nv_bfloat16)));
+  k_slice_real<<<grid1d((long)plane), 256, 0, ctx->stream>>>(ctx->Lt, M, (long)X * N, M,
+                                                             ctx->Mpad, S, ctx->Lt_sl);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+// Per walker set: theta slices, force-bias partials and all tensor maps.
+int mixed_init_walkers(afq_ctx* ctx) {
+  const int S = ctx->S, X = ctx->X, N = ctx->N, W = ctx->ws.W, Mp = ctx->Mpad;
+  if (ctx->th_sl) cudaFree(ctx->th_sl);
+  if (ctx->fb_part) cudaFree(ctx->fb_part);
+  ctx->th_sl = nullptr;
+  ctx->fb_part = nullptr;
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_sl,
+                           (size_t)S * W * 2 * N * Mp * sizeof(__nv_bfloat16)));
+  // force bias: rows g (X), columns (z, re/im) (2W), K = N Mpad
+  const int W2 = 2 * W;
+  ctx->fb_BN = W2 >= 256 ? 256 : round_up(W2, 16);
+  const int nkb = N * Mp / kBK;
+  const int tiles = ((X + 127) / 128) * ((W2 + ctx->fb_BN - 1) / ctx->fb_BN);
+  int ks = (296 + tiles - 1) / tiles;
+  if (ks > nkb) ks = nkb;
+  if (ks < 1) ks = 1;
+  ctx->fb_kbper = (nkb + ks - 1) / ks;
+  ctx->fb_ksplit = (nkb + ctx->fb_kbper - 1) / ctx->fb_kbper;
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->fb_part, (size_t)ctx->fb_ksplit * W2 * X * sizeof(float)));
+  {
+    const uint64_t da[3] = {(uint64_t)N * Mp, (uint64_t)X, (uint64_t)S};
+    const uint32_t ba[3] = {kBK, 128, 1};
+    const uint64_t db[3] = {(uint64_t)N * Mp, (uint64_t)W2, (uint64_t)S};
+    const uint32_t bb[3] = {kBK, (uint32_t)ctx->fb_BN, 1};
+    if (!make_tmap(&ctx->tm_fb_a, ctx->Lt_sl, 3, da, ba) ||
+        !make_tmap(&ctx->tm_fb_b, ctx->th_sl, 3, db, bb))
+      return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (force bias) failed");
+  }
+  // exchange: per spin
+  for (int s = 0; s < 2; ++s) {
+    const int n = s ? ctx->nb : ctx->na;
+    if (!mixed_exchange_tiles(n, &ctx->ex_G[s], &ctx->ex_zb[s], &ctx->ex_BN[s])) continue;
+    const uint64_t da[4] = {(uint64_t)Mp, (uint64_t)N, (uint64_t)X, (uint64_t)S};
+    const uint32_t ba[4] = {kBK, (uint32_t)n, (uint32_t)ctx->ex_G[s], 1};
+    const uint64_t db[4] = {(uint64_t)Mp, (uint64_t)N, (uint64_t)W2, (uint64_t)S};
+    const uint32_t bb[4] = {kBK, (uint32_t)n, (uint32_t)(2 * ctx->ex_zb[s]), 1};
+    if (!make_tmap(&ctx->tm_ex_a[s], ctx->Lt_sl, 4, da, ba) ||
+        !make_tmap(&ctx->tm_ex_b[s], ctx->th_sl, 4, db, bb))
+      return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (exchange) failed");
+  }
+  return AFQ_OK;
+}
+
+int launch_slice_theta(afq_ctx* ctx, WalkerSet& s) {
+  const long total = (long)s.W * ctx->N * ctx->Mpad;
+  k_slice_theta<<<grid1d(total), 256, 0, ctx->stream>>>(s.thetaT, s.W, ctx->N, ctx->M, ctx->Mpad,
+                                                        ctx->S, ctx->th_sl);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_force_bias_tc(afq_ctx* ctx, WalkerSet& s) {
+  FbP::Args a{};
+  a.c.nkb = ctx->N * ctx->Mpad / kBK;
+  a.c.BN = ctx->fb_BN;
+  a.c.tx_bytes = (uint32_t)ctx->S * (kBK * 128 * 2 + kBK * ctx->fb_BN * 2);
+  a.c.tmem_cols = tmem_cols_for(ctx->fb_BN);
+  a.c.err = ctx->flags + 2;
+  a.X = ctx->X;
+  a.W2 = 2 * s.W;
+  a.kbper = ctx->fb_kbper;
+  a.part = ctx->fb_part;
+  dim3 grid((a.W2 + a.c.BN - 1) / a.c.BN, (ctx->X + 127) / 128, ctx->fb_ksplit);
+  cudaError_t e = launch_tc_s<FbP>(ctx->S, grid, tc_smem(ctx->S, a.c.BN, 0), ctx->stream,
+                                   ctx->tm_fb_a, ctx->tm_fb_b, a);
+  ctx->launches++;
+  if (e != cudaSuccess) return afq_fail(ctx, AFQ_ERR_CUDA, std::string("force bias tc: ") + cudaGetErrorString(e));
+  k_fb_reduce<<<grid1d((long)s.W * ctx->X), 256, 0, ctx->stream>>>(ctx->X, s.W, ctx->fb_ksplit,
+                                                                   ctx->fb_part, s.c);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+int launch_exchange_tc(afq_ctx* ctx, WalkerSet& s) {
+  for (int spin = 0; spin < 2; ++spin) {
+    const int n = spin ? ctx->nb : ctx->na;
+    if (n == 0) continue;
+    ExP::Args a{};
+    a.c.nkb = ctx->Mpad / kBK;
+    a.c.BN = ctx->ex_BN[spin];
+    a.n = n;
+    a.off = spin ? ctx->na : 0;
+    a.G = ctx->ex_G[spin];
+    a.zb = ctx->ex_zb[spin];
+    a.c.tx_bytes = (uint32_t)ctx->S * (kBK * n * a.G * 2 + kBK * n * 2 * a.zb * 2);
+    a.c.tmem_cols = tmem_cols_for(a.c.BN);
+    a.c.err = ctx->flags + 2;
+    a.X = ctx->X;
+    a.W = s.W;
+    a.spin = spin;
+    a.ex_groups = ctx->ex_groups;
+    a.ekp = s.ekp;
+    const int ngt = (ctx->X + a.G - 1) / a.G;
+    if (ngt > ctx->ex_groups) return afq_fail(ctx, AFQ_ERR_STATE, "exchange tiles exceed slots");
+    dim3 grid(ngt, (s.W + a.zb - 1) / a.zb);
+    const size_t smem = tc_smem(ctx->S, a.c.BN, (size_t)128 * (a.c.BN + 1) * 4);
+    cudaError_t e = launch_tc_s<ExP>(ctx->S, grid, smem, ctx->stream, ctx->tm_ex_a[spin],
+                                     ctx->tm_ex_b[spin], a);
+    ctx->launches++;
+    if (e != cudaSuccess)
+      return afq_fail(ctx, AFQ_ERR_CUDA, std::string("exchange tc: ") + cudaGetErrorString(e));
+  }
+  return AFQ_OK;
+}
+
+// ===========================================================================
+// Library GEMM on the same engine (C ABI)
+// ===========================================================================
+extern "C" int afq_gemm_split_bf16(int m, int n, int k, int slices, const double* A_dev,
+                                   const double* B_dev, double* C_dev, void* cuda_stream) {
+  if (m < 1 || n < 1 || k < 1 || slices < 1 || slices > kMaxSlices || !A_dev || !B_dev || !C_dev)
+    return AFQ_ERR_ARG;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  const int Kp = round_up(k, kBK);
+  const int BN = n >= 256 ? 256 : round_up(n, 16);
+  __nv_bfloat16 *As = nullptr, *Bs = nullptr;
+  int* err = nullptr;
+  int rc = AFQ_OK;
+  if (cudaMalloc((void**)&As, (size_t)slices * m * Kp * 2) != cudaSuccess ||
+      cudaMalloc((void**)&Bs, (size_t)slices * n * Kp * 2) != cudaSuccess ||
+      cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, sizeof(int), stream) != cudaSuccess)
+    rc = AFQ_ERR_NOMEM;
+  CUtensorMap ta, tb;
+  if (rc == AFQ_OK) {
+    k_slice_real<<<grid1d((long)m * Kp), 256, 0, stream>>>(A_dev, k, m, k, Kp, slices, As);
+    k_slice_real<<<grid1d((long)n * Kp), 256, 0, stream>>>(B_dev, k, n, k, Kp, slices, Bs);
+    const uint64_t da[3] = {(uint64_t)Kp, (uint64_t)m, (uint64_t)slices};
+    const uint32_t ba[3] = {kBK, 128, 1};
+    const uint64_t db[3] = {(uint64_t)Kp, (uint64_t)n, (uint64_t)slices};
+    const uint32_t bb[3] = {kBK, (uint32_t)BN, 1};
+    if (!make_tmap(&ta, As, 3, da, ba) || !make_tmap(&tb, Bs, 3, db, bb)) rc = AFQ_ERR_CUDA;
+  }
+  if (rc == AFQ_OK) {
+    GemmP::Args a{};
+    a.c.nkb = Kp / kBK;
+    a.c.BN = BN;
+    a.c.tx_bytes = (uint32_t)slices * (kBK * 128 * 2 + kBK * BN * 2);
+    a.c.tmem_cols = tmem_cols_for(BN);
+    a.c.err = err;
+    a.m = m;
+    a.n = n;
+    a.C = C_dev;
+    a.ldc = n;
+    dim3 grid((n + BN - 1) / BN, (m + 127) / 128);
+    if (launch_tc_s<GemmP>(slices, grid, tc_smem(slices, BN, 0), stream, ta, tb, a) != cudaSuccess)
+      rc = AFQ_ERR_CUDA;
+  }
+  int herr = 0;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) rc = AFQ_ERR_CUDA;
+  if (err && cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && herr)
+    rc = AFQ_ERR_CUDA;
+  cudaFree(As);
+  cudaFree(Bs);
+  cudaFree(err);
+  return rc;
+}

@@ -19,14 +19,15 @@ def make_pair(sysm, W, phi=None, dt=0.005, qr_period=5, seed=1, **kw):
     free = kw.pop("free_projection", False)
     cap = kw.pop("fb_cap", 0.0)
     order = kw.pop("taylor_order", 6)
+    e_shift = kw.pop("e_shift", None)
     ctx = AfqContext(dt=dt, qr_period=qr_period, seed=seed, free_projection=free, fb_cap=cap,
-                     taylor_order=order, **kw)
+                     taylor_order=order, e_shift=e_shift, **kw)
     ctx.init_hamiltonian(sysm.h1, sysm.L, sysm.e0)
     ctx.init_trial(sysm.psi_a, sysm.psi_b)
     phi0 = trial_walkers(sysm, W) if phi is None else phi
     ctx.init_walkers(W, phi0)
     orc = Oracle(sysm.h1, sysm.L, sysm.e0, sysm.psi_a, sysm.psi_b, dt=dt, qr_period=qr_period,
-                 free_projection=free, fb_cap=cap, taylor_order=order, e_shift=kw.get("e_shift"))
+                 free_projection=free, fb_cap=cap, taylor_order=order, e_shift=e_shift)
     orc.init_walkers(phi0)
     return ctx, orc
 

@@ -1,0 +1,105 @@
+"""Split-precision (bf16 slices on tcgen05 tensor cores) against FP64 references.
+
+Tolerances: the mixed-precision target is a mixed-energy error of at most 1e-6 Ha
+per walker against the FP64 oracle.  The GEMM engine's error, relative to
+max|A| max|B| sqrt(K), must fall by 30x from one slice (bf16, 2^-8) to two
+(~2^-16); a third slice then meets the FP32 accumulation floor of the tensor core
+(measured ~3e-7 at K = 150 and ~9e-7 at K = 1000), so it must stay within 1.5x of
+two slices and below 2e-6.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import make_pair, need_gpu, walker_rel
+from oracle import philox
+from paper_2209_04015_b300.synthetic import make_config, make_system, perturbed_walkers
+
+pytestmark = pytest.mark.gpu
+E_TOL = 1e-6  # Ha per walker
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def split_gemm(A, B, slices):
+    import torch
+    from paper_2209_04015_b300 import afqmc as binding
+    Ad = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    Bd = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    Cd = torch.empty((A.shape[0], B.shape[0]), dtype=torch.float64, device="cuda")
+    binding.gemm_split_bf16(A.shape[0], B.shape[0], A.shape[1], slices, Ad.data_ptr(),
+                            Bd.data_ptr(), Cd.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    return Cd.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,k", [(300, 200, 150), (128, 300, 64), (77, 16, 1000)])
+def test_split_gemm_error_shrinks_with_slices(m, n, k):
+    rng = np.random.default_rng(m + n + k)
+    A = rng.standard_normal((m, k))
+    B = rng.standard_normal((n, k)) * np.exp(rng.standard_normal((n, 1)))
+    ref = A @ B.T
+    scale = np.abs(A).max() * np.abs(B).max() * np.sqrt(k)
+    errs = [np.abs(split_gemm(A, B, s) - ref).max() / scale for s in (1, 2, 3)]
+    assert errs[0] < 2e-2
+    assert errs[1] < errs[0] / 30
+    assert errs[2] <= 1.5 * errs[1]
+    assert errs[2] < 2e-6, errs
+
+
+def mixed_vs_oracle(s, W, phi, nsteps, fields=None, **kw):
+    ctx, orc = make_pair(s, W, phi=phi, precision="split_bf16", **kw)
+    e0, _ = ctx.local_energy()
+    e0_ref, _ = orc.local_energy()
+    if nsteps:
+        if fields is None:
+            fields = [philox.gaussian_fields(k, W, s.X, 1) for k in range(nsteps)]
+        ctx.propagate(np.stack(fields), nsteps)
+        orc.propagate(list(fields))
+    e1, _ = ctx.local_energy()
+    e1_ref, _ = orc.local_energy()
+    return ctx, orc, e0, e0_ref, e1, e1_ref
+
+
+@pytest.mark.parametrize("cfg", ["ragged", "c2"])
+def test_mixed_energy_within_1e6_of_fp64_oracle(cfg):
+    if cfg == "ragged":
+        s = make_system(37, 5, 3, 71, seed=4, decay="geometric", e0=0.37)
+        W = 13
+    else:
+        s, c = make_config("c2")
+        W = c["W"]
+    phi = perturbed_walkers(s, W, eps=0.3, seed=2)
+    ctx, orc, e0, e0r, e1, e1r = mixed_vs_oracle(s, W, phi, 2)
+    for e, er in ((e0, e0r), (e1, e1r)):
+        assert np.max(np.abs(e[:, 3] - er[:, 3])) <= E_TOL
+        assert np.max(np.abs(e[:, 2] - er[:, 2])) <= E_TOL   # exchange
+        assert np.max(np.abs(e[:, 1] - er[:, 1])) <= E_TOL   # Coulomb
+    # the propagated walkers stay close: only the force bias is split-precision here
+    assert walker_rel(ctx.get_walkers(), orc.phi).max() < 1e-7
+
+
+def test_mixed_c3_shape_sampled_walkers():
+    """The paper's large shape (290 orbitals, 26+26 electrons, 1500 Cholesky vectors,
+    640 walkers), one step with device fields; 4 walkers re-run by the oracle."""
+    s, c = make_config("c3")
+    W = c["W"]
+    phi = perturbed_walkers(s, W, eps=0.3, seed=2)
+    from paper_2209_04015_b300 import AfqContext
+    from oracle.afqmc import Oracle
+    ctx = AfqContext(dt=0.005, precision="split_bf16")
+    ctx.init_hamiltonian(s.h1, s.L, s.e0)
+    ctx.init_trial(s.psi_a, s.psi_b)
+    ctx.init_walkers(W, phi)
+    e0, _ = ctx.local_energy()
+    ctx.propagate(None, 1)
+    e1, _ = ctx.local_energy()
+    idx = np.array([0, 211, 503, 639])
+    orc = Oracle(s.h1, s.L, s.e0, s.psi_a, s.psi_b, dt=0.005)
+    orc.init_walkers(phi[idx])
+    e0r, _ = orc.local_energy()
+    orc.propagate([philox.gaussian_fields(0, W, s.X, 1)[idx]])
+    e1r, _ = orc.local_energy()
+    assert np.max(np.abs(e0[idx, 3] - e0r[:, 3])) <= E_TOL
+    assert np.max(np.abs(e1[idx, 3] - e1r[:, 3])) <= E_TOL
