@@ -46,9 +46,9 @@ typedef enum afq_status {
 
 typedef enum afq_precision {
   AFQ_FP64 = 0,       /* every contraction in float64                         */
-  AFQ_SPLIT_BF16 = 1, /* the force bias and exchange contractions as split-bf16
-                         tensor-core GEMMs (tcgen05) with FP32 accumulation;
-                         overlaps, inverses, QR and weights stay float64      */
+  AFQ_SPLIT_BF16 = 1, /* force bias, exchange, VHS and propagator contractions as
+                         split-bf16 tensor-core GEMMs (tcgen05); overlaps,
+                         inverses, QR and weights stay float64                */
   AFQ_SPLIT_TF32 = 2  /* reserved                                              */
 } afq_precision;
 
@@ -63,12 +63,17 @@ typedef struct afq_params {
   double e_shift;      /* energy shift in exp(-dt (H - E_shift))                 */
   double fb_cap;       /* |xbar_g| cap; 0 = off                                  */
   int free_projection; /* 1: complex weights w <- w I (no phaseless cut)         */
-  int split_slices;    /* AFQ_SPLIT_BF16: bf16 slices per FP64 operand, 1..4
-                          (slice products s + t <= slices - 1 are kept); 0 = 3  */
+  int split_slices;    /* AFQ_SPLIT_BF16: bf16 slices per FP64 operand of the force
+                          bias and exchange, 1..4 (slice products s + t <= slices - 1
+                          are kept, FP32 accumulation); 0 = 3                    */
+  int prop_slices;     /* AFQ_SPLIT_BF16: exact 8-bit digits per FP64 operand of the
+                          VHS and propagator GEMMs, 1..4 (per-row power-of-two scale,
+                          one exact TMEM accumulator per digit order); 0 = 4     */
 } afq_params;
 
 /* Fill *p with the defaults: dt 0.005, Taylor order 6, QR every 5 steps, seed 1,
-   FP64, E_shift = trial energy, no cap, phaseless, 3 slices in split mode. */
+   FP64, E_shift = trial energy, no cap, phaseless; in split mode 3 slices for the
+   force bias and exchange and 4 exact digits for the propagation. */
 void afq_default_params(afq_params* p);
 
 /* Create a context bound to cuda_stream (a cudaStream_t, or NULL for the legacy

@@ -28,7 +28,8 @@ class AfqParams(ctypes.Structure):
                 ("qr_period", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int), ("has_e_shift", ctypes.c_int),
                 ("e_shift", ctypes.c_double), ("fb_cap", ctypes.c_double),
-                ("free_projection", ctypes.c_int), ("split_slices", ctypes.c_int)]
+                ("free_projection", ctypes.c_int), ("split_slices", ctypes.c_int),
+                ("prop_slices", ctypes.c_int)]
 
 
 class AfqError(RuntimeError):
@@ -124,7 +125,7 @@ class AfqContext:
     def __init__(self, dt: float = 0.005, taylor_order: int = 6, qr_period: int = 5,
                  seed: int = 1, precision: str = "fp64", e_shift: float | None = None,
                  fb_cap: float = 0.0, free_projection: bool = False, stream: int | None = None,
-                 split_slices: int = 3):
+                 split_slices: int = 3, prop_slices: int = 4):
         self.lib = load_library()
         p = AfqParams()
         self.lib.afq_default_params(ctypes.byref(p))
@@ -135,6 +136,7 @@ class AfqContext:
         p.fb_cap = fb_cap
         p.free_projection = 1 if free_projection else 0
         p.split_slices = split_slices
+        p.prop_slices = prop_slices
         self.params = p
         h = _P()
         rc = self.lib.afq_create(ctypes.byref(h), ctypes.byref(p), _P(stream or 0))

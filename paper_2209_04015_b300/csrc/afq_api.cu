@@ -200,8 +200,13 @@ int one_step(afq_ctx* ctx, const double* xi_dev) {
   const double log_const = -ctx->p.dt * (ctx->e0 - 0.5 * ctx->sum_vbar2 - ctx->e_shift);
   const uint64_t step = ctx->step;
   AFQ_TRY(timed(ctx, AFQ_K_FIELDS, [&] { return launch_fields(ctx, xi_dev, step); }));
-  AFQ_TRY(timed(ctx, AFQ_K_VHS, [&] { return launch_vhs_fp64(ctx); }));
-  AFQ_TRY(timed(ctx, AFQ_K_PROPAGATE, [&] { return launch_propagate_fp64(ctx); }));
+  if (ctx->mixed) {
+    AFQ_TRY(timed(ctx, AFQ_K_VHS, [&] { return launch_vhs_tc(ctx); }));
+    AFQ_TRY(timed(ctx, AFQ_K_PROPAGATE, [&] { return launch_propagate_tc(ctx); }));
+  } else {
+    AFQ_TRY(timed(ctx, AFQ_K_VHS, [&] { return launch_vhs_fp64(ctx); }));
+    AFQ_TRY(timed(ctx, AFQ_K_PROPAGATE, [&] { return launch_propagate_fp64(ctx); }));
+  }
   AFQ_TRY(green_and_bias(ctx, ctx->ws));
   AFQ_TRY(timed(ctx, AFQ_K_WEIGHTS, [&] { return launch_weights(ctx, log_const); }));
   ctx->step++;
@@ -227,6 +232,7 @@ void afq_default_params(afq_params* p) {
   p->fb_cap = 0.0;
   p->free_projection = 0;
   p->split_slices = 3;
+  p->prop_slices = 4;
 }
 
 int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
@@ -240,15 +246,18 @@ int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
     afq_default_params(&ctx->p);
   }
   if (ctx->p.split_slices == 0) ctx->p.split_slices = 3;
+  if (ctx->p.prop_slices == 0) ctx->p.prop_slices = 4;
   if (!(ctx->p.dt > 0.0) || ctx->p.taylor_order < 1 || ctx->p.taylor_order > 32 ||
       ctx->p.qr_period < 0 ||
       (ctx->p.precision != AFQ_FP64 && ctx->p.precision != AFQ_SPLIT_BF16) ||
-      ctx->p.split_slices < 1 || ctx->p.split_slices > 4) {
+      ctx->p.split_slices < 1 || ctx->p.split_slices > 4 || ctx->p.prop_slices < 1 ||
+      ctx->p.prop_slices > 4) {
     delete ctx;
     return AFQ_ERR_ARG;
   }
   ctx->mixed = ctx->p.precision == AFQ_SPLIT_BF16;
   ctx->S = ctx->p.split_slices;
+  ctx->Sp = ctx->p.prop_slices;
   ctx->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     delete ctx;
@@ -438,6 +447,7 @@ int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a, const doub
   ctx->e_shift = ctx->p.has_e_shift ? ctx->p.e_shift : ctx->e_trial;
   if (ctx->mixed) {
     AFQ_TRY(mixed_init_trial(ctx));
+    AFQ_TRY(mixed_prop_init_trial(ctx));
     AFQ_TRY(sync(ctx));
   }
   return AFQ_OK;
@@ -483,7 +493,10 @@ int afq_init_walkers(afq_ctx* ctx, int W, const double* phi, const double* w) {
   std::vector<double2> wv(W);
   for (int z = 0; z < W; ++z) wv[z] = make_double2(w ? w[z] : 1.0, 0.0);
   AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->ws.w, wv.data(), W * 16, cudaMemcpyHostToDevice, ctx->stream));
-  if (ctx->mixed) AFQ_TRY(mixed_init_walkers(ctx));
+  if (ctx->mixed) {
+    AFQ_TRY(mixed_init_walkers(ctx));
+    AFQ_TRY(mixed_prop_init_walkers(ctx));
+  }
   AFQ_TRY(green_and_bias(ctx, ctx->ws));
   AFQ_TRY(launch_init_overlap(ctx, ctx->ws));
   AFQ_TRY(sync(ctx));

@@ -100,7 +100,8 @@ struct afq_ctx {
 
   // split-precision (AFQ_SPLIT_BF16) state
   bool mixed = false;
-  int S = 3;                          // bf16 slices per operand
+  int S = 3;                          // bf16 slices per operand (force bias, exchange)
+  int Sp = 4;                         // exact digits per operand (propagation)
   int Mpad = 0;                       // M rounded up to the 32-wide K block
   __nv_bfloat16* Lt_sl = nullptr;     // S x X x N x Mpad slices of L~
   __nv_bfloat16* th_sl = nullptr;     // S x W x 2 x N x Mpad slices of theta (re, im planes)
@@ -108,6 +109,18 @@ struct afq_ctx {
   int fb_BN = 0, fb_kbper = 0, fb_ksplit = 0;
   int ex_G[2] = {0, 0}, ex_zb[2] = {0, 0}, ex_BN[2] = {0, 0};
   CUtensorMap tm_fb_a, tm_fb_b, tm_ex_a[2], tm_ex_b[2];
+  // split-precision propagation operands (k_mixed_prop.cu)
+  int Xpad = 0, vhs_BN = 0, prop_BN = 0;
+  __nv_bfloat16* LT_sl = nullptr;     // S x M^2 x Xpad: L^T, the VHS operand
+  __nv_bfloat16* Pm_sl = nullptr;     // S x M x Mpad: P - I
+  __nv_bfloat16* y_sl = nullptr;      // S x 2W x Xpad: shifted fields (re, im rows)
+  __nv_bfloat16* A_sl = nullptr;      // S x 2W x M x Mpad: i sqrt(dt) V (re, im planes)
+  __nv_bfloat16* T_sl[2] = {nullptr, nullptr};  // S x 2W x N x Mpad: Taylor operands
+  double2* accT = nullptr;            // W x N x M FP64 accumulator of the propagated walker
+  double2* tout = nullptr;            // W x N x M FP64 operand between propagation launches
+  int *e_lt = nullptr, *e_pm = nullptr, *e_y = nullptr, *e_a = nullptr;  // row exponents
+  int* e_t[2] = {nullptr, nullptr};
+  CUtensorMap tm_vhs_a, tm_vhs_b, tm_pm, tm_az, tm_t[2];
 
   // built-in profiler: event pairs around launches of each kernel class
   bool profiling = false;
@@ -174,3 +187,8 @@ void mixed_free(afq_ctx* ctx);
 int launch_slice_theta(afq_ctx* ctx, WalkerSet& s);
 int launch_force_bias_tc(afq_ctx* ctx, WalkerSet& s);
 int launch_exchange_tc(afq_ctx* ctx, WalkerSet& s);
+void mixed_prop_free(afq_ctx* ctx);
+int mixed_prop_init_trial(afq_ctx* ctx);
+int mixed_prop_init_walkers(afq_ctx* ctx);
+int launch_vhs_tc(afq_ctx* ctx);
+int launch_propagate_tc(afq_ctx* ctx);

@@ -1,180 +1,14 @@
-// Split-precision tensor-core contractions of libafqmc (precision AFQ_SPLIT_BF16).
-//
-// Each FP64 operand x is split into S bfloat16 slices, x ~ x_0 + x_1 + ... + x_{S-1}
-// (x_0 = bf16(x), x_k = bf16 of the remainder), and a product A B^T becomes the sum of
-// the slice products A_s B_t^T with s + t <= S - 1, issued as tcgen05.mma (BF16 in,
-// FP32 accumulate in TMEM) into one accumulator, smallest terms first.  With S = 3
-// (six products) the result carries about 24 significant bits.
-//
-// One kernel template serves three contractions (the force bias / Coulomb vector of
-// Eq. rfb, the exchange term of Sec. "Local energy", and a plain GEMM used to test
-// the engine); a policy supplies the tile coordinates, the TMA loads and the
-// epilogue.  Roles inside a 128-thread CTA: thread 0 issues TMA loads into a
-// three-stage ring (all slices of one 32-wide K block per stage, 64-byte swizzle),
-// thread 32 issues the MMAs and commits each stage back to the producer, and all four
-// warps read the 128 x BN accumulator out of TMEM for the epilogue.
-#include <cudaTypedefs.h>
-
+// Split-precision tensor-core contractions of the walker's Green's-function
+// intermediates (precision AFQ_SPLIT_BF16): the force bias / Coulomb vector of
+// Eq. rfb and the exchange term of Sec. "Local energy", plus a plain GEMM entry
+// point that exercises the same engine (tc_engine.cuh).
 #include <cstdio>
-#include <mutex>
 
-#include "afq_internal.cuh"
-#include "tc_sm103.cuh"
+#include "tc_engine.cuh"
+
+using namespace tce;
 
 namespace {
-
-constexpr int kThreads = 128;
-constexpr int kBK = 32;             // K elements per block: one 64-byte row
-constexpr int kASlot = 128 * 64;    // bytes of one A slice of one K block
-constexpr int kStages = 3;
-constexpr int kMaxSlices = 4;
-
-// Slice pairs (s, t) with s + t <= S - 1, ordered from the smallest contributions.
-template <int S>
-__device__ __forceinline__ void slice_pair(int k, int& s, int& t) {
-  int idx = 0;
-#pragma unroll
-  for (int d = S - 1; d >= 0; --d)
-#pragma unroll
-    for (int ss = d; ss >= 0; --ss) {
-      if (idx == k) {
-        s = ss;
-        t = d - ss;
-      }
-      ++idx;
-    }
-}
-
-struct TcCommon {
-  int nkb;            // K blocks in the whole K range
-  int BN;             // MMA N (multiple of 16, <= 256)
-  uint32_t tx_bytes;  // bytes the TMA loads of one stage deliver
-  uint32_t tmem_cols;
-  int* err;           // set to 1 when a pipeline wait times out
-};
-
-// ---------------------------------------------------------------------------
-// The kernel template
-// ---------------------------------------------------------------------------
-template <int S, class P>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_tc_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const typename P::Args args) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  __shared__ __align__(8) uint64_t full[kStages];
-  __shared__ __align__(8) uint64_t empty[kStages];
-  __shared__ __align__(8) uint64_t done;
-  __shared__ uint32_t tmem_base;
-  __shared__ int fail;
-  __shared__ int skip;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const typename P::Tile t = P::tile(args);
-  const int BN = args.c.BN;
-  const uint32_t bslot = (uint32_t)BN * 64u;
-  const uint32_t stage_bytes = S * (kASlot + bslot);
-  int* err = args.c.err;
-  // another CTA already failed: do nothing (decided once for the whole CTA, before
-  // any barrier or TMEM is set up)
-  if (threadIdx.x == 0) skip = *(const volatile int*)err;
-  __syncthreads();
-  if (skip) return;
-
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) {
-      tc::mbar_init(&full[i], 1);
-      tc::mbar_init(&empty[i], 1);
-    }
-    tc::mbar_init(&done, 1);
-    fail = 0;
-    tc::fence_mbar_init();
-    tc::prefetch_tmap(&tmA);
-    tc::prefetch_tmap(&tmB);
-  }
-  if (warp == 0) {
-    tc::tmem_alloc(&tmem_base, args.c.tmem_cols);
-    tc::tmem_relinquish();
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = tmem_base;
-  const int nkb = t.kb1 - t.kb0;
-
-  if (threadIdx.x == 0) {
-    // TMA producer
-    int issued = 0;
-    for (int i = 0; i < nkb; ++i) {
-      const int st = i % kStages;
-      if (i >= kStages && !tc::mbar_wait(&empty[st], ((i / kStages) - 1) & 1, err)) {
-        fail = 1;
-        atomicExch(err, 1);
-        break;
-      }
-      tc::mbar_arrive_expect_tx(&full[st], args.c.tx_bytes);
-      uint8_t* sa = smem + st * stage_bytes;
-      uint8_t* sb = sa + S * kASlot;
-#pragma unroll
-      for (int s = 0; s < S; ++s) P::load_a(&tmA, sa + s * kASlot, args, t, s, t.kb0 + i, &full[st]);
-#pragma unroll
-      for (int s = 0; s < S; ++s) P::load_b(&tmB, sb + s * bslot, args, t, s, t.kb0 + i, &full[st]);
-      ++issued;
-    }
-    // no TMA write may still be in flight when the CTA moves on
-    for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
-      tc::mbar_wait(&full[i % kStages], (i / kStages) & 1, err);
-  } else if (threadIdx.x == 32) {
-    // MMA issuer
-    const uint32_t idesc = tc::idesc_bf16(128, BN);
-    for (int i = 0; i < nkb; ++i) {
-      const int st = i % kStages;
-      if (!tc::mbar_wait(&full[st], (i / kStages) & 1, err)) {
-        fail = 1;
-        atomicExch(err, 1);
-        break;
-      }
-      tc::fence_after_sync();
-      const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
-      const uint32_t sb = sa + S * kASlot;
-#pragma unroll
-      for (int k = 0; k < S * (S + 1) / 2; ++k) {
-        int s = 0, u = 0;
-        slice_pair<S>(k, s, u);
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks)
-          tc::mma_bf16(tmem, tc::sdesc_k64(sa + s * kASlot + ks * 32),
-                       tc::sdesc_k64(sb + u * bslot + ks * 32), idesc, (i | k | ks) != 0);
-      }
-      tc::mma_commit(&empty[st]);
-    }
-    tc::mma_commit(&done);
-  }
-  bool ok = tc::mbar_wait(&done, 0, err);
-  // the MMAs already issued must finish before TMEM is read or freed: wait again,
-  // bounded by time only
-  if (!ok) {
-    static const int zero = 0;
-    ok = tc::mbar_wait(&done, 0, &zero);
-  }
-  if (!ok) fail = 1;
-  tc::fence_after_sync();
-  __syncthreads();
-  const bool bad = fail != 0;
-  __syncwarp();
-  if (bad) {
-    if (threadIdx.x == 0) atomicExch(args.c.err, 1);
-  } else {
-    P::epilogue(args, t, tmem, smem, warp, lane);
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, args.c.tmem_cols);
-}
-
-__device__ __forceinline__ void tmem_row16(uint32_t tmem, int warp, int c0, float (&v)[16]) {
-  tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-}
 
 // ---------------------------------------------------------------------------
 // Policy: plain GEMM C (m x n, FP64) = A (m x K) B (n x K)^T from slice planes
@@ -187,20 +21,27 @@ struct GemmP {
     double* C;
     long ldc;
   };
+  static constexpr int kUA = 1, kUB = 1;
+  template <int S>
+  static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
+                               uint32_t bslot, bool first) {
+    issue_pairs<S>(tmem, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN), first);
+  }
   struct Tile {
     int m0, n0, kb0, kb1;
   };
   static __device__ Tile tile(const Args& a) {
     return Tile{(int)blockIdx.y * 128, (int)blockIdx.x * a.c.BN, 0, a.c.nkb};
   }
-  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int s,
-                                int kb, uint64_t* bar) {
+  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int,
+                                int s, int kb, uint64_t* bar) {
     tc::tma_load_3d(dst, tm, kb * kBK, t.m0, s, bar);
   }
-  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int s,
-                                int kb, uint64_t* bar) {
+  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int,
+                                int s, int kb, uint64_t* bar) {
     tc::tma_load_3d(dst, tm, kb * kBK, t.n0, s, bar);
   }
+  template <int S>
   static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t*, int warp,
                                   int lane) {
     const int row = t.m0 + warp * 32 + lane;
@@ -227,6 +68,12 @@ struct FbP {
     int X, W2, kbper;
     float* part;
   };
+  static constexpr int kUA = 1, kUB = 1;
+  template <int S>
+  static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
+                               uint32_t bslot, bool first) {
+    issue_pairs<S>(tmem, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN), first);
+  }
   struct Tile {
     int g0, n0, ks, kb0, kb1;
   };
@@ -236,14 +83,15 @@ struct FbP {
     const int kb1 = min(a.c.nkb, kb0 + a.kbper);
     return Tile{(int)blockIdx.y * 128, (int)blockIdx.x * a.c.BN, ks, kb0, kb1};
   }
-  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int s,
-                                int kb, uint64_t* bar) {
+  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int,
+                                int s, int kb, uint64_t* bar) {
     tc::tma_load_3d(dst, tm, kb * kBK, t.g0, s, bar);
   }
-  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int s,
-                                int kb, uint64_t* bar) {
+  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int,
+                                int s, int kb, uint64_t* bar) {
     tc::tma_load_3d(dst, tm, kb * kBK, t.n0, s, bar);
   }
+  template <int S>
   static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t*, int warp,
                                   int lane) {
     const int g = t.g0 + warp * 32 + lane;
@@ -274,6 +122,12 @@ struct ExP {
     int n, off, G, zb, X, W, spin, ex_groups;
     double2* ekp;
   };
+  static constexpr int kUA = 1, kUB = 1;
+  template <int S>
+  static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
+                               uint32_t bslot, bool first) {
+    issue_pairs<S>(tmem, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN), first);
+  }
   struct Tile {
     int gt, g0, z0, kb0, kb1;
   };
@@ -281,13 +135,14 @@ struct ExP {
     return Tile{(int)blockIdx.x, (int)blockIdx.x * a.G, (int)blockIdx.y * a.zb, 0, a.c.nkb};
   }
   static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args& a, const Tile& t,
-                                int s, int kb, uint64_t* bar) {
+                                int, int s, int kb, uint64_t* bar) {
     tc::tma_load_4d(dst, tm, kb * kBK, a.off, t.g0, s, bar);
   }
   static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args& a, const Tile& t,
-                                int s, int kb, uint64_t* bar) {
+                                int, int s, int kb, uint64_t* bar) {
     tc::tma_load_4d(dst, tm, kb * kBK, a.off, 2 * t.z0, s, bar);
   }
+  template <int S>
   static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t* smem,
                                   int warp, int lane) {
     const int n = a.n, BN = a.c.BN, pitch = BN + 1;
@@ -328,15 +183,6 @@ struct ExP {
 // ---------------------------------------------------------------------------
 // slicing kernels: FP64 -> S bfloat16 planes
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void split_bf16(double x, int S, __nv_bfloat16* out, long plane) {
-  double r = x;
-  for (int s = 0; s < S; ++s) {
-    const __nv_bfloat16 h = __double2bfloat16(r);
-    out[s * plane] = h;
-    r -= (double)__bfloat162float(h);
-  }
-}
-
 // in: rows x K (row pitch ld); out: S planes of rows x Kp, zero for k >= K
 __global__ void k_slice_real(const double* __restrict__ in, long ld, long rows, int K, int Kp,
                              int S, __nv_bfloat16* __restrict__ out) {
@@ -382,83 +228,6 @@ __global__ void k_fb_reduce(int X, int W, int ksplit, const float* __restrict__ 
   }
 }
 
-int grid1d(long n) {
-  long g = (n + 255) / 256;
-  return (int)(g < 1 ? 1 : (g > 148 * 32 ? 148 * 32 : g));
-}
-
-// ---------------------------------------------------------------------------
-// host helpers
-// ---------------------------------------------------------------------------
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
-
-// BF16 tensor map with the 64-byte swizzle; dims[0] is the contiguous K axis.
-bool make_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dims,
-               const uint32_t* box) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t gdim[5], gstride[4];
-  cuuint32_t bdim[5], estr[5];
-  uint64_t stride = 2;
-  for (int i = 0; i < rank; ++i) {
-    gdim[i] = dims[i];
-    bdim[i] = box[i];
-    estr[i] = 1;
-    if (i > 0) gstride[i - 1] = stride;
-    stride *= dims[i];
-  }
-  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), gdim, gstride,
-            bdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-uint32_t tmem_cols_for(int BN) {
-  uint32_t c = 32;
-  while (c < (uint32_t)BN) c <<= 1;
-  return c;
-}
-
-size_t tc_smem(int S, int BN, size_t epilogue_bytes) {
-  size_t pipe = (size_t)kStages * S * (kASlot + (size_t)BN * 64);
-  return (pipe > epilogue_bytes ? pipe : epilogue_bytes) + 1024;
-}
-
-template <int S, class P>
-cudaError_t launch_tc(dim3 grid, size_t smem, cudaStream_t stream, const CUtensorMap& a,
-                      const CUtensorMap& b, const typename P::Args& args) {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_split<S, P>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_tc_split<S, P><<<grid, kThreads, smem, stream>>>(a, b, args);
-  return cudaGetLastError();
-}
-
-template <class P>
-cudaError_t launch_tc_s(int S, dim3 grid, size_t smem, cudaStream_t stream, const CUtensorMap& a,
-                        const CUtensorMap& b, const typename P::Args& args) {
-  switch (S) {
-    case 1: return launch_tc<1, P>(grid, smem, stream, a, b, args);
-    case 2: return launch_tc<2, P>(grid, smem, stream, a, b, args);
-    case 3: return launch_tc<3, P>(grid, smem, stream, a, b, args);
-    case 4: return launch_tc<4, P>(grid, smem, stream, a, b, args);
-  }
-  return cudaErrorInvalidValue;
-}
-
-int round_up(int v, int m) { return (v + m - 1) / m * m; }
-
 }  // namespace
 
 // ===========================================================================
@@ -477,6 +246,7 @@ int mixed_exchange_tiles(int n, int* G, int* zb, int* BN) {
 }
 
 void mixed_free(afq_ctx* ctx) {
+  mixed_prop_free(ctx);
   if (ctx->Lt_sl) cudaFree(ctx->Lt_sl);
   if (ctx->th_sl) cudaFree(ctx->th_sl);
   if (ctx->fb_part) cudaFree(ctx->fb_part);
@@ -562,9 +332,10 @@ int launch_force_bias_tc(afq_ctx* ctx, WalkerSet& s) {
   a.W2 = 2 * s.W;
   a.kbper = ctx->fb_kbper;
   a.part = ctx->fb_part;
+  size_t smem = 0;
+  plan_smem(ctx->S, 1, 1, a.c.BN, 0, &a.c.stages, &smem);
   dim3 grid((a.W2 + a.c.BN - 1) / a.c.BN, (ctx->X + 127) / 128, ctx->fb_ksplit);
-  cudaError_t e = launch_tc_s<FbP>(ctx->S, grid, tc_smem(ctx->S, a.c.BN, 0), ctx->stream,
-                                   ctx->tm_fb_a, ctx->tm_fb_b, a);
+  cudaError_t e = launch_tc_s<FbP>(ctx->S, grid, smem, ctx->stream, ctx->tm_fb_a, ctx->tm_fb_b, a);
   ctx->launches++;
   if (e != cudaSuccess) return afq_fail(ctx, AFQ_ERR_CUDA, std::string("force bias tc: ") + cudaGetErrorString(e));
   k_fb_reduce<<<grid1d((long)s.W * ctx->X), 256, 0, ctx->stream>>>(ctx->X, s.W, ctx->fb_ksplit,
@@ -595,7 +366,8 @@ int launch_exchange_tc(afq_ctx* ctx, WalkerSet& s) {
     const int ngt = (ctx->X + a.G - 1) / a.G;
     if (ngt > ctx->ex_groups) return afq_fail(ctx, AFQ_ERR_STATE, "exchange tiles exceed slots");
     dim3 grid(ngt, (s.W + a.zb - 1) / a.zb);
-    const size_t smem = tc_smem(ctx->S, a.c.BN, (size_t)128 * (a.c.BN + 1) * 4);
+    size_t smem = 0;
+    plan_smem(ctx->S, 1, 1, a.c.BN, (size_t)128 * (a.c.BN + 1) * 4, &a.c.stages, &smem);
     cudaError_t e = launch_tc_s<ExP>(ctx->S, grid, smem, ctx->stream, ctx->tm_ex_a[spin],
                                      ctx->tm_ex_b[spin], a);
     ctx->launches++;
@@ -640,12 +412,14 @@ extern "C" int afq_gemm_split_bf16(int m, int n, int k, int slices, const double
     a.c.tx_bytes = (uint32_t)slices * (kBK * 128 * 2 + kBK * BN * 2);
     a.c.tmem_cols = tmem_cols_for(BN);
     a.c.err = err;
+    size_t smem = 0;
+    plan_smem(slices, 1, 1, BN, 0, &a.c.stages, &smem);
     a.m = m;
     a.n = n;
     a.C = C_dev;
     a.ldc = n;
     dim3 grid((n + BN - 1) / BN, (m + 127) / 128);
-    if (launch_tc_s<GemmP>(slices, grid, tc_smem(slices, BN, 0), stream, ta, tb, a) != cudaSuccess)
+    if (launch_tc_s<GemmP>(slices, grid, smem, stream, ta, tb, a) != cudaSuccess)
       rc = AFQ_ERR_CUDA;
   }
   int herr = 0;

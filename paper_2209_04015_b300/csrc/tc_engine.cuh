@@ -1,0 +1,370 @@
+// The split-precision tensor-core GEMM engine of libafqmc (sm_103a).
+//
+// Each FP64 operand x is split into S bfloat16 slices, x ~ x_0 + x_1 + ... + x_{S-1}
+// (x_0 = bf16(x), x_k = bf16 of the remainder), and a product A B^T becomes the sum
+// of the slice products A_s B_t^T with s + t <= S - 1, issued as tcgen05.mma (BF16 in,
+// FP32 accumulate in TMEM), smallest terms first.
+//
+// k_tc_split is one kernel template for every contraction; a policy P supplies the
+// tile coordinates, the TMA loads of its operand units, the MMAs of one stage and
+// the epilogue.  A stage holds all S slices of P::kUA A units (128 rows x 32 K,
+// 8 KB each) and P::kUB B units (BN rows x 32 K) of one K block, 64-byte swizzled.
+// Roles in a 128-thread CTA: thread 0 issues the TMA loads into a ring of stages,
+// thread 32 issues the MMAs and commits each stage back to the producer, and all
+// four warps (one per 32 TMEM lanes) run the epilogue out of TMEM.  Every wait is
+// bounded in time and by a grid-wide error flag, so a broken pipeline ends the
+// kernel with an error instead of hanging.
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include <string>
+
+#include "afq_internal.cuh"
+#include "tc_sm103.cuh"
+
+namespace tce {
+
+constexpr int kThreads = 128;
+constexpr int kBK = 32;           // K elements per block: one 64-byte row
+constexpr int kASlot = 128 * 64;  // bytes of one 128-row A unit of one K block
+constexpr int kMaxStages = 4;
+constexpr int kMaxSlices = 4;
+constexpr size_t kSmemLimit = 227 * 1024;
+
+struct TcCommon {
+  int nkb;            // K blocks of a full K range
+  int BN;             // MMA N (multiple of 16, <= 256)
+  uint32_t tx_bytes;  // bytes the TMA loads of one stage deliver
+  uint32_t tmem_cols;
+  int stages;         // ring depth, 1..kMaxStages
+  int* err;           // grid-wide error flag: set to 1 when a pipeline wait gives up
+};
+
+// Slice pairs (s, t) with s + t <= S - 1, from the smallest contributions up.
+template <int S>
+__device__ __forceinline__ void slice_pair(int k, int& s, int& t) {
+  int idx = 0;
+#pragma unroll
+  for (int d = S - 1; d >= 0; --d)
+#pragma unroll
+    for (int ss = d; ss >= 0; --ss) {
+      if (idx == k) {
+        s = ss;
+        t = d - ss;
+      }
+      ++idx;
+    }
+}
+
+// Shared-memory byte address of A unit u, slice s (and the same for B).
+__device__ __forceinline__ uint32_t a_unit(uint32_t sa, int S, int u, int s) {
+  return sa + (uint32_t)(u * S + s) * kASlot;
+}
+__device__ __forceinline__ uint32_t b_unit(uint32_t sb, uint32_t bslot, int S, int u, int s) {
+  return sb + (uint32_t)(u * S + s) * bslot;
+}
+
+// The MMAs of one stage for one A unit and one B unit into one accumulator.
+template <int S>
+__device__ __forceinline__ void issue_pairs(uint32_t acc, uint32_t sa, uint32_t sb, uint32_t bslot,
+                                            int ua, int ub, uint32_t idesc, bool first) {
+#pragma unroll
+  for (int k = 0; k < S * (S + 1) / 2; ++k) {
+    int s = 0, t = 0;
+    slice_pair<S>(k, s, t);
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+      tc::mma_bf16(acc, tc::sdesc_k64(a_unit(sa, S, ua, s) + ks * 32),
+                   tc::sdesc_k64(b_unit(sb, bslot, S, ub, t) + ks * 32), idesc,
+                   !(first && k == 0 && ks == 0));
+  }
+}
+
+// Exact-diagonal form: pair (s, d - s) goes to accumulator d (acc0 + d * stride
+// columns).  With integer slices (split_exact) every accumulator holds an integer
+// sum below 2^24, so the FP32 accumulation is exact and the diagonals are combined
+// in FP64 afterwards.
+template <int S>
+__device__ __forceinline__ void issue_diagonals(uint32_t acc0, uint32_t stride, uint32_t sa,
+                                                uint32_t sb, uint32_t bslot, int ua, int ub,
+                                                uint32_t idesc, bool first) {
+#pragma unroll
+  for (int d = 0; d < S; ++d)
+#pragma unroll
+    for (int s = 0; s <= d; ++s)
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks)
+        tc::mma_bf16(acc0 + (uint32_t)d * stride, tc::sdesc_k64(a_unit(sa, S, ua, s) + ks * 32),
+                     tc::sdesc_k64(b_unit(sb, bslot, S, ub, d - s) + ks * 32), idesc,
+                     !(first && s == 0 && ks == 0));
+}
+
+// Biased exponent field of a double (0 for zero and subnormals).  On B300 the
+// FP64 pipe is ~64x slower than the integer pipe, so the row scales, the digits and
+// the recombination below are done on the bits with integer instructions.
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// Row exponent e with |x| <= 2^e for a row whose largest exponent field is emax.
+__device__ __forceinline__ int row_exponent_field(int emax) { return emax ? emax - 1022 : 0; }
+
+// Integer digits of x relative to the row scale 2^e (|x| <= 2^e):
+// x ~ 2^(e-7) sum_s q_s 256^-s with balanced digits q_s in [-128, 128] (exact in
+// bfloat16), written S planes apart.  Rounds x 2^(7-e+8(S-1)) to the nearest
+// integer and cuts it into base-256 digits.
+__device__ __forceinline__ void split_exact(double x, int e, int S, __nv_bfloat16* out,
+                                            long plane) {
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long v = 0;
+  if (E != 0) {
+    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = E - 1075 + 7 - e + 8 * (S - 1);  // value = mant 2^(E-1075)
+    if (sh >= 0)
+      v = sh < 10 ? mant << sh : 0;  // cannot happen for |x| <= 2^e and S <= 4
+    else if (sh > -64)
+      v = (mant + (1LL << (-sh - 1))) >> (-sh);
+  }
+  const bool neg = bits < 0;
+  int q[kMaxSlices];
+#pragma unroll
+  for (int s = kMaxSlices - 1; s >= 0; --s) {
+    if (s >= S) continue;
+    int d = (int)(v & 255);
+    if (d > 128) d -= 256;
+    q[s] = d;
+    v = (v - d) >> 8;
+  }
+#pragma unroll
+  for (int s = 0; s < kMaxSlices; ++s)
+    if (s < S) out[s * plane] = __float2bfloat16_rn((float)(neg ? -q[s] : q[s]));
+}
+
+// Recombines the S exact diagonal accumulators of one element:
+// value = 2^scale_exp sum_d acc_d 256^-d, through one int64 and one conversion.
+template <int S>
+__device__ __forceinline__ double combine_exact(const float (&acc)[S], int scale_exp) {
+  long long t = 0;
+#pragma unroll
+  for (int d = 0; d < S; ++d) t += (long long)__float2int_rn(acc[d]) * (1LL << (8 * (S - 1 - d)));
+  if (t == 0) return 0.0;
+  const double v = __ll2double_rn(t);
+  return __longlong_as_double(__double_as_longlong(v) +
+                              ((long long)(scale_exp - 8 * (S - 1)) << 52));
+}
+
+__device__ __forceinline__ void tmem_row16(uint32_t tmem, int warp, int c0, float (&v)[16]) {
+  tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+}
+
+// Split x into S bfloat16 slices written S planes apart.
+__device__ __forceinline__ void split_bf16(double x, int S, __nv_bfloat16* out, long plane) {
+  double r = x;
+  for (int s = 0; s < S; ++s) {
+    const __nv_bfloat16 h = __double2bfloat16(r);
+    out[s * plane] = h;
+    r -= (double)__bfloat162float(h);
+  }
+}
+
+template <int S, class P>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const typename P::Args args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full[kMaxStages];
+  __shared__ __align__(8) uint64_t empty[kMaxStages];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fail;
+  __shared__ int skip;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const typename P::Tile t = P::tile(args);
+  const int BN = args.c.BN, nst = args.c.stages;
+  const uint32_t bslot = (uint32_t)BN * 64u;
+  const uint32_t stage_bytes = S * (P::kUA * kASlot + P::kUB * bslot);
+  int* err = args.c.err;
+  // another CTA already failed: do nothing (decided once for the whole CTA, before
+  // any barrier or TMEM is set up)
+  if (threadIdx.x == 0) skip = *(const volatile int*)err;
+  __syncthreads();
+  if (skip) return;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nst; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(&done, 1);
+    fail = 0;
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, args.c.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const int nkb = t.kb1 - t.kb0;
+
+  if (threadIdx.x == 0) {
+    // TMA producer
+    int issued = 0;
+    for (int i = 0; i < nkb; ++i) {
+      const int st = i % nst;
+      if (i >= nst && !tc::mbar_wait(&empty[st], ((i / nst) - 1) & 1, err)) {
+        fail = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      tc::mbar_arrive_expect_tx(&full[st], args.c.tx_bytes);
+      uint8_t* sa = smem + st * stage_bytes;
+      uint8_t* sb = sa + S * P::kUA * kASlot;
+      const int kb = t.kb0 + i;
+#pragma unroll
+      for (int u = 0; u < P::kUA; ++u)
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+          P::load_a(&tmA, sa + (u * S + s) * kASlot, args, t, u, s, kb, &full[st]);
+#pragma unroll
+      for (int u = 0; u < P::kUB; ++u)
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+          P::load_b(&tmB, sb + (u * S + s) * bslot, args, t, u, s, kb, &full[st]);
+      ++issued;
+    }
+    // no TMA write may still be in flight when the CTA moves on
+    for (int i = issued > nst ? issued - nst : 0; i < issued; ++i)
+      tc::mbar_wait(&full[i % nst], (i / nst) & 1, err);
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    for (int i = 0; i < nkb; ++i) {
+      const int st = i % nst;
+      if (!tc::mbar_wait(&full[st], (i / nst) & 1, err)) {
+        fail = 1;
+        atomicExch(err, 1);
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
+      const uint32_t sb = sa + S * P::kUA * kASlot;
+      P::template issue<S>(args, tmem, sa, sb, bslot, i == 0);
+      tc::mma_commit(&empty[st]);
+    }
+    tc::mma_commit(&done);
+  }
+  bool ok = tc::mbar_wait(&done, 0, err);
+  // the MMAs already issued must finish before TMEM is read or freed: wait again,
+  // bounded by time only
+  if (!ok) {
+    static const int zero = 0;
+    ok = tc::mbar_wait(&done, 0, &zero);
+  }
+  if (!ok) fail = 1;
+  tc::fence_after_sync();
+  __syncthreads();
+  const bool bad = fail != 0;
+  __syncwarp();
+  if (bad) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+  } else {
+    P::template epilogue<S>(args, t, tmem, smem, warp, lane);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, args.c.tmem_cols);
+}
+
+// ---------------------------------------------------------------------------- host
+inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return static_cast<PFN_cuTensorMapEncodeTiled_v12000>(nullptr);
+  }();
+  return fn;
+}
+
+// BF16 tensor map with the 64-byte swizzle over a dense array; dims[0] is the
+// contiguous K axis (its byte size must be a multiple of 16).
+inline bool make_tmap(CUtensorMap* tm, const void* base, int rank, const uint64_t* dims,
+                      const uint32_t* box) {
+  auto fn = encode_fn();
+  if (!fn || rank < 1 || rank > 5) return false;
+  cuuint64_t gdim[5], gstride[4];
+  cuuint32_t bdim[5], estr[5];
+  uint64_t stride = 2;
+  for (int i = 0; i < rank; ++i) {
+    gdim[i] = dims[i];
+    bdim[i] = box[i];
+    estr[i] = 1;
+    if (i > 0) gstride[i - 1] = stride;
+    stride *= dims[i];
+  }
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), gdim, gstride,
+            bdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline uint32_t tmem_cols_for(int cols) {
+  uint32_t c = 32;
+  while (c < (uint32_t)cols) c <<= 1;
+  return c;
+}
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Ring depth and dynamic shared memory for a policy shape; stages = 0 if even one
+// stage does not fit.
+inline void plan_smem(int S, int kUA, int kUB, int BN, size_t epilogue_bytes, int* stages,
+                      size_t* smem) {
+  const size_t stage = (size_t)S * (kUA * (size_t)kASlot + kUB * (size_t)BN * 64);
+  int n = (int)((kSmemLimit - 2048) / stage);
+  if (n > 3) n = 3;
+  *stages = n < 1 ? 0 : n;
+  const size_t pipe = stage * (size_t)(*stages);
+  *smem = (pipe > epilogue_bytes ? pipe : epilogue_bytes) + 1024;
+}
+
+template <int S, class P>
+cudaError_t launch_tc(dim3 grid, size_t smem, cudaStream_t stream, const CUtensorMap& a,
+                      const CUtensorMap& b, const typename P::Args& args) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_split<S, P>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tc_split<S, P><<<grid, kThreads, smem, stream>>>(a, b, args);
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_tc_s(int S, dim3 grid, size_t smem, cudaStream_t stream, const CUtensorMap& a,
+                        const CUtensorMap& b, const typename P::Args& args) {
+  if (args.c.stages < 1 || args.c.stages > kMaxStages || smem > kSmemLimit)
+    return cudaErrorInvalidValue;
+  switch (S) {
+    case 1: return launch_tc<1, P>(grid, smem, stream, a, b, args);
+    case 2: return launch_tc<2, P>(grid, smem, stream, a, b, args);
+    case 3: return launch_tc<3, P>(grid, smem, stream, a, b, args);
+    case 4: return launch_tc<4, P>(grid, smem, stream, a, b, args);
+  }
+  return cudaErrorInvalidValue;
+}
+
+inline int grid1d(long n) {
+  long g = (n + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 148 * 32 ? 148 * 32 : g));
+}
+
+}  // namespace tce

@@ -76,8 +76,24 @@ def test_mixed_energy_within_1e6_of_fp64_oracle(cfg):
         assert np.max(np.abs(e[:, 3] - er[:, 3])) <= E_TOL
         assert np.max(np.abs(e[:, 2] - er[:, 2])) <= E_TOL   # exchange
         assert np.max(np.abs(e[:, 1] - er[:, 1])) <= E_TOL   # Coulomb
-    # the propagated walkers stay close: only the force bias is split-precision here
-    assert walker_rel(ctx.get_walkers(), orc.phi).max() < 1e-7
+    # propagated in split precision (VHS, Taylor terms and one-body halves on the tensor
+    # cores, identity parts in FP64): walkers stay within 1e-6 relative after 2 steps
+    dphi = walker_rel(ctx.get_walkers(), orc.phi).max()
+    print(f"{cfg}: 2-step max rel dPhi {dphi:.2e}, max |dE_L| {np.max(np.abs(e1[:, 3] - e1r[:, 3])):.2e}")
+    assert dphi < 1e-6
+
+
+def test_mixed_trajectory_error_over_20_steps():
+    """Error growth of the split-precision trajectory (stated, loosely bounded)."""
+    s = make_system(37, 5, 3, 71, seed=4, decay="geometric", e0=0.37)
+    W = 13
+    phi = perturbed_walkers(s, W, eps=0.3, seed=2)
+    ctx, orc, _, _, e1, e1r = mixed_vs_oracle(s, W, phi, 20)
+    de = np.max(np.abs(e1[:, 3] - e1r[:, 3]))
+    dphi = walker_rel(ctx.get_walkers(), orc.phi).max()
+    dw = np.max(np.abs(ctx.get_weights().real - orc.w) / np.abs(orc.w))
+    print(f"20 steps: max |dE_L| {de:.2e} Ha, max rel dPhi {dphi:.2e}, max rel dw {dw:.2e}")
+    assert de < 1e-5 and dphi < 1e-5 and dw < 1e-5
 
 
 def test_mixed_c3_shape_sampled_walkers():
