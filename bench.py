@@ -37,6 +37,15 @@ WORKLOAD_TEXT = ("ph-AFQMC step + E_loc, 100 orbitals, 10a+10b electrons, 400 Ch
                  "vectors (geometric norm decay), 128 complex128 walkers, dt 0.005, QR every "
                  "5 steps, Philox fields")
 FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 nominal: 148 SMs x 2032 MHz x ~4.15 flop/clk/SM
+SPLIT_PRODUCTS = 6          # bf16 slice products of the 3-slice exchange (s + t <= 2)
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def parse_args():
@@ -48,6 +57,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the split-precision legs")
+    ap.add_argument("--mixed-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -158,6 +169,89 @@ def cpu_baseline(seconds: float, W_sample: int = 8) -> dict:
     return {"value": W_sample * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{W_sample} of the {c['W']} walkers of the {WORKLOAD} workload, "
                       f"{steps} steps (step + QR cadence + E_loc), {dt:.1f} s of host time"}
+
+
+def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int = 16,
+              long_steps: int = 100) -> dict:
+    """Split-precision (tcgen05) throughput on one workload, and its |dE_L| against
+    the FP64 path on the first walkers after 1 and after long_steps steps.  Walkers
+    are independent and the Philox counters are keyed by walker index, so an FP64
+    context holding only the first walkers sees exactly the same fields."""
+    import torch
+    from paper_2209_04015_b300 import AfqContext
+    from paper_2209_04015_b300.synthetic import make_config
+
+    s, c = make_config(name, seed=1 + rank)
+    W, X, M, na, nb = c["W"], s.X, s.M, s.na, s.nb
+    stream = torch.cuda.current_stream()
+
+    def context(precision, nw):
+        ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, precision=precision,
+                         stream=stream.cuda_stream)
+        ctx.init_hamiltonian(s.h1, s.L, s.e0)
+        ctx.init_trial(s.psi_a, s.psi_b)
+        ctx.init_walkers(nw)
+        return ctx
+
+    mix = context("split_bf16", W)
+    ref = context("fp64", check_walkers)
+    errs = {}
+    for k in range(1, long_steps + 1):
+        mix.propagate(None, 1)
+        ref.propagate(None, 1)
+        if k in (1, long_steps):
+            em, _ = mix.local_energy()
+            er, _ = ref.local_energy()
+            errs[k] = float(np.max(np.abs(em[:check_walkers, 3] - er[:, 3])))
+    ref.close()
+    e_dev = torch.empty((W, 4, 2), dtype=torch.float64, device="cuda")
+    emix_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def step():
+        mix.propagate_dev(None, 1)
+        mix.local_energy_dev(e_dev.data_ptr(), emix_dev.data_ptr())
+
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mix.profile_enable(True)
+    n0 = mix.launch_count()
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = mix.profile_read()
+    mix.profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / steps
+    ex_ms, ex_n = prof["exchange"]
+    ex_avg = ex_ms / max(ex_n, 1) / 1e3
+    useful = exchange_flops(W, X, M, na, nb)
+    bf16_flops = SPLIT_PRODUCTS * useful
+    peak = measured_peaks().get("bf16_tflops", 1800.0)
+    achieved = bf16_flops / ex_avg / 1e12
+    out = {"workload": name, "M": M, "na": na, "nb": nb, "X": X, "W": W,
+           "value": W / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "precision": "split_bf16: force bias and exchange 3 bf16 slices (6 products, FP32 "
+                        "accumulation); VHS and propagator 4 exact 8-bit digits; overlaps, "
+                        "inverses, QR and weights FP64",
+           "dE_L_max_1_step": errs[1], f"dE_L_max_{long_steps}_steps": errs[long_steps],
+           "dE_reference": f"FP64 path (parity-checked against the FP64 oracle at 1e-10) on the "
+                           f"first {check_walkers} walkers, same Philox fields",
+           "gpu_launches": mix.launch_count() - n0,
+           "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]}
+                       for k, v in prof.items() if v[1]},
+           "roofline": {"bound": "tensor", "kernel": "exchange (k_tc_split<ExP>)",
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
+                        "flops_per_launch": bf16_flops,
+                        "flops_note": f"{SPLIT_PRODUCTS} bf16 slice products x the exchange's "
+                                      "algorithmic flops (no padding counted)",
+                        "avg_launch_ms": ex_avg * 1e3}}
+    mix.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- arms
@@ -313,6 +407,12 @@ def run_afq(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if not args.no_mixed:
+        line["mixed"] = {"same_workload": mixed_leg(WORKLOAD, args.mixed_steps * 5, args.warmup,
+                                                    rank),
+                         "large_shape": mixed_leg("c3", args.mixed_steps, args.warmup, rank)}
+        line["mixed"]["same_workload"]["speedup_vs_fp64"] = (
+            line["mixed"]["same_workload"]["value"] / (value / world))
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
