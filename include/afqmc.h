@@ -176,6 +176,50 @@ int afq_profile_read(afq_ctx* ctx, int kernel, double* total_ms, uint64_t* launc
 /* Name of a kernel class, or NULL when kernel is out of range. */
 const char* afq_kernel_name(int kernel);
 
+/* ---- CUDA graphs, batches of systems, autotuning (no counterpart in the paper:
+   these serve the data-parallel step at scale) ---- */
+
+/* Capture nsteps steps (fields drawn by the device Philox stream, whose step
+   counter lives in device memory) each followed by the local energy, as one CUDA
+   graph on the context's stream.  With qr_period > 0, nsteps must be a multiple of
+   qr_period and the context's step counter must sit on a QR boundary, so that every
+   replay performs the same QR cadence.  No host work runs during a replay. */
+int afq_graph_capture(afq_ctx* ctx, int nsteps);
+/* Launch the captured graph nreplays times (asynchronous, on the context's stream);
+   the step counter advances by nreplays * nsteps. */
+int afq_graph_launch(afq_ctx* ctx, int nreplays);
+/* Energies of the last local-energy evaluation (from a graph or afq_local_energy_dev):
+   e_out W x 4 complex and/or e_mix, host outputs; synchronises the stream. */
+int afq_get_energy(afq_ctx* ctx, double* e_out, double* e_mix);
+
+/* A batch of independent systems (contexts with walkers, possibly of uneven M, N,
+   X and W) stepped by one CUDA graph in which every system is its own concurrent
+   branch.  The batch owns its streams; the contexts stay owned by the caller and
+   must outlive the batch. */
+typedef struct afq_batch afq_batch;
+int afq_batch_create(afq_batch** batch, int n, afq_ctx* const* ctxs);
+int afq_batch_destroy(afq_batch* batch);
+const char* afq_batch_last_error(const afq_batch* batch);
+/* Capture nsteps steps + local energies of every system (same rules as
+   afq_graph_capture, for each context). */
+int afq_batch_capture(afq_batch* batch, int nsteps);
+/* Replay nreplays times after the work already queued on the contexts' streams;
+   later work on those streams waits for the replays. */
+int afq_batch_launch(afq_batch* batch, int nreplays);
+/* Wait for the replays and report the contexts' device flags. */
+int afq_batch_synchronize(afq_batch* batch);
+
+/* Autotuner: times candidate tiles of the kernels on the context's current walkers
+   with CUDA events and keeps the fastest.  FP64: the g-group of the exchange kernel
+   and the walker-column chunk of the propagator (timed on a copy, walkers
+   restored).  AFQ_SPLIT_BF16: walkers per exchange tile for each spin and the
+   split-K depth of the force bias.  Results do not change values beyond rounding
+   order; they are read back with afq_get_tiles. */
+int afq_autotune(afq_ctx* ctx);
+/* tiles[0..n): FP64 exchange g-group (0 = default), FP64 propagator columns,
+   split exchange walkers per tile (alpha, beta), force-bias split-K depth. */
+int afq_get_tiles(afq_ctx* ctx, int* tiles, int n);
+
 /* Exchange energy without any device allocation.  The paper has no counterpart:
    this exists for callers that cannot call cudaMalloc, such as a host framework
    that owns all device memory through its own pool or fixed arena, or a

@@ -67,6 +67,17 @@ _SIGS = {
     "afq_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "afq_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_uint64)]),
     "afq_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "afq_graph_capture": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afq_graph_launch": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afq_get_energy": (ctypes.c_int, [_P, _P, _D]),
+    "afq_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]),
+    "afq_batch_destroy": (ctypes.c_int, [_P]),
+    "afq_batch_last_error": (ctypes.c_char_p, [_P]),
+    "afq_batch_capture": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afq_batch_launch": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afq_batch_synchronize": (ctypes.c_int, [_P]),
+    "afq_autotune": (ctypes.c_int, [_P]),
+    "afq_get_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "afq_gemm_split_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             _P, _P, _P, _P]),
     "afq_exchange_energy_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -274,7 +285,70 @@ class AfqContext:
             k += 1
         return out
 
+    def graph_capture(self, nsteps: int) -> None:
+        """Capture nsteps Philox steps + local energies as one CUDA graph."""
+        self._check(self.lib.afq_graph_capture(self.h, nsteps))
+
+    def graph_launch(self, nreplays: int = 1) -> None:
+        self._check(self.lib.afq_graph_launch(self.h, nreplays))
+
+    def get_energy(self) -> tuple[np.ndarray, float]:
+        """Energies of the last evaluation (e.g. the last graph replay)."""
+        e = np.empty((self.W, 4), dtype=np.complex128)
+        emix = ctypes.c_double()
+        self._check(self.lib.afq_get_energy(self.h, _ptr(e), ctypes.byref(emix)))
+        return e, emix.value
+
+    def autotune(self) -> None:
+        self._check(self.lib.afq_autotune(self.h))
+
+    def get_tiles(self) -> list[int]:
+        """FP64 exchange g-group, FP64 propagator columns, split exchange walkers per
+        tile (alpha, beta), force-bias split-K depth."""
+        t = (ctypes.c_int * 5)()
+        self._check(self.lib.afq_get_tiles(self.h, t, 5))
+        return list(t)
+
     def launch_count(self) -> int:
         c = ctypes.c_uint64()
         self._check(self.lib.afq_launch_count(self.h, ctypes.byref(c)))
         return c.value
+
+
+class AfqBatch:
+    """Several contexts stepped by one CUDA graph, one concurrent branch per system
+    (wraps afq_batch*).  The contexts must outlive the batch."""
+
+    def __init__(self, contexts: list[AfqContext]):
+        self.lib = load_library()
+        self.contexts = list(contexts)
+        arr = (_P * len(self.contexts))(*[c.h for c in self.contexts])
+        h = _P()
+        rc = self.lib.afq_batch_create(ctypes.byref(h), len(self.contexts), arr)
+        if rc != AFQ_OK:
+            raise AfqError(rc, "afq_batch_create failed")
+        self.h = h
+
+    def _check(self, rc: int) -> None:
+        if rc != AFQ_OK:
+            raise AfqError(rc, self.lib.afq_batch_last_error(self.h).decode())
+
+    def capture(self, nsteps: int) -> None:
+        self._check(self.lib.afq_batch_capture(self.h, nsteps))
+
+    def launch(self, nreplays: int = 1) -> None:
+        self._check(self.lib.afq_batch_launch(self.h, nreplays))
+
+    def synchronize(self) -> None:
+        self._check(self.lib.afq_batch_synchronize(self.h))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.afq_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -15,6 +15,8 @@ int afq_fail(afq_ctx* ctx, int code, const std::string& msg) {
 
 namespace {
 
+void drop_graph(afq_ctx* ctx);
+
 template <class T>
 int dalloc(afq_ctx* ctx, T** p, size_t n) {
   if (*p) {
@@ -86,9 +88,11 @@ int check_flags(afq_ctx* ctx) {
   AFQ_CUDA(ctx, cudaMemcpyAsync(h, ctx->flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   AFQ_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(h), ctx->stream));
   AFQ_TRY(sync(ctx));
-  if (h[0]) return afq_fail(ctx, AFQ_ERR_SINGULAR, std::to_string(h[0]) + " singular pivot(s)");
-  if (h[1]) return afq_fail(ctx, AFQ_ERR_NAN, std::to_string(h[1]) + " non-finite weight(s)");
-  if (h[2]) return afq_fail(ctx, AFQ_ERR_CUDA, "tensor-core pipeline wait timed out");
+  const std::string all = " (singular pivots " + std::to_string(h[0]) + ", non-finite values " +
+                          std::to_string(h[1]) + ", tensor-core time-outs " + std::to_string(h[2]) + ")";
+  if (h[2]) return afq_fail(ctx, AFQ_ERR_CUDA, "tensor-core pipeline wait timed out" + all);
+  if (h[0]) return afq_fail(ctx, AFQ_ERR_SINGULAR, "singular pivot(s)" + all);
+  if (h[1]) return afq_fail(ctx, AFQ_ERR_NAN, "non-finite weight(s)" + all);
   return AFQ_OK;
 }
 
@@ -106,7 +110,7 @@ cudaEvent_t take_event(afq_ctx* ctx) {
 // Runs one launch wrapper, bracketed by an event pair when profiling is on.
 template <class F>
 int timed(afq_ctx* ctx, int kid, F&& launch) {
-  if (!ctx->profiling) return launch();
+  if (!ctx->profiling || ctx->capturing) return launch();
   afq_ctx::ProfRec r{kid, take_event(ctx), take_event(ctx)};
   AFQ_CUDA(ctx, cudaEventRecord(r.a, ctx->stream));
   int rc = launch();
@@ -198,8 +202,7 @@ bool symmetric(const double* a, int M, double* dev_out) {
 // One hybrid-propagation step (Sec. "Review of AFQMC") on the context's stream.
 int one_step(afq_ctx* ctx, const double* xi_dev) {
   const double log_const = -ctx->p.dt * (ctx->e0 - 0.5 * ctx->sum_vbar2 - ctx->e_shift);
-  const uint64_t step = ctx->step;
-  AFQ_TRY(timed(ctx, AFQ_K_FIELDS, [&] { return launch_fields(ctx, xi_dev, step); }));
+  AFQ_TRY(timed(ctx, AFQ_K_FIELDS, [&] { return launch_fields(ctx, xi_dev); }));
   if (ctx->mixed) {
     AFQ_TRY(timed(ctx, AFQ_K_VHS, [&] { return launch_vhs_tc(ctx); }));
     AFQ_TRY(timed(ctx, AFQ_K_PROPAGATE, [&] { return launch_propagate_tc(ctx); }));
@@ -265,6 +268,8 @@ int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
   }
   if (cudaMalloc((void**)&ctx->flags, 3 * sizeof(int)) != cudaSuccess ||
       cudaMemset(ctx->flags, 0, 3 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&ctx->d_step, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(ctx->d_step, 0, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc((void**)&ctx->emix, sizeof(double)) != cudaSuccess) {
     cudaFree(ctx->flags);
     delete ctx;
@@ -282,7 +287,9 @@ int afq_destroy(afq_ctx* ctx) {
   dfree(&ctx->L);
   dfree(&ctx->Lpk);
   dfree(&ctx->tpq);
+  drop_graph(ctx);
   dfree(&ctx->flags);
+  dfree(&ctx->d_step);
   dfree(&ctx->emix);
   dfree(&ctx->scratch);
   for (auto& r : ctx->prof) {
@@ -343,7 +350,9 @@ int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a, const doub
   ctx->na = na;
   ctx->nb = nb;
   ctx->N = N;
-  ctx->ex_groups = (X + exchange_group_size(na > nb ? na : nb) - 1) / exchange_group_size(na > nb ? na : nb);
+  ctx->ex_groups = X;  // one slot per g: room for any g-group size
+  ctx->ex_G_fp64 = 0;
+  ctx->prop_nc = 4;
   const size_t MM = (size_t)M * M;
   std::vector<double> psiT((size_t)N * M);
   for (int p = 0; p < M; ++p) {
@@ -499,6 +508,7 @@ int afq_init_walkers(afq_ctx* ctx, int W, const double* phi, const double* w) {
   }
   AFQ_TRY(green_and_bias(ctx, ctx->ws));
   AFQ_TRY(launch_init_overlap(ctx, ctx->ws));
+  AFQ_CUDA(ctx, cudaMemsetAsync(ctx->d_step, 0, sizeof(unsigned long long), ctx->stream));
   AFQ_TRY(sync(ctx));
   ctx->step = 0;
   ctx->have_walkers = true;
@@ -614,6 +624,8 @@ int afq_set_state(afq_ctx* ctx, const double* phi, const double* w, const double
     AFQ_TRY(launch_init_overlap(ctx, ctx->ws));
   }
   ctx->step = step;
+  const unsigned long long st = step;
+  AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->d_step, &st, sizeof(st), cudaMemcpyHostToDevice, ctx->stream));
   AFQ_TRY(sync(ctx));
   return check_flags(ctx);
 }
@@ -674,6 +686,332 @@ const char* afq_kernel_name(int kernel) {
   static const char* names[AFQ_K_COUNT] = {"fields", "vhs", "propagate", "overlap_theta",
                                            "force_bias", "weights", "qr", "exchange", "energy"};
   return kernel >= 0 && kernel < AFQ_K_COUNT ? names[kernel] : nullptr;
+}
+
+
+// ===========================================================================
+// CUDA graphs, batches of systems and the autotuner
+// ===========================================================================
+}  // extern "C"
+
+struct afq_batch {
+  std::vector<afq_ctx*> ctx;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaStream_t origin = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int nsteps = 0;
+  std::string err;
+};
+
+namespace {
+
+// Records nsteps steps (device Philox fields) and the local energy after each one
+// on ctx->stream, which is being captured; the host step mirror is restored.
+int record_steps(afq_ctx* ctx, int nsteps) {
+  const uint64_t step0 = ctx->step;
+  ctx->capturing = true;
+  int rc = AFQ_OK;
+  for (int k = 0; k < nsteps && rc == AFQ_OK; ++k) {
+    rc = one_step(ctx, nullptr);
+    if (rc == AFQ_OK) rc = energy_impl(ctx);
+  }
+  ctx->capturing = false;
+  ctx->step = step0;
+  return rc;
+}
+
+int check_capturable(afq_ctx* ctx, int nsteps) {
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  if (nsteps < 1) return afq_fail(ctx, AFQ_ERR_ARG, "nsteps < 1");
+  const int q = ctx->p.qr_period;
+  if (q > 0 && (nsteps % q != 0 || ctx->step % (uint64_t)q != 0))
+    return afq_fail(ctx, AFQ_ERR_ARG,
+                    "a captured block must hold whole QR periods and start on one");
+  return AFQ_OK;
+}
+
+void drop_graph(afq_ctx* ctx) {
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->graph_exec = nullptr;
+  ctx->graph = nullptr;
+  ctx->graph_steps = 0;
+}
+
+// Times one launch sequence (after one warm-up run) with events on the stream.
+template <class F>
+float time_launch(afq_ctx* ctx, F&& f, int reps = 3) {
+  if (f() != AFQ_OK) return 1e30f;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, ctx->stream);
+  int rc = AFQ_OK;
+  for (int r = 0; r < reps && rc == AFQ_OK; ++r) rc = f();
+  cudaEventRecord(b, ctx->stream);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc == AFQ_OK ? ms / reps : 1e30f;
+}
+
+}  // namespace
+
+extern "C" {
+
+int afq_graph_capture(afq_ctx* ctx, int nsteps) {
+  if (!ctx) return AFQ_ERR_ARG;
+  AFQ_TRY(check_capturable(ctx, nsteps));
+  drop_graph(ctx);
+  AFQ_TRY(sync(ctx));
+  // the legacy default stream cannot be captured: record on a private stream
+  cudaStream_t s = ctx->stream, rec = nullptr;
+  if (!s) {
+    AFQ_CUDA(ctx, cudaStreamCreateWithFlags(&rec, cudaStreamNonBlocking));
+    ctx->stream = rec;
+  }
+  cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+  int rc = e == cudaSuccess ? record_steps(ctx, nsteps) : afq_fail(ctx, AFQ_ERR_CUDA, "begin capture");
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(ctx->stream, &g);
+  ctx->stream = s;
+  if (rec) cudaStreamDestroy(rec);
+  if (rc != AFQ_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return afq_fail(ctx, AFQ_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+  ctx->graph = g;
+  AFQ_CUDA(ctx, cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+  ctx->graph_steps = nsteps;
+  return AFQ_OK;
+}
+
+int afq_graph_launch(afq_ctx* ctx, int nreplays) {
+  if (!ctx || nreplays < 0) return AFQ_ERR_ARG;
+  if (!ctx->graph_exec) return afq_fail(ctx, AFQ_ERR_STATE, "afq_graph_capture first");
+  for (int r = 0; r < nreplays; ++r) {
+    AFQ_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    ctx->launches++;
+  }
+  ctx->step += (uint64_t)ctx->graph_steps * nreplays;
+  return AFQ_OK;
+}
+
+int afq_get_energy(afq_ctx* ctx, double* e_out, double* e_mix) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  if (e_out)
+    AFQ_CUDA(ctx, cudaMemcpyAsync(e_out, ctx->ws.energy, (size_t)ctx->ws.W * 4 * 16,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  if (e_mix)
+    AFQ_CUDA(ctx, cudaMemcpyAsync(e_mix, ctx->emix, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  AFQ_TRY(sync(ctx));
+  return check_flags(ctx);
+}
+
+int afq_batch_create(afq_batch** out, int n, afq_ctx* const* ctxs) {
+  if (!out || n < 1 || !ctxs) return AFQ_ERR_ARG;
+  *out = nullptr;
+  afq_batch* b = new (std::nothrow) afq_batch();
+  if (!b) return AFQ_ERR_NOMEM;
+  bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < n && ok; ++i) {
+    if (!ctxs[i] || !ctxs[i]->have_walkers) ok = false;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    b->ctx.push_back(ctxs[i]);
+    b->streams.push_back(st);
+    b->events.push_back(ev);
+  }
+  if (!ok) {
+    afq_batch_destroy(b);
+    return AFQ_ERR_ARG;
+  }
+  *out = b;
+  return AFQ_OK;
+}
+
+int afq_batch_destroy(afq_batch* b) {
+  if (!b) return AFQ_ERR_ARG;
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto s : b->streams)
+    if (s) cudaStreamDestroy(s);
+  for (auto e : b->events)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+  return AFQ_OK;
+}
+
+const char* afq_batch_last_error(const afq_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int afq_batch_capture(afq_batch* b, int nsteps) {
+  if (!b) return AFQ_ERR_ARG;
+  for (auto* c : b->ctx) {
+    int rc = check_capturable(c, nsteps);
+    if (rc == AFQ_OK) rc = sync(c);
+    if (rc != AFQ_OK) {
+      b->err = c->err;
+      return rc;
+    }
+  }
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    b->err = "begin capture";
+    return AFQ_ERR_CUDA;
+  }
+  int rc = cudaEventRecord(b->fork, b->origin) == cudaSuccess ? AFQ_OK : AFQ_ERR_CUDA;
+  // one branch per system: its steps run concurrently with the other systems'
+  for (size_t i = 0; i < b->ctx.size() && rc == AFQ_OK; ++i) {
+    afq_ctx* c = b->ctx[i];
+    cudaStream_t own = c->stream;
+    c->stream = b->streams[i];
+    rc = cudaStreamWaitEvent(c->stream, b->fork, 0) == cudaSuccess ? AFQ_OK : AFQ_ERR_CUDA;
+    if (rc == AFQ_OK) rc = record_steps(c, nsteps);
+    if (rc == AFQ_OK && (cudaEventRecord(b->events[i], c->stream) != cudaSuccess ||
+                         cudaStreamWaitEvent(b->origin, b->events[i], 0) != cudaSuccess))
+      rc = AFQ_ERR_CUDA;
+    if (rc != AFQ_OK) b->err = c->err.empty() ? "capture failed" : c->err;
+    c->stream = own;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->origin, &g);
+  if (rc != AFQ_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (b->err.empty()) b->err = std::string("end capture: ") + cudaGetErrorString(e);
+    return rc != AFQ_OK ? rc : AFQ_ERR_CUDA;
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    b->err = "graph instantiate";
+    return AFQ_ERR_CUDA;
+  }
+  b->nsteps = nsteps;
+  return AFQ_OK;
+}
+
+int afq_batch_launch(afq_batch* b, int nreplays) {
+  if (!b || nreplays < 0) return AFQ_ERR_ARG;
+  if (!b->exec) {
+    b->err = "afq_batch_capture first";
+    return AFQ_ERR_STATE;
+  }
+  // work already queued on the systems' own streams comes first ...
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    if (cudaEventRecord(b->events[i], b->ctx[i]->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(b->origin, b->events[i], 0) != cudaSuccess)
+      return AFQ_ERR_CUDA;
+  for (int r = 0; r < nreplays; ++r)
+    if (cudaGraphLaunch(b->exec, b->origin) != cudaSuccess) {
+      b->err = "graph launch";
+      return AFQ_ERR_CUDA;
+    }
+  // ... and later work on them waits for the replays
+  if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) return AFQ_ERR_CUDA;
+  for (auto* c : b->ctx) {
+    if (cudaStreamWaitEvent(c->stream, b->fork, 0) != cudaSuccess) return AFQ_ERR_CUDA;
+    c->step += (uint64_t)b->nsteps * nreplays;
+    c->launches += (uint64_t)nreplays;
+  }
+  return AFQ_OK;
+}
+
+int afq_batch_synchronize(afq_batch* b) {
+  if (!b) return AFQ_ERR_ARG;
+  if (cudaStreamSynchronize(b->origin) != cudaSuccess) return AFQ_ERR_CUDA;
+  for (auto* c : b->ctx) {
+    const int rc = check_flags(c);
+    if (rc != AFQ_OK) {
+      b->err = c->err;
+      return rc;
+    }
+  }
+  return AFQ_OK;
+}
+
+int afq_autotune(afq_ctx* ctx) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  if (ctx->capturing) return afq_fail(ctx, AFQ_ERR_STATE, "cannot tune while capturing");
+  const bool prof = ctx->profiling;
+  ctx->profiling = false;
+  WalkerSet& s = ctx->ws;
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  int rc = AFQ_OK;
+  if (!ctx->mixed) {
+    // FP64 exchange: g-group size (pure: it only rewrites its partial sums)
+    float best = 1e30f;
+    int bestG = exchange_group_size(nmax);
+    for (int G = 1; G <= exchange_group_max(nmax); G = G < 4 ? G + 1 : G * 3 / 2) {
+      ctx->ex_G_fp64 = G;
+      const float ms = time_launch(ctx, [&] { return launch_exchange_fp64(ctx, s); });
+      if (ms < best) {
+        best = ms;
+        bestG = G;
+      }
+    }
+    ctx->ex_G_fp64 = bestG;
+    // FP64 propagator column chunk: timed on a copy, the walkers are restored
+    double2* backup = nullptr;
+    const size_t bytes = (size_t)s.W * ctx->M * ctx->N * sizeof(double2);
+    if (cudaMalloc((void**)&backup, bytes) != cudaSuccess) rc = AFQ_ERR_NOMEM;
+    if (rc == AFQ_OK && cudaMemcpyAsync(backup, s.phi, bytes, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) rc = AFQ_ERR_CUDA;
+    if (rc == AFQ_OK) rc = launch_fields(ctx, nullptr);
+    if (rc == AFQ_OK) rc = launch_vhs_fp64(ctx);
+    best = 1e30f;
+    int bestNC = 4;
+    for (int nc : {2, 4, 8}) {
+      if (rc != AFQ_OK) break;
+      ctx->prop_nc = nc;
+      const float ms = time_launch(ctx, [&] {
+        if (cudaMemcpyAsync(s.phi, backup, bytes, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+          return (int)AFQ_ERR_CUDA;
+        return launch_propagate_fp64(ctx);
+      });
+      if (ms < best) {
+        best = ms;
+        bestNC = nc;
+      }
+    }
+    ctx->prop_nc = bestNC;
+    if (backup) {
+      cudaMemcpyAsync(s.phi, backup, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(backup);
+    }
+  } else {
+    rc = mixed_autotune(ctx);
+  }
+  // slots written under another tiling must not leak into the energy
+  if (rc == AFQ_OK)
+    rc = cudaMemsetAsync(s.ekp, 0, (size_t)s.W * 2 * ctx->ex_groups * sizeof(double2),
+                         ctx->stream) == cudaSuccess ? AFQ_OK : AFQ_ERR_CUDA;
+  if (rc == AFQ_OK) rc = green_and_bias(ctx, s);  // theta and c are recomputed unchanged
+  if (rc == AFQ_OK) rc = sync(ctx);
+  ctx->profiling = prof;
+  return rc == AFQ_OK ? check_flags(ctx) : rc;
+}
+
+int afq_get_tiles(afq_ctx* ctx, int* tiles, int n) {
+  if (!ctx || !tiles || n < 1) return AFQ_ERR_ARG;
+  const int v[5] = {ctx->ex_G_fp64, ctx->prop_nc, ctx->ex_zb[0], ctx->ex_zb[1], ctx->fb_ksplit};
+  for (int i = 0; i < n && i < 5; ++i) tiles[i] = v[i];
+  return AFQ_OK;
 }
 
 int afq_launch_count(afq_ctx* ctx, uint64_t* count) {

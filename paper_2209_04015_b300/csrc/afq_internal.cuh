@@ -68,8 +68,15 @@ struct afq_ctx {
   int M = 0, X = 0, na = 0, nb = 0, N = 0, Mp = 0;
   double e0 = 0.0, e_trial = 0.0, e_shift = 0.0, sum_vbar2 = 0.0;
   bool have_ham = false, have_trial = false, have_walkers = false;
-  uint64_t step = 0;
-  int ex_groups = 0;  // number of g-groups of the exchange kernel
+  uint64_t step = 0;                   // host mirror of the step counter
+  unsigned long long* d_step = nullptr; // device step counter (Philox fields, graphs)
+  int ex_groups = 0;  // exchange partial-sum slots per (walker, spin)
+  int ex_G_fp64 = 0;  // g-group of the FP64 exchange (0: default), autotuned
+  int prop_nc = 4;    // walker columns per CTA of the FP64 propagator, autotuned
+  bool capturing = false;  // a CUDA graph is being captured: no host syncs, no events
+  cudaGraph_t graph = nullptr;          // afq_graph_capture: a block of steps
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_steps = 0;
 
   // Hamiltonian
   double* h1 = nullptr;   // M x M
@@ -106,7 +113,7 @@ struct afq_ctx {
   __nv_bfloat16* Lt_sl = nullptr;     // S x X x N x Mpad slices of L~
   __nv_bfloat16* th_sl = nullptr;     // S x W x 2 x N x Mpad slices of theta (re, im planes)
   float* fb_part = nullptr;           // ksplit x 2W x X force-bias partial sums
-  int fb_BN = 0, fb_kbper = 0, fb_ksplit = 0;
+  int fb_BN = 0, fb_kbper = 0, fb_ksplit = 0, fb_ksplit_cap = 0;
   int ex_G[2] = {0, 0}, ex_zb[2] = {0, 0}, ex_BN[2] = {0, 0};
   CUtensorMap tm_fb_a, tm_fb_b, tm_ex_a[2], tm_ex_b[2];
   // split-precision propagation operands (k_mixed_prop.cu)
@@ -170,10 +177,11 @@ int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s);
 int launch_energy_assemble(afq_ctx* ctx, WalkerSet& s);
 int launch_qr(afq_ctx* ctx, WalkerSet& s, double2* Qw);  // Qw: W x N x M workspace
 int exchange_group_size(int nmax);
+int exchange_group_max(int nmax);
 int launch_init_overlap(afq_ctx* ctx, WalkerSet& s);
 
 // step kernels (k_step.cu)
-int launch_fields(afq_ctx* ctx, const double* xi_dev, uint64_t step);
+int launch_fields(afq_ctx* ctx, const double* xi_dev);
 int launch_philox_fields(afq_ctx* ctx, uint64_t step, double* out, uint32_t* words);
 int launch_vhs_fp64(afq_ctx* ctx);
 int launch_propagate_fp64(afq_ctx* ctx);
@@ -187,6 +195,7 @@ void mixed_free(afq_ctx* ctx);
 int launch_slice_theta(afq_ctx* ctx, WalkerSet& s);
 int launch_force_bias_tc(afq_ctx* ctx, WalkerSet& s);
 int launch_exchange_tc(afq_ctx* ctx, WalkerSet& s);
+int mixed_autotune(afq_ctx* ctx);
 void mixed_prop_free(afq_ctx* ctx);
 int mixed_prop_init_trial(afq_ctx* ctx);
 int mixed_prop_init_walkers(afq_ctx* ctx);

@@ -233,6 +233,17 @@ __global__ void k_fb_reduce(int X, int W, int ksplit, const float* __restrict__ 
 // ===========================================================================
 // context integration
 // ===========================================================================
+// Walkers per exchange tile for one spin: the MMA width and the theta tensor map.
+bool set_exchange_zb(afq_ctx* ctx, int spin, int zb) {
+  const int n = spin ? ctx->nb : ctx->na;
+  ctx->ex_zb[spin] = zb;
+  ctx->ex_BN[spin] = round_up(2 * n * zb, 16);
+  const uint64_t db[4] = {(uint64_t)ctx->Mpad, (uint64_t)ctx->N, (uint64_t)(2 * ctx->ws.W),
+                          (uint64_t)ctx->S};
+  const uint32_t bb[4] = {kBK, (uint32_t)n, (uint32_t)(2 * zb), 1};
+  return make_tmap(&ctx->tm_ex_b[spin], ctx->th_sl, 4, db, bb);
+}
+
 int mixed_exchange_tiles(int n, int* G, int* zb, int* BN) {
   if (n <= 0) return 0;
   *G = 128 / n;
@@ -288,7 +299,9 @@ int mixed_init_walkers(afq_ctx* ctx) {
   if (ks < 1) ks = 1;
   ctx->fb_kbper = (nkb + ks - 1) / ks;
   ctx->fb_ksplit = (nkb + ctx->fb_kbper - 1) / ctx->fb_kbper;
-  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->fb_part, (size_t)ctx->fb_ksplit * W2 * X * sizeof(float)));
+  ctx->fb_ksplit_cap = 4 * ctx->fb_ksplit;  // the autotuner may deepen the split
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->fb_part,
+                           (size_t)ctx->fb_ksplit_cap * W2 * X * sizeof(float)));
   {
     const uint64_t da[3] = {(uint64_t)N * Mp, (uint64_t)X, (uint64_t)S};
     const uint32_t ba[3] = {kBK, 128, 1};
@@ -304,12 +317,68 @@ int mixed_init_walkers(afq_ctx* ctx) {
     if (!mixed_exchange_tiles(n, &ctx->ex_G[s], &ctx->ex_zb[s], &ctx->ex_BN[s])) continue;
     const uint64_t da[4] = {(uint64_t)Mp, (uint64_t)N, (uint64_t)X, (uint64_t)S};
     const uint32_t ba[4] = {kBK, (uint32_t)n, (uint32_t)ctx->ex_G[s], 1};
-    const uint64_t db[4] = {(uint64_t)Mp, (uint64_t)N, (uint64_t)W2, (uint64_t)S};
-    const uint32_t bb[4] = {kBK, (uint32_t)n, (uint32_t)(2 * ctx->ex_zb[s]), 1};
-    if (!make_tmap(&ctx->tm_ex_a[s], ctx->Lt_sl, 4, da, ba) ||
-        !make_tmap(&ctx->tm_ex_b[s], ctx->th_sl, 4, db, bb))
+    if (!make_tmap(&ctx->tm_ex_a[s], ctx->Lt_sl, 4, da, ba) || !set_exchange_zb(ctx, s, ctx->ex_zb[s]))
       return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (exchange) failed");
   }
+  return AFQ_OK;
+}
+
+// Tunable tiles of the split-precision energy contractions: walkers per exchange
+// tile (per spin) and the split-K depth of the force bias, timed on the walkers.
+int mixed_autotune(afq_ctx* ctx) {
+  WalkerSet& s = ctx->ws;
+  auto timeit = [&](auto&& f) {
+    if (f() != AFQ_OK) return 1e30f;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, ctx->stream);
+    int rc = AFQ_OK;
+    for (int r = 0; r < 3 && rc == AFQ_OK; ++r) rc = f();
+    cudaEventRecord(b, ctx->stream);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc == AFQ_OK ? ms / 3 : 1e30f;
+  };
+  for (int spin = 0; spin < 2; ++spin) {
+    const int n = spin ? ctx->nb : ctx->na;
+    if (n == 0) continue;
+    const int zbmax = ctx->ex_zb[spin];
+    int best_zb = zbmax;
+    float best = 1e30f;
+    for (int zb : {zbmax, zbmax * 3 / 4, zbmax / 2, zbmax / 3, zbmax / 4}) {
+      if (zb < 1 || (zb != zbmax && zb == best_zb)) continue;
+      if (!set_exchange_zb(ctx, spin, zb)) return afq_fail(ctx, AFQ_ERR_CUDA, "exchange map");
+      const float ms = timeit([&] { return launch_exchange_tc(ctx, s); });
+      if (ms < best) {
+        best = ms;
+        best_zb = zb;
+      }
+    }
+    if (!set_exchange_zb(ctx, spin, best_zb)) return afq_fail(ctx, AFQ_ERR_CUDA, "exchange map");
+  }
+  // force bias split-K: K blocks per CTA, within the partial-sum buffer's ksplit bound
+  const int nkb = ctx->N * ctx->Mpad / kBK;
+  const int kb0 = ctx->fb_kbper, cap = ctx->fb_ksplit_cap;
+  int best_kb = kb0;
+  float best = 1e30f;
+  for (int kb : {kb0, kb0 * 2, kb0 * 4, (kb0 + 1) / 2, (kb0 + 3) / 4}) {
+    if (kb < 1 || kb > nkb) continue;
+    const int ks = (nkb + kb - 1) / kb;
+    if (ks > cap) continue;
+    ctx->fb_kbper = kb;
+    ctx->fb_ksplit = ks;
+    const float ms = timeit([&] { return launch_force_bias_tc(ctx, s); });
+    if (ms < best) {
+      best = ms;
+      best_kb = kb;
+    }
+  }
+  ctx->fb_kbper = best_kb;
+  ctx->fb_ksplit = (nkb + best_kb - 1) / best_kb;
   return AFQ_OK;
 }
 

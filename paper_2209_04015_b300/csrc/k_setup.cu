@@ -114,9 +114,11 @@ __global__ void k_hpp(int M, int X, const double* __restrict__ h1,
   }
 }
 
+// y = a x + b y; with b == 0 the old y is not read (it may be uninitialised memory,
+// and 0 * NaN would poison the result)
 __global__ void k_axpby(int n, double a, const double* __restrict__ x, double b, double* y) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-    y[e] = a * x[e] + b * y[e];
+    y[e] = b == 0.0 ? a * x[e] : a * x[e] + b * y[e];
 }
 
 __global__ void k_identity(int M, double* out) {

@@ -76,7 +76,8 @@ __device__ double2 block_sum2(double2 v, double2* red) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fields(int X, double sdt, double cap,
                                                 const double* __restrict__ xi_in, uint64_t seed,
-                                                uint64_t step, const double2* __restrict__ c,
+                                                const unsigned long long* __restrict__ step_dev,
+                                                const double2* __restrict__ c,
                                                 const double* __restrict__ vbar,
                                                 double2* __restrict__ xbar, double2* __restrict__ y,
                                                 double2* __restrict__ cfb,
@@ -84,6 +85,9 @@ __global__ void __launch_bounds__(256) k_fields(int X, double sdt, double cap,
   __shared__ double2 red[8];
   const int z = blockIdx.x;
   const int npair = (X + 1) / 2;
+  // the step counter lives on the device so that a captured graph draws new fields
+  // on every replay
+  const uint64_t step = *step_dev;
   double2 sfb = cmk(0.0, 0.0), smf = cmk(0.0, 0.0);
   for (int m = threadIdx.x; m < npair; m += 256) {
     double xi2[2];
@@ -323,8 +327,10 @@ __global__ void k_propagate_fp64(int M, int N, int order, const double* __restri
 // ---------------------------------------------------------------------------
 __global__ void k_weights(int W, double log_const, int free_proj, const double2* __restrict__ det,
                           const double2* __restrict__ cfb, const double2* __restrict__ cmf,
-                          double2* __restrict__ ovlp, double2* __restrict__ w, int* flags) {
+                          double2* __restrict__ ovlp, double2* __restrict__ w, int* flags,
+                          unsigned long long* __restrict__ step_dev) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z == 0) *step_dev += 1;  // the step's fields were drawn by k_fields earlier in order
   if (z >= W) return;
   const double2 onew = cmul(det[2 * z], det[2 * z + 1]);
   const double2 ratio = cmul(cdiv(onew, ovlp[z]), cexp(cmf[z]));
@@ -365,9 +371,9 @@ __global__ void __launch_bounds__(256) k_emix(int W, int free_proj, const double
 
 }  // namespace
 
-int launch_fields(afq_ctx* ctx, const double* xi_dev, uint64_t step) {
+int launch_fields(afq_ctx* ctx, const double* xi_dev) {
   k_fields<<<ctx->ws.W, 256, 0, ctx->stream>>>(ctx->X, sqrt(ctx->p.dt), ctx->p.fb_cap, xi_dev,
-                                               ctx->p.seed, step, ctx->ws.c, ctx->vbar,
+                                               ctx->p.seed, ctx->d_step, ctx->ws.c, ctx->vbar,
                                                ctx->xbar, ctx->y, ctx->cfb, ctx->cmf);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
@@ -391,8 +397,8 @@ int launch_vhs_fp64(afq_ctx* ctx) {
   return AFQ_OK;
 }
 
-int launch_propagate_fp64(afq_ctx* ctx) {
-  constexpr int NC = 4;
+template <int NC>
+int launch_propagate_nc(afq_ctx* ctx) {
   const int threads = 32 * ((ctx->M + 31) / 32);
   const size_t smem = (size_t)3 * ctx->M * NC * sizeof(double2);
   static size_t configured = 0;
@@ -408,10 +414,19 @@ int launch_propagate_fp64(afq_ctx* ctx) {
   return AFQ_OK;
 }
 
+// Column chunk NC (2, 4 or 8 walker columns per CTA) as chosen by the autotuner.
+int launch_propagate_fp64(afq_ctx* ctx) {
+  switch (ctx->prop_nc) {
+    case 2: return launch_propagate_nc<2>(ctx);
+    case 8: return launch_propagate_nc<8>(ctx);
+    default: return launch_propagate_nc<4>(ctx);
+  }
+}
+
 int launch_weights(afq_ctx* ctx, double log_const) {
   k_weights<<<(ctx->ws.W + 127) / 128, 128, 0, ctx->stream>>>(
       ctx->ws.W, log_const, ctx->p.free_projection, ctx->ws.det, ctx->cfb, ctx->cmf,
-      ctx->ws.ovlp, ctx->ws.w, ctx->flags);
+      ctx->ws.ovlp, ctx->ws.w, ctx->flags, ctx->d_step);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }

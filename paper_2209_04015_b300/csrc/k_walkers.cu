@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) k_force_bias_fp64(int X, int W, int K,
 constexpr int ET = 256, EKC = 32;
 constexpr int MAXO6 = (64 * AFQ_NMAX + ET - 1) / ET;
 __global__ void __launch_bounds__(ET) k_exchange_fp64(int M, int N, int na, int nb, int X,
-                                                      int G, int ngroups,
+                                                      int G, int slots,
                                                       const double* __restrict__ Lt,
                                                       const double2* __restrict__ thetaT,
                                                       double2* __restrict__ ekp) {
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(ET) k_exchange_fp64(int M, int N, int na, int 
   __shared__ double2 red[ET / 32];
   const int grp = blockIdx.x, z = blockIdx.y, s = blockIdx.z, tid = threadIdx.x;
   const int n = s ? nb : na, off = s ? na : 0;
-  const long oidx = ((long)z * 2 + s) * ngroups + grp;
+  const long oidx = ((long)z * 2 + s) * slots + grp;
   if (n == 0) {
     if (tid == 0) ekp[oidx] = cmk(0.0, 0.0);
     return;
@@ -437,11 +437,20 @@ int launch_force_bias_fp64(afq_ctx* ctx, WalkerSet& s) {
   return AFQ_OK;
 }
 
+// Largest g-group for n_max electrons per spin: G n^2 outputs fit the per-thread
+// register tile and the shared memory of one CTA.
+int exchange_group_max(int nmax) {
+  if (nmax <= 0) return 1;
+  int g = (64 * AFQ_NMAX) / (nmax * nmax);
+  while (g > 1 && exchange_smem(g, nmax) > 200 * 1024) --g;
+  return g < 1 ? 1 : g;
+}
+
 int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s) {
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
-  const int G = exchange_group_size(nmax);
+  const int G = ctx->ex_G_fp64 > 0 ? ctx->ex_G_fp64 : exchange_group_size(nmax);
   const int ngroups = (ctx->X + G - 1) / G;
-  if (ngroups != ctx->ex_groups) return afq_fail(ctx, AFQ_ERR_STATE, "exchange groups changed");
+  if (ngroups > ctx->ex_groups) return afq_fail(ctx, AFQ_ERR_STATE, "exchange groups exceed slots");
   const size_t smem = exchange_smem(G, nmax);
   static size_t configured = 0;
   if (smem > configured) {
@@ -450,7 +459,7 @@ int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s) {
     configured = smem;
   }
   k_exchange_fp64<<<dim3(ngroups, s.W, 2), ET, smem, ctx->stream>>>(
-      ctx->M, ctx->N, ctx->na, ctx->nb, ctx->X, G, ngroups, ctx->Lt, s.thetaT, s.ekp);
+      ctx->M, ctx->N, ctx->na, ctx->nb, ctx->X, G, ctx->ex_groups, ctx->Lt, s.thetaT, s.ekp);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }

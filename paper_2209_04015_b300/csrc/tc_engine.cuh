@@ -341,9 +341,15 @@ inline void plan_smem(int S, int kUA, int kUB, int BN, size_t epilogue_bytes, in
 template <int S, class P>
 cudaError_t launch_tc(dim3 grid, size_t smem, cudaStream_t stream, const CUtensorMap& a,
                       const CUtensorMap& b, const typename P::Args& args) {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_split<S, P>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  // set once per instantiation and size, so that no attribute call is issued while a
+  // graph is being captured after a first ordinary step
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_split<S, P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
   k_tc_split<S, P><<<grid, kThreads, smem, stream>>>(a, b, args);
   return cudaGetLastError();
 }

@@ -193,3 +193,35 @@ def test_c2_full_size_sampled_walkers():
     assert rel(ctx.get_weights()[idx], orc.w).max() <= TOL
     eref, _ = orc.local_energy()
     assert rel(e[idx, 3], eref[:, 3]).max() <= TOL
+
+
+def test_recreated_contexts_on_reused_memory_are_identical():
+    """Contexts destroyed and re-created while others stay alive reuse device memory
+    that holds stale values (NaN bit patterns included); no kernel may read memory it
+    did not write first (a set-up y = a x + 0 y once turned such NaNs into P)."""
+    from paper_2209_04015_b300 import AfqContext
+    others = []
+    for k in range(3):
+        s = make_system(30 + 7 * k, 4, 3, 40, seed=20 + k)
+        c = AfqContext(precision="split_bf16" if k % 2 else "fp64")
+        c.init_hamiltonian(s.h1, s.L, s.e0)
+        c.init_trial(s.psi_a, s.psi_b)
+        c.init_walkers(16)
+        c.propagate(None, 2)
+        others.append(c)
+    s = make_system(48, 6, 5, 90, seed=3)
+    results = []
+    for rep in range(3):
+        for prec in ("fp64", "split_bf16"):
+            c = AfqContext(precision=prec)
+            c.init_hamiltonian(s.h1, s.L, s.e0)
+            c.init_trial(s.psi_a, s.psi_b)
+            c.init_walkers(24)
+            c.propagate(None, 3)
+            e, _ = c.local_energy()
+            results.append((prec, c.get_walkers(), e))
+            c.close()
+    for i in range(2, len(results)):
+        assert results[i][0] == results[i - 2][0]
+        assert np.array_equal(results[i][1], results[i - 2][1])
+        assert np.array_equal(results[i][2], results[i - 2][2])
