@@ -254,6 +254,58 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
     return out
 
 
+def batched_leg(rank: int, replays: int = 8, precision: str = "split_bf16") -> dict:
+    """The eight uneven systems (48..220 orbitals, 0.2 M electrons per spin, X = 5 M,
+    512..32 walkers) autotuned and stepped by one CUDA graph (one branch per system,
+    5 steps + local energies per replay), against eager stepping of the same contexts."""
+    import torch
+    from paper_2209_04015_b300 import AfqBatch, AfqContext
+    from paper_2209_04015_b300.synthetic import make_c4
+
+    systems = make_c4(seed0=1 + 10 * rank)
+    ctxs = []
+    for k, (s, W) in enumerate(systems):
+        c = AfqContext(dt=0.005, qr_period=5, seed=1 + k, precision=precision)
+        c.init_hamiltonian(s.h1, s.L, s.e0)
+        c.init_trial(s.psi_a, s.psi_b)
+        c.init_walkers(W)
+        c.autotune()
+        ctxs.append(c)
+    walkers = sum(W for _, W in systems)
+    # eager: each system in turn, one host call per step and energy (warm up first)
+    for c in ctxs:
+        c.propagate(None, 5)
+        c.local_energy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in ctxs:
+        for _ in range(5):
+            c.propagate_dev(None, 1)
+            c.local_energy_dev(None, None)
+    torch.cuda.synchronize()
+    eager_s = (time.perf_counter() - t0) / 5
+    b = AfqBatch(ctxs)
+    b.capture(5)
+    b.launch(1)
+    b.synchronize()
+    t0 = time.perf_counter()
+    b.launch(replays)
+    b.synchronize()
+    graph_s = (time.perf_counter() - t0) / (5 * replays)
+    tiles = {f"system{k}": c.get_tiles() for k, c in enumerate(ctxs)}
+    b.close()
+    for c in ctxs:
+        c.close()
+    return {"workload": "8 uneven systems: orbitals 48..220, 0.2 M electrons per spin, "
+                        "X = 5 M, walkers 512..32, split_bf16",
+            "walkers_total": walkers, "value": walkers / graph_s, "unit": UNIT,
+            "ms_per_step": graph_s * 1e3, "eager_value": walkers / eager_s,
+            "eager_ms_per_step": eager_s * 1e3, "graph_speedup": eager_s / graph_s,
+            "replays": replays, "steps_per_replay": 5,
+            "timing": "host wall clock around synchronised replays (graph) or eager steps",
+            "autotuned_tiles": tiles}
+
+
 # ----------------------------------------------------------------------------- arms
 
 def run_reference(args):
@@ -413,6 +465,7 @@ def run_afq(args):
                          "large_shape": mixed_leg("c3", args.mixed_steps, args.warmup, rank)}
         line["mixed"]["same_workload"]["speedup_vs_fp64"] = (
             line["mixed"]["same_workload"]["value"] / (value / world))
+        line["batched"] = batched_leg(rank)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
