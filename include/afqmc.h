@@ -176,6 +176,22 @@ int afq_profile_read(afq_ctx* ctx, int kernel, double* total_ms, uint64_t* launc
 /* Name of a kernel class, or NULL when kernel is out of range. */
 const char* afq_kernel_name(int kernel);
 
+/* ---- Adjoint of the mixed local energy (the paper lists automatic differentiation
+   as future work, Sec. "Customized mixed estimators"; closed forms of the local
+   energy of Sec. "Local energy") ----
+   For a cotangent gE (W complex; PyTorch's convention gE = dLoss/dRe E + i dLoss/dIm E)
+   of Loss(E_L), at the current walkers:
+     dh1  (M x M)          = Re sum_z conj(g_z) G_z   (G = the mixed one-body density
+                            matrix sum_s Psi_s theta_s^T; dE/dh1 = G)
+     dL   (X x M x M)      = Re sum_z conj(g_z) (c_zg G_z - sum_s G^s_z L_g^T G^s_z)
+     dphi (W x M x N cplx) = g_z conj(dE_z/dPhi_z) = dLoss/dRe Phi + i dLoss/dIm Phi
+   h1 and L_g entries are treated as independent (no symmetrisation).  Any output
+   may be NULL.  Needs max(na, nb) * M <= 8192.  FP64 in both precision modes. */
+int afq_local_energy_backward(afq_ctx* ctx, const double* gE, double* dh1, double* dL,
+                              double* dphi);
+int afq_local_energy_backward_dev(afq_ctx* ctx, const double* gE_dev, double* dh1_dev,
+                                  double* dL_dev, double* dphi_dev);
+
 /* ---- CUDA graphs, batches of systems, autotuning (no counterpart in the paper:
    these serve the data-parallel step at scale) ---- */
 

@@ -55,6 +55,8 @@ _SIGS = {
     "afq_local_energy": (ctypes.c_int, [_P, _P, _D]),
     "afq_local_energy_dev": (ctypes.c_int, [_P, _P, _P]),
     "afq_orthogonalise": (ctypes.c_int, [_P]),
+    "afq_local_energy_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "afq_local_energy_backward_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "afq_get_walkers": (ctypes.c_int, [_P, _P]),
     "afq_get_weights": (ctypes.c_int, [_P, _P]),
     "afq_get_overlaps": (ctypes.c_int, [_P, _P]),
@@ -154,6 +156,7 @@ class AfqContext:
         if rc != AFQ_OK:
             raise AfqError(rc, "afq_create failed")
         self.h = h
+        self.stream = stream or 0
         self.M = self.X = self.na = self.nb = self.W = 0
 
     # -- plumbing ---------------------------------------------------------------
@@ -224,6 +227,25 @@ class AfqContext:
 
     def orthogonalise(self) -> None:
         self._check(self.lib.afq_orthogonalise(self.h))
+
+    def local_energy_backward(self, gE: np.ndarray, want=("h1", "L", "phi")):
+        """Gradients of sum_z Re(conj(gE_z) E_L,z) at the current walkers: (dh1 (M, M),
+        dL (X, M, M), dphi (W, M, N) complex), None for outputs not in ``want``."""
+        g = _c(gE, np.complex128)
+        if g.size != self.W:
+            raise ValueError("gE must hold W complex values")
+        dh = np.empty((self.M, self.M)) if "h1" in want else None
+        dL = np.empty((self.X, self.M, self.M)) if "L" in want else None
+        dp = np.empty((self.W, self.M, self.N), dtype=np.complex128) if "phi" in want else None
+        self._check(self.lib.afq_local_energy_backward(self.h, _ptr(g), _ptr(dh), _ptr(dL),
+                                                       _ptr(dp)))
+        return dh, dL, dp
+
+    def local_energy_backward_dev(self, gE_ptr: int, dh1_ptr: int | None, dL_ptr: int | None,
+                                  dphi_ptr: int | None) -> None:
+        self._check(self.lib.afq_local_energy_backward_dev(
+            self.h, _P(gE_ptr), _P(dh1_ptr) if dh1_ptr else None, _P(dL_ptr) if dL_ptr else None,
+            _P(dphi_ptr) if dphi_ptr else None))
 
     def get_walkers(self) -> np.ndarray:
         out = np.empty((self.W, self.M, self.N), dtype=np.complex128)

@@ -1007,6 +1007,43 @@ int afq_autotune(afq_ctx* ctx) {
   return rc == AFQ_OK ? check_flags(ctx) : rc;
 }
 
+int afq_local_energy_backward_dev(afq_ctx* ctx, const double* gE_dev, double* dh1_dev,
+                                  double* dL_dev, double* dphi_dev) {
+  if (!ctx || !gE_dev) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  if (ctx->capturing) return afq_fail(ctx, AFQ_ERR_STATE, "not during capture");
+  AFQ_TRY(adjoint_local_energy(ctx, reinterpret_cast<const double2*>(gE_dev), dh1_dev, dL_dev,
+                               reinterpret_cast<double2*>(dphi_dev)));
+  return check_flags(ctx);  // the backward synchronises the stream before returning
+}
+
+int afq_local_energy_backward(afq_ctx* ctx, const double* gE, double* dh1, double* dL,
+                              double* dphi) {
+  if (!ctx || !gE) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  const size_t W = ctx->ws.W, M = ctx->M, N = ctx->N, X = ctx->X;
+  double *g = nullptr, *a = nullptr, *b = nullptr, *c = nullptr;
+  int rc = AFQ_OK;
+  if (cudaMalloc((void**)&g, W * 16) != cudaSuccess ||
+      (dh1 && cudaMalloc((void**)&a, M * M * 8) != cudaSuccess) ||
+      (dL && cudaMalloc((void**)&b, X * M * M * 8) != cudaSuccess) ||
+      (dphi && cudaMalloc((void**)&c, W * M * N * 16) != cudaSuccess))
+    rc = afq_fail(ctx, AFQ_ERR_NOMEM, "backward outputs");
+  if (rc == AFQ_OK && cudaMemcpyAsync(g, gE, W * 16, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "copy gE");
+  if (rc == AFQ_OK) rc = adjoint_local_energy(ctx, reinterpret_cast<double2*>(g), a, b,
+                                              reinterpret_cast<double2*>(c));
+  if (rc == AFQ_OK && dh1) rc = cudaMemcpy(dh1, a, M * M * 8, cudaMemcpyDeviceToHost) == cudaSuccess ? rc : AFQ_ERR_CUDA;
+  if (rc == AFQ_OK && dL) rc = cudaMemcpy(dL, b, X * M * M * 8, cudaMemcpyDeviceToHost) == cudaSuccess ? rc : AFQ_ERR_CUDA;
+  if (rc == AFQ_OK && dphi) rc = cudaMemcpy(dphi, c, W * M * N * 16, cudaMemcpyDeviceToHost) == cudaSuccess ? rc : AFQ_ERR_CUDA;
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(g);
+  if (a) cudaFree(a);
+  if (b) cudaFree(b);
+  if (c) cudaFree(c);
+  return rc != AFQ_OK ? rc : check_flags(ctx);
+}
+
 int afq_get_tiles(afq_ctx* ctx, int* tiles, int n) {
   if (!ctx || !tiles || n < 1) return AFQ_ERR_ARG;
   const int v[5] = {ctx->ex_G_fp64, ctx->prop_nc, ctx->ex_zb[0], ctx->ex_zb[1], ctx->fb_ksplit};

@@ -188,6 +188,9 @@ int launch_propagate_fp64(afq_ctx* ctx);
 int launch_weights(afq_ctx* ctx, double log_const);
 int launch_emix(afq_ctx* ctx, WalkerSet& s, double* out);
 
+// adjoint of the local energy (k_adjoint.cu)
+int adjoint_local_energy(afq_ctx* ctx, const double2* gE, double* dh1, double* dL, double2* dphi);
+
 // split-precision tensor-core path (k_mixed.cu)
 int mixed_init_trial(afq_ctx* ctx);
 int mixed_init_walkers(afq_ctx* ctx);
