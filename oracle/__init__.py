@@ -14,8 +14,10 @@ afqmc     one imaginary-time step, local energy and QR re-orthogonalisation,
           complex128 NumPy.
 philox    Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the
           Box-Muller map to Gaussian auxiliary fields.
-gradients closed-form gradients of the mixed local energy and the
-          finite-difference objective of the multi-step chain.
+gradients closed-form gradients of the mixed local energy.
+chain     the objective of a K-step chain (fixed fields, detached weights) through
+          the NumPy oracle, and the same steps in PyTorch CPU float64 whose
+          autograd gives the chain's gradient.
 
 Every function says which passage of the paper it follows.  Where the paper is
 silent or ambiguous the reading taken is stated in the function's docstring.
