@@ -192,6 +192,34 @@ int afq_local_energy_backward(afq_ctx* ctx, const double* gE, double* dh1, doubl
 int afq_local_energy_backward_dev(afq_ctx* ctx, const double* gE_dev, double* dh1_dev,
                                   double* dL_dev, double* dphi_dev);
 
+/* ---- Adjoint of a K-step chain (FP64 contexts, fb_cap = 0) ----
+   Objective: Loss = sum_z Re(conj(g_z) E_L(Phi_z^K)) after K steps of the hybrid
+   propagation (Sec. "Review of AFQMC") from the walkers Phi^0 held at the call, with
+   the fields xi of every step held fixed.  The force bias is differentiated through
+   (it depends on Phi and L); the weights are not part of the objective (the phaseless
+   max(0, cos) is not differentiable); vbar, L~ and P = exp(-dt h''/2) depend on h1
+   and L.  QR re-orthogonalisation is a gauge (E_L and theta are invariant under
+   Phi -> Phi C), so the cotangent maps through it as lam_pre = lam_post R^-T.
+
+   afq_chain_forward runs K ordinary steps (weights, overlaps and QR as afq_propagate;
+   fields: K x W x X N(0,1) values, or NULL for the device Philox stream at the
+   current step counter), keeps a tape (the fields and the walkers at the chain start,
+   after every QR and every ceil(sqrt(K)) steps when qr_period = 0) and returns the
+   energies at Phi^K in e_out (W x 4 complex, as afq_local_energy; may be NULL).
+   afq_chain_backward then gives, for a cotangent gE (W complex):
+     dh1   (M x M)          symmetrised dLoss/dh1
+     dL    (X x M x M)      symmetrised dLoss/dL_g
+     dphi0 (W x M x N cplx) dLoss/dRe Phi^0 + i dLoss/dIm Phi^0
+   recomputing each segment from its checkpoint.  Any output may be NULL.  It fails
+   with AFQ_ERR_STATE if the walkers changed after the forward (a step, QR, set_state
+   or init_walkers), and needs max(na, nb) * M <= 8192.  The context's walkers,
+   weights and force bias are left as the forward left them. */
+int afq_chain_forward(afq_ctx* ctx, int K, const double* fields, double* e_out);
+int afq_chain_forward_dev(afq_ctx* ctx, int K, const double* fields_dev, double* e_out_dev);
+int afq_chain_backward(afq_ctx* ctx, const double* gE, double* dh1, double* dL, double* dphi0);
+int afq_chain_backward_dev(afq_ctx* ctx, const double* gE_dev, double* dh1_dev, double* dL_dev,
+                           double* dphi0_dev);
+
 /* ---- CUDA graphs, batches of systems, autotuning (no counterpart in the paper:
    these serve the data-parallel step at scale) ---- */
 

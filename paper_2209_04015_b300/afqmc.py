@@ -57,6 +57,10 @@ _SIGS = {
     "afq_orthogonalise": (ctypes.c_int, [_P]),
     "afq_local_energy_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "afq_local_energy_backward_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "afq_chain_forward": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "afq_chain_forward_dev": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "afq_chain_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "afq_chain_backward_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "afq_get_walkers": (ctypes.c_int, [_P, _P]),
     "afq_get_weights": (ctypes.c_int, [_P, _P]),
     "afq_get_overlaps": (ctypes.c_int, [_P, _P]),
@@ -240,6 +244,37 @@ class AfqContext:
         self._check(self.lib.afq_local_energy_backward(self.h, _ptr(g), _ptr(dh), _ptr(dL),
                                                        _ptr(dp)))
         return dh, dL, dp
+
+    def chain_forward(self, K: int, fields: np.ndarray | None = None) -> np.ndarray:
+        """K steps with a tape for chain_backward; returns the energies (W, 4) at the end."""
+        f = None if fields is None else _c(fields, np.float64)
+        if f is not None and f.size != K * self.W * self.X:
+            raise ValueError("fields must hold K x W x X values")
+        e = np.empty((self.W, 4), dtype=np.complex128)
+        self._check(self.lib.afq_chain_forward(self.h, K, _ptr(f), _ptr(e)))
+        return e
+
+    def chain_forward_dev(self, K: int, fields_ptr: int | None, e_ptr: int | None) -> None:
+        self._check(self.lib.afq_chain_forward_dev(self.h, K, _P(fields_ptr) if fields_ptr else None,
+                                                   _P(e_ptr) if e_ptr else None))
+
+    def chain_backward(self, gE: np.ndarray, want=("h1", "L", "phi")):
+        """Gradients of sum_z Re(conj(gE_z) E_L(Phi_z^K)) for the chain on the tape:
+        (dh1 (M, M), dL (X, M, M)) symmetrised and dphi0 (W, M, N) complex."""
+        g = _c(gE, np.complex128)
+        if g.size != self.W:
+            raise ValueError("gE must hold W complex values")
+        dh = np.empty((self.M, self.M)) if "h1" in want else None
+        dL = np.empty((self.X, self.M, self.M)) if "L" in want else None
+        dp = np.empty((self.W, self.M, self.N), dtype=np.complex128) if "phi" in want else None
+        self._check(self.lib.afq_chain_backward(self.h, _ptr(g), _ptr(dh), _ptr(dL), _ptr(dp)))
+        return dh, dL, dp
+
+    def chain_backward_dev(self, gE_ptr: int, dh1_ptr: int | None, dL_ptr: int | None,
+                           dphi0_ptr: int | None) -> None:
+        self._check(self.lib.afq_chain_backward_dev(
+            self.h, _P(gE_ptr), _P(dh1_ptr) if dh1_ptr else None, _P(dL_ptr) if dL_ptr else None,
+            _P(dphi0_ptr) if dphi0_ptr else None))
 
     def local_energy_backward_dev(self, gE_ptr: int, dh1_ptr: int | None, dL_ptr: int | None,
                                   dphi_ptr: int | None) -> None:

@@ -38,12 +38,6 @@ void dfree(T** p) {
   *p = nullptr;
 }
 
-#define AFQ_TRY(x)            \
-  do {                        \
-    int rc_ = (x);            \
-    if (rc_ != AFQ_OK) return rc_; \
-  } while (0)
-
 int free_walker_set(WalkerSet& s) {
   dfree(&s.phi);
   dfree(&s.thetaT);
@@ -164,6 +158,7 @@ int energy_kernels(afq_ctx* ctx, WalkerSet& s) {
 }
 
 int free_walkers(afq_ctx* ctx) {
+  chain_free(ctx);
   free_walker_set(ctx->ws);
   dfree(&ctx->xi);
   dfree(&ctx->xbar);
@@ -575,6 +570,7 @@ int afq_local_energy_dev(afq_ctx* ctx, double* e_out_dev, double* e_mix_dev) {
 int afq_orthogonalise(afq_ctx* ctx) {
   if (!ctx) return AFQ_ERR_ARG;
   if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  chain_free(ctx);  // a chain tape refers to the walkers before this QR
   AFQ_TRY(timed(ctx, AFQ_K_QR, [&] { return launch_qr(ctx, ctx->ws, ctx->A); }));
   AFQ_TRY(sync(ctx));
   return check_flags(ctx);
@@ -613,6 +609,7 @@ int afq_set_state(afq_ctx* ctx, const double* phi, const double* w, const double
                   uint64_t step) {
   if (!ctx || !phi || !w) return AFQ_ERR_ARG;
   if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  chain_free(ctx);
   const size_t W = ctx->ws.W;
   AFQ_CUDA(ctx, cudaMemcpyAsync(ctx->ws.phi, phi, W * ctx->M * ctx->N * 16, cudaMemcpyHostToDevice,
                                 ctx->stream));
@@ -1036,6 +1033,133 @@ int afq_local_energy_backward(afq_ctx* ctx, const double* gE, double* dh1, doubl
   if (rc == AFQ_OK && dh1) rc = cudaMemcpy(dh1, a, M * M * 8, cudaMemcpyDeviceToHost) == cudaSuccess ? rc : AFQ_ERR_CUDA;
   if (rc == AFQ_OK && dL) rc = cudaMemcpy(dL, b, X * M * M * 8, cudaMemcpyDeviceToHost) == cudaSuccess ? rc : AFQ_ERR_CUDA;
   if (rc == AFQ_OK && dphi) rc = cudaMemcpy(dphi, c, W * M * N * 16, cudaMemcpyDeviceToHost) == cudaSuccess ? rc : AFQ_ERR_CUDA;
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(g);
+  if (a) cudaFree(a);
+  if (b) cudaFree(b);
+  if (c) cudaFree(c);
+  return rc != AFQ_OK ? rc : check_flags(ctx);
+}
+
+static int chain_forward_impl(afq_ctx* ctx, int K, const double* fields, bool dev,
+                              double* e_out, bool e_dev) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  if (ctx->capturing) return afq_fail(ctx, AFQ_ERR_STATE, "not during capture");
+  if (ctx->mixed) return afq_fail(ctx, AFQ_ERR_ARG, "the chain adjoint needs an FP64 context");
+  if (ctx->p.fb_cap > 0.0)
+    return afq_fail(ctx, AFQ_ERR_ARG, "the chain adjoint needs fb_cap = 0 (a cap is not smooth)");
+  if (K < 0) return afq_fail(ctx, AFQ_ERR_ARG, "K must be >= 0");
+  chain_free(ctx);
+  ChainTape& t = ctx->chain;
+  const size_t W = ctx->ws.W, WX = W * ctx->X, WMN = W * ctx->M * ctx->N;
+  const int qr = ctx->p.qr_period;
+  t.K = K;
+  t.W = (int)W;
+  t.s0 = ctx->step;
+  t.seg_cap = qr > 0 ? qr : (int)std::ceil(std::sqrt((double)(K > 1 ? K : 1)));
+  // segments end after every QR and after seg_cap steps; checkpoints hold the walkers
+  // at the chain start, after every QR and at every inner segment boundary
+  std::vector<int> ck_step{0};
+  int last = 0;
+  for (int k = 1; k <= K; ++k) {
+    const bool q = qr > 0 && (t.s0 + k) % (uint64_t)qr == 0;
+    if (q || k - last >= t.seg_cap || k == K) {
+      ChainSeg sg;
+      sg.start = last;
+      sg.len = k - last;
+      sg.ck_in = (int)ck_step.size() - 1;
+      sg.qr_end = q;
+      if (q || k < K) {
+        ck_step.push_back(k);
+        sg.ck_out = (int)ck_step.size() - 1;
+      }
+      t.segs.push_back(sg);
+      last = k;
+    }
+  }
+  t.nck = (int)ck_step.size();
+  if (cudaMalloc((void**)&t.fields, (K > 0 ? (size_t)K : 1) * WX * 8) != cudaSuccess ||
+      cudaMalloc((void**)&t.ckpt, (size_t)t.nck * WMN * 16) != cudaSuccess) {
+    chain_free(ctx);
+    return afq_fail(ctx, AFQ_ERR_NOMEM, "chain tape");
+  }
+  int rc = AFQ_OK;
+  if (K > 0 && fields) {
+    if (cudaMemcpyAsync(t.fields, fields, (size_t)K * WX * 8,
+                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess)
+      rc = afq_fail(ctx, AFQ_ERR_CUDA, "copy chain fields");
+  } else {
+    for (int k = 0; k < K && rc == AFQ_OK; ++k)
+      rc = launch_philox_fields(ctx, t.s0 + k, t.fields + (size_t)k * WX, nullptr);
+  }
+  if (rc == AFQ_OK &&
+      cudaMemcpyAsync(t.ckpt, ctx->ws.phi, WMN * 16, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "chain checkpoint");
+  size_t ci = 1;
+  for (int k = 1; k <= K && rc == AFQ_OK; ++k) {
+    rc = one_step(ctx, t.fields + (size_t)(k - 1) * WX);
+    if (rc == AFQ_OK && ci < ck_step.size() && ck_step[ci] == k) {
+      if (cudaMemcpyAsync(t.ckpt + ci * WMN, ctx->ws.phi, WMN * 16, cudaMemcpyDeviceToDevice,
+                          ctx->stream) != cudaSuccess)
+        rc = afq_fail(ctx, AFQ_ERR_CUDA, "chain checkpoint");
+      ++ci;
+    }
+  }
+  if (rc == AFQ_OK) rc = energy_impl(ctx);
+  if (rc == AFQ_OK && e_out &&
+      cudaMemcpyAsync(e_out, ctx->ws.energy, W * 4 * 16,
+                      e_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "copy chain energies");
+  if (rc == AFQ_OK) rc = sync(ctx);
+  if (rc == AFQ_OK) rc = check_flags(ctx);
+  if (rc != AFQ_OK) {
+    chain_free(ctx);
+    return rc;
+  }
+  t.valid = true;
+  return AFQ_OK;
+}
+
+int afq_chain_forward(afq_ctx* ctx, int K, const double* fields, double* e_out) {
+  return chain_forward_impl(ctx, K, fields, false, e_out, false);
+}
+
+int afq_chain_forward_dev(afq_ctx* ctx, int K, const double* fields_dev, double* e_out_dev) {
+  return chain_forward_impl(ctx, K, fields_dev, true, e_out_dev, true);
+}
+
+int afq_chain_backward_dev(afq_ctx* ctx, const double* gE_dev, double* dh1_dev, double* dL_dev,
+                           double* dphi0_dev) {
+  if (!ctx || !gE_dev) return AFQ_ERR_ARG;
+  if (ctx->capturing) return afq_fail(ctx, AFQ_ERR_STATE, "not during capture");
+  AFQ_TRY(chain_backward(ctx, reinterpret_cast<const double2*>(gE_dev), dh1_dev, dL_dev,
+                         reinterpret_cast<double2*>(dphi0_dev)));
+  return check_flags(ctx);  // the backward synchronises the stream before returning
+}
+
+int afq_chain_backward(afq_ctx* ctx, const double* gE, double* dh1, double* dL, double* dphi0) {
+  if (!ctx || !gE) return AFQ_ERR_ARG;
+  if (!ctx->chain.valid) return afq_fail(ctx, AFQ_ERR_STATE, "afq_chain_forward first");
+  const size_t W = ctx->chain.W, M = ctx->M, N = ctx->N, X = ctx->X;
+  double *g = nullptr, *a = nullptr, *b = nullptr, *c = nullptr;
+  int rc = AFQ_OK;
+  if (cudaMalloc((void**)&g, W * 16) != cudaSuccess ||
+      (dh1 && cudaMalloc((void**)&a, M * M * 8) != cudaSuccess) ||
+      (dL && cudaMalloc((void**)&b, X * M * M * 8) != cudaSuccess) ||
+      (dphi0 && cudaMalloc((void**)&c, W * M * N * 16) != cudaSuccess))
+    rc = afq_fail(ctx, AFQ_ERR_NOMEM, "chain backward outputs");
+  if (rc == AFQ_OK && cudaMemcpyAsync(g, gE, W * 16, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "copy gE");
+  if (rc == AFQ_OK)
+    rc = chain_backward(ctx, reinterpret_cast<double2*>(g), a, b, reinterpret_cast<double2*>(c));
+  if (rc == AFQ_OK && dh1 && cudaMemcpy(dh1, a, M * M * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = AFQ_ERR_CUDA;
+  if (rc == AFQ_OK && dL && cudaMemcpy(dL, b, X * M * M * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = AFQ_ERR_CUDA;
+  if (rc == AFQ_OK && dphi0 && cudaMemcpy(dphi0, c, W * M * N * 16, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = AFQ_ERR_CUDA;
   cudaStreamSynchronize(ctx->stream);
   cudaFree(g);
   if (a) cudaFree(a);

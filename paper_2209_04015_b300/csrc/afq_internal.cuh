@@ -58,6 +58,24 @@ struct WalkerSet {
   double2* ovlp = nullptr;    // W           stored overlaps
 };
 
+// Tape of a K-step chain for its adjoint (k_chain.cu): the fields of every step and
+// the walkers at segment boundaries (chain start, after every QR, and every seg_cap
+// steps); the backward recomputes each segment from its checkpoint.
+struct ChainSeg {
+  int start = 0, len = 0;  // chain steps start .. start + len - 1 (0-based)
+  int ck_in = 0;           // checkpoint holding the walkers before step start
+  int ck_out = -1;         // checkpoint after the segment (the QR output), or -1
+  bool qr_end = false;     // the segment's last step ends with a QR
+};
+struct ChainTape {
+  bool valid = false;
+  int K = 0, W = 0, nck = 0, seg_cap = 0;
+  uint64_t s0 = 0;           // step counter at the chain start
+  double* fields = nullptr;  // K x W x X
+  double2* ckpt = nullptr;   // nck x W x M x N
+  std::vector<ChainSeg> segs;
+};
+
 struct afq_ctx {
   afq_params p{};
   cudaStream_t stream = nullptr;
@@ -129,6 +147,8 @@ struct afq_ctx {
   int* e_t[2] = {nullptr, nullptr};
   CUtensorMap tm_vhs_a, tm_vhs_b, tm_pm, tm_az, tm_t[2];
 
+  ChainTape chain;  // afq_chain_forward
+
   // built-in profiler: event pairs around launches of each kernel class
   bool profiling = false;
   struct ProfRec {
@@ -148,6 +168,11 @@ int afq_fail(afq_ctx* ctx, int code, const std::string& msg);
     cudaError_t e_ = (call);                                                             \
     if (e_ != cudaSuccess)                                                               \
       return afq_fail(ctx, AFQ_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define AFQ_TRY(x)                 \
+  do {                             \
+    int rc_ = (x);                 \
+    if (rc_ != AFQ_OK) return rc_; \
   } while (0)
 #define AFQ_LAUNCHED(ctx)                                                                \
   do {                                                                                   \
@@ -190,6 +215,19 @@ int launch_emix(afq_ctx* ctx, WalkerSet& s, double* out);
 
 // adjoint of the local energy (k_adjoint.cu)
 int adjoint_local_energy(afq_ctx* ctx, const double2* gE, double* dh1, double* dL, double2* dphi);
+// t holds theta and c of its walkers.  F (X x N x M, accumulated) may be NULL; out
+// receives the walker cotangent: mode 0 g conj(dE/dPhi), mode 1 conj(g) dE/dPhi.
+int adjoint_energy_core(afq_ctx* ctx, WalkerSet& t, const double2* gE, double* dh1, double* F,
+                        double2* out, int mode);
+// lam += (I - Psi theta^T) lamT^T S^-T per walker (the adjoint of theta = Phi S^-1)
+int launch_bwd_theta(afq_ctx* ctx, WalkerSet& t, const double2* lamT, double2* lam);
+
+// K-step chain adjoint (k_chain.cu)
+void chain_free(afq_ctx* ctx);
+int chain_backward(afq_ctx* ctx, const double2* gE, double* dh1, double* dL, double2* dphi0);
+// out = exp(scale * src) (n x n, FP64) by scaling and squaring of a degree-18 Taylor
+// polynomial; norm1 bounds ||scale * src||_1.
+int expm_taylor(afq_ctx* ctx, const double* src, double scale, int n, double norm1, double* out);
 
 // split-precision tensor-core path (k_mixed.cu)
 int mixed_init_trial(afq_ctx* ctx);

@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(BT) k_bwd_gbar(int M, int N, int na, int nb, i
 // dLoss/dPhi for one (walker, spin): S = Psi^T Phi and its inverse (Gauss-Jordan,
 // partial pivoting), W1 = theta^T Gbar, Y = Gbar - Psi W1, dE/dPhi = Y S^-T.
 // ---------------------------------------------------------------------------
+// MODE 0: out = g conj(d) (dLoss/dRe Phi + i dLoss/dIm Phi); MODE 1: out = conj(g) d
+// (the holomorphic cotangent); MODE 2: out += d (accumulate; gE unused).  d = Y S^-T.
+template <int MODE>
 __global__ void __launch_bounds__(BT) k_bwd_dphi(int M, int N, int na, int nb,
                                                  const double* __restrict__ psiT,
                                                  const double2* __restrict__ phi,
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(BT) k_bwd_dphi(int M, int N, int na, int nb,
     }
     __syncthreads();
   }
-  const double2 g = gE[z];
+  const double2 g = MODE == 2 ? cmk(1.0, 0.0) : gE[z];
   for (int e = tid; e < M * n; e += BT) {
     const int p = e / n, k = e % n;
     double2 d = cmk(0.0, 0.0);
@@ -167,7 +170,10 @@ __global__ void __launch_bounds__(BT) k_bwd_dphi(int M, int N, int na, int nb,
         y = csub(y, cscale(W1[i * n + j], psiT[(long)(off + i) * M + p]));
       d = cadd(d, cmul(y, aug[k * n2 + n + j]));  // (S^-1)_kj
     }
-    dphi[(long)z * M * N + (long)p * N + off + k] = cmul(g, cconj(d));
+    double2* o = dphi + (long)z * M * N + (long)p * N + off + k;
+    if (MODE == 0) *o = cmul(g, cconj(d));
+    else if (MODE == 1) *o = cmul(cconj(g), d);
+    else *o = cadd(*o, d);
   }
 }
 
@@ -186,7 +192,7 @@ __global__ void k_bwd_theta_sum(int W, long NM, const double2* __restrict__ thet
   }
 }
 
-// Re F_g,s[j][p] for one (g, spin): loops over every walker.
+// Re F_g,s[j][p] for one (g, spin), added to F: loops over every walker.
 __global__ void __launch_bounds__(BT) k_bwd_lfac(int M, int N, int na, int nb, int X, int W,
                                                  const double* __restrict__ Lt,
                                                  const double2* __restrict__ thetaT,
@@ -234,58 +240,69 @@ __global__ void __launch_bounds__(BT) k_bwd_lfac(int M, int N, int na, int nb, i
 #pragma unroll
   for (int k = 0; k < MAXE; ++k) {
     const int e = tid + k * BT;
-    if (e < nM) F[((long)g * N + off) * M + e] = acc[k].x;
+    if (e < nM) F[((long)g * N + off) * M + e] += acc[k].x;
   }
 }
 
 size_t bwd_smem(int n, int M) { return (size_t)n * M * 24 + (size_t)n * n * 16 + 16; }
+size_t dphi_smem(int n) { return (size_t)n * 2 * n * 16 + (size_t)n * n * 16 + (size_t)n * 16; }
 
-}  // namespace
-
-// Gradients of sum_z Re(conj(g_z) E_L,z) at the current walkers; any output may be
-// NULL.  gE: W complex, dh1: M x M, dL: X x M x M, dphi: W x M x N complex (device).
-int adjoint_local_energy(afq_ctx* ctx, const double2* gE, double* dh1, double* dL, double2* dphi) {
-  const int M = ctx->M, N = ctx->N, X = ctx->X, W = ctx->ws.W;
-  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
-  if ((long)nmax * M > (long)BT * MAXE)
-    return afq_fail(ctx, AFQ_ERR_ARG, "local-energy backward needs max(na, nb) * M <= 8192");
-  const size_t smem = bwd_smem(nmax, M);
-  if (smem > 220 * 1024) return afq_fail(ctx, AFQ_ERR_ARG, "local-energy backward: shared memory");
-  static size_t configured = 0;
+int configure_bwd(afq_ctx* ctx, size_t smem, size_t sm2) {
+  static size_t configured = 0, configured2 = 0;
   if (smem > configured) {
     AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_gbar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_lfac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = smem;
   }
-  const size_t sm2 = (size_t)nmax * 2 * nmax * 16 + (size_t)nmax * nmax * 16 + (size_t)nmax * 16;
-  static size_t configured2 = 0;
   if (sm2 > configured2) {
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_dphi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_dphi<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_dphi<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_dphi<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     configured2 = sm2;
   }
-  // theta and c of the current walkers, recomputed in FP64 into private buffers so
-  // that the context's own state (and a split-precision trajectory) is untouched
-  WalkerSet t;
-  t.W = W;
-  t.phi = ctx->ws.phi;
+  return AFQ_OK;
+}
+
+int launch_bwd_dphi(afq_ctx* ctx, WalkerSet& t, const double2* gbarT, const double2* gE,
+                    double2* out, int mode) {
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  const size_t sm2 = dphi_smem(nmax);
+  const dim3 grid(t.W, 2);
+  if (mode == 0)
+    k_bwd_dphi<0><<<grid, BT, sm2, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT,
+                                                  t.phi, t.thetaT, gbarT, gE, out);
+  else if (mode == 1)
+    k_bwd_dphi<1><<<grid, BT, sm2, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT,
+                                                  t.phi, t.thetaT, gbarT, gE, out);
+  else
+    k_bwd_dphi<2><<<grid, BT, sm2, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT,
+                                                  t.phi, t.thetaT, gbarT, gE, out);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
+}  // namespace
+
+int adjoint_energy_core(afq_ctx* ctx, WalkerSet& t, const double2* gE, double* dh1, double* F,
+                        double2* out, int mode) {
+  const int M = ctx->M, N = ctx->N, X = ctx->X, W = t.W;
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  if ((long)nmax * M > (long)BT * MAXE)
+    return afq_fail(ctx, AFQ_ERR_ARG, "local-energy backward needs max(na, nb) * M <= 8192");
+  const size_t smem = bwd_smem(nmax, M);
+  if (smem > 220 * 1024) return afq_fail(ctx, AFQ_ERR_ARG, "local-energy backward: shared memory");
+  AFQ_TRY(configure_bwd(ctx, smem, dphi_smem(nmax)));
   double2* buf = nullptr;  // Gbar^T (W x N x M complex), then Theta (N x M reals)
+  if (cudaMalloc((void**)&buf, (size_t)W * N * M * sizeof(double2)) != cudaSuccess)
+    return afq_fail(ctx, AFQ_ERR_NOMEM, "local-energy backward workspace");
   int rc = AFQ_OK;
-  if (cudaMalloc((void**)&buf, (size_t)W * N * M * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&t.thetaT, (size_t)W * N * M * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&t.det, (size_t)W * 2 * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&t.e1, (size_t)W * 2 * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&t.c, (size_t)W * X * sizeof(double2)) != cudaSuccess)
-    rc = afq_fail(ctx, AFQ_ERR_NOMEM, "local-energy backward workspace");
-  if (rc == AFQ_OK) rc = launch_overlap_theta(ctx, t);
-  if (rc == AFQ_OK) rc = launch_force_bias_fp64(ctx, t);
-  if (dphi && rc == AFQ_OK) {
+  if (out) {
     k_bwd_gbar<<<dim3(W, 2), BT, smem, ctx->stream>>>(M, N, ctx->na, ctx->nb, X, ctx->Lt, ctx->ht,
                                                       t.thetaT, t.c, buf);
     ctx->launches++;
-    k_bwd_dphi<<<dim3(W, 2), BT, sm2, ctx->stream>>>(M, N, ctx->na, ctx->nb, ctx->psiT, ctx->ws.phi,
-                                                     t.thetaT, buf, gE, dphi);
-    ctx->launches++;
-    if (cudaGetLastError() != cudaSuccess) rc = afq_fail(ctx, AFQ_ERR_CUDA, "backward dPhi launch");
+    rc = launch_bwd_dphi(ctx, t, buf, gE, out, mode);
+    if (rc == AFQ_OK && cudaGetLastError() != cudaSuccess)
+      rc = afq_fail(ctx, AFQ_ERR_CUDA, "backward dPhi launch");
   }
   if (dh1 && rc == AFQ_OK) {
     double* theta_sum = reinterpret_cast<double*>(buf);  // N x M reals (after the dPhi kernels)
@@ -299,24 +316,54 @@ int adjoint_local_energy(afq_ctx* ctx, const double2* gE, double* dh1, double* d
       rc = launch_dgemm(ctx, M, M, N, 1.0, ctx->psiT, 1, M, 0, theta_sum, M, 1, 0, 0.0, dh1, M, 1, 0,
                         1, 1);
   }
-  double* F = nullptr;
-  if (dL && rc == AFQ_OK) {
-    if (cudaMalloc((void**)&F, (size_t)X * N * M * sizeof(double)) != cudaSuccess)
-      rc = afq_fail(ctx, AFQ_ERR_NOMEM, "backward dL workspace");
-    if (rc == AFQ_OK) {
-      k_bwd_lfac<<<dim3(X, 2), BT, smem, ctx->stream>>>(M, N, ctx->na, ctx->nb, X, W, ctx->Lt,
-                                                        t.thetaT, t.c, gE, F);
-      ctx->launches++;
-      if (cudaGetLastError() != cudaSuccess) rc = afq_fail(ctx, AFQ_ERR_CUDA, "k_bwd_lfac");
-    }
-    // dL_g = Psi (M x N) F_g (N x M), batched over g
-    if (rc == AFQ_OK)
-      rc = launch_dgemm(ctx, M, M, N, 1.0, ctx->psiT, 1, M, 0, F, M, 1, (long)N * M, 0.0, dL, M, 1,
-                        (long)M * M, X, 1);
+  if (F && rc == AFQ_OK) {
+    k_bwd_lfac<<<dim3(X, 2), BT, smem, ctx->stream>>>(M, N, ctx->na, ctx->nb, X, W, ctx->Lt,
+                                                      t.thetaT, t.c, gE, F);
+    ctx->launches++;
+    if (cudaGetLastError() != cudaSuccess) rc = afq_fail(ctx, AFQ_ERR_CUDA, "k_bwd_lfac");
   }
-  // the workspaces are released only after the kernels that read them are done
+  // the workspace is released only after the kernels that read it are done
   cudaStreamSynchronize(ctx->stream);
   cudaFree(buf);
+  return rc;
+}
+
+// lambda_in += (I - Psi theta^T) lambda_theta S^-T for every walker (lamT: W x N x M,
+// the cotangent of theta stored transposed like thetaT).
+int launch_bwd_theta(afq_ctx* ctx, WalkerSet& t, const double2* lamT, double2* lam) {
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  AFQ_TRY(configure_bwd(ctx, bwd_smem(nmax, ctx->M), dphi_smem(nmax)));
+  return launch_bwd_dphi(ctx, t, lamT, nullptr, lam, 2);
+}
+
+// Gradients of sum_z Re(conj(g_z) E_L,z) at the current walkers; any output may be
+// NULL.  gE: W complex, dh1: M x M, dL: X x M x M, dphi: W x M x N complex (device).
+int adjoint_local_energy(afq_ctx* ctx, const double2* gE, double* dh1, double* dL, double2* dphi) {
+  const int M = ctx->M, N = ctx->N, X = ctx->X, W = ctx->ws.W;
+  // theta and c of the current walkers, recomputed in FP64 into private buffers so
+  // that the context's own state (and a split-precision trajectory) is untouched
+  WalkerSet t;
+  t.W = W;
+  t.phi = ctx->ws.phi;
+  double* F = nullptr;
+  int rc = AFQ_OK;
+  if (cudaMalloc((void**)&t.thetaT, (size_t)W * N * M * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&t.det, (size_t)W * 2 * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&t.e1, (size_t)W * 2 * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&t.c, (size_t)W * X * sizeof(double2)) != cudaSuccess ||
+      (dL && cudaMalloc((void**)&F, (size_t)X * N * M * sizeof(double)) != cudaSuccess))
+    rc = afq_fail(ctx, AFQ_ERR_NOMEM, "local-energy backward workspace");
+  if (rc == AFQ_OK) rc = launch_overlap_theta(ctx, t);
+  if (rc == AFQ_OK) rc = launch_force_bias_fp64(ctx, t);
+  if (rc == AFQ_OK && F &&
+      cudaMemsetAsync(F, 0, (size_t)X * N * M * sizeof(double), ctx->stream) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "backward dL workspace");
+  if (rc == AFQ_OK) rc = adjoint_energy_core(ctx, t, gE, dh1, F, dphi, 0);
+  // dL_g = Psi (M x N) F_g (N x M), batched over g
+  if (rc == AFQ_OK && dL)
+    rc = launch_dgemm(ctx, M, M, N, 1.0, ctx->psiT, 1, M, 0, F, M, 1, (long)N * M, 0.0, dL, M, 1,
+                      (long)M * M, X, 1);
+  cudaStreamSynchronize(ctx->stream);
   cudaFree(t.thetaT);
   cudaFree(t.det);
   cudaFree(t.e1);
