@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the split-precision legs")
     ap.add_argument("--mixed-steps", type=int, default=20)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     return ap.parse_args()
 
 
@@ -306,6 +307,52 @@ def batched_leg(rank: int, replays: int = 8, precision: str = "split_bf16") -> d
             "autotuned_tiles": tiles}
 
 
+def adjoint_leg(rank: int, K: int = 20) -> dict:
+    """Adjoint on 150 orbitals, 15+15 electrons, 750 Cholesky vectors, 256 walkers:
+    the local-energy backward, and a K-step chain (QR every 5 steps, Philox fields)
+    forward with its checkpoint tape plus the recomputing backward."""
+    import torch
+    from paper_2209_04015_b300 import AfqContext
+    from paper_2209_04015_b300.synthetic import make_config, perturbed_walkers
+
+    s, c = make_config("c5", seed=1 + rank)
+    W = c["W"]
+    ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank)
+    ctx.init_hamiltonian(s.h1, s.L, s.e0)
+    ctx.init_trial(s.psi_a, s.psi_b)
+    ctx.init_walkers(W, perturbed_walkers(s, W, eps=0.3, seed=9 + rank))
+    dev = torch.device("cuda")
+    g = torch.ones(W, dtype=torch.complex128, device=dev)
+    e = torch.empty((W, 4), dtype=torch.complex128, device=dev)
+    dh1 = torch.empty((s.M, s.M), dtype=torch.float64, device=dev)
+    dL = torch.empty((s.X, s.M, s.M), dtype=torch.float64, device=dev)
+    dphi = torch.empty((W, s.M, s.na + s.nb), dtype=torch.complex128, device=dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    e_fwd = timed(lambda: ctx.local_energy_dev(e.data_ptr(), None), 5)
+    e_bwd = timed(lambda: ctx.local_energy_backward_dev(g.data_ptr(), dh1.data_ptr(),
+                                                        dL.data_ptr(), dphi.data_ptr()), 3)
+    fwd = timed(lambda: ctx.chain_forward_dev(K, None, e.data_ptr()), 2)
+    bwd = timed(lambda: ctx.chain_backward_dev(g.data_ptr(), dh1.data_ptr(), dL.data_ptr(),
+                                               dphi.data_ptr()), 2)
+    ctx.close()
+    return {"workload": f"150 orbitals, 15a+15b electrons, 750 Cholesky vectors, {W} walkers, "
+                        f"{K}-step chain, QR every 5 steps, FP64",
+            "local_energy_ms": e_fwd * 1e3, "local_energy_backward_ms": e_bwd * 1e3,
+            "chain_forward_ms": fwd * 1e3, "chain_backward_ms": bwd * 1e3,
+            "backward_over_forward": bwd / fwd,
+            "value": W * K / (fwd + bwd), "unit": "walker-steps/s (chain forward + backward)",
+            "timing": "host wall clock around synchronised calls (device buffers)"}
+
+
 # ----------------------------------------------------------------------------- arms
 
 def run_reference(args):
@@ -466,6 +513,8 @@ def run_afq(args):
         line["mixed"]["same_workload"]["speedup_vs_fp64"] = (
             line["mixed"]["same_workload"]["value"] / (value / world))
         line["batched"] = batched_leg(rank)
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_leg(rank)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
