@@ -60,6 +60,12 @@ def parse_args():
     ap.add_argument("--no-mixed", action="store_true", help="skip the split-precision legs")
     ap.add_argument("--mixed-steps", type=int, default=20)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
+    ap.add_argument("--profile-leg", choices=["mixed-c2", "mixed-c3", "batched", "adjoint"],
+                    default=None, help="run one secondary leg alone and print its JSON (for ncu)")
+    ap.add_argument("--profile-walkers", type=int, default=0,
+                    help="walker count of a --profile-leg mixed leg (0: the workload's)")
+    ap.add_argument("--error-steps", type=int, default=100,
+                    help="steps of the split-precision drift check")
     return ap.parse_args()
 
 
@@ -173,7 +179,8 @@ def cpu_baseline(seconds: float, W_sample: int = 8) -> dict:
 
 
 def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int = 16,
-              long_steps: int = 100) -> dict:
+              long_steps: int = 100, walkers: int = 0) -> dict:
+    long_steps = max(long_steps, 1)
     """Split-precision (tcgen05) throughput on one workload, and its |dE_L| against
     the FP64 path on the first walkers after 1 and after long_steps steps.  Walkers
     are independent and the Philox counters are keyed by walker index, so an FP64
@@ -183,7 +190,8 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
     from paper_2209_04015_b300.synthetic import make_config
 
     s, c = make_config(name, seed=1 + rank)
-    W, X, M, na, nb = c["W"], s.X, s.M, s.na, s.nb
+    W, X, M, na, nb = walkers or c["W"], s.X, s.M, s.na, s.nb
+    check_walkers = min(check_walkers, W)
     stream = torch.cuda.current_stream()
 
     def context(precision, nw):
@@ -398,6 +406,21 @@ def run_reference(args):
     return 0
 
 
+def run_leg(args) -> int:
+    import torch
+    torch.cuda.set_device(0)
+    leg = args.profile_leg
+    if leg.startswith("mixed"):
+        out = mixed_leg(leg.split("-")[1], args.mixed_steps, args.warmup, 0,
+                        long_steps=args.error_steps, walkers=args.profile_walkers)
+    elif leg == "batched":
+        out = batched_leg(0)
+    else:
+        out = adjoint_leg(0)
+    print(json.dumps({"leg": leg, **out}), flush=True)
+    return 0
+
+
 def run_afq(args):
     import torch
     rank, world, local = dist_info()
@@ -508,8 +531,9 @@ def run_afq(args):
     }
     if not args.no_mixed:
         line["mixed"] = {"same_workload": mixed_leg(WORKLOAD, args.mixed_steps * 5, args.warmup,
-                                                    rank),
-                         "large_shape": mixed_leg("c3", args.mixed_steps, args.warmup, rank)}
+                                                    rank, long_steps=args.error_steps),
+                         "large_shape": mixed_leg("c3", args.mixed_steps, args.warmup, rank,
+                                                  long_steps=args.error_steps)}
         line["mixed"]["same_workload"]["speedup_vs_fp64"] = (
             line["mixed"]["same_workload"]["value"] / (value / world))
         line["batched"] = batched_leg(rank)
@@ -528,6 +552,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_leg:
+        return run_leg(args)
     return run_afq(args)
 
 

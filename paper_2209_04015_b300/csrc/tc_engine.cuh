@@ -82,9 +82,10 @@ __device__ __forceinline__ void issue_pairs(uint32_t acc, uint32_t sa, uint32_t 
 }
 
 // Exact-diagonal form: pair (s, d - s) goes to accumulator d (acc0 + d * stride
-// columns).  With integer slices (split_exact) every accumulator holds an integer
-// sum below 2^24, so the FP32 accumulation is exact and the diagonals are combined
-// in FP64 afterwards.
+// columns).  With integer slices (split_exact) every accumulator holds a sum of
+// integer products, exact in FP32 while its magnitude stays below 2^24 (balanced
+// random-sign digits keep typical sums far below; a larger sum is rounded like any
+// FP32 sum of that diagonal), and the diagonals are combined in FP64 afterwards.
 template <int S>
 __device__ __forceinline__ void issue_diagonals(uint32_t acc0, uint32_t stride, uint32_t sa,
                                                 uint32_t sb, uint32_t bslot, int ua, int ub,
