@@ -110,77 +110,6 @@ struct FbP {
 };
 
 // ---------------------------------------------------------------------------
-// Policy: exchange for one spin.  A tile rows (g, i): G Cholesky indices x n
-// orbitals of L~ (4D map {Mpad, N, X, S}, box {32, n, G, 1}); B tile rows
-// (z, re/im, j): zb walkers of theta (4D map {Mpad, N, 2W, S}, box {32, n, 2 zb, 1});
-// K = Mpad.  The 128 x BN accumulator holds T^{g z}_ij for every (g, z) pair of
-// the tile; the epilogue stages it in shared memory and forms sum_ij T_ij T_ji.
-// ---------------------------------------------------------------------------
-struct ExP {
-  struct Args {
-    TcCommon c;
-    int n, off, G, zb, X, W, spin, ex_groups;
-    double2* ekp;
-  };
-  static constexpr int kUA = 1, kUB = 1;
-  template <int S>
-  static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
-                               uint32_t bslot, bool first) {
-    issue_pairs<S>(tmem, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN), first);
-  }
-  struct Tile {
-    int gt, g0, z0, kb0, kb1;
-  };
-  static __device__ Tile tile(const Args& a) {
-    return Tile{(int)blockIdx.x, (int)blockIdx.x * a.G, (int)blockIdx.y * a.zb, 0, a.c.nkb};
-  }
-  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args& a, const Tile& t,
-                                int, int s, int kb, uint64_t* bar) {
-    tc::tma_load_4d(dst, tm, kb * kBK, a.off, t.g0, s, bar);
-  }
-  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args& a, const Tile& t,
-                                int, int s, int kb, uint64_t* bar) {
-    tc::tma_load_4d(dst, tm, kb * kBK, a.off, 2 * t.z0, s, bar);
-  }
-  template <int S>
-  static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t* smem,
-                                  int warp, int lane) {
-    const int n = a.n, BN = a.c.BN, pitch = BN + 1;
-    float* Ts = reinterpret_cast<float*>(smem);
-    const int r = warp * 32 + lane;
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      float v[16];
-      tmem_row16(tmem, warp, c0, v);
-      if (r < a.G * n)
-#pragma unroll
-        for (int j = 0; j < 16; ++j) Ts[r * pitch + c0 + j] = v[j];
-    }
-    __syncthreads();
-    const int gc = min(a.G, a.X - t.g0), nn = n * n;
-    for (int zl = warp; zl < a.zb; zl += 4) {
-      const int z = t.z0 + zl;
-      const int cb = zl * 2 * n;
-      float sr = 0.f, si = 0.f;
-      for (int e = lane; e < gc * nn; e += 32) {
-        const int gl = e / nn, ij = e % nn, i = ij / n, j = ij % n;
-        const float* ri = Ts + (gl * n + i) * pitch + cb;
-        const float* rj = Ts + (gl * n + j) * pitch + cb;
-        const float ar = ri[j], ai = ri[n + j], br = rj[i], bi = rj[n + i];
-        sr = fmaf(ar, br, fmaf(-ai, bi, sr));
-        si = fmaf(ar, bi, fmaf(ai, br, si));
-      }
-      double dr = sr, di = si;
-      for (int o = 16; o > 0; o >>= 1) {
-        dr += __shfl_down_sync(0xffffffffu, dr, o);
-        di += __shfl_down_sync(0xffffffffu, di, o);
-      }
-      if (lane == 0 && z < a.W)
-        a.ekp[((long)z * 2 + a.spin) * a.ex_groups + t.gt] = make_double2(-0.5 * dr, -0.5 * di);
-    }
-  }
-};
-
-// ---------------------------------------------------------------------------
 // slicing kernels: FP64 -> S bfloat16 planes
 // ---------------------------------------------------------------------------
 // in: rows x K (row pitch ld); out: S planes of rows x Kp, zero for k >= K
@@ -410,39 +339,6 @@ int launch_force_bias_tc(afq_ctx* ctx, WalkerSet& s) {
   k_fb_reduce<<<grid1d((long)s.W * ctx->X), 256, 0, ctx->stream>>>(ctx->X, s.W, ctx->fb_ksplit,
                                                                    ctx->fb_part, s.c);
   AFQ_LAUNCHED(ctx);
-  return AFQ_OK;
-}
-
-int launch_exchange_tc(afq_ctx* ctx, WalkerSet& s) {
-  for (int spin = 0; spin < 2; ++spin) {
-    const int n = spin ? ctx->nb : ctx->na;
-    if (n == 0) continue;
-    ExP::Args a{};
-    a.c.nkb = ctx->Mpad / kBK;
-    a.c.BN = ctx->ex_BN[spin];
-    a.n = n;
-    a.off = spin ? ctx->na : 0;
-    a.G = ctx->ex_G[spin];
-    a.zb = ctx->ex_zb[spin];
-    a.c.tx_bytes = (uint32_t)ctx->S * (kBK * n * a.G * 2 + kBK * n * 2 * a.zb * 2);
-    a.c.tmem_cols = tmem_cols_for(a.c.BN);
-    a.c.err = ctx->flags + 2;
-    a.X = ctx->X;
-    a.W = s.W;
-    a.spin = spin;
-    a.ex_groups = ctx->ex_groups;
-    a.ekp = s.ekp;
-    const int ngt = (ctx->X + a.G - 1) / a.G;
-    if (ngt > ctx->ex_groups) return afq_fail(ctx, AFQ_ERR_STATE, "exchange tiles exceed slots");
-    dim3 grid(ngt, (s.W + a.zb - 1) / a.zb);
-    size_t smem = 0;
-    plan_smem(ctx->S, 1, 1, a.c.BN, (size_t)128 * (a.c.BN + 1) * 4, &a.c.stages, &smem);
-    cudaError_t e = launch_tc_s<ExP>(ctx->S, grid, smem, ctx->stream, ctx->tm_ex_a[spin],
-                                     ctx->tm_ex_b[spin], a);
-    ctx->launches++;
-    if (e != cudaSuccess)
-      return afq_fail(ctx, AFQ_ERR_CUDA, std::string("exchange tc: ") + cudaGetErrorString(e));
-  }
   return AFQ_OK;
 }
 
