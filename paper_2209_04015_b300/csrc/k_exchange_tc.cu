@@ -5,7 +5,8 @@
 // The GEMM: A rows (g, i) are G Cholesky indices x n orbitals of L~ (K = Mpad), B rows
 // (z, re/im, j) are zb walkers of theta; one 128 x BN accumulator holds T^{gz} for every
 // (g, z) pair of a tile, and T is never written to HBM.  Each CTA stays resident and
-// walks tiles g fastest (so resident CTAs share a walker block in L2):
+// walks the tiles in chunks of walker blocks whose theta stays in L2, g-tile major
+// inside a chunk (so resident CTAs share each L~ g-tile):
 //   warp 0   TMA producer: the S slices of the A and B units of every K block into a
 //            ring of stages;
 //   warp 1   MMA issuer: the float-split slice products into one of two TMEM
@@ -33,11 +34,21 @@ struct ExArgs {
   // tiles [0, ntiles) cover spin `spin` and, when nspin = 2 (equal spins), spin + 1 with
   // the same maps at column offset `off2`; zc walkers are staged per epilogue round
   int n, off, off2, nspin, G, zb, zc, BN, bstride, X, W, spin, ex_groups, nkb, stages, ngt,
-      tiles_per_spin, ntiles, pitch;
+      nzt, zchunk, tiles_per_spin, ntiles, pitch;
   uint32_t tx_bytes, tmem_cols;
   double2* ekp;
   int* err;
 };
+
+// Tile order within a spin: walker blocks in chunks of zchunk (whose theta stays in
+// L2), and inside a chunk g-tile major, so that resident CTAs share each L~ g-tile.
+__device__ __forceinline__ void tile_coords(const ExArgs& a, int tl, int* gt, int* zt) {
+  const int per = a.ngt * a.zchunk;
+  const int c = tl / per, r = tl - c * per;
+  const int zn = min(a.zchunk, a.nzt - c * a.zchunk);
+  *gt = r / zn;
+  *zt = c * a.zchunk + (r - *gt * zn);
+}
 
 __device__ __forceinline__ void epi_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
@@ -98,8 +109,10 @@ __global__ void __launch_bounds__(kExThreads, 1)
       int it = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-        const int sp = tile / a.tiles_per_spin, tl = tile % a.tiles_per_spin;
-        const int g0 = (tl % a.ngt) * a.G, z0 = (tl / a.ngt) * a.zb;
+        const int sp = tile / a.tiles_per_spin;
+        int gt, zt;
+        tile_coords(a, tile % a.tiles_per_spin, &gt, &zt);
+        const int g0 = gt * a.G, z0 = zt * a.zb;
         const int off = sp ? a.off2 : a.off;
         for (int kb = 0; kb < a.nkb; ++kb, ++it) {
           const int st = it % nst;
@@ -169,8 +182,10 @@ __global__ void __launch_bounds__(kExThreads, 1)
       epi_sync();
       if (!ep_ok) break;
       tc::fence_after_sync();
-      const int sp = tile / a.tiles_per_spin, tl = tile % a.tiles_per_spin;
-      const int gt = tl % a.ngt, g0 = gt * a.G, z0 = (tl / a.ngt) * a.zb;
+      const int sp = tile / a.tiles_per_spin;
+      int gt, zt;
+      tile_coords(a, tile % a.tiles_per_spin, &gt, &zt);
+      const int g0 = gt * a.G, z0 = zt * a.zb;
       const int gc = min(a.G, a.X - g0);
       const int nblk = gc > q ? (gc - q + kEpiWarps - 1) / kEpiWarps : 0;  // this warp's g-blocks
       const uint32_t acc = tmem + (uint32_t)(buf * a.bstride) + ((uint32_t)(32 * lq) << 16);
@@ -292,7 +307,14 @@ int launch_exchange_tc(afq_ctx* ctx, WalkerSet& s) {
     a.err = ctx->flags + 2;
     a.nkb = ctx->Mpad / kBK;
     a.ngt = (ctx->X + a.G - 1) / a.G;
-    a.tiles_per_spin = a.ngt * ((s.W + a.zb - 1) / a.zb);
+    a.nzt = (s.W + a.zb - 1) / a.zb;
+    a.tiles_per_spin = a.ngt * a.nzt;
+    {
+      // walker blocks per chunk: their theta slices within ~24 MB of L2
+      const long bblock = (long)ctx->S * 2 * n * a.zb * ctx->Mpad * 2;
+      long zc = (24L << 20) / (bblock > 0 ? bblock : 1);
+      a.zchunk = (int)(zc < 1 ? 1 : (zc > a.nzt ? a.nzt : zc));
+    }
     a.ntiles = a.tiles_per_spin * a.nspin;
     // walkers staged per epilogue round: 128 rows x (zc 2n + 1) floats within 32 KB
     a.zc = (8192 / 128 - 1) / (2 * n);

@@ -13,9 +13,10 @@
 // row scales and the recombination run on the integer pipe (tc_engine.cuh): B300's
 // FP64 pipe would otherwise dominate these memory-bound passes.
 //
-// VHS: D[(p,q)][(z, re/im)] = sum_g L_g,pq y_zg, A operand the unpacked Cholesky
-// tensor (rows (p, q), K = g); the epilogue writes V_z in FP64 (the factor i sqrt(dt)
-// of A_z is applied with 1/k in the Taylor epilogue).
+// VHS: D[(p,q)][(z, re/im)] = sum_g L_g,pq y_zg, A operand the Cholesky tensor over
+// its packed upper triangle (rows (p <= q), K = g: half the MMAs of the dense form);
+// the epilogue writes V_z in FP64 to both triangles (the factor i sqrt(dt) of
+// A_z is applied with 1/k in the Taylor epilogue).
 // Taylor terms and one-body halves: per walker, 128-row tile of p and 64-column
 // tile of j, Re and Im accumulators of A T (A M x M, T M x N as K-major T^T rows
 // j), four MMA streams per slice pair with the negate-A bit for -Im A Im T.  The
@@ -35,10 +36,11 @@ constexpr int kPropBN = 64;  // columns j per tile of the propagation GEMMs
 struct VhsP {
   struct Args {
     TcCommon c;
-    int M, W;
-    const int* ea;  // row exponents of L^T, per (p, q)
-    const int* eb;  // row exponents of y, per (z, re/im)
-    double2* V;     // W x M x M: V_z = sum_g y_zg L_g, FP64
+    int M, W, Mp;
+    const int2* tpq;  // packed row t -> (p, q), p <= q
+    const int* ea;    // row exponents of L^T, per packed (p, q)
+    const int* eb;    // row exponents of y, per (z, re/im)
+    double2* V;       // W x M x M: V_z = sum_g y_zg L_g, FP64, both triangles
   };
   struct Tile {
     int r0, n0, kb0, kb1;
@@ -66,8 +68,10 @@ struct VhsP {
                                   int lane) {
     const long MM = (long)a.M * a.M;
     const long row = (long)t.r0 + warp * 32 + lane;
-    const bool valid = row < MM;
+    const bool valid = row < a.Mp;
     const int er = valid ? a.ea[row] : 0;
+    const int2 pq = valid ? a.tpq[row] : make_int2(0, 0);
+    const long e_pq = (long)pq.x * a.M + pq.y, e_qp = (long)pq.y * a.M + pq.x;
     for (int c0 = 0; c0 < a.c.BN; c0 += 16) {
       float f[S][16];
 #pragma unroll
@@ -83,8 +87,10 @@ struct VhsP {
           ar[d] = f[d][jj];
           ai[d] = f[d][jj + 1];
         }
-        a.V[(long)z * MM + row] = make_double2(combine_exact<S>(ar, er + a.eb[col] - 14),
-                                               combine_exact<S>(ai, er + a.eb[col + 1] - 14));
+        const double2 v = make_double2(combine_exact<S>(ar, er + a.eb[col] - 14),
+                                       combine_exact<S>(ai, er + a.eb[col + 1] - 14));
+        a.V[(long)z * MM + e_pq] = v;
+        if (e_qp != e_pq) a.V[(long)z * MM + e_qp] = v;
       }
     }
   }
@@ -251,33 +257,42 @@ __global__ void k_transpose_phi(const double2* __restrict__ phi, int W, int M, i
 }
 
 // exponent of each (p, q) row of L^T: max over g of |L_g,pq|
-__global__ void k_lt_exponents(const double* __restrict__ L, int X, long MM, int* __restrict__ e) {
-  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < MM;
+// Row exponents of L^T over the packed upper triangle (rows t -> (p, q), p <= q).
+__global__ void k_lt_exponents(const double* __restrict__ L, int X, int M, long Mp,
+                               const int2* __restrict__ tpq, int* __restrict__ e) {
+  const long MM = (long)M * M;
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < Mp;
        r += (long)gridDim.x * blockDim.x) {
+    const int2 pq = tpq[r];
+    const long o = (long)pq.x * M + pq.y;
     int m = 0;
-    for (int g = 0; g < X; ++g) m = max(m, exp_field(L[(long)g * MM + r]));
+    for (int g = 0; g < X; ++g) m = max(m, exp_field(L[(long)g * MM + o]));
     e[r] = row_exponent_field(m);
   }
 }
 
-// L (X x M x M) -> planes [(p, q)][Xpad] of integer digits: 32 x 32 tile transpose
-__global__ void k_slice_LT(const double* __restrict__ L, int X, long MM, int Xpad, int S,
-                           const int* __restrict__ e, __nv_bfloat16* __restrict__ out) {
+// L (X x M x M) -> planes [t][Xpad] of integer digits over the packed upper triangle
+// (t -> (p, q), p <= q): 32 x 32 tile transpose
+__global__ void k_slice_LT(const double* __restrict__ L, int X, int M, long Mp, int Xpad, int S,
+                           const int2* __restrict__ tpq, const int* __restrict__ e,
+                           __nv_bfloat16* __restrict__ out) {
   __shared__ double tileb[32][33];
+  const long MM = (long)M * M;
   const long r0 = (long)blockIdx.x * 32;
   const int g0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const long r = r0 + tx;
+  const int2 pq = r < Mp ? tpq[r] : make_int2(0, 0);
   for (int k = ty; k < 32; k += 8) {
     const int g = g0 + k;
-    const long r = r0 + tx;
-    tileb[k][tx] = (g < X && r < MM) ? L[(long)g * MM + r] : 0.0;
+    tileb[k][tx] = (g < X && r < Mp) ? L[(long)g * MM + (long)pq.x * M + pq.y] : 0.0;
   }
   __syncthreads();
-  const long plane = MM * Xpad;
+  const long plane = Mp * Xpad;
   for (int k = ty; k < 32; k += 8) {
-    const long r = r0 + k;
+    const long rr = r0 + k;
     const int g = g0 + tx;
-    if (r < MM && g < Xpad) split_exact(tileb[tx][k], e[r], S, out + r * Xpad + g, plane);
+    if (rr < Mp && g < Xpad) split_exact(tileb[tx][k], e[rr], S, out + rr * Xpad + g, plane);
   }
 }
 
@@ -327,17 +342,17 @@ void mixed_prop_free(afq_ctx* ctx) {
 // Once per trial: digits of L^T (the VHS operand) and of P - I, with row exponents.
 int mixed_prop_init_trial(afq_ctx* ctx) {
   const int S = ctx->Sp, M = ctx->M, X = ctx->X;
-  const long MM = (long)M * M;
   ctx->Xpad = round_up(X, kBK);
-  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->LT_sl, (size_t)S * MM * ctx->Xpad * 2));
+  const long Mp = ctx->Mp;  // packed upper-triangle rows of L^T
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->LT_sl, (size_t)S * Mp * ctx->Xpad * 2));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->Pm_sl, (size_t)S * M * ctx->Mpad * 2));
-  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_lt, (size_t)MM * sizeof(int)));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_lt, (size_t)Mp * sizeof(int)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_pm, (size_t)M * sizeof(int)));
-  k_lt_exponents<<<grid1d(MM), 256, 0, ctx->stream>>>(ctx->L, X, MM, ctx->e_lt);
+  k_lt_exponents<<<grid1d(Mp), 256, 0, ctx->stream>>>(ctx->L, X, M, Mp, ctx->tpq, ctx->e_lt);
   AFQ_LAUNCHED(ctx);
-  dim3 g((unsigned)((MM + 31) / 32), (unsigned)((ctx->Xpad + 31) / 32));
-  k_slice_LT<<<g, dim3(32, 8), 0, ctx->stream>>>(ctx->L, X, MM, ctx->Xpad, S, ctx->e_lt,
-                                                 ctx->LT_sl);
+  dim3 g((unsigned)((Mp + 31) / 32), (unsigned)((ctx->Xpad + 31) / 32));
+  k_slice_LT<<<g, dim3(32, 8), 0, ctx->stream>>>(ctx->L, X, M, Mp, ctx->Xpad, S, ctx->tpq,
+                                                 ctx->e_lt, ctx->LT_sl);
   AFQ_LAUNCHED(ctx);
   k_slice_pm<<<warp_grid(M), 256, 0, ctx->stream>>>(ctx->P, M, ctx->Mpad, S, ctx->Pm_sl, ctx->e_pm);
   AFQ_LAUNCHED(ctx);
@@ -347,7 +362,6 @@ int mixed_prop_init_trial(afq_ctx* ctx) {
 // Per walker set: operand buffers and tensor maps of the propagation.
 int mixed_prop_init_walkers(afq_ctx* ctx) {
   const int S = ctx->Sp, M = ctx->M, N = ctx->N, W = ctx->ws.W, Mp = ctx->Mpad;
-  const long MM = (long)M * M;
   for (auto** p : {&ctx->y_sl, &ctx->A_sl, &ctx->T_sl[0], &ctx->T_sl[1]})
     if (*p) {
       cudaFree(*p);
@@ -380,7 +394,7 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
   const uint32_t brows = (uint32_t)(N >= kPropBN ? kPropBN : N);
   bool ok = true;
   {
-    const uint64_t da[3] = {(uint64_t)ctx->Xpad, (uint64_t)MM, (uint64_t)S};
+    const uint64_t da[3] = {(uint64_t)ctx->Xpad, (uint64_t)ctx->Mp, (uint64_t)S};
     const uint32_t ba[3] = {kBK, 128, 1};
     const uint64_t db[3] = {(uint64_t)ctx->Xpad, (uint64_t)(2 * W), (uint64_t)S};
     const uint32_t bb[3] = {kBK, (uint32_t)ctx->vhs_BN, 1};
@@ -418,12 +432,14 @@ int launch_vhs_tc(afq_ctx* ctx) {
   a.c.err = ctx->flags + 2;
   a.M = M;
   a.W = W;
+  a.Mp = ctx->Mp;
+  a.tpq = ctx->tpq;
   a.ea = ctx->e_lt;
   a.eb = ctx->e_y;
   a.V = ctx->A;
   size_t smem = 0;
   plan_smem(S, 1, 1, a.c.BN, 0, &a.c.stages, &smem);
-  dim3 grid((2 * W + a.c.BN - 1) / a.c.BN, (unsigned)(((long)M * M + 127) / 128));
+  dim3 grid((2 * W + a.c.BN - 1) / a.c.BN, (unsigned)(((long)ctx->Mp + 127) / 128));
   cudaError_t e = launch_tc_s<VhsP>(S, grid, smem, ctx->stream, ctx->tm_vhs_a, ctx->tm_vhs_b, a);
   ctx->launches++;
   if (e != cudaSuccess) return afq_fail(ctx, AFQ_ERR_CUDA, std::string("vhs tc: ") + cudaGetErrorString(e));
