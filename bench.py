@@ -37,6 +37,10 @@ WORKLOAD_TEXT = ("ph-AFQMC step + E_loc, 100 orbitals, 10a+10b electrons, 400 Ch
                  "vectors (geometric norm decay), 128 complex128 walkers, dt 0.005, QR every "
                  "5 steps, Philox fields")
 FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 nominal: 148 SMs x 2032 MHz x ~4.15 flop/clk/SM
+# DRAM bytes (read + write) per launch of the dominant kernel, from one-pass ncu
+# captures of these exact workloads (profiles/exchange_fp64_c2.md,
+# profiles/exchange_tc_c3.md); None where no capture of the current kernel exists.
+TRAFFIC = {("fp64", "c2"): 10565888 + 0, ("split_bf16", "c3"): 574247168 + 10140928}
 SPLIT_PRODUCTS = 6          # bf16 slice products of the 3-slice exchange (s + t <= 2)
 
 
@@ -252,9 +256,10 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
            "gpu_launches": mix.launch_count() - n0,
            "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]}
                        for k, v in prof.items() if v[1]},
-           "roofline": {"bound": "tensor", "kernel": "exchange (k_tc_split<ExP>)",
+           "roofline": {"bound": "tensor", "kernel": "exchange (k_exchange_tc, persistent)",
                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak,
+                        "traffic": TRAFFIC.get(("split_bf16", name)) if W == c["W"] else None,
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
                         "flops_per_launch": bf16_flops,
                         "flops_note": f"{SPLIT_PRODUCTS} bf16 slice products x the exchange's "
@@ -517,9 +522,10 @@ def run_afq(args):
                    "X": X, "W_per_gpu": W, "dt": 0.005, "qr_period": 5, "precision": "fp64",
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MB write, outside the step events)"},
-        "roofline": {"bound": "alu", "kernel": "exchange", "achieved": ex_achieved,
+        "roofline": {"bound": "alu", "kernel": "exchange (k_exchange_fp64)", "achieved": ex_achieved,
                      "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ex_achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "frac": ex_achieved / FP64_NOMINAL_TFLOPS,
+                     "traffic": TRAFFIC.get(("fp64", WORKLOAD)) if W == 128 else None,
                      "peak_source": "FP64 nominal (148 SMs x 2032 MHz x 4.15 flop/clk/SM)",
                      "flops_per_launch": exchange_flops(W, X, M, na, nb),
                      "avg_launch_ms": ex_avg_s * 1e3},
