@@ -135,12 +135,12 @@ struct afq_ctx {
   int ex_G[2] = {0, 0}, ex_zb[2] = {0, 0}, ex_BN[2] = {0, 0};
   CUtensorMap tm_fb_a, tm_fb_b, tm_ex_a[2], tm_ex_b[2];
   // split-precision propagation operands (k_mixed_prop.cu)
-  int Xpad = 0, vhs_BN = 0, prop_BN = 0;
+  int Xpad = 0, vhs_BN = 0, prop_rows = 0;  // prop_rows: walker columns per propagation tile
   __nv_bfloat16* LT_sl = nullptr;     // S x M^2 x Xpad: L^T, the VHS operand
   __nv_bfloat16* Pm_sl = nullptr;     // S x M x Mpad: P - I
   __nv_bfloat16* y_sl = nullptr;      // S x 2W x Xpad: shifted fields (re, im rows)
   __nv_bfloat16* A_sl = nullptr;      // S x 2W x M x Mpad: i sqrt(dt) V (re, im planes)
-  __nv_bfloat16* T_sl[2] = {nullptr, nullptr};  // S x 2W x N x Mpad: Taylor operands
+  __nv_bfloat16* T_sl[2] = {nullptr, nullptr};  // S x 2W x N x Mpad: Taylor operands [Re; Im]
   double2* accT = nullptr;            // W x N x M FP64 accumulator of the propagated walker
   double2* tout = nullptr;            // W x N x M FP64 operand between propagation launches
   int *e_lt = nullptr, *e_pm = nullptr, *e_y = nullptr, *e_a = nullptr;  // row exponents

@@ -28,7 +28,7 @@ using namespace tce;
 
 namespace {
 
-constexpr int kPropBN = 64;  // columns j per tile of the propagation GEMMs
+constexpr int kPropRows = 64;  // walker columns j per propagation tile (x2: re and im)
 
 // ---------------------------------------------------------------------------
 // VHS policy
@@ -97,102 +97,232 @@ struct VhsP {
 };
 
 // ---------------------------------------------------------------------------
-// Complex (or real-A) times complex policy
+// Taylor terms and one-body halves: a persistent kernel per GEMM pass
 // ---------------------------------------------------------------------------
+// Tile: rows p (128) x columns (re | im, j) (2 brows, brows a multiple of 16), for one
+// walker.  With B = [Re T; Im T] (one operand tile, K = q) the complex product
+// D = A T is, per K block,
+//   D[:, re|im] += Re A B                   (N = 2 brows)
+//   D[:, re]    += -Im A (Im T rows of B)   (N = brows, negate-A)
+//   D[:, im]    +=  Im A (Re T rows of B)   (N = brows)
+// (real A = P - I: the first product only).  Exact digit diagonals accumulate in S
+// TMEM regions of BN columns; each epilogue thread recombines a real column and its
+// imaginary partner brows columns later and writes whole complex FP64 values.
+// Roles: warp 0 TMA, warp 1 MMA (and TMEM), warps 2-9 epilogue (two per TMEM lane
+// quarter, splitting the column chunks); the producer runs ahead across tiles while
+// the epilogue drains TMEM.
 enum { kModeFirst = 0, kModeTerm = 1, kModeLast = 2 };
+constexpr int kPropWarps = 10;
+constexpr int kPropEpi = 8;
 
-template <bool REAL>
-struct CplxP {
-  struct Args {
-    TcCommon c;
-    int M, N, W, mode, acc_out;
-    double coef;            // term k: sqrt(dt) / k (A = i sqrt(dt) V)
-    const int* ea;          // row exponents of A: P - I per p, or V_z per (z, p)
-    const int* eb;          // row exponents of T^T per (z, j)
-    const double2* phi_in;  // mode first: Phi (W x M x N)
-    double2* accT;          // W x N x M FP64 accumulator of P T_n(A) P Phi, transposed
-    double2* phi_out;       // mode last: Phi (W x M x N)
-    double2* tout;          // W x N x M FP64: the next operand (sliced by the next kernel)
-  };
-  struct Tile {
-    int p0, z, n0, kb0, kb1;
-  };
-  static constexpr int kUA = REAL ? 1 : 2, kUB = 2;
-  template <int S>
-  static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
-                               uint32_t bslot, bool first) {
-    const int BN = a.c.BN;
-    const uint32_t id = tc::idesc_bf16(128, BN), idn = tc::idesc_bf16(128, BN, true);
-    const uint32_t acc_re = tmem, acc_im = tmem + (uint32_t)(S * BN);
-    issue_diagonals<S>(acc_re, BN, sa, sb, bslot, 0, 0, id, first);     // Re A Re T
-    issue_diagonals<S>(acc_im, BN, sa, sb, bslot, 0, 1, id, first);     // Re A Im T
-    if (!REAL) {
-      issue_diagonals<S>(acc_re, BN, sa, sb, bslot, 1, 1, idn, false);  // -Im A Im T
-      issue_diagonals<S>(acc_im, BN, sa, sb, bslot, 1, 0, id, false);   // Im A Re T
-    }
-  }
-  static __device__ Tile tile(const Args& a) {
-    return Tile{(int)blockIdx.x * 128, (int)blockIdx.y, (int)blockIdx.z * kPropBN, 0, a.c.nkb};
-  }
-  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t,
-                                int u, int s, int kb, uint64_t* bar) {
-    if (REAL)
-      tc::tma_load_3d(dst, tm, kb * kBK, t.p0, s, bar);
-    else
-      tc::tma_load_4d(dst, tm, kb * kBK, t.p0, 2 * t.z + u, s, bar);
-  }
-  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args&, const Tile& t,
-                                int u, int s, int kb, uint64_t* bar) {
-    tc::tma_load_4d(dst, tm, kb * kBK, t.n0, 2 * t.z + u, s, bar);
-  }
-  template <int S>
-  static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t*, int warp,
-                                  int lane) {
-    const int p = t.p0 + warp * 32 + lane, z = t.z, N = a.N, BN = a.c.BN;
-    const bool valid = p < a.M;
-    const int ep = valid ? (REAL ? a.ea[p] : a.ea[(long)z * a.M + p]) : 0;
-    for (int c0 = 0; c0 < BN && t.n0 + c0 < N; c0 += 16) {
-      float fr[S][16], fi[S][16];
-#pragma unroll
-      for (int d = 0; d < S; ++d) {
-        tmem_row16(tmem + (uint32_t)(d * BN), warp, c0, fr[d]);
-        tmem_row16(tmem + (uint32_t)((S + d) * BN), warp, c0, fi[d]);
-      }
-      if (!valid) continue;
-#pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        const int j = t.n0 + c0 + jj;
-        if (j >= N) continue;
-        const int sc = ep + a.eb[(long)z * N + j] - 14;
-        float ar[S], ai[S];
-#pragma unroll
-        for (int d = 0; d < S; ++d) {
-          ar[d] = fr[d][jj];
-          ai[d] = fi[d][jj];
-        }
-        const double dr = combine_exact<S>(ar, sc), di = combine_exact<S>(ai, sc);
-        const long ia = ((long)z * N + j) * a.M + p;    // [z][j][p]
-        const long iphi = ((long)z * a.M + p) * N + j;  // [z][p][j]
-        if (a.mode == kModeFirst) {
-          const double2 f = a.phi_in[iphi];
-          const double2 out = make_double2(dr + f.x, di + f.y);
-          a.accT[ia] = out;
-          a.tout[ia] = out;
-        } else if (a.mode == kModeTerm) {
-          // T_k = i sqrt(dt) V T_{k-1} / k = c (-Im(V T), Re(V T)), c = sqrt(dt) / k
-          const double2 out = make_double2(-a.coef * di, a.coef * dr);
-          const double2 acc = a.accT[ia];
-          const double2 sum = make_double2(acc.x + out.x, acc.y + out.y);
-          a.accT[ia] = sum;
-          a.tout[ia] = a.acc_out ? sum : out;
-        } else {
-          const double2 acc = a.accT[ia];
-          a.phi_out[iphi] = make_double2(dr + acc.x, di + acc.y);
-        }
-      }
-    }
-  }
+struct PropArgs {
+  int M, N, W, mode, acc_out, brows, BN, nkb, stages, npt, njt, ntiles;
+  uint32_t tx_bytes, tmem_cols;
+  double coef;            // term k: sqrt(dt) / k (A = i sqrt(dt) V)
+  const int* ea;          // row exponents of A: P - I per p, or V_z per (z, p)
+  const int* eb;          // row exponents of T^T per (z, j)
+  const double2* phi_in;  // mode first: Phi (W x M x N)
+  double2* accT;          // W x N x M FP64 accumulator of P T_n(A) P Phi, transposed
+  double2* phi_out;       // mode last: Phi (W x M x N)
+  double2* tout;          // W x N x M FP64: the next operand (sliced by the next kernel)
+  int* err;
 };
+
+__device__ __forceinline__ void prop_epi_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kPropEpi * 32) : "memory");
+}
+
+template <int S, bool REAL>
+__global__ void __launch_bounds__(32 * kPropWarps, 1)
+    k_prop_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const PropArgs a) {
+  constexpr int kUA = REAL ? 1 : 2;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full[kMaxStages];
+  __shared__ __align__(8) uint64_t empty[kMaxStages];
+  __shared__ __align__(8) uint64_t tfull;
+  __shared__ __align__(8) uint64_t tempty;
+  __shared__ __align__(8) uint64_t fin;
+  __shared__ uint32_t tmem_base;
+  __shared__ int skip;
+  __shared__ int ep_ok;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nst = a.stages, BN = a.BN, brows = a.brows;
+  const uint32_t bslot = (uint32_t)BN * 64u;
+  const uint32_t stage_bytes = S * (kUA * kASlot + bslot);
+  int* err = a.err;
+  if (threadIdx.x == 0) skip = *(const volatile int*)err;
+  __syncthreads();
+  if (skip) return;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nst; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    tc::mbar_init(&tfull, 1);
+    tc::mbar_init(&tempty, kPropEpi);
+    tc::mbar_init(&fin, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&tmem_base, a.tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const int per_z = a.njt * a.npt;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+        const int z = tile / per_z, r = tile - z * per_z;
+        const int p0 = (r % a.npt) * 128, j0 = (r / a.npt) * brows;
+        for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+          const int st = it % nst;
+          if (it >= nst && !tc::mbar_wait(&empty[st], ((it / nst) - 1) & 1, err)) {
+            atomicExch(err, 1);
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&full[st], a.tx_bytes);
+          uint8_t* sa = smem + st * stage_bytes;
+          uint8_t* sb = sa + S * kUA * kASlot;
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            if (REAL) {
+              tc::tma_load_3d(sa + s * kASlot, &tmA, kb * kBK, p0, s, &full[st]);
+            } else {
+              tc::tma_load_4d(sa + s * kASlot, &tmA, kb * kBK, p0, 2 * z, s, &full[st]);
+              tc::tma_load_4d(sa + (S + s) * kASlot, &tmA, kb * kBK, p0, 2 * z + 1, s, &full[st]);
+            }
+            tc::tma_load_4d(sb + s * bslot, &tmB, kb * kBK, j0, 2 * z, s, &full[st]);
+            tc::tma_load_4d(sb + s * bslot + brows * 64, &tmB, kb * kBK, j0, 2 * z + 1, s,
+                            &full[st]);
+          }
+        }
+      }
+      for (int i = it > nst ? it - nst : 0; i < it; ++i)
+        tc::mbar_wait(&full[i % nst], (i / nst) & 1, err);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id_full = tc::idesc_bf16(128, BN);
+      const uint32_t id_half = tc::idesc_bf16(128, brows), id_half_neg = tc::idesc_bf16(128, brows, true);
+      int it = 0, lt = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++lt) {
+        if (lt >= 1 && !tc::mbar_wait(&tempty, (lt - 1) & 1, err)) {
+          atomicExch(err, 1);
+          break;
+        }
+        tc::fence_after_sync();
+        for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+          const int st = it % nst;
+          if (!tc::mbar_wait(&full[st], (it / nst) & 1, err)) {
+            atomicExch(err, 1);
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
+          const uint32_t sb = sa + S * kUA * kASlot;
+          issue_diagonals<S>(tmem, (uint32_t)BN, sa, sb, bslot, 0, 0, id_full, kb == 0);
+          if (!REAL) {
+            issue_diagonals<S>(tmem, (uint32_t)BN, sa, sb + (uint32_t)brows * 64u, bslot, 1, 0,
+                               id_half_neg, false);
+            issue_diagonals<S>(tmem + (uint32_t)brows, (uint32_t)BN, sa, sb, bslot, 1, 0, id_half,
+                               false);
+          }
+          tc::mma_commit(&empty[st]);
+        }
+        if (ok) tc::mma_commit(&tfull);
+      }
+      tc::mma_commit(&fin);
+    }
+  } else {
+    const int q = warp - 2, lq = warp & 3, part = q >> 2;  // two warps per lane quarter
+    const int M = a.M, N = a.N;
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++lt) {
+      if (q == 0 && lane == 0) {
+        ep_ok = tc::mbar_wait(&tfull, lt & 1, err) ? 1 : 0;
+        if (!ep_ok) atomicExch(err, 1);
+      }
+      prop_epi_sync();
+      if (!ep_ok) break;
+      tc::fence_after_sync();
+      const int z = tile / per_z, r = tile - z * per_z;
+      const int p0 = (r % a.npt) * 128, j0 = (r / a.npt) * brows;
+      const int p = p0 + 32 * lq + lane;
+      const bool valid = p < M;
+      const int ep = valid ? (REAL ? a.ea[p] : a.ea[(long)z * M + p]) : 0;
+      const uint32_t trow = tmem + ((uint32_t)(32 * lq) << 16);
+      for (int c0 = 16 * part; c0 < brows; c0 += 32) {
+        // real parts of 16 columns first (digits -> FP64), then their imaginary partners
+        float f[S][16];
+        double dre[16];
+#pragma unroll
+        for (int d = 0; d < S; ++d) tc::tmem_ld16(trow + (uint32_t)(d * BN + c0), f[d]);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = j0 + c0 + jj;
+          float ar[S];
+#pragma unroll
+          for (int d = 0; d < S; ++d) ar[d] = f[d][jj];
+          dre[jj] = (valid && j < N) ? combine_exact<S>(ar, ep + a.eb[(long)z * N + j] - 14) : 0.0;
+        }
+#pragma unroll
+        for (int d = 0; d < S; ++d) tc::tmem_ld16(trow + (uint32_t)(d * BN + brows + c0), f[d]);
+        if (!valid) continue;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = j0 + c0 + jj;
+          if (j >= N) continue;
+          float ai[S];
+#pragma unroll
+          for (int d = 0; d < S; ++d) ai[d] = f[d][jj];
+          const int sc = ep + a.eb[(long)z * N + j] - 14;
+          const double dr = dre[jj], di = combine_exact<S>(ai, sc);
+          const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
+          const long iphi = ((long)z * M + p) * N + j;  // [z][p][j]
+          if (a.mode == kModeFirst) {
+            const double2 f = a.phi_in[iphi];
+            const double2 out = make_double2(dr + f.x, di + f.y);
+            a.accT[ia] = out;
+            a.tout[ia] = out;
+          } else if (a.mode == kModeTerm) {
+            // T_k = i c V T_{k-1} = c (-Im(V T), Re(V T))
+            const double2 out = make_double2(-a.coef * di, a.coef * dr);
+            const double2 acc = a.accT[ia];
+            const double2 sum = make_double2(acc.x + out.x, acc.y + out.y);
+            a.accT[ia] = sum;
+            a.tout[ia] = a.acc_out ? sum : out;
+          } else {
+            const double2 acc = a.accT[ia];
+            a.phi_out[iphi] = make_double2(dr + acc.x, di + acc.y);
+          }
+        }
+      }
+      tc::fence_before_sync();
+      if (lane == 0) tc::mbar_arrive(&tempty);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    static const int zero = 0;
+    tc::mbar_wait(&fin, 0, &zero);
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, a.tmem_cols);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // slicing kernels (one warp per row: row maximum, then integer digits)
@@ -388,10 +518,10 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_t[0], (size_t)W * N * sizeof(int)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_t[1], (size_t)W * N * sizeof(int)));
   ctx->vhs_BN = 2 * W >= 128 ? 128 : round_up(2 * W, 16);
-  ctx->prop_BN = N >= kPropBN ? kPropBN : round_up(N, 16);
-  if (S * ctx->vhs_BN > 512 || 2 * S * ctx->prop_BN > 512)
+  ctx->prop_rows = N >= kPropRows ? kPropRows : round_up(N, 16);
+  if (S * ctx->vhs_BN > 512 || 2 * S * ctx->prop_rows > 512)
     return afq_fail(ctx, AFQ_ERR_ARG, "split propagation: too many slices for TMEM");
-  const uint32_t brows = (uint32_t)(N >= kPropBN ? kPropBN : N);
+  const uint32_t brows = (uint32_t)ctx->prop_rows;
   bool ok = true;
   {
     const uint64_t da[3] = {(uint64_t)ctx->Xpad, (uint64_t)ctx->Mp, (uint64_t)S};
@@ -450,34 +580,73 @@ int launch_vhs_tc(afq_ctx* ctx) {
 }
 
 namespace {
+int sm_count_prop() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+template <int S, bool REAL>
+cudaError_t launch_prop_s(int grid, size_t smem, cudaStream_t stream, const CUtensorMap& ta,
+                          const CUtensorMap& tb, const PropArgs& a) {
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_prop_tc<S, REAL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  k_prop_tc<S, REAL><<<grid, 32 * kPropWarps, smem, stream>>>(ta, tb, a);
+  return cudaGetLastError();
+}
+
+// One GEMM pass of the propagation (mode first / term / last) on operand buffer b.
 template <bool REAL>
-int launch_cplx(afq_ctx* ctx, const CUtensorMap& ta, const CUtensorMap& tb, const int* ea,
-                const int* eb, int mode, double coef, int acc_out) {
-  using P = CplxP<REAL>;
-  typename P::Args a{};
+int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int mode, double coef,
+                int acc_out) {
+  PropArgs a{};
   const int N = ctx->N, S = ctx->Sp;
-  const int brows = N >= kPropBN ? kPropBN : N;
-  a.c.nkb = ctx->Mpad / kBK;
-  a.c.BN = ctx->prop_BN;
-  a.c.tx_bytes = (uint32_t)S * (P::kUA * kBK * 128 * 2 + 2 * kBK * brows * 2);
-  a.c.tmem_cols = tmem_cols_for(2 * S * a.c.BN);
-  a.c.err = ctx->flags + 2;
   a.M = ctx->M;
   a.N = N;
   a.W = ctx->ws.W;
   a.mode = mode;
   a.acc_out = acc_out;
+  a.brows = ctx->prop_rows;
+  a.BN = 2 * a.brows;
+  a.nkb = ctx->Mpad / kBK;
+  a.npt = (ctx->M + 127) / 128;
+  a.njt = (N + a.brows - 1) / a.brows;
+  a.ntiles = a.W * a.njt * a.npt;
+  const int kUA = REAL ? 1 : 2;
+  a.tx_bytes = (uint32_t)S * (kUA * kBK * 128 * 2 + 2 * kBK * a.brows * 2);
+  a.tmem_cols = tmem_cols_for(S * a.BN);
   a.coef = coef;
   a.ea = ea;
-  a.eb = eb;
+  a.eb = ctx->e_t[b];
   a.phi_in = ctx->ws.phi;
   a.accT = ctx->accT;
   a.phi_out = ctx->ws.phi;
   a.tout = ctx->tout;
-  size_t smem = 0;
-  plan_smem(S, P::kUA, P::kUB, a.c.BN, 0, &a.c.stages, &smem);
-  dim3 grid((ctx->M + 127) / 128, ctx->ws.W, (N + kPropBN - 1) / kPropBN);
-  cudaError_t e = launch_tc_s<P>(S, grid, smem, ctx->stream, ta, tb, a);
+  a.err = ctx->flags + 2;
+  const size_t stage = (size_t)S * (kUA * (size_t)kASlot + (size_t)a.BN * 64);
+  int nst = (int)((kSmemLimit - 2048 - 1024) / stage);
+  if (nst > kMaxStages) nst = kMaxStages;
+  if (nst < 1 || S * a.BN > 512) return afq_fail(ctx, AFQ_ERR_ARG, "propagation tile does not fit");
+  a.stages = nst;
+  const size_t smem = stage * nst + 1024;
+  const int grid = a.ntiles < sm_count_prop() ? a.ntiles : sm_count_prop();
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (S) {
+    case 1: e = launch_prop_s<1, REAL>(grid, smem, ctx->stream, ta, ctx->tm_t[b], a); break;
+    case 2: e = launch_prop_s<2, REAL>(grid, smem, ctx->stream, ta, ctx->tm_t[b], a); break;
+    case 3: e = launch_prop_s<3, REAL>(grid, smem, ctx->stream, ta, ctx->tm_t[b], a); break;
+    case 4: e = launch_prop_s<4, REAL>(grid, smem, ctx->stream, ta, ctx->tm_t[b], a); break;
+  }
   ctx->launches++;
   if (e != cudaSuccess)
     return afq_fail(ctx, AFQ_ERR_CUDA, std::string("propagate tc: ") + cudaGetErrorString(e));
@@ -504,20 +673,17 @@ int launch_propagate_tc(afq_ctx* ctx) {
   int cur = 0, rc;
   if ((rc = slice_tout(ctx, cur)) != AFQ_OK) return rc;
   // T_0 = P Phi = Phi + (P - I) Phi
-  rc = launch_cplx<true>(ctx, ctx->tm_pm, ctx->tm_t[cur], ctx->e_pm, ctx->e_t[cur], kModeFirst,
-                         1.0, 0);
+  rc = launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeFirst, 1.0, 0);
   if (rc != AFQ_OK) return rc;
   cur = 1 - cur;
   if ((rc = slice_tout(ctx, cur)) != AFQ_OK) return rc;
   const int n = ctx->p.taylor_order;
   for (int k = 1; k <= n; ++k) {
-    rc = launch_cplx<false>(ctx, ctx->tm_az, ctx->tm_t[cur], ctx->e_a, ctx->e_t[cur], kModeTerm,
-                            sqrt(ctx->p.dt) / k, k == n);
+    rc = launch_prop<false>(ctx, ctx->tm_az, cur, ctx->e_a, kModeTerm, sqrt(ctx->p.dt) / k, k == n);
     if (rc != AFQ_OK) return rc;
     cur = 1 - cur;
     if ((rc = slice_tout(ctx, cur)) != AFQ_OK) return rc;
   }
   // Phi = P acc = acc + (P - I) acc
-  return launch_cplx<true>(ctx, ctx->tm_pm, ctx->tm_t[cur], ctx->e_pm, ctx->e_t[cur], kModeLast,
-                           1.0, 0);
+  return launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeLast, 1.0, 0);
 }
