@@ -62,11 +62,21 @@ def mixed_vs_oracle(s, W, phi, nsteps, fields=None, **kw):
     return ctx, orc, e0, e0_ref, e1, e1_ref
 
 
-@pytest.mark.parametrize("cfg", ["ragged", "c2"])
+@pytest.mark.parametrize("cfg", ["ragged", "wide", "uneven", "c2"])
 def test_mixed_energy_within_1e6_of_fp64_oracle(cfg):
     if cfg == "ragged":
         s = make_system(37, 5, 3, 71, seed=4, decay="geometric", e0=0.37)
         W = 13
+    elif cfg == "wide":
+        # 80 walker columns (two propagation column tiles), 40 electrons per spin
+        # (exchange rows beyond one warp), 7 walkers (not a multiple of the exchange
+        # walker block)
+        s = make_system(96, 40, 40, 101, seed=6, decay="geometric", e0=-0.2)
+        W = 7
+    elif cfg == "uneven":
+        # unequal spins (two exchange launches), one electron in one spin
+        s = make_system(45, 9, 1, 57, seed=8, decay="geometric", e0=0.1)
+        W = 5
     else:
         s, c = make_config("c2")
         W = c["W"]
