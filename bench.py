@@ -182,8 +182,31 @@ def cpu_baseline(seconds: float, W_sample: int = 8) -> dict:
                       f"{steps} steps (step + QR cadence + E_loc), {dt:.1f} s of host time"}
 
 
+def fp64_step_ms(s, W: int, rank: int, steps: int = 2) -> float:
+    """Event-timed FP64 step + local energy on the same system (all walkers)."""
+    import torch
+    from paper_2209_04015_b300 import AfqContext
+    stream = torch.cuda.current_stream()
+    ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, stream=stream.cuda_stream)
+    ctx.init_hamiltonian(s.h1, s.L, s.e0)
+    ctx.init_trial(s.psi_a, s.psi_b)
+    ctx.init_walkers(W)
+    ctx.propagate_dev(None, 1)
+    ctx.local_energy_dev(None, None)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        ctx.propagate_dev(None, 1)
+        ctx.local_energy_dev(None, None)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ctx.close()
+    return a.elapsed_time(b) / steps
+
+
 def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int = 16,
-              long_steps: int = 100, walkers: int = 0) -> dict:
+              long_steps: int = 100, walkers: int = 0, fp64_compare: bool = False) -> dict:
     long_steps = max(long_steps, 0)  # 0: no drift check (no FP64 reference context)
     """Split-precision (tcgen05) throughput on one workload, and its |dE_L| against
     the FP64 path on the first walkers after 1 and after long_steps steps.  Walkers
@@ -266,6 +289,11 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
                                       "algorithmic flops (no padding counted)",
                         "avg_launch_ms": ex_avg * 1e3}}
     mix.close()
+    if fp64_compare:
+        f_ms = fp64_step_ms(s, W, rank)
+        out["fp64_ms_per_step"] = f_ms
+        out["fp64_value"] = W / (f_ms / 1e3)
+        out["speedup_vs_fp64"] = f_ms / ms
     return out
 
 
@@ -540,7 +568,8 @@ def run_afq(args):
         line["mixed"] = {"same_workload": mixed_leg(WORKLOAD, args.mixed_steps * 5, args.warmup,
                                                     rank, long_steps=args.error_steps),
                          "large_shape": mixed_leg("c3", args.mixed_steps, args.warmup, rank,
-                                                  long_steps=args.error_steps)}
+                                                  long_steps=args.error_steps,
+                                                  fp64_compare=True)}
         line["mixed"]["same_workload"]["speedup_vs_fp64"] = (
             line["mixed"]["same_workload"]["value"] / (value / world))
         line["batched"] = batched_leg(rank)
