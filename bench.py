@@ -82,6 +82,20 @@ def dist_info():
     return rank, world, local
 
 
+def job_throughput(total_ms: float, units_per_rank: int, world: int, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank processed
+    units_per_rank units; the job time is the slowest rank's (MAX over ranks, the only
+    collective, outside the data path).  Returns (units per second, max ms)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    return world * units_per_rank / (total_ms / 1e3), total_ms
+
+
 def exchange_flops(W, X, M, na, nb):
     """Algorithmic flops of the exchange kernel for W walkers: T = L~ theta
     (4 n^2 M real flops per g and spin, real x complex) plus sum T_ij T_ji
@@ -503,13 +517,7 @@ def run_afq(args):
     ctx.profile_enable(False)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
-    value = world * W * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(float(sum(step_ms)), W * args.steps, world, device="cuda")
 
     # end to end through the public host-buffer API: the step's fields go host -> device
     # from pinned memory, the energies come back to the host, every step
