@@ -372,6 +372,72 @@ __global__ void k_slice_cplx(const double2* __restrict__ in, long rows, int R, i
   }
 }
 
+int warp_grid(long rows);
+
+// One-pass form of k_slice_cplx for rows of K <= 64 NP: each lane holds NP pairs of
+// consecutive elements in registers (one read of the row), the warp takes the row
+// exponent, and every digit plane is written as bfloat16 pairs (128-byte warp stores).
+template <int NP>
+__global__ void __launch_bounds__(256) k_slice_cplx1(const double2* __restrict__ in, long rows,
+                                                     int R, int K, int Kp, int S,
+                                                     __nv_bfloat16* __restrict__ out,
+                                                     int* __restrict__ eout) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const long plane = 2L * rows * Kp;
+  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
+       r += (long)gridDim.x * warps) {
+    const double2* row = in + r * K;
+    double2 v[NP][2];
+    int m = 0;
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+      const int k = 2 * lane + 64 * t;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        v[t][h] = k + h < K ? row[k + h] : make_double2(0.0, 0.0);
+        m = max(m, max(exp_field(v[t][h].x), exp_field(v[t][h].y)));
+      }
+    }
+    const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
+    if (lane == 0) eout[r] = e;
+    const long z = r / R, i = r % R;
+    __nv_bfloat16* ore = out + ((z * 2) * R + i) * Kp;
+    __nv_bfloat16* oim = ore + (long)R * Kp;
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+      const int k = 2 * lane + 64 * t;
+      if (k >= Kp) continue;
+      int q0[kMaxSlices], q1[kMaxSlices];
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        exact_digits(part ? v[t][0].y : v[t][0].x, e, S, q0);
+        exact_digits(part ? v[t][1].y : v[t][1].x, e, S, q1);
+        __nv_bfloat16* o = (part ? oim : ore) + k;
+#pragma unroll
+        for (int s = 0; s < kMaxSlices; ++s)
+          if (s < S)
+            *reinterpret_cast<__nv_bfloat162*>(o + s * plane) =
+                __floats2bfloat162_rn((float)q0[s], (float)q1[s]);
+      }
+    }
+  }
+}
+
+// Digits of complex rows (z, i) of K elements into planes [s][z][re/im][i][Kp]: the
+// one-pass kernel for K <= 1024, else the two-pass one.
+void slice_rows(const double2* in, long rows, int R, int K, int Kp, int S,
+                __nv_bfloat16* out, int* eout, cudaStream_t st) {
+  const int g = warp_grid(rows);
+  if (Kp <= 128)
+    k_slice_cplx1<2><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+  else if (Kp <= 256)
+    k_slice_cplx1<4><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+  else if (Kp <= 512)
+    k_slice_cplx1<8><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+  else
+    k_slice_cplx<<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+}
+
 // Phi (W x M x N) -> W x N x M (transposed copy, FP64)
 __global__ void k_transpose_phi(const double2* __restrict__ phi, int W, int M, int N,
                                 double2* __restrict__ out) {
@@ -573,8 +639,7 @@ int launch_vhs_tc(afq_ctx* ctx) {
   cudaError_t e = launch_tc_s<VhsP>(S, grid, smem, ctx->stream, ctx->tm_vhs_a, ctx->tm_vhs_b, a);
   ctx->launches++;
   if (e != cudaSuccess) return afq_fail(ctx, AFQ_ERR_CUDA, std::string("vhs tc: ") + cudaGetErrorString(e));
-  k_slice_cplx<<<warp_grid((long)W * M), 256, 0, ctx->stream>>>(ctx->A, (long)W * M, M, M,
-                                                               ctx->Mpad, S, ctx->A_sl, ctx->e_a);
+  slice_rows(ctx->A, (long)W * M, M, M, ctx->Mpad, S, ctx->A_sl, ctx->e_a, ctx->stream);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }
@@ -656,9 +721,8 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
 // digits of tout (W x N x M) into Taylor operand buffer b
 int slice_tout(afq_ctx* ctx, int b) {
   const int W = ctx->ws.W, N = ctx->N, M = ctx->M;
-  k_slice_cplx<<<warp_grid((long)W * N), 256, 0, ctx->stream>>>(ctx->tout, (long)W * N, N, M,
-                                                               ctx->Mpad, ctx->Sp, ctx->T_sl[b],
-                                                               ctx->e_t[b]);
+  slice_rows(ctx->tout, (long)W * N, N, M, ctx->Mpad, ctx->Sp, ctx->T_sl[b], ctx->e_t[b],
+             ctx->stream);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }

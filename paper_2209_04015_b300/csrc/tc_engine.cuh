@@ -143,6 +143,31 @@ __device__ __forceinline__ void split_exact(double x, int e, int S, __nv_bfloat1
     if (s < S) out[s * plane] = __float2bfloat16_rn((float)(neg ? -q[s] : q[s]));
 }
 
+// The same digits returned in q[0..S-1] (q[s] = digit of weight 256^-s).
+__device__ __forceinline__ void exact_digits(double x, int e, int S, int (&q)[kMaxSlices]) {
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long v = 0;
+  if (E != 0) {
+    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = E - 1075 + 7 - e + 8 * (S - 1);
+    if (sh >= 0)
+      v = sh < 10 ? mant << sh : 0;
+    else if (sh > -64)
+      v = (mant + (1LL << (-sh - 1))) >> (-sh);
+  }
+  const bool neg = bits < 0;
+#pragma unroll
+  for (int s = kMaxSlices - 1; s >= 0; --s) {
+    q[s] = 0;
+    if (s >= S) continue;
+    int d = (int)(v & 255);
+    if (d > 128) d -= 256;
+    q[s] = neg ? -d : d;
+    v = (v - d) >> 8;
+  }
+}
+
 // Recombines the S exact diagonal accumulators of one element:
 // value = 2^scale_exp sum_d acc_d 256^-d, through one int64 and one conversion.
 template <int S>
