@@ -116,9 +116,8 @@ constexpr int kPropWarps = 10;
 constexpr int kPropEpi = 8;
 
 struct PropArgs {
-  int M, N, W, mode, acc_out, brows, BN, nkb, stages, npt, njt, ntiles;
+  int M, N, W, mode, brows, BN, nkb, stages, npt, njt, ntiles;
   uint32_t tx_bytes, tmem_cols;
-  double coef;            // term k: sqrt(dt) / k (A = i sqrt(dt) V)
   const int* ea;          // row exponents of A: P - I per p, or V_z per (z, p)
   const int* eb;          // row exponents of T^T per (z, j)
   const double2* phi_in;  // mode first: Phi (W x M x N)
@@ -299,12 +298,9 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
             a.accT[ia] = out;
             a.tout[ia] = out;
           } else if (a.mode == kModeTerm) {
-            // T_k = i c V T_{k-1} = c (-Im(V T), Re(V T))
-            const double2 out = make_double2(-a.coef * di, a.coef * dr);
-            const double2 acc = a.accT[ia];
-            const double2 sum = make_double2(acc.x + out.x, acc.y + out.y);
-            a.accT[ia] = sum;
-            a.tout[ia] = a.acc_out ? sum : out;
+            // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k to
+            // the FP64 Taylor sum
+            a.tout[ia] = make_double2(dr, di);
           } else {
             const double2 acc = a.accT[ia];
             a.phi_out[iphi] = make_double2(dr + acc.x, di + acc.y);
@@ -420,6 +416,90 @@ __global__ void __launch_bounds__(256) k_slice_cplx1(const double2* __restrict__
                 __floats2bfloat162_rn((float)q0[s], (float)q1[s]);
       }
     }
+  }
+}
+
+// Taylor step of the split propagation, one pass over u_k (W x N x M, rows (z, j)):
+// acc += i^k g_k u_k (FP64), then the digits of u_k for the next term -- or, after
+// the last term (last != 0), the digits of the finished sum acc for the second
+// one-body half.  kmod = k mod 4 selects the rotation i^k.
+template <int NP>
+__global__ void __launch_bounds__(256) k_taylor_slice(const double2* __restrict__ in,
+                                                      double2* __restrict__ acc, long rows,
+                                                      int R, int K, int Kp, int S, double gk,
+                                                      int kmod, int last,
+                                                      __nv_bfloat16* __restrict__ out,
+                                                      int* __restrict__ eout) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const long plane = 2L * rows * Kp;
+  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
+       r += (long)gridDim.x * warps) {
+    const double2* row = in + r * K;
+    double2* arow = acc + r * K;
+    double2 v[NP][2];
+    int m = 0;
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+      const int k = 2 * lane + 64 * t;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        double2 u = make_double2(0.0, 0.0);
+        if (k + h < K) {
+          u = row[k + h];
+          // i^k u: multiply by i kmod times
+          double2 w = u;
+          if (kmod == 1) w = make_double2(-u.y, u.x);
+          else if (kmod == 2) w = make_double2(-u.x, -u.y);
+          else if (kmod == 3) w = make_double2(u.y, -u.x);
+          double2 a = arow[k + h];
+          a.x = fma(gk, w.x, a.x);
+          a.y = fma(gk, w.y, a.y);
+          arow[k + h] = a;
+          if (last) u = a;
+        }
+        v[t][h] = u;
+        m = max(m, max(exp_field(u.x), exp_field(u.y)));
+      }
+    }
+    const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
+    if (lane == 0) eout[r] = e;
+    const long z = r / R, i = r % R;
+    __nv_bfloat16* ore = out + ((z * 2) * R + i) * Kp;
+    __nv_bfloat16* oim = ore + (long)R * Kp;
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+      const int k = 2 * lane + 64 * t;
+      if (k >= Kp) continue;
+      int q0[kMaxSlices], q1[kMaxSlices];
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        exact_digits(part ? v[t][0].y : v[t][0].x, e, S, q0);
+        exact_digits(part ? v[t][1].y : v[t][1].x, e, S, q1);
+        __nv_bfloat16* o = (part ? oim : ore) + k;
+#pragma unroll
+        for (int s = 0; s < kMaxSlices; ++s)
+          if (s < S)
+            *reinterpret_cast<__nv_bfloat162*>(o + s * plane) =
+                __floats2bfloat162_rn((float)q0[s], (float)q1[s]);
+      }
+    }
+  }
+}
+
+// acc += i^k g_k u_k elementwise (the long-row form of k_taylor_slice's update)
+__global__ void k_taylor_acc(const double2* __restrict__ u, double2* __restrict__ acc, long n,
+                             double gk, int kmod) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x) {
+    const double2 x = u[e];
+    double2 w = x;
+    if (kmod == 1) w = make_double2(-x.y, x.x);
+    else if (kmod == 2) w = make_double2(-x.x, -x.y);
+    else if (kmod == 3) w = make_double2(x.y, -x.x);
+    double2 a = acc[e];
+    a.x = fma(gk, w.x, a.x);
+    a.y = fma(gk, w.y, a.y);
+    acc[e] = a;
   }
 }
 
@@ -672,15 +752,13 @@ cudaError_t launch_prop_s(int grid, size_t smem, cudaStream_t stream, const CUte
 
 // One GEMM pass of the propagation (mode first / term / last) on operand buffer b.
 template <bool REAL>
-int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int mode, double coef,
-                int acc_out) {
+int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int mode) {
   PropArgs a{};
   const int N = ctx->N, S = ctx->Sp;
   a.M = ctx->M;
   a.N = N;
   a.W = ctx->ws.W;
   a.mode = mode;
-  a.acc_out = acc_out;
   a.brows = ctx->prop_rows;
   a.BN = 2 * a.brows;
   a.nkb = ctx->Mpad / kBK;
@@ -690,7 +768,6 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   const int kUA = REAL ? 1 : 2;
   a.tx_bytes = (uint32_t)S * (kUA * kBK * 128 * 2 + 2 * kBK * a.brows * 2);
   a.tmem_cols = tmem_cols_for(S * a.BN);
-  a.coef = coef;
   a.ea = ea;
   a.eb = ctx->e_t[b];
   a.phi_in = ctx->ws.phi;
@@ -718,6 +795,32 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   return AFQ_OK;
 }
 
+// acc += i^k g_k u_k and the digits of u_k (or of acc after the last term) into
+// operand buffer b; rows longer than 512 take the two-kernel form
+int taylor_slice(afq_ctx* ctx, int b, double gk, int kmod, int last) {
+  const int W = ctx->ws.W, N = ctx->N, M = ctx->M, Kp = ctx->Mpad, S = ctx->Sp;
+  const long rows = (long)W * N;
+  const int g = warp_grid(rows);
+  if (Kp <= 128)
+    k_taylor_slice<2><<<g, 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows, N, M, Kp, S, gk,
+                                                  kmod, last, ctx->T_sl[b], ctx->e_t[b]);
+  else if (Kp <= 256)
+    k_taylor_slice<4><<<g, 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows, N, M, Kp, S, gk,
+                                                  kmod, last, ctx->T_sl[b], ctx->e_t[b]);
+  else if (Kp <= 512)
+    k_taylor_slice<8><<<g, 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows, N, M, Kp, S, gk,
+                                                  kmod, last, ctx->T_sl[b], ctx->e_t[b]);
+  else {
+    k_taylor_acc<<<grid1d(rows * M), 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows * M, gk,
+                                                            kmod);
+    AFQ_LAUNCHED(ctx);
+    slice_rows(last ? ctx->accT : ctx->tout, rows, N, M, Kp, S, ctx->T_sl[b], ctx->e_t[b],
+               ctx->stream);
+  }
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
+
 // digits of tout (W x N x M) into Taylor operand buffer b
 int slice_tout(afq_ctx* ctx, int b) {
   const int W = ctx->ws.W, N = ctx->N, M = ctx->M;
@@ -728,7 +831,10 @@ int slice_tout(afq_ctx* ctx, int b) {
 }
 }  // namespace
 
-// Phi <- P T_n(A) P Phi for every walker, A from the last launch_vhs_tc.
+// Phi <- P T_n(A) P Phi for every walker, A from the last launch_vhs_tc.  With
+// A = i sqrt(dt) V the Taylor terms are t_k = i^k g_k u_k, g_k = dt^(k/2) / k!, and
+// u_k = V u_{k-1} (u_0 = P Phi) runs on the tensor cores unscaled; the FP64 sum of the
+// t_k is kept by the slicing passes.
 int launch_propagate_tc(afq_ctx* ctx) {
   const int W = ctx->ws.W;
   k_transpose_phi<<<grid1d((long)W * ctx->N * ctx->M), 256, 0, ctx->stream>>>(
@@ -736,18 +842,20 @@ int launch_propagate_tc(afq_ctx* ctx) {
   AFQ_LAUNCHED(ctx);
   int cur = 0, rc;
   if ((rc = slice_tout(ctx, cur)) != AFQ_OK) return rc;
-  // T_0 = P Phi = Phi + (P - I) Phi
-  rc = launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeFirst, 1.0, 0);
+  // u_0 = P Phi = Phi + (P - I) Phi, also the first term of the sum
+  rc = launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeFirst);
   if (rc != AFQ_OK) return rc;
   cur = 1 - cur;
   if ((rc = slice_tout(ctx, cur)) != AFQ_OK) return rc;
   const int n = ctx->p.taylor_order;
+  double gk = 1.0;
   for (int k = 1; k <= n; ++k) {
-    rc = launch_prop<false>(ctx, ctx->tm_az, cur, ctx->e_a, kModeTerm, sqrt(ctx->p.dt) / k, k == n);
+    rc = launch_prop<false>(ctx, ctx->tm_az, cur, ctx->e_a, kModeTerm);
     if (rc != AFQ_OK) return rc;
     cur = 1 - cur;
-    if ((rc = slice_tout(ctx, cur)) != AFQ_OK) return rc;
+    gk *= sqrt(ctx->p.dt) / k;
+    if ((rc = taylor_slice(ctx, cur, gk, k & 3, k == n)) != AFQ_OK) return rc;
   }
   // Phi = P acc = acc + (P - I) acc
-  return launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeLast, 1.0, 0);
+  return launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeLast);
 }
