@@ -14,7 +14,8 @@
 //   warps 2-5 epilogue: a few walkers of the tile at a time, their 2n columns are
 //            copied from TMEM (each warp its 32 lanes) to shared memory, and each warp
 //            reduces sum_ij T_ij T_ji of its g-blocks (lanes over (g-block, row i);
-//            conflict-free rows and columns; FP32 over j, then FP64).
+//            conflict-free rows and columns; FP32 within the warp, FP64 across warps
+//            and tiles).
 // With equal spins both spins' tiles run in one launch (the same maps, another
 // orbital offset).
 // With two accumulators the epilogue of one tile runs under the MMAs of the next.
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kExThreads, 1)
         epi_sync();
         for (int zl = zr; zl < min(a.zb, zr + a.zc); ++zl) {
           const int cb = (zl - zr) * w2n;
-          double dr = 0.0, di = 0.0;
+          float dr = 0.f, di = 0.f;
           // lanes over (g-block of this warp, row i): sum_j T_ij T_ji in FP32, then FP64
           for (int e = lane; e < nblk * n; e += 32) {
             const int b = e / n, i = e - b * n, gl = q + kEpiWarps * b;
@@ -220,11 +221,13 @@ __global__ void __launch_bounds__(kExThreads, 1)
             dr += sr;
             di += si;
           }
+          // FP32 across the warp (B300's FP64 pipe would cost more than the tile's MMAs
+          // leave to the epilogue), FP64 from the warp partials on
           for (int o = 16; o > 0; o >>= 1) {
             dr += __shfl_down_sync(0xffffffffu, dr, o);
             di += __shfl_down_sync(0xffffffffu, di, o);
           }
-          if (lane == 0) red[zl * kEpiWarps + q] = make_double2(dr, di);
+          if (lane == 0) red[zl * kEpiWarps + q] = make_double2((double)dr, (double)di);
         }
         epi_sync();  // Ts is rewritten for the next walkers
       }
