@@ -136,8 +136,15 @@ __global__ void k_slice_theta(const double2* __restrict__ thetaT, int W, int N, 
     const long z = zj / N;
     const double2 v = p < M ? thetaT[zj * M + p] : make_double2(0.0, 0.0);
     const long base = ((z * 2) * N + j) * Mpad + p;
-    split_bf16(v.x, S, out + base, plane);
-    split_bf16(v.y, S, out + base + (long)N * Mpad, plane);
+    if (S <= 3) {
+      // three bf16 slices hold 24 bits: split the FP32 rounding of theta on the FP32
+      // pipe (the FP64 remainders would run on B300's slow FP64 pipe)
+      split_bf16_f32(__double2float_rn(v.x), S, out + base, plane);
+      split_bf16_f32(__double2float_rn(v.y), S, out + base + (long)N * Mpad, plane);
+    } else {
+      split_bf16(v.x, S, out + base, plane);
+      split_bf16(v.y, S, out + base + (long)N * Mpad, plane);
+    }
   }
 }
 

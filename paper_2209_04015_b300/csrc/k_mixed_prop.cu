@@ -120,7 +120,6 @@ struct PropArgs {
   uint32_t tx_bytes, tmem_cols;
   const int* ea;          // row exponents of A: P - I per p, or V_z per (z, p)
   const int* eb;          // row exponents of T^T per (z, j)
-  const double2* phi_in;  // mode first: Phi (W x M x N)
   double2* accT;          // W x N x M FP64 accumulator of P T_n(A) P Phi, transposed
   double2* phi_out;       // mode last: Phi (W x M x N)
   double2* tout;          // W x N x M FP64: the next operand (sliced by the next kernel)
@@ -293,10 +292,8 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
           const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
           const long iphi = ((long)z * M + p) * N + j;  // [z][p][j]
           if (a.mode == kModeFirst) {
-            const double2 f = a.phi_in[iphi];
-            const double2 out = make_double2(dr + f.x, di + f.y);
-            a.accT[ia] = out;
-            a.tout[ia] = out;
+            // (P - I) Phi; the slicing pass adds Phi (FP64) and cuts u_0 = P Phi
+            a.accT[ia] = make_double2(dr, di);
           } else if (a.mode == kModeTerm) {
             // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k to
             // the FP64 Taylor sum
@@ -770,7 +767,6 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   a.tmem_cols = tmem_cols_for(S * a.BN);
   a.ea = ea;
   a.eb = ctx->e_t[b];
-  a.phi_in = ctx->ws.phi;
   a.accT = ctx->accT;
   a.phi_out = ctx->ws.phi;
   a.tout = ctx->tout;
@@ -842,11 +838,12 @@ int launch_propagate_tc(afq_ctx* ctx) {
   AFQ_LAUNCHED(ctx);
   int cur = 0, rc;
   if ((rc = slice_tout(ctx, cur)) != AFQ_OK) return rc;
-  // u_0 = P Phi = Phi + (P - I) Phi, also the first term of the sum
+  // u_0 = P Phi = Phi + (P - I) Phi, also the first term of the sum: the GEMM writes
+  // (P - I) Phi into the sum, the slicing pass adds Phi^T (in tout) and cuts u_0
   rc = launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeFirst);
   if (rc != AFQ_OK) return rc;
   cur = 1 - cur;
-  if ((rc = slice_tout(ctx, cur)) != AFQ_OK) return rc;
+  if ((rc = taylor_slice(ctx, cur, 1.0, 0, 1)) != AFQ_OK) return rc;
   const int n = ctx->p.taylor_order;
   double gk = 1.0;
   for (int k = 1; k <= n; ++k) {

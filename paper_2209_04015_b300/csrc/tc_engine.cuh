@@ -195,6 +195,16 @@ __device__ __forceinline__ void split_bf16(double x, int S, __nv_bfloat16* out, 
   }
 }
 
+// The same for an FP32 value (exact remainders in FP32; S <= 3 covers its 24 bits).
+__device__ __forceinline__ void split_bf16_f32(float x, int S, __nv_bfloat16* out, long plane) {
+  float r = x;
+  for (int s = 0; s < S; ++s) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(r);
+    out[s * plane] = h;
+    r -= __bfloat162float(h);
+  }
+}
+
 template <int S, class P>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
