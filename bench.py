@@ -40,7 +40,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 nominal: 148 SMs x 2032 MHz x ~4.15 flop
 # DRAM bytes (read + write) per launch of the dominant kernel, from one-pass ncu
 # captures of these exact workloads (profiles/exchange_fp64_c2.md,
 # profiles/exchange_tc_c3.md); None where no capture of the current kernel exists.
-TRAFFIC = {("fp64", "c2"): 10565888 + 0, ("split_bf16", "c3"): 574247168 + 10140928}
+TRAFFIC = {("fp64", "c2"): 10565888 + 0, ("split_bf16", "c3"): 572279808 + 10032128}
 SPLIT_PRODUCTS = 6          # bf16 slice products of the 3-slice exchange (s + t <= 2)
 
 
