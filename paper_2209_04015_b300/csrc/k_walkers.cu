@@ -266,18 +266,31 @@ __global__ void __launch_bounds__(ET) k_exchange_fp64(int M, int N, int na, int 
       Bs[j * lda + kk] = p0 + kk < M ? thz[(long)j * M + p0 + kk] : cmk(0.0, 0.0);
     }
     __syncthreads();
+    // the last chunk of a ragged M runs only over its valid orbitals (no FMAs on the
+    // zero padding: at M = 100 that was 28 of every 128)
+    const int kc = min(EKC, M - p0);
 #pragma unroll
     for (int k = 0; k < MAXO6; ++k) {
       const int o = tid + k * ET;
       if (o < total) {
         const int r = o / n, j = o % n;
         double2 a = acc[k];
+        if (kc == EKC) {
 #pragma unroll 8
-        for (int kk = 0; kk < EKC; ++kk) {
-          const double l = As[r * lda + kk];
-          const double2 t = Bs[j * lda + kk];
-          a.x = fma(l, t.x, a.x);
-          a.y = fma(l, t.y, a.y);
+          for (int kk = 0; kk < EKC; ++kk) {
+            const double l = As[r * lda + kk];
+            const double2 t = Bs[j * lda + kk];
+            a.x = fma(l, t.x, a.x);
+            a.y = fma(l, t.y, a.y);
+          }
+        } else {
+#pragma unroll 4
+          for (int kk = 0; kk < kc; ++kk) {
+            const double l = As[r * lda + kk];
+            const double2 t = Bs[j * lda + kk];
+            a.x = fma(l, t.x, a.x);
+            a.y = fma(l, t.y, a.y);
+          }
         }
         acc[k] = a;
       }
