@@ -207,11 +207,12 @@ __global__ void __launch_bounds__(256) k_vhs_fp64(int W, int X, int M, int Mp, d
 // each is read with the lanes running over p (coalesced), and the column chunk
 // of the current Taylor term is broadcast from shared memory.
 // ---------------------------------------------------------------------------
-template <int NC>
+template <int NC, int NCg>
 __device__ __forceinline__ void sym_apply_real(int M, int p, const double* __restrict__ S,
-                                               const double2* __restrict__ in, double2 out[NC]) {
+                                               const double2* __restrict__ in, int cb,
+                                               double2 out[NCg]) {
 #pragma unroll
-  for (int c = 0; c < NC; ++c) out[c] = cmk(0.0, 0.0);
+  for (int c = 0; c < NCg; ++c) out[c] = cmk(0.0, 0.0);
   int q = 0;
   for (; q + 4 <= M; q += 4) {
     double s[4];
@@ -220,8 +221,8 @@ __device__ __forceinline__ void sym_apply_real(int M, int p, const double* __res
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const double2 b = in[(q + u) * NC + c];
+      for (int c = 0; c < NCg; ++c) {
+        const double2 b = in[(q + u) * NC + cb + c];
         out[c].x = fma(s[u], b.x, out[c].x);
         out[c].y = fma(s[u], b.y, out[c].y);
       }
@@ -229,19 +230,21 @@ __device__ __forceinline__ void sym_apply_real(int M, int p, const double* __res
   for (; q < M; ++q) {
     const double sv = S[(long)q * M + p];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const double2 b = in[q * NC + c];
+    for (int c = 0; c < NCg; ++c) {
+      const double2 b = in[q * NC + cb + c];
       out[c].x = fma(sv, b.x, out[c].x);
       out[c].y = fma(sv, b.y, out[c].y);
     }
   }
 }
 
-template <int NC>
+// out[c] = sum_q S_qp in[q][cb + c] for a complex symmetric S (row p read as column p).
+template <int NC, int NCg>
 __device__ __forceinline__ void sym_apply_cplx(int M, int p, const double2* __restrict__ S,
-                                               const double2* __restrict__ in, double2 out[NC]) {
+                                               const double2* __restrict__ in, int cb,
+                                               double2 out[NCg]) {
 #pragma unroll
-  for (int c = 0; c < NC; ++c) out[c] = cmk(0.0, 0.0);
+  for (int c = 0; c < NCg; ++c) out[c] = cmk(0.0, 0.0);
   int q = 0;
   for (; q + 4 <= M; q += 4) {
     double2 s[4];
@@ -250,8 +253,8 @@ __device__ __forceinline__ void sym_apply_cplx(int M, int p, const double2* __re
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const double2 b = in[(q + u) * NC + c];
+      for (int c = 0; c < NCg; ++c) {
+        const double2 b = in[(q + u) * NC + cb + c];
         out[c].x = fma(s[u].x, b.x, fma(-s[u].y, b.y, out[c].x));
         out[c].y = fma(s[u].x, b.y, fma(s[u].y, b.x, out[c].y));
       }
@@ -259,65 +262,71 @@ __device__ __forceinline__ void sym_apply_cplx(int M, int p, const double2* __re
   for (; q < M; ++q) {
     const double2 sv = S[(long)q * M + p];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const double2 b = in[q * NC + c];
+    for (int c = 0; c < NCg; ++c) {
+      const double2 b = in[q * NC + cb + c];
       out[c].x = fma(sv.x, b.x, fma(-sv.y, b.y, out[c].x));
       out[c].y = fma(sv.x, b.y, fma(sv.y, b.x, out[c].y));
     }
   }
 }
 
-template <int NC>
+// K5 (FP64): Phi <- P T_n(A) P Phi for NC walker columns of one walker per CTA, the
+// current Taylor term in shared memory.  G threads share each row p (each owns NC/G
+// of the columns), so that G M threads fill whole warps for M not a multiple of 32.
+template <int NC, int G>
 __global__ void k_propagate_fp64(int M, int N, int order, const double* __restrict__ P,
                                  const double2* __restrict__ A, double2* __restrict__ phi) {
+  constexpr int NCg = NC / G;
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* cur = reinterpret_cast<double2*>(smraw);  // M x NC
   double2* nxt = cur + M * NC;
   double2* acc = nxt + M * NC;
-  const int z = blockIdx.y, c0 = blockIdx.x * NC, p = threadIdx.x;
+  const int z = blockIdx.y, c0 = blockIdx.x * NC, t = threadIdx.x;
+  const bool act = t < G * M;
+  const int p = act ? t % M : 0, cb = act ? (t / M) * NCg : 0;
   const double2* Az = A + (long)z * M * M;
   double2* phz = phi + (long)z * M * N;
-  if (p < M)
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      cur[p * NC + c] = c0 + c < N ? phz[(long)p * N + c0 + c] : cmk(0.0, 0.0);
+  for (int e = t; e < M * NC; e += blockDim.x) {
+    const int q = e / NC, c = e % NC;
+    cur[e] = c0 + c < N ? phz[(long)q * N + c0 + c] : cmk(0.0, 0.0);
+  }
   __syncthreads();
-  double2 r[NC];
-  if (p < M) {
-    sym_apply_real<NC>(M, p, P, cur, r);
+  double2 r[NCg];
+  if (act) {
+    sym_apply_real<NC, NCg>(M, p, P, cur, cb, r);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      acc[p * NC + c] = r[c];
-      nxt[p * NC + c] = r[c];
+    for (int c = 0; c < NCg; ++c) {
+      acc[p * NC + cb + c] = r[c];
+      nxt[p * NC + cb + c] = r[c];
     }
   }
   __syncthreads();
   {
-    double2* t = cur;
+    double2* tt = cur;
     cur = nxt;
-    nxt = t;
+    nxt = tt;
   }
   for (int k = 1; k <= order; ++k) {
     const double inv = 1.0 / k;
-    if (p < M) {
-      sym_apply_cplx<NC>(M, p, Az, cur, r);
+    if (act) {
+      sym_apply_cplx<NC, NCg>(M, p, Az, cur, cb, r);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const double2 t = cscale(r[c], inv);
-        nxt[p * NC + c] = t;
-        acc[p * NC + c] = cadd(acc[p * NC + c], t);
+      for (int c = 0; c < NCg; ++c) {
+        const double2 v = cscale(r[c], inv);
+        nxt[p * NC + cb + c] = v;
+        acc[p * NC + cb + c] = cadd(acc[p * NC + cb + c], v);
       }
     }
     __syncthreads();
-    double2* t = cur;
+    double2* tt = cur;
     cur = nxt;
-    nxt = t;
+    nxt = tt;
   }
-  if (p < M) {
-    sym_apply_real<NC>(M, p, P, acc, r);
+  if (act) {
+    sym_apply_real<NC, NCg>(M, p, P, acc, cb, r);
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (c0 + c < N) phz[(long)p * N + c0 + c] = r[c];
+    for (int c = 0; c < NCg; ++c)
+      if (c0 + cb + c < N) phz[(long)p * N + c0 + cb + c] = r[c];
   }
 }
 
@@ -397,21 +406,48 @@ int launch_vhs_fp64(afq_ctx* ctx) {
   return AFQ_OK;
 }
 
-template <int NC>
-int launch_propagate_nc(afq_ctx* ctx) {
-  const int threads = 32 * ((ctx->M + 31) / 32);
+template <int NC, int G>
+int launch_propagate_g(afq_ctx* ctx) {
+  const int threads = 32 * ((G * ctx->M + 31) / 32);
   const size_t smem = (size_t)3 * ctx->M * NC * sizeof(double2);
   static size_t configured = 0;
   if (smem > configured) {
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_propagate_fp64<NC>,
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_propagate_fp64<NC, G>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = smem;
   }
   dim3 grid((ctx->N + NC - 1) / NC, ctx->ws.W);
-  k_propagate_fp64<NC><<<grid, threads, smem, ctx->stream>>>(ctx->M, ctx->N, ctx->p.taylor_order,
-                                                             ctx->P, ctx->A, ctx->ws.phi);
+  k_propagate_fp64<NC, G><<<grid, threads, smem, ctx->stream>>>(
+      ctx->M, ctx->N, ctx->p.taylor_order, ctx->P, ctx->A, ctx->ws.phi);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
+}
+
+// Threads per row: the G (dividing NC, G M <= 1024) that leaves the fewest idle
+// lanes in the last warp.
+int propagate_rows_per_thread(int M, int NC) {
+  int best = 1;
+  double eff = 0.0;
+  for (int G = 1; G <= NC; G *= 2) {
+    if (G * M > 1024) break;
+    const double e = (double)(G * M) / (32.0 * ((G * M + 31) / 32));
+    if (e > eff + 1e-9) {
+      eff = e;
+      best = G;
+    }
+  }
+  return best;
+}
+
+template <int NC>
+int launch_propagate_nc(afq_ctx* ctx) {
+  switch (propagate_rows_per_thread(ctx->M, NC)) {
+    case 2: if (NC >= 2) return launch_propagate_g<NC, (NC >= 2 ? 2 : 1)>(ctx); break;
+    case 4: if (NC >= 4) return launch_propagate_g<NC, (NC >= 4 ? 4 : 1)>(ctx); break;
+    case 8: if (NC >= 8) return launch_propagate_g<NC, (NC >= 8 ? 8 : 1)>(ctx); break;
+    default: break;
+  }
+  return launch_propagate_g<NC, 1>(ctx);
 }
 
 // Column chunk NC (2, 4 or 8 walker columns per CTA) as chosen by the autotuner.
