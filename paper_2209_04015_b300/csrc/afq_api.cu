@@ -167,6 +167,8 @@ int free_walkers(afq_ctx* ctx) {
   dfree(&ctx->cmf);
   dfree(&ctx->A);
   dfree(&ctx->detR);
+  dfree(&ctx->fb64_part);
+  ctx->fb64_part_wx = 0;
   ctx->have_walkers = false;
   return AFQ_OK;
 }
@@ -479,6 +481,8 @@ int afq_init_walkers(afq_ctx* ctx, int W, const double* phi, const double* w) {
   // A holds i sqrt(dt) V per walker during a step and is the QR workspace after it
   AFQ_TRY(dalloc(ctx, &ctx->A, (size_t)W * M * (M > N ? M : N)));
   AFQ_TRY(dalloc(ctx, &ctx->detR, 2 * (size_t)W));
+  AFQ_TRY(dalloc(ctx, &ctx->fb64_part, (size_t)kFbSplitMax * W * ctx->X));
+  ctx->fb64_part_wx = (long)W * ctx->X;
   AFQ_CUDA(ctx, cudaMemsetAsync(ctx->xbar, 0, W * X * 16, ctx->stream));
   std::vector<double2> h;
   if (phi) {

@@ -42,6 +42,8 @@ __device__ __forceinline__ double2 cexp(double2 a) {
   return cmk(e * c, e * s);
 }
 
+constexpr int kFbSplitMax = 8;  // K splits of the FP64 force bias
+
 // ----------------------------------------------------------------------------
 // walker-set buffers: everything the overlap / force-bias / energy kernels need
 // ----------------------------------------------------------------------------
@@ -117,6 +119,8 @@ struct afq_ctx {
   double2* cmf = nullptr;    // W
   double2* A = nullptr;      // W x M x M  i sqrt(dt) V, symmetric
   double* detR = nullptr;    // W x 2
+  double2* fb64_part = nullptr;  // kFbSplitMax x W x X: K-split partials of the FP64 force bias
+  long fb64_part_wx = 0;         // W X the buffer was sized for
   double* emix = nullptr;    // 1
   int* flags = nullptr;      // [0] singular pivots, [1] non-finite values,
                              // [2] tensor-core pipeline time-outs

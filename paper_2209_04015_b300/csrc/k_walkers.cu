@@ -192,37 +192,55 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
 // K2 (FP64): c_zg = sum_k L~_g,k theta^T_z,k over k = (sigma, j, p), K = N M.
 // 32 g x 8 walkers per CTA, one complex output per thread.
 // ---------------------------------------------------------------------------
-constexpr int FG = 32, FZ = 8, FK = 64;
-__global__ void __launch_bounds__(256) k_force_bias_fp64(int X, int W, int K,
+constexpr int FG = 32, FZ = 16, FK = 64;
+__global__ void __launch_bounds__(256) k_force_bias_fp64(int X, int W, int K, int kchunk,
                                                          const double* __restrict__ Lt,
                                                          const double2* __restrict__ thetaT,
-                                                         double2* __restrict__ c) {
+                                                         double2* __restrict__ out) {
   __shared__ double As[FG][FK + 1];
   __shared__ double2 Bs[FZ][FK];
   const int g0 = blockIdx.x * FG, z0 = blockIdx.y * FZ;
-  const int tg = threadIdx.x % 32, tz = threadIdx.x / 32;
-  double2 acc = cmk(0.0, 0.0);
-  for (int k0 = 0; k0 < K; k0 += FK) {
+  const int tg = threadIdx.x % 32, tz = threadIdx.x / 32;  // walkers tz and tz + 8
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  double2 acc0 = cmk(0.0, 0.0), acc1 = cmk(0.0, 0.0);
+  for (int k0 = kb; k0 < ke; k0 += FK) {
     for (int e = threadIdx.x; e < FG * FK; e += 256) {
       const int r = e / FK, kk = e % FK;
-      As[r][kk] = (g0 + r < X && k0 + kk < K) ? Lt[(long)(g0 + r) * K + k0 + kk] : 0.0;
+      As[r][kk] = (g0 + r < X && k0 + kk < ke) ? Lt[(long)(g0 + r) * K + k0 + kk] : 0.0;
     }
     for (int e = threadIdx.x; e < FZ * FK; e += 256) {
       const int r = e / FK, kk = e % FK;
-      Bs[r][kk] = (z0 + r < W && k0 + kk < K) ? thetaT[(long)(z0 + r) * K + k0 + kk]
-                                              : cmk(0.0, 0.0);
+      Bs[r][kk] = (z0 + r < W && k0 + kk < ke) ? thetaT[(long)(z0 + r) * K + k0 + kk]
+                                               : cmk(0.0, 0.0);
     }
     __syncthreads();
-#pragma unroll 16
-    for (int kk = 0; kk < FK; ++kk) {
+    const int kc = min(FK, ke - k0);
+    for (int kk = 0; kk < kc; ++kk) {
       const double a = As[tg][kk];
-      const double2 b = Bs[tz][kk];
-      acc.x = fma(a, b.x, acc.x);
-      acc.y = fma(a, b.y, acc.y);
+      const double2 b0 = Bs[tz][kk], b1 = Bs[tz + 8][kk];
+      acc0.x = fma(a, b0.x, acc0.x);
+      acc0.y = fma(a, b0.y, acc0.y);
+      acc1.x = fma(a, b1.x, acc1.x);
+      acc1.y = fma(a, b1.y, acc1.y);
     }
     __syncthreads();
   }
-  if (g0 + tg < X && z0 + tz < W) c[(long)(z0 + tz) * X + g0 + tg] = acc;
+  // out: c (W x X) without a K split, else the partial sums [split][W][X]
+  double2* o = out + (long)blockIdx.z * W * X;
+  if (g0 + tg < X) {
+    if (z0 + tz < W) o[(long)(z0 + tz) * X + g0 + tg] = acc0;
+    if (z0 + tz + 8 < W) o[(long)(z0 + tz + 8) * X + g0 + tg] = acc1;
+  }
+}
+
+__global__ void k_fb64_reduce(long n, int ks, const double2* __restrict__ part,
+                              double2* __restrict__ c) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
+       e += (long)gridDim.x * blockDim.x) {
+    double2 v = part[e];
+    for (int k = 1; k < ks; ++k) v = cadd(v, part[(long)k * n + e]);
+    c[e] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -442,11 +460,30 @@ int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s) {
   return AFQ_OK;
 }
 
+// c = L~ theta over K = N M.  Small grids are split over K (partial sums reduced in a
+// fixed order, so the result does not depend on scheduling) when the walker set fits
+// the context's partial-sum buffer.
 int launch_force_bias_fp64(afq_ctx* ctx, WalkerSet& s) {
-  dim3 grid((ctx->X + FG - 1) / FG, (s.W + FZ - 1) / FZ);
-  k_force_bias_fp64<<<grid, 256, 0, ctx->stream>>>(ctx->X, s.W, ctx->N * ctx->M, ctx->Lt,
-                                                   s.thetaT, s.c);
+  const int K = ctx->N * ctx->M;
+  dim3 grid((ctx->X + FG - 1) / FG, (s.W + FZ - 1) / FZ, 1);
+  const long tiles = (long)grid.x * grid.y;
+  int ks = (int)((4 * 148 + tiles - 1) / tiles);
+  const int kblocks = (K + FK - 1) / FK;
+  if (ks > kblocks) ks = kblocks;
+  if (ks > kFbSplitMax) ks = kFbSplitMax;
+  if (ks < 1 || !ctx->fb64_part || (long)s.W * ctx->X > ctx->fb64_part_wx) ks = 1;
+  const int kchunk = ((kblocks + ks - 1) / ks) * FK;
+  ks = (K + kchunk - 1) / kchunk;
+  grid.z = ks;
+  k_force_bias_fp64<<<grid, 256, 0, ctx->stream>>>(ctx->X, s.W, K, kchunk, ctx->Lt, s.thetaT,
+                                                   ks > 1 ? ctx->fb64_part : s.c);
   AFQ_LAUNCHED(ctx);
+  if (ks > 1) {
+    const long n = (long)s.W * ctx->X;
+    k_fb64_reduce<<<(int)((n + 255) / 256 < 148 * 16 ? (n + 255) / 256 : 148 * 16), 256, 0,
+                    ctx->stream>>>(n, ks, ctx->fb64_part, s.c);
+    AFQ_LAUNCHED(ctx);
+  }
   return AFQ_OK;
 }
 
