@@ -25,6 +25,17 @@ __host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return cmk(a.x * s, a.y * s); }
+// acc + a b, acc - a b and acc + conj(a) b as four fused multiply-adds (the unfused
+// forms cost six FP64 operations, on a pipe that runs 2 lanes per clock per SM)
+__host__ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  return cmk(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 acc) {
+  return cmk(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ double2 cfma_conj(double2 a, double2 b, double2 acc) {
+  return cmk(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
 __host__ __device__ __forceinline__ double2 cconj(double2 a) { return cmk(a.x, -a.y); }
 __host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 __device__ __forceinline__ double cabs(double2 a) { return hypot(a.x, a.y); }

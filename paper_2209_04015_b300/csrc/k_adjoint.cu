@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(BT) k_bwd_dphi(int M, int N, int na, int nb,
     double2 sv = cmk(0.0, 0.0), wv = cmk(0.0, 0.0);
     for (int p = 0; p < M; ++p) {
       sv = cfma_r(psiT[(long)(off + i) * M + p], phz[(long)p * N + off + j], sv);
-      wv = cadd(wv, cmul(thz[(long)i * M + p], gbz[(long)j * M + p]));
+      wv = cfma(thz[(long)i * M + p], gbz[(long)j * M + p], wv);
     }
     aug[i * n2 + j] = sv;
     aug[i * n2 + n + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(BT) k_bwd_dphi(int M, int N, int na, int nb,
     __syncthreads();
     for (int e = tid; e < n * n2; e += BT) {
       const int r = e / n2, cc = e % n2;
-      if (r != kc) aug[e] = csub(aug[e], cmul(fac[r], aug[kc * n2 + cc]));
+      if (r != kc) aug[e] = cfms(fac[r], aug[kc * n2 + cc], aug[e]);
     }
     __syncthreads();
   }
@@ -166,9 +166,12 @@ __global__ void __launch_bounds__(BT) k_bwd_dphi(int M, int N, int na, int nb,
     double2 d = cmk(0.0, 0.0);
     for (int j = 0; j < n; ++j) {
       double2 y = gbz[(long)j * M + p];
-      for (int i = 0; i < n; ++i)
-        y = csub(y, cscale(W1[i * n + j], psiT[(long)(off + i) * M + p]));
-      d = cadd(d, cmul(y, aug[k * n2 + n + j]));  // (S^-1)_kj
+      for (int i = 0; i < n; ++i) {
+        const double2 wv = W1[i * n + j];
+        const double ps = psiT[(long)(off + i) * M + p];
+        y = cmk(fma(-wv.x, ps, y.x), fma(-wv.y, ps, y.y));
+      }
+      d = cfma(y, aug[k * n2 + n + j], d);  // (S^-1)_kj
     }
     double2* o = dphi + (long)z * M * N + (long)p * N + off + k;
     if (MODE == 0) *o = cmul(g, cconj(d));
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(BT) k_bwd_lfac(int M, int N, int na, int nb, i
         const int j = e / M, p = e % M;
         double2 v = cmul(wc, th[j * M + p]);
         double2 u = cmk(0.0, 0.0);
-        for (int i = 0; i < n; ++i) u = cadd(u, cmul(T[i * n + j], th[i * M + p]));
+        for (int i = 0; i < n; ++i) u = cfma(T[i * n + j], th[i * M + p], u);
         v = csub(v, cmul(wg, u));
         acc[k] = cadd(acc[k], v);
       }

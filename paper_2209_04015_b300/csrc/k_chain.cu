@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) k_bwd_qr(int M, int N, int na, int nb,
     double2 v = cmk(0.0, 0.0);
     if (i <= j)
       for (int p = 0; p < M; ++p)
-        v = cadd(v, cmul(cconj(Qz[(long)p * N + off + i]), Pz[(long)p * N + off + j]));
+        v = cfma_conj(Qz[(long)p * N + off + i], Pz[(long)p * N + off + j], v);
     R[e] = v;
   }
   __syncthreads();
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) k_bwd_qr(int M, int N, int na, int nb,
     double2* row = Lz + (long)p * N + off;
     for (int j = n - 1; j >= 0; --j) {
       double2 v = row[j];
-      for (int k = j + 1; k < n; ++k) v = csub(v, cmul(R[j * n + k], row[k]));
+      for (int k = j + 1; k < n; ++k) v = cfms(R[j * n + k], row[k], v);
       row[j] = cdiv(v, R[j * n + j]);
     }
   }

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
     __syncthreads();
     for (int e = tid; e < n * n2; e += OT) {
       const int r = e / n2, c = e % n2;
-      if (r != kc) aug[e] = csub(aug[e], cmul(fac[r], aug[kc * n2 + c]));
+      if (r != kc) aug[e] = cfms(fac[r], aug[kc * n2 + c], aug[e]);
     }
     __syncthreads();
   }
@@ -389,14 +389,14 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
       for (int i = wid; i < j; i += 8) {
         const double2* qi = Q + (long)i * M;
         double2 d = cmk(0.0, 0.0);
-        for (int p = lane; p < M; p += 32) d = cadd(d, cmul(cconj(qi[p]), v[p]));
+        for (int p = lane; p < M; p += 32) d = cfma_conj(qi[p], v[p], d);
         d = warp_sum2(d);
         if (lane == 0) rs[i] = d;
       }
       __syncthreads();
       for (int p = tid; p < M; p += 256) {
         double2 t = v[p];
-        for (int i = 0; i < j; ++i) t = csub(t, cmul(Q[(long)i * M + p], rs[i]));
+        for (int i = 0; i < j; ++i) t = cfms(Q[(long)i * M + p], rs[i], t);
         v[p] = t;
       }
       __syncthreads();
