@@ -186,7 +186,10 @@ const char* afq_kernel_name(int kernel);
      dL   (X x M x M)      = Re sum_z conj(g_z) (c_zg G_z - sum_s G^s_z L_g^T G^s_z)
      dphi (W x M x N cplx) = g_z conj(dE_z/dPhi_z) = dLoss/dRe Phi + i dLoss/dIm Phi
    h1 and L_g entries are treated as independent (no symmetrisation).  Any output
-   may be NULL.  Needs max(na, nb) * M <= 8192.  FP64 in both precision modes. */
+   may be NULL.  FP64 in both precision modes.  The first call with dphi keeps a
+   trial-fixed tensor of na^2 M^2 + nb^2 M^2 doubles on the device (released with the
+   trial); a dL request takes a temporary workspace of max(na, nb)^2 M^2 doubles.
+   AFQ_ERR_NOMEM when either cannot be allocated. */
 int afq_local_energy_backward(afq_ctx* ctx, const double* gE, double* dh1, double* dL,
                               double* dphi);
 int afq_local_energy_backward_dev(afq_ctx* ctx, const double* gE_dev, double* dh1_dev,
@@ -210,10 +213,13 @@ int afq_local_energy_backward_dev(afq_ctx* ctx, const double* gE_dev, double* dh
      dh1   (M x M)          symmetrised dLoss/dh1
      dL    (X x M x M)      symmetrised dLoss/dL_g
      dphi0 (W x M x N cplx) dLoss/dRe Phi^0 + i dLoss/dIm Phi^0
-   recomputing each segment from its checkpoint.  Any output may be NULL.  It fails
+   recomputing each segment from its checkpoint and keeping, for every step of the
+   longest segment, the walkers, i sqrt(dt) V and the taylor_order + 1 Taylor terms
+   (about (taylor_order + 2) W M N + W M^2 complex values per step) until it returns.
+   Any output may be NULL.  It fails
    with AFQ_ERR_STATE if the walkers changed after the forward (a step, QR, set_state
-   or init_walkers), and needs max(na, nb) * M <= 8192.  The context's walkers,
-   weights and force bias are left as the forward left them. */
+   or init_walkers).  The context's walkers, weights and force bias are left as the
+   forward left them. */
 int afq_chain_forward(afq_ctx* ctx, int K, const double* fields, double* e_out);
 int afq_chain_forward_dev(afq_ctx* ctx, int K, const double* fields_dev, double* e_out_dev);
 int afq_chain_backward(afq_ctx* ctx, const double* gE, double* dh1, double* dL, double* dphi0);

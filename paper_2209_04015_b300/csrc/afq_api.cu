@@ -181,6 +181,7 @@ int free_trial(afq_ctx* ctx) {
   dfree(&ctx->vbar);
   dfree(&ctx->hpp);
   dfree(&ctx->P);
+  dfree(&ctx->bwdV);
   ctx->have_trial = false;
   return free_walkers(ctx);
 }

@@ -163,6 +163,9 @@ struct afq_ctx {
   CUtensorMap tm_vhs_a, tm_vhs_b, tm_pm, tm_az, tm_t[2];
 
   ChainTape chain;  // afq_chain_forward
+  // local-energy adjoint: V_s[(j,p),(i,q)] = sum_g L~_g,s[j][q] L~_g,s[i][p] per spin
+  // (alpha block, then beta block), built on first use and kept with the trial
+  double* bwdV = nullptr;
 
   // built-in profiler: event pairs around launches of each kernel class
   bool profiling = false;

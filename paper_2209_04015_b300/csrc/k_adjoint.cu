@@ -3,86 +3,46 @@
 //
 // The paper leaves automatic differentiation to future work (Sec. "Customized
 // mixed estimators"); these are the closed forms of its local energy
-// (Sec. "Local energy"), theta = Phi (Psi^T Phi)^-1, G^s = Psi_s theta_s^T:
-//   dLoss/dh1  = Re sum_z conj(g_z) G_z = Psi Re(Theta),  Theta_s = sum_z conj(g_z) theta_s,z^T
+// (Sec. "Local energy"), theta = Phi (Psi^T Phi)^-1, G^s = Psi_s theta_s^T,
+// w_z = conj(g_z):
+//   dLoss/dh1  = Re sum_z w_z G_z = Psi Re(Theta),  Theta_s = sum_z w_z theta_s,z^T
 //   dLoss/dL_g = Re sum_s Psi_s F_g,s,
-//                F_g,s = sum_z conj(g_z) (c_zg theta_s,z^T - T_zg,s^T theta_s,z^T),
+//                F_g,s = sum_z w_z (c_zg theta_s,z^T - T_zg,s^T theta_s,z^T),
 //                T_zg,s = L~_g,s theta_s,z
 //   dLoss/dPhi_s = g conj((I - Psi_s theta_s^T) Gbar_s S_s^-T),
 //                Gbar_s = h~_s^T + (sum_g c_g L~_g,s)^T - (sum_g T_g,s L~_g,s)^T
-// Like the forward exchange, T is rebuilt per (walker, g) in shared memory and never
-// stored.  Accumulators live in registers: n_s M <= 8192 per spin.
+// The two terms with T are contracted without forming T (index pairs (j,p) run over
+// the n_s x M entries of theta^T, row-major):
+//   (sum_g T_zg L~_g)^T[(j,p)] = sum_(i,q) V[(j,p),(i,q)] theta^T_z[(i,q)],
+//        V[(j,p),(i,q)] = sum_g L~_g[j][q] L~_g[i][p]   (symmetric; trial-fixed, cached)
+//   (sum_z w_z T_zg^T theta_z^T)[(j,p)] = sum_(i,q) L~_g[(i,q)] Y[(i,q),(j,p)],
+//        Y[(i,q),(j,p)] = sum_z w_z theta^T_z[j][q] theta^T_z[i][p]   (symmetric)
+// so both become FP64 GEMMs of (n_s M)^2 size: W (n_s M)^2 and X (n_s M)^2
+// multiply-adds instead of W X n_s^2 M per pass over T.
 #include "afq_internal.cuh"
 
 namespace {
 
 constexpr int BT = 256;
-constexpr int MAXE = 32;  // accumulator elements per thread: n M <= BT * MAXE
 
 __device__ __forceinline__ double2 cfma_r(double a, double2 b, double2 acc) {
   return cmk(fma(a, b.x, acc.x), fma(a, b.y, acc.y));
 }
 
-// ---------------------------------------------------------------------------
-// Gbar^T_z[j][p] for one (walker, spin): loops over every g.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(BT) k_bwd_gbar(int M, int N, int na, int nb, int X,
-                                                 const double* __restrict__ Lt,
-                                                 const double* __restrict__ ht,
-                                                 const double2* __restrict__ thetaT,
-                                                 const double2* __restrict__ c,
-                                                 double2* __restrict__ gbarT) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int z = blockIdx.x, s = blockIdx.y, tid = threadIdx.x;
-  const int n = s ? nb : na, off = s ? na : 0;
-  if (n == 0) return;
-  const int nM = n * M;
-  double2* th = reinterpret_cast<double2*>(smraw);  // n x M
-  double2* T = th + nM;                             // n x n
-  double* Lg = reinterpret_cast<double*>(T + n * n);  // n x M
-  for (int e = tid; e < nM; e += BT) th[e] = thetaT[((long)z * N + off) * M + e];
-  double2 acc[MAXE];
-#pragma unroll
-  for (int k = 0; k < MAXE; ++k) acc[k] = cmk(0.0, 0.0);
-  __syncthreads();
-  for (int g = 0; g < X; ++g) {
-    for (int e = tid; e < nM; e += BT) Lg[e] = Lt[((long)g * N + off) * M + e];
-    __syncthreads();
-    // T_ij = sum_p L~_ip theta_pj = sum_p Lg[i][p] th[j][p]
-    for (int e = tid; e < n * n; e += BT) {
-      const int i = e / n, j = e % n;
-      double2 t = cmk(0.0, 0.0);
-      for (int p = 0; p < M; ++p) t = cfma_r(Lg[i * M + p], th[j * M + p], t);
-      T[i * n + j] = t;
-    }
-    __syncthreads();
-    const double2 cg = c[(long)z * X + g];
-#pragma unroll
-    for (int k = 0; k < MAXE; ++k) {
-      const int e = tid + k * BT;
-      if (e < nM) {
-        const int j = e / M, p = e % M;
-        double2 a = acc[k];
-        const double l = Lg[j * M + p];
-        a = cmk(fma(cg.x, l, a.x), fma(cg.y, l, a.y));
-        for (int i = 0; i < n; ++i) {
-          const double2 tji = T[j * n + i];
-          const double li = Lg[i * M + p];
-          a = cmk(fma(-tji.x, li, a.x), fma(-tji.y, li, a.y));
-        }
-        acc[k] = a;
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int k = 0; k < MAXE; ++k) {
-    const int e = tid + k * BT;
-    if (e < nM) {
-      const double h = ht[(long)off * M + e];
-      gbarT[((long)z * N + off) * M + e] = cmk(acc[k].x + h, acc[k].y);
-    }
-  }
+// Gbar^T_z[e] = h~[e] for every walker (both spins; e < N M), the first term of Gbar
+__global__ void k_bwd_gbar_init(long W, long NM, const double* __restrict__ ht,
+                                double2* __restrict__ gbarT) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < W * NM;
+       e += (long)gridDim.x * blockDim.x)
+    gbarT[e] = cmk(ht[e % NM], 0.0);
+}
+
+// out[z n + e] = conj(g_z) in[z n + e]: the walker-weighted operands of dL
+__global__ void k_bwd_weight(long W, long n, const double2* __restrict__ gE,
+                             const double2* __restrict__ in, double2* __restrict__ out) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < W * n;
+       e += (long)gridDim.x * blockDim.x)
+    out[e] = cmul(cconj(gE[e / n]), in[e]);
 }
 
 // ---------------------------------------------------------------------------
@@ -195,68 +155,25 @@ __global__ void k_bwd_theta_sum(int W, long NM, const double2* __restrict__ thet
   }
 }
 
-// Re F_g,s[j][p] for one (g, spin), added to F: loops over every walker.
-__global__ void __launch_bounds__(BT) k_bwd_lfac(int M, int N, int na, int nb, int X, int W,
-                                                 const double* __restrict__ Lt,
-                                                 const double2* __restrict__ thetaT,
-                                                 const double2* __restrict__ c,
-                                                 const double2* __restrict__ gE,
-                                                 double* __restrict__ F) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int g = blockIdx.x, s = blockIdx.y, tid = threadIdx.x;
-  const int n = s ? nb : na, off = s ? na : 0;
-  if (n == 0) return;
-  const int nM = n * M;
-  double2* th = reinterpret_cast<double2*>(smraw);    // n x M
-  double2* T = th + nM;                               // n x n
-  double* Lg = reinterpret_cast<double*>(T + n * n);  // n x M
-  for (int e = tid; e < nM; e += BT) Lg[e] = Lt[((long)g * N + off) * M + e];
-  double2 acc[MAXE];
-#pragma unroll
-  for (int k = 0; k < MAXE; ++k) acc[k] = cmk(0.0, 0.0);
-  for (int z = 0; z < W; ++z) {
-    __syncthreads();
-    for (int e = tid; e < nM; e += BT) th[e] = thetaT[((long)z * N + off) * M + e];
-    __syncthreads();
-    for (int e = tid; e < n * n; e += BT) {
-      const int i = e / n, j = e % n;
-      double2 t = cmk(0.0, 0.0);
-      for (int p = 0; p < M; ++p) t = cfma_r(Lg[i * M + p], th[j * M + p], t);
-      T[i * n + j] = t;
-    }
-    __syncthreads();
-    const double2 wg = cconj(gE[z]);
-    const double2 wc = cmul(wg, c[(long)z * X + g]);
-#pragma unroll
-    for (int k = 0; k < MAXE; ++k) {
-      const int e = tid + k * BT;
-      if (e < nM) {
-        const int j = e / M, p = e % M;
-        double2 v = cmul(wc, th[j * M + p]);
-        double2 u = cmk(0.0, 0.0);
-        for (int i = 0; i < n; ++i) u = cfma(T[i * n + j], th[i * M + p], u);
-        v = csub(v, cmul(wg, u));
-        acc[k] = cadd(acc[k], v);
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < MAXE; ++k) {
-    const int e = tid + k * BT;
-    if (e < nM) F[((long)g * N + off) * M + e] += acc[k].x;
-  }
+int bwd_grid(long n, int threads) {
+  const long g = (n + threads - 1) / threads;
+  return (int)(g < 148 * 16 ? (g < 1 ? 1 : g) : 148 * 16);
 }
 
-size_t bwd_smem(int n, int M) { return (size_t)n * M * 24 + (size_t)n * n * 16 + 16; }
+// counts one launch and reports a launch error without returning early (the caller
+// still frees its workspaces)
+int launched(afq_ctx* ctx) {
+  ctx->launches++;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? AFQ_OK
+                          : afq_fail(ctx, AFQ_ERR_CUDA, std::string("kernel launch: ") +
+                                                            cudaGetErrorString(e));
+}
+
 size_t dphi_smem(int n) { return (size_t)n * 2 * n * 16 + (size_t)n * n * 16 + (size_t)n * 16; }
 
-int configure_bwd(afq_ctx* ctx, size_t smem, size_t sm2) {
-  static size_t configured = 0, configured2 = 0;
-  if (smem > configured) {
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_gbar, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_lfac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+int configure_bwd(afq_ctx* ctx, size_t sm2) {
+  static size_t configured2 = 0;
   if (sm2 > configured2) {
     AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_dphi<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
     AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_dphi<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
@@ -286,48 +203,122 @@ int launch_bwd_dphi(afq_ctx* ctx, WalkerSet& t, const double2* gbarT, const doub
 
 }  // namespace
 
+// V_s[(j,p),(i,q)] = sum_g L~_g,s[j][q] L~_g,s[i][p] for both spins, once per trial:
+// for each j, one GEMM batched over i gives the M x M block (p, q) = A_i^T A_j with
+// A_i = L~_g,s[i][.] over g (X x M).
+int build_bwd_v(afq_ctx* ctx) {
+  if (ctx->bwdV) return AFQ_OK;
+  const int M = ctx->M, N = ctx->N, X = ctx->X;
+  const long NM = (long)N * M;
+  const long nMa = (long)ctx->na * M, nMb = (long)ctx->nb * M;
+  if (cudaMalloc((void**)&ctx->bwdV, (size_t)(nMa * nMa + nMb * nMb) * sizeof(double)) !=
+      cudaSuccess) {
+    ctx->bwdV = nullptr;
+    return afq_fail(ctx, AFQ_ERR_NOMEM, "local-energy backward: V tensor");
+  }
+  for (int s = 0; s < 2; ++s) {
+    const int n = s ? ctx->nb : ctx->na, off = s ? ctx->na : 0;
+    const long nM = (long)n * M;
+    double* V = ctx->bwdV + (s ? nMa * nMa : 0);
+    for (int j = 0; j < n; ++j)
+      AFQ_TRY(launch_dgemm(ctx, M, M, X, 1.0, ctx->Lt + (long)off * M, 1, NM, M,
+                           ctx->Lt + (long)(off + j) * M, NM, 1, 0, 0.0, V + j * M * nM, nM, 1,
+                           M, n, 1));
+  }
+  return AFQ_OK;
+}
+
 int adjoint_energy_core(afq_ctx* ctx, WalkerSet& t, const double2* gE, double* dh1, double* F,
                         double2* out, int mode) {
   const int M = ctx->M, N = ctx->N, X = ctx->X, W = t.W;
+  const long NM = (long)N * M;
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
-  if ((long)nmax * M > (long)BT * MAXE)
-    return afq_fail(ctx, AFQ_ERR_ARG, "local-energy backward needs max(na, nb) * M <= 8192");
-  const size_t smem = bwd_smem(nmax, M);
-  if (smem > 220 * 1024) return afq_fail(ctx, AFQ_ERR_ARG, "local-energy backward: shared memory");
-  AFQ_TRY(configure_bwd(ctx, smem, dphi_smem(nmax)));
-  double2* buf = nullptr;  // Gbar^T (W x N x M complex), then Theta (N x M reals)
-  if (cudaMalloc((void**)&buf, (size_t)W * N * M * sizeof(double2)) != cudaSuccess)
-    return afq_fail(ctx, AFQ_ERR_NOMEM, "local-energy backward workspace");
+  if (nmax > 64)
+    return afq_fail(ctx, AFQ_ERR_ARG, "local-energy backward needs max(na, nb) <= 64");
+  AFQ_TRY(configure_bwd(ctx, dphi_smem(nmax)));
+  if (out) AFQ_TRY(build_bwd_v(ctx));
+  const long nmM = (long)nmax * M;
+  // buf: Gbar^T (W x N x M complex), then Theta (N x M reals); for dL also
+  // u = conj(g) theta^T (W x N x M complex), q = conj(g) c (W x X complex) and
+  // Y (n_s M x n_s M, one spin at a time)
+  double2 *buf = nullptr, *u = nullptr, *q = nullptr;
+  double* Y = nullptr;
   int rc = AFQ_OK;
-  if (out) {
-    k_bwd_gbar<<<dim3(W, 2), BT, smem, ctx->stream>>>(M, N, ctx->na, ctx->nb, X, ctx->Lt, ctx->ht,
-                                                      t.thetaT, t.c, buf);
-    ctx->launches++;
-    rc = launch_bwd_dphi(ctx, t, buf, gE, out, mode);
-    if (rc == AFQ_OK && cudaGetLastError() != cudaSuccess)
-      rc = afq_fail(ctx, AFQ_ERR_CUDA, "backward dPhi launch");
+  if ((out || dh1) && cudaMalloc((void**)&buf, (size_t)W * NM * sizeof(double2)) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_NOMEM, "local-energy backward workspace");
+  if (rc == AFQ_OK && F &&
+      (cudaMalloc((void**)&u, (size_t)W * NM * sizeof(double2)) != cudaSuccess ||
+       cudaMalloc((void**)&q, (size_t)W * X * sizeof(double2)) != cudaSuccess ||
+       cudaMalloc((void**)&Y, (size_t)nmM * nmM * sizeof(double)) != cudaSuccess))
+    rc = afq_fail(ctx, AFQ_ERR_NOMEM, "local-energy backward dL workspace");
+  const double* th = reinterpret_cast<const double*>(t.thetaT);
+  if (rc == AFQ_OK && out) {
+    double* gb = reinterpret_cast<double*>(buf);
+    k_bwd_gbar_init<<<bwd_grid((long)W * NM, 256), 256, 0, ctx->stream>>>(W, NM, ctx->ht, buf);
+    rc = launched(ctx);
+    for (int s = 0; s < 2 && rc == AFQ_OK; ++s) {
+      const int n = s ? ctx->nb : ctx->na, off = s ? ctx->na : 0;
+      if (n == 0) continue;
+      const long nM = (long)n * M, o2 = 2L * off * M;
+      const double* V = ctx->bwdV + (s ? (long)ctx->na * M * ctx->na * M : 0);
+      // Gbar^T += sum_g c_zg L~_g (re and im rows as a batch of two)
+      rc = launch_dgemm(ctx, W, (int)nM, X, 1.0, reinterpret_cast<const double*>(t.c), 2L * X, 2,
+                        1, ctx->Lt + (long)off * M, NM, 1, 0, 1.0, gb + o2, 2 * NM, 2, 1, 2, 1);
+      // Gbar^T -= theta^T V
+      if (rc == AFQ_OK)
+        rc = launch_dgemm(ctx, W, (int)nM, (int)nM, -1.0, th + o2, 2 * NM, 2, 1, V, nM, 1, 0, 1.0,
+                          gb + o2, 2 * NM, 2, 1, 2, 1);
+    }
+    if (rc == AFQ_OK) rc = launch_bwd_dphi(ctx, t, buf, gE, out, mode);
   }
   if (dh1 && rc == AFQ_OK) {
     double* theta_sum = reinterpret_cast<double*>(buf);  // N x M reals (after the dPhi kernels)
-    const long NM = (long)N * M;
     k_bwd_theta_sum<<<(int)((NM + 255) / 256), 256, 0, ctx->stream>>>(W, NM, t.thetaT, gE,
                                                                       theta_sum);
-    ctx->launches++;
-    if (cudaGetLastError() != cudaSuccess) rc = afq_fail(ctx, AFQ_ERR_CUDA, "backward dh1 launch");
+    rc = launched(ctx);
     // dh1 = Psi (M x N) Re(Theta) (N x M); Psi(p, j) = psiT[j M + p]
     if (rc == AFQ_OK)
-      rc = launch_dgemm(ctx, M, M, N, 1.0, ctx->psiT, 1, M, 0, theta_sum, M, 1, 0, 0.0, dh1, M, 1, 0,
-                        1, 1);
+      rc = launch_dgemm(ctx, M, M, N, 1.0, ctx->psiT, 1, M, 0, theta_sum, M, 1, 0, 0.0, dh1, M, 1,
+                        0, 1, 1);
   }
   if (F && rc == AFQ_OK) {
-    k_bwd_lfac<<<dim3(X, 2), BT, smem, ctx->stream>>>(M, N, ctx->na, ctx->nb, X, W, ctx->Lt,
-                                                      t.thetaT, t.c, gE, F);
+    k_bwd_weight<<<bwd_grid((long)W * NM, 256), 256, 0, ctx->stream>>>(W, NM, gE, t.thetaT, u);
+    k_bwd_weight<<<bwd_grid((long)W * X, 256), 256, 0, ctx->stream>>>(W, X, gE, t.c, q);
     ctx->launches++;
-    if (cudaGetLastError() != cudaSuccess) rc = afq_fail(ctx, AFQ_ERR_CUDA, "k_bwd_lfac");
+    rc = launched(ctx);
+    const double* ur = reinterpret_cast<const double*>(u);
+    const double* qr = reinterpret_cast<const double*>(q);
+    for (int s = 0; s < 2 && rc == AFQ_OK; ++s) {
+      const int n = s ? ctx->nb : ctx->na, off = s ? ctx->na : 0;
+      if (n == 0) continue;
+      const long nM = (long)n * M, o2 = 2L * off * M;
+      double* Fs = F + (long)off * M;
+      // F += Re sum_z q_zg theta^T_z
+      rc = launch_dgemm(ctx, X, (int)nM, W, 1.0, qr, 2, 2L * X, 0, th + o2, 2 * NM, 2, 0, 1.0, Fs,
+                        NM, 1, 0, 1, 1);
+      if (rc == AFQ_OK)
+        rc = launch_dgemm(ctx, X, (int)nM, W, -1.0, qr + 1, 2, 2L * X, 0, th + o2 + 1, 2 * NM, 2,
+                          0, 1.0, Fs, NM, 1, 0, 1, 1);
+      // Y: for each j, the blocks (q, p) of every i: Re sum_z u_z[j][q] theta_z[i][p]
+      for (int j = 0; j < n && rc == AFQ_OK; ++j)
+        for (int ri = 0; ri < 2 && rc == AFQ_OK; ++ri)
+          rc = launch_dgemm(ctx, M, M, W, ri ? -1.0 : 1.0, ur + 2L * (off + j) * M + ri, 2, 2 * NM,
+                            0, th + o2 + ri, 2 * NM, 2, 2L * M, ri ? 1.0 : 0.0, Y + (long)j * M,
+                            nM, 1, (long)M * nM, n, 1);
+      // F -= L~ Y
+      if (rc == AFQ_OK)
+        rc = launch_dgemm(ctx, X, (int)nM, (int)nM, -1.0, ctx->Lt + (long)off * M, NM, 1, 0, Y,
+                          nM, 1, 0, 1.0, Fs, NM, 1, 0, 1, 1);
+    }
   }
-  // the workspace is released only after the kernels that read it are done
+  if (rc == AFQ_OK && cudaGetLastError() != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "local-energy backward launch");
+  // the workspaces are released only after the kernels that read them are done
   cudaStreamSynchronize(ctx->stream);
-  cudaFree(buf);
+  if (buf) cudaFree(buf);
+  if (u) cudaFree(u);
+  if (q) cudaFree(q);
+  if (Y) cudaFree(Y);
   return rc;
 }
 
@@ -335,7 +326,8 @@ int adjoint_energy_core(afq_ctx* ctx, WalkerSet& t, const double2* gE, double* d
 // the cotangent of theta stored transposed like thetaT).
 int launch_bwd_theta(afq_ctx* ctx, WalkerSet& t, const double2* lamT, double2* lam) {
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
-  AFQ_TRY(configure_bwd(ctx, bwd_smem(nmax, ctx->M), dphi_smem(nmax)));
+  if (nmax > 64) return afq_fail(ctx, AFQ_ERR_ARG, "adjoint needs max(na, nb) <= 64");
+  AFQ_TRY(configure_bwd(ctx, dphi_smem(nmax)));
   return launch_bwd_dphi(ctx, t, lamT, nullptr, lam, 2);
 }
 

@@ -285,14 +285,46 @@ __global__ void k_dl_assemble(int X, int M, int Mp, const double* __restrict__ D
   }
 }
 
-// out = sym(a + b)
+// out = sym(a + b); b may be NULL
 __global__ void k_sym_sum(int M, const double* __restrict__ a, const double* __restrict__ b,
                           double* __restrict__ out) {
   const long n = (long)M * M;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
        e += (long)gridDim.x * blockDim.x) {
     const int p = (int)(e / M), q = (int)(e % M);
-    out[e] = 0.5 * (a[(long)p * M + q] + a[(long)q * M + p] + b[(long)p * M + q] + b[(long)q * M + p]);
+    const long et = (long)q * M + p;
+    out[e] = 0.5 * (a[e] + a[et] + (b ? b[e] + b[et] : 0.0));
+  }
+}
+
+// q[(z X + g) 2 + ri] = sum_ks part[((ri ksplit + ks) W + z) X + g]  (fixed order)
+__global__ void k_q_reduce(long WX, int ksplit, const double* __restrict__ part,
+                           double* __restrict__ q) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < 2 * WX;
+       e += (long)gridDim.x * blockDim.x) {
+    const int ri = (int)(e / WX);
+    const long zg = e % WX;
+    double s = 0.0;
+    for (int ks = 0; ks < ksplit; ++ks) s += part[((long)ri * ksplit + ks) * WX + zg];
+    q[2 * zg + ri] = s;
+  }
+}
+
+// lv_g += <L_g, a> over the M x M entries (one block per g, fixed-order reduction)
+__global__ void __launch_bounds__(256) k_dot_rows(long MM, const double* __restrict__ L,
+                                                  const double* __restrict__ a,
+                                                  double* __restrict__ lv) {
+  __shared__ double red[8];
+  const int g = blockIdx.x;
+  double v = 0.0;
+  for (long e = threadIdx.x; e < MM; e += 256) v = fma(L[(long)g * MM + e], a[e], v);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    lv[g] += t;
   }
 }
 
@@ -323,6 +355,7 @@ struct ChainWork {
   double2 *A = nullptr, *xbar = nullptr, *y = nullptr, *cfb = nullptr, *cmf = nullptr;
   double *Ppart = nullptr, *Pbar = nullptr, *F = nullptr, *Lpkb = nullptr, *lv = nullptr;
   double *dh1E = nullptr, *hb = nullptr, *Pt = nullptr, *Z = nullptr, *D = nullptr;
+  double *qpart = nullptr, *hs = nullptr;
   WalkerSet ws;
   std::vector<void*> owned;
 };
@@ -354,28 +387,61 @@ int add_re_outer(afq_ctx* ctx, ChainWork& w, const double2* Xm, const double2* Y
   return AFQ_OK;
 }
 
-// Backward of one step at walkers phi_in with fields xi: lam (cotangent of the
-// step's output before any QR) becomes the cotangent of phi_in; Pbar, F, Lpkb and lv
-// accumulate.
-int step_backward(afq_ctx* ctx, ChainWork& w, double2* phi_in, const double* xi) {
-  const int M = ctx->M, N = ctx->N, X = ctx->X, W = ctx->chain.W, Mp = ctx->Mp;
-  const int n = ctx->p.taylor_order;
-  const long MN = (long)M * N, WMN = (long)W * MN, MM = (long)M * M, NM = (long)N * M;
-  const long RT = (long)(n + 1) * N, RU = (long)n * N;
-  const double dt = ctx->p.dt, sdt = std::sqrt(dt);
+constexpr int QSPLIT = 4;  // K split of the Q = <Abar, L_g> contraction (load balance)
+
+// The step's operands live in per-step slots of the segment: i sqrt(dt) V (ctx->A),
+// the shifted fields y and the Taylor tape t_0 .. t_n.
+void point_step(afq_ctx* ctx, ChainWork& w, int i) {
+  const long W = ctx->chain.W, MM = (long)ctx->M * ctx->M;
+  ctx->A = w.A + i * W * MM;
+  ctx->y = w.y + i * W * ctx->X;
+}
+double2* tape_of(afq_ctx* ctx, ChainWork& w, int i) {
+  return w.T + (long)i * (ctx->p.taylor_order + 1) * ctx->chain.W * ctx->M * ctx->N;
+}
+
+// Recompute step i of a segment from phi_in (fields xi) into phi_out, keeping its
+// operands for the backward: t_0 = P phi_in (real P on re/im interleaved rows),
+// t_k = A t_{k-1} / k, phi_out = P sum_k t_k.
+int forward_tape(afq_ctx* ctx, ChainWork& w, int i, double2* phi_in, const double* xi,
+                 double2* phi_out) {
+  const int M = ctx->M, N = ctx->N, W = ctx->chain.W, n = ctx->p.taylor_order;
+  const long MN = (long)M * N, WMN = (long)W * MN, MM = (long)M * M, RT = (long)(n + 1) * N;
+  double2* T = tape_of(ctx, w, i);
+  point_step(ctx, w, i);
   ctx->ws.phi = phi_in;
   AFQ_TRY(launch_overlap_theta(ctx, ctx->ws));
   AFQ_TRY(launch_force_bias_fp64(ctx, ctx->ws));
   AFQ_TRY(launch_fields(ctx, xi));
   AFQ_TRY(launch_vhs_fp64(ctx));
-  // forward tape: t_0 = P phi_in (real P on re/im interleaved rows), t_k = A t_{k-1} / k
   AFQ_TRY(launch_dgemm(ctx, M, 2 * N, M, 1.0, ctx->P, M, 1, 0, reinterpret_cast<double*>(phi_in),
-                       2 * N, 1, 2 * MN, 0.0, reinterpret_cast<double*>(w.T), 2 * RT, 1, 2 * M * RT,
+                       2 * N, 1, 2 * MN, 0.0, reinterpret_cast<double*>(T), 2 * RT, 1, 2 * M * RT,
                        W, 1));
   for (int k = 1; k <= n; ++k)
-    AFQ_TRY(launch_zgemm(ctx, M, N, M, 1.0 / k, ctx->A, M, 1, MM, w.T + (long)(k - 1) * N, RT, 1,
-                         M * RT, nullptr, 0, 0, 0, 0.0, w.T + (long)k * N, RT, 1, M * RT, W));
-  k_sum_blocks<<<grid_of(WMN), 256, 0, ctx->stream>>>((long)W * M, N, n + 1, w.T, w.phi2);
+    AFQ_TRY(launch_zgemm(ctx, M, N, M, 1.0 / k, ctx->A, M, 1, MM, T + (long)(k - 1) * N, RT, 1,
+                         M * RT, nullptr, 0, 0, 0, 0.0, T + (long)k * N, RT, 1, M * RT, W));
+  k_sum_blocks<<<grid_of(WMN), 256, 0, ctx->stream>>>((long)W * M, N, n + 1, T, w.phi2);
+  AFQ_LAUNCHED(ctx);
+  AFQ_TRY(launch_dgemm(ctx, M, 2 * N, M, 1.0, ctx->P, M, 1, 0, reinterpret_cast<double*>(w.phi2),
+                       2 * N, 1, 2 * MN, 0.0, reinterpret_cast<double*>(phi_out), 2 * N, 1, 2 * MN,
+                       W, 1));
+  return AFQ_OK;
+}
+
+// Backward of step i of a segment at walkers phi_in (its operands kept by
+// forward_tape): lam (cotangent of the step's output before any QR) becomes the
+// cotangent of phi_in; Pbar, F, Lpkb and lv accumulate.
+int step_backward(afq_ctx* ctx, ChainWork& w, double2* phi_in, int i) {
+  const int M = ctx->M, N = ctx->N, X = ctx->X, W = ctx->chain.W, Mp = ctx->Mp;
+  const int n = ctx->p.taylor_order;
+  const long MN = (long)M * N, WMN = (long)W * MN, MM = (long)M * M, NM = (long)N * M;
+  const long RT = (long)(n + 1) * N, RU = (long)n * N;
+  const double dt = ctx->p.dt, sdt = std::sqrt(dt);
+  double2* T = tape_of(ctx, w, i);
+  point_step(ctx, w, i);
+  ctx->ws.phi = phi_in;
+  AFQ_TRY(launch_overlap_theta(ctx, ctx->ws));  // theta at phi_in
+  k_sum_blocks<<<grid_of(WMN), 256, 0, ctx->stream>>>((long)W * M, N, n + 1, T, w.phi2);
   AFQ_LAUNCHED(ctx);
   // outer P: lam2 = P lam, Pbar += Re lam Phi2^T
   AFQ_TRY(launch_dgemm(ctx, M, 2 * N, M, 1.0, ctx->P, M, 1, 0, reinterpret_cast<double*>(w.lam),
@@ -396,21 +462,24 @@ int step_backward(afq_ctx* ctx, ChainWork& w, double2* phi_in, const double* xi)
                            MN, 0.0, w.mu0, N, 1, MN, W));
   }
   // Abar = [mu_1/1 .. mu_n/n] [t_0 .. t_{n-1}]^T
-  AFQ_TRY(launch_zgemm(ctx, M, M, n * N, 1.0, w.U, RU, 1, M * RU, w.T, 1, RT, M * RT, nullptr, 0, 0,
+  AFQ_TRY(launch_zgemm(ctx, M, M, n * N, 1.0, w.U, RU, 1, M * RU, T, 1, RT, M * RT, nullptr, 0, 0,
                        0, 0.0, w.Abar, M, 1, MM, W));
   // inner P: lam = P mu0, Pbar += Re mu0 phi_in^T
   AFQ_TRY(add_re_outer(ctx, w, w.mu0, phi_in));
   AFQ_TRY(launch_dgemm(ctx, M, 2 * N, M, 1.0, ctx->P, M, 1, 0, reinterpret_cast<double*>(w.mu0),
                        2 * N, 1, 2 * MN, 0.0, reinterpret_cast<double*>(w.lam), 2 * N, 1, 2 * MN,
                        W, 1));
-  // VHS: Q_zg = <Abar_z, L_g> over packed symmetric pairs
+  // VHS: Q_zg = <Abar_z, L_g> over packed symmetric pairs; re and im as a batch of two,
+  // the packed dimension split QSPLIT ways (partials summed in a fixed order)
   k_pack_sym<<<grid_of((long)W * Mp), 256, 0, ctx->stream>>>(W, M, Mp, ctx->tpq, w.Abar, w.Apk);
   AFQ_LAUNCHED(ctx);
   const double* apk = reinterpret_cast<const double*>(w.Apk);
   double* q = reinterpret_cast<double*>(w.Q);
-  for (int ri = 0; ri < 2; ++ri)
-    AFQ_TRY(launch_dgemm(ctx, W, X, Mp, 1.0, apk + ri, 2L * Mp, 2, 0, ctx->Lpk, 1, Mp, 0, 0.0,
-                         q + ri, 2L * X, 2, 0, 1, 1));
+  const long WX = (long)W * X;
+  AFQ_TRY(launch_dgemm(ctx, W, X, Mp, 1.0, apk, 2L * Mp, 2, 1, ctx->Lpk, 1, Mp, 0, 0.0, w.qpart, X,
+                       1, WX, 2, QSPLIT));
+  k_q_reduce<<<grid_of(2 * WX), 256, 0, ctx->stream>>>(WX, QSPLIT, w.qpart, q);
+  AFQ_LAUNCHED(ctx);
   // Lbar (packed) += Re(i sqrt(dt) sum_z y_zg Abar''_z) = -sqrt(dt) (y_i Abar''_r + y_r Abar''_i)
   const double* yv = reinterpret_cast<const double*>(ctx->y);
   AFQ_TRY(launch_dgemm(ctx, X, Mp, W, -sdt, yv + 1, 2, 2L * X, 0, apk, 2L * Mp, 2, 0, 1.0, w.Lpkb,
@@ -493,14 +562,7 @@ int run_backward(afq_ctx* ctx, ChainWork& w, const double2* gE, double* dh1, dou
                                   cudaMemcpyDeviceToDevice, ctx->stream));
     for (int i = 0; i < sg.len; ++i) {
       double2* cur = w.seg + (long)i * WMN;
-      ctx->ws.phi = cur;
-      AFQ_TRY(launch_overlap_theta(ctx, ctx->ws));
-      AFQ_TRY(launch_force_bias_fp64(ctx, ctx->ws));
-      AFQ_TRY(launch_fields(ctx, tp.fields + (long)(sg.start + i) * WX));
-      AFQ_TRY(launch_vhs_fp64(ctx));
-      AFQ_CUDA(ctx, cudaMemcpyAsync(cur + WMN, cur, WMN * 16, cudaMemcpyDeviceToDevice, ctx->stream));
-      ctx->ws.phi = cur + WMN;
-      AFQ_TRY(launch_propagate_fp64(ctx));
+      AFQ_TRY(forward_tape(ctx, w, i, cur, tp.fields + (long)(sg.start + i) * WX, cur + WMN));
     }
     if (sg.qr_end) {
       const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
@@ -516,7 +578,7 @@ int run_backward(afq_ctx* ctx, ChainWork& w, const double2* gE, double* dh1, dou
       AFQ_LAUNCHED(ctx);
     }
     for (int i = sg.len - 1; i >= 0; --i)
-      AFQ_TRY(step_backward(ctx, w, w.seg + (long)i * WMN, tp.fields + (long)(sg.start + i) * WX));
+      AFQ_TRY(step_backward(ctx, w, w.seg + (long)i * WMN, i));
   }
   // parameters
   AFQ_TRY(exp_adjoint(ctx, w));
@@ -529,20 +591,22 @@ int run_backward(afq_ctx* ctx, ChainWork& w, const double2* gE, double* dh1, dou
     AFQ_LAUNCHED(ctx);
   }
   if (dL) {
-    // lv_g += <hbar'', L_g>
-    AFQ_TRY(launch_dgemm(ctx, X, 1, (int)MM, 1.0, ctx->L, MM, 1, 0, w.hb, 1, 0, 0, 1.0, w.lv, 1, 0,
-                         0, 1, 1));
+    // hs = sym(hbar''); with L_g symmetric, <hbar'', L_g> = <hs, L_g> and
+    // sym(hbar'' L_g + L_g hbar'') = sym(2 hs L_g)
+    k_sym_sum<<<grid_of(MM), 256, 0, ctx->stream>>>(M, w.hb, nullptr, w.hs);
+    AFQ_LAUNCHED(ctx);
+    // lv_g += <hs, L_g>
+    k_dot_rows<<<X, 256, 0, ctx->stream>>>(MM, ctx->L, w.hs, w.lv);
+    AFQ_LAUNCHED(ctx);
     // Pt = Psi Psi^T
     AFQ_TRY(launch_dgemm(ctx, M, M, N, 1.0, ctx->psiT, 1, M, 0, ctx->psiT, M, 1, 0, 0.0, w.Pt, M, 1,
                          0, 1, 1));
-    // D_g = Psi F_g - 1/2 (hbar L_g + L_g hbar)
+    // D_g = Psi F_g - hs L_g (symmetrised by the assembly)
     AFQ_TRY(launch_dgemm(ctx, M, M, N, 1.0, ctx->psiT, 1, M, 0, w.F, M, 1, NM, 0.0, w.D, M, 1, MM,
                          X, 1));
-    AFQ_TRY(launch_dgemm(ctx, M, M, M, -0.5, w.hb, M, 1, 0, ctx->L, M, 1, MM, 1.0, w.D, M, 1, MM, X,
+    AFQ_TRY(launch_dgemm(ctx, M, M, M, -1.0, w.hs, M, 1, 0, ctx->L, M, 1, MM, 1.0, w.D, M, 1, MM, X,
                          1));
-    AFQ_TRY(launch_dgemm(ctx, M, M, M, -0.5, ctx->L, M, 1, MM, w.hb, M, 1, 0, 1.0, w.D, M, 1, MM, X,
-                         1));
-    k_dl_assemble<<<grid_of((long)X * MM), 256, 0, ctx->stream>>>(X, M, Mp, w.D, w.hb, ctx->vbar,
+    k_dl_assemble<<<grid_of((long)X * MM), 256, 0, ctx->stream>>>(X, M, Mp, w.D, w.hs, ctx->vbar,
                                                                   w.lv, w.Pt, w.Lpkb, dL);
     AFQ_LAUNCHED(ctx);
   }
@@ -608,16 +672,17 @@ int chain_backward(afq_ctx* ctx, const double2* gE, double* dh1, double* dL, dou
   A(&w.lam2, WMN);
   A(&w.mu0, WMN);
   A(&w.phi2, WMN);
-  A(&w.T, WMN * (n + 1));
+  const size_t cap = (size_t)tp.seg_cap;  // per-step operands of the longest segment
+  A(&w.T, cap * WMN * (n + 1));
   A(&w.U, WMN * n);
   A(&w.Abar, (size_t)W * MM);
   A(&w.Apk, (size_t)W * Mp);
   A(&w.Q, (size_t)W * X);
   A(&w.lamT, WMN);
   A(&w.seg, WMN * (tp.seg_cap + 1));
-  A(&w.A, (size_t)W * MM);
+  A(&w.A, cap * W * MM);
   A(&w.xbar, (size_t)W * X);
-  A(&w.y, (size_t)W * X);
+  A(&w.y, cap * W * X);
   A(&w.cfb, (size_t)W);
   A(&w.cmf, (size_t)W);
   A(&w.Ppart, (size_t)ZSPLIT * MM);
@@ -629,6 +694,8 @@ int chain_backward(afq_ctx* ctx, const double2* gE, double* dh1, double* dL, dou
   A(&w.hb, MM);
   A(&w.Pt, MM);
   A(&w.Z, 9 * MM);
+  A(&w.qpart, (size_t)2 * QSPLIT * W * X);
+  A(&w.hs, MM);
   if (dL) A(&w.D, (size_t)X * MM);
   w.ws.W = W;
   A(&w.ws.thetaT, WMN);

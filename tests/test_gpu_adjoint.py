@@ -82,13 +82,19 @@ def test_backward_c5_sampled_walkers():
     assert np.max(np.abs(dp[others])) == 0.0
 
 
-def test_backward_rejects_oversized_blocks():
-    from paper_2209_04015_b300.afqmc import AFQ_ERR_ARG, AfqError
+def test_backward_large_spin_block():
+    """n_alpha M = 8400: more entries of theta per spin than one thread block holds,
+    and a beta block of a different size."""
     s = make_system(300, 28, 2, 40, seed=1)
-    ctx, _ = make_pair(s, 2)
-    with pytest.raises(AfqError) as e:
-        ctx.local_energy_backward(np.ones(2, dtype=np.complex128))
-    assert e.value.code == AFQ_ERR_ARG
+    W = 3
+    phi = perturbed_walkers(s, W, eps=0.3, seed=5)
+    ctx, orc = make_pair(s, W, phi=phi)
+    g = _cot(W, 8)
+    dh, dL, dp = ctx.local_energy_backward(g)
+    rh, rL, rp = local_energy_vjp(orc, phi, g)
+    _close(dh, rh)
+    _close(dL, rL)
+    _close(dp, rp)
 
 
 def test_torch_autograd_function():
