@@ -37,10 +37,13 @@ WORKLOAD_TEXT = ("ph-AFQMC step + E_loc, 100 orbitals, 10a+10b electrons, 400 Ch
                  "vectors (geometric norm decay), 128 complex128 walkers, dt 0.005, QR every "
                  "5 steps, Philox fields")
 FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 nominal: 148 SMs x 2032 MHz x ~4.15 flop/clk/SM
-# DRAM bytes (read + write) per launch of the dominant kernel, from one-pass ncu
-# captures of these exact workloads (profiles/exchange_fp64_c2.md,
-# profiles/exchange_tc_c3.md); None where no capture of the current kernel exists.
-TRAFFIC = {("fp64", "c2"): 10565888 + 0, ("split_bf16", "c3"): 572279808 + 10032128}
+# DRAM bytes (read + write) per launch of the dominant kernel, from ncu captures of
+# these exact workloads (profiles/propagation_fp64_c2.md, profiles/exchange_tc_c3.md);
+# absent where no capture of the current kernel exists.
+TRAFFIC = {("split_bf16", "c3", "exchange"): 572279808 + 10032128,
+           ("fp64", "c2", "propagate"): 24697856 + 0}  # captured with 4 columns per CTA
+FP64_KERNELS = {"propagate": "k_propagate_fp64", "exchange": "k_exchange_v / k_exchange_fp64",
+                "vhs": "k_vhs_fp64", "force_bias": "k_force_bias_fp64"}
 SPLIT_PRODUCTS = 6          # bf16 slice products of the 3-slice exchange (s + t <= 2)
 
 
@@ -96,14 +99,17 @@ def job_throughput(total_ms: float, units_per_rank: int, world: int, device="cpu
     return world * units_per_rank / (total_ms / 1e3), total_ms
 
 
-def exchange_flops(W, X, M, na, nb):
-    """Algorithmic flops of the exchange kernel for W walkers: T = L~ theta
-    (4 n^2 M real flops per g and spin, real x complex) plus sum T_ij T_ji
-    (8 n^2 flops per g and spin)."""
+def exchange_flops(W, X, M, na, nb, algorithm="direct"):
+    """Algorithmic flops of the exchange for W walkers.  direct: T = L~ theta
+    (4 n^2 M real flops per g and spin, real x complex) plus sum T_ij T_ji (8 n^2 flops
+    per g and spin).  stored: x^T V x over the K (K + 1) / 2 distinct entries of the
+    symmetric V (K = n M; real x complex, 4 flops each) plus the dot (8 K)."""
+    if algorithm == "stored":
+        return W * sum(2 * (n * M) * (n * M + 1) + 8 * n * M for n in (na, nb))
     return W * X * sum(n * n * (4 * M + 8) for n in (na, nb))
 
 
-def step_flops(W, X, M, na, nb, order=6):
+def step_flops(W, X, M, na, nb, order=6, exchange="direct"):
     """Algorithmic flops of one walker step (all walkers), by part."""
     N = na + nb
     Mp = M * (M + 1) // 2
@@ -112,7 +118,7 @@ def step_flops(W, X, M, na, nb, order=6):
         "vhs": W * 4 * X * Mp,
         "propagate": W * (order * 8 + 2 * 4) * M * M * N,
         "overlap_theta": W * sum(4 * M * n * n + 8 * M * n * n for n in (na, nb)),
-        "exchange": exchange_flops(W, X, M, na, nb),
+        "exchange": exchange_flops(W, X, M, na, nb, exchange),
     }
 
 
@@ -296,7 +302,7 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
            "roofline": {"bound": "tensor", "kernel": "exchange (k_exchange_tc, persistent)",
                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak,
-                        "traffic": TRAFFIC.get(("split_bf16", name)) if W == c["W"] else None,
+                        "traffic": TRAFFIC.get(("split_bf16", name, "exchange")) if W == c["W"] else None,
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
                         "flops_per_launch": bf16_flops,
                         "flops_note": f"{SPLIT_PRODUCTS} bf16 slice products x the exchange's "
@@ -486,6 +492,7 @@ def run_afq(args):
     ctx.init_hamiltonian(s.h1, s.L, s.e0)
     ctx.init_trial(s.psi_a, s.psi_b)
     ctx.init_walkers(W)
+    ctx.autotune()  # launch shapes (set-up, outside the timed region); walkers restored
     e_dev = torch.empty((W, 4, 2), dtype=torch.float64, device="cuda")
     emix_dev = torch.empty(1, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -542,10 +549,14 @@ def run_afq(args):
             torch.distributed.destroy_process_group()
         return 0
 
-    flops = step_flops(W, X, M, na, nb)
-    ex_ms, ex_n = prof["exchange"]
-    ex_avg_s = ex_ms / max(ex_n, 1) / 1e3
-    ex_achieved = exchange_flops(W, X, M, na, nb) / ex_avg_s / 1e12
+    ex_algo = ctx.exchange_algorithm()
+    tiles = ctx.get_tiles()
+    flops = step_flops(W, X, M, na, nb, exchange=ex_algo)
+    # the dominant FP64 kernel by device time
+    dom = max(FP64_KERNELS, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    dom_avg_s = dom_ms / max(dom_n, 1) / 1e3
+    dom_achieved = flops[dom] / dom_avg_s / 1e12
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)}
                for k, v in prof.items() if v[1]}
@@ -558,13 +569,15 @@ def run_afq(args):
                    "X": X, "W_per_gpu": W, "dt": 0.005, "qr_period": 5, "precision": "fp64",
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MB write, outside the step events)"},
-        "roofline": {"bound": "alu", "kernel": "exchange (k_exchange_fp64)", "achieved": ex_achieved,
-                     "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ex_achieved / FP64_NOMINAL_TFLOPS,
-                     "traffic": TRAFFIC.get(("fp64", WORKLOAD)) if W == 128 else None,
+        "roofline": {"bound": "alu", "kernel": f"{dom} ({FP64_KERNELS[dom]})",
+                     "achieved": dom_achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": dom_achieved / FP64_NOMINAL_TFLOPS,
+                     "traffic": (TRAFFIC.get(("fp64", WORKLOAD, dom))
+                                 if W == 128 and (dom != "propagate" or tiles[1] == 4) else None),
                      "peak_source": "FP64 nominal (148 SMs x 2032 MHz x 4.15 flop/clk/SM)",
-                     "flops_per_launch": exchange_flops(W, X, M, na, nb),
-                     "avg_launch_ms": ex_avg_s * 1e3},
+                     "flops_per_launch": flops[dom], "avg_launch_ms": dom_avg_s * 1e3},
+        "exchange_algorithm": ex_algo,
+        "autotuned_tiles": tiles,
         "step_flops": total_flops,
         "step_tflops": total_flops / (total_ms / args.steps / 1e3) / 1e12,
         "kernels": kernels,

@@ -52,6 +52,21 @@ typedef enum afq_precision {
   AFQ_SPLIT_TF32 = 2  /* reserved                                              */
 } afq_precision;
 
+typedef enum afq_exchange {
+  AFQ_EXCHANGE_AUTO = 0,   /* STORED when its tensor fits the memory budget (1/4 of the
+                              free device memory at afq_init_trial, at most 16 GiB) and
+                              takes fewer multiply-adds (M < 1.5 X); else DIRECT      */
+  AFQ_EXCHANGE_DIRECT = 1, /* T_zg = L~_g theta_z formed and consumed per (walker, g)
+                              (Sec. "Local energy"): 2 X n^2 M multiply-adds per walker
+                              and spin, no extra memory                             */
+  AFQ_EXCHANGE_STORED = 2  /* the half-rotated two-electron tensor
+                              V[(j,p),(i,q)] = sum_g L~_g,jq L~_g,ip kept per spin
+                              (na^2 M^2 + nb^2 M^2 doubles, built by afq_init_trial):
+                              E_K = -1/2 sum_s theta_s^T V_s theta_s, about (n M)^2
+                              multiply-adds per walker and spin (V is symmetric:
+                              only its upper blocks are read)                        */
+} afq_exchange;
+
 typedef struct afq_params {
   double dt;           /* imaginary time step (the paper's Delta tau)            */
   int taylor_order;    /* order n of the Taylor series of exp(A); default 6      */
@@ -69,11 +84,12 @@ typedef struct afq_params {
   int prop_slices;     /* AFQ_SPLIT_BF16: exact 8-bit digits per FP64 operand of the
                           VHS and propagator GEMMs, 1..4 (per-row power-of-two scale,
                           one exact TMEM accumulator per digit order); 0 = 4     */
+  int exchange;        /* an afq_exchange: algorithm of the FP64 exchange energy  */
 } afq_params;
 
 /* Fill *p with the defaults: dt 0.005, Taylor order 6, QR every 5 steps, seed 1,
    FP64, E_shift = trial energy, no cap, phaseless; in split mode 3 slices for the
-   force bias and exchange and 4 exact digits for the propagation. */
+   force bias and exchange and 4 exact digits for the propagation; exchange AUTO. */
 void afq_default_params(afq_params* p);
 
 /* Create a context bound to cuda_stream (a cudaStream_t, or NULL for the legacy
@@ -94,12 +110,16 @@ int afq_init_hamiltonian(afq_ctx* ctx, int M, int X, const double* h1, const dou
 /* Single-determinant trial Psi_T (Sec. "Overlap"): psi_a M x na, psi_b M x nb, real,
    with orthonormal columns.  Builds the half-rotated vectors L~_g = Psi^T L_g
    (Sec. "One-body Green's function and force bias"), the rotated h~ = Psi^T h1, the
-   mean field vbar_g, h'' = h1 - 1/2 sum_g L_g L_g + sum_g vbar_g L_g and the
-   half-step propagator exp(-dt h''/2).  Needs afq_init_hamiltonian first. */
+   mean field vbar_g, h'' = h1 - 1/2 sum_g L_g L_g + sum_g vbar_g L_g, the
+   half-step propagator exp(-dt h''/2) and, with the stored exchange (see
+   afq_exchange), the half-rotated tensor V.  Needs afq_init_hamiltonian first. */
 int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a,
                    const double* psi_b);
 /* Local energy of the trial determinant itself (its Hartree-Fock energy). */
 int afq_trial_energy(afq_ctx* ctx, double* e_out);
+/* The FP64 exchange algorithm afq_init_trial resolved params.exchange to:
+   AFQ_EXCHANGE_DIRECT or AFQ_EXCHANGE_STORED. */
+int afq_exchange_algorithm(afq_ctx* ctx, int* algo_out);
 
 /* Walker ensemble of Eq. stat_wfs.  phi: W x M x (na+nb) complex, or NULL for W
    copies of the trial.  w: W real weights, or NULL for all ones.  Computes the

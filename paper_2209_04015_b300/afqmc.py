@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libafqmc.so")
 AFQ_OK, AFQ_ERR_ARG, AFQ_ERR_CUDA, AFQ_ERR_SINGULAR, AFQ_ERR_NAN, AFQ_ERR_STATE, AFQ_ERR_NOMEM = range(7)
 AFQ_STATIC_EXCHANGE_SLOTS = 262144  # complex partial-sum slots of the static scratch array
 PRECISIONS = {"fp64": 0, "split_bf16": 1, "split_tf32": 2}
+EXCHANGES = {"auto": 0, "direct": 1, "stored": 2}
 STATUS_NAMES = {0: "AFQ_OK", 1: "AFQ_ERR_ARG", 2: "AFQ_ERR_CUDA", 3: "AFQ_ERR_SINGULAR",
                 4: "AFQ_ERR_NAN", 5: "AFQ_ERR_STATE", 6: "AFQ_ERR_NOMEM"}
 
@@ -29,7 +30,7 @@ class AfqParams(ctypes.Structure):
                 ("precision", ctypes.c_int), ("has_e_shift", ctypes.c_int),
                 ("e_shift", ctypes.c_double), ("fb_cap", ctypes.c_double),
                 ("free_projection", ctypes.c_int), ("split_slices", ctypes.c_int),
-                ("prop_slices", ctypes.c_int)]
+                ("prop_slices", ctypes.c_int), ("exchange", ctypes.c_int)]
 
 
 class AfqError(RuntimeError):
@@ -49,6 +50,7 @@ _SIGS = {
     "afq_init_hamiltonian": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_double]),
     "afq_init_trial": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "afq_trial_energy": (ctypes.c_int, [_P, _D]),
+    "afq_exchange_algorithm": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "afq_init_walkers": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "afq_propagate": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "afq_propagate_dev": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -142,7 +144,7 @@ class AfqContext:
     def __init__(self, dt: float = 0.005, taylor_order: int = 6, qr_period: int = 5,
                  seed: int = 1, precision: str = "fp64", e_shift: float | None = None,
                  fb_cap: float = 0.0, free_projection: bool = False, stream: int | None = None,
-                 split_slices: int = 3, prop_slices: int = 4):
+                 split_slices: int = 3, prop_slices: int = 4, exchange: str = "auto"):
         self.lib = load_library()
         p = AfqParams()
         self.lib.afq_default_params(ctypes.byref(p))
@@ -154,6 +156,7 @@ class AfqContext:
         p.free_projection = 1 if free_projection else 0
         p.split_slices = split_slices
         p.prop_slices = prop_slices
+        p.exchange = EXCHANGES[exchange]
         self.params = p
         h = _P()
         rc = self.lib.afq_create(ctypes.byref(h), ctypes.byref(p), _P(stream or 0))
@@ -201,6 +204,12 @@ class AfqContext:
         e = ctypes.c_double()
         self._check(self.lib.afq_trial_energy(self.h, ctypes.byref(e)))
         return e.value
+
+    def exchange_algorithm(self) -> str:
+        """The FP64 exchange the trial resolved to: "direct" or "stored"."""
+        a = ctypes.c_int()
+        self._check(self.lib.afq_exchange_algorithm(self.h, ctypes.byref(a)))
+        return {v: k for k, v in EXCHANGES.items()}[a.value]
 
     def init_walkers(self, W: int, phi: np.ndarray | None = None,
                      w: np.ndarray | None = None) -> None:

@@ -181,7 +181,8 @@ int free_trial(afq_ctx* ctx) {
   dfree(&ctx->vbar);
   dfree(&ctx->hpp);
   dfree(&ctx->P);
-  dfree(&ctx->bwdV);
+  dfree(&ctx->Vx);
+  ctx->ex_stored = false;
   ctx->have_trial = false;
   return free_walkers(ctx);
 }
@@ -234,6 +235,7 @@ void afq_default_params(afq_params* p) {
   p->free_projection = 0;
   p->split_slices = 3;
   p->prop_slices = 4;
+  p->exchange = AFQ_EXCHANGE_AUTO;
 }
 
 int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
@@ -252,7 +254,8 @@ int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
       ctx->p.qr_period < 0 ||
       (ctx->p.precision != AFQ_FP64 && ctx->p.precision != AFQ_SPLIT_BF16) ||
       ctx->p.split_slices < 1 || ctx->p.split_slices > 4 || ctx->p.prop_slices < 1 ||
-      ctx->p.prop_slices > 4) {
+      ctx->p.prop_slices > 4 || ctx->p.exchange < AFQ_EXCHANGE_AUTO ||
+      ctx->p.exchange > AFQ_EXCHANGE_STORED) {
     delete ctx;
     return AFQ_ERR_ARG;
   }
@@ -427,6 +430,23 @@ int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a, const doub
   dfree(&E);
   dfree(&T);
   AFQ_TRY(rc);
+  // FP64 exchange: the stored half-rotated tensor when asked for, or (AUTO, FP64
+  // contexts) when it fits a quarter of the free memory (at most 16 GiB) and needs
+  // fewer multiply-adds than forming T per (walker, g): (n M)^2 against 2 X n^2 M
+  {
+    const double vbytes = 8.0 * ((double)na * M * na * M + (double)nb * M * nb * M);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+    const double budget = std::fmin(0.25 * (double)fr, 16.0 * 1073741824.0);
+    ctx->ex_stored = ctx->p.exchange == AFQ_EXCHANGE_STORED ||
+                     (ctx->p.exchange == AFQ_EXCHANGE_AUTO && !ctx->mixed && vbytes <= budget &&
+                      M < 1.5 * X);
+    if (ctx->ex_stored) {
+      AFQ_TRY(build_exchange_v(ctx));
+      const int slots = exchange_v_slots(ctx);
+      if (slots > ctx->ex_groups) ctx->ex_groups = slots;
+    }
+  }
   ctx->have_trial = true;
   // trial energy: the energy kernels on a one-walker set equal to the trial
   WalkerSet t;
@@ -464,6 +484,13 @@ int afq_trial_energy(afq_ctx* ctx, double* e_out) {
   if (!ctx || !e_out) return AFQ_ERR_ARG;
   if (!ctx->have_trial) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_trial first");
   *e_out = ctx->e_trial;
+  return AFQ_OK;
+}
+
+int afq_exchange_algorithm(afq_ctx* ctx, int* algo_out) {
+  if (!ctx || !algo_out) return AFQ_ERR_ARG;
+  if (!ctx->have_trial) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_trial first");
+  *algo_out = ctx->ex_stored ? AFQ_EXCHANGE_STORED : AFQ_EXCHANGE_DIRECT;
   return AFQ_OK;
 }
 
@@ -956,10 +983,11 @@ int afq_autotune(afq_ctx* ctx) {
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
   int rc = AFQ_OK;
   if (!ctx->mixed) {
-    // FP64 exchange: g-group size (pure: it only rewrites its partial sums)
+    // FP64 exchange (direct form): g-group size (pure: it only rewrites its partial sums)
     float best = 1e30f;
     int bestG = exchange_group_size(nmax);
-    for (int G = 1; G <= exchange_group_max(nmax); G = G < 4 ? G + 1 : G * 3 / 2) {
+    for (int G = 1; !ctx->ex_stored && G <= exchange_group_max(nmax);
+         G = G < 4 ? G + 1 : G * 3 / 2) {
       ctx->ex_G_fp64 = G;
       const float ms = time_launch(ctx, [&] { return launch_exchange_fp64(ctx, s); });
       if (ms < best) {

@@ -163,9 +163,11 @@ struct afq_ctx {
   CUtensorMap tm_vhs_a, tm_vhs_b, tm_pm, tm_az, tm_t[2];
 
   ChainTape chain;  // afq_chain_forward
-  // local-energy adjoint: V_s[(j,p),(i,q)] = sum_g L~_g,s[j][q] L~_g,s[i][p] per spin
-  // (alpha block, then beta block), built on first use and kept with the trial
-  double* bwdV = nullptr;
+  // half-rotated exchange tensor V_s[(j,p),(i,q)] = sum_g L~_g,s[j][q] L~_g,s[i][p] per
+  // spin (alpha block, then beta block): built by afq_init_trial when the stored
+  // exchange is chosen, else on the first local-energy adjoint; kept with the trial
+  double* Vx = nullptr;
+  bool ex_stored = false;  // FP64 exchange from Vx (else T per (walker, g))
 
   // built-in profiler: event pairs around launches of each kernel class
   bool profiling = false;
@@ -204,6 +206,10 @@ int afq_fail(afq_ctx* ctx, int code, const std::string& msg);
 // launch wrappers (each returns AFQ_OK or an error code via afq_fail)
 // ----------------------------------------------------------------------------
 // set-up (k_setup.cu)
+// stored-tensor exchange (k_exchange_v.cu)
+int build_exchange_v(afq_ctx* ctx);
+int exchange_v_slots(const afq_ctx* ctx);
+int launch_exchange_v(afq_ctx* ctx, WalkerSet& s);
 int launch_dgemm(afq_ctx* ctx, int m, int n, int k, double alpha, const double* A, long sam,
                  long sak, long sab, const double* B, long sbk, long sbn, long sbb, double beta,
                  double* C, long scm, long scn, long scb, int batch, int ksplit);

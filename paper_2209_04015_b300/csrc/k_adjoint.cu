@@ -203,31 +203,6 @@ int launch_bwd_dphi(afq_ctx* ctx, WalkerSet& t, const double2* gbarT, const doub
 
 }  // namespace
 
-// V_s[(j,p),(i,q)] = sum_g L~_g,s[j][q] L~_g,s[i][p] for both spins, once per trial:
-// for each j, one GEMM batched over i gives the M x M block (p, q) = A_i^T A_j with
-// A_i = L~_g,s[i][.] over g (X x M).
-int build_bwd_v(afq_ctx* ctx) {
-  if (ctx->bwdV) return AFQ_OK;
-  const int M = ctx->M, N = ctx->N, X = ctx->X;
-  const long NM = (long)N * M;
-  const long nMa = (long)ctx->na * M, nMb = (long)ctx->nb * M;
-  if (cudaMalloc((void**)&ctx->bwdV, (size_t)(nMa * nMa + nMb * nMb) * sizeof(double)) !=
-      cudaSuccess) {
-    ctx->bwdV = nullptr;
-    return afq_fail(ctx, AFQ_ERR_NOMEM, "local-energy backward: V tensor");
-  }
-  for (int s = 0; s < 2; ++s) {
-    const int n = s ? ctx->nb : ctx->na, off = s ? ctx->na : 0;
-    const long nM = (long)n * M;
-    double* V = ctx->bwdV + (s ? nMa * nMa : 0);
-    for (int j = 0; j < n; ++j)
-      AFQ_TRY(launch_dgemm(ctx, M, M, X, 1.0, ctx->Lt + (long)off * M, 1, NM, M,
-                           ctx->Lt + (long)(off + j) * M, NM, 1, 0, 0.0, V + j * M * nM, nM, 1,
-                           M, n, 1));
-  }
-  return AFQ_OK;
-}
-
 int adjoint_energy_core(afq_ctx* ctx, WalkerSet& t, const double2* gE, double* dh1, double* F,
                         double2* out, int mode) {
   const int M = ctx->M, N = ctx->N, X = ctx->X, W = t.W;
@@ -236,7 +211,7 @@ int adjoint_energy_core(afq_ctx* ctx, WalkerSet& t, const double2* gE, double* d
   if (nmax > 64)
     return afq_fail(ctx, AFQ_ERR_ARG, "local-energy backward needs max(na, nb) <= 64");
   AFQ_TRY(configure_bwd(ctx, dphi_smem(nmax)));
-  if (out) AFQ_TRY(build_bwd_v(ctx));
+  if (out) AFQ_TRY(build_exchange_v(ctx));
   const long nmM = (long)nmax * M;
   // buf: Gbar^T (W x N x M complex), then Theta (N x M reals); for dL also
   // u = conj(g) theta^T (W x N x M complex), q = conj(g) c (W x X complex) and
@@ -260,7 +235,7 @@ int adjoint_energy_core(afq_ctx* ctx, WalkerSet& t, const double2* gE, double* d
       const int n = s ? ctx->nb : ctx->na, off = s ? ctx->na : 0;
       if (n == 0) continue;
       const long nM = (long)n * M, o2 = 2L * off * M;
-      const double* V = ctx->bwdV + (s ? (long)ctx->na * M * ctx->na * M : 0);
+      const double* V = ctx->Vx + (s ? (long)ctx->na * M * ctx->na * M : 0);
       // Gbar^T += sum_g c_zg L~_g (re and im rows as a batch of two)
       rc = launch_dgemm(ctx, W, (int)nM, X, 1.0, reinterpret_cast<const double*>(t.c), 2L * X, 2,
                         1, ctx->Lt + (long)off * M, NM, 1, 0, 1.0, gb + o2, 2 * NM, 2, 1, 2, 1);

@@ -497,6 +497,7 @@ int exchange_group_max(int nmax) {
 }
 
 int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s) {
+  if (ctx->ex_stored) return launch_exchange_v(ctx, s);
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
   const int G = ctx->ex_G_fp64 > 0 ? ctx->ex_G_fp64 : exchange_group_size(nmax);
   const int ngroups = (ctx->X + G - 1) / G;

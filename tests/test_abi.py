@@ -60,6 +60,7 @@ def test_default_params_are_host_only(lib):
     lib.afq_default_params(ctypes.byref(p))
     assert p.dt == 0.005 and p.taylor_order == 6 and p.qr_period == 5 and p.seed == 1
     assert p.precision == 0 and p.fb_cap == 0.0 and p.free_projection == 0
+    assert p.exchange == binding.EXCHANGES["auto"]
     assert lib.afq_last_error(None) == b"null context"
 
 

@@ -43,28 +43,31 @@ def test_philox_words_bit_exact_and_fields_match():
         assert np.all(np.abs(f - fr) <= 4e-16 * np.maximum(1.0, np.abs(fr)) * 8)
 
 
+@pytest.mark.parametrize("exchange", ["direct", "stored"])
 @pytest.mark.parametrize("cfg", ["c1", "ragged", "c2"])
-def test_trial_energy_and_initial_energy(cfg):
+def test_trial_energy_and_initial_energy(cfg, exchange):
     if cfg == "ragged":
         s, W = ragged_system(), RAGGED["W"]
     else:
         s, c = make_config(cfg)
         W = c["W"]
     phi = perturbed_walkers(s, W, eps=0.3, seed=2)
-    ctx, orc = make_pair(s, W, phi=phi)
+    ctx, orc = make_pair(s, W, phi=phi, exchange=exchange)
+    assert ctx.exchange_algorithm() == exchange
     assert abs(ctx.trial_energy() - orc.trial_energy()) <= TOL * abs(orc.trial_energy())
     assert rel(ctx.get_overlaps(), orc.ovlp).max() <= TOL
     assert_energy_parity(ctx, orc, TOL)
 
 
+@pytest.mark.parametrize("exchange", ["direct", "stored"])
 @pytest.mark.parametrize("cfg,nsteps", [("c1", 10), ("ragged", 12), ("c2", 3)])
-def test_propagation_with_host_fields(cfg, nsteps):
+def test_propagation_with_host_fields(cfg, nsteps, exchange):
     if cfg == "ragged":
         s, W = ragged_system(), RAGGED["W"]
     else:
         s, c = make_config(cfg)
         W = c["W"]
-    ctx, orc = make_pair(s, W)
+    ctx, orc = make_pair(s, W, exchange=exchange)
     fields = np.stack([gaussian_fields(W, s.X, seed=100 + k) for k in range(nsteps)])
     ctx.propagate(fields, nsteps)
     orc.propagate(list(fields))
@@ -110,12 +113,13 @@ def test_force_bias_cap_parity():
     assert_state_parity(ctx, orc, TOL)
 
 
+@pytest.mark.parametrize("exchange", ["direct", "stored"])
 @pytest.mark.parametrize("M,na,nb,X,W", [(6, 3, 0, 5, 4), (5, 1, 1, 1, 1), (33, 1, 2, 2, 3),
-                                         (40, 12, 11, 64, 5)])
-def test_edge_shapes(M, na, nb, X, W):
+                                         (40, 12, 11, 64, 5), (70, 9, 5, 90, 37)])
+def test_edge_shapes(M, na, nb, X, W, exchange):
     s = make_system(M, na, nb, X, seed=9, decay="half")
     phi = perturbed_walkers(s, W, eps=0.2, seed=5)
-    ctx, orc = make_pair(s, W, phi=phi, qr_period=2)
+    ctx, orc = make_pair(s, W, phi=phi, qr_period=2, exchange=exchange)
     fields = np.stack([gaussian_fields(W, X, seed=400 + k) for k in range(4)])
     ctx.propagate(fields, 4)
     orc.propagate(list(fields))
@@ -225,3 +229,20 @@ def test_recreated_contexts_on_reused_memory_are_identical():
         assert results[i][0] == results[i - 2][0]
         assert np.array_equal(results[i][1], results[i - 2][1])
         assert np.array_equal(results[i][2], results[i - 2][2])
+
+
+def test_auto_exchange_choice_and_agreement():
+    """AUTO takes the stored tensor where it needs fewer multiply-adds (M < 1.5 X) and
+    the direct form elsewhere; both give the same energies to rounding."""
+    s, c = make_config("c2")
+    W = 40
+    phi = perturbed_walkers(s, W, eps=0.3, seed=4)
+    ctx_a, _ = make_pair(s, W, phi=phi)
+    ctx_d, _ = make_pair(s, W, phi=phi, exchange="direct")
+    assert ctx_a.exchange_algorithm() == "stored"
+    ea, _ = ctx_a.local_energy()
+    ed, _ = ctx_d.local_energy()
+    assert np.max(np.abs(ea[:, 2] - ed[:, 2])) <= 1e-12 * np.max(np.abs(ed[:, 2]))
+    wide = make_system(60, 4, 4, 30, seed=3)
+    ctx_w, _ = make_pair(wide, 3)
+    assert ctx_w.exchange_algorithm() == "direct"
