@@ -40,11 +40,11 @@ FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 nominal: 148 SMs x 2032 MHz x ~4.15 flop
 # DRAM bytes (read + write) per launch of the dominant kernel, from ncu captures of
 # these exact workloads (profiles/propagation_fp64_c2.md, profiles/exchange_tc_c3.md);
 # absent where no capture of the current kernel exists.
-TRAFFIC = {("split_bf16", "c3", "exchange"): 572279808 + 10032128,
+TRAFFIC = {("split_bf16", "c3", "exchange_direct"): 572279808 + 10032128,
            ("fp64", "c2", "propagate"): 24697856 + 0}  # captured with 4 columns per CTA
 FP64_KERNELS = {"propagate": "k_propagate_fp64", "exchange": "k_exchange_v / k_exchange_fp64",
                 "vhs": "k_vhs_fp64", "force_bias": "k_force_bias_fp64"}
-SPLIT_PRODUCTS = 6          # bf16 slice products of the 3-slice exchange (s + t <= 2)
+SPLIT_PRODUCTS = 6          # bf16 slice products of 3 slices or digits (s + t <= 2)
 
 
 def measured_peaks() -> dict:
@@ -107,6 +107,18 @@ def exchange_flops(W, X, M, na, nb, algorithm="direct"):
     if algorithm == "stored":
         return W * sum(2 * (n * M) * (n * M + 1) + 8 * n * M for n in (na, nb))
     return W * X * sum(n * n * (4 * M + 8) for n in (na, nb))
+
+
+def stored_tc_macs(W, M, na, nb):
+    """Multiply-adds of the tensor-core stored exchange: per spin the 128-row tiles of
+    V' (K = n Mpad) from their diagonal block on, against the 2W theta columns."""
+    Mpad = (M + 31) // 32 * 32
+    total = 0
+    for n in (na, nb):
+        Kp = n * Mpad
+        for r0 in range(0, Kp, 128):
+            total += min(128, Kp - r0) * (Kp - r0) * 2 * W
+    return total
 
 
 def step_flops(W, X, M, na, nb, order=6, exchange="direct"):
@@ -282,31 +294,44 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
     prof = mix.profile_read()
     mix.profile_enable(False)
     ms = ev0.elapsed_time(ev1) / steps
+    algo = mix.exchange_algorithm()
     ex_ms, ex_n = prof["exchange"]
     ex_avg = ex_ms / max(ex_n, 1) / 1e3
-    useful = exchange_flops(W, X, M, na, nb)
+    if algo == "stored":
+        useful = 2 * stored_tc_macs(W, M, na, nb)
+        kname = "exchange (k_tc_split<ExVP>: stored V' x theta, exact digits)"
+        note = (f"{SPLIT_PRODUCTS} digit products x 2 x the multiply-adds of the upper block "
+                "triangle of V' against theta (padding of M to 32 counted)")
+    else:
+        useful = exchange_flops(W, X, M, na, nb)
+        kname = "exchange (k_exchange_tc, persistent, direct)"
+        note = (f"{SPLIT_PRODUCTS} bf16 slice products x the exchange's algorithmic flops "
+                "(no padding counted)")
     bf16_flops = SPLIT_PRODUCTS * useful
     peak = measured_peaks().get("bf16_tflops", 1800.0)
     achieved = bf16_flops / ex_avg / 1e12
     out = {"workload": name, "M": M, "na": na, "nb": nb, "X": X, "W": W,
            "value": W / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-           "precision": "split_bf16: force bias and exchange 3 bf16 slices (6 products, FP32 "
-                        "accumulation); VHS and propagator 4 exact 8-bit digits; overlaps, "
-                        "inverses, QR and weights FP64",
+           "precision": ("split_bf16: force bias 3 exact 8-bit digits per operand (6 products, "
+                         "exact integer sums in TMEM); exchange " +
+                         ("stored V' and theta as 3 exact digits (6 products)" if algo == "stored"
+                          else "direct, 3 bf16 float slices (6 products, FP32 accumulation)") +
+                         "; VHS and propagator 4 exact digits; overlaps, inverses, QR and "
+                         "weights FP64"),
+           "exchange_algorithm": algo,
            "dE_L_max_1_step": errs[1], f"dE_L_max_{long_steps}_steps": errs[long_steps],
            "dE_reference": f"FP64 path (parity-checked against the FP64 oracle at 1e-10) on the "
                            f"first {check_walkers} walkers, same Philox fields",
            "gpu_launches": mix.launch_count() - n0,
            "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]}
                        for k, v in prof.items() if v[1]},
-           "roofline": {"bound": "tensor", "kernel": "exchange (k_exchange_tc, persistent)",
+           "roofline": {"bound": "tensor", "kernel": kname,
                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak,
-                        "traffic": TRAFFIC.get(("split_bf16", name, "exchange")) if W == c["W"] else None,
+                        "traffic": (TRAFFIC.get(("split_bf16", name, "exchange_" + algo))
+                                    if W == c["W"] else None),
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
-                        "flops_per_launch": bf16_flops,
-                        "flops_note": f"{SPLIT_PRODUCTS} bf16 slice products x the exchange's "
-                                      "algorithmic flops (no padding counted)",
+                        "flops_per_launch": bf16_flops, "flops_note": note,
                         "avg_launch_ms": ex_avg * 1e3}}
     mix.close()
     if fp64_compare:

@@ -64,7 +64,10 @@ typedef enum afq_exchange {
                               (na^2 M^2 + nb^2 M^2 doubles, built by afq_init_trial):
                               E_K = -1/2 sum_s theta_s^T V_s theta_s, about (n M)^2
                               multiply-adds per walker and spin (V is symmetric:
-                              only its upper blocks are read)                        */
+                              only its upper blocks are read).  AFQ_SPLIT_BF16
+                              contexts also keep split_slices bf16 planes of V in
+                              the padded layout (2 S (n Mpad)^2 bytes per spin) and
+                              run V theta as one tensor-core GEMM per spin         */
 } afq_exchange;
 
 typedef struct afq_params {
@@ -84,7 +87,7 @@ typedef struct afq_params {
   int prop_slices;     /* AFQ_SPLIT_BF16: exact 8-bit digits per FP64 operand of the
                           VHS and propagator GEMMs, 1..4 (per-row power-of-two scale,
                           one exact TMEM accumulator per digit order); 0 = 4     */
-  int exchange;        /* an afq_exchange: algorithm of the FP64 exchange energy  */
+  int exchange;        /* an afq_exchange: algorithm of the exchange energy        */
 } afq_params;
 
 /* Fill *p with the defaults: dt 0.005, Taylor order 6, QR every 5 steps, seed 1,
@@ -117,7 +120,7 @@ int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a,
                    const double* psi_b);
 /* Local energy of the trial determinant itself (its Hartree-Fock energy). */
 int afq_trial_energy(afq_ctx* ctx, double* e_out);
-/* The FP64 exchange algorithm afq_init_trial resolved params.exchange to:
+/* The exchange algorithm afq_init_trial resolved params.exchange to:
    AFQ_EXCHANGE_DIRECT or AFQ_EXCHANGE_STORED. */
 int afq_exchange_algorithm(afq_ctx* ctx, int* algo_out);
 

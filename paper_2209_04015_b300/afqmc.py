@@ -206,7 +206,7 @@ class AfqContext:
         return e.value
 
     def exchange_algorithm(self) -> str:
-        """The FP64 exchange the trial resolved to: "direct" or "stored"."""
+        """The exchange algorithm the trial resolved to: "direct" or "stored"."""
         a = ctypes.c_int()
         self._check(self.lib.afq_exchange_algorithm(self.h, ctypes.byref(a)))
         return {v: k for k, v in EXCHANGES.items()}[a.value]

@@ -430,17 +430,18 @@ int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a, const doub
   dfree(&E);
   dfree(&T);
   AFQ_TRY(rc);
-  // FP64 exchange: the stored half-rotated tensor when asked for, or (AUTO, FP64
-  // contexts) when it fits a quarter of the free memory (at most 16 GiB) and needs
-  // fewer multiply-adds than forming T per (walker, g): (n M)^2 against 2 X n^2 M
+  // Exchange: the stored half-rotated tensor when asked for, or (AUTO) when it fits a
+  // quarter of the free memory (at most 16 GiB) and needs fewer multiply-adds than
+  // forming T per (walker, g): (n M)^2 against 2 X n^2 M.  Split-precision contexts
+  // add the bf16 planes of V' for the tensor-core form.
   {
-    const double vbytes = 8.0 * ((double)na * M * na * M + (double)nb * M * nb * M);
+    double vbytes = 8.0 * ((double)na * M * na * M + (double)nb * M * nb * M);
+    if (ctx->mixed) vbytes += exchange_tcv_bytes(ctx, (M + 31) / 32 * 32);
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
     const double budget = std::fmin(0.25 * (double)fr, 16.0 * 1073741824.0);
     ctx->ex_stored = ctx->p.exchange == AFQ_EXCHANGE_STORED ||
-                     (ctx->p.exchange == AFQ_EXCHANGE_AUTO && !ctx->mixed && vbytes <= budget &&
-                      M < 1.5 * X);
+                     (ctx->p.exchange == AFQ_EXCHANGE_AUTO && vbytes <= budget && M < 1.5 * X);
     if (ctx->ex_stored) {
       AFQ_TRY(build_exchange_v(ctx));
       const int slots = exchange_v_slots(ctx);
@@ -474,6 +475,7 @@ int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a, const doub
   ctx->e_shift = ctx->p.has_e_shift ? ctx->p.e_shift : ctx->e_trial;
   if (ctx->mixed) {
     AFQ_TRY(mixed_init_trial(ctx));
+    if (ctx->ex_stored) AFQ_TRY(mixed_exchange_v_init(ctx));
     AFQ_TRY(mixed_prop_init_trial(ctx));
     AFQ_TRY(sync(ctx));
   }

@@ -143,9 +143,11 @@ struct afq_ctx {
   int S = 3;                          // bf16 slices per operand (force bias, exchange)
   int Sp = 4;                         // exact digits per operand (propagation)
   int Mpad = 0;                       // M rounded up to the 32-wide K block
-  __nv_bfloat16* Lt_sl = nullptr;     // S x X x N x Mpad slices of L~
-  __nv_bfloat16* th_sl = nullptr;     // S x W x 2 x N x Mpad slices of theta (re, im planes)
-  float* fb_part = nullptr;           // ksplit x 2W x X force-bias partial sums
+  __nv_bfloat16* Lt_sl = nullptr;     // S x X x N x Mpad float slices of L~ (direct exchange)
+  __nv_bfloat16* th_sl = nullptr;     // S x W x 2 x N x Mpad float slices of theta (direct exchange)
+  __nv_bfloat16* Lt_ex = nullptr;     // S x X x N x Mpad integer digits of L~ (force bias)
+  int* e_fb = nullptr;                // X row exponents of Lt_ex
+  double* fb_part = nullptr;          // ksplit x 2W x X force-bias partial sums (exact, FP64)
   int fb_BN = 0, fb_kbper = 0, fb_ksplit = 0, fb_ksplit_cap = 0;
   int ex_G[2] = {0, 0}, ex_zb[2] = {0, 0}, ex_BN[2] = {0, 0};
   CUtensorMap tm_fb_a, tm_fb_b, tm_ex_a[2], tm_ex_b[2];
@@ -161,6 +163,17 @@ struct afq_ctx {
   int *e_lt = nullptr, *e_pm = nullptr, *e_y = nullptr, *e_a = nullptr;  // row exponents
   int* e_t[2] = {nullptr, nullptr};
   CUtensorMap tm_vhs_a, tm_vhs_b, tm_pm, tm_az, tm_t[2];
+  // theta's integer digit planes (S x 2W x N x Mpad, one exponent per (z, re/im)):
+  // the B operand of the force bias and of the stored exchange.  Stored exchange
+  // (k_exchange_tcv.cu): S integer-digit planes of V' per spin (n Mpad)^2 with row
+  // exponents, y^T (2W x max n Mpad FP64) and the maps of both GEMM operands
+  __nv_bfloat16* Vsl = nullptr;
+  int* exv_ea = nullptr;
+  __nv_bfloat16* exv_th = nullptr;
+  int* exv_eb = nullptr;
+  double* exv_y = nullptr;
+  int exv_BN = 0;
+  CUtensorMap tm_exv_a[2], tm_exv_b;
 
   ChainTape chain;  // afq_chain_forward
   // half-rotated exchange tensor V_s[(j,p),(i,q)] = sum_g L~_g,s[j][q] L~_g,s[i][p] per
@@ -206,8 +219,12 @@ int afq_fail(afq_ctx* ctx, int code, const std::string& msg);
 // launch wrappers (each returns AFQ_OK or an error code via afq_fail)
 // ----------------------------------------------------------------------------
 // set-up (k_setup.cu)
-// stored-tensor exchange (k_exchange_v.cu)
+// stored-tensor exchange (k_exchange_v.cu; split precision: k_exchange_tcv.cu)
 int build_exchange_v(afq_ctx* ctx);
+double exchange_tcv_bytes(const afq_ctx* ctx, int Mpad);
+int mixed_exchange_v_init(afq_ctx* ctx);
+int mixed_exchange_v_walkers(afq_ctx* ctx);
+int launch_exchange_tcv(afq_ctx* ctx, WalkerSet& s);
 int exchange_v_slots(const afq_ctx* ctx);
 int launch_exchange_v(afq_ctx* ctx, WalkerSet& s);
 int launch_dgemm(afq_ctx* ctx, int m, int n, int k, double alpha, const double* A, long sam,

@@ -288,6 +288,7 @@ cudaError_t launch_ex(int grid, size_t smem, cudaStream_t stream, const CUtensor
 }  // namespace
 
 int launch_exchange_tc(afq_ctx* ctx, WalkerSet& s) {
+  if (ctx->Vsl) return launch_exchange_tcv(ctx, s);  // stored half-rotated tensor
   // equal spins share tile shapes and maps: one launch covers both
   const bool fuse = ctx->na == ctx->nb && ctx->na > 0 && ctx->ex_zb[0] == ctx->ex_zb[1];
   for (int spin = 0; spin < 2; ++spin) {

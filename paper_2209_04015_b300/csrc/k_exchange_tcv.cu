@@ -1,0 +1,244 @@
+// Split-precision exchange from the stored half-rotated tensor (AFQ_SPLIT_BF16 with
+// the stored exchange): E_K = -1/2 sum_s x_s^T V_s x_s (Sec. "Local energy" summed
+// over g first; see k_exchange_v.cu for the identity), x_s = theta^T_s per walker.
+//
+// y = V' x runs on the tensor cores as one GEMM per spin (the k_tc_split engine):
+// rows of V' (128 per tile) against the walkers' theta (columns (z, re/im)).
+// V' holds V in the padded (j, p) layout with its blocks above the 128 x 128
+// diagonal doubled and those below unused, so row tile I reads only the K blocks
+// from its own diagonal on: x^T V x = sum_I x_I^T (V_II x_I + 2 sum_{J>I} V_IJ x_J),
+// half the products of a full GEMM.
+//
+// K = n Mpad is long (8320 at 290 orbitals and 26 electrons), and the tensor core's
+// FP32 accumulation is biased: measured on float slices its error grew with K to
+// 3e-5 of E_K.  Both operands are therefore cut into exact integer digits (8 bits
+// each, a power-of-two scale per row of V' and per (walker, re/im) of theta),
+// every digit order accumulates in its own TMEM region, and the integer sums stay
+// exact in FP32 (they stay far below 2^24 for these magnitudes); the epilogue
+// recombines them in FP64 and a small FP64 kernel forms x^T y per walker.
+#include "tc_engine.cuh"
+
+using namespace tce;
+
+namespace {
+
+struct ExVP {
+  struct Args {
+    TcCommon c;  // c.nkb = Kp / 32: the K blocks of one spin
+    int Kp, W2, kb_off;
+    const int* ea;  // row exponents of V' (Kp)
+    const int* eb;  // exponents of theta per column (z, re/im) (W2)
+    double* y;      // W2 x Kp: y^T, column (z, re/im) major
+  };
+  static constexpr int kUA = 1, kUB = 1;
+  template <int S>
+  static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
+                               uint32_t bslot, bool first) {
+    issue_diagonals<S>(tmem, (uint32_t)a.c.BN, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN),
+                       first);
+  }
+  struct Tile {
+    int r0, n0, kb0, kb1;
+  };
+  static __device__ Tile tile(const Args& a) {
+    const int I = blockIdx.y;  // row tile; K starts at its diagonal block
+    return Tile{I * 128, (int)blockIdx.x * a.c.BN, I * (128 / kBK), a.c.nkb};
+  }
+  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int,
+                                int s, int kb, uint64_t* bar) {
+    tc::tma_load_3d(dst, tm, kb * kBK, t.r0, s, bar);
+  }
+  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args& a, const Tile& t,
+                                int, int s, int kb, uint64_t* bar) {
+    tc::tma_load_3d(dst, tm, (a.kb_off + kb) * kBK, t.n0, s, bar);
+  }
+  template <int S>
+  static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t*, int warp,
+                                  int lane) {
+    const int row = t.r0 + warp * 32 + lane;
+    const bool valid = row < a.Kp;
+    const int er = valid ? a.ea[row] : 0;
+    for (int c0 = 0; c0 < a.c.BN; c0 += 16) {
+      float f[S][16];
+#pragma unroll
+      for (int d = 0; d < S; ++d) tmem_row16(tmem + (uint32_t)(d * a.c.BN), warp, c0, f[d]);
+      if (!valid) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = t.n0 + c0 + j;
+        if (col >= a.W2) continue;
+        float acc[S];
+#pragma unroll
+        for (int d = 0; d < S; ++d) acc[d] = f[d][j];
+        a.y[(long)col * a.Kp + row] = combine_exact<S>(acc, er + a.eb[col] - 14);
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
+
+// Entry (r, k) of V' (Kp x Kp, Kp = n Mpad) from V (K x K over (j, p), K = n M):
+// w V[(j,p)][(i,q)] with r = j Mpad + p, k = i Mpad + q, zero on the padding,
+// w = 2 above the 128 x 128 diagonal blocks, 1 on them, 0 below.
+__device__ __forceinline__ double v_prime(const double* __restrict__ V, int M, int Mpad, long K,
+                                          long r, long k) {
+  const int j = (int)(r / Mpad), p = (int)(r % Mpad), i = (int)(k / Mpad), q = (int)(k % Mpad);
+  const long tr = r / 128, tk = k / 128;
+  if (p >= M || q >= M || tk < tr) return 0.0;
+  const double v = V[((long)j * M + p) * K + (long)i * M + q];
+  return tk > tr ? 2.0 * v : v;
+}
+
+// One warp per row r of V': the row exponent, then the S integer digit planes.
+__global__ void k_slice_v_exact(const double* __restrict__ V, int n, int M, int Mpad, int S,
+                                __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
+  const long Kp = (long)n * Mpad, K = (long)n * M, plane = Kp * Kp;
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < Kp;
+       r += (long)gridDim.x * warps) {
+    int m = 0;
+    for (long k = lane; k < Kp; k += 32) m = max(m, exp_field(v_prime(V, M, Mpad, K, r, k)));
+    const int e = row_exponent_field(warp_max(m));
+    if (lane == 0) eout[r] = e;
+    for (long k = lane; k < Kp; k += 32)
+      split_exact(v_prime(V, M, Mpad, K, r, k), e, S, out + r * Kp + k, plane);
+  }
+}
+
+// ekp[z][spin][0] = -1/2 sum_rows x[row] y[row] (complex, FP64), x = theta^T_s,z
+__global__ void __launch_bounds__(256) k_exv_dot(int Kp, int M, int Mpad, long offM, long NM,
+                                                 const double* __restrict__ y,
+                                                 const double2* __restrict__ thetaT,
+                                                 int ex_groups, int spin,
+                                                 double2* __restrict__ ekp) {
+  __shared__ double2 red[8];
+  const int z = blockIdx.x;
+  const double* yr = y + (long)(2 * z) * Kp;
+  const double* yi = yr + Kp;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int r = threadIdx.x; r < Kp; r += 256) {
+    const int j = r / Mpad, p = r % Mpad;
+    if (p >= M) continue;
+    const double2 x = thetaT[(long)z * NM + offM + (long)j * M + p];
+    const double a = yr[r], b = yi[r];
+    acc.x = fma(x.x, a, fma(-x.y, b, acc.x));
+    acc.y = fma(x.x, b, fma(x.y, a, acc.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = red[0];
+    for (int w = 1; w < 8; ++w) t = make_double2(t.x + red[w].x, t.y + red[w].y);
+    ekp[((long)z * 2 + spin) * ex_groups] = make_double2(-0.5 * t.x, -0.5 * t.y);
+  }
+}
+
+long kp_of(const afq_ctx* ctx, int spin) {
+  return (long)(spin ? ctx->nb : ctx->na) * ctx->Mpad;
+}
+
+int warp_blocks(long rows) {
+  const long b = (rows + 7) / 8;  // 8 warps per 256-thread block
+  return (int)(b < 1 ? 1 : (b > 148 * 64 ? 148 * 64 : b));
+}
+
+}  // namespace
+
+// Bytes of the digit planes of V' for both spins (S planes each) and their exponents.
+double exchange_tcv_bytes(const afq_ctx* ctx, int Mpad) {
+  const double ka = (double)ctx->na * Mpad, kb = (double)ctx->nb * Mpad;
+  return 2.0 * ctx->S * (ka * ka + kb * kb) + 4.0 * (ka + kb);
+}
+
+// Once per trial (after mixed_init_trial set Mpad and after the FP64 V was built):
+// the digit planes of V', their row exponents and tensor maps.
+int mixed_exchange_v_init(afq_ctx* ctx) {
+  if (!ctx->Vx) return afq_fail(ctx, AFQ_ERR_STATE, "stored exchange: V not built");
+  const int S = ctx->S;
+  const long Ka = kp_of(ctx, 0), Kb = kp_of(ctx, 1);
+  if (ctx->Vsl) cudaFree(ctx->Vsl);
+  if (ctx->exv_ea) cudaFree(ctx->exv_ea);
+  ctx->Vsl = nullptr;
+  ctx->exv_ea = nullptr;
+  if (cudaMalloc((void**)&ctx->Vsl, (size_t)S * (Ka * Ka + Kb * Kb) * sizeof(__nv_bfloat16)) !=
+          cudaSuccess ||
+      cudaMalloc((void**)&ctx->exv_ea, (size_t)(Ka + Kb) * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return afq_fail(ctx, AFQ_ERR_NOMEM, "stored exchange: digit planes of V");
+  }
+  const long nMa = (long)ctx->na * ctx->M;
+  for (int spin = 0; spin < 2; ++spin) {
+    const int n = spin ? ctx->nb : ctx->na;
+    if (n == 0) continue;
+    const long Kp = spin ? Kb : Ka;
+    __nv_bfloat16* out = ctx->Vsl + (spin ? (long)S * Ka * Ka : 0);
+    k_slice_v_exact<<<warp_blocks(Kp), 256, 0, ctx->stream>>>(
+        ctx->Vx + (spin ? nMa * nMa : 0), n, ctx->M, ctx->Mpad, S, out,
+        ctx->exv_ea + (spin ? Ka : 0));
+    AFQ_LAUNCHED(ctx);
+    const uint64_t da[3] = {(uint64_t)Kp, (uint64_t)Kp, (uint64_t)S};
+    const uint32_t ba[3] = {kBK, 128, 1};
+    if (!make_tmap(&ctx->tm_exv_a[spin], out, 3, da, ba))
+      return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (stored exchange)");
+  }
+  return AFQ_OK;
+}
+
+// Per walker set (after the theta digit planes exist): y and the B-operand map.
+int mixed_exchange_v_walkers(afq_ctx* ctx) {
+  if (ctx->exv_y) cudaFree(ctx->exv_y);
+  ctx->exv_y = nullptr;
+  const int W2 = 2 * ctx->ws.W;
+  const long Kp = kp_of(ctx, 0) > kp_of(ctx, 1) ? kp_of(ctx, 0) : kp_of(ctx, 1);
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->exv_y, (size_t)W2 * Kp * sizeof(double)));
+  // S diagonal accumulators of BN columns must fit the 512 TMEM columns
+  ctx->exv_BN = W2 >= 128 ? 128 : round_up(W2, 16);
+  const uint64_t db[3] = {(uint64_t)ctx->N * ctx->Mpad, (uint64_t)W2, (uint64_t)ctx->S};
+  const uint32_t bb[3] = {kBK, (uint32_t)ctx->exv_BN, 1};
+  if (!make_tmap(&ctx->tm_exv_b, ctx->exv_th, 3, db, bb))
+    return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (stored exchange theta)");
+  return AFQ_OK;
+}
+
+// Needs theta's digit planes of the current walkers (launch_slice_theta).
+int launch_exchange_tcv(afq_ctx* ctx, WalkerSet& s) {
+  const int W2 = 2 * s.W;
+  for (int spin = 0; spin < 2; ++spin) {
+    const int n = spin ? ctx->nb : ctx->na;
+    if (n == 0) continue;
+    const int Kp = (int)kp_of(ctx, spin);
+    ExVP::Args a{};
+    a.c.nkb = Kp / kBK;
+    a.c.BN = ctx->exv_BN;
+    a.c.tx_bytes = (uint32_t)ctx->S * (kBK * 128 * 2 + kBK * ctx->exv_BN * 2);
+    a.c.tmem_cols = tmem_cols_for(ctx->S * ctx->exv_BN);
+    a.c.err = ctx->flags + 2;
+    a.Kp = Kp;
+    a.W2 = W2;
+    a.kb_off = (spin ? ctx->na : 0) * ctx->Mpad / kBK;
+    a.ea = ctx->exv_ea + (spin ? kp_of(ctx, 0) : 0);
+    a.eb = ctx->exv_eb;
+    a.y = ctx->exv_y;
+    size_t smem = 0;
+    plan_smem(ctx->S, 1, 1, a.c.BN, 0, &a.c.stages, &smem);
+    if (a.c.stages < 1 || a.c.tmem_cols > 512)
+      return afq_fail(ctx, AFQ_ERR_ARG, "stored exchange tile does not fit");
+    dim3 grid((W2 + a.c.BN - 1) / a.c.BN, (Kp + 127) / 128);
+    cudaError_t e = launch_tc_s<ExVP>(ctx->S, grid, smem, ctx->stream, ctx->tm_exv_a[spin],
+                                      ctx->tm_exv_b, a);
+    ctx->launches++;
+    if (e != cudaSuccess)
+      return afq_fail(ctx, AFQ_ERR_CUDA, std::string("stored exchange tc: ") + cudaGetErrorString(e));
+    k_exv_dot<<<s.W, 256, 0, ctx->stream>>>(Kp, ctx->M, ctx->Mpad,
+                                            (long)(spin ? ctx->na : 0) * ctx->M,
+                                            (long)ctx->N * ctx->M, ctx->exv_y, s.thetaT,
+                                            ctx->ex_groups, spin, s.ekp);
+    AFQ_LAUNCHED(ctx);
+  }
+  return AFQ_OK;
+}

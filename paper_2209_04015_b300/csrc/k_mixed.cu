@@ -60,19 +60,26 @@ struct GemmP {
 
 // ---------------------------------------------------------------------------
 // Policy: force bias / Coulomb vector, split over K.  Rows g of L~ (K = N Mpad),
-// columns (z, re/im) of theta; partial sums part[ks][col][g] (FP32, g contiguous).
+// columns (z, re/im) of theta, both as exact integer digits (a power-of-two scale per
+// row g and per column); every digit order accumulates in its own TMEM region, where
+// the integer sums are exact in FP32, so the result carries only the digits' own
+// rounding (the tensor core's FP32 accumulation of float slices is biased and its
+// error grew with K).  Partial sums part[ks][col][g] in FP64 (g contiguous).
 // ---------------------------------------------------------------------------
 struct FbP {
   struct Args {
     TcCommon c;
     int X, W2, kbper;
-    float* part;
+    const int* ea;  // row exponents of L~ (X)
+    const int* eb;  // exponents of theta per column (z, re/im) (W2)
+    double* part;
   };
   static constexpr int kUA = 1, kUB = 1;
   template <int S>
   static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
                                uint32_t bslot, bool first) {
-    issue_pairs<S>(tmem, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN), first);
+    issue_diagonals<S>(tmem, (uint32_t)a.c.BN, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN),
+                       first);
   }
   struct Tile {
     int g0, n0, ks, kb0, kb1;
@@ -95,16 +102,23 @@ struct FbP {
   static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t*, int warp,
                                   int lane) {
     const int g = t.g0 + warp * 32 + lane;
-    float* out = a.part + (long)t.ks * a.W2 * a.X;
+    const bool valid = g < a.X;
+    const int eg = valid ? a.ea[g] : 0;
+    double* out = a.part + (long)t.ks * a.W2 * a.X;
     for (int c0 = 0; c0 < a.c.BN; c0 += 16) {
-      float v[16];
-      tmem_row16(tmem, warp, c0, v);
-      if (g < a.X)
+      float f[S][16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = t.n0 + c0 + j;
-          if (col < a.W2) out[(long)col * a.X + g] = v[j];
-        }
+      for (int d = 0; d < S; ++d) tmem_row16(tmem + (uint32_t)(d * a.c.BN), warp, c0, f[d]);
+      if (!valid) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = t.n0 + c0 + j;
+        if (col >= a.W2) continue;
+        float acc[S];
+#pragma unroll
+        for (int d = 0; d < S; ++d) acc[d] = f[d][j];
+        out[(long)col * a.X + g] = combine_exact<S>(acc, eg + a.eb[col] - 14);
+      }
     }
   }
 };
@@ -148,8 +162,8 @@ __global__ void k_slice_theta(const double2* __restrict__ thetaT, int W, int N, 
   }
 }
 
-// c_zg = sum_ks part[ks][2z + re/im][g] in FP64
-__global__ void k_fb_reduce(int X, int W, int ksplit, const float* __restrict__ part,
+// c_zg = sum_ks part[ks][2z + re/im][g] in FP64 (fixed order)
+__global__ void k_fb_reduce(int X, int W, int ksplit, const double* __restrict__ part,
                             double2* __restrict__ c) {
   const long total = (long)W * X;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
@@ -162,6 +176,54 @@ __global__ void k_fb_reduce(int X, int W, int ksplit, const float* __restrict__ 
     }
     c[e] = make_double2(re, im);
   }
+}
+
+__device__ __forceinline__ int warp_max_e(int v) { return __reduce_max_sync(0xffffffffu, v); }
+
+// L~ (X rows of N x M) -> integer digit planes [s][g][N Mpad] with one exponent per g
+// (one warp per row; zero padding)
+__global__ void k_slice_lt_exact(const double* __restrict__ Lt, int X, int N, int M, int Mpad,
+                                 int S, __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const long NM = (long)N * M, NMp = (long)N * Mpad, plane = (long)X * NMp;
+  for (long g = (long)blockIdx.x * warps + (threadIdx.x >> 5); g < X;
+       g += (long)gridDim.x * warps) {
+    const double* row = Lt + g * NM;
+    int m = 0;
+    for (long e = lane; e < NM; e += 32) m = max(m, exp_field(row[e]));
+    const int ex = row_exponent_field(warp_max_e(m));
+    if (lane == 0) eout[g] = ex;
+    for (long e = lane; e < NMp; e += 32) {
+      const int j = (int)(e / Mpad), p = (int)(e % Mpad);
+      split_exact(p < M ? row[(long)j * M + p] : 0.0, ex, S, out + g * NMp + e, plane);
+    }
+  }
+}
+
+// theta^T (W x N x M complex) -> integer digit planes [s][z][re/im][N Mpad] with one
+// exponent per (z, re/im) over both spins (one warp per row; zero padding)
+__global__ void k_slice_theta_exact(const double2* __restrict__ thetaT, int W, int N, int M,
+                                    int Mpad, int S, __nv_bfloat16* __restrict__ out,
+                                    int* __restrict__ eb) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const long W2 = 2L * W, NM = (long)N * M, NMp = (long)N * Mpad, plane = W2 * NMp;
+  for (long col = (long)blockIdx.x * warps + (threadIdx.x >> 5); col < W2;
+       col += (long)gridDim.x * warps) {
+    const double* th = reinterpret_cast<const double*>(thetaT + (col >> 1) * NM) + (col & 1);
+    int m = 0;
+    for (long e = lane; e < NM; e += 32) m = max(m, exp_field(th[2 * e]));
+    const int ex = row_exponent_field(warp_max_e(m));
+    if (lane == 0) eb[col] = ex;
+    for (long e = lane; e < NMp; e += 32) {
+      const int j = (int)(e / Mpad), p = (int)(e % Mpad);
+      split_exact(p < M ? th[2 * ((long)j * M + p)] : 0.0, ex, S, out + col * NMp + e, plane);
+    }
+  }
+}
+
+int warp_grid_rows(long rows) {
+  const long b = (rows + 7) / 8;  // 8 warps per 256-thread block
+  return (int)(b < 1 ? 1 : (b > 148 * 64 ? 148 * 64 : b));
 }
 
 }  // namespace
@@ -197,37 +259,65 @@ void mixed_free(afq_ctx* ctx) {
   if (ctx->Lt_sl) cudaFree(ctx->Lt_sl);
   if (ctx->th_sl) cudaFree(ctx->th_sl);
   if (ctx->fb_part) cudaFree(ctx->fb_part);
+  for (void* p : {(void*)ctx->Vsl, (void*)ctx->exv_ea, (void*)ctx->exv_th, (void*)ctx->exv_eb,
+                  (void*)ctx->exv_y, (void*)ctx->Lt_ex, (void*)ctx->e_fb})
+    if (p) cudaFree(p);
   ctx->Lt_sl = nullptr;
   ctx->th_sl = nullptr;
   ctx->fb_part = nullptr;
+  ctx->Lt_ex = nullptr;
+  ctx->e_fb = nullptr;
+  ctx->Vsl = nullptr;
+  ctx->exv_ea = nullptr;
+  ctx->exv_th = nullptr;
+  ctx->exv_eb = nullptr;
+  ctx->exv_y = nullptr;
 }
 
-// Slices L~ once per trial: S planes of [g][j][Mpad].
+// Slices L~ once per trial: integer digits with one exponent per g for the force bias,
+// and float slices for the direct exchange when it is the chosen exchange; S planes
+// of [g][j][Mpad] each.
 int mixed_init_trial(afq_ctx* ctx) {
   const int S = ctx->S, X = ctx->X, N = ctx->N, M = ctx->M;
   ctx->Mpad = round_up(M, kBK);
   const size_t plane = (size_t)X * N * ctx->Mpad;
-  if (ctx->Lt_sl) cudaFree(ctx->Lt_sl);
+  for (void* p : {(void*)ctx->Lt_sl, (void*)ctx->Lt_ex, (void*)ctx->e_fb})
+    if (p) cudaFree(p);
   ctx->Lt_sl = nullptr;
-  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->Lt_sl, plane * S * sizeof(__nv_bfloat16)));
-  k_slice_real<<<grid1d((long)plane), 256, 0, ctx->stream>>>(ctx->Lt, M, (long)X * N, M,
-                                                             ctx->Mpad, S, ctx->Lt_sl);
+  ctx->Lt_ex = nullptr;
+  ctx->e_fb = nullptr;
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->Lt_ex, plane * S * sizeof(__nv_bfloat16)));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_fb, (size_t)X * sizeof(int)));
+  k_slice_lt_exact<<<warp_grid_rows(X), 256, 0, ctx->stream>>>(ctx->Lt, X, N, M, ctx->Mpad, S,
+                                                               ctx->Lt_ex, ctx->e_fb);
   AFQ_LAUNCHED(ctx);
+  if (!ctx->ex_stored) {
+    AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->Lt_sl, plane * S * sizeof(__nv_bfloat16)));
+    k_slice_real<<<grid1d((long)plane), 256, 0, ctx->stream>>>(ctx->Lt, M, (long)X * N, M,
+                                                               ctx->Mpad, S, ctx->Lt_sl);
+    AFQ_LAUNCHED(ctx);
+  }
   return AFQ_OK;
 }
 
 // Per walker set: theta slices, force-bias partials and all tensor maps.
 int mixed_init_walkers(afq_ctx* ctx) {
   const int S = ctx->S, X = ctx->X, N = ctx->N, W = ctx->ws.W, Mp = ctx->Mpad;
-  if (ctx->th_sl) cudaFree(ctx->th_sl);
-  if (ctx->fb_part) cudaFree(ctx->fb_part);
+  for (void* p : {(void*)ctx->th_sl, (void*)ctx->fb_part, (void*)ctx->exv_th, (void*)ctx->exv_eb})
+    if (p) cudaFree(p);
   ctx->th_sl = nullptr;
   ctx->fb_part = nullptr;
-  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_sl,
-                           (size_t)S * W * 2 * N * Mp * sizeof(__nv_bfloat16)));
-  // force bias: rows g (X), columns (z, re/im) (2W), K = N Mpad
+  ctx->exv_th = nullptr;
+  ctx->exv_eb = nullptr;
   const int W2 = 2 * W;
-  ctx->fb_BN = W2 >= 256 ? 256 : round_up(W2, 16);
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->exv_th, (size_t)S * W2 * N * Mp * sizeof(__nv_bfloat16)));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->exv_eb, (size_t)W2 * sizeof(int)));
+  if (!ctx->Vsl)  // float slices of theta for the direct exchange
+    AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_sl,
+                             (size_t)S * W * 2 * N * Mp * sizeof(__nv_bfloat16)));
+  // force bias: rows g (X), columns (z, re/im) (2W), K = N Mpad; S digit accumulators
+  // of BN columns fit the 512 TMEM columns
+  ctx->fb_BN = W2 >= 128 ? 128 : round_up(W2, 16);
   const int nkb = N * Mp / kBK;
   const int tiles = ((X + 127) / 128) * ((W2 + ctx->fb_BN - 1) / ctx->fb_BN);
   int ks = (296 + tiles - 1) / tiles;
@@ -237,18 +327,18 @@ int mixed_init_walkers(afq_ctx* ctx) {
   ctx->fb_ksplit = (nkb + ctx->fb_kbper - 1) / ctx->fb_kbper;
   ctx->fb_ksplit_cap = 4 * ctx->fb_ksplit;  // the autotuner may deepen the split
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->fb_part,
-                           (size_t)ctx->fb_ksplit_cap * W2 * X * sizeof(float)));
+                           (size_t)ctx->fb_ksplit_cap * W2 * X * sizeof(double)));
   {
     const uint64_t da[3] = {(uint64_t)N * Mp, (uint64_t)X, (uint64_t)S};
     const uint32_t ba[3] = {kBK, 128, 1};
     const uint64_t db[3] = {(uint64_t)N * Mp, (uint64_t)W2, (uint64_t)S};
     const uint32_t bb[3] = {kBK, (uint32_t)ctx->fb_BN, 1};
-    if (!make_tmap(&ctx->tm_fb_a, ctx->Lt_sl, 3, da, ba) ||
-        !make_tmap(&ctx->tm_fb_b, ctx->th_sl, 3, db, bb))
+    if (!make_tmap(&ctx->tm_fb_a, ctx->Lt_ex, 3, da, ba) ||
+        !make_tmap(&ctx->tm_fb_b, ctx->exv_th, 3, db, bb))
       return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (force bias) failed");
   }
-  // exchange: per spin
-  for (int s = 0; s < 2; ++s) {
+  // direct exchange: per spin
+  for (int s = 0; s < 2 && !ctx->Vsl; ++s) {
     const int n = s ? ctx->nb : ctx->na;
     if (!mixed_exchange_tiles(n, &ctx->ex_G[s], &ctx->ex_zb[s], &ctx->ex_BN[s])) continue;
     const uint64_t da[4] = {(uint64_t)Mp, (uint64_t)N, (uint64_t)X, (uint64_t)S};
@@ -256,6 +346,7 @@ int mixed_init_walkers(afq_ctx* ctx) {
     if (!make_tmap(&ctx->tm_ex_a[s], ctx->Lt_sl, 4, da, ba) || !set_exchange_zb(ctx, s, ctx->ex_zb[s]))
       return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (exchange) failed");
   }
+  if (ctx->Vsl) AFQ_TRY(mixed_exchange_v_walkers(ctx));
   return AFQ_OK;
 }
 
@@ -279,7 +370,7 @@ int mixed_autotune(afq_ctx* ctx) {
     cudaEventDestroy(b);
     return rc == AFQ_OK ? ms / 3 : 1e30f;
   };
-  for (int spin = 0; spin < 2; ++spin) {
+  for (int spin = 0; spin < 2 && !ctx->Vsl; ++spin) {  // direct exchange only
     const int n = spin ? ctx->nb : ctx->na;
     if (n == 0) continue;
     const int zbmax = ctx->ex_zb[spin];
@@ -318,11 +409,18 @@ int mixed_autotune(afq_ctx* ctx) {
   return AFQ_OK;
 }
 
+// theta's integer digits (force bias, stored exchange) and, for the direct exchange,
+// its float slices
 int launch_slice_theta(afq_ctx* ctx, WalkerSet& s) {
-  const long total = (long)s.W * ctx->N * ctx->Mpad;
-  k_slice_theta<<<grid1d(total), 256, 0, ctx->stream>>>(s.thetaT, s.W, ctx->N, ctx->M, ctx->Mpad,
-                                                        ctx->S, ctx->th_sl);
+  k_slice_theta_exact<<<warp_grid_rows(2L * s.W), 256, 0, ctx->stream>>>(
+      s.thetaT, s.W, ctx->N, ctx->M, ctx->Mpad, ctx->S, ctx->exv_th, ctx->exv_eb);
   AFQ_LAUNCHED(ctx);
+  if (ctx->th_sl) {
+    const long total = (long)s.W * ctx->N * ctx->Mpad;
+    k_slice_theta<<<grid1d(total), 256, 0, ctx->stream>>>(s.thetaT, s.W, ctx->N, ctx->M,
+                                                          ctx->Mpad, ctx->S, ctx->th_sl);
+    AFQ_LAUNCHED(ctx);
+  }
   return AFQ_OK;
 }
 
@@ -331,11 +429,13 @@ int launch_force_bias_tc(afq_ctx* ctx, WalkerSet& s) {
   a.c.nkb = ctx->N * ctx->Mpad / kBK;
   a.c.BN = ctx->fb_BN;
   a.c.tx_bytes = (uint32_t)ctx->S * (kBK * 128 * 2 + kBK * ctx->fb_BN * 2);
-  a.c.tmem_cols = tmem_cols_for(ctx->fb_BN);
+  a.c.tmem_cols = tmem_cols_for(ctx->S * ctx->fb_BN);
   a.c.err = ctx->flags + 2;
   a.X = ctx->X;
   a.W2 = 2 * s.W;
   a.kbper = ctx->fb_kbper;
+  a.ea = ctx->e_fb;
+  a.eb = ctx->exv_eb;
   a.part = ctx->fb_part;
   size_t smem = 0;
   plan_smem(ctx->S, 1, 1, a.c.BN, 0, &a.c.stages, &smem);
