@@ -134,7 +134,7 @@ int drain_profile(afq_ctx* ctx) {
 // other sets (the trial at set-up) always use FP64.
 int green_and_bias(afq_ctx* ctx, WalkerSet& s) {
   const bool tc = ctx->mixed && &s == &ctx->ws;
-  AFQ_TRY(timed(ctx, AFQ_K_OVERLAP, [&] { return launch_overlap_theta(ctx, s); }));
+  AFQ_TRY(timed(ctx, AFQ_K_OVERLAP, [&] { return launch_overlap_theta(ctx, s, tc); }));
   if (tc) {
     AFQ_TRY(timed(ctx, AFQ_K_FORCE_BIAS, [&] {
       int rc = launch_slice_theta(ctx, s);

@@ -237,7 +237,7 @@ int launch_axpby(afq_ctx* ctx, int n, double a, const double* x, double b, doubl
 int launch_set_identity(afq_ctx* ctx, int M, double* out);
 
 // walker kernels (k_walkers.cu)
-int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s);
+int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s, bool df = false);
 int launch_force_bias_fp64(afq_ctx* ctx, WalkerSet& s);
 int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s);
 int launch_energy_assemble(afq_ctx* ctx, WalkerSet& s);

@@ -40,6 +40,31 @@ __device__ double2 block_sum2(double2 v, double2* red) {
 // det S_s and S_s^-1, theta_s^T = S_s^-T Phi_s^T, and E1_s = sum h~ . theta.
 // One CTA per (walker, spin).
 // ---------------------------------------------------------------------------
+// Double-float (hi + lo FP32 pairs, Dekker / Knuth) arithmetic for theta in the
+// split-precision mode: x = hi + lo with |lo| <= ulp(hi) / 2, products with their
+// exact FMA error term and two-sum accumulation, ~2^-44 relative -- near FP64 for
+// one-body energies while running on the FP32 pipe (64x B300's FP64 rate).
+struct DF2 {
+  float2 hi, lo;  // complex: (re, im) of the high and the low parts
+};
+__device__ __forceinline__ void df_split(double x, float& h, float& l) {
+  h = __double2float_rn(x);
+  l = __double2float_rn(x - (double)h);
+}
+// (sh, sl) += a * b for real double-floats a = (ah, al), b = (bh, bl)
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh,
+                                       float bl) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p);             // exact error of the head product
+  const float c = fmaf(ah, bl, al * bh);        // cross terms (low order)
+  const float t = sh + p;                       // two-sum of the heads
+  const float bv = t - sh;
+  const float err = (sh - (t - bv)) + (p - bv);
+  sl += err + e + c;
+  sh = t;
+}
+
+template <bool DF>
 __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int nb,
                                                       const double* __restrict__ psiT,
                                                       const double* __restrict__ ht,
@@ -155,7 +180,51 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
 
   // 3. theta^T_jp = sum_k (S^-1)_kj Phi_pk and E1 = sum_jp h~_jp theta^T_jp
   double2 e1acc = cmk(0.0, 0.0);
-  for (int p0 = 0; p0 < M; p0 += PC) {
+  if (DF) {
+    // S^-1 as double-floats, over the (now unused) left half of aug
+    DF2* sdf = reinterpret_cast<DF2*>(aug);  // [k][j] at slot k * n2 + j
+    for (int e = tid; e < n * n; e += OT) {
+      const int k = e / n, j = e % n;
+      const double2 v = aug[k * n2 + n + j];
+      DF2 d;
+      df_split(v.x, d.hi.x, d.lo.x);
+      df_split(v.y, d.hi.y, d.lo.y);
+      sdf[k * n2 + j] = d;
+    }
+    DF2* pdf = reinterpret_cast<DF2*>(cphi);  // Phi chunk as double-floats
+    for (int p0 = 0; p0 < M; p0 += PC) {
+      const int pc = min(PC, M - p0);
+      __syncthreads();
+      for (int e = tid; e < PC * n; e += OT) {
+        const int pp = e / n, j = e % n;
+        const double2 v = pp < pc ? phiz[(long)(p0 + pp) * N + off + j] : cmk(0.0, 0.0);
+        DF2 d;
+        df_split(v.x, d.hi.x, d.lo.x);
+        df_split(v.y, d.hi.y, d.lo.y);
+        pdf[pp * ldn + j] = d;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * PC; e += OT) {
+        const int j = e / PC, pp = e % PC;
+        if (pp >= pc) continue;
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        for (int k = 0; k < n; ++k) {
+          const DF2 a = sdf[k * n2 + j];
+          const DF2 b = pdf[pp * ldn + k];
+          df_mac(rh, rl, a.hi.x, a.lo.x, b.hi.x, b.lo.x);
+          df_mac(rh, rl, -a.hi.y, -a.lo.y, b.hi.y, b.lo.y);
+          df_mac(ih, il, a.hi.x, a.lo.x, b.hi.y, b.lo.y);
+          df_mac(ih, il, a.hi.y, a.lo.y, b.hi.x, b.lo.x);
+        }
+        const double2 t = cmk((double)rh + (double)rl, (double)ih + (double)il);
+        thetaT[((long)z * N + off + j) * M + p0 + pp] = t;
+        const double hv = ht[(long)(off + j) * M + p0 + pp];
+        e1acc.x = fma(hv, t.x, e1acc.x);
+        e1acc.y = fma(hv, t.y, e1acc.y);
+      }
+    }
+  }
+  for (int p0 = 0; p0 < M && !DF; p0 += PC) {
     const int pc = min(PC, M - p0);
     for (int e = tid; e < PC * n; e += OT) {
       const int pp = e / n, j = e % n;
@@ -444,18 +513,27 @@ size_t exchange_smem(int G, int n) {
 
 int exchange_group_size(int nmax) { return nmax > 0 ? (64 / nmax > 1 ? 64 / nmax : 1) : 1; }
 
-int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s) {
+// df: theta by double-float arithmetic (split-precision walker ensembles); S, its
+// determinant and inverse and the one-body energy stay FP64 either way.
+int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s, bool df) {
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
   const size_t smem = overlap_smem(nmax);
   static size_t configured = 0;
   if (smem > configured) {
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_overlap_theta,
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_overlap_theta<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_overlap_theta<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = smem;
   }
-  k_overlap_theta<<<dim3(s.W, 2), OT, smem, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb,
-                                                          ctx->psiT, ctx->ht, s.phi, s.thetaT,
-                                                          s.det, s.e1, ctx->flags);
+  if (df)
+    k_overlap_theta<true><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
+        ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
+        ctx->flags);
+  else
+    k_overlap_theta<false><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
+        ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
+        ctx->flags);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }
