@@ -295,6 +295,7 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
     mix.profile_enable(False)
     ms = ev0.elapsed_time(ev1) / steps
     algo = mix.exchange_algorithm()
+    digits, xest = mix.prop_digits()
     ex_ms, ex_n = prof["exchange"]
     ex_avg = ex_ms / max(ex_n, 1) / 1e3
     if algo == "stored":
@@ -316,9 +317,13 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
                          "exact integer sums in TMEM); exchange " +
                          ("stored V' and theta as 3 exact digits (6 products)" if algo == "stored"
                           else "direct, 3 bf16 float slices (6 products, FP32 accumulation)") +
-                         "; VHS and propagator 4 exact digits; overlaps, inverses, QR and "
+                         "; VHS 4 exact digits; propagator 4 exact digits for the P passes "
+                         "and the leading powers, fewer for the small high powers "
+                         "(prop_digits); theta double-float; overlaps, inverses, QR and "
                          "weights FP64"),
            "exchange_algorithm": algo,
+           "prop_digits": {"per_pass": digits, "sqrt_dt_V2_estimate": xest,
+                           "passes": "first P, Taylor powers 1..n, last P"},
            "dE_L_max_1_step": errs[1], f"dE_L_max_{long_steps}_steps": errs[long_steps],
            "dE_reference": f"FP64 path (parity-checked against the FP64 oracle at 1e-10) on the "
                            f"first {check_walkers} walkers, same Philox fields",

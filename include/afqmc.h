@@ -123,6 +123,12 @@ int afq_trial_energy(afq_ctx* ctx, double* e_out);
 /* The exchange algorithm afq_init_trial resolved params.exchange to:
    AFQ_EXCHANGE_DIRECT or AFQ_EXCHANGE_STORED. */
 int afq_exchange_algorithm(afq_ctx* ctx, int* algo_out);
+/* AFQ_SPLIT_BF16: exact digits of each propagation GEMM pass chosen by
+   afq_init_trial -- digits[0] the first P, digits[1..n] the Taylor powers,
+   digits[n+1] the last P (n = taylor_order; a power with x^k / k! small gets fewer,
+   at most prop_slices) -- and x_out the estimate of sqrt(dt) |V|_2 behind them.
+   Writes min(n + 2, count) entries; AFQ_ERR_STATE in FP64 contexts. */
+int afq_prop_digits(afq_ctx* ctx, int* digits, int count, double* x_out);
 
 /* Walker ensemble of Eq. stat_wfs.  phi: W x M x (na+nb) complex, or NULL for W
    copies of the trial.  w: W real weights, or NULL for all ones.  Computes the

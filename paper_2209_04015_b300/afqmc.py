@@ -51,6 +51,7 @@ _SIGS = {
     "afq_init_trial": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "afq_trial_energy": (ctypes.c_int, [_P, _D]),
     "afq_exchange_algorithm": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "afq_prop_digits": (ctypes.c_int, [_P, _P, ctypes.c_int, _D]),
     "afq_init_walkers": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "afq_propagate": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "afq_propagate_dev": (ctypes.c_int, [_P, _P, ctypes.c_int]),
@@ -210,6 +211,15 @@ class AfqContext:
         a = ctypes.c_int()
         self._check(self.lib.afq_exchange_algorithm(self.h, ctypes.byref(a)))
         return {v: k for k, v in EXCHANGES.items()}[a.value]
+
+    def prop_digits(self) -> tuple[list[int], float]:
+        """Split precision: exact digits per propagation pass (first P, the Taylor
+        powers, last P) and the sqrt(dt) |V|_2 estimate they were chosen for."""
+        n = self.params.taylor_order + 2
+        d = (ctypes.c_int * n)()
+        x = ctypes.c_double()
+        self._check(self.lib.afq_prop_digits(self.h, ctypes.cast(d, _P), n, ctypes.byref(x)))
+        return list(d), x.value
 
     def init_walkers(self, W: int, phi: np.ndarray | None = None,
                      w: np.ndarray | None = None) -> None:

@@ -496,6 +496,16 @@ int afq_exchange_algorithm(afq_ctx* ctx, int* algo_out) {
   return AFQ_OK;
 }
 
+int afq_prop_digits(afq_ctx* ctx, int* digits, int count, double* x_out) {
+  if (!ctx || !digits || count < 0) return AFQ_ERR_ARG;
+  if (!ctx->have_trial || !ctx->mixed)
+    return afq_fail(ctx, AFQ_ERR_STATE, "split-precision context with a trial needed");
+  const int n = ctx->p.taylor_order + 2;
+  for (int i = 0; i < n && i < count; ++i) digits[i] = ctx->prop_digits[i];
+  if (x_out) *x_out = ctx->prop_x;
+  return AFQ_OK;
+}
+
 int afq_init_walkers(afq_ctx* ctx, int W, const double* phi, const double* w) {
   if (!ctx) return AFQ_ERR_ARG;
   if (!ctx->have_trial) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_trial first");

@@ -153,6 +153,11 @@ struct afq_ctx {
   CUtensorMap tm_fb_a, tm_fb_b, tm_ex_a[2], tm_ex_b[2];
   // split-precision propagation operands (k_mixed_prop.cu)
   int Xpad = 0, vhs_BN = 0, prop_rows = 0;  // prop_rows: walker columns per propagation tile
+  // exact digits per propagation GEMM pass: [0] the first P, [1..n] the Taylor powers,
+  // [n+1] the last P (at most Sp; fewer for the small high powers), and the estimate
+  // x = sqrt(dt) |V|_2 they were chosen for
+  int prop_digits[40] = {};
+  double prop_x = 0.0;
   __nv_bfloat16* LT_sl = nullptr;     // S x M^2 x Xpad: L^T, the VHS operand
   __nv_bfloat16* Pm_sl = nullptr;     // S x M x Mpad: P - I
   __nv_bfloat16* y_sl = nullptr;      // S x 2W x Xpad: shifted fields (re, im rows)

@@ -200,24 +200,47 @@ __global__ void k_slice_lt_exact(const double* __restrict__ Lt, int X, int N, in
   }
 }
 
-// theta^T (W x N x M complex) -> integer digit planes [s][z][re/im][N Mpad] with one
-// exponent per (z, re/im) over both spins (one warp per row; zero padding)
-__global__ void k_slice_theta_exact(const double2* __restrict__ thetaT, int W, int N, int M,
-                                    int Mpad, int S, __nv_bfloat16* __restrict__ out,
-                                    int* __restrict__ eb) {
-  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
-  const long W2 = 2L * W, NM = (long)N * M, NMp = (long)N * Mpad, plane = W2 * NMp;
-  for (long col = (long)blockIdx.x * warps + (threadIdx.x >> 5); col < W2;
-       col += (long)gridDim.x * warps) {
-    const double* th = reinterpret_cast<const double*>(thetaT + (col >> 1) * NM) + (col & 1);
+// Exponents of theta^T per (z, re/im) over both spins: one block per walker, the
+// walker's N x M complex values read once, coalesced.
+__global__ void __launch_bounds__(256) k_theta_exponents(const double2* __restrict__ thetaT,
+                                                         long NM, int* __restrict__ eb) {
+  __shared__ int red[2][8];
+  const long z = blockIdx.x;
+  const double2* th = thetaT + z * NM;
+  int mr = 0, mi = 0;
+  for (long e = threadIdx.x; e < NM; e += 256) {
+    const double2 v = th[e];
+    mr = max(mr, exp_field(v.x));
+    mi = max(mi, exp_field(v.y));
+  }
+  mr = warp_max_e(mr);
+  mi = warp_max_e(mi);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = mr;
+    red[1][threadIdx.x >> 5] = mi;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
     int m = 0;
-    for (long e = lane; e < NM; e += 32) m = max(m, exp_field(th[2 * e]));
-    const int ex = row_exponent_field(warp_max_e(m));
-    if (lane == 0) eb[col] = ex;
-    for (long e = lane; e < NMp; e += 32) {
-      const int j = (int)(e / Mpad), p = (int)(e % Mpad);
-      split_exact(p < M ? th[2 * ((long)j * M + p)] : 0.0, ex, S, out + col * NMp + e, plane);
-    }
+    for (int w = 0; w < 8; ++w) m = max(m, red[threadIdx.x][w]);
+    eb[2 * z + threadIdx.x] = row_exponent_field(m);
+  }
+}
+
+// theta^T (W x N x M complex) -> integer digit planes [s][z][re/im][N Mpad] with the
+// exponents above (zero padding); one thread per (z, j, p < Mpad)
+__global__ void k_slice_theta_exact(const double2* __restrict__ thetaT, int W, int N, int M,
+                                    int Mpad, int S, const int* __restrict__ eb,
+                                    __nv_bfloat16* __restrict__ out) {
+  const long NMp = (long)N * Mpad, total = (long)W * NMp, plane = 2 * total;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long z = e / NMp, r = e % NMp;
+    const int j = (int)(r / Mpad), p = (int)(r % Mpad);
+    const double2 v = p < M ? thetaT[(z * N + j) * M + p] : make_double2(0.0, 0.0);
+    __nv_bfloat16* o = out + (2 * z) * NMp + r;
+    split_exact(v.x, eb[2 * z], S, o, plane);
+    split_exact(v.y, eb[2 * z + 1], S, o + NMp, plane);
   }
 }
 
@@ -412,8 +435,10 @@ int mixed_autotune(afq_ctx* ctx) {
 // theta's integer digits (force bias, stored exchange) and, for the direct exchange,
 // its float slices
 int launch_slice_theta(afq_ctx* ctx, WalkerSet& s) {
-  k_slice_theta_exact<<<warp_grid_rows(2L * s.W), 256, 0, ctx->stream>>>(
-      s.thetaT, s.W, ctx->N, ctx->M, ctx->Mpad, ctx->S, ctx->exv_th, ctx->exv_eb);
+  k_theta_exponents<<<s.W, 256, 0, ctx->stream>>>(s.thetaT, (long)ctx->N * ctx->M, ctx->exv_eb);
+  AFQ_LAUNCHED(ctx);
+  k_slice_theta_exact<<<grid1d((long)s.W * ctx->N * ctx->Mpad), 256, 0, ctx->stream>>>(
+      s.thetaT, s.W, ctx->N, ctx->M, ctx->Mpad, ctx->S, ctx->exv_eb, ctx->exv_th);
   AFQ_LAUNCHED(ctx);
   if (ctx->th_sl) {
     const long total = (long)s.W * ctx->N * ctx->Mpad;

@@ -22,6 +22,9 @@
 // j), four MMA streams per slice pair with the negate-A bit for -Im A Im T.  The
 // identity parts stay in FP64: P Phi = Phi + (P - I) Phi, and each Taylor term is
 // added to an FP64 accumulator.
+#include <cmath>
+#include <vector>
+
 #include "tc_engine.cuh"
 
 using namespace tce;
@@ -613,6 +616,95 @@ void mixed_prop_free(afq_ctx* ctx) {
 }
 
 // Once per trial: digits of L^T (the VHS operand) and of P - I, with row exponents.
+// Digits per pass.  A Taylor power u_k = V u_{k-1} enters the sum scaled by
+// g_k = dt^(k/2) / k!, so with x = sqrt(dt) |V|_2 the term is at most x^k / k! of Phi,
+// and cutting both its operands to S exact digits costs about 2^-(8S-1) of the term.
+// Each power gets the fewest digits that keep this below 2^-31 of Phi (the level of
+// the leading term with 4 digits); the P passes keep all Sp.  |V|_2 is estimated at
+// set-up by power iteration on V = sum_g y_g L_g for four seeded N(0,1) field draws,
+// times 1.5 for the force-bias shift and the spread over walkers (a term whose x is
+// twice the estimate still stays near 2^-30).
+int prop_digit_schedule(afq_ctx* ctx) {
+  const int M = ctx->M, X = ctx->X, n = ctx->p.taylor_order, Sp = ctx->Sp;
+  const long MM = (long)M * M;
+  constexpr int kDraws = 4;
+  std::vector<double> y((size_t)kDraws * X), V((size_t)kDraws * MM);
+  uint64_t st = 0x9E3779B97F4A7C15ull;  // splitmix64 stream, Box-Muller pairs
+  auto uni = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  for (size_t i = 0; i < y.size(); i += 2) {
+    const double r = std::sqrt(-2.0 * std::log(uni())), t = 6.283185307179586 * uni();
+    y[i] = r * std::cos(t);
+    if (i + 1 < y.size()) y[i + 1] = r * std::sin(t);
+  }
+  double *dy = nullptr, *dv = nullptr;
+  int rc = AFQ_OK;
+  if (cudaMalloc((void**)&dy, y.size() * 8) != cudaSuccess ||
+      cudaMalloc((void**)&dv, V.size() * 8) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_NOMEM, "propagation digit schedule");
+  if (rc == AFQ_OK && cudaMemcpyAsync(dy, y.data(), y.size() * 8, cudaMemcpyHostToDevice,
+                                      ctx->stream) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "propagation digit schedule");
+  // V_d = sum_g y_dg L_g: (kDraws x X) (X x M^2)
+  if (rc == AFQ_OK)
+    rc = launch_dgemm(ctx, kDraws, (int)MM, X, 1.0, dy, X, 1, 0, ctx->L, MM, 1, 0, 0.0, dv, MM, 1,
+                      0, 1, 1);
+  if (rc == AFQ_OK && (cudaMemcpyAsync(V.data(), dv, V.size() * 8, cudaMemcpyDeviceToHost,
+                                       ctx->stream) != cudaSuccess ||
+                       cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "propagation digit schedule");
+  if (dy) cudaFree(dy);
+  if (dv) cudaFree(dv);
+  if (rc != AFQ_OK) return rc;
+  double rho = 0.0;
+  std::vector<double> v(M), w(M);
+  for (int d = 0; d < kDraws; ++d) {
+    const double* A = V.data() + (size_t)d * MM;
+    for (int p = 0; p < M; ++p) v[p] = 1.0 + 0.01 * p;
+    double lam = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double nv = 0.0;
+      for (int p = 0; p < M; ++p) nv += v[p] * v[p];
+      nv = std::sqrt(nv);
+      if (!(nv > 0.0)) break;
+      for (int p = 0; p < M; ++p) v[p] /= nv;
+      for (int p = 0; p < M; ++p) {
+        double s = 0.0;
+        for (int q = 0; q < M; ++q) s += 0.5 * (A[(size_t)p * M + q] + A[(size_t)q * M + p]) * v[q];
+        w[p] = s;
+      }
+      double r = 0.0;
+      for (int p = 0; p < M; ++p) r += v[p] * w[p];
+      lam = std::fabs(r);
+      v.swap(w);
+    }
+    rho = std::fmax(rho, lam);
+  }
+  const double x = 1.5 * std::sqrt(ctx->p.dt) * rho;
+  ctx->prop_x = x;
+  if (n + 2 > (int)(sizeof(ctx->prop_digits) / sizeof(int)))
+    return afq_fail(ctx, AFQ_ERR_ARG, "Taylor order too high for the split propagation");
+  ctx->prop_digits[0] = ctx->prop_digits[n + 1] = Sp;
+  double term = 1.0;
+  for (int k = 1; k <= n; ++k) {
+    term *= x / k;
+    int S = Sp;
+    if (std::isfinite(term) && term > 0.0) {
+      S = (int)std::ceil((32.0 + std::log2(term)) / 8.0);
+      if (S < 1) S = 1;
+      if (S > Sp) S = Sp;
+    }
+    ctx->prop_digits[k] = S;
+  }
+  return AFQ_OK;
+}
+
 int mixed_prop_init_trial(afq_ctx* ctx) {
   const int S = ctx->Sp, M = ctx->M, X = ctx->X;
   ctx->Xpad = round_up(X, kBK);
@@ -629,7 +721,7 @@ int mixed_prop_init_trial(afq_ctx* ctx) {
   AFQ_LAUNCHED(ctx);
   k_slice_pm<<<warp_grid(M), 256, 0, ctx->stream>>>(ctx->P, M, ctx->Mpad, S, ctx->Pm_sl, ctx->e_pm);
   AFQ_LAUNCHED(ctx);
-  return AFQ_OK;
+  return prop_digit_schedule(ctx);
 }
 
 // Per walker set: operand buffers and tensor maps of the propagation.
@@ -749,9 +841,9 @@ cudaError_t launch_prop_s(int grid, size_t smem, cudaStream_t stream, const CUte
 
 // One GEMM pass of the propagation (mode first / term / last) on operand buffer b.
 template <bool REAL>
-int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int mode) {
+int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int mode, int S) {
   PropArgs a{};
-  const int N = ctx->N, S = ctx->Sp;
+  const int N = ctx->N;
   a.M = ctx->M;
   a.N = N;
   a.W = ctx->ws.W;
@@ -793,8 +885,8 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
 
 // acc += i^k g_k u_k and the digits of u_k (or of acc after the last term) into
 // operand buffer b; rows longer than 512 take the two-kernel form
-int taylor_slice(afq_ctx* ctx, int b, double gk, int kmod, int last) {
-  const int W = ctx->ws.W, N = ctx->N, M = ctx->M, Kp = ctx->Mpad, S = ctx->Sp;
+int taylor_slice(afq_ctx* ctx, int b, double gk, int kmod, int last, int S) {
+  const int W = ctx->ws.W, N = ctx->N, M = ctx->M, Kp = ctx->Mpad;
   const long rows = (long)W * N;
   const int g = warp_grid(rows);
   if (Kp <= 128)
@@ -817,10 +909,10 @@ int taylor_slice(afq_ctx* ctx, int b, double gk, int kmod, int last) {
   return AFQ_OK;
 }
 
-// digits of tout (W x N x M) into Taylor operand buffer b
-int slice_tout(afq_ctx* ctx, int b) {
+// S digits of tout (W x N x M) into Taylor operand buffer b
+int slice_tout(afq_ctx* ctx, int b, int S) {
   const int W = ctx->ws.W, N = ctx->N, M = ctx->M;
-  slice_rows(ctx->tout, (long)W * N, N, M, ctx->Mpad, ctx->Sp, ctx->T_sl[b], ctx->e_t[b],
+  slice_rows(ctx->tout, (long)W * N, N, M, ctx->Mpad, S, ctx->T_sl[b], ctx->e_t[b],
              ctx->stream);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
@@ -837,22 +929,23 @@ int launch_propagate_tc(afq_ctx* ctx) {
       ctx->ws.phi, W, ctx->M, ctx->N, ctx->tout);
   AFQ_LAUNCHED(ctx);
   int cur = 0, rc;
-  if ((rc = slice_tout(ctx, cur)) != AFQ_OK) return rc;
+  const int n = ctx->p.taylor_order;
+  const int* dg = ctx->prop_digits;  // digits of each pass (prop_digit_schedule)
+  if ((rc = slice_tout(ctx, cur, dg[0])) != AFQ_OK) return rc;
   // u_0 = P Phi = Phi + (P - I) Phi, also the first term of the sum: the GEMM writes
   // (P - I) Phi into the sum, the slicing pass adds Phi^T (in tout) and cuts u_0
-  rc = launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeFirst);
+  rc = launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeFirst, dg[0]);
   if (rc != AFQ_OK) return rc;
   cur = 1 - cur;
-  if ((rc = taylor_slice(ctx, cur, 1.0, 0, 1)) != AFQ_OK) return rc;
-  const int n = ctx->p.taylor_order;
+  if ((rc = taylor_slice(ctx, cur, 1.0, 0, 1, dg[n >= 1 ? 1 : n + 1])) != AFQ_OK) return rc;
   double gk = 1.0;
   for (int k = 1; k <= n; ++k) {
-    rc = launch_prop<false>(ctx, ctx->tm_az, cur, ctx->e_a, kModeTerm);
+    rc = launch_prop<false>(ctx, ctx->tm_az, cur, ctx->e_a, kModeTerm, dg[k]);
     if (rc != AFQ_OK) return rc;
     cur = 1 - cur;
     gk *= sqrt(ctx->p.dt) / k;
-    if ((rc = taylor_slice(ctx, cur, gk, k & 3, k == n)) != AFQ_OK) return rc;
+    if ((rc = taylor_slice(ctx, cur, gk, k & 3, k == n, dg[k + 1])) != AFQ_OK) return rc;
   }
   // Phi = P acc = acc + (P - I) acc
-  return launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeLast);
+  return launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeLast, dg[n + 1]);
 }
