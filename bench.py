@@ -128,7 +128,9 @@ def step_flops(W, X, M, na, nb, order=6, exchange="direct"):
     return {
         "force_bias": W * 4 * X * N * M,
         "vhs": W * 4 * X * Mp,
-        "propagate": W * (order * 8 + 2 * 4) * M * M * N,
+        # Taylor powers as 3 real products per complex multiply-add (Gauss), the two
+        # real P applications as 2
+        "propagate": W * (order * 6 + 2 * 4) * M * M * N,
         "overlap_theta": W * sum(4 * M * n * n + 8 * M * n * n for n in (na, nb)),
         "exchange": exchange_flops(W, X, M, na, nb, exchange),
     }

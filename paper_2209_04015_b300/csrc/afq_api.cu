@@ -166,6 +166,7 @@ int free_walkers(afq_ctx* ctx) {
   dfree(&ctx->cfb);
   dfree(&ctx->cmf);
   dfree(&ctx->A);
+  dfree(&ctx->Asum);
   dfree(&ctx->detR);
   dfree(&ctx->fb64_part);
   ctx->fb64_part_wx = 0;
@@ -520,6 +521,7 @@ int afq_init_walkers(afq_ctx* ctx, int W, const double* phi, const double* w) {
   AFQ_TRY(dalloc(ctx, &ctx->cmf, (size_t)W));
   // A holds i sqrt(dt) V per walker during a step and is the QR workspace after it
   AFQ_TRY(dalloc(ctx, &ctx->A, (size_t)W * M * (M > N ? M : N)));
+  if (!ctx->mixed) AFQ_TRY(dalloc(ctx, &ctx->Asum, (size_t)W * M * M));
   AFQ_TRY(dalloc(ctx, &ctx->detR, 2 * (size_t)W));
   AFQ_TRY(dalloc(ctx, &ctx->fb64_part, (size_t)kFbSplitMax * W * ctx->X));
   ctx->fb64_part_wx = (long)W * ctx->X;

@@ -129,6 +129,7 @@ struct afq_ctx {
   double2* cfb = nullptr;    // W
   double2* cmf = nullptr;    // W
   double2* A = nullptr;      // W x M x M  i sqrt(dt) V, symmetric
+  double* Asum = nullptr;    // W x M x M  Re A + Im A (FP64 propagation, 3-product form)
   double* detR = nullptr;    // W x 2
   double2* fb64_part = nullptr;  // kFbSplitMax x W x X: K-split partials of the FP64 force bias
   long fb64_part_wx = 0;         // W X the buffer was sized for

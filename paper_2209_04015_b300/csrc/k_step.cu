@@ -158,7 +158,8 @@ __global__ void __launch_bounds__(256) k_vhs_fp64(int W, int X, int M, int Mp, d
                                                   const double2* __restrict__ y,
                                                   const double* __restrict__ Lpk,
                                                   const int2* __restrict__ tpq,
-                                                  double2* __restrict__ A) {
+                                                  double2* __restrict__ A,
+                                                  double* __restrict__ Asum) {
   __shared__ double2 Ys[VZ][VK];
   __shared__ double Ls[VK][VT];
   const int t0 = blockIdx.x * VT, z0 = blockIdx.y * VZ;
@@ -197,6 +198,11 @@ __global__ void __launch_bounds__(256) k_vhs_fp64(int W, int X, int M, int Mp, d
       const int2 pq = tpq[t];
       Az[(long)pq.x * M + pq.y] = v;
       if (pq.x != pq.y) Az[(long)pq.y * M + pq.x] = v;
+      if (Asum) {  // Re A + Im A, the third operand of the 3-product complex multiply
+        double* Sz = Asum + (long)z * M * M;
+        Sz[(long)pq.x * M + pq.y] = v.x + v.y;
+        if (pq.x != pq.y) Sz[(long)pq.y * M + pq.x] = v.x + v.y;
+      }
     }
   }
 }
@@ -270,21 +276,72 @@ __device__ __forceinline__ void sym_apply_cplx(int M, int p, const double2* __re
   }
 }
 
+// out[c] = sum_q S_qp in[q][cb + c] for a complex symmetric S by Gauss's three real
+// products: with Ssum = Re S + Im S and insum = Re in + Im in,
+//   Re = sum Re S Re in - sum Im S Im in,  Im = sum Ssum insum - (the two sums above),
+// 3 multiply-adds per complex term instead of 4 (the sums cost M and M NC additions).
+template <int NC, int NCg>
+__device__ __forceinline__ void sym_apply_cplx3(int M, int p, const double2* __restrict__ S,
+                                                const double* __restrict__ Ssum,
+                                                const double2* __restrict__ in,
+                                                const double* __restrict__ insum, int cb,
+                                                double2 out[NCg]) {
+  double p1[NCg], p2[NCg], p3[NCg];
+#pragma unroll
+  for (int c = 0; c < NCg; ++c) p1[c] = p2[c] = p3[c] = 0.0;
+  int q = 0;
+  for (; q + 4 <= M; q += 4) {
+    double2 s[4];
+    double ss[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      s[u] = S[(long)(q + u) * M + p];
+      ss[u] = Ssum[(long)(q + u) * M + p];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < NCg; ++c) {
+        const double2 b = in[(q + u) * NC + cb + c];
+        p1[c] = fma(s[u].x, b.x, p1[c]);
+        p2[c] = fma(s[u].y, b.y, p2[c]);
+        p3[c] = fma(ss[u], insum[(q + u) * NC + cb + c], p3[c]);
+      }
+  }
+  for (; q < M; ++q) {
+    const double2 sv = S[(long)q * M + p];
+    const double sv2 = Ssum[(long)q * M + p];
+#pragma unroll
+    for (int c = 0; c < NCg; ++c) {
+      const double2 b = in[q * NC + cb + c];
+      p1[c] = fma(sv.x, b.x, p1[c]);
+      p2[c] = fma(sv.y, b.y, p2[c]);
+      p3[c] = fma(sv2, insum[q * NC + cb + c], p3[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NCg; ++c) out[c] = cmk(p1[c] - p2[c], p3[c] - p1[c] - p2[c]);
+}
+
 // K5 (FP64): Phi <- P T_n(A) P Phi for NC walker columns of one walker per CTA, the
 // current Taylor term in shared memory.  G threads share each row p (each owns NC/G
 // of the columns), so that G M threads fill whole warps for M not a multiple of 32.
 template <int NC, int G>
 __global__ void k_propagate_fp64(int M, int N, int order, const double* __restrict__ P,
-                                 const double2* __restrict__ A, double2* __restrict__ phi) {
+                                 const double2* __restrict__ A, const double* __restrict__ Asum,
+                                 double2* __restrict__ phi) {
   constexpr int NCg = NC / G;
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* cur = reinterpret_cast<double2*>(smraw);  // M x NC
   double2* nxt = cur + M * NC;
   double2* acc = nxt + M * NC;
+  double* curs = reinterpret_cast<double*>(acc + M * NC);  // Re + Im of cur (M x NC)
+  double* nxts = curs + M * NC;
   const int z = blockIdx.y, c0 = blockIdx.x * NC, t = threadIdx.x;
   const bool act = t < G * M;
   const int p = act ? t % M : 0, cb = act ? (t / M) * NCg : 0;
   const double2* Az = A + (long)z * M * M;
+  const double* Sz = Asum + (long)z * M * M;
   double2* phz = phi + (long)z * M * N;
   for (int e = t; e < M * NC; e += blockDim.x) {
     const int q = e / NC, c = e % NC;
@@ -298,6 +355,7 @@ __global__ void k_propagate_fp64(int M, int N, int order, const double* __restri
     for (int c = 0; c < NCg; ++c) {
       acc[p * NC + cb + c] = r[c];
       nxt[p * NC + cb + c] = r[c];
+      nxts[p * NC + cb + c] = r[c].x + r[c].y;
     }
   }
   __syncthreads();
@@ -305,15 +363,19 @@ __global__ void k_propagate_fp64(int M, int N, int order, const double* __restri
     double2* tt = cur;
     cur = nxt;
     nxt = tt;
+    double* ts = curs;
+    curs = nxts;
+    nxts = ts;
   }
   for (int k = 1; k <= order; ++k) {
     const double inv = 1.0 / k;
     if (act) {
-      sym_apply_cplx<NC, NCg>(M, p, Az, cur, cb, r);
+      sym_apply_cplx3<NC, NCg>(M, p, Az, Sz, cur, curs, cb, r);
 #pragma unroll
       for (int c = 0; c < NCg; ++c) {
         const double2 v = cscale(r[c], inv);
         nxt[p * NC + cb + c] = v;
+        nxts[p * NC + cb + c] = v.x + v.y;
         acc[p * NC + cb + c] = cadd(acc[p * NC + cb + c], v);
       }
     }
@@ -321,6 +383,9 @@ __global__ void k_propagate_fp64(int M, int N, int order, const double* __restri
     double2* tt = cur;
     cur = nxt;
     nxt = tt;
+    double* ts = curs;
+    curs = nxts;
+    nxts = ts;
   }
   if (act) {
     sym_apply_real<NC, NCg>(M, p, P, acc, cb, r);
@@ -401,7 +466,7 @@ int launch_philox_fields(afq_ctx* ctx, uint64_t step, double* out, uint32_t* wor
 int launch_vhs_fp64(afq_ctx* ctx) {
   dim3 grid((ctx->Mp + VT - 1) / VT, (ctx->ws.W + VZ - 1) / VZ);
   k_vhs_fp64<<<grid, 256, 0, ctx->stream>>>(ctx->ws.W, ctx->X, ctx->M, ctx->Mp, sqrt(ctx->p.dt),
-                                            ctx->y, ctx->Lpk, ctx->tpq, ctx->A);
+                                            ctx->y, ctx->Lpk, ctx->tpq, ctx->A, ctx->Asum);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }
@@ -409,7 +474,7 @@ int launch_vhs_fp64(afq_ctx* ctx) {
 template <int NC, int G>
 int launch_propagate_g(afq_ctx* ctx) {
   const int threads = 32 * ((G * ctx->M + 31) / 32);
-  const size_t smem = (size_t)3 * ctx->M * NC * sizeof(double2);
+  const size_t smem = (size_t)3 * ctx->M * NC * sizeof(double2) + (size_t)2 * ctx->M * NC * 8;
   static size_t configured = 0;
   if (smem > configured) {
     AFQ_CUDA(ctx, cudaFuncSetAttribute(k_propagate_fp64<NC, G>,
@@ -417,8 +482,9 @@ int launch_propagate_g(afq_ctx* ctx) {
     configured = smem;
   }
   dim3 grid((ctx->N + NC - 1) / NC, ctx->ws.W);
+  if (!ctx->Asum) return afq_fail(ctx, AFQ_ERR_STATE, "FP64 propagation needs Re A + Im A");
   k_propagate_fp64<NC, G><<<grid, threads, smem, ctx->stream>>>(
-      ctx->M, ctx->N, ctx->p.taylor_order, ctx->P, ctx->A, ctx->ws.phi);
+      ctx->M, ctx->N, ctx->p.taylor_order, ctx->P, ctx->A, ctx->Asum, ctx->ws.phi);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }
