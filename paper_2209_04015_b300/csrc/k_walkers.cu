@@ -47,9 +47,37 @@ __device__ double2 block_sum2(double2 v, double2* red) {
 struct DF2 {
   float2 hi, lo;  // complex: (re, im) of the high and the low parts
 };
+// x = h + l from the bits on the integer pipe (B300 runs double <-> float conversions
+// on its 2-lane FP64 pipe): h keeps the top 24 significant bits of x (truncated), l the
+// next 29 rounded to 24, so |x - h - l| <= 2^-48 |x|.  Zero, subnormal and
+// out-of-float-range inputs (not met by walkers or S^-1 of bounded condition) give
+// h = l = 0 or a saturated h.
 __device__ __forceinline__ void df_split(double x, float& h, float& l) {
-  h = __double2float_rn(x);
-  l = __double2float_rn(x - (double)h);
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
+  if (E < 897 || E > 1150) {  // outside the normal float range: zero or saturate
+    h = E < 897 ? 0.f : __int_as_float((int)(sign | 0x7F7FFFFFu));
+    l = 0.f;
+    return;
+  }
+  const long long m = b & 0xFFFFFFFFFFFFFLL;
+  h = __int_as_float((int)(sign | ((unsigned)(E - 896) << 23) | (unsigned)(m >> 29)));
+  const int low = (int)(m & 0x1FFFFFFF);  // the 29 bits below h: low 2^(E - 1075)
+  const int se = E - 1075 + 127;          // biased exponent of 2^(E - 1075)
+  const float scale = se > 0 ? __int_as_float(se << 23) : 0.f;
+  l = (float)low * scale;
+  if (sign) l = -l;
+}
+// float -> double from the bits (normal floats; zero and subnormals give 0)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = (unsigned)__float_as_int(f);
+  const unsigned e = (u >> 23) & 0xFF;
+  if (e == 0) return 0.0;
+  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(e + 896) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFF) << 29);
+  return __longlong_as_double((long long)b);
 }
 // (sh, sl) += a * b for real double-floats a = (ah, al), b = (bh, bl)
 __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh,
@@ -216,7 +244,7 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
           df_mac(ih, il, a.hi.x, a.lo.x, b.hi.y, b.lo.y);
           df_mac(ih, il, a.hi.y, a.lo.y, b.hi.x, b.lo.x);
         }
-        const double2 t = cmk((double)rh + (double)rl, (double)ih + (double)il);
+        const double2 t = cmk(f2d_bits(rh) + f2d_bits(rl), f2d_bits(ih) + f2d_bits(il));
         thetaT[((long)z * N + off + j) * M + p0 + pp] = t;
         const double hv = ht[(long)(off + j) * M + p0 + pp];
         e1acc.x = fma(hv, t.x, e1acc.x);
