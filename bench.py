@@ -41,7 +41,7 @@ FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 nominal: 148 SMs x 2032 MHz x ~4.15 flop
 # these exact workloads (profiles/propagation_fp64_c2.md, profiles/exchange_tc_c3.md);
 # absent where no capture of the current kernel exists.
 TRAFFIC = {("split_bf16", "c3", "exchange_direct"): 572279808 + 10032128,
-           ("fp64", "c2", "propagate"): 24697856 + 0}  # captured with 4 columns per CTA
+           ("fp64", "c2", "propagate"): 34943232 + 16384}  # captured with 2 columns per CTA
 FP64_KERNELS = {"propagate": "k_propagate_fp64", "exchange": "k_exchange_v / k_exchange_fp64",
                 "vhs": "k_vhs_fp64", "force_bias": "k_force_bias_fp64"}
 SPLIT_PRODUCTS = 6          # bf16 slice products of 3 slices or digits (s + t <= 2)
@@ -605,7 +605,7 @@ def run_afq(args):
                      "achieved": dom_achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                      "frac": dom_achieved / FP64_NOMINAL_TFLOPS,
                      "traffic": (TRAFFIC.get(("fp64", WORKLOAD, dom))
-                                 if W == 128 and (dom != "propagate" or tiles[1] == 4) else None),
+                                 if W == 128 and (dom != "propagate" or tiles[1] == 2) else None),
                      "peak_source": "FP64 nominal (148 SMs x 2032 MHz x 4.15 flop/clk/SM)",
                      "flops_per_launch": flops[dom], "avg_launch_ms": dom_avg_s * 1e3},
         "exchange_algorithm": ex_algo,
