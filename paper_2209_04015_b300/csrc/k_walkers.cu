@@ -92,7 +92,9 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
   sh = t;
 }
 
-template <bool DF>
+// MO: S entries per thread (n^2 <= OT MO); the launch picks the smallest that fits,
+// so that the accumulators do not hold registers sized for 64 electrons.
+template <bool DF, int MO>
 __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int nb,
                                                       const double* __restrict__ psiT,
                                                       const double* __restrict__ ht,
@@ -121,9 +123,9 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
   const double2* phiz = phi + (long)z * M * N;
 
   // 1. S_ij = sum_p Psi_pi Phi_pj
-  double2 acc[MAXO1];
+  double2 acc[MO];
 #pragma unroll
-  for (int k = 0; k < MAXO1; ++k) acc[k] = cmk(0.0, 0.0);
+  for (int k = 0; k < MO; ++k) acc[k] = cmk(0.0, 0.0);
   for (int p0 = 0; p0 < M; p0 += PC) {
     const int pc = min(PC, M - p0);
     for (int e = tid; e < PC * n; e += OT) {
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < MAXO1; ++k) {
+    for (int k = 0; k < MO; ++k) {
       const int o = tid + k * OT;
       if (o < n * n) {
         const int i = o / n, j = o % n;
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
     __syncthreads();
   }
 #pragma unroll
-  for (int k = 0; k < MAXO1; ++k) {
+  for (int k = 0; k < MO; ++k) {
     const int o = tid + k * OT;
     if (o < n * n) {
       const int i = o / n, j = o % n;
@@ -543,27 +545,36 @@ int exchange_group_size(int nmax) { return nmax > 0 ? (64 / nmax > 1 ? 64 / nmax
 
 // df: theta by double-float arithmetic (split-precision walker ensembles); S, its
 // determinant and inverse and the one-body energy stay FP64 either way.
-int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s, bool df) {
+template <bool DF, int MO>
+int launch_overlap_mo(afq_ctx* ctx, WalkerSet& s) {
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
   const size_t smem = overlap_smem(nmax);
   static size_t configured = 0;
   if (smem > configured) {
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_overlap_theta<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_overlap_theta<true>,
+    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_overlap_theta<DF, MO>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = smem;
   }
-  if (df)
-    k_overlap_theta<true><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
-        ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
-        ctx->flags);
-  else
-    k_overlap_theta<false><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
-        ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
-        ctx->flags);
+  k_overlap_theta<DF, MO><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
+      ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
+      ctx->flags);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
+}
+
+template <bool DF>
+int launch_overlap_df(afq_ctx* ctx, WalkerSet& s) {
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  const int need = (nmax * nmax + OT - 1) / OT;
+  if (need <= 1) return launch_overlap_mo<DF, 1>(ctx, s);
+  if (need <= 2) return launch_overlap_mo<DF, 2>(ctx, s);
+  if (need <= 4) return launch_overlap_mo<DF, 4>(ctx, s);
+  if (need <= 8) return launch_overlap_mo<DF, 8>(ctx, s);
+  return launch_overlap_mo<DF, MAXO1>(ctx, s);
+}
+
+int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s, bool df) {
+  return df ? launch_overlap_df<true>(ctx, s) : launch_overlap_df<false>(ctx, s);
 }
 
 // c = L~ theta over K = N M.  Small grids are split over K (partial sums reduced in a
