@@ -226,9 +226,9 @@ int mixed_exchange_v_init(afq_ctx* ctx) {
 }
 
 // Per walker set (after the theta digit planes exist): y, the column tile and the
-// B-operand map.  The column tile is the widest (<= 128, S accumulators fit TMEM)
-// that still gives about two CTAs per SM, but not below 64 (narrower MMAs waste the
-// tensor core on re-reading A).
+// B-operand map.  The column tile is the widest that fits the S accumulators in TMEM
+// with little padding (pick_bn) and still gives about two CTAs per SM, but not below
+// 64 (narrower MMAs waste the tensor core on re-reading A).
 int mixed_exchange_v_walkers(afq_ctx* ctx) {
   if (ctx->exv_y) cudaFree(ctx->exv_y);
   ctx->exv_y = nullptr;
@@ -236,9 +236,8 @@ int mixed_exchange_v_walkers(afq_ctx* ctx) {
   const ExVGeom g = geometry(ctx, ctx->Mpad);
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->exv_y, (size_t)W2 * (g.Ka + g.Kb) * sizeof(double)));
   const int rows = g.nrt_a + g.nrt_b;
-  int BN = 128;
+  int BN = pick_bn(W2, ctx->S, 256);
   while (BN > 64 && rows * ((W2 + BN - 1) / BN) < 2 * 148) BN -= 16;
-  if (BN > round_up(W2, 16)) BN = round_up(W2, 16);
   ctx->exv_BN = BN;
   const uint64_t db[3] = {(uint64_t)ctx->N * ctx->Mpad, (uint64_t)W2, (uint64_t)ctx->S};
   const uint32_t bb[3] = {kBK, (uint32_t)ctx->exv_BN, 1};

@@ -340,7 +340,7 @@ int mixed_init_walkers(afq_ctx* ctx) {
                              (size_t)S * W * 2 * N * Mp * sizeof(__nv_bfloat16)));
   // force bias: rows g (X), columns (z, re/im) (2W), K = N Mpad; S digit accumulators
   // of BN columns fit the 512 TMEM columns
-  ctx->fb_BN = W2 >= 128 ? 128 : round_up(W2, 16);
+  ctx->fb_BN = pick_bn(W2, S, 256);
   const int nkb = N * Mp / kBK;
   const int tiles = ((X + 127) / 128) * ((W2 + ctx->fb_BN - 1) / ctx->fb_BN);
   int ks = (296 + tiles - 1) / tiles;

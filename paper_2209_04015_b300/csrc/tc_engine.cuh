@@ -362,6 +362,18 @@ inline uint32_t tmem_cols_for(int cols) {
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// Column tile for `cols` GEMM columns with S TMEM accumulators of BN columns each
+// (S BN <= 512, BN a multiple of 16, <= cap): the fewest tiles (wider tiles re-read
+// A less often), and among tilings with that count the narrowest (least padding).
+inline int pick_bn(int cols, int S, int cap) {
+  int hi = 512 / (S > 0 ? S : 1);
+  if (hi > cap) hi = cap;
+  hi -= hi % 16;
+  if (hi < 16) hi = 16;
+  const int tiles = (cols + hi - 1) / hi;
+  return round_up((cols + tiles - 1) / tiles, 16);
+}
+
 // Ring depth and dynamic shared memory for a policy shape; stages = 0 if even one
 // stage does not fit.
 inline void plan_smem(int S, int kUA, int kUB, int BN, size_t epilogue_bytes, int* stages,

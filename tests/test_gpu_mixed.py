@@ -63,7 +63,7 @@ def mixed_vs_oracle(s, W, phi, nsteps, fields=None, **kw):
 
 
 @pytest.mark.parametrize("exchange", ["direct", "stored"])
-@pytest.mark.parametrize("cfg", ["ragged", "wide", "uneven", "c2"])
+@pytest.mark.parametrize("cfg", ["ragged", "wide", "uneven", "one_spin", "c2"])
 def test_mixed_energy_within_1e6_of_fp64_oracle(cfg, exchange):
     if cfg == "ragged":
         s = make_system(37, 5, 3, 71, seed=4, decay="geometric", e0=0.37)
@@ -78,6 +78,10 @@ def test_mixed_energy_within_1e6_of_fp64_oracle(cfg, exchange):
         # unequal spins (two exchange launches), one electron in one spin
         s = make_system(45, 9, 1, 57, seed=8, decay="geometric", e0=0.1)
         W = 5
+    elif cfg == "one_spin":
+        # no beta electrons: the beta blocks of every contraction are empty
+        s = make_system(50, 7, 0, 66, seed=12, decay="geometric", e0=0.2)
+        W = 9
     else:
         s, c = make_config("c2")
         W = c["W"]
