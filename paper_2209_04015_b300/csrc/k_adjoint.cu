@@ -155,6 +155,16 @@ __global__ void k_bwd_theta_sum(int W, long NM, const double2* __restrict__ thet
   }
 }
 
+// Y[(i,q),(j,p)] = Y[(j,p),(i,q)] for the blocks i < j (Y: n M x n M, blocks M x M)
+__global__ void k_mirror_blocks(int n, int M, double* __restrict__ Y) {
+  const long nM = (long)n * M, total = nM * nM;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long r = e / nM, c = e % nM;
+    if (r / M < c / M) Y[e] = Y[c * nM + r];
+  }
+}
+
 int bwd_grid(long n, int threads) {
   const long g = (n + threads - 1) / threads;
   return (int)(g < 148 * 16 ? (g < 1 ? 1 : g) : 148 * 16);
@@ -274,12 +284,17 @@ int adjoint_energy_core(afq_ctx* ctx, WalkerSet& t, const double2* gE, double* d
       if (rc == AFQ_OK)
         rc = launch_dgemm(ctx, X, (int)nM, W, -1.0, qr + 1, 2, 2L * X, 0, th + o2 + 1, 2 * NM, 2,
                           0, 1.0, Fs, NM, 1, 0, 1, 1);
-      // Y: for each j, the blocks (q, p) of every i: Re sum_z u_z[j][q] theta_z[i][p]
+      // Y: for each j, the blocks (q, p) of the i >= j: Re sum_z u_z[j][q] theta_z[i][p];
+      // Y is symmetric, so the blocks i < j are the transposes of blocks (j, i)
       for (int j = 0; j < n && rc == AFQ_OK; ++j)
         for (int ri = 0; ri < 2 && rc == AFQ_OK; ++ri)
           rc = launch_dgemm(ctx, M, M, W, ri ? -1.0 : 1.0, ur + 2L * (off + j) * M + ri, 2, 2 * NM,
-                            0, th + o2 + ri, 2 * NM, 2, 2L * M, ri ? 1.0 : 0.0, Y + (long)j * M,
-                            nM, 1, (long)M * nM, n, 1);
+                            0, th + o2 + ri + 2L * j * M, 2 * NM, 2, 2L * M, ri ? 1.0 : 0.0,
+                            Y + (long)j * M + (long)j * M * nM, nM, 1, (long)M * nM, n - j, 1);
+      if (rc == AFQ_OK && n > 1) {
+        k_mirror_blocks<<<bwd_grid((long)n * n * M * M, 256), 256, 0, ctx->stream>>>(n, M, Y);
+        rc = launched(ctx);
+      }
       // F -= L~ Y
       if (rc == AFQ_OK)
         rc = launch_dgemm(ctx, X, (int)nM, (int)nM, -1.0, ctx->Lt + (long)off * M, NM, 1, 0, Y,
