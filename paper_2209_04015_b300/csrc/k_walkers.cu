@@ -465,10 +465,10 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
                                             double2* __restrict__ phi, double2* __restrict__ Qw,
                                             double* __restrict__ detR, int* flags) {
   __shared__ double2 rs[AFQ_NMAX];
-  __shared__ double2 red[8];
+  __shared__ double2 red[32];
   __shared__ double s_norm;
   const int z = blockIdx.x, s = blockIdx.y, tid = threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5;
+  const int lane = tid & 31, wid = tid >> 5, nt = blockDim.x, nw = nt >> 5;
   const int n = s ? nb : na, off = s ? na : 0;
   if (n == 0) {
     if (tid == 0) detR[2 * z + s] = 1.0;
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
   }
   double2* phz = phi + (long)z * M * N;
   double2* Q = Qw + ((long)z * N + off) * M;  // column j at Q + j * M
-  for (int e = tid; e < M * n; e += 256) {
+  for (int e = tid; e < M * n; e += nt) {
     const int p = e / n, j = e % n;
     Q[(long)j * M + p] = phz[(long)p * N + off + j];
   }
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
   for (int j = 0; j < n; ++j) {
     double2* v = Q + (long)j * M;
     for (int pass = 0; pass < 2; ++pass) {
-      for (int i = wid; i < j; i += 8) {
+      for (int i = wid; i < j; i += nw) {
         const double2* qi = Q + (long)i * M;
         double2 d = cmk(0.0, 0.0);
         for (int p = lane; p < M; p += 32) d = cfma_conj(qi[p], v[p], d);
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
         if (lane == 0) rs[i] = d;
       }
       __syncthreads();
-      for (int p = tid; p < M; p += 256) {
+      for (int p = tid; p < M; p += nt) {
         double2 t = v[p];
         for (int i = 0; i < j; ++i) t = cfms(Q[(long)i * M + p], rs[i], t);
         v[p] = t;
@@ -501,18 +501,18 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
       __syncthreads();
     }
     double2 nr = cmk(0.0, 0.0);
-    for (int p = tid; p < M; p += 256) nr.x += cabs2(v[p]);
+    for (int p = tid; p < M; p += nt) nr.x += cabs2(v[p]);
     nr = block_sum2(nr, red);
     if (tid == 0) s_norm = sqrt(nr.x);
     __syncthreads();
     const double rjj = s_norm;
     if (!(rjj > 0.0) && tid == 0) atomicAdd(&flags[0], 1);
     const double inv = rjj > 0.0 ? 1.0 / rjj : 1.0;
-    for (int p = tid; p < M; p += 256) v[p] = cscale(v[p], inv);
+    for (int p = tid; p < M; p += nt) v[p] = cscale(v[p], inv);
     logdet += log(rjj > 0.0 ? rjj : 1.0);
     __syncthreads();
   }
-  for (int e = tid; e < M * n; e += 256) {
+  for (int e = tid; e < M * n; e += nt) {
     const int p = e / n, j = e % n;
     phz[(long)p * N + off + j] = Q[(long)j * M + p];
   }
@@ -656,7 +656,13 @@ int launch_energy_assemble(afq_ctx* ctx, WalkerSet& s) {
 }
 
 int launch_qr(afq_ctx* ctx, WalkerSet& s, double2* Qw) {
-  k_qr<<<dim3(s.W, 2), 256, 0, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb, s.phi, Qw,
+  // one thread per orbital row up to 256 (whole warps); larger M loops over the rows
+  // (the FP64 pipe is already busy with several 256-thread CTAs per SM: measured no
+  // gain from 320 threads at M = 290)
+  int nt = (ctx->M + 31) / 32 * 32;
+  if (nt < 64) nt = 64;
+  if (nt > 256) nt = 256;
+  k_qr<<<dim3(s.W, 2), nt, 0, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb, s.phi, Qw,
                                               ctx->detR, ctx->flags);
   AFQ_LAUNCHED(ctx);
   k_qr_finish<<<(s.W + 127) / 128, 128, 0, ctx->stream>>>(s.W, ctx->detR, s.ovlp);

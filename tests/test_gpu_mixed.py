@@ -146,3 +146,34 @@ def test_mixed_c3_shape_sampled_walkers(exchange):
         assert np.max(np.abs(e[:, 3] - er[:, 3])) <= tol
         assert np.max(np.abs(e[:, 2] - er[:, 2])) <= tol
         assert np.max(np.abs(e[:, 1] - er[:, 1])) <= E_TOL   # Coulomb (exact digits)
+
+
+def test_propagation_digit_schedule():
+    """The split propagation keeps all prop_slices digits on the two P passes and on
+    powers larger than ~1e-3 of Phi, and never more digits on a power than on the
+    one before it; an FP64 context has no schedule."""
+    from paper_2209_04015_b300 import AfqContext
+    from paper_2209_04015_b300.afqmc import AFQ_ERR_STATE, AfqError
+    s, c = make_config("c2")
+    for slices in (4, 3):
+        ctx = AfqContext(dt=0.005, precision="split_bf16", prop_slices=slices)
+        ctx.init_hamiltonian(s.h1, s.L, s.e0)
+        ctx.init_trial(s.psi_a, s.psi_b)
+        digits, x = ctx.prop_digits()
+        n = ctx.params.taylor_order
+        assert len(digits) == n + 2 and digits[0] == digits[-1] == slices
+        powers = digits[1:-1]
+        assert all(1 <= d <= slices for d in powers)
+        assert all(a >= b for a, b in zip(powers, powers[1:]))
+        assert 0.01 < x < 1.0
+        import math
+        for k, d in enumerate(powers, start=1):
+            if x ** k / math.factorial(k) > 1e-3:
+                assert d == slices, (k, d)
+        ctx.close()
+    fp = AfqContext(dt=0.005)
+    fp.init_hamiltonian(s.h1, s.L, s.e0)
+    fp.init_trial(s.psi_a, s.psi_b)
+    with pytest.raises(AfqError) as e:
+        fp.prop_digits()
+    assert e.value.code == AFQ_ERR_STATE
