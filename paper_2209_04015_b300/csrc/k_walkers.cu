@@ -163,7 +163,13 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
   if (tid == 0) s_det = cmk(1.0, 0.0);
   __syncthreads();
 
-  // 2. Gauss-Jordan elimination with partial pivoting (ties -> lowest row)
+  // 2. Gauss-Jordan elimination with partial pivoting (ties -> lowest row).  Per pivot
+  // three barriers: warp 0 picks the pivot row and its reciprocal; all threads swap
+  // the pivot row into place scaled by the reciprocal and keep the column-kc factors
+  // of the other rows; then every other row is updated on the columns not yet reduced
+  // (left columns > kc and the whole right half), warps over rows, lanes over columns.
+  __shared__ double2 s_inv, s_old;
+  const int wid = tid >> 5, lane = tid & 31;
   for (int kc = 0; kc < n; ++kc) {
     if (tid < 32) {
       double best = -1.0;
@@ -177,33 +183,36 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (tid == 0) s_piv = bi;
+      if (tid == 0) {
+        double2 pv = aug[bi * n2 + kc];
+        const bool bad = !(cabs2(pv) >= 1e-300);
+        if (bad) atomicAdd(&flags[0], 1);
+        const double2 d = cmul(s_det, pv);
+        s_det = bi != kc ? cmk(-d.x, -d.y) : d;
+        if (bad) pv = cmk(1.0, 0.0);
+        s_inv = cdiv(cmk(1.0, 0.0), pv);
+        s_old = aug[kc * n2 + kc];  // column kc of the row that moves to row bi
+        s_piv = bi;
+      }
     }
     __syncthreads();
     const int piv = s_piv;
-    if (piv != kc)
-      for (int c = tid; c < n2; c += OT) {
-        const double2 t = aug[kc * n2 + c];
-        aug[kc * n2 + c] = aug[piv * n2 + c];
-        aug[piv * n2 + c] = t;
-      }
-    __syncthreads();
-    double2 pv = aug[kc * n2 + kc];
-    const bool bad = !(cabs2(pv) >= 1e-300);
-    if (tid == 0) {
-      if (bad) atomicAdd(&flags[0], 1);
-      double2 d = cmul(s_det, pv);
-      s_det = piv != kc ? cmk(-d.x, -d.y) : d;
+    const double2 inv = s_inv;
+    // factors of column kc for the rows after the swap (row piv receives old row kc;
+    // the swap below writes only rows kc and piv, so the other reads are unaffected)
+    for (int r = tid; r < n; r += OT)
+      if (r != kc) fac[r] = r == piv ? s_old : aug[r * n2 + kc];
+    for (int c = kc + tid; c < n2; c += OT) {
+      const double2 top = aug[piv * n2 + c];
+      if (piv != kc) aug[piv * n2 + c] = aug[kc * n2 + c];
+      aug[kc * n2 + c] = cmul(top, inv);
     }
-    if (bad) pv = cmk(1.0, 0.0);
-    const double2 inv = cdiv(cmk(1.0, 0.0), pv);
-    for (int r = tid; r < n; r += OT) fac[r] = aug[r * n2 + kc];
     __syncthreads();
-    for (int c = tid; c < n2; c += OT) aug[kc * n2 + c] = cmul(aug[kc * n2 + c], inv);
-    __syncthreads();
-    for (int e = tid; e < n * n2; e += OT) {
-      const int r = e / n2, c = e % n2;
-      if (r != kc) aug[e] = cfms(fac[r], aug[kc * n2 + c], aug[e]);
+    for (int r = wid; r < n; r += OT / 32) {
+      if (r == kc) continue;
+      const double2 f = fac[r];
+      for (int c = kc + 1 + lane; c < n2; c += 32)
+        aug[r * n2 + c] = cfms(f, aug[kc * n2 + c], aug[r * n2 + c]);
     }
     __syncthreads();
   }
