@@ -83,6 +83,11 @@ __global__ void __launch_bounds__(BT) k_bwd_dphi(int M, int N, int na, int nb,
     W1[i * n + j] = wv;
   }
   __syncthreads();
+  // Gauss-Jordan with partial pivoting, three barriers per pivot (as in the forward
+  // overlap kernel): pivot and reciprocal in warp 0; swap, scaling and the column
+  // factors in one phase; updates of the unreduced columns, warps over rows
+  __shared__ double2 s_inv, s_old;
+  const int wid = tid >> 5, lane = tid & 31;
   for (int kc = 0; kc < n; ++kc) {
     if (tid < 32) {
       double best = -1.0;
@@ -96,27 +101,30 @@ __global__ void __launch_bounds__(BT) k_bwd_dphi(int M, int N, int na, int nb,
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (tid == 0) s_piv = bi;
+      if (tid == 0) {
+        double2 pv = aug[bi * n2 + kc];
+        if (!(cabs2(pv) >= 1e-300)) pv = cmk(1.0, 0.0);
+        s_inv = cdiv(cmk(1.0, 0.0), pv);
+        s_old = aug[kc * n2 + kc];
+        s_piv = bi;
+      }
     }
     __syncthreads();
     const int piv = s_piv;
-    if (piv != kc)
-      for (int cc = tid; cc < n2; cc += BT) {
-        const double2 t = aug[kc * n2 + cc];
-        aug[kc * n2 + cc] = aug[piv * n2 + cc];
-        aug[piv * n2 + cc] = t;
-      }
+    const double2 inv = s_inv;
+    for (int r = tid; r < n; r += BT)
+      if (r != kc) fac[r] = r == piv ? s_old : aug[r * n2 + kc];
+    for (int c = kc + tid; c < n2; c += BT) {
+      const double2 top = aug[piv * n2 + c];
+      if (piv != kc) aug[piv * n2 + c] = aug[kc * n2 + c];
+      aug[kc * n2 + c] = cmul(top, inv);
+    }
     __syncthreads();
-    double2 pv = aug[kc * n2 + kc];
-    if (!(cabs2(pv) >= 1e-300)) pv = cmk(1.0, 0.0);
-    const double2 inv = cdiv(cmk(1.0, 0.0), pv);
-    for (int r = tid; r < n; r += BT) fac[r] = aug[r * n2 + kc];
-    __syncthreads();
-    for (int cc = tid; cc < n2; cc += BT) aug[kc * n2 + cc] = cmul(aug[kc * n2 + cc], inv);
-    __syncthreads();
-    for (int e = tid; e < n * n2; e += BT) {
-      const int r = e / n2, cc = e % n2;
-      if (r != kc) aug[e] = cfms(fac[r], aug[kc * n2 + cc], aug[e]);
+    for (int r = wid; r < n; r += BT / 32) {
+      if (r == kc) continue;
+      const double2 f = fac[r];
+      for (int c = kc + 1 + lane; c < n2; c += 32)
+        aug[r * n2 + c] = cfms(f, aug[kc * n2 + c], aug[r * n2 + c]);
     }
     __syncthreads();
   }

@@ -476,6 +476,7 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
   __shared__ double2 rs[AFQ_NMAX];
   __shared__ double2 red[32];
   __shared__ double s_norm;
+  __shared__ double rdiag[AFQ_NMAX];  // diag R, logged once at the end
   const int z = blockIdx.x, s = blockIdx.y, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nt = blockDim.x, nw = nt >> 5;
   const int n = s ? nb : na, off = s ? na : 0;
@@ -490,7 +491,6 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
     Q[(long)j * M + p] = phz[(long)p * N + off + j];
   }
   __syncthreads();
-  double logdet = 0.0;
   for (int j = 0; j < n; ++j) {
     double2* v = Q + (long)j * M;
     for (int pass = 0; pass < 2; ++pass) {
@@ -512,15 +512,21 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
     double2 nr = cmk(0.0, 0.0);
     for (int p = tid; p < M; p += nt) nr.x += cabs2(v[p]);
     nr = block_sum2(nr, red);
-    if (tid == 0) s_norm = sqrt(nr.x);
+    if (tid == 0) {
+      const double rjj = sqrt(nr.x);
+      if (!(rjj > 0.0)) atomicAdd(&flags[0], 1);
+      s_norm = rjj > 0.0 ? 1.0 / rjj : 1.0;
+      rdiag[j] = rjj > 0.0 ? rjj : 1.0;
+    }
     __syncthreads();
-    const double rjj = s_norm;
-    if (!(rjj > 0.0) && tid == 0) atomicAdd(&flags[0], 1);
-    const double inv = rjj > 0.0 ? 1.0 / rjj : 1.0;
+    const double inv = s_norm;
     for (int p = tid; p < M; p += nt) v[p] = cscale(v[p], inv);
-    logdet += log(rjj > 0.0 ? rjj : 1.0);
     __syncthreads();
   }
+  // log det R = sum_j log R_jj, the logs in parallel off the column loop
+  double lg = 0.0;
+  for (int j = tid; j < n; j += nt) lg += log(rdiag[j]);
+  const double logdet = block_sum2(cmk(lg, 0.0), red).x;
   for (int e = tid; e < M * n; e += nt) {
     const int p = e / n, j = e % n;
     phz[(long)p * N + off + j] = Q[(long)j * M + p];
