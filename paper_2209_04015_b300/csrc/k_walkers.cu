@@ -467,15 +467,21 @@ __global__ void __launch_bounds__(256) k_energy_assemble(int X, int ngroups, dou
 }
 
 // ---------------------------------------------------------------------------
-// K7: QR of each spin block by classical Gram-Schmidt applied twice (CGS2), which
-// yields diag(R) real and positive.  Works on a column-major copy Qw of the block.
+// K7: QR of each spin block by classical Gram-Schmidt with reorthogonalisation
+// (Daniel, Gragg, Kaufman and Stewart, Math. Comp. 30, 1976): a column is projected
+// once, and a second time only when the first projection removed more than half of
+// its squared norm (|v'|^2 < |v|^2 / 2); otherwise the one pass already leaves it
+// orthogonal to working precision.  Walkers re-orthogonalised every few steps are
+// close to orthonormal, so the second pass (half of classical Gram-Schmidt twice) is
+// rarely taken.  diag(R) comes out real and positive.  Works on a column-major copy Qw.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
                                             double2* __restrict__ phi, double2* __restrict__ Qw,
                                             double* __restrict__ detR, int* flags) {
-  __shared__ double2 rs[AFQ_NMAX];
+  __shared__ double2 rs[AFQ_NMAX + 1];
   __shared__ double2 red[32];
   __shared__ double s_norm;
+  __shared__ int s_again;
   __shared__ double rdiag[AFQ_NMAX];  // diag R, logged once at the end
   const int z = blockIdx.x, s = blockIdx.y, tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5, nt = blockDim.x, nw = nt >> 5;
@@ -494,31 +500,40 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
   for (int j = 0; j < n; ++j) {
     double2* v = Q + (long)j * M;
     for (int pass = 0; pass < 2; ++pass) {
-      for (int i = wid; i < j; i += nw) {
-        const double2* qi = Q + (long)i * M;
-        double2 d = cmk(0.0, 0.0);
-        for (int p = lane; p < M; p += 32) d = cfma_conj(qi[p], v[p], d);
-        d = warp_sum2(d);
-        if (lane == 0) rs[i] = d;
+      if (j > 0) {
+        // r_i = q_i^H v for i < j; the first pass also takes |v|^2 as index j
+        const int last = pass == 0 ? j : j - 1;
+        for (int i = wid; i <= last; i += nw) {
+          const double2* qi = i < j ? Q + (long)i * M : v;
+          double2 d = cmk(0.0, 0.0);
+          for (int p = lane; p < M; p += 32) d = cfma_conj(qi[p], v[p], d);
+          d = warp_sum2(d);
+          if (lane == 0) rs[i] = d;
+        }
+        __syncthreads();
+        for (int p = tid; p < M; p += nt) {
+          double2 t = v[p];
+          for (int i = 0; i < j; ++i) t = cfms(Q[(long)i * M + p], rs[i], t);
+          v[p] = t;
+        }
+        __syncthreads();
+      }
+      double2 nr = cmk(0.0, 0.0);
+      for (int p = tid; p < M; p += nt) nr.x += cabs2(v[p]);
+      nr = block_sum2(nr, red);
+      if (tid == 0) {
+        const int again = pass == 0 && j > 0 && nr.x < 0.5 * rs[j].x;
+        s_again = again;
+        if (!again) {
+          const double rjj = sqrt(nr.x);
+          if (!(rjj > 0.0)) atomicAdd(&flags[0], 1);
+          s_norm = rjj > 0.0 ? 1.0 / rjj : 1.0;
+          rdiag[j] = rjj > 0.0 ? rjj : 1.0;
+        }
       }
       __syncthreads();
-      for (int p = tid; p < M; p += nt) {
-        double2 t = v[p];
-        for (int i = 0; i < j; ++i) t = cfms(Q[(long)i * M + p], rs[i], t);
-        v[p] = t;
-      }
-      __syncthreads();
+      if (!s_again) break;
     }
-    double2 nr = cmk(0.0, 0.0);
-    for (int p = tid; p < M; p += nt) nr.x += cabs2(v[p]);
-    nr = block_sum2(nr, red);
-    if (tid == 0) {
-      const double rjj = sqrt(nr.x);
-      if (!(rjj > 0.0)) atomicAdd(&flags[0], 1);
-      s_norm = rjj > 0.0 ? 1.0 / rjj : 1.0;
-      rdiag[j] = rjj > 0.0 ? rjj : 1.0;
-    }
-    __syncthreads();
     const double inv = s_norm;
     for (int p = tid; p < M; p += nt) v[p] = cscale(v[p], inv);
     __syncthreads();

@@ -140,6 +140,27 @@ def test_orthogonalise_entry_point():
     assert np.max(rel(e_after[:, 3], e_before[:, 3])) <= TOL
 
 
+def test_orthogonalise_nearly_dependent_columns():
+    """Second columns of each spin block within 1e-4 of the first (condition ~1e4)
+    take the Gram-Schmidt reorthogonalisation pass: Q matches the oracle's Householder
+    QR and stays orthonormal to working precision (a single classical pass would lose
+    orthogonality at ~eps cond^2 ~ 1e-8)."""
+    s = ragged_system(seed=3)
+    W, na = 6, RAGGED["na"]
+    phi = perturbed_walkers(s, W, eps=0.3, seed=11)
+    for c0 in (0, na):
+        phi[:, :, c0 + 1] = phi[:, :, c0] + 1e-4 * phi[:, :, c0 + 1]
+    ctx, orc = make_pair(s, W, phi=phi)
+    ctx.orthogonalise()
+    orc.orthogonalise()
+    assert_state_parity(ctx, orc, TOL)
+    q = ctx.get_walkers()
+    for cols in (slice(0, na), slice(na, None)):
+        qs = q[:, :, cols]
+        gram = np.einsum("zpi,zpj->zij", qs.conj(), qs)
+        assert np.max(np.abs(gram - np.eye(qs.shape[2]))) <= 1e-13
+
+
 def test_checkpoint_resume_is_bit_exact():
     s, c = make_config("c1")
     W = c["W"]
