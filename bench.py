@@ -280,11 +280,11 @@ def block_leg(name: str, precision: str, rank: int, blocks: int = 4, block_steps
 
 def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int = 16,
               long_steps: int = 100, walkers: int = 0, fp64_compare: bool = False) -> dict:
-    long_steps = max(long_steps, 0)  # 0: no drift check (no FP64 reference context)
-    """Split-precision (tcgen05) throughput on one workload, and its |dE_L| against
+    """Split-precision (tcgen05) throughput on one workload, and its errors against
     the FP64 path on the first walkers after 1 and after long_steps steps.  Walkers
     are independent and the Philox counters are keyed by walker index, so an FP64
     context holding only the first walkers sees exactly the same fields."""
+    long_steps = max(long_steps, 0)  # 0: no drift check (no FP64 reference context)
     import torch
     from paper_2209_04015_b300 import AfqContext
     from paper_2209_04015_b300.synthetic import make_config
@@ -294,25 +294,50 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
     check_walkers = min(check_walkers, W)
     stream = torch.cuda.current_stream()
 
-    def context(precision, nw):
+    def context(precision, nw, phi=None):
         ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, precision=precision,
                          stream=stream.cuda_stream)
         ctx.init_hamiltonian(s.h1, s.L, s.e0)
         ctx.init_trial(s.psi_a, s.psi_b)
-        ctx.init_walkers(nw)
+        ctx.init_walkers(nw, phi)
         return ctx
+
+    def split_errors(mix, ref, n, gE):
+        """Errors of the split-precision walkers against the FP64 path (first n walkers):
+        max |dE| per energy part (Ha), max relative error of weights, overlaps and
+        walker matrices, and of the local-energy gradients, which the FP64 adjoint
+        (the one a split context runs) gives at the split-propagated walkers against
+        those at the FP64-propagated ones (max |d| / max |ref| per output)."""
+        em, _ = mix.local_energy()
+        er, _ = ref.local_energy()
+        out = {part: float(np.max(np.abs(em[:n, i] - er[:, i])))
+               for i, part in enumerate(("E1", "EJ", "EK", "E_L"))}
+        wm, wr = np.abs(mix.get_weights()[:n]), np.abs(ref.get_weights())
+        live = wr > 0
+        out["w_rel"] = float(np.max(np.abs(wm - wr)[live] / wr[live])) if live.any() else 0.0
+        om, orf = mix.get_overlaps()[:n], ref.get_overlaps()
+        out["overlap_rel"] = float(np.max(np.abs(om - orf) / np.abs(orf)))
+        pm, pr = mix.get_walkers()[:n], ref.get_walkers()
+        out["phi_rel"] = float(np.max(np.linalg.norm((pm - pr).reshape(n, -1), axis=1) /
+                                      np.linalg.norm(pr.reshape(n, -1), axis=1)))
+        probe = context("fp64", n, phi=pm)
+        gm, gr = probe.local_energy_backward(gE), ref.local_energy_backward(gE)
+        probe.close()
+        for name_, a, b in zip(("dh1", "dL", "dphi"), gm, gr):
+            out[name_ + "_rel"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        return out
 
     mix = context("split_bf16", W)
     errs = {1: None, long_steps: None}
     if long_steps > 0:
         ref = context("fp64", check_walkers)
+        rng = np.random.default_rng(5)
+        gE = rng.standard_normal(check_walkers) + 1j * rng.standard_normal(check_walkers)
         for k in range(1, long_steps + 1):
             mix.propagate(None, 1)
             ref.propagate(None, 1)
             if k in (1, long_steps):
-                em, _ = mix.local_energy()
-                er, _ = ref.local_energy()
-                errs[k] = float(np.max(np.abs(em[:check_walkers, 3] - er[:, 3])))
+                errs[k] = split_errors(mix, ref, check_walkers, gE)
         ref.close()
     e_dev = torch.empty((W, 4, 2), dtype=torch.float64, device="cuda")
     emix_dev = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -365,7 +390,13 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
            "exchange_algorithm": algo,
            "prop_digits": {"per_pass": digits, "sqrt_dt_V2_estimate": xest,
                            "passes": "first P, Taylor powers 1..n, last P"},
-           "dE_L_max_1_step": errs[1], f"dE_L_max_{long_steps}_steps": errs[long_steps],
+           "dE_L_max_1_step": errs[1] and errs[1]["E_L"],
+           f"dE_L_max_{long_steps}_steps": errs[long_steps] and errs[long_steps]["E_L"],
+           "errors": {"after_1_step": errs[1], f"after_{long_steps}_steps": errs[long_steps],
+                      "units": "E1, EJ, EK, E_L: max |d| in Ha; *_rel: max relative error "
+                               "(weights, overlaps per walker; walkers Frobenius per walker; "
+                               "gradients max |d| / max |ref|, FP64 adjoint at the "
+                               "split-propagated walkers, cotangent seeded)"},
            "dE_reference": f"FP64 path (parity-checked against the FP64 oracle at 1e-10) on the "
                            f"first {check_walkers} walkers, same Philox fields",
            "gpu_launches": mix.launch_count() - n0,
