@@ -67,7 +67,8 @@ def parse_args():
     ap.add_argument("--no-mixed", action="store_true", help="skip the split-precision legs")
     ap.add_argument("--mixed-steps", type=int, default=20)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
-    ap.add_argument("--profile-leg", choices=["mixed-c2", "mixed-c3", "batched", "adjoint"],
+    ap.add_argument("--profile-leg", choices=["mixed-c2", "mixed-c3", "batched", "adjoint",
+                                              "blocks"],
                     default=None, help="run one secondary leg alone and print its JSON (for ncu)")
     ap.add_argument("--profile-walkers", type=int, default=0,
                     help="walker count of a --profile-leg mixed leg (0: the workload's)")
@@ -240,8 +241,9 @@ def fp64_step_ms(s, W: int, rank: int, steps: int = 2) -> float:
 
 
 def block_leg(name: str, precision: str, rank: int, blocks: int = 4, block_steps: int = 25) -> dict:
-    """The paper's block cadence (25 propagation steps, then one local energy and the
-    orthogonalisation: qr_period = 25), device-event timed over `blocks` blocks after
+    """The paper's block cadence through the native block driver (afq_run_blocks): 25
+    propagation steps, then one local energy, the orthogonalisation (qr_period = 25)
+    and population control by the comb, device-event timed over `blocks` blocks after
     one warm-up block.  Context for the per-step metric, which evaluates the energy
     every step and orthogonalises every 5."""
     import torch
@@ -257,17 +259,12 @@ def block_leg(name: str, precision: str, rank: int, blocks: int = 4, block_steps
     ctx.init_trial(s.psi_a, s.psi_b)
     ctx.init_walkers(W)
     ctx.autotune()
-
-    def block():
-        ctx.propagate_dev(None, block_steps)
-        ctx.local_energy_dev(None, None)
-
-    block()
+    u = np.random.default_rng(7 + rank).random(blocks + 1)
+    ctx.run_blocks(1, block_steps, u=u[:1])
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for _ in range(blocks):
-        block()
+    ctx.run_blocks(blocks, block_steps, u=u[1:])
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / blocks
@@ -275,7 +272,45 @@ def block_leg(name: str, precision: str, rank: int, blocks: int = 4, block_steps
     return {"workload": name, "precision": precision, "W": W, "blocks": blocks,
             "ms_per_block": ms, "value": W * block_steps / (ms / 1e3),
             "unit": "walker-steps/s at the block cadence",
-            "cadence": f"{block_steps} propagation steps + 1 local energy + QR per block"}
+            "cadence": f"{block_steps} propagation steps + 1 local energy + QR + comb per block "
+                       "(afq_run_blocks)"}
+
+
+def workflow_leg(name: str, precision: str, rank: int, blocks: int = 160, discard: int = 40,
+                 block_steps: int = 25) -> dict:
+    """The paper's analysis workflow on one workload: blocks of block_steps steps with
+    one energy evaluation, the energy-shift feedback and the comb each, the first
+    `discard` blocks dropped for equilibration and the rest reblocked
+    (Flyvbjerg-Petersen, optimal level by the Lee-Needs-Drummond criterion) into an
+    energy and its error bar."""
+    import torch
+    from paper_2209_04015_b300 import AfqContext
+    from paper_2209_04015_b300.blocking import block_energies, estimate
+    from paper_2209_04015_b300.synthetic import make_config
+
+    s, c = make_config(name, seed=1 + rank)
+    W = c["W"]
+    stream = torch.cuda.current_stream()
+    ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, precision=precision,
+                     stream=stream.cuda_stream)
+    ctx.init_hamiltonian(s.h1, s.L, s.e0)
+    ctx.init_trial(s.psi_a, s.psi_b)
+    ctx.init_walkers(W)
+    e_trial = ctx.trial_energy()
+    u = np.random.default_rng(11 + rank).random(blocks)
+    t0 = time.perf_counter()
+    sums = ctx.run_blocks(blocks, block_steps, u=u, shift_feedback=True)
+    seconds = time.perf_counter() - t0
+    ctx.close()
+    est = estimate(block_energies(sums), discard=discard)
+    return {"workload": name, "precision": precision, "W": W, "blocks": blocks,
+            "discarded": discard, "steps_per_block": block_steps, "seconds": seconds,
+            "energy": est.mean, "error": est.error, "reblock_level": est.level,
+            "trial_energy": e_trial,
+            "note": "synthetic Hamiltonian and a random orthonormal (not self-consistent) "
+                    "trial, so the projected energy lies far below the trial's: the number "
+                    "shows the workflow (blocks, comb, shift feedback, reblocking), not a "
+                    "physical energy"}
 
 
 def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int = 16,
@@ -571,6 +606,9 @@ def run_leg(args) -> int:
                         long_steps=args.error_steps, walkers=args.profile_walkers)
     elif leg == "batched":
         out = batched_leg(0)
+    elif leg == "blocks":
+        out = {"fp64_c2": block_leg("c2", "fp64", 0),
+               "workflow_split_c2": workflow_leg("c2", "split_bf16", 0)}
     else:
         out = adjoint_leg(0)
     print(json.dumps({"leg": leg, **out}), flush=True)
@@ -697,7 +735,8 @@ def run_afq(args):
             line["mixed"]["same_workload"]["value"] / (value / world))
         line["batched"] = batched_leg(rank)
         line["paper_block"] = {"fp64_c2": block_leg("c2", "fp64", rank),
-                               "split_c3": block_leg("c3", "split_bf16", rank)}
+                               "split_c3": block_leg("c3", "split_bf16", rank),
+                               "workflow_split_c2": workflow_leg("c2", "split_bf16", rank)}
     if not args.no_adjoint:
         line["adjoint"] = adjoint_leg(rank)
     if world == 1 and not args.no_cpu_baseline:

@@ -49,7 +49,7 @@ typedef enum afq_precision {
   AFQ_SPLIT_BF16 = 1, /* force bias, exchange, VHS and propagator contractions as
                          split-bf16 tensor-core GEMMs (tcgen05); overlaps,
                          inverses, QR and weights stay float64                */
-  AFQ_SPLIT_TF32 = 2  /* reserved                                              */
+  AFQ_SPLIT_TF32 = 2  /* reserved: afq_create rejects it (AFQ_ERR_ARG)          */
 } afq_precision;
 
 typedef enum afq_exchange {
@@ -157,6 +157,42 @@ int afq_local_energy_dev(afq_ctx* ctx, double* e_out_dev, double* e_mix_dev);
    real and positive; Phi_s <- Q and the stored overlap is divided by
    prod_s det R_s. */
 int afq_orthogonalise(afq_ctx* ctx);
+
+/* Population control by the comb.  The paper counts population control among the
+   light parts of AFQMC (Sec. "Introduction") without fixing an algorithm; the comb
+   (systematic resampling) is the reading taken.  With the phaseless weights w_z,
+   first capped at w_cap when w_cap > 0 (0 = no cap), their running sums
+   C_z = w_0 + ... + w_z in index order and T = C_{W-1}, the teeth
+   t_k = (k + u) (T / W), k = 0..W-1, select parents: new walker k copies the walker
+   z with C_{z-1} <= t_k < C_z (its matrix and stored overlap; a tooth at or above
+   C_{W-1} goes to the last walker with positive weight) and every new walker gets
+   weight T / W.  theta, the determinants and the Coulomb vector are then rebuilt,
+   and a chain tape is discarded.
+   u: the comb's offset in [0, 1), drawn by the caller (AFQ_ERR_ARG outside).
+   parents: host array of W ints receiving the parent of each new walker, or NULL.
+   AFQ_ERR_STATE in free projection (complex weights); AFQ_ERR_NAN when T is not
+   positive and finite (the walkers are then left as they were). */
+int afq_comb(afq_ctx* ctx, double u, double w_cap, int* parents);
+
+/* The block workflow of the paper's example (Sec. "Interface with PySCF": blocks of
+   propagation steps, typically 25, each followed by one energy evaluation): for each
+   block b, steps_per_block steps with the device fields (QR at its cadence), then the
+   local energies and the block sums written to sums[4 b .. 4 b + 3] =
+   (Re, Im of sum_z w_z; Re, Im of sum_z w_z E_L,z), then, when u is not NULL, the comb
+   with offset u[b] and cap w_cap (as afq_comb).  sums: host, nblocks x 4 doubles.
+   shift_feedback != 0: after each block the energy shift E_shift of the weight factor
+   exp(-dt (e0 - 1/2 sum vbar^2 - E_shift)) becomes E_b - ln(T_b / W) / (dt
+   steps_per_block), on the device, with E_b = Re(sum w E_L / sum w) the block's
+   estimate and T_b = |sum w| its total weight (population feedback: the total weight
+   returns towards W; the shift multiplies every weight of a step by the same factor,
+   so ratio estimators do not change); the context keeps the last shift afterwards
+   (afq_get_e_shift).  0: E_shift stays as set at afq_init_trial.
+   One host synchronisation at the end; errors of any block are reported then.
+   AFQ_ERR_ARG for nblocks < 0, steps_per_block < 1 or an offset outside [0, 1). */
+int afq_run_blocks(afq_ctx* ctx, int nblocks, int steps_per_block, const double* u,
+                   double w_cap, int shift_feedback, double* sums);
+/* The energy shift the weight update uses now. */
+int afq_get_e_shift(afq_ctx* ctx, double* e_shift);
 
 /* Getters (host outputs): walkers W x M x (na+nb) complex; weights W complex
    (imaginary parts are zero in phaseless mode); stored overlaps W complex; the

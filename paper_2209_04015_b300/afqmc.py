@@ -58,6 +58,10 @@ _SIGS = {
     "afq_local_energy": (ctypes.c_int, [_P, _P, _D]),
     "afq_local_energy_dev": (ctypes.c_int, [_P, _P, _P]),
     "afq_orthogonalise": (ctypes.c_int, [_P]),
+    "afq_comb": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, _P]),
+    "afq_run_blocks": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_double,
+                                      ctypes.c_int, _P]),
+    "afq_get_e_shift": (ctypes.c_int, [_P, _P]),
     "afq_local_energy_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "afq_local_energy_backward_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "afq_chain_forward": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
@@ -250,6 +254,35 @@ class AfqContext:
 
     def orthogonalise(self) -> None:
         self._check(self.lib.afq_orthogonalise(self.h))
+
+    def comb(self, u: float, w_cap: float = 0.0) -> np.ndarray:
+        """Population control by the comb with offset u in [0, 1); returns the parent
+        index of every new walker."""
+        parents = np.empty(self.W, dtype=np.int32)
+        self._check(self.lib.afq_comb(self.h, float(u), float(w_cap), _ptr(parents)))
+        return parents
+
+    def run_blocks(self, nblocks: int, steps_per_block: int = 25,
+                   u: np.ndarray | None = None, w_cap: float = 0.0,
+                   shift_feedback: bool = False) -> np.ndarray:
+        """Blocks of steps_per_block steps, each followed by the local energy, the energy
+        shift feedback (when asked) and, when u is given (one offset per block), the
+        comb.  Returns (nblocks, 4): Re, Im of sum w and Re, Im of sum w E_L per block."""
+        sums = np.empty((nblocks, 4), dtype=np.float64)
+        uu = None if u is None else _c(u, np.float64)
+        if uu is not None and uu.size != nblocks:
+            raise ValueError("one comb offset per block")
+        self._check(self.lib.afq_run_blocks(self.h, int(nblocks), int(steps_per_block),
+                                            _ptr(uu), float(w_cap), 1 if shift_feedback else 0,
+                                            _ptr(sums)))
+        return sums
+
+    def get_e_shift(self) -> float:
+        """The energy shift of the weight update (E_HF of the trial unless set or fed
+        back by run_blocks)."""
+        out = ctypes.c_double()
+        self._check(self.lib.afq_get_e_shift(self.h, ctypes.byref(out)))
+        return out.value
 
     def local_energy_backward(self, gE: np.ndarray, want=("h1", "L", "phi")):
         """Gradients of sum_z Re(conj(gE_z) E_L,z) at the current walkers: (dh1 (M, M),

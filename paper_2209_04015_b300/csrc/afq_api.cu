@@ -78,7 +78,7 @@ int sync(afq_ctx* ctx) {
 
 // Reads and clears the device flags; maps them to a status.
 int check_flags(afq_ctx* ctx) {
-  int h[3] = {0, 0, 0};
+  int h[4] = {0, 0, 0, 0};
   AFQ_CUDA(ctx, cudaMemcpyAsync(h, ctx->flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   AFQ_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(h), ctx->stream));
   AFQ_TRY(sync(ctx));
@@ -87,6 +87,9 @@ int check_flags(afq_ctx* ctx) {
   if (h[2]) return afq_fail(ctx, AFQ_ERR_CUDA, "tensor-core pipeline wait timed out" + all);
   if (h[0]) return afq_fail(ctx, AFQ_ERR_SINGULAR, "singular pivot(s)" + all);
   if (h[1]) return afq_fail(ctx, AFQ_ERR_NAN, "non-finite weight(s)" + all);
+  if (h[3])
+    return afq_fail(ctx, AFQ_ERR_NAN,
+                    "population control: total weight not positive and finite (walkers kept)");
   return AFQ_OK;
 }
 
@@ -159,6 +162,7 @@ int energy_kernels(afq_ctx* ctx, WalkerSet& s) {
 
 int free_walkers(afq_ctx* ctx) {
   chain_free(ctx);
+  comb_free(ctx);
   free_walker_set(ctx->ws);
   dfree(&ctx->xi);
   dfree(&ctx->xbar);
@@ -200,7 +204,7 @@ bool symmetric(const double* a, int M, double* dev_out) {
 }
 
 // One hybrid-propagation step (Sec. "Review of AFQMC") on the context's stream.
-int one_step(afq_ctx* ctx, const double* xi_dev) {
+int one_step(afq_ctx* ctx, const double* xi_dev, const double* e_shift_dev = nullptr) {
   const double log_const = -ctx->p.dt * (ctx->e0 - 0.5 * ctx->sum_vbar2 - ctx->e_shift);
   AFQ_TRY(timed(ctx, AFQ_K_FIELDS, [&] { return launch_fields(ctx, xi_dev); }));
   if (ctx->mixed) {
@@ -211,7 +215,7 @@ int one_step(afq_ctx* ctx, const double* xi_dev) {
     AFQ_TRY(timed(ctx, AFQ_K_PROPAGATE, [&] { return launch_propagate_fp64(ctx); }));
   }
   AFQ_TRY(green_and_bias(ctx, ctx->ws));
-  AFQ_TRY(timed(ctx, AFQ_K_WEIGHTS, [&] { return launch_weights(ctx, log_const); }));
+  AFQ_TRY(timed(ctx, AFQ_K_WEIGHTS, [&] { return launch_weights(ctx, log_const, e_shift_dev); }));
   ctx->step++;
   if (ctx->p.qr_period > 0 && ctx->step % (uint64_t)ctx->p.qr_period == 0)
     AFQ_TRY(timed(ctx, AFQ_K_QR, [&] { return launch_qr(ctx, ctx->ws, ctx->A); }));
@@ -268,8 +272,8 @@ int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
     delete ctx;
     return AFQ_ERR_CUDA;
   }
-  if (cudaMalloc((void**)&ctx->flags, 3 * sizeof(int)) != cudaSuccess ||
-      cudaMemset(ctx->flags, 0, 3 * sizeof(int)) != cudaSuccess ||
+  if (cudaMalloc((void**)&ctx->flags, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->flags, 0, 4 * sizeof(int)) != cudaSuccess ||
       cudaMalloc((void**)&ctx->d_step, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(ctx->d_step, 0, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc((void**)&ctx->emix, sizeof(double)) != cudaSuccess) {
@@ -620,6 +624,80 @@ int afq_orthogonalise(afq_ctx* ctx) {
   AFQ_TRY(timed(ctx, AFQ_K_QR, [&] { return launch_qr(ctx, ctx->ws, ctx->A); }));
   AFQ_TRY(sync(ctx));
   return check_flags(ctx);
+}
+
+static int comb_checks(afq_ctx* ctx, double w_cap) {
+  if (ctx->p.free_projection)
+    return afq_fail(ctx, AFQ_ERR_STATE, "the comb needs the phaseless (real) weights");
+  if (!(w_cap >= 0.0) || !std::isfinite(w_cap))
+    return afq_fail(ctx, AFQ_ERR_ARG, "w_cap must be finite and >= 0");
+  return AFQ_OK;
+}
+
+int afq_comb(afq_ctx* ctx, double u, double w_cap, int* parents) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  AFQ_TRY(comb_checks(ctx, w_cap));
+  if (!(u >= 0.0 && u < 1.0)) return afq_fail(ctx, AFQ_ERR_ARG, "comb offset u outside [0, 1)");
+  chain_free(ctx);  // a chain tape refers to the walkers before the comb
+  AFQ_TRY(comb_walkers(ctx, u, w_cap));
+  AFQ_TRY(green_and_bias(ctx, ctx->ws));
+  if (parents)
+    AFQ_CUDA(ctx, cudaMemcpyAsync(parents, ctx->comb_parents, (size_t)ctx->ws.W * sizeof(int),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  AFQ_TRY(sync(ctx));
+  return check_flags(ctx);
+}
+
+int afq_run_blocks(afq_ctx* ctx, int nblocks, int steps_per_block, const double* u,
+                   double w_cap, int shift_feedback, double* sums) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  if (nblocks < 0 || steps_per_block < 1)
+    return afq_fail(ctx, AFQ_ERR_ARG, "nblocks < 0 or steps_per_block < 1");
+  if (nblocks > 0 && !sums) return afq_fail(ctx, AFQ_ERR_ARG, "sums is NULL");
+  if (u) {
+    AFQ_TRY(comb_checks(ctx, w_cap));
+    for (int b = 0; b < nblocks; ++b)
+      if (!(u[b] >= 0.0 && u[b] < 1.0))
+        return afq_fail(ctx, AFQ_ERR_ARG, "comb offset u outside [0, 1)");
+  }
+  if (nblocks == 0) return AFQ_OK;
+  chain_free(ctx);
+  double* d = nullptr;  // nblocks x 4 block sums, then the device energy shift
+  AFQ_TRY(dalloc(ctx, &d, (size_t)nblocks * 4 + 1));
+  double* es = shift_feedback ? d + (size_t)nblocks * 4 : nullptr;
+  int rc = es ? launch_set_scalar(ctx, es, ctx->e_shift) : AFQ_OK;
+  for (int b = 0; b < nblocks && rc == AFQ_OK; ++b) {
+    for (int k = 0; k < steps_per_block && rc == AFQ_OK; ++k) rc = one_step(ctx, nullptr, es);
+    if (rc == AFQ_OK) rc = energy_kernels(ctx, ctx->ws);
+    if (rc == AFQ_OK) rc = launch_block_sums(ctx, d + 4 * (size_t)b);
+    if (rc == AFQ_OK && es)
+      rc = launch_shift_from_block(ctx, d + 4 * (size_t)b, steps_per_block, es);
+    if (rc == AFQ_OK && u) {
+      rc = comb_walkers(ctx, u[b], w_cap);
+      if (rc == AFQ_OK) rc = green_and_bias(ctx, ctx->ws);
+    }
+  }
+  if (rc == AFQ_OK &&
+      cudaMemcpyAsync(sums, d, (size_t)nblocks * 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                      ctx->stream) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "copy block sums");
+  double shift = ctx->e_shift;
+  if (rc == AFQ_OK && es &&
+      cudaMemcpyAsync(&shift, es, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) !=
+          cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "copy energy shift");
+  if (rc == AFQ_OK) rc = sync(ctx);
+  if (rc == AFQ_OK) ctx->e_shift = shift;  // later steps continue with the fed-back shift
+  dfree(&d);
+  return rc == AFQ_OK ? check_flags(ctx) : rc;
+}
+
+int afq_get_e_shift(afq_ctx* ctx, double* e_shift) {
+  if (!ctx || !e_shift) return AFQ_ERR_ARG;
+  *e_shift = ctx->e_shift;
+  return AFQ_OK;
 }
 
 static int get_impl(afq_ctx* ctx, void* dst, const void* src, size_t bytes) {

@@ -135,7 +135,13 @@ struct afq_ctx {
   long fb64_part_wx = 0;         // W X the buffer was sized for
   double* emix = nullptr;    // 1
   int* flags = nullptr;      // [0] singular pivots, [1] non-finite values,
-                             // [2] tensor-core pipeline time-outs
+                             // [2] tensor-core pipeline time-outs,
+                             // [3] population control without positive total weight
+  // population control (comb) workspace, allocated on first use
+  double2* comb_phi = nullptr;   // W x M x N gathered walkers
+  double2* comb_ovlp = nullptr;  // W gathered stored overlaps
+  double* comb_cum = nullptr;    // W running weight sums, then T / W
+  int* comb_parents = nullptr;   // W parent index of each new walker
   double* scratch = nullptr; // set-up workspace
   size_t scratch_bytes = 0;
 
@@ -257,8 +263,13 @@ int launch_fields(afq_ctx* ctx, const double* xi_dev);
 int launch_philox_fields(afq_ctx* ctx, uint64_t step, double* out, uint32_t* words);
 int launch_vhs_fp64(afq_ctx* ctx);
 int launch_propagate_fp64(afq_ctx* ctx);
-int launch_weights(afq_ctx* ctx, double log_const);
+int launch_weights(afq_ctx* ctx, double log_const, const double* e_shift_dev = nullptr);
 int launch_emix(afq_ctx* ctx, WalkerSet& s, double* out);
+int comb_walkers(afq_ctx* ctx, double u, double w_cap);  // k_population.cu
+void comb_free(afq_ctx* ctx);
+int launch_block_sums(afq_ctx* ctx, double* out_dev);
+int launch_shift_from_block(afq_ctx* ctx, const double* sums_dev, int steps, double* e_shift_dev);
+int launch_set_scalar(afq_ctx* ctx, double* dst_dev, double value);
 
 // adjoint of the local energy (k_adjoint.cu)
 int adjoint_local_energy(afq_ctx* ctx, const double2* gE, double* dh1, double* dL, double2* dphi);

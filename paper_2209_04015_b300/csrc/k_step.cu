@@ -399,13 +399,18 @@ __global__ void k_propagate_fp64(int M, int N, int order, const double* __restri
 // K8: overlap ratio R = (O'/O) e^{cmf}, importance I = R e^{cfb} e^{log_const},
 // phaseless weight w <- w |I| max(0, cos arg R) (or w <- w I in free projection).
 // ---------------------------------------------------------------------------
-__global__ void k_weights(int W, double log_const, int free_proj, const double2* __restrict__ det,
+// With e_shift_dev set, log_const = -dt (base - E_shift) takes E_shift from the device
+// (the block driver's energy-shift feedback); base = e0 - 1/2 sum vbar^2, the same
+// operations in the same order as the host's value.
+__global__ void k_weights(int W, double log_const, const double* __restrict__ e_shift_dev,
+                          double dt, double base, int free_proj, const double2* __restrict__ det,
                           const double2* __restrict__ cfb, const double2* __restrict__ cmf,
                           double2* __restrict__ ovlp, double2* __restrict__ w, int* flags,
                           unsigned long long* __restrict__ step_dev) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   if (z == 0) *step_dev += 1;  // the step's fields were drawn by k_fields earlier in order
   if (z >= W) return;
+  if (e_shift_dev) log_const = -dt * (base - *e_shift_dev);
   const double2 onew = cmul(det[2 * z], det[2 * z + 1]);
   const double2 ratio = cmul(cdiv(onew, ovlp[z]), cexp(cmf[z]));
   const double2 imp = cmul(cmul(ratio, cexp(cfb[z])), cmk(exp(log_const), 0.0));
@@ -525,10 +530,11 @@ int launch_propagate_fp64(afq_ctx* ctx) {
   }
 }
 
-int launch_weights(afq_ctx* ctx, double log_const) {
+int launch_weights(afq_ctx* ctx, double log_const, const double* e_shift_dev) {
   k_weights<<<(ctx->ws.W + 127) / 128, 128, 0, ctx->stream>>>(
-      ctx->ws.W, log_const, ctx->p.free_projection, ctx->ws.det, ctx->cfb, ctx->cmf,
-      ctx->ws.ovlp, ctx->ws.w, ctx->flags, ctx->d_step);
+      ctx->ws.W, log_const, e_shift_dev, ctx->p.dt, ctx->e0 - 0.5 * ctx->sum_vbar2,
+      ctx->p.free_projection, ctx->ws.det, ctx->cfb, ctx->cmf, ctx->ws.ovlp, ctx->ws.w,
+      ctx->flags, ctx->d_step);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }
