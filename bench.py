@@ -301,12 +301,18 @@ def workflow_leg(name: str, precision: str, rank: int, blocks: int = 160, discar
     t0 = time.perf_counter()
     sums = ctx.run_blocks(blocks, block_steps, u=u, shift_feedback=True)
     seconds = time.perf_counter() - t0
+    _, s2_mix = ctx.spin_squared()  # the <S^2> mixed estimator on the final walkers
+    t1 = time.perf_counter()
+    for _ in range(5):
+        ctx.spin_squared()
+    s2_ms = (time.perf_counter() - t1) / 5 * 1e3
     ctx.close()
     est = estimate(block_energies(sums), discard=discard)
     return {"workload": name, "precision": precision, "W": W, "blocks": blocks,
             "discarded": discard, "steps_per_block": block_steps, "seconds": seconds,
             "energy": est.mean, "error": est.error, "reblock_level": est.level,
-            "trial_energy": e_trial,
+            "trial_energy": e_trial, "s2_mixed_final": s2_mix,
+            "s2_call_ms": s2_ms,
             "note": "synthetic Hamiltonian and a random orthonormal (not self-consistent) "
                     "trial, so the projected energy lies far below the trial's: the number "
                     "shows the workflow (blocks, comb, shift feedback, reblocking), not a "

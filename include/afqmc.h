@@ -194,6 +194,15 @@ int afq_run_blocks(afq_ctx* ctx, int nblocks, int steps_per_block, const double*
 /* The energy shift the weight update uses now. */
 int afq_get_e_shift(afq_ctx* ctx, double* e_shift);
 
+/* Mixed estimator of S^2 (Sec. "Customized mixed estimators"; S^2 commutes with H,
+   so the mixed estimate is unbiased): per walker
+     <Psi_T|S^2|Phi_z> / <Psi_T|Phi_z> = N_beta + M_S (M_S + 1) - tr(G_alpha G_beta),
+   M_S = (na - nb) / 2, G_s the walker's Green's function of spin s (the trace of
+   the product, from Wick's theorem; the paper's printed sum drops the transpose,
+   which only agrees for symmetric G).  FP64 from the walkers' current theta.
+   s2_out: W complex (host) or NULL; s2_mix: Re(sum w S2 / sum w) (host) or NULL. */
+int afq_spin_squared(afq_ctx* ctx, double* s2_out, double* s2_mix);
+
 /* Getters (host outputs): walkers W x M x (na+nb) complex; weights W complex
    (imaginary parts are zero in phaseless mode); stored overlaps W complex; the
    force bias xbar of the last step, W x X complex. */

@@ -62,6 +62,7 @@ _SIGS = {
     "afq_run_blocks": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_double,
                                       ctypes.c_int, _P]),
     "afq_get_e_shift": (ctypes.c_int, [_P, _P]),
+    "afq_spin_squared": (ctypes.c_int, [_P, _P, _P]),
     "afq_local_energy_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "afq_local_energy_backward_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "afq_chain_forward": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
@@ -276,6 +277,13 @@ class AfqContext:
                                             _ptr(uu), float(w_cap), 1 if shift_feedback else 0,
                                             _ptr(sums)))
         return sums
+
+    def spin_squared(self) -> tuple[np.ndarray, float]:
+        """Mixed <S^2> per walker (complex) and the weighted estimate."""
+        out = np.empty(self.W, dtype=np.complex128)
+        mix = ctypes.c_double()
+        self._check(self.lib.afq_spin_squared(self.h, _ptr(out), ctypes.byref(mix)))
+        return out, mix.value
 
     def get_e_shift(self) -> float:
         """The energy shift of the weight update (E_HF of the trial unless set or fed

@@ -700,6 +700,26 @@ int afq_get_e_shift(afq_ctx* ctx, double* e_shift) {
   return AFQ_OK;
 }
 
+int afq_spin_squared(afq_ctx* ctx, double* s2_out, double* s2_mix) {
+  if (!ctx) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  const size_t W = ctx->ws.W;
+  double* d = nullptr;  // W complex values, then the weighted estimate
+  AFQ_TRY(dalloc(ctx, &d, 2 * W + 1));
+  int rc = launch_spin_squared(ctx, ctx->ws, reinterpret_cast<double2*>(d), d + 2 * W);
+  if (rc == AFQ_OK && s2_out &&
+      cudaMemcpyAsync(s2_out, d, 2 * W * sizeof(double), cudaMemcpyDeviceToHost,
+                      ctx->stream) != cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "copy S^2");
+  if (rc == AFQ_OK && s2_mix &&
+      cudaMemcpyAsync(s2_mix, d + 2 * W, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) !=
+          cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "copy weighted S^2");
+  if (rc == AFQ_OK) rc = sync(ctx);
+  dfree(&d);
+  return rc == AFQ_OK ? check_flags(ctx) : rc;
+}
+
 static int get_impl(afq_ctx* ctx, void* dst, const void* src, size_t bytes) {
   if (!ctx || !dst) return AFQ_ERR_ARG;
   if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
