@@ -476,10 +476,16 @@ int launch_vhs_fp64(afq_ctx* ctx) {
   return AFQ_OK;
 }
 
+// Shared memory of one CTA of the FP64 propagator: three complex planes (the walker
+// columns, the current and the next Taylor term) and two real ones of M x NC.
+size_t propagate_fp64_smem(int M, int NC) {
+  return (size_t)3 * M * NC * sizeof(double2) + (size_t)2 * M * NC * 8;
+}
+
 template <int NC, int G>
 int launch_propagate_g(afq_ctx* ctx) {
   const int threads = 32 * ((G * ctx->M + 31) / 32);
-  const size_t smem = (size_t)3 * ctx->M * NC * sizeof(double2) + (size_t)2 * ctx->M * NC * 8;
+  const size_t smem = propagate_fp64_smem(ctx->M, NC);
   static size_t configured = 0;
   if (smem > configured) {
     AFQ_CUDA(ctx, cudaFuncSetAttribute(k_propagate_fp64<NC, G>,
@@ -521,9 +527,13 @@ int launch_propagate_nc(afq_ctx* ctx) {
   return launch_propagate_g<NC, 1>(ctx);
 }
 
-// Column chunk NC (2, 4 or 8 walker columns per CTA) as chosen by the autotuner.
+// Column chunk NC (2, 4 or 8 walker columns per CTA) as chosen by the autotuner,
+// narrowed while its planes do not fit one CTA's shared memory (227 KB: NC = 4
+// up to M = 908, NC = 2 up to M = 1816).
 int launch_propagate_fp64(afq_ctx* ctx) {
-  switch (ctx->prop_nc) {
+  int nc = ctx->prop_nc == 2 || ctx->prop_nc == 8 ? ctx->prop_nc : 4;
+  while (nc > 2 && propagate_fp64_smem(ctx->M, nc) > 227 * 1024) nc /= 2;
+  switch (nc) {
     case 2: return launch_propagate_nc<2>(ctx);
     case 8: return launch_propagate_nc<8>(ctx);
     default: return launch_propagate_nc<4>(ctx);

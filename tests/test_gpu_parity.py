@@ -127,6 +127,26 @@ def test_edge_shapes(M, na, nb, X, W, exchange):
     assert_energy_parity(ctx, orc, TOL)
 
 
+@pytest.mark.parametrize("exchange", ["direct", "stored"])
+def test_maximum_sizes(exchange):
+    """The ABI's limits: 64 electrons per spin, and 1024 orbitals with the direct
+    exchange (the FP64 propagator narrows its column chunk to fit shared memory; the
+    split path's long rows take the two-pass slicing); the stored exchange at 64 + 64
+    electrons on 200 orbitals (its tensor at 1024 orbitals would be (64 x 1024)^2
+    doubles per spin)."""
+    M = 1024 if exchange == "direct" else 200
+    s = make_system(M, 64, 64, 5, seed=9, decay="half")
+    W = 2
+    phi = perturbed_walkers(s, W, eps=0.2, seed=5)
+    ctx, orc = make_pair(s, W, phi=phi, qr_period=2, exchange=exchange)
+    assert ctx.exchange_algorithm() == exchange
+    fields = np.stack([gaussian_fields(W, s.X, seed=600 + k) for k in range(2)])
+    ctx.propagate(fields, 2)
+    orc.propagate(list(fields))
+    assert_state_parity(ctx, orc, TOL)
+    assert_energy_parity(ctx, orc, TOL)
+
+
 def test_orthogonalise_entry_point():
     s = ragged_system(seed=2)
     W = 5
