@@ -47,8 +47,9 @@ typedef enum afq_status {
 typedef enum afq_precision {
   AFQ_FP64 = 0,       /* every contraction in float64                         */
   AFQ_SPLIT_BF16 = 1, /* force bias, exchange, VHS and propagator contractions as
-                         split-bf16 tensor-core GEMMs (tcgen05); overlaps,
-                         inverses, QR and weights stay float64                */
+                         bf16 tensor-core GEMMs (tcgen05) on exact 8-bit integer
+                         digits of their operands; theta by double-float
+                         arithmetic; overlaps, inverses, QR and weights float64 */
   AFQ_SPLIT_TF32 = 2  /* reserved: afq_create rejects it (AFQ_ERR_ARG)          */
 } afq_precision;
 
@@ -65,9 +66,10 @@ typedef enum afq_exchange {
                               E_K = -1/2 sum_s theta_s^T V_s theta_s, about (n M)^2
                               multiply-adds per walker and spin (V is symmetric:
                               only its upper blocks are read).  AFQ_SPLIT_BF16
-                              contexts also keep split_slices bf16 planes of V in
-                              the padded layout (2 S (n Mpad)^2 bytes per spin) and
-                              run V theta as one tensor-core GEMM per spin         */
+                              contexts also keep split_slices exact-digit planes of
+                              V in the padded layout, blocks above the diagonal
+                              doubled (2 S (n Mpad)^2 bytes per spin), and run
+                              V theta for both spins as one tensor-core GEMM      */
 } afq_exchange;
 
 typedef struct afq_params {
@@ -81,9 +83,12 @@ typedef struct afq_params {
   double e_shift;      /* energy shift in exp(-dt (H - E_shift))                 */
   double fb_cap;       /* |xbar_g| cap; 0 = off                                  */
   int free_projection; /* 1: complex weights w <- w I (no phaseless cut)         */
-  int split_slices;    /* AFQ_SPLIT_BF16: bf16 slices per FP64 operand of the force
-                          bias and exchange, 1..4 (slice products s + t <= slices - 1
-                          are kept, FP32 accumulation); 0 = 3                    */
+  int split_slices;    /* AFQ_SPLIT_BF16: digits S per FP64 operand of the force bias
+                          and the exchange, 1..4; 0 = 3.  Force bias and stored
+                          exchange: exact 8-bit digits, the products of digit
+                          orders s + t <= S - 1 each in its own exact TMEM
+                          accumulator; direct exchange: bf16 float slices with
+                          FP32 accumulation                                      */
   int prop_slices;     /* AFQ_SPLIT_BF16: exact 8-bit digits per FP64 operand of the
                           VHS and propagator GEMMs, 1..4 (per-row power-of-two scale,
                           one exact TMEM accumulator per digit order); 0 = 4     */
