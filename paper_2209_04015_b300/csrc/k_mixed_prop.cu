@@ -120,6 +120,8 @@ constexpr int kPropEpi = 8;
 
 struct PropArgs {
   int M, N, W, mode, brows, BN, nkb, stages, npt, njt, ntiles;
+  int nbuf;               // TMEM accumulator sets (2 when 2 S BN <= 512: the epilogue of
+                          // one tile overlaps the MMAs of the next)
   uint32_t tx_bytes, tmem_cols;
   const int* ea;          // row exponents of A: P - I per p, or V_z per (z, p)
   const int* eb;          // row exponents of T^T per (z, j)
@@ -143,8 +145,8 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   __shared__ __align__(8) uint64_t full[kMaxStages];
   __shared__ __align__(8) uint64_t empty[kMaxStages];
-  __shared__ __align__(8) uint64_t tfull;
-  __shared__ __align__(8) uint64_t tempty;
+  __shared__ __align__(8) uint64_t tfull[2];
+  __shared__ __align__(8) uint64_t tempty[2];
   __shared__ __align__(8) uint64_t fin;
   __shared__ uint32_t tmem_base;
   __shared__ int skip;
@@ -162,8 +164,10 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&empty[i], 1);
     }
-    tc::mbar_init(&tfull, 1);
-    tc::mbar_init(&tempty, kPropEpi);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&tfull[b], 1);
+      tc::mbar_init(&tempty[b], kPropEpi);
+    }
     tc::mbar_init(&fin, 1);
     tc::fence_mbar_init();
     tc::prefetch_tmap(&tmA);
@@ -219,12 +223,15 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
       const uint32_t id_half = tc::idesc_bf16(128, brows), id_half_neg = tc::idesc_bf16(128, brows, true);
       int it = 0, lt = 0;
       bool ok = true;
+      const int nbuf = a.nbuf;
       for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++lt) {
-        if (lt >= 1 && !tc::mbar_wait(&tempty, (lt - 1) & 1, err)) {
+        const int buf = lt % nbuf, use = lt / nbuf;  // use-th fill of accumulator set buf
+        if (use >= 1 && !tc::mbar_wait(&tempty[buf], (use - 1) & 1, err)) {
           atomicExch(err, 1);
           break;
         }
         tc::fence_after_sync();
+        const uint32_t acc = tmem + (uint32_t)(buf * S * BN);
         for (int kb = 0; kb < a.nkb; ++kb, ++it) {
           const int st = it % nst;
           if (!tc::mbar_wait(&full[st], (it / nst) & 1, err)) {
@@ -235,16 +242,16 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
           const uint32_t sb = sa + S * kUA * kASlot;
-          issue_diagonals<S>(tmem, (uint32_t)BN, sa, sb, bslot, 0, 0, id_full, kb == 0);
+          issue_diagonals<S>(acc, (uint32_t)BN, sa, sb, bslot, 0, 0, id_full, kb == 0);
           if (!REAL) {
-            issue_diagonals<S>(tmem, (uint32_t)BN, sa, sb + (uint32_t)brows * 64u, bslot, 1, 0,
+            issue_diagonals<S>(acc, (uint32_t)BN, sa, sb + (uint32_t)brows * 64u, bslot, 1, 0,
                                id_half_neg, false);
-            issue_diagonals<S>(tmem + (uint32_t)brows, (uint32_t)BN, sa, sb, bslot, 1, 0, id_half,
+            issue_diagonals<S>(acc + (uint32_t)brows, (uint32_t)BN, sa, sb, bslot, 1, 0, id_half,
                                false);
           }
           tc::mma_commit(&empty[st]);
         }
-        if (ok) tc::mma_commit(&tfull);
+        if (ok) tc::mma_commit(&tfull[buf]);
       }
       tc::mma_commit(&fin);
     }
@@ -253,8 +260,9 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
     const int M = a.M, N = a.N;
     int lt = 0;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++lt) {
+      const int buf = lt % a.nbuf;
       if (q == 0 && lane == 0) {
-        ep_ok = tc::mbar_wait(&tfull, lt & 1, err) ? 1 : 0;
+        ep_ok = tc::mbar_wait(&tfull[buf], (lt / a.nbuf) & 1, err) ? 1 : 0;
         if (!ep_ok) atomicExch(err, 1);
       }
       prop_epi_sync();
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
       const int p = p0 + 32 * lq + lane;
       const bool valid = p < M;
       const int ep = valid ? (REAL ? a.ea[p] : a.ea[(long)z * M + p]) : 0;
-      const uint32_t trow = tmem + ((uint32_t)(32 * lq) << 16);
+      const uint32_t trow = tmem + (uint32_t)(buf * S * BN) + ((uint32_t)(32 * lq) << 16);
       for (int c0 = 16 * part; c0 < brows; c0 += 32) {
         // real parts of 16 columns first (digits -> FP64), then their imaginary partners
         float f[S][16];
@@ -308,7 +316,7 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
         }
       }
       tc::fence_before_sync();
-      if (lane == 0) tc::mbar_arrive(&tempty);
+      if (lane == 0) tc::mbar_arrive(&tempty[buf]);
     }
   }
   __syncthreads();
@@ -856,7 +864,8 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   a.ntiles = a.W * a.njt * a.npt;
   const int kUA = REAL ? 1 : 2;
   a.tx_bytes = (uint32_t)S * (kUA * kBK * 128 * 2 + 2 * kBK * a.brows * 2);
-  a.tmem_cols = tmem_cols_for(S * a.BN);
+  a.nbuf = 2 * S * a.BN <= 512 ? 2 : 1;
+  a.tmem_cols = tmem_cols_for(a.nbuf * S * a.BN);
   a.ea = ea;
   a.eb = ctx->e_t[b];
   a.accT = ctx->accT;
