@@ -175,6 +175,8 @@ struct afq_ctx {
   int *e_lt = nullptr, *e_pm = nullptr, *e_y = nullptr, *e_a = nullptr;  // row exponents
   int* e_t[2] = {nullptr, nullptr};
   CUtensorMap tm_vhs_a, tm_vhs_b, tm_pm, tm_az, tm_t[2];
+  CUtensorMap tm_t_real[2];  // the same operands in prop_rows_real-row boxes (P passes)
+  int prop_rows_real = 0;    // walker columns per tile of the real P passes
   // theta's integer digit planes (S x 2W x N x Mpad, one exponent per (z, re/im)):
   // the B operand of the force bias and of the stored exchange.  Stored exchange
   // (k_exchange_tcv.cu): S integer-digit planes of V' per spin (n Mpad)^2 with row

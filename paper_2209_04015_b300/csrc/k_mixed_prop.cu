@@ -781,10 +781,17 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
     const uint32_t baz[4] = {kBK, 128, 1, 1};
     const uint64_t dt[4] = {(uint64_t)Mp, (uint64_t)N, (uint64_t)(2 * W), (uint64_t)S};
     const uint32_t bt[4] = {kBK, brows, 1, 1};
+    // the real P passes read A = P - I from L2 (one matrix for all walkers), so they
+    // take half-width column tiles whose accumulators fit twice in TMEM (the epilogue
+    // of one tile overlaps the MMAs of the next)
+    ctx->prop_rows_real = ctx->prop_rows > 32 ? 32 : ctx->prop_rows;
+    const uint32_t btr[4] = {kBK, (uint32_t)ctx->prop_rows_real, 1, 1};
     ok = ok && make_tmap(&ctx->tm_pm, ctx->Pm_sl, 3, dp, bp) &&
          make_tmap(&ctx->tm_az, ctx->A_sl, 4, daz, baz) &&
          make_tmap(&ctx->tm_t[0], ctx->T_sl[0], 4, dt, bt) &&
-         make_tmap(&ctx->tm_t[1], ctx->T_sl[1], 4, dt, bt);
+         make_tmap(&ctx->tm_t[1], ctx->T_sl[1], 4, dt, bt) &&
+         make_tmap(&ctx->tm_t_real[0], ctx->T_sl[0], 4, dt, btr) &&
+         make_tmap(&ctx->tm_t_real[1], ctx->T_sl[1], 4, dt, btr);
   }
   if (!ok) return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (propagation) failed");
   return AFQ_OK;
@@ -856,7 +863,7 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   a.N = N;
   a.W = ctx->ws.W;
   a.mode = mode;
-  a.brows = ctx->prop_rows;
+  a.brows = REAL ? ctx->prop_rows_real : ctx->prop_rows;
   a.BN = 2 * a.brows;
   a.nkb = ctx->Mpad / kBK;
   a.npt = (ctx->M + 127) / 128;
@@ -879,12 +886,13 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   a.stages = nst;
   const size_t smem = stage * nst + 1024;
   const int grid = a.ntiles < sm_count_prop() ? a.ntiles : sm_count_prop();
+  const CUtensorMap& tb = REAL ? ctx->tm_t_real[b] : ctx->tm_t[b];
   cudaError_t e = cudaErrorInvalidValue;
   switch (S) {
-    case 1: e = launch_prop_s<1, REAL>(grid, smem, ctx->stream, ta, ctx->tm_t[b], a); break;
-    case 2: e = launch_prop_s<2, REAL>(grid, smem, ctx->stream, ta, ctx->tm_t[b], a); break;
-    case 3: e = launch_prop_s<3, REAL>(grid, smem, ctx->stream, ta, ctx->tm_t[b], a); break;
-    case 4: e = launch_prop_s<4, REAL>(grid, smem, ctx->stream, ta, ctx->tm_t[b], a); break;
+    case 1: e = launch_prop_s<1, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
+    case 2: e = launch_prop_s<2, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
+    case 3: e = launch_prop_s<3, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
+    case 4: e = launch_prop_s<4, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
   }
   ctx->launches++;
   if (e != cudaSuccess)
