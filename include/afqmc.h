@@ -208,6 +208,14 @@ int afq_get_e_shift(afq_ctx* ctx, double* e_shift);
    s2_out: W complex (host) or NULL; s2_mix: Re(sum w S2 / sum w) (host) or NULL. */
 int afq_spin_squared(afq_ctx* ctx, double* s2_out, double* s2_mix);
 
+/* Weighted mixed one-body density matrix of each spin (a Green's-function mixed
+   estimator, Sec. "Customized mixed estimators"):
+     <G^s>_pq = sum_z w_z G^s_z,pq / sum_z w_z,   G_pq = <a+_p a_q> = sum_j Psi_pj theta_qj,
+   formed as Psi_s (sum_z w_z theta_z,s)^T / sum_z w_z from the walkers' current theta
+   (FP64; complex weights in free projection).  g_out: host, 2 x M x M complex, the
+   alpha matrix first. */
+int afq_one_rdm(afq_ctx* ctx, double* g_out);
+
 /* Getters (host outputs): walkers W x M x (na+nb) complex; weights W complex
    (imaginary parts are zero in phaseless mode); stored overlaps W complex; the
    force bias xbar of the last step, W x X complex. */

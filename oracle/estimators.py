@@ -38,3 +38,14 @@ def spin_squared(orc) -> tuple[np.ndarray, float]:
     s2 = spin_squared_of(orc, orc.phi)
     w = np.asarray(orc.w, dtype=np.complex128)
     return s2, float((np.sum(w * s2) / np.sum(w)).real)
+
+
+def one_rdm(orc) -> np.ndarray:
+    """Weighted mixed one-body density matrix per spin, (2, M, M) complex:
+    sum_z w_z G^s_z / sum_z w_z with G_pq = <a+_p a_q> of each walker (reading of
+    Eq. halfgf, as for the energy)."""
+    ta, tb = orc.thetas(orc.phi)
+    w = np.asarray(orc.w, dtype=np.complex128)
+    ga = greens_function(orc.psi_a, ta)
+    gb = greens_function(orc.psi_b, tb)
+    return np.stack([np.einsum("z,zpq->pq", w, ga), np.einsum("z,zpq->pq", w, gb)]) / np.sum(w)

@@ -63,6 +63,7 @@ _SIGS = {
                                       ctypes.c_int, _P]),
     "afq_get_e_shift": (ctypes.c_int, [_P, _P]),
     "afq_spin_squared": (ctypes.c_int, [_P, _P, _P]),
+    "afq_one_rdm": (ctypes.c_int, [_P, _P]),
     "afq_local_energy_backward": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "afq_local_energy_backward_dev": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "afq_chain_forward": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
@@ -284,6 +285,12 @@ class AfqContext:
         mix = ctypes.c_double()
         self._check(self.lib.afq_spin_squared(self.h, _ptr(out), ctypes.byref(mix)))
         return out, mix.value
+
+    def one_rdm(self) -> np.ndarray:
+        """Weighted mixed one-body density matrix, (2, M, M) complex (alpha, beta)."""
+        out = np.empty((2, self.M, self.M), dtype=np.complex128)
+        self._check(self.lib.afq_one_rdm(self.h, _ptr(out)))
+        return out
 
     def get_e_shift(self) -> float:
         """The energy shift of the weight update (E_HF of the trial unless set or fed

@@ -720,6 +720,24 @@ int afq_spin_squared(afq_ctx* ctx, double* s2_out, double* s2_mix) {
   return rc == AFQ_OK ? check_flags(ctx) : rc;
 }
 
+int afq_one_rdm(afq_ctx* ctx, double* g_out) {
+  if (!ctx || !g_out) return AFQ_ERR_ARG;
+  if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
+  const size_t NM = (size_t)ctx->N * ctx->M, MM2 = 2 * (size_t)ctx->M * ctx->M;
+  double* d = nullptr;  // Thetabar (N x M complex), sum w, then the two matrices
+  AFQ_TRY(dalloc(ctx, &d, 2 * (NM + 1 + MM2)));
+  double2* work = reinterpret_cast<double2*>(d);
+  double2* out = work + NM + 1;
+  int rc = launch_one_rdm(ctx, ctx->ws, work, out);
+  if (rc == AFQ_OK &&
+      cudaMemcpyAsync(g_out, out, MM2 * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream) !=
+          cudaSuccess)
+    rc = afq_fail(ctx, AFQ_ERR_CUDA, "copy one-body density matrix");
+  if (rc == AFQ_OK) rc = sync(ctx);
+  dfree(&d);
+  return rc == AFQ_OK ? check_flags(ctx) : rc;
+}
+
 static int get_impl(afq_ctx* ctx, void* dst, const void* src, size_t bytes) {
   if (!ctx || !dst) return AFQ_ERR_ARG;
   if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");

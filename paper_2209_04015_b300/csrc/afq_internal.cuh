@@ -273,6 +273,7 @@ int launch_block_sums(afq_ctx* ctx, double* out_dev);
 int launch_shift_from_block(afq_ctx* ctx, const double* sums_dev, int steps, double* e_shift_dev);
 int launch_set_scalar(afq_ctx* ctx, double* dst_dev, double value);
 int launch_spin_squared(afq_ctx* ctx, WalkerSet& s, double2* out_dev, double* mix_dev);  // k_estimators.cu
+int launch_one_rdm(afq_ctx* ctx, WalkerSet& s, double2* work_dev, double2* out_dev);
 
 // adjoint of the local energy (k_adjoint.cu)
 int adjoint_local_energy(afq_ctx* ctx, const double2* gE, double* dh1, double* dL, double2* dphi);

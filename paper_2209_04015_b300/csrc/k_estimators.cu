@@ -131,7 +131,70 @@ cudaError_t launch_s2(const afq_ctx* ctx, const WalkerSet& s, double2* out) {
   return cudaGetLastError();
 }
 
+// sum_z w_z theta^T_z (N x M complex) and sum_z w_z: one thread per element, the
+// walkers added in index order.
+__global__ void __launch_bounds__(256)
+    k_theta_wsum(int W, long NM, const double2* __restrict__ w,
+                 const double2* __restrict__ thetaT, double2* __restrict__ out,
+                 double2* __restrict__ wsum) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < NM;
+       e += (long)gridDim.x * blockDim.x) {
+    double2 a = cmk(0.0, 0.0);
+    for (int z = 0; z < W; ++z) a = cadd(a, cmul(w[z], thetaT[(long)z * NM + e]));
+    out[e] = a;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double2 t = cmk(0.0, 0.0);
+    for (int z = 0; z < W; ++z) t = cadd(t, w[z]);
+    *wsum = t;
+  }
+}
+
+// <G^s>_pq = sum_j Psi_s,pj Thetabar_s,qj / sum_z w_z (G_pq = sum_j Psi_pj theta_qj),
+// both spins: out is 2 x M x M complex.
+__global__ void __launch_bounds__(256)
+    k_one_rdm(int M, int na, int nb, const double* __restrict__ psiT,
+              const double2* __restrict__ tbar, const double2* __restrict__ wsum,
+              double2* __restrict__ out) {
+  const long MM = (long)M * M;
+  const double2 ws = *wsum;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * MM;
+       e += (long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / MM);
+    const long r = e - s * MM;
+    const int p = (int)(r / M), q = (int)(r - (long)p * M);
+    const int n = s ? nb : na, off = s ? na : 0;
+    double2 a = cmk(0.0, 0.0);
+    for (int j = 0; j < n; ++j) {
+      const double ps = psiT[(long)(off + j) * M + p];
+      const double2 t = tbar[(long)(off + j) * M + q];
+      a.x = fma(ps, t.x, a.x);
+      a.y = fma(ps, t.y, a.y);
+    }
+    out[e] = cdiv(a, ws);
+  }
+}
+
+// grid-stride launches: enough CTAs to fill the machine, at most one per 256 elements
+int stride_grid(long n) {
+  const long g = (n + 255) / 256;
+  return (int)(g < 148L * 16 ? (g > 0 ? g : 1) : 148L * 16);
+}
+
 }  // namespace
+
+// Weighted mixed one-body density matrix of both spins into out_dev (2 x M x M
+// complex); work: N x M complex + 1 (device scratch).
+int launch_one_rdm(afq_ctx* ctx, WalkerSet& s, double2* work_dev, double2* out_dev) {
+  const long NM = (long)ctx->N * ctx->M;
+  k_theta_wsum<<<stride_grid(NM), 256, 0, ctx->stream>>>(s.W, NM, s.w, s.thetaT, work_dev,
+                                                    work_dev + NM);
+  AFQ_LAUNCHED(ctx);
+  k_one_rdm<<<stride_grid(2L * ctx->M * ctx->M), 256, 0, ctx->stream>>>(
+      ctx->M, ctx->na, ctx->nb, ctx->psiT, work_dev, work_dev + NM, out_dev);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
+}
 
 int launch_spin_squared(afq_ctx* ctx, WalkerSet& s, double2* out_dev, double* mix_dev) {
   const int pairs = ctx->na * ctx->nb;

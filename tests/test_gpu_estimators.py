@@ -1,12 +1,13 @@
-"""Mixed <S^2> estimator on the GPU (through the C ABI) against the oracle, which
-forms both Green's functions and the trace of their product; the oracle itself is
-pinned by brute force in Fock space.  Tolerance 1e-10 relative (of max(1, |S2|)),
-as for every FP64 quantity."""
+"""Mixed <S^2> estimator and the weighted mixed one-body density matrix on the GPU
+(through the C ABI) against the oracle, which forms the Green's functions walker by
+walker; the oracle itself is pinned by brute force in Fock space.  Tolerance 1e-10
+relative (of max(1, |S2|), or of the largest matrix entry), as for every FP64
+quantity."""
 import numpy as np
 import pytest
 
 from gpu_common import make_pair, need_gpu
-from oracle.estimators import spin_squared
+from oracle.estimators import one_rdm, spin_squared
 from paper_2209_04015_b300.synthetic import gaussian_fields, make_system, perturbed_walkers
 
 pytestmark = pytest.mark.gpu
@@ -52,3 +53,20 @@ def test_s2_of_a_closed_shell_trial_is_zero_and_split_contexts_agree():
     for precision in ("fp64", "split_bf16"):
         c2, o2 = make_pair(s, 6, phi=phi, precision=precision)
         _check(c2, o2)
+
+
+@pytest.mark.parametrize("shape,free", [((37, 5, 3, 71, 9), False), ((37, 5, 3, 71, 9), True),
+                                        ((29, 4, 0, 33, 5), False)])
+def test_one_rdm_matches_oracle(shape, free):
+    M, na, nb, X, W = shape
+    s = make_system(M, na, nb, X, seed=8, decay="geometric", e0=0.2)
+    phi = perturbed_walkers(s, W, eps=0.4, seed=3)
+    ctx, orc = make_pair(s, W, phi=phi, qr_period=2, free_projection=free,
+                         dt=0.01 if free else 0.005)
+    fields = np.stack([gaussian_fields(W, X, seed=70 + k) for k in range(3)])
+    ctx.propagate(fields, 3)  # weights (complex in free projection) and a QR in between
+    orc.propagate(list(fields))
+    g = ctx.one_rdm()
+    ref = one_rdm(orc)
+    assert np.max(np.abs(g - ref)) <= TOL * np.max(np.abs(ref))
+    assert abs(np.trace(g[0]) - na) < 1e-10 and abs(np.trace(g[1]) - nb) < 1e-10

@@ -3,13 +3,15 @@ operator S^2 = S_- S_+ + S_z (S_z + 1) built from Jordan-Wigner matrices (no Wic
 theorem), on general complex walkers whose Green's functions are not symmetric (so
 the index order of the trace is tested); the textbook spin contamination of a
 determinant (Szabo and Ostlund, Eq. 2.271); a closed-shell singlet and a high-spin
-determinant; invariance under Phi -> Phi C."""
+determinant; invariance under Phi -> Phi C.  The weighted mixed one-body density
+matrix: its trace, the one-body energy it gives against the local energy's E1, and
+Fock-space matrix elements for a single walker."""
 import numpy as np
 import pytest
 
 from fockspace import FockSpace
 from oracle.afqmc import Oracle
-from oracle.estimators import spin_squared, spin_squared_of
+from oracle.estimators import one_rdm, spin_squared, spin_squared_of
 from paper_2209_04015_b300.synthetic import make_system, perturbed_walkers
 
 
@@ -88,3 +90,35 @@ def test_gauge_invariance_and_weighted_estimate():
     orc.init_walkers(phi, w=np.array([0.5, 1.0, 2.0, 0.25]))
     s2, mix = spin_squared(orc)
     assert mix == pytest.approx(float((np.sum(orc.w * s2) / np.sum(orc.w)).real), rel=1e-14)
+
+
+def test_one_rdm_trace_one_body_energy_and_fock_space():
+    """The weighted mixed 1-RDM: trace n_s per spin (every walker's G has trace n_s);
+    sum_pq h1_pq (G^a + G^b)_pq equals the weighted one-body energy E1 of the local
+    energy; with one walker it is <Psi_T|a+_p a_q|phi>/<Psi_T|phi> in Fock space."""
+    s = make_system(9, 3, 2, 6, seed=4, decay="half")
+    orc = _oracle(s, s.psi_a, s.psi_b)
+    W = 5
+    orc.init_walkers(perturbed_walkers(s, W, eps=0.5, seed=3), w=np.array([0.3, 1.0, 2.0, 0.7, 1.1]))
+    g = one_rdm(orc)
+    assert abs(np.trace(g[0]) - 3) < 1e-12 and abs(np.trace(g[1]) - 2) < 1e-12
+    e = orc.local_energy_of(orc.phi)
+    w = orc.w
+    e1 = np.sum(w * e[:, 0]) / np.sum(w)
+    assert abs(np.sum(s.h1 * (g[0] + g[1])) - e1) < 1e-11 * max(1.0, abs(e1))
+    M = 4
+    s4 = make_system(M, 2, 1, 3, seed=2, decay="half")
+    o4 = _oracle(s4, s4.psi_a, s4.psi_b)
+    phi = perturbed_walkers(s4, 1, eps=0.8, seed=4)
+    o4.init_walkers(phi)
+    g4 = one_rdm(o4)
+    fs = FockSpace(M)
+    trial = fs.determinant(s4.psi_a, s4.psi_b)
+    v = fs.walker_state(phi[0], 2)
+    den = np.vdot(trial, v)
+    for sigma in (0, 1):
+        for p_ in range(M):
+            for q in range(M):
+                op = fs.cre[fs.so(p_, sigma)] @ fs.ann[fs.so(q, sigma)]
+                ref = np.vdot(trial, op @ v) / den
+                assert abs(g4[sigma][p_, q] - ref) < 1e-12, (sigma, p_, q)
