@@ -196,7 +196,7 @@ int afq_comb(afq_ctx* ctx, double u, double w_cap, int* parents);
    AFQ_ERR_ARG for nblocks < 0, steps_per_block < 1 or an offset outside [0, 1). */
 int afq_run_blocks(afq_ctx* ctx, int nblocks, int steps_per_block, const double* u,
                    double w_cap, int shift_feedback, double* sums);
-/* The energy shift the weight update uses now. */
+/* The energy shift the weight update uses now (AFQ_ERR_ARG for a NULL pointer). */
 int afq_get_e_shift(afq_ctx* ctx, double* e_shift);
 
 /* Mixed estimator of S^2 (Sec. "Customized mixed estimators"; S^2 commutes with H,
@@ -205,7 +205,8 @@ int afq_get_e_shift(afq_ctx* ctx, double* e_shift);
    M_S = (na - nb) / 2, G_s the walker's Green's function of spin s (the trace of
    the product, from Wick's theorem; the paper's printed sum drops the transpose,
    which only agrees for symmetric G).  FP64 from the walkers' current theta.
-   s2_out: W complex (host) or NULL; s2_mix: Re(sum w S2 / sum w) (host) or NULL. */
+   s2_out: W complex (host) or NULL; s2_mix: Re(sum w S2 / sum w) (host) or NULL.
+   AFQ_ERR_STATE before afq_init_walkers. */
 int afq_spin_squared(afq_ctx* ctx, double* s2_out, double* s2_mix);
 
 /* Weighted mixed one-body density matrix of each spin (a Green's-function mixed
@@ -213,7 +214,7 @@ int afq_spin_squared(afq_ctx* ctx, double* s2_out, double* s2_mix);
      <G^s>_pq = sum_z w_z G^s_z,pq / sum_z w_z,   G_pq = <a+_p a_q> = sum_j Psi_pj theta_qj,
    formed as Psi_s (sum_z w_z theta_z,s)^T / sum_z w_z from the walkers' current theta
    (FP64; complex weights in free projection).  g_out: host, 2 x M x M complex, the
-   alpha matrix first. */
+   alpha matrix first (AFQ_ERR_ARG if NULL); AFQ_ERR_STATE before afq_init_walkers. */
 int afq_one_rdm(afq_ctx* ctx, double* g_out);
 
 /* Getters (host outputs): walkers W x M x (na+nb) complex; weights W complex
