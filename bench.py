@@ -454,6 +454,24 @@ def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int 
                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
                         "flops_per_launch": bf16_flops, "flops_note": note,
                         "avg_launch_ms": ex_avg * 1e3}}
+    # the propagation (the split step's largest part): every digit product of the 8 GEMM
+    # passes at its algorithmic flops, over the propagation's event time (which also
+    # holds the digit slicing between the passes)
+    pr_ms, _ = prof["propagate"]
+    pr_s = pr_ms / steps / 1e3
+    N = na + nb
+    prods = [d * (d + 1) // 2 for d in digits]
+    pr_flops = W * M * M * N * (4 * (prods[0] + prods[-1]) + 8 * sum(prods[1:-1]))
+    pr_achieved = pr_flops / pr_s / 1e12
+    out["propagation_roofline"] = {
+        "bound": "tensor", "kernel": "propagation (k_prop_tc, 8 passes per step, with the "
+                                     "digit slicing between them)",
+        "achieved": pr_achieved, "peak": peak, "unit": "TFLOP/s", "frac": pr_achieved / peak,
+        "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
+        "flops_per_step": pr_flops,
+        "flops_note": "digit products of each pass (d (d + 1) / 2 for d digits) x 8 M^2 N "
+                      "(complex Taylor powers) or 4 M^2 N (real P passes), no padding",
+        "ms_per_step": pr_s * 1e3}
     mix.close()
     if fp64_compare:
         f_ms = fp64_step_ms(s, W, rank)
