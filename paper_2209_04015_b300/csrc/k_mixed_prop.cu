@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
   __shared__ __align__(8) uint64_t fin;
   __shared__ uint32_t tmem_base;
   __shared__ int skip;
-  __shared__ int ep_ok;
+  __shared__ int ep_ok[2];  // per tile parity: with two accumulator sets the lead
+                            // epilogue thread can reach the next tile before every
+                            // warp has read this tile's flag
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nst = a.stages, BN = a.BN, brows = a.brows;
   const uint32_t bslot = (uint32_t)BN * 64u;
@@ -262,11 +264,11 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++lt) {
       const int buf = lt % a.nbuf;
       if (q == 0 && lane == 0) {
-        ep_ok = tc::mbar_wait(&tfull[buf], (lt / a.nbuf) & 1, err) ? 1 : 0;
-        if (!ep_ok) atomicExch(err, 1);
+        ep_ok[lt & 1] = tc::mbar_wait(&tfull[buf], (lt / a.nbuf) & 1, err) ? 1 : 0;
+        if (!ep_ok[lt & 1]) atomicExch(err, 1);
       }
       prop_epi_sync();
-      if (!ep_ok) break;
+      if (!ep_ok[lt & 1]) break;
       tc::fence_after_sync();
       const int z = tile / per_z, r = tile - z * per_z;
       const int p0 = (r % a.npt) * 128, j0 = (r / a.npt) * brows;
