@@ -165,3 +165,28 @@ def test_comb_errors_are_reported():
     with pytest.raises(AfqError) as e:
         ctx.run_blocks(2, 0)
     assert e.value.code == 1
+
+
+def test_run_blocks_free_projection_with_shift_feedback():
+    """Complex weights (free projection): no comb, the shift feedback takes the real
+    part of the complex block estimate and |sum w| as the total weight."""
+    s, c = make_config("c1")
+    W = c["W"]
+    ctx, orc = make_pair(s, W, seed=1, free_projection=True, dt=0.01)
+    sums = ctx.run_blocks(3, 4, shift_feedback=True)
+    ref = run_blocks(orc, lambda k: philox.gaussian_fields(k, W, s.X, 1), 3, 4,
+                     shift_feedback=True)
+    np.testing.assert_allclose(sums, ref, rtol=TOL, atol=TOL * np.abs(ref).max())
+    assert_state_parity(ctx, orc, TOL)
+    assert ctx.get_e_shift() == pytest.approx(orc.e_shift, rel=TOL)
+
+
+def test_comb_single_walker_and_zero_blocks():
+    s = _system()
+    ctx, orc = _pair_with_weights(s, 1, np.array([2.5]))
+    phi = ctx.get_walkers()
+    assert ctx.comb(0.7).tolist() == [0]
+    assert np.array_equal(ctx.get_walkers(), phi)
+    assert ctx.get_weights().real.tolist() == [2.5]
+    assert ctx.run_blocks(0, 5).shape == (0, 4)
+    assert ctx.get_step() == 0
