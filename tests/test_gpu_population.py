@@ -107,15 +107,15 @@ def test_run_blocks_is_the_step_sequence(precision):
     assert np.array_equal(a.get_weights(), b.get_weights())
 
 
-@pytest.mark.parametrize("feedback", [False, True])
-def test_run_blocks_matches_oracle_blocks(feedback):
+@pytest.mark.parametrize("feedback,cap", [(False, 0.0), (True, 0.0), (True, 1.05)])
+def test_run_blocks_matches_oracle_blocks(feedback, cap):
     s, c = make_config("c1")
     W = c["W"]
     u = np.array([0.42, 0.05, 0.9, 0.5])
     ctx, orc = make_pair(s, W, seed=1)
-    sums = ctx.run_blocks(4, 5, u=u, shift_feedback=feedback)
+    sums = ctx.run_blocks(4, 5, u=u, w_cap=cap, shift_feedback=feedback)
     ref = run_blocks(orc, lambda k: philox.gaussian_fields(k, W, s.X, 1), 4, 5, u=u,
-                     shift_feedback=feedback)
+                     w_cap=cap, shift_feedback=feedback)
     np.testing.assert_allclose(sums, ref, rtol=TOL, atol=TOL * np.abs(ref).max())
     assert_state_parity(ctx, orc, TOL)
     assert ctx.get_e_shift() == pytest.approx(orc.e_shift, rel=TOL)
