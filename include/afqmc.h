@@ -376,6 +376,9 @@ int afq_get_tiles(afq_ctx* ctx, int* tiles, int n);
    stderr.  The first call on a device looks up the array's device address (make
    that first call before any stream capture).  All calls share the array, so
    calls that overlap on the GPU race; each call writes every slot it reads.
+   The exchange kernel's shared-memory limit is a process-wide attribute that the
+   context path shares: a call only ever raises it (never lowers it), so it does
+   not affect launches of contexts on other streams or host threads.
    Returns AFQ_OK, AFQ_ERR_ARG or AFQ_ERR_CUDA. */
 #define AFQ_STATIC_EXCHANGE_SLOTS 262144
 int afq_exchange_energy_static(int M, int X, int na, int nb, int W, const double* Lt_dev,

@@ -210,6 +210,15 @@ struct afq_ctx {
 
 // status helpers -------------------------------------------------------------
 int afq_fail(afq_ctx* ctx, int code, const std::string& msg);
+
+// Make the dynamic shared-memory limit of kernel fn on the current device at least
+// smem bytes.  The limit is a process-wide attribute of the kernel that every caller
+// (every context, stream and host thread) shares, so it is only ever raised: a
+// smaller request after a larger one keeps the larger limit, and launches sized for
+// the larger request stay valid.  The largest size set per (device, kernel) is kept
+// under a mutex, so the attribute call is issued only when the limit grows (none in
+// steady state, and none while a graph captured after a first ordinary step runs).
+cudaError_t raise_smem_limit(const void* fn, size_t smem);
 #define AFQ_CUDA(ctx, call)                                                              \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \

@@ -191,13 +191,9 @@ int launched(afq_ctx* ctx) {
 size_t dphi_smem(int n) { return (size_t)n * 2 * n * 16 + (size_t)n * n * 16 + (size_t)n * 16; }
 
 int configure_bwd(afq_ctx* ctx, size_t sm2) {
-  static size_t configured2 = 0;
-  if (sm2 > configured2) {
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_dphi<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_dphi<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_dphi<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    configured2 = sm2;
-  }
+  AFQ_CUDA(ctx, raise_smem_limit((const void*)k_bwd_dphi<0>, sm2));
+  AFQ_CUDA(ctx, raise_smem_limit((const void*)k_bwd_dphi<1>, sm2));
+  AFQ_CUDA(ctx, raise_smem_limit((const void*)k_bwd_dphi<2>, sm2));
   return AFQ_OK;
 }
 

@@ -576,11 +576,7 @@ int run_backward(afq_ctx* ctx, ChainWork& w, const double2* gE, double* dh1, dou
     if (sg.qr_end) {
       const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
       const size_t sm = (size_t)nmax * nmax * 16;
-      static size_t configured = 0;
-      if (sm > configured) {
-        AFQ_CUDA(ctx, cudaFuncSetAttribute(k_bwd_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        configured = sm;
-      }
+      AFQ_CUDA(ctx, raise_smem_limit((const void*)k_bwd_qr, sm));
       k_bwd_qr<<<dim3(W, 2), 256, sm, ctx->stream>>>(M, N, ctx->na, ctx->nb,
                                                      tp.ckpt + (long)sg.ck_out * WMN,
                                                      w.seg + (long)sg.len * WMN, w.lam);

@@ -119,12 +119,9 @@ __global__ void __launch_bounds__(256)
 template <int PT>
 cudaError_t launch_s2(const afq_ctx* ctx, const WalkerSet& s, double2* out) {
   const size_t smem = s2_smem(ctx->N);
-  static size_t configured = 48 * 1024;
-  if (smem > configured) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_spin_squared<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = raise_smem_limit((const void*)k_spin_squared<PT>, smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   k_spin_squared<PT><<<s.W, ST, smem, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb,
                                                       ctx->psiT, s.thetaT, out);

@@ -274,13 +274,8 @@ int sm_count() {
 template <int S>
 cudaError_t launch_ex(int grid, size_t smem, cudaStream_t stream, const CUtensorMap& ta,
                       const CUtensorMap& tb, const ExArgs& a) {
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_exchange_tc<S>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t e = raise_smem_limit((const void*)k_exchange_tc<S>, smem);
+  if (e != cudaSuccess) return e;
   k_exchange_tc<S><<<grid, kExThreads, smem, stream>>>(ta, tb, a);
   return cudaGetLastError();
 }

@@ -845,13 +845,8 @@ int sm_count_prop() {
 template <int S, bool REAL>
 cudaError_t launch_prop_s(int grid, size_t smem, cudaStream_t stream, const CUtensorMap& ta,
                           const CUtensorMap& tb, const PropArgs& a) {
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_prop_tc<S, REAL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t e = raise_smem_limit((const void*)k_prop_tc<S, REAL>, smem);
+  if (e != cudaSuccess) return e;
   k_prop_tc<S, REAL><<<grid, 32 * kPropWarps, smem, stream>>>(ta, tb, a);
   return cudaGetLastError();
 }

@@ -486,12 +486,7 @@ template <int NC, int G>
 int launch_propagate_g(afq_ctx* ctx) {
   const int threads = 32 * ((G * ctx->M + 31) / 32);
   const size_t smem = propagate_fp64_smem(ctx->M, NC);
-  static size_t configured = 0;
-  if (smem > configured) {
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_propagate_fp64<NC, G>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  AFQ_CUDA(ctx, raise_smem_limit((const void*)k_propagate_fp64<NC, G>, smem));
   dim3 grid((ctx->N + NC - 1) / NC, ctx->ws.W);
   if (!ctx->Asum) return afq_fail(ctx, AFQ_ERR_STATE, "FP64 propagation needs Re A + Im A");
   k_propagate_fp64<NC, G><<<grid, threads, smem, ctx->stream>>>(

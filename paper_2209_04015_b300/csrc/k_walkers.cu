@@ -579,12 +579,7 @@ template <bool DF, int MO>
 int launch_overlap_mo(afq_ctx* ctx, WalkerSet& s) {
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
   const size_t smem = overlap_smem(nmax);
-  static size_t configured = 0;
-  if (smem > configured) {
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_overlap_theta<DF, MO>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  AFQ_CUDA(ctx, raise_smem_limit((const void*)k_overlap_theta<DF, MO>, smem));
   k_overlap_theta<DF, MO><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
       ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
       ctx->flags);
@@ -650,12 +645,7 @@ int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s) {
   const int ngroups = (ctx->X + G - 1) / G;
   if (ngroups > ctx->ex_groups) return afq_fail(ctx, AFQ_ERR_STATE, "exchange groups exceed slots");
   const size_t smem = exchange_smem(G, nmax);
-  static size_t configured = 0;
-  if (smem > configured) {
-    AFQ_CUDA(ctx, cudaFuncSetAttribute(k_exchange_fp64,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  AFQ_CUDA(ctx, raise_smem_limit((const void*)k_exchange_fp64, smem));
   k_exchange_fp64<<<dim3(ngroups, s.W, 2), ET, smem, ctx->stream>>>(
       ctx->M, ctx->N, ctx->na, ctx->nb, ctx->X, G, ctx->ex_groups, ctx->Lt, s.thetaT, s.ekp);
   AFQ_LAUNCHED(ctx);
@@ -670,8 +660,8 @@ cudaError_t launch_exchange_fp64_raw(int M, int X, int na, int nb, int W, const 
   const int G = exchange_group_size(nmax);
   const int ngroups = (X + G - 1) / G;
   const size_t smem = exchange_smem(G, nmax);
-  cudaError_t e = cudaFuncSetAttribute(k_exchange_fp64,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // shared with the context path: never lowers the limit its launches rely on
+  cudaError_t e = raise_smem_limit((const void*)k_exchange_fp64, smem);
   if (e != cudaSuccess) return e;
   k_exchange_fp64<<<dim3(ngroups, W, 2), ET, smem, stream>>>(M, na + nb, na, nb, X, G, ngroups,
                                                              Lt, thetaT, ekp);

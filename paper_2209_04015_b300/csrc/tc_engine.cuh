@@ -389,15 +389,10 @@ inline void plan_smem(int S, int kUA, int kUB, int BN, size_t epilogue_bytes, in
 template <int S, class P>
 cudaError_t launch_tc(dim3 grid, size_t smem, cudaStream_t stream, const CUtensorMap& a,
                       const CUtensorMap& b, const typename P::Args& args) {
-  // set once per instantiation and size, so that no attribute call is issued while a
-  // graph is being captured after a first ordinary step
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_split<S, P>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  // raised only when it grows, so that no attribute call is issued while a graph is
+  // being captured after a first ordinary step
+  cudaError_t e = raise_smem_limit((const void*)k_tc_split<S, P>, smem);
+  if (e != cudaSuccess) return e;
   k_tc_split<S, P><<<grid, kThreads, smem, stream>>>(a, b, args);
   return cudaGetLastError();
 }

@@ -37,9 +37,12 @@ def rel(a, b, floor=1e-300):
 
 
 def walker_rel(a, b):
-    """Per-walker relative Frobenius distance of (W, M, N) stacks."""
-    num = np.linalg.norm((a - b).reshape(a.shape[0], -1), axis=1)
-    return num / np.linalg.norm(b.reshape(b.shape[0], -1), axis=1)
+    """Per walker, the largest element difference over the walker's largest element:
+    max_pj |a_z,pj - b_z,pj| / max_pj |b_z,pj| for (W, M, N) stacks.  Every element is
+    compared, so a wrong sign on a small element shows up (a norm ratio could hide it)."""
+    W = a.shape[0]
+    num = np.abs(a - b).reshape(W, -1).max(axis=1)
+    return num / np.abs(b).reshape(W, -1).max(axis=1)
 
 
 def assert_state_parity(ctx, orc, tol=1e-10):
