@@ -6,6 +6,11 @@ Taylor propagator with the one-body halves, overlap ratio and phaseless weight,
 QR every 5th step) followed by the mixed local energy of every walker.  The
 metric is walker-steps per second.
 
+The headline workload is the paper's large molecular shape (52 electrons in 290
+orbitals, 1500 Cholesky vectors, 640 walkers) stepped in FP64; the same workload in
+split precision on the tensor cores, the 100-orbital workload, the batched uneven
+systems, the paper's block cadence and the adjoint are reported beside it.
+
   python bench.py [--gpus N --steps K --warmup W] [--impl afq|reference]
 
 With N > 1 (under torch.distributed.run) every rank runs an independent replica
@@ -32,19 +37,29 @@ sys.path.insert(0, ROOT)
 
 METRIC = "walker-steps/s/B300 (propagate+E_loc), FP64 vs mixed, |ΔE| vs FP64 oracle"
 UNIT = "walker-steps/s"
-WORKLOAD = "c2"
-WORKLOAD_TEXT = ("ph-AFQMC step + E_loc, 100 orbitals, 10a+10b electrons, 400 Cholesky "
-                 "vectors (geometric norm decay), 128 complex128 walkers, dt 0.005, QR every "
-                 "5 steps, Philox fields")
-FP64_NOMINAL_TFLOPS = 1.25  # B300 FP64 nominal: 148 SMs x 2032 MHz x ~4.15 flop/clk/SM
-# DRAM bytes (read + write) per launch of the dominant kernel, from ncu captures of
-# these exact workloads (profiles/propagation_fp64_c2.md, profiles/exchange_tc_c3.md);
-# absent where no capture of the current kernel exists.
-TRAFFIC = {("split_bf16", "c3", "exchange_direct"): 572279808 + 10032128,
-           ("fp64", "c2", "propagate"): 34943232 + 16384}  # captured with 2 columns per CTA
+WORKLOAD = "c3"
+WORKLOAD_TEXT = {
+    "c2": ("ph-AFQMC step + E_loc, 100 orbitals, 10a+10b electrons, 400 Cholesky vectors "
+           "(geometric norm decay), 128 complex128 walkers, dt 0.005, QR every 5 steps, "
+           "Philox fields"),
+    "c3": ("ph-AFQMC step + E_loc, 290 orbitals, 26a+26b electrons, 1500 Cholesky vectors "
+           "(geometric norm decay), 640 complex128 walkers, dt 0.005, QR every 5 steps, "
+           "Philox fields"),
+}
+# NVIDIA's rated FP64 throughput of B300 (context only; fractions use the FP64 rate
+# measured in the run)
+FP64_VENDOR_TFLOPS = 1.25
+# DRAM bytes (read + write) of the dominant kernel class from one-pass ncu captures of
+# these exact workloads: per launch for the FP64 kernels, per step (every launch of
+# the class) for the split propagation; absent where no capture of the current
+# kernels exists.
+TRAFFIC = {("fp64", "c2", "propagate"): 34943232 + 16384}
 FP64_KERNELS = {"propagate": "k_propagate_fp64", "exchange": "k_exchange_v / k_exchange_fp64",
                 "vhs": "k_vhs_fp64", "force_bias": "k_force_bias_fp64"}
-SPLIT_PRODUCTS = 6          # bf16 slice products of 3 slices or digits (s + t <= 2)
+SPLIT_KERNELS = {"propagate": "k_prop_tc (8 GEMM passes) + k_taylor_slice / k_slice_cplx1",
+                 "exchange": "k_tc_split<ExVP> + k_exv_dot (stored) / k_exchange_tc (direct)",
+                 "vhs": "k_slice_y + k_tc_split<VhsP> + k_slice_cplx1",
+                 "force_bias": "k_tc_split<FbP> + reduction"}
 
 
 def measured_peaks() -> dict:
@@ -58,20 +73,22 @@ def measured_peaks() -> dict:
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["afq", "reference"], default="afq")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="budget of the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the split-precision legs")
-    ap.add_argument("--mixed-steps", type=int, default=20)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline only: skip the split-precision, c2, batched, block and "
+                         "adjoint legs")
+    ap.add_argument("--split-steps", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
-    ap.add_argument("--profile-leg", choices=["mixed-c2", "mixed-c3", "batched", "adjoint",
-                                              "blocks"],
-                    default=None, help="run one secondary leg alone and print its JSON (for ncu)")
+    ap.add_argument("--profile-leg", choices=["fp64-c3", "split-c3", "fp64-c2", "split-c2",
+                                              "batched", "batched-fp64", "adjoint", "blocks"],
+                    default=None, help="run one leg alone and print its JSON (for ncu)")
     ap.add_argument("--profile-walkers", type=int, default=0,
-                    help="walker count of a --profile-leg mixed leg (0: the workload's)")
+                    help="walker count of a --profile-leg step leg (0: the workload's)")
     ap.add_argument("--error-steps", type=int, default=100,
                     help="steps of the split-precision drift check")
     return ap.parse_args()
@@ -100,6 +117,14 @@ def job_throughput(total_ms: float, units_per_rank: int, world: int, device="cpu
     return world * units_per_rank / (total_ms / 1e3), total_ms
 
 
+def host_cores() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        return max([p.get("num_threads", 1) for p in threadpool_info()] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def exchange_flops(W, X, M, na, nb, algorithm="direct"):
     """Algorithmic flops of the exchange for W walkers.  direct: T = L~ theta
     (4 n^2 M real flops per g and spin, real x complex) plus sum T_ij T_ji (8 n^2 flops
@@ -123,7 +148,7 @@ def stored_tc_macs(W, M, na, nb):
 
 
 def step_flops(W, X, M, na, nb, order=6, exchange="direct"):
-    """Algorithmic flops of one walker step (all walkers), by part."""
+    """Algorithmic flops of one FP64 walker step (all walkers), by kernel class."""
     N = na + nb
     Mp = M * (M + 1) // 2
     return {
@@ -135,6 +160,58 @@ def step_flops(W, X, M, na, nb, order=6, exchange="direct"):
         "overlap_theta": W * sum(4 * M * n * n + 8 * M * n * n for n in (na, nb)),
         "exchange": exchange_flops(W, X, M, na, nb, exchange),
     }
+
+
+def split_flops(W, X, M, na, nb, algo, S, digits):
+    """Digit-product flops of the split-precision tensor-core GEMMs per step, by
+    kernel class: each product of an S-digit operand pair with s + t <= S - 1 counts
+    the GEMM's algorithmic flops (no padding counted, except the stored exchange's
+    128-row tile triangle)."""
+    N = na + nb
+    Mp = M * (M + 1) // 2
+    prods = lambda d: d * (d + 1) // 2  # noqa: E731
+    out = {"force_bias": prods(S) * 2 * X * N * M * 2 * W,
+           "vhs": prods(4) * 2 * Mp * X * 2 * W}
+    if digits:
+        Sp = max(digits)
+        out["vhs"] = prods(Sp) * 2 * Mp * X * 2 * W
+        out["propagate"] = W * M * M * N * (4 * (prods(digits[0]) + prods(digits[-1])) +
+                                            8 * sum(prods(d) for d in digits[1:-1]))
+    if algo == "stored":
+        out["exchange"] = prods(S) * 2 * stored_tc_macs(W, M, na, nb)
+    else:
+        out["exchange"] = prods(S) * exchange_flops(W, X, M, na, nb)
+    return out
+
+
+def fp64_peak() -> dict:
+    """FP64 throughput of this GPU, measured: the FMA-loop probe of the library
+    (afq_fp64_fma_rate: independent FMA chains filling every SM, CUDA events, best of
+    three), the roofline denominator of the FP64 kernels; cuBLAS DGEMM (torch.matmul on
+    float64, 4096^3, best of 5, CUDA events) beside it."""
+    import torch
+    from paper_2209_04015_b300.afqmc import fp64_fma_rate
+    fma = fp64_fma_rate(torch.cuda.current_stream().cuda_stream)
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ b
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c = a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b, c
+    torch.cuda.empty_cache()
+    return {"tflops": fma, "how": "FMA-loop probe afq_fp64_fma_rate (8 CTAs x 256 threads per "
+            "SM, 8 independent chains per thread), best of 3, CUDA events",
+            "dgemm_tflops": 2 * n ** 3 / (best / 1e3) / 1e12,
+            "dgemm_how": f"cuBLAS DGEMM {n}^3 (torch.matmul float64), best of 5, CUDA events",
+            "vendor_tflops": FP64_VENDOR_TFLOPS}
 
 
 class ClockSampler:
@@ -187,65 +264,276 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(seconds: float, W_sample: int = 8) -> dict:
-    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+def oracle_sample(name: str, walkers: int, seconds: float, min_steps: int, max_steps: int,
+                  seed_step: int = 0):
+    """The FP64 oracle as it stands on a bounded sample of a workload: `walkers` of its
+    walkers (started at the trial), steps with Philox fields, the QR cadence and the
+    local energy every step, until `seconds` have passed (at least min_steps, at most
+    max_steps).  Walkers are independent, so walker-steps/s of the sample carries over
+    to the full walker count (the oracle loops over walkers or vectorises them).
+    Returns (walker-steps/s, steps, seconds)."""
     from oracle.afqmc import Oracle
     from oracle.philox import gaussian_fields
     from paper_2209_04015_b300.synthetic import make_config, trial_walkers
-    s, c = make_config(WORKLOAD)
+    s, _ = make_config(name)
     orc = Oracle(s.h1, s.L, s.e0, s.psi_a, s.psi_b, dt=0.005, qr_period=5)
-    orc.init_walkers(trial_walkers(s, W_sample))
+    orc.init_walkers(trial_walkers(s, walkers))
     t0 = time.perf_counter()
     steps = 0
     while True:
-        xi = gaussian_fields(steps, W_sample, s.X, 1)
-        orc.step(xi)
+        orc.step(gaussian_fields(seed_step + steps, walkers, s.X, 1))
         if orc.nstep % 5 == 0:
             orc.orthogonalise()
         orc.local_energy()
         steps += 1
-        if time.perf_counter() - t0 > seconds or steps >= 200:
+        el = time.perf_counter() - t0
+        if steps >= max_steps or (steps >= min_steps and el > seconds):
             break
     dt = time.perf_counter() - t0
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([p.get("num_threads", 1) for p in threadpool_info()] + [1])
-    except Exception:
-        cores = os.cpu_count() or 1
-    return {"value": W_sample * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{W_sample} of the {c['W']} walkers of the {WORKLOAD} workload, "
-                      f"{steps} steps (step + QR cadence + E_loc), {dt:.1f} s of host time"}
+    return walkers * steps / dt, steps, dt
 
 
-def fp64_step_ms(s, W: int, rank: int, steps: int = 2) -> float:
-    """Event-timed FP64 step + local energy on the same system (all walkers)."""
-    import torch
+def cpu_baseline(name: str, seconds: float, walkers: int) -> dict:
+    from paper_2209_04015_b300.synthetic import CONFIGS
+    value, steps, dt = oracle_sample(name, walkers, seconds, 3, 200)
+    return {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": f"{walkers} of the {CONFIGS[name]['W']} walkers of the {name} workload, "
+                      f"{steps} steps (step + QR cadence + E_loc every step), {dt:.1f} s of "
+                      "host time; walker-steps/s extrapolated to all walkers (walkers are "
+                      "independent); set-up excluded"}
+
+
+# ----------------------------------------------------------------------------- legs
+
+def new_context(s, W, precision, rank, stream, autotune=True, **kw):
     from paper_2209_04015_b300 import AfqContext
-    stream = torch.cuda.current_stream()
-    ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, stream=stream.cuda_stream)
+    ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, precision=precision,
+                     stream=stream.cuda_stream, **kw)
     ctx.init_hamiltonian(s.h1, s.L, s.e0)
     ctx.init_trial(s.psi_a, s.psi_b)
     ctx.init_walkers(W)
-    ctx.propagate_dev(None, 1)
-    ctx.local_energy_dev(None, None)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
+    if autotune:
+        ctx.autotune()  # launch shapes (set-up, outside the timed region); walkers restored
+    return ctx
+
+
+def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, world: int,
+             local: int, walkers: int = 0, e2e_steps: int = 0, clocks: bool = False) -> dict:
+    """Device-timed steps (propagate + local energy of every walker) of one workload in
+    one precision: W untimed warm-up steps, then `steps` steps, each between CUDA events
+    on the context's stream with a 256 MB L2 flush before it (outside the events), the
+    built-in per-kernel-class event profiler on; the dominant kernel class and its
+    roofline; then the same metric end to end through the host-buffer C-ABI calls
+    (pinned host fields in, energies out, every step) on a fresh context."""
+    import torch
+    from paper_2209_04015_b300.synthetic import make_config
+
+    s, c = make_config(name, seed=1 + rank)
+    W, X, M, na, nb = walkers or c["W"], s.X, s.M, s.na, s.nb
+    stream = torch.cuda.current_stream()
+    ctx = new_context(s, W, precision, rank, stream)
+    e_dev = torch.empty((W, 4, 2), dtype=torch.float64, device="cuda")
+    emix_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
         ctx.propagate_dev(None, 1)
-        ctx.local_energy_dev(None, None)
-    b.record(stream)
+        ctx.local_energy_dev(e_dev.data_ptr(), emix_dev.data_ptr())
+
+    for _ in range(max(warmup, 3)):
+        step()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local) if clocks else None
+    if sampler:
+        time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    ctx.profile_enable(True)
+    n0 = ctx.launch_count()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()                      # write 256 MB: evicts L2 between timed steps
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - n0
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    clk = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    value, total_ms = job_throughput(float(sum(step_ms)), W * steps, world, device="cuda")
+    algo = ctx.exchange_algorithm()
+    tiles = ctx.get_tiles()
+    digits = ctx.prop_digits()[0] if precision != "fp64" else None
+    S = ctx.params.split_slices or 4
     ctx.close()
-    return a.elapsed_time(b) / steps
+    del flush
+
+    # end to end through the public host-buffer API on a fresh context (the synthetic
+    # trial lies hundreds of Ha above the projected energy, so with E_shift = E_HF a
+    # long-running context's weights eventually overflow -- harmless to the timed
+    # kernels, which do not read them, but reported by the checked host-buffer calls)
+    e2e = None
+    if e2e_steps > 0:
+        host_fields = torch.empty((e2e_steps + 1, W, X), dtype=torch.float64).pin_memory()
+        host_fields.copy_(torch.from_numpy(
+            np.random.default_rng(5 + rank).standard_normal((e2e_steps + 1, W, X))))
+        hf = host_fields.numpy()
+        ectx = new_context(s, W, precision, rank, stream)
+        ectx.propagate(hf[0], 1)
+        ectx.local_energy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            ectx.propagate(hf[k + 1], 1)
+            ectx.local_energy()
+        e2e_s = time.perf_counter() - t0
+        ectx.close()
+        e2e_value, _ = job_throughput(e2e_s * 1e3, W * e2e_steps, world, device="cuda")
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": W * X * 8,
+               "d2h_bytes_per_step": W * 4 * 16 + 8, "steps": e2e_steps,
+               "api": "afq_propagate (host N(0,1) fields, pinned) + afq_local_energy (host "
+                      "energies and weighted estimate) per step; host wall clock"}
+
+    # the dominant kernel class by device time, its algorithmic rate and roofline
+    kernels = {k: {"ms_per_step": v[0] / steps, "launches": v[1],
+                   "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)}
+               for k, v in prof.items() if v[1]}
+    names = FP64_KERNELS if precision == "fp64" else SPLIT_KERNELS
+    dom = max(names, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    out = {"workload": name, "precision": precision, "M": M, "na": na, "nb": nb, "X": X, "W": W,
+           "value": value, "unit": UNIT, "ms_per_step": total_ms / steps, "steps": steps,
+           "warmup": warmup, "exchange_algorithm": algo, "autotuned_tiles": tiles,
+           "kernels": kernels, "gpu_launches": launches, "e2e": e2e, "clocks": clk,
+           "l2": "flushed between timed steps (256 MB write, outside the step events)"}
+    if precision == "fp64":
+        flops = step_flops(W, X, M, na, nb, exchange=algo)
+        per_launch = flops[dom] / max(dom_n / steps, 1)
+        avg_s = dom_ms / max(dom_n, 1) / 1e3
+        out["step_flops"] = sum(flops.values())
+        out["step_tflops"] = out["step_flops"] / (out["ms_per_step"] / 1e3) / 1e12
+        out["roofline"] = {"bound": "alu", "kernel": f"{dom} ({FP64_KERNELS[dom]})",
+                           "achieved": per_launch / avg_s / 1e12, "unit": "TFLOP/s",
+                           "traffic": TRAFFIC.get(("fp64", name, dom)) if not walkers else None,
+                           "flops_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3,
+                           "per": "launch"}
+    else:
+        flops = split_flops(W, X, M, na, nb, algo, S, digits)
+        per_step = flops[dom]
+        dom_s = dom_ms / steps / 1e3
+        out["prop_digits"] = digits
+        out["split_slices"] = S
+        out["tensor_flops_per_step"] = sum(flops.values())
+        out["roofline"] = {"bound": "tensor", "kernel": f"{dom} ({SPLIT_KERNELS[dom]})",
+                           "achieved": per_step / dom_s / 1e12, "unit": "TFLOP/s",
+                           "traffic": (TRAFFIC.get(("split_bf16", name, dom))
+                                       if not walkers else None),
+                           "flops_per_step": per_step, "ms_per_step": dom_s * 1e3,
+                           "per": "step (every launch of the class, digit slicing included)",
+                           "flops_note": "digit products (s + t <= S - 1 of S digits) x the "
+                                         "GEMM's algorithmic flops, no padding counted"}
+        out["class_rates_tflops"] = {k: flops[k] / (prof[k][0] / steps / 1e3) / 1e12
+                                     for k in flops if prof.get(k, (0, 0))[0] > 0}
+    return out
+
+
+def attach_peak(roof: dict, peaks: dict, fp64: dict | None) -> dict:
+    """Roofline denominators: measured BF16 (MEASURED_PEAKS.json, burst and sustained)
+    for tensor-bound classes, the DGEMM rate measured in this run for FP64 ones."""
+    if roof["bound"] == "tensor":
+        burst = peaks.get("bf16_tflops", 1800.0)
+        sust = peaks.get("bf16_tflops_sustained", 1400.0)
+        roof.update(peak=burst, frac=roof["achieved"] / burst,
+                    frac_of_sustained=roof["achieved"] / sust,
+                    peak_source="MEASURED_PEAKS.json bf16_tflops (burst, measured; "
+                                "bf16_tflops_sustained for frac_of_sustained)"
+                    if "bf16_tflops" in peaks else "fallback 1.8 PFLOP/s bf16 burst")
+    else:
+        p = fp64["tflops"]
+        roof.update(peak=p, frac=roof["achieved"] / p,
+                    frac_of_vendor=roof["achieved"] / FP64_VENDOR_TFLOPS,
+                    frac_of_dgemm=roof["achieved"] / fp64["dgemm_tflops"],
+                    peak_source=f"FP64 measured in this run: {fp64['how']} "
+                                f"({p:.3f} TFLOP/s); cuBLAS DGEMM {fp64['dgemm_tflops']:.3f} "
+                                f"TFLOP/s for frac_of_dgemm; vendor rating "
+                                f"{FP64_VENDOR_TFLOPS} TFLOP/s for frac_of_vendor")
+    return roof
+
+
+def mixed_errors(name: str, rank: int, long_steps: int = 100, check_walkers: int = 16) -> dict:
+    """Errors of the split-precision path against the FP64 path on the first walkers
+    after 1 and after long_steps steps of device Philox fields.  Walkers are
+    independent and the Philox counters are keyed by walker index, so an FP64 context
+    holding only the first walkers sees exactly the same fields."""
+    import torch
+    from paper_2209_04015_b300 import AfqContext
+    from paper_2209_04015_b300.synthetic import make_config
+
+    s, c = make_config(name, seed=1 + rank)
+    W = c["W"]
+    stream = torch.cuda.current_stream()
+
+    def context(precision, nw, phi=None):
+        ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, precision=precision,
+                         stream=stream.cuda_stream)
+        ctx.init_hamiltonian(s.h1, s.L, s.e0)
+        ctx.init_trial(s.psi_a, s.psi_b)
+        ctx.init_walkers(nw, phi)
+        return ctx
+
+    def errors(mix, ref, n, gE):
+        em, _ = mix.local_energy()
+        er, _ = ref.local_energy()
+        out = {part: float(np.max(np.abs(em[:n, i] - er[:, i])))
+               for i, part in enumerate(("E1", "EJ", "EK", "E_L"))}
+        wm, wr = np.abs(mix.get_weights()[:n]), np.abs(ref.get_weights())
+        live = wr > 0
+        out["w_rel"] = float(np.max(np.abs(wm - wr)[live] / wr[live])) if live.any() else 0.0
+        om, orf = mix.get_overlaps()[:n], ref.get_overlaps()
+        out["overlap_rel"] = float(np.max(np.abs(om - orf) / np.abs(orf)))
+        pm, pr = mix.get_walkers()[:n], ref.get_walkers()
+        out["phi_rel"] = float(np.max(np.abs(pm - pr).reshape(n, -1).max(axis=1) /
+                                      np.abs(pr).reshape(n, -1).max(axis=1)))
+        probe = context("fp64", n, phi=pm)
+        gm, gr = probe.local_energy_backward(gE), ref.local_energy_backward(gE)
+        probe.close()
+        for name_, a, b in zip(("dh1", "dL", "dphi"), gm, gr):
+            out[name_ + "_rel"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        return out
+
+    mix = context("split_bf16", W)
+    ref = context("fp64", check_walkers)
+    rng = np.random.default_rng(5)
+    gE = rng.standard_normal(check_walkers) + 1j * rng.standard_normal(check_walkers)
+    errs = {}
+    for k in range(1, long_steps + 1):
+        mix.propagate(None, 1)
+        ref.propagate(None, 1)
+        if k in (1, long_steps):
+            errs[k] = errors(mix, ref, check_walkers, gE)
+    mix.close()
+    ref.close()
+    return {"after_1_step": errs[1], f"after_{long_steps}_steps": errs[long_steps],
+            "dE_L_max_1_step": errs[1]["E_L"],
+            f"dE_L_max_{long_steps}_steps": errs[long_steps]["E_L"],
+            "reference": f"FP64 path (parity-checked against the FP64 oracle at 1e-10) on the "
+                         f"first {check_walkers} of {W} walkers, same Philox fields",
+            "units": "E1, EJ, EK, E_L: max |d| in Ha; *_rel: max relative error (weights, "
+                     "overlaps per walker; walkers: max element difference over the walker's "
+                     "largest element; gradients max |d| / max |ref|, FP64 adjoint at the "
+                     "split-propagated walkers, cotangent seeded)"}
 
 
 def block_leg(name: str, precision: str, rank: int, blocks: int = 4, block_steps: int = 25) -> dict:
     """The paper's block cadence through the native block driver (afq_run_blocks): 25
     propagation steps, then one local energy, the orthogonalisation (qr_period = 25),
     the energy-shift feedback and population control by the comb, device-event timed
-    over `blocks` blocks after one warm-up block.  Context for the per-step metric, which evaluates the energy
-    every step and orthogonalises every 5."""
+    over `blocks` blocks after one warm-up block.  Context for the per-step metric,
+    which evaluates the energy every step and orthogonalises every 5."""
     import torch
     from paper_2209_04015_b300 import AfqContext
     from paper_2209_04015_b300.synthetic import make_config
@@ -322,166 +610,7 @@ def workflow_leg(name: str, precision: str, rank: int, blocks: int = 160, discar
                     "physical energy"}
 
 
-def mixed_leg(name: str, steps: int, warmup: int, rank: int, check_walkers: int = 16,
-              long_steps: int = 100, walkers: int = 0, fp64_compare: bool = False) -> dict:
-    """Split-precision (tcgen05) throughput on one workload, and its errors against
-    the FP64 path on the first walkers after 1 and after long_steps steps.  Walkers
-    are independent and the Philox counters are keyed by walker index, so an FP64
-    context holding only the first walkers sees exactly the same fields."""
-    long_steps = max(long_steps, 0)  # 0: no drift check (no FP64 reference context)
-    import torch
-    from paper_2209_04015_b300 import AfqContext
-    from paper_2209_04015_b300.synthetic import make_config
-
-    s, c = make_config(name, seed=1 + rank)
-    W, X, M, na, nb = walkers or c["W"], s.X, s.M, s.na, s.nb
-    check_walkers = min(check_walkers, W)
-    stream = torch.cuda.current_stream()
-
-    def context(precision, nw, phi=None):
-        ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, precision=precision,
-                         stream=stream.cuda_stream)
-        ctx.init_hamiltonian(s.h1, s.L, s.e0)
-        ctx.init_trial(s.psi_a, s.psi_b)
-        ctx.init_walkers(nw, phi)
-        return ctx
-
-    def split_errors(mix, ref, n, gE):
-        """Errors of the split-precision walkers against the FP64 path (first n walkers):
-        max |dE| per energy part (Ha), max relative error of weights, overlaps and
-        walker matrices, and of the local-energy gradients, which the FP64 adjoint
-        (the one a split context runs) gives at the split-propagated walkers against
-        those at the FP64-propagated ones (max |d| / max |ref| per output)."""
-        em, _ = mix.local_energy()
-        er, _ = ref.local_energy()
-        out = {part: float(np.max(np.abs(em[:n, i] - er[:, i])))
-               for i, part in enumerate(("E1", "EJ", "EK", "E_L"))}
-        wm, wr = np.abs(mix.get_weights()[:n]), np.abs(ref.get_weights())
-        live = wr > 0
-        out["w_rel"] = float(np.max(np.abs(wm - wr)[live] / wr[live])) if live.any() else 0.0
-        om, orf = mix.get_overlaps()[:n], ref.get_overlaps()
-        out["overlap_rel"] = float(np.max(np.abs(om - orf) / np.abs(orf)))
-        pm, pr = mix.get_walkers()[:n], ref.get_walkers()
-        out["phi_rel"] = float(np.max(np.linalg.norm((pm - pr).reshape(n, -1), axis=1) /
-                                      np.linalg.norm(pr.reshape(n, -1), axis=1)))
-        probe = context("fp64", n, phi=pm)
-        gm, gr = probe.local_energy_backward(gE), ref.local_energy_backward(gE)
-        probe.close()
-        for name_, a, b in zip(("dh1", "dL", "dphi"), gm, gr):
-            out[name_ + "_rel"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
-        return out
-
-    mix = context("split_bf16", W)
-    errs = {1: None, long_steps: None}
-    if long_steps > 0:
-        ref = context("fp64", check_walkers)
-        rng = np.random.default_rng(5)
-        gE = rng.standard_normal(check_walkers) + 1j * rng.standard_normal(check_walkers)
-        for k in range(1, long_steps + 1):
-            mix.propagate(None, 1)
-            ref.propagate(None, 1)
-            if k in (1, long_steps):
-                errs[k] = split_errors(mix, ref, check_walkers, gE)
-        ref.close()
-    e_dev = torch.empty((W, 4, 2), dtype=torch.float64, device="cuda")
-    emix_dev = torch.empty(1, dtype=torch.float64, device="cuda")
-
-    def step():
-        mix.propagate_dev(None, 1)
-        mix.local_energy_dev(e_dev.data_ptr(), emix_dev.data_ptr())
-
-    for _ in range(max(warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    mix.profile_enable(True)
-    n0 = mix.launch_count()
-    ev0.record(stream)
-    for _ in range(steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    prof = mix.profile_read()
-    mix.profile_enable(False)
-    ms = ev0.elapsed_time(ev1) / steps
-    algo = mix.exchange_algorithm()
-    digits, xest = mix.prop_digits()
-    ex_ms, ex_n = prof["exchange"]
-    ex_avg = ex_ms / max(ex_n, 1) / 1e3
-    if algo == "stored":
-        useful = 2 * stored_tc_macs(W, M, na, nb)
-        kname = "exchange (k_tc_split<ExVP>: stored V' x theta, exact digits)"
-        note = (f"{SPLIT_PRODUCTS} digit products x 2 x the multiply-adds of the upper block "
-                "triangle of V' against theta (padding of M to 32 counted)")
-    else:
-        useful = exchange_flops(W, X, M, na, nb)
-        kname = "exchange (k_exchange_tc, persistent, direct)"
-        note = (f"{SPLIT_PRODUCTS} bf16 slice products x the exchange's algorithmic flops "
-                "(no padding counted)")
-    bf16_flops = SPLIT_PRODUCTS * useful
-    peak = measured_peaks().get("bf16_tflops", 1800.0)
-    achieved = bf16_flops / ex_avg / 1e12
-    out = {"workload": name, "M": M, "na": na, "nb": nb, "X": X, "W": W,
-           "value": W / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-           "precision": ("split_bf16: force bias 3 exact 8-bit digits per operand (6 products, "
-                         "exact integer sums in TMEM); exchange " +
-                         ("stored V' and theta as 3 exact digits (6 products)" if algo == "stored"
-                          else "direct, 3 bf16 float slices (6 products, FP32 accumulation)") +
-                         "; VHS 4 exact digits; propagator 4 exact digits for the P passes "
-                         "and the leading powers, fewer for the small high powers "
-                         "(prop_digits); theta double-float; overlaps, inverses, QR and "
-                         "weights FP64"),
-           "exchange_algorithm": algo,
-           "prop_digits": {"per_pass": digits, "sqrt_dt_V2_estimate": xest,
-                           "passes": "first P, Taylor powers 1..n, last P"},
-           "dE_L_max_1_step": errs[1] and errs[1]["E_L"],
-           f"dE_L_max_{long_steps}_steps": errs[long_steps] and errs[long_steps]["E_L"],
-           "errors": {"after_1_step": errs[1], f"after_{long_steps}_steps": errs[long_steps],
-                      "units": "E1, EJ, EK, E_L: max |d| in Ha; *_rel: max relative error "
-                               "(weights, overlaps per walker; walkers Frobenius per walker; "
-                               "gradients max |d| / max |ref|, FP64 adjoint at the "
-                               "split-propagated walkers, cotangent seeded)"},
-           "dE_reference": f"FP64 path (parity-checked against the FP64 oracle at 1e-10) on the "
-                           f"first {check_walkers} walkers, same Philox fields",
-           "gpu_launches": mix.launch_count() - n0,
-           "kernels": {k: {"ms_per_step": v[0] / steps, "launches": v[1]}
-                       for k, v in prof.items() if v[1]},
-           "roofline": {"bound": "tensor", "kernel": kname,
-                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak,
-                        "traffic": (TRAFFIC.get(("split_bf16", name, "exchange_" + algo))
-                                    if W == c["W"] else None),
-                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
-                        "flops_per_launch": bf16_flops, "flops_note": note,
-                        "avg_launch_ms": ex_avg * 1e3}}
-    # the propagation (the split step's largest part): every digit product of the 8 GEMM
-    # passes at its algorithmic flops, over the propagation's event time (which also
-    # holds the digit slicing between the passes)
-    pr_ms, _ = prof["propagate"]
-    pr_s = pr_ms / steps / 1e3
-    N = na + nb
-    prods = [d * (d + 1) // 2 for d in digits]
-    pr_flops = W * M * M * N * (4 * (prods[0] + prods[-1]) + 8 * sum(prods[1:-1]))
-    pr_achieved = pr_flops / pr_s / 1e12
-    out["propagation_roofline"] = {
-        "bound": "tensor", "kernel": "propagation (k_prop_tc, 8 passes per step, with the "
-                                     "digit slicing between them)",
-        "achieved": pr_achieved, "peak": peak, "unit": "TFLOP/s", "frac": pr_achieved / peak,
-        "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, measured)",
-        "flops_per_step": pr_flops,
-        "flops_note": "digit products of each pass (d (d + 1) / 2 for d digits) x 8 M^2 N "
-                      "(complex Taylor powers) or 4 M^2 N (real P passes), no padding",
-        "ms_per_step": pr_s * 1e3}
-    mix.close()
-    if fp64_compare:
-        f_ms = fp64_step_ms(s, W, rank)
-        out["fp64_ms_per_step"] = f_ms
-        out["fp64_value"] = W / (f_ms / 1e3)
-        out["speedup_vs_fp64"] = f_ms / ms
-    return out
-
-
-def batched_leg(rank: int, replays: int = 8, precision: str = "split_bf16") -> dict:
+def batched_leg(rank: int, precision: str, replays: int) -> dict:
     """The eight uneven systems (48..220 orbitals, 0.2 M electrons per spin, X = 5 M,
     512..32 walkers) autotuned and stepped by one CUDA graph (one branch per system,
     5 steps + local energies per replay), against eager stepping of the same contexts."""
@@ -524,9 +653,9 @@ def batched_leg(rank: int, replays: int = 8, precision: str = "split_bf16") -> d
     for c in ctxs:
         c.close()
     return {"workload": "8 uneven systems: orbitals 48..220, 0.2 M electrons per spin, "
-                        "X = 5 M, walkers 512..32, split_bf16",
-            "walkers_total": walkers, "value": walkers / graph_s, "unit": UNIT,
-            "ms_per_step": graph_s * 1e3, "eager_value": walkers / eager_s,
+                        f"X = 5 M, walkers 512..32, {precision}",
+            "precision": precision, "walkers_total": walkers, "value": walkers / graph_s,
+            "unit": UNIT, "ms_per_step": graph_s * 1e3, "eager_value": walkers / eager_s,
             "eager_ms_per_step": eager_s * 1e3, "graph_speedup": eager_s / graph_s,
             "replays": replays, "steps_per_replay": 5,
             "timing": "host wall clock around synchronised replays (graph) or eager steps",
@@ -582,6 +711,8 @@ def adjoint_leg(rank: int, K: int = 20) -> dict:
 # ----------------------------------------------------------------------------- arms
 
 def run_reference(args):
+    """The oracle (the reference arm of this build: the paper has no code) on the
+    headline workload: each step a bounded sample of 2 of its walkers."""
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
@@ -589,7 +720,7 @@ def run_reference(args):
     from oracle.philox import gaussian_fields
     from paper_2209_04015_b300.synthetic import make_config, trial_walkers
     s, c = make_config(WORKLOAD)
-    Ws = 4
+    Ws = 2
     orc = Oracle(s.h1, s.L, s.e0, s.psi_a, s.psi_b, dt=0.005, qr_period=5)
     orc.init_walkers(trial_walkers(s, Ws))
 
@@ -606,18 +737,16 @@ def run_reference(args):
         one(args.warmup + k)
     dt = time.perf_counter() - t0
     value = Ws * args.steps / dt
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([p.get("num_threads", 1) for p in threadpool_info()] + [1])
-    except Exception:
-        cores = os.cpu_count() or 1
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT, "name": WORKLOAD, "sample_walkers": Ws},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{Ws} of {c['W']} walkers per step"},
+            "config": {"workload": WORKLOAD_TEXT[WORKLOAD], "name": WORKLOAD,
+                       "sample_walkers": Ws},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(),
+                             "kind": "oracle",
+                             "sample": f"{Ws} of {c['W']} walkers per step (walker-steps/s "
+                                       "carries over: walkers are independent)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -628,11 +757,12 @@ def run_leg(args) -> int:
     import torch
     torch.cuda.set_device(0)
     leg = args.profile_leg
-    if leg.startswith("mixed"):
-        out = mixed_leg(leg.split("-")[1], args.mixed_steps, args.warmup, 0,
-                        long_steps=args.error_steps, walkers=args.profile_walkers)
-    elif leg == "batched":
-        out = batched_leg(0)
+    if leg.startswith(("fp64", "split")):
+        prec, name = leg.split("-")
+        out = step_leg(name, "fp64" if prec == "fp64" else "split_bf16", args.steps,
+                       args.warmup, 0, 1, 0, walkers=args.profile_walkers)
+    elif leg.startswith("batched"):
+        out = batched_leg(0, "fp64" if leg.endswith("fp64") else "split_bf16", 2)
     elif leg == "blocks":
         out = {"fp64_c2": block_leg("c2", "fp64", 0),
                "workflow_split_c2": workflow_leg("c2", "split_bf16", 0)}
@@ -649,135 +779,68 @@ def run_afq(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    from paper_2209_04015_b300 import AfqContext
-    from paper_2209_04015_b300.synthetic import make_config
-
-    s, c = make_config(WORKLOAD, seed=1 + rank)
-    W, X, M, na, nb = c["W"], s.X, s.M, s.na, s.nb
-    stream = torch.cuda.current_stream()
-    ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, stream=stream.cuda_stream)
-    ctx.init_hamiltonian(s.h1, s.L, s.e0)
-    ctx.init_trial(s.psi_a, s.psi_b)
-    ctx.init_walkers(W)
-    ctx.autotune()  # launch shapes (set-up, outside the timed region); walkers restored
-    e_dev = torch.empty((W, 4, 2), dtype=torch.float64, device="cuda")
-    emix_dev = torch.empty(1, dtype=torch.float64, device="cuda")
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-
-    def step():
-        ctx.propagate_dev(None, 1)
-        ctx.local_energy_dev(e_dev.data_ptr(), emix_dev.data_ptr())
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = ClockSampler(local)
-    time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    ctx.profile_enable(True)
-    n0 = ctx.launch_count()
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()                      # write 256 MB: evicts L2 between timed steps
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    launches = ctx.launch_count() - n0
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    value, total_ms = job_throughput(float(sum(step_ms)), W * args.steps, world, device="cuda")
-
-    # end to end through the public host-buffer API: the step's fields go host -> device
-    # from pinned memory, the energies come back to the host, every step
-    K2 = max(10, min(args.steps, 50))
-    host_fields = torch.empty((K2, W, X), dtype=torch.float64).pin_memory()
-    host_fields.copy_(torch.from_numpy(np.random.default_rng(5 + rank).standard_normal((K2, W, X))))
-    hf = host_fields.numpy()
-    # a fresh context of the same configuration: the synthetic trial lies ~300 Ha above
-    # the projected energy, so with E_shift = E_HF the timed context's weights grow
-    # ~e^1.6 per step and overflow after ~440 steps (harmless to the timed kernels,
-    # which do not read them, but reported by the checked host-buffer calls)
-    ectx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, stream=stream.cuda_stream)
-    ectx.init_hamiltonian(s.h1, s.L, s.e0)
-    ectx.init_trial(s.psi_a, s.psi_b)
-    ectx.init_walkers(W)
-    ectx.autotune()
-    ectx.propagate(hf[0], 1)
-    ectx.local_energy()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(K2):
-        ectx.propagate(hf[k], 1)
-        ectx.local_energy()
-    e2e_s = time.perf_counter() - t0
-    ectx.close()
-    e2e = {"value": W * K2 / e2e_s * world, "unit": UNIT, "h2d_bytes_per_step": W * X * 8,
-           "d2h_bytes_per_step": W * 4 * 16 + 8, "steps": K2}
-
+    peaks = measured_peaks()
+    fp64 = fp64_peak()
+    e2e_steps = max(10, min(args.steps, 50))
+    head = step_leg(WORKLOAD, "fp64", args.steps, args.warmup, rank, world, local,
+                    e2e_steps=e2e_steps, clocks=True)
+    attach_peak(head["roofline"], peaks, fp64)
     if rank != 0:
         if world > 1:
             torch.distributed.barrier()
             torch.distributed.destroy_process_group()
         return 0
 
-    ex_algo = ctx.exchange_algorithm()
-    tiles = ctx.get_tiles()
-    flops = step_flops(W, X, M, na, nb, exchange=ex_algo)
-    # the dominant FP64 kernel by device time
-    dom = max(FP64_KERNELS, key=lambda k: prof[k][0])
-    dom_ms, dom_n = prof[dom]
-    dom_avg_s = dom_ms / max(dom_n, 1) / 1e3
-    dom_achieved = flops[dom] / dom_avg_s / 1e12
-    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1],
-                   "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)}
-               for k, v in prof.items() if v[1]}
-    total_flops = sum(flops.values())
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT, "name": WORKLOAD, "M": M, "na": na, "nb": nb,
-                   "X": X, "W_per_gpu": W, "dt": 0.005, "qr_period": 5, "precision": "fp64",
-                   "parallelism": f"replicas x{world}",
-                   "l2": "flushed between timed steps (256 MB write, outside the step events)"},
-        "roofline": {"bound": "alu", "kernel": f"{dom} ({FP64_KERNELS[dom]})",
-                     "achieved": dom_achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": dom_achieved / FP64_NOMINAL_TFLOPS,
-                     "traffic": (TRAFFIC.get(("fp64", WORKLOAD, dom))
-                                 if W == 128 and (dom != "propagate" or tiles[1] == 2) else None),
-                     "peak_source": "FP64 nominal (148 SMs x 2032 MHz x 4.15 flop/clk/SM)",
-                     "flops_per_launch": flops[dom], "avg_launch_ms": dom_avg_s * 1e3},
-        "exchange_algorithm": ex_algo,
-        "autotuned_tiles": tiles,
-        "step_flops": total_flops,
-        "step_tflops": total_flops / (total_ms / args.steps / 1e3) / 1e12,
-        "kernels": kernels,
-        "e2e": e2e,
-        "gpu_launches": launches,
-        "clocks": clk,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Hamiltonian and trial with the paper's 52e/290o shape)",
+        "config": {"workload": WORKLOAD_TEXT[WORKLOAD], "name": WORKLOAD, "M": head["M"],
+                   "na": head["na"], "nb": head["nb"], "X": head["X"], "W_per_gpu": head["W"],
+                   "dt": 0.005, "qr_period": 5, "precision": "fp64",
+                   "parallelism": f"replicas x{world}", "l2": head["l2"]},
+        "roofline": head["roofline"],
+        "e2e": head["e2e"],
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
+        "fp64_peak": fp64,
+        "exchange_algorithm": head["exchange_algorithm"],
+        "autotuned_tiles": head["autotuned_tiles"],
+        "step_flops": head["step_flops"],
+        "step_tflops": head["step_tflops"],
+        "kernels": head["kernels"],
     }
-    if not args.no_mixed:
-        line["mixed"] = {"same_workload": mixed_leg(WORKLOAD, args.mixed_steps * 5, args.warmup,
-                                                    rank, long_steps=args.error_steps),
-                         "large_shape": mixed_leg("c3", args.mixed_steps, args.warmup, rank,
-                                                  long_steps=args.error_steps,
-                                                  fp64_compare=True)}
-        line["mixed"]["same_workload"]["speedup_vs_fp64"] = (
-            line["mixed"]["same_workload"]["value"] / (value / world))
-        line["batched"] = batched_leg(rank)
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(WORKLOAD, args.cpu_seconds, 2)
+    if not args.no_extra:
+        split = step_leg(WORKLOAD, "split_bf16", args.split_steps, args.warmup, rank, 1, local,
+                         e2e_steps=e2e_steps)
+        attach_peak(split["roofline"], peaks, fp64)
+        split["speedup_vs_fp64"] = split["value"] / head["value"] * world
+        split["errors"] = mixed_errors(WORKLOAD, rank, args.error_steps)
+        if "cpu_baseline" in line:
+            split["cpu_baseline"] = dict(line["cpu_baseline"],
+                                         note="the FP64 oracle (the split path's reference)")
+        line["split_bf16"] = split
+        c2 = {}
+        for prec in ("fp64", "split_bf16"):
+            leg = step_leg("c2", prec, 5 * args.steps, args.warmup, rank, 1, local,
+                           e2e_steps=e2e_steps)
+            attach_peak(leg["roofline"], peaks, fp64)
+            c2[prec] = leg
+        c2["split_bf16"]["speedup_vs_fp64"] = c2["split_bf16"]["value"] / c2["fp64"]["value"]
+        c2["split_bf16"]["errors"] = mixed_errors("c2", rank, args.error_steps)
+        if world == 1 and not args.no_cpu_baseline:
+            c2["cpu_baseline"] = cpu_baseline("c2", args.cpu_seconds / 2, 8)
+        line["c2"] = c2
+        line["batched"] = {"fp64": batched_leg(rank, "fp64", 2),
+                           "split_bf16": batched_leg(rank, "split_bf16", 8)}
         line["paper_block"] = {"fp64_c2": block_leg("c2", "fp64", rank),
                                "split_c3": block_leg("c3", "split_bf16", rank),
                                "workflow_split_c2": workflow_leg("c2", "split_bf16", rank)}
-    if not args.no_adjoint:
-        line["adjoint"] = adjoint_leg(rank)
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if not args.no_adjoint:
+            line["adjoint"] = adjoint_leg(rank)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

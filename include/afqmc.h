@@ -84,11 +84,12 @@ typedef struct afq_params {
   double fb_cap;       /* |xbar_g| cap; 0 = off                                  */
   int free_projection; /* 1: complex weights w <- w I (no phaseless cut)         */
   int split_slices;    /* AFQ_SPLIT_BF16: digits S per FP64 operand of the force bias
-                          and the exchange, 1..4; 0 = 3.  Force bias and stored
+                          and the exchange, 1..4; 0 = 4.  Force bias and stored
                           exchange: exact 8-bit digits, the products of digit
                           orders s + t <= S - 1 each in its own exact TMEM
-                          accumulator; direct exchange: bf16 float slices with
-                          FP32 accumulation                                      */
+                          accumulator; direct exchange: the same digits stored at
+                          their weights, the leading product in an exact TMEM
+                          accumulator and the smaller ones in a second (FP32)   */
   int prop_slices;     /* AFQ_SPLIT_BF16: exact 8-bit digits per FP64 operand of the
                           VHS and propagator GEMMs, 1..4 (per-row power-of-two scale,
                           one exact TMEM accumulator per digit order); 0 = 4     */
@@ -96,8 +97,8 @@ typedef struct afq_params {
 } afq_params;
 
 /* Fill *p with the defaults: dt 0.005, Taylor order 6, QR every 5 steps, seed 1,
-   FP64, E_shift = trial energy, no cap, phaseless; in split mode 3 slices for the
-   force bias and exchange and 4 exact digits for the propagation; exchange AUTO. */
+   FP64, E_shift = trial energy, no cap, phaseless; in split mode 4 exact digits for
+   the force bias, the exchange and the propagation; exchange AUTO. */
 void afq_default_params(afq_params* p);
 
 /* Create a context bound to cuda_stream (a cudaStream_t, or NULL for the legacy
@@ -383,6 +384,14 @@ int afq_get_tiles(afq_ctx* ctx, int* tiles, int n);
 #define AFQ_STATIC_EXCHANGE_SLOTS 262144
 int afq_exchange_energy_static(int M, int X, int na, int nb, int W, const double* Lt_dev,
                                const double* thetaT_dev, double* ek_dev, void* cuda_stream);
+
+/* Measured FP64 fused multiply-add throughput of the current device in TFLOP/s (2
+   flops per FMA): 8 CTAs of 256 threads per SM, 8 independent FMA chains per thread,
+   CUDA-event timed on cuda_stream, best of three launches after a warm-up (about
+   0.15 s).  A measurement helper with no counterpart in the paper: the denominator of
+   the FP64 kernels' roofline.  Returns AFQ_OK, AFQ_ERR_ARG (NULL output) or
+   AFQ_ERR_CUDA. */
+int afq_fp64_fma_rate(double* tflops, void* cuda_stream);
 
 /* Split-precision real GEMM on the tensor cores: C = A B^T with A m x k, B n x k and
    C m x n, all row-major FP64 DEVICE arrays, read and written on cuda_stream.  Each

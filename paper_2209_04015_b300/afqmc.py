@@ -95,6 +95,7 @@ _SIGS = {
     "afq_get_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "afq_gemm_split_bf16": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             _P, _P, _P, _P]),
+    "afq_fp64_fma_rate": (ctypes.c_int, [_D, _P]),
     "afq_exchange_energy_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
 }
@@ -128,6 +129,16 @@ def exchange_energy_static(M: int, X: int, na: int, nb: int, W: int, Lt_ptr: int
         raise AfqError(rc, "afq_exchange_energy_static failed (details on stderr)")
 
 
+def fp64_fma_rate(stream_ptr: int | None = None) -> float:
+    """afq_fp64_fma_rate: measured FP64 FMA throughput of the current device, TFLOP/s."""
+    lib = load_library()
+    out = ctypes.c_double()
+    rc = lib.afq_fp64_fma_rate(ctypes.byref(out), _P(stream_ptr) if stream_ptr else None)
+    if rc != AFQ_OK:
+        raise AfqError(rc, "afq_fp64_fma_rate failed")
+    return out.value
+
+
 def gemm_split_bf16(m: int, n: int, k: int, slices: int, A_ptr: int, B_ptr: int, C_ptr: int,
                     stream: int | None = None) -> None:
     """afq_gemm_split_bf16 on device pointers: C = A B^T in split-bf16 on the tensor cores."""
@@ -151,7 +162,7 @@ class AfqContext:
     def __init__(self, dt: float = 0.005, taylor_order: int = 6, qr_period: int = 5,
                  seed: int = 1, precision: str = "fp64", e_shift: float | None = None,
                  fb_cap: float = 0.0, free_projection: bool = False, stream: int | None = None,
-                 split_slices: int = 3, prop_slices: int = 4, exchange: str = "auto"):
+                 split_slices: int = 4, prop_slices: int = 4, exchange: str = "auto"):
         self.lib = load_library()
         p = AfqParams()
         self.lib.afq_default_params(ctypes.byref(p))

@@ -254,7 +254,7 @@ void afq_default_params(afq_params* p) {
   p->e_shift = 0.0;
   p->fb_cap = 0.0;
   p->free_projection = 0;
-  p->split_slices = 3;
+  p->split_slices = 4;
   p->prop_slices = 4;
   p->exchange = AFQ_EXCHANGE_AUTO;
 }
@@ -269,7 +269,7 @@ int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
   } else {
     afq_default_params(&ctx->p);
   }
-  if (ctx->p.split_slices == 0) ctx->p.split_slices = 3;
+  if (ctx->p.split_slices == 0) ctx->p.split_slices = 4;
   if (ctx->p.prop_slices == 0) ctx->p.prop_slices = 4;
   if (!(ctx->p.dt > 0.0) || ctx->p.taylor_order < 1 || ctx->p.taylor_order > 32 ||
       ctx->p.qr_period < 0 ||

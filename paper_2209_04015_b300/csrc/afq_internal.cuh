@@ -147,11 +147,11 @@ struct afq_ctx {
 
   // split-precision (AFQ_SPLIT_BF16) state
   bool mixed = false;
-  int S = 3;                          // bf16 slices per operand (force bias, exchange)
+  int S = 4;                          // exact digits per operand (force bias, exchange)
   int Sp = 4;                         // exact digits per operand (propagation)
   int Mpad = 0;                       // M rounded up to the 32-wide K block
-  __nv_bfloat16* Lt_sl = nullptr;     // S x X x N x Mpad float slices of L~ (direct exchange)
-  __nv_bfloat16* th_sl = nullptr;     // S x W x 2 x N x Mpad float slices of theta (direct exchange)
+  __nv_bfloat16* Lt_sl = nullptr;     // S x X x N x Mpad scaled digits of L~ (direct exchange)
+  __nv_bfloat16* th_sl = nullptr;     // S x W x 2 x N x Mpad scaled digits of theta (direct exchange)
   __nv_bfloat16* Lt_ex = nullptr;     // S x X x N x Mpad integer digits of L~ (force bias)
   int* e_fb = nullptr;                // X row exponents of Lt_ex
   double* fb_part = nullptr;          // ksplit x 2W x X force-bias partial sums (exact, FP64)
@@ -166,7 +166,8 @@ struct afq_ctx {
   int prop_digits[40] = {};
   double prop_x = 0.0;
   __nv_bfloat16* LT_sl = nullptr;     // S x M^2 x Xpad: L^T, the VHS operand
-  __nv_bfloat16* Pm_sl = nullptr;     // S x M x Mpad: P - I
+  __nv_bfloat16* Pm_sl = nullptr;     // S x M x Mpad: the off-diagonal part of P
+  double* pdiag = nullptr;            // M: the diagonal of P, applied in FP64
   __nv_bfloat16* y_sl = nullptr;      // S x 2W x Xpad: shifted fields (re, im rows)
   __nv_bfloat16* A_sl = nullptr;      // S x 2W x M x Mpad: i sqrt(dt) V (re, im planes)
   __nv_bfloat16* T_sl[2] = {nullptr, nullptr};  // S x 2W x N x Mpad: Taylor operands [Re; Im]

@@ -3,22 +3,27 @@
 // persistent tcgen05 kernel.
 //
 // The GEMM: A rows (g, i) are G Cholesky indices x n orbitals of L~ (K = Mpad), B rows
-// (z, re/im, j) are zb walkers of theta; one 128 x BN accumulator holds T^{gz} for every
-// (g, z) pair of a tile, and T is never written to HBM.  Each CTA stays resident and
+// (z, re/im, j) are zb walkers of theta; a 128 x BN accumulator pair holds T^{gz} for
+// every (g, z) pair of a tile, and T is never written to HBM.  Both operands are cut
+// into S scaled digits (split_scaled: per-row power-of-two scales, each digit stored at
+// its true weight): the leading product (0, 0) accumulates exactly (integer multiples
+// of one power of two) in a head accumulator and the smaller products in a tail
+// accumulator, so the tensor core's biased FP32 accumulation only touches the tail,
+// ~2^-8 of T.  Each CTA stays resident and
 // walks the tiles in chunks of walker blocks whose theta stays in L2, g-tile major
 // inside a chunk (so resident CTAs share each L~ g-tile):
 //   warp 0   TMA producer: the S slices of the A and B units of every K block into a
 //            ring of stages;
-//   warp 1   MMA issuer: the float-split slice products into one of two TMEM
-//            accumulators, then a commit to the epilogue;
+//   warp 1   MMA issuer: the digit products into one of two head / tail TMEM
+//            accumulator pairs, then a commit to the epilogue;
 //   warps 2-5 epilogue: a few walkers of the tile at a time, their 2n columns are
-//            copied from TMEM (each warp its 32 lanes) to shared memory, and each warp
+//            copied from TMEM (head + tail, each warp its 32 lanes) to shared memory, and each warp
 //            reduces sum_ij T_ij T_ji of its g-blocks (lanes over (g-block, row i);
 //            conflict-free rows and columns; FP32 within the warp, FP64 across warps
 //            and tiles).
 // With equal spins both spins' tiles run in one launch (the same maps, another
 // orbital offset).
-// With two accumulators the epilogue of one tile runs under the MMAs of the next.
+// With two accumulator pairs the epilogue of one tile runs under the MMAs of the next.
 // Every mbarrier wait is bounded (time, or the grid-wide error flag), as in the
 // generic engine.
 #include "tc_engine.cuh"
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(kExThreads, 1)
           break;
         }
         tc::fence_after_sync();
-        const uint32_t acc = tmem + (uint32_t)(buf * a.bstride);
+        const uint32_t acc = tmem + (uint32_t)(buf * 2 * a.bstride);
         for (int kb = 0; kb < a.nkb; ++kb, ++it) {
           const int st = it % nst;
           if (!tc::mbar_wait(&full[st], (it / nst) & 1, err)) {
@@ -160,7 +165,7 @@ __global__ void __launch_bounds__(kExThreads, 1)
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
           const uint32_t sb = sa + S * kASlot;
-          issue_pairs<S>(acc, sa, sb, bslot, 0, 0, idesc, kb == 0);
+          issue_head_tail<S>(acc, acc + (uint32_t)a.bstride, sa, sb, bslot, idesc, kb == 0);
           tc::mma_commit(&empty[st]);
         }
         if (ok) tc::mma_commit(&tfull[buf]);
@@ -189,13 +194,19 @@ __global__ void __launch_bounds__(kExThreads, 1)
       const int g0 = gt * a.G, z0 = zt * a.zb;
       const int gc = min(a.G, a.X - g0);
       const int nblk = gc > q ? (gc - q + kEpiWarps - 1) / kEpiWarps : 0;  // this warp's g-blocks
-      const uint32_t acc = tmem + (uint32_t)(buf * a.bstride) + ((uint32_t)(32 * lq) << 16);
+      const uint32_t acc = tmem + (uint32_t)(buf * 2 * a.bstride) + ((uint32_t)(32 * lq) << 16);
       for (int zr = 0; zr < a.zb; zr += a.zc) {
         // stage walkers zr .. zr + zc - 1: their columns c_lo .. c_hi - 1, row by lane
         const int c_lo = zr * w2n, c_hi = min(a.zb, zr + a.zc) * w2n;
         for (int c0 = c_lo & ~15; c0 < c_hi; c0 += 16) {
           float v[16];
           tc::tmem_ld16(acc + (uint32_t)c0, v);
+          if (S > 1) {
+            float t[16];
+            tc::tmem_ld16(acc + (uint32_t)(a.bstride + c0), t);
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) v[jj] += t[jj];
+          }
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int c = c0 + jj;
@@ -321,9 +332,9 @@ int launch_exchange_tc(afq_ctx* ctx, WalkerSet& s) {
     if (a.zc > a.zb) a.zc = a.zb;
     a.pitch = a.zc * 2 * n + 1;
     a.tx_bytes = (uint32_t)ctx->S * (kBK * n * a.G * 2 + kBK * n * 2 * a.zb * 2);
-    a.tmem_cols = tmem_cols_for(2 * a.bstride);
+    a.tmem_cols = tmem_cols_for(4 * a.bstride);
     if (a.ngt > ctx->ex_groups) return afq_fail(ctx, AFQ_ERR_STATE, "exchange tiles exceed slots");
-    if (2 * a.bstride > 512) return afq_fail(ctx, AFQ_ERR_ARG, "exchange tile too wide");
+    if (4 * a.bstride > 512) return afq_fail(ctx, AFQ_ERR_ARG, "exchange tile too wide");
     const size_t stage = (size_t)ctx->S * (kASlot + (size_t)a.BN * 64);
     const size_t fixed = (size_t)128 * a.pitch * 4 + (size_t)a.zb * kEpiWarps * 16 + 1024;
     int nst = (int)((kSmemLimit - 2048 - fixed) / stage);

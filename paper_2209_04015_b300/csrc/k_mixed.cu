@@ -138,27 +138,36 @@ __global__ void k_slice_real(const double* __restrict__ in, long ld, long rows, 
   }
 }
 
-// thetaT W x N x M complex -> S planes of [z][re/im][j][Mpad]
-__global__ void k_slice_theta(const double2* __restrict__ thetaT, int W, int N, int M, int Mpad,
-                              int S, __nv_bfloat16* __restrict__ out) {
-  const long total = (long)W * N * Mpad, plane = 2 * total;
+// Rows of K doubles (row pitch ld) -> S planes of scaled digits (split_scaled) of
+// rows x Kp, zero for k >= K, with one exponent per row (one warp per row)
+__global__ void k_slice_rows_scaled(const double* __restrict__ in, long ld, long rows, int K,
+                                    int Kp, int S, __nv_bfloat16* __restrict__ out) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const long plane = rows * Kp;
+  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
+       r += (long)gridDim.x * warps) {
+    const double* row = in + r * ld;
+    int m = 0;
+    for (int k = lane; k < K; k += 32) m = max(m, exp_field(row[k]));
+    const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
+    for (int k = lane; k < Kp; k += 32) split_scaled(k < K ? row[k] : 0.0, e, S, out + r * Kp + k, plane);
+  }
+}
+
+// thetaT W x N x M complex -> S planes of scaled digits [z][re/im][j][Mpad], with the
+// exponents eb of the exact digits (one per walker and re/im)
+__global__ void k_slice_theta_scaled(const double2* __restrict__ thetaT, int W, int N, int M,
+                                     int Mpad, int S, const int* __restrict__ eb,
+                                     __nv_bfloat16* __restrict__ out) {
+  const long NMp = (long)N * Mpad, total = (long)W * NMp, plane = 2 * total;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
-    const int p = (int)(e % Mpad);
-    const long zj = e / Mpad;
-    const int j = (int)(zj % N);
-    const long z = zj / N;
-    const double2 v = p < M ? thetaT[zj * M + p] : make_double2(0.0, 0.0);
-    const long base = ((z * 2) * N + j) * Mpad + p;
-    if (S <= 3) {
-      // three bf16 slices hold 24 bits: split the FP32 rounding of theta on the FP32
-      // pipe (the FP64 remainders would run on B300's slow FP64 pipe)
-      split_bf16_f32(__double2float_rn(v.x), S, out + base, plane);
-      split_bf16_f32(__double2float_rn(v.y), S, out + base + (long)N * Mpad, plane);
-    } else {
-      split_bf16(v.x, S, out + base, plane);
-      split_bf16(v.y, S, out + base + (long)N * Mpad, plane);
-    }
+    const long z = e / NMp, r = e % NMp;
+    const int j = (int)(r / Mpad), p = (int)(r % Mpad);
+    const double2 v = p < M ? thetaT[(z * N + j) * M + p] : make_double2(0.0, 0.0);
+    __nv_bfloat16* o = out + (2 * z) * NMp + r;
+    split_scaled(v.x, eb[2 * z], S, o, plane);
+    split_scaled(v.y, eb[2 * z + 1], S, o + NMp, plane);
   }
 }
 
@@ -265,12 +274,16 @@ bool set_exchange_zb(afq_ctx* ctx, int spin, int zb) {
   return make_tmap(&ctx->tm_ex_b[spin], ctx->th_sl, 4, db, bb);
 }
 
+// Tile of the direct exchange for n electrons: G Cholesky indices of n rows each (128
+// rows), zb walkers of 2n columns; the head and tail accumulators of two tiles in
+// flight take 4 BN-wide regions of the 512 TMEM columns, so BN <= 128.
 int mixed_exchange_tiles(int n, int* G, int* zb, int* BN) {
   if (n <= 0) return 0;
   *G = 128 / n;
-  *zb = 256 / (2 * n);
+  *zb = 128 / (2 * n);
+  if (*zb < 1) *zb = 1;
   *BN = round_up(2 * n * *zb, 16);
-  if (*BN > 256) {
+  while (*BN > 128 && *zb > 1) {
     *zb -= 1;
     *BN = round_up(2 * n * *zb, 16);
   }
@@ -298,8 +311,8 @@ void mixed_free(afq_ctx* ctx) {
 }
 
 // Slices L~ once per trial: integer digits with one exponent per g for the force bias,
-// and float slices for the direct exchange when it is the chosen exchange; S planes
-// of [g][j][Mpad] each.
+// and scaled digits with one exponent per row (g, j) for the direct exchange when it
+// is the chosen exchange; S planes of [g][j][Mpad] each.
 int mixed_init_trial(afq_ctx* ctx) {
   const int S = ctx->S, X = ctx->X, N = ctx->N, M = ctx->M;
   ctx->Mpad = round_up(M, kBK);
@@ -316,8 +329,8 @@ int mixed_init_trial(afq_ctx* ctx) {
   AFQ_LAUNCHED(ctx);
   if (!ctx->ex_stored) {
     AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->Lt_sl, plane * S * sizeof(__nv_bfloat16)));
-    k_slice_real<<<grid1d((long)plane), 256, 0, ctx->stream>>>(ctx->Lt, M, (long)X * N, M,
-                                                               ctx->Mpad, S, ctx->Lt_sl);
+    k_slice_rows_scaled<<<warp_grid_rows((long)X * N), 256, 0, ctx->stream>>>(
+        ctx->Lt, M, (long)X * N, M, ctx->Mpad, S, ctx->Lt_sl);
     AFQ_LAUNCHED(ctx);
   }
   return AFQ_OK;
@@ -335,7 +348,7 @@ int mixed_init_walkers(afq_ctx* ctx) {
   const int W2 = 2 * W;
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->exv_th, (size_t)S * W2 * N * Mp * sizeof(__nv_bfloat16)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->exv_eb, (size_t)W2 * sizeof(int)));
-  if (!ctx->Vsl)  // float slices of theta for the direct exchange
+  if (!ctx->Vsl)  // scaled digits of theta for the direct exchange
     AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_sl,
                              (size_t)S * W * 2 * N * Mp * sizeof(__nv_bfloat16)));
   // force bias: rows g (X), columns (z, re/im) (2W), K = N Mpad; S digit accumulators
@@ -433,7 +446,7 @@ int mixed_autotune(afq_ctx* ctx) {
 }
 
 // theta's integer digits (force bias, stored exchange) and, for the direct exchange,
-// its float slices
+// its scaled digits (the same exponents)
 int launch_slice_theta(afq_ctx* ctx, WalkerSet& s) {
   k_theta_exponents<<<s.W, 256, 0, ctx->stream>>>(s.thetaT, (long)ctx->N * ctx->M, ctx->exv_eb);
   AFQ_LAUNCHED(ctx);
@@ -442,8 +455,8 @@ int launch_slice_theta(afq_ctx* ctx, WalkerSet& s) {
   AFQ_LAUNCHED(ctx);
   if (ctx->th_sl) {
     const long total = (long)s.W * ctx->N * ctx->Mpad;
-    k_slice_theta<<<grid1d(total), 256, 0, ctx->stream>>>(s.thetaT, s.W, ctx->N, ctx->M,
-                                                          ctx->Mpad, ctx->S, ctx->th_sl);
+    k_slice_theta_scaled<<<grid1d(total), 256, 0, ctx->stream>>>(
+        s.thetaT, s.W, ctx->N, ctx->M, ctx->Mpad, ctx->S, ctx->exv_eb, ctx->th_sl);
     AFQ_LAUNCHED(ctx);
   }
   return AFQ_OK;

@@ -20,8 +20,10 @@
 // Taylor terms and one-body halves: per walker, 128-row tile of p and 64-column
 // tile of j, Re and Im accumulators of A T (A M x M, T M x N as K-major T^T rows
 // j), four MMA streams per slice pair with the negate-A bit for -Im A Im T.  The
-// identity parts stay in FP64: P Phi = Phi + (P - I) Phi, and each Taylor term is
-// added to an FP64 accumulator.
+// diagonal of P stays in FP64: P Phi = diag(P) Phi + O Phi with O the off-diagonal
+// part of P, so the digits of O carry its own row scale (the off-diagonal elements
+// are ~100x smaller than the diagonal ones, which would otherwise set the scale), and
+// each Taylor term is added to an FP64 accumulator.
 #include <cmath>
 #include <vector>
 
@@ -108,9 +110,10 @@ struct VhsP {
 //   D[:, re|im] += Re A B                   (N = 2 brows)
 //   D[:, re]    += -Im A (Im T rows of B)   (N = brows, negate-A)
 //   D[:, im]    +=  Im A (Re T rows of B)   (N = brows)
-// (real A = P - I: the first product only).  Exact digit diagonals accumulate in S
-// TMEM regions of BN columns; each epilogue thread recombines a real column and its
-// imaginary partner brows columns later and writes whole complex FP64 values.
+// (real A = O, the off-diagonal part of P: the first product only).  Exact digit
+// diagonals accumulate in S TMEM regions of BN columns; each epilogue thread
+// recombines a real column and its imaginary partner brows columns later and writes
+// whole complex FP64 values.
 // Roles: warp 0 TMA, warp 1 MMA (and TMEM), warps 2-9 epilogue (two per TMEM lane
 // quarter, splitting the column chunks); the producer runs ahead across tiles while
 // the epilogue drains TMEM.
@@ -123,7 +126,8 @@ struct PropArgs {
   int nbuf;               // TMEM accumulator sets (2 when 2 S BN <= 512: the epilogue of
                           // one tile overlaps the MMAs of the next)
   uint32_t tx_bytes, tmem_cols;
-  const int* ea;          // row exponents of A: P - I per p, or V_z per (z, p)
+  const int* ea;          // row exponents of A: O (P off the diagonal) per p, or V_z per (z, p)
+  const double* pdiag;    // M: diagonal of P (mode last adds diag(P) acc in FP64)
   const int* eb;          // row exponents of T^T per (z, j)
   double2* accT;          // W x N x M FP64 accumulator of P T_n(A) P Phi, transposed
   double2* phi_out;       // mode last: Phi (W x M x N)
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
           const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
           const long iphi = ((long)z * M + p) * N + j;  // [z][p][j]
           if (a.mode == kModeFirst) {
-            // (P - I) Phi; the slicing pass adds Phi (FP64) and cuts u_0 = P Phi
+            // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
             a.accT[ia] = make_double2(dr, di);
           } else if (a.mode == kModeTerm) {
             // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k to
@@ -313,7 +317,8 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
             a.tout[ia] = make_double2(dr, di);
           } else {
             const double2 acc = a.accT[ia];
-            a.phi_out[iphi] = make_double2(dr + acc.x, di + acc.y);
+            const double d = a.pdiag[p];
+            a.phi_out[iphi] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
           }
         }
       }
@@ -432,12 +437,14 @@ __global__ void __launch_bounds__(256) k_slice_cplx1(const double2* __restrict__
 // Taylor step of the split propagation, one pass over u_k (W x N x M, rows (z, j)):
 // acc += i^k g_k u_k (FP64), then the digits of u_k for the next term -- or, after
 // the last term (last != 0), the digits of the finished sum acc for the second
-// one-body half.  kmod = k mod 4 selects the rotation i^k.
+// one-body half.  kmod = k mod 4 selects the rotation i^k; kscale (M values, or NULL)
+// scales element p of every row first (the diagonal of P in the first call).
 template <int NP>
 __global__ void __launch_bounds__(256) k_taylor_slice(const double2* __restrict__ in,
                                                       double2* __restrict__ acc, long rows,
                                                       int R, int K, int Kp, int S, double gk,
                                                       int kmod, int last,
+                                                      const double* __restrict__ kscale,
                                                       __nv_bfloat16* __restrict__ out,
                                                       int* __restrict__ eout) {
   const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
@@ -461,6 +468,11 @@ __global__ void __launch_bounds__(256) k_taylor_slice(const double2* __restrict_
           if (kmod == 1) w = make_double2(-u.y, u.x);
           else if (kmod == 2) w = make_double2(-u.x, -u.y);
           else if (kmod == 3) w = make_double2(u.y, -u.x);
+          if (kscale) {
+            const double sc = kscale[k + h];
+            w.x *= sc;
+            w.y *= sc;
+          }
           double2 a = arow[k + h];
           a.x = fma(gk, w.x, a.x);
           a.y = fma(gk, w.y, a.y);
@@ -496,9 +508,10 @@ __global__ void __launch_bounds__(256) k_taylor_slice(const double2* __restrict_
   }
 }
 
-// acc += i^k g_k u_k elementwise (the long-row form of k_taylor_slice's update)
+// acc += i^k g_k u_k elementwise (the long-row form of k_taylor_slice's update; rows
+// of K elements, element p scaled by kscale[p] when kscale is not NULL)
 __global__ void k_taylor_acc(const double2* __restrict__ u, double2* __restrict__ acc, long n,
-                             double gk, int kmod) {
+                             int K, double gk, int kmod, const double* __restrict__ kscale) {
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n;
        e += (long)gridDim.x * blockDim.x) {
     const double2 x = u[e];
@@ -506,6 +519,11 @@ __global__ void k_taylor_acc(const double2* __restrict__ u, double2* __restrict_
     if (kmod == 1) w = make_double2(-x.y, x.x);
     else if (kmod == 2) w = make_double2(-x.x, -x.y);
     else if (kmod == 3) w = make_double2(x.y, -x.x);
+    if (kscale) {
+      const double sc = kscale[e % K];
+      w.x *= sc;
+      w.y *= sc;
+    }
     double2 a = acc[e];
     a.x = fma(gk, w.x, a.x);
     a.y = fma(gk, w.y, a.y);
@@ -582,17 +600,23 @@ __global__ void k_slice_LT(const double* __restrict__ L, int X, int M, long Mp, 
   }
 }
 
-// P - I -> rows p of K = M, padded to Mpad (one warp per row)
-__global__ void k_slice_pm(const double* __restrict__ P, int M, int Mpad, int S,
-                           __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
+// P -> its diagonal (FP64, pdiag) and the digits of its off-diagonal part O as rows p
+// of K = M, padded to Mpad, with O's own row exponents (one warp per row)
+__global__ void k_slice_poff(const double* __restrict__ P, int M, int Mpad, int S,
+                             __nv_bfloat16* __restrict__ out, int* __restrict__ eout,
+                             double* __restrict__ pdiag) {
   const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
   for (int p = blockIdx.x * warps + (threadIdx.x >> 5); p < M; p += gridDim.x * warps) {
     int m = 0;
-    for (int q = lane; q < M; q += 32) m = max(m, exp_field(P[(long)p * M + q] - (p == q ? 1.0 : 0.0)));
+    for (int q = lane; q < M; q += 32)
+      if (q != p) m = max(m, exp_field(P[(long)p * M + q]));
     const int e = row_exponent_field(warp_max_int(m));
-    if (lane == 0) eout[p] = e;
+    if (lane == 0) {
+      eout[p] = e;
+      pdiag[p] = P[(long)p * M + p];
+    }
     for (int q = lane; q < Mpad; q += 32) {
-      const double v = q < M ? P[(long)p * M + q] - (p == q ? 1.0 : 0.0) : 0.0;
+      const double v = (q < M && q != p) ? P[(long)p * M + q] : 0.0;
       split_exact(v, e, S, out + (long)p * Mpad + q, (long)M * Mpad);
     }
   }
@@ -621,11 +645,14 @@ void mixed_prop_free(afq_ctx* ctx) {
     }
   if (ctx->accT) cudaFree(ctx->accT);
   if (ctx->tout) cudaFree(ctx->tout);
+  if (ctx->pdiag) cudaFree(ctx->pdiag);
   ctx->accT = nullptr;
   ctx->tout = nullptr;
+  ctx->pdiag = nullptr;
 }
 
-// Once per trial: digits of L^T (the VHS operand) and of P - I, with row exponents.
+// Once per trial: digits of L^T (the VHS operand) and of the off-diagonal part of P,
+// with row exponents, and the diagonal of P.
 // Digits per pass.  A Taylor power u_k = V u_{k-1} enters the sum scaled by
 // g_k = dt^(k/2) / k!, so with x = sqrt(dt) |V|_2 the term is at most x^k / k! of Phi,
 // and cutting both its operands to S exact digits costs about 2^-(8S-1) of the term.
@@ -723,13 +750,15 @@ int mixed_prop_init_trial(afq_ctx* ctx) {
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->Pm_sl, (size_t)S * M * ctx->Mpad * 2));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_lt, (size_t)Mp * sizeof(int)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_pm, (size_t)M * sizeof(int)));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->pdiag, (size_t)M * sizeof(double)));
   k_lt_exponents<<<grid1d(Mp), 256, 0, ctx->stream>>>(ctx->L, X, M, Mp, ctx->tpq, ctx->e_lt);
   AFQ_LAUNCHED(ctx);
   dim3 g((unsigned)((Mp + 31) / 32), (unsigned)((ctx->Xpad + 31) / 32));
   k_slice_LT<<<g, dim3(32, 8), 0, ctx->stream>>>(ctx->L, X, M, Mp, ctx->Xpad, S, ctx->tpq,
                                                  ctx->e_lt, ctx->LT_sl);
   AFQ_LAUNCHED(ctx);
-  k_slice_pm<<<warp_grid(M), 256, 0, ctx->stream>>>(ctx->P, M, ctx->Mpad, S, ctx->Pm_sl, ctx->e_pm);
+  k_slice_poff<<<warp_grid(M), 256, 0, ctx->stream>>>(ctx->P, M, ctx->Mpad, S, ctx->Pm_sl,
+                                                      ctx->e_pm, ctx->pdiag);
   AFQ_LAUNCHED(ctx);
   return prop_digit_schedule(ctx);
 }
@@ -783,7 +812,7 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
     const uint32_t baz[4] = {kBK, 128, 1, 1};
     const uint64_t dt[4] = {(uint64_t)Mp, (uint64_t)N, (uint64_t)(2 * W), (uint64_t)S};
     const uint32_t bt[4] = {kBK, brows, 1, 1};
-    // the real P passes read A = P - I from L2 (one matrix for all walkers), so they
+    // the real P passes read A = O from L2 (one matrix for all walkers), so they
     // take half-width column tiles whose accumulators fit twice in TMEM (the epilogue
     // of one tile overlaps the MMAs of the next)
     ctx->prop_rows_real = ctx->prop_rows > 32 ? 32 : ctx->prop_rows;
@@ -873,6 +902,7 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   a.ea = ea;
   a.eb = ctx->e_t[b];
   a.accT = ctx->accT;
+  a.pdiag = ctx->pdiag;
   a.phi_out = ctx->ws.phi;
   a.tout = ctx->tout;
   a.err = ctx->flags + 2;
@@ -899,22 +929,23 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
 
 // acc += i^k g_k u_k and the digits of u_k (or of acc after the last term) into
 // operand buffer b; rows longer than 512 take the two-kernel form
-int taylor_slice(afq_ctx* ctx, int b, double gk, int kmod, int last, int S) {
+int taylor_slice(afq_ctx* ctx, int b, double gk, int kmod, int last, int S,
+                 const double* kscale = nullptr) {
   const int W = ctx->ws.W, N = ctx->N, M = ctx->M, Kp = ctx->Mpad;
   const long rows = (long)W * N;
   const int g = warp_grid(rows);
   if (Kp <= 128)
     k_taylor_slice<2><<<g, 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows, N, M, Kp, S, gk,
-                                                  kmod, last, ctx->T_sl[b], ctx->e_t[b]);
+                                                  kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
   else if (Kp <= 256)
     k_taylor_slice<4><<<g, 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows, N, M, Kp, S, gk,
-                                                  kmod, last, ctx->T_sl[b], ctx->e_t[b]);
+                                                  kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
   else if (Kp <= 512)
     k_taylor_slice<8><<<g, 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows, N, M, Kp, S, gk,
-                                                  kmod, last, ctx->T_sl[b], ctx->e_t[b]);
+                                                  kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
   else {
-    k_taylor_acc<<<grid1d(rows * M), 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows * M, gk,
-                                                            kmod);
+    k_taylor_acc<<<grid1d(rows * M), 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows * M, M,
+                                                            gk, kmod, kscale);
     AFQ_LAUNCHED(ctx);
     slice_rows(last ? ctx->accT : ctx->tout, rows, N, M, Kp, S, ctx->T_sl[b], ctx->e_t[b],
                ctx->stream);
@@ -946,12 +977,13 @@ int launch_propagate_tc(afq_ctx* ctx) {
   const int n = ctx->p.taylor_order;
   const int* dg = ctx->prop_digits;  // digits of each pass (prop_digit_schedule)
   if ((rc = slice_tout(ctx, cur, dg[0])) != AFQ_OK) return rc;
-  // u_0 = P Phi = Phi + (P - I) Phi, also the first term of the sum: the GEMM writes
-  // (P - I) Phi into the sum, the slicing pass adds Phi^T (in tout) and cuts u_0
+  // u_0 = P Phi = diag(P) Phi + O Phi, also the first term of the sum: the GEMM writes
+  // O Phi into the sum, the slicing pass adds diag(P) Phi^T (Phi^T in tout) and cuts u_0
   rc = launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeFirst, dg[0]);
   if (rc != AFQ_OK) return rc;
   cur = 1 - cur;
-  if ((rc = taylor_slice(ctx, cur, 1.0, 0, 1, dg[n >= 1 ? 1 : n + 1])) != AFQ_OK) return rc;
+  if ((rc = taylor_slice(ctx, cur, 1.0, 0, 1, dg[n >= 1 ? 1 : n + 1], ctx->pdiag)) != AFQ_OK)
+    return rc;
   double gk = 1.0;
   for (int k = 1; k <= n; ++k) {
     rc = launch_prop<false>(ctx, ctx->tm_az, cur, ctx->e_a, kModeTerm, dg[k]);
@@ -960,6 +992,6 @@ int launch_propagate_tc(afq_ctx* ctx) {
     gk *= sqrt(ctx->p.dt) / k;
     if ((rc = taylor_slice(ctx, cur, gk, k & 3, k == n, dg[k + 1])) != AFQ_OK) return rc;
   }
-  // Phi = P acc = acc + (P - I) acc
+  // Phi = P acc = diag(P) acc + O acc
   return launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeLast, dg[n + 1]);
 }

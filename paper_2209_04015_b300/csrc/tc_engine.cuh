@@ -81,6 +81,30 @@ __device__ __forceinline__ void issue_pairs(uint32_t acc, uint32_t sa, uint32_t 
   }
 }
 
+// Head-and-tail form for scaled digits (split_scaled): the leading pair (0, 0) goes to
+// accumulator acc_head (exact), every other pair with s + t <= S - 1 to acc_tail.
+template <int S>
+__device__ __forceinline__ void issue_head_tail(uint32_t acc_head, uint32_t acc_tail, uint32_t sa,
+                                                uint32_t sb, uint32_t bslot, uint32_t idesc,
+                                                bool first) {
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks)
+    tc::mma_bf16(acc_head, tc::sdesc_k64(a_unit(sa, S, 0, 0) + ks * 32),
+                 tc::sdesc_k64(b_unit(sb, bslot, S, 0, 0) + ks * 32), idesc, !(first && ks == 0));
+  bool lead = true;
+#pragma unroll
+  for (int d = 1; d < S; ++d)
+#pragma unroll
+    for (int s = 0; s <= d; ++s)
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        tc::mma_bf16(acc_tail, tc::sdesc_k64(a_unit(sa, S, 0, s) + ks * 32),
+                     tc::sdesc_k64(b_unit(sb, bslot, S, 0, d - s) + ks * 32), idesc,
+                     !(first && lead));
+        lead = false;
+      }
+}
+
 // Exact-diagonal form: pair (s, d - s) goes to accumulator d (acc0 + d * stride
 // columns).  With integer slices (split_exact) every accumulator holds a sum of
 // integer products, exact in FP32 while its magnitude stays below 2^24 (balanced
@@ -168,6 +192,21 @@ __device__ __forceinline__ void exact_digits(double x, int e, int S, int (&q)[kM
   }
 }
 
+// Scaled digits: the same digits as exact_digits, each written as its value
+// q_s 2^(e - 7 - 8 s) (exact in bfloat16: an 8-bit integer times a power of two), S
+// planes apart.  Products of scaled digits land at their true weights, so a GEMM over
+// them can keep the leading product (0, 0) -- a sum of integer multiples of one power
+// of two, exact in FP32 -- in one accumulator and every smaller product in another,
+// whose FP32 rounding then only touches digits ~2^-8 below the leading ones.
+__device__ __forceinline__ void split_scaled(double x, int e, int S, __nv_bfloat16* out,
+                                             long plane) {
+  int q[kMaxSlices];
+  exact_digits(x, e, S, q);
+#pragma unroll
+  for (int s = 0; s < kMaxSlices; ++s)
+    if (s < S) out[s * plane] = __float2bfloat16_rn(ldexpf((float)q[s], e - 7 - 8 * s));
+}
+
 // Recombines the S exact diagonal accumulators of one element:
 // value = 2^scale_exp sum_d acc_d 256^-d, through one int64 and one conversion.
 template <int S>
@@ -192,16 +231,6 @@ __device__ __forceinline__ void split_bf16(double x, int S, __nv_bfloat16* out, 
     const __nv_bfloat16 h = __double2bfloat16(r);
     out[s * plane] = h;
     r -= (double)__bfloat162float(h);
-  }
-}
-
-// The same for an FP32 value (exact remainders in FP32; S <= 3 covers its 24 bits).
-__device__ __forceinline__ void split_bf16_f32(float x, int S, __nv_bfloat16* out, long plane) {
-  float r = x;
-  for (int s = 0; s < S; ++s) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(r);
-    out[s * plane] = h;
-    r -= __bfloat162float(h);
   }
 }
 

@@ -2,9 +2,10 @@
 
 A replayed graph runs the same kernels in the same order as eager stepping, so its
 walkers, weights and energies must be bit-identical; a batch of uneven systems in
-one graph must reproduce each system stepped on its own; autotuned tiles change
-only the order of floating-point sums (results within 1e-12 relative in FP64, and
-the FP64 path still matches the oracle at 1e-10).
+one graph must reproduce each system stepped on its own, and in FP64 match the
+oracle at 1e-10; autotuned tiles change only the order of floating-point sums
+(results within 1e-12 relative in FP64, and the FP64 path still matches the oracle
+at 1e-10).
 """
 import numpy as np
 import pytest
@@ -100,6 +101,48 @@ def test_c4_batch_in_split_precision_matches_individual():
         assert np.all(np.isfinite(e))
         ref.close()
     b.close()
+
+
+def test_c4_batch_in_fp64_matches_oracle():
+    """The batched workload in FP64 (eight uneven systems: 48..220 orbitals, 0.2 M
+    electrons per spin, X = 5 M, 512..32 walkers) stepped by one graph for one QR
+    period with device Philox fields, against the oracle: two walkers of every system
+    re-run by the oracle alone with the same counter-based field stream drawn by its
+    own Philox (walkers are independent and the counters are keyed by walker index).
+    Walkers, overlaps, weights and every energy part within 1e-10 relative."""
+    from oracle.afqmc import Oracle
+    from paper_2209_04015_b300 import AfqBatch
+    systems = make_c4()
+    nsteps = 5
+    phis = [perturbed_walkers(s, W, eps=0.3, seed=30 + k) for k, (s, W) in enumerate(systems)]
+    bctx = [new_ctx(s, W, phis[k], seed=7 + k) for k, (s, W) in enumerate(systems)]
+    for c in bctx:
+        c.autotune()
+    b = AfqBatch(bctx)
+    b.capture(nsteps)
+    b.launch(1)
+    b.synchronize()
+    for k, (s, W) in enumerate(systems):
+        ctx = bctx[k]
+        idx = np.array([0, W - 1])
+        orc = Oracle(s.h1, s.L, s.e0, s.psi_a, s.psi_b, dt=0.005, qr_period=5)
+        orc.init_walkers(phis[k][idx])
+        orc.propagate([philox.gaussian_fields(t, W, s.X, 7 + k)[idx] for t in range(nsteps)])
+        e, emix = ctx.get_energy()
+        eref, _ = orc.local_energy()
+        phi = ctx.get_walkers()[idx]
+        dphi = (np.abs(phi - orc.phi).reshape(2, -1).max(axis=1) /
+                np.abs(orc.phi).reshape(2, -1).max(axis=1))
+        assert dphi.max() <= 1e-10, (k, dphi)
+        assert np.max(np.abs(ctx.get_overlaps()[idx] - orc.ovlp) / np.abs(orc.ovlp)) <= 1e-10
+        w = ctx.get_weights()[idx].real
+        assert np.all(np.abs(w - orc.w) <= 1e-10 * np.abs(orc.w)), (k, w, orc.w)
+        for part in range(4):
+            scale = np.maximum(np.abs(eref[:, part]), 1e-3 * np.abs(eref[:, 3]))
+            assert np.all(np.abs(e[idx, part] - eref[:, part]) <= 1e-10 * scale), (k, part)
+    b.close()
+    for c in bctx:
+        c.close()
 
 
 def test_autotune_fp64_keeps_parity():
