@@ -46,9 +46,11 @@ WORKLOAD_TEXT = {
            "(geometric norm decay), 640 complex128 walkers, dt 0.005, QR every 5 steps, "
            "Philox fields"),
 }
-# NVIDIA's rated FP64 throughput of B300 (context only; fractions use the FP64 rate
-# measured in the run)
+# NVIDIA's rated FP64 throughput of B300, and the FP64 ALU peak the FP64 kernels'
+# roofline uses: 148 SMs x 4 flops per clock per SM (two FP64 FMA lanes, the count the
+# rating implies: 1.25e12 / (148 x 2.032e9) = 4.16) x the 2032 MHz maximum SM clock
 FP64_VENDOR_TFLOPS = 1.25
+FP64_ALU_TFLOPS = 148 * 4 * 2.032e9 / 1e12
 # DRAM bytes (read + write) of the dominant kernel class from one-pass ncu captures of
 # these exact workloads: per launch for the FP64 kernels, per step (every launch of
 # the class) for the split propagation; absent where no capture of the current
@@ -185,10 +187,11 @@ def split_flops(W, X, M, na, nb, algo, S, digits):
 
 
 def fp64_peak() -> dict:
-    """FP64 throughput of this GPU, measured: the FMA-loop probe of the library
-    (afq_fp64_fma_rate: independent FMA chains filling every SM, CUDA events, best of
-    three), the roofline denominator of the FP64 kernels; cuBLAS DGEMM (torch.matmul on
-    float64, 4096^3, best of 5, CUDA events) beside it."""
+    """FP64 throughput of this GPU: the ALU peak from the unit count and the maximum SM
+    clock (the roofline denominator of the FP64 kernels), with two measurements beside
+    it: the FMA-loop probe of the library (afq_fp64_fma_rate: independent FMA chains
+    filling every SM, CUDA events, best of five) and cuBLAS DGEMM (torch.matmul on
+    float64, 4096^3, best of 5, CUDA events)."""
     import torch
     from paper_2209_04015_b300.afqmc import fp64_fma_rate
     fma = fp64_fma_rate(torch.cuda.current_stream().cuda_stream)
@@ -207,8 +210,11 @@ def fp64_peak() -> dict:
         best = min(best, e0.elapsed_time(e1))
     del a, b, c
     torch.cuda.empty_cache()
-    return {"tflops": fma, "how": "FMA-loop probe afq_fp64_fma_rate (8 CTAs x 256 threads per "
-            "SM, 8 independent chains per thread), best of 3, CUDA events",
+    return {"tflops": FP64_ALU_TFLOPS,
+            "how": "ALU peak: 148 SMs x 4 FP64 flops per clock (2 FMA lanes) x 2032 MHz",
+            "fma_probe_tflops": fma,
+            "fma_probe_how": "afq_fp64_fma_rate (8 CTAs x 256 threads per SM, 16 independent "
+                             "chains per thread), best of 5, CUDA events",
             "dgemm_tflops": 2 * n ** 3 / (best / 1e3) / 1e12,
             "dgemm_how": f"cuBLAS DGEMM {n}^3 (torch.matmul float64), best of 5, CUDA events",
             "vendor_tflops": FP64_VENDOR_TFLOPS}
@@ -457,10 +463,11 @@ def attach_peak(roof: dict, peaks: dict, fp64: dict | None) -> dict:
         roof.update(peak=p, frac=roof["achieved"] / p,
                     frac_of_vendor=roof["achieved"] / FP64_VENDOR_TFLOPS,
                     frac_of_dgemm=roof["achieved"] / fp64["dgemm_tflops"],
-                    peak_source=f"FP64 measured in this run: {fp64['how']} "
-                                f"({p:.3f} TFLOP/s); cuBLAS DGEMM {fp64['dgemm_tflops']:.3f} "
-                                f"TFLOP/s for frac_of_dgemm; vendor rating "
-                                f"{FP64_VENDOR_TFLOPS} TFLOP/s for frac_of_vendor")
+                    frac_of_fma_probe=roof["achieved"] / fp64["fma_probe_tflops"],
+                    peak_source=f"{fp64['how']} ({p:.3f} TFLOP/s); measured beside it: the "
+                                f"FMA-loop probe {fp64['fma_probe_tflops']:.3f} and cuBLAS "
+                                f"DGEMM {fp64['dgemm_tflops']:.3f} TFLOP/s; vendor rating "
+                                f"{FP64_VENDOR_TFLOPS} TFLOP/s")
     return roof
 
 

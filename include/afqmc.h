@@ -94,6 +94,14 @@ typedef struct afq_params {
                           VHS and propagator GEMMs, 1..4 (per-row power-of-two scale,
                           one exact TMEM accumulator per digit order); 0 = 4     */
   int exchange;        /* an afq_exchange: algorithm of the exchange energy        */
+  int prop_kernel;     /* AFQ_SPLIT_BF16 propagation: 0 = one launch per GEMM pass with
+                          digit slicing launches between them (default); 1 = one
+                          persistent kernel of thread-block clusters for all GEMM
+                          passes of a step (each walker's 128-row slabs form a
+                          cluster that exchanges the digit exponents on chip; about
+                          2x slower on this part, kept as an option), falling back
+                          to 0 where a shape cannot take it.  Both give the same
+                          bits.                                                    */
 } afq_params;
 
 /* Fill *p with the defaults: dt 0.005, Taylor order 6, QR every 5 steps, seed 1,
@@ -386,10 +394,10 @@ int afq_exchange_energy_static(int M, int X, int na, int nb, int W, const double
                                const double* thetaT_dev, double* ek_dev, void* cuda_stream);
 
 /* Measured FP64 fused multiply-add throughput of the current device in TFLOP/s (2
-   flops per FMA): 8 CTAs of 256 threads per SM, 8 independent FMA chains per thread,
-   CUDA-event timed on cuda_stream, best of three launches after a warm-up (about
-   0.15 s).  A measurement helper with no counterpart in the paper: the denominator of
-   the FP64 kernels' roofline.  Returns AFQ_OK, AFQ_ERR_ARG (NULL output) or
+   flops per FMA): 8 CTAs of 256 threads per SM, 16 independent FMA chains per thread,
+   CUDA-event timed on cuda_stream, best of five launches after three untimed ones
+   (about 0.3 s).  A measurement helper with no counterpart in the paper, reported
+   beside the FP64 kernels' roofline.  Returns AFQ_OK, AFQ_ERR_ARG (NULL output) or
    AFQ_ERR_CUDA. */
 int afq_fp64_fma_rate(double* tflops, void* cuda_stream);
 

@@ -20,6 +20,7 @@ AFQ_OK, AFQ_ERR_ARG, AFQ_ERR_CUDA, AFQ_ERR_SINGULAR, AFQ_ERR_NAN, AFQ_ERR_STATE,
 AFQ_STATIC_EXCHANGE_SLOTS = 262144  # complex partial-sum slots of the static scratch array
 PRECISIONS = {"fp64": 0, "split_bf16": 1, "split_tf32": 2}
 EXCHANGES = {"auto": 0, "direct": 1, "stored": 2}
+PROP_KERNELS = {"per_pass": 0, "fused": 1}
 STATUS_NAMES = {0: "AFQ_OK", 1: "AFQ_ERR_ARG", 2: "AFQ_ERR_CUDA", 3: "AFQ_ERR_SINGULAR",
                 4: "AFQ_ERR_NAN", 5: "AFQ_ERR_STATE", 6: "AFQ_ERR_NOMEM"}
 
@@ -30,7 +31,8 @@ class AfqParams(ctypes.Structure):
                 ("precision", ctypes.c_int), ("has_e_shift", ctypes.c_int),
                 ("e_shift", ctypes.c_double), ("fb_cap", ctypes.c_double),
                 ("free_projection", ctypes.c_int), ("split_slices", ctypes.c_int),
-                ("prop_slices", ctypes.c_int), ("exchange", ctypes.c_int)]
+                ("prop_slices", ctypes.c_int), ("exchange", ctypes.c_int),
+                ("prop_kernel", ctypes.c_int)]
 
 
 class AfqError(RuntimeError):
@@ -162,7 +164,8 @@ class AfqContext:
     def __init__(self, dt: float = 0.005, taylor_order: int = 6, qr_period: int = 5,
                  seed: int = 1, precision: str = "fp64", e_shift: float | None = None,
                  fb_cap: float = 0.0, free_projection: bool = False, stream: int | None = None,
-                 split_slices: int = 4, prop_slices: int = 4, exchange: str = "auto"):
+                 split_slices: int = 4, prop_slices: int = 4, exchange: str = "auto",
+                 prop_kernel: str = "per_pass"):
         self.lib = load_library()
         p = AfqParams()
         self.lib.afq_default_params(ctypes.byref(p))
@@ -175,6 +178,7 @@ class AfqContext:
         p.split_slices = split_slices
         p.prop_slices = prop_slices
         p.exchange = EXCHANGES[exchange]
+        p.prop_kernel = PROP_KERNELS[prop_kernel]
         self.params = p
         h = _P()
         rc = self.lib.afq_create(ctypes.byref(h), ctypes.byref(p), _P(stream or 0))

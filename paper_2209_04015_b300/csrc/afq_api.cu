@@ -257,6 +257,7 @@ void afq_default_params(afq_params* p) {
   p->split_slices = 4;
   p->prop_slices = 4;
   p->exchange = AFQ_EXCHANGE_AUTO;
+  p->prop_kernel = 0;
 }
 
 int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
@@ -276,7 +277,8 @@ int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
       (ctx->p.precision != AFQ_FP64 && ctx->p.precision != AFQ_SPLIT_BF16) ||
       ctx->p.split_slices < 1 || ctx->p.split_slices > 4 || ctx->p.prop_slices < 1 ||
       ctx->p.prop_slices > 4 || ctx->p.exchange < AFQ_EXCHANGE_AUTO ||
-      ctx->p.exchange > AFQ_EXCHANGE_STORED) {
+      ctx->p.exchange > AFQ_EXCHANGE_STORED || ctx->p.prop_kernel < 0 ||
+      ctx->p.prop_kernel > 1) {
     delete ctx;
     return AFQ_ERR_ARG;
   }

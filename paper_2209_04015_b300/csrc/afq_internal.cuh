@@ -178,6 +178,8 @@ struct afq_ctx {
   CUtensorMap tm_vhs_a, tm_vhs_b, tm_pm, tm_az, tm_t[2];
   CUtensorMap tm_t_real[2];  // the same operands in prop_rows_real-row boxes (P passes)
   int prop_rows_real = 0;    // walker columns per tile of the real P passes
+  CUtensorMap tm_t_fused[2]; // the same operands in prop_rows_fused-row boxes (cluster kernel)
+  int prop_rows_fused = 0;   // walker columns per chain of the cluster kernel
   // theta's integer digit planes (S x 2W x N x Mpad, one exponent per (z, re/im)):
   // the B operand of the force bias and of the stored exchange.  Stored exchange
   // (k_exchange_tcv.cu): S integer-digit planes of V' per spin (n Mpad)^2 with row
@@ -314,3 +316,7 @@ int mixed_prop_init_trial(afq_ctx* ctx);
 int mixed_prop_init_walkers(afq_ctx* ctx);
 int launch_vhs_tc(afq_ctx* ctx);
 int launch_propagate_tc(afq_ctx* ctx);
+// the cluster kernel of every propagation pass (k_prop_fused.cu): AFQ_OK, an error,
+// or -1 when the shape cannot take it (nothing launched)
+int launch_propagate_fused(afq_ctx* ctx);
+int fused_prop_rows(int N);  // walker columns per chain of that kernel

@@ -817,12 +817,16 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
     // of one tile overlaps the MMAs of the next)
     ctx->prop_rows_real = ctx->prop_rows > 32 ? 32 : ctx->prop_rows;
     const uint32_t btr[4] = {kBK, (uint32_t)ctx->prop_rows_real, 1, 1};
+    ctx->prop_rows_fused = fused_prop_rows(N);
+    const uint32_t btf[4] = {kBK, (uint32_t)ctx->prop_rows_fused, 1, 1};
     ok = ok && make_tmap(&ctx->tm_pm, ctx->Pm_sl, 3, dp, bp) &&
          make_tmap(&ctx->tm_az, ctx->A_sl, 4, daz, baz) &&
          make_tmap(&ctx->tm_t[0], ctx->T_sl[0], 4, dt, bt) &&
          make_tmap(&ctx->tm_t[1], ctx->T_sl[1], 4, dt, bt) &&
          make_tmap(&ctx->tm_t_real[0], ctx->T_sl[0], 4, dt, btr) &&
-         make_tmap(&ctx->tm_t_real[1], ctx->T_sl[1], 4, dt, btr);
+         make_tmap(&ctx->tm_t_real[1], ctx->T_sl[1], 4, dt, btr) &&
+         make_tmap(&ctx->tm_t_fused[0], ctx->T_sl[0], 4, dt, btf) &&
+         make_tmap(&ctx->tm_t_fused[1], ctx->T_sl[1], 4, dt, btf);
   }
   if (!ok) return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (propagation) failed");
   return AFQ_OK;
@@ -967,8 +971,13 @@ int slice_tout(afq_ctx* ctx, int b, int S) {
 // Phi <- P T_n(A) P Phi for every walker, A from the last launch_vhs_tc.  With
 // A = i sqrt(dt) V the Taylor terms are t_k = i^k g_k u_k, g_k = dt^(k/2) / k!, and
 // u_k = V u_{k-1} (u_0 = P Phi) runs on the tensor cores unscaled; the FP64 sum of the
-// t_k is kept by the slicing passes.
+// t_k is kept by the slicing passes.  With prop_kernel = 1 the cluster kernel of
+// k_prop_fused.cu runs every pass in one launch instead (the same arithmetic).
 int launch_propagate_tc(afq_ctx* ctx) {
+  if (ctx->p.prop_kernel == 1) {
+    const int rc = launch_propagate_fused(ctx);
+    if (rc != -1) return rc;
+  }
   const int W = ctx->ws.W;
   k_transpose_phi<<<grid1d((long)W * ctx->N * ctx->M), 256, 0, ctx->stream>>>(
       ctx->ws.phi, W, ctx->M, ctx->N, ctx->tout);

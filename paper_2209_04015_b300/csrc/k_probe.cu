@@ -1,31 +1,34 @@
-// Throughput probe of the FP64 pipe: the measured denominator of the FP64 kernels'
-// roofline (a measurement helper; the method itself has no counterpart).
+// Throughput probe of the FP64 pipe, measured beside the FP64 kernels' roofline (a
+// measurement helper; the method itself has no counterpart).
 //
 // Every thread runs kChains independent fused multiply-add chains, the grid holds 8
 // CTAs of 256 threads per SM (64 warps, far more independent FMAs in flight than the
 // pipe's latency needs), and the chains' values feed a store that the compiler cannot
-// drop.  Timed with CUDA events on the caller's
-// stream, best of three launches after a warm-up.
+// drop.  Timed with CUDA events on the caller's stream, best of five launches after
+// three untimed ones.
 #include <cstdio>
 
 #include "afq_internal.cuh"
 
 namespace {
 
-constexpr int kChains = 8;
+constexpr int kChains = 16;
 constexpr int kThreadsProbe = 256;
 
 // written only if the chains' sum were -1, which cannot happen (every chain stays near
-// 1 for m just below 1 and c > 0); the store keeps the loop from being removed
+// 1 for multipliers just below 1 and c > 0); the store keeps the loop from being removed
 __device__ double g_probe_sink[1];
 
 __global__ void __launch_bounds__(kThreadsProbe) k_fp64_fma_loop(int iters, double m, double c) {
-  double a[kChains];
+  double a[kChains], f[kChains];
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+  for (int k = 0; k < kChains; ++k) {
+    a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    f[k] = m - 1e-12 * k;  // a multiplier per chain: no operand is shared between chains
+  }
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], m, c);
+    for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], f[k], c);
   }
   double s = 0.0;
 #pragma unroll
@@ -43,7 +46,7 @@ extern "C" int afq_fp64_fma_rate(double* tflops, void* cuda_stream) {
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       sms <= 0)
     return AFQ_ERR_CUDA;
-  const int blocks = sms * 8, iters = 8192;
+  const int blocks = sms * 8, iters = 4096;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -51,14 +54,15 @@ extern "C" int afq_fp64_fma_rate(double* tflops, void* cuda_stream) {
   }
   float best = 1e30f;
   cudaError_t e = cudaSuccess;
-  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+  // three untimed launches bring the clocks up, then the best of five timed ones
+  for (int rep = 0; rep < 8 && e == cudaSuccess; ++rep) {
     cudaEventRecord(e0, st);
     k_fp64_fma_loop<<<blocks, kThreadsProbe, 0, st>>>(iters, 0.999999999, 1e-9);
     cudaEventRecord(e1, st);
     e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) e = cudaGetLastError();
     float ms = 0.f;
-    if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+    if (e == cudaSuccess && rep >= 3 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
         ms > 0.f && ms < best)
       best = ms;
   }
