@@ -55,7 +55,9 @@ FP64_ALU_TFLOPS = 148 * 4 * 2.032e9 / 1e12
 # these exact workloads: per launch for the FP64 kernels, per step (every launch of
 # the class) for the split propagation; absent where no capture of the current
 # kernels exists.
-TRAFFIC = {("fp64", "c2", "propagate"): 34943232 + 16384}
+TRAFFIC = {("fp64", "c2", "propagate"): 34943232 + 16384,
+           ("fp64", "c3", "vhs"): 40627748352 + 1298133760,
+           ("split_bf16", "c3", "propagate"): 7590425344 + 2743548160}
 FP64_KERNELS = {"propagate": "k_propagate_fp64", "exchange": "k_exchange_v / k_exchange_fp64",
                 "vhs": "k_vhs_fp64", "force_bias": "k_force_bias_fp64"}
 SPLIT_KERNELS = {"propagate": "k_prop_tc (8 GEMM passes) + k_taylor_slice / k_slice_cplx1",
@@ -87,8 +89,13 @@ def parse_args():
     ap.add_argument("--split-steps", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--profile-leg", choices=["fp64-c3", "split-c3", "fp64-c2", "split-c2",
-                                              "batched", "batched-fp64", "adjoint", "blocks"],
-                    default=None, help="run one leg alone and print its JSON (for ncu)")
+                                              "mixed-c3", "mixed-c2", "batched",
+                                              "batched-fp64", "adjoint", "blocks"],
+                    default=None, help="run one leg alone and print its JSON (for ncu); "
+                                       "mixed-c3 / mixed-c2 are the split-c3 / split-c2 legs")
+    ap.add_argument("--mixed-steps", type=int, default=None,
+                    help="timed steps of a mixed-* profile leg (default: --steps)")
+    ap.add_argument("--no-mixed", action="store_true", help="the same as --no-extra")
     ap.add_argument("--profile-walkers", type=int, default=0,
                     help="walker count of a --profile-leg step leg (0: the workload's)")
     ap.add_argument("--error-steps", type=int, default=100,
@@ -184,6 +191,40 @@ def split_flops(W, X, M, na, nb, algo, S, digits):
     else:
         out["exchange"] = prods(S) * exchange_flops(W, X, M, na, nb)
     return out
+
+
+def algorithmic_bytes(precision, kernel, W, X, M, na, nb, digits=None):
+    """Bytes the dominant kernel class must move per launch (FP64) or per step (split
+    propagation, every launch of the class) if every operand were read and every
+    result written once; None where not modelled.
+    FP64 VHS: packed L (X M(M+1)/2 doubles) and y (W X complex) in, A (W M^2 complex)
+    and Re A + Im A (W M^2 doubles) out.  FP64 propagation: A, Re A + Im A, P and Phi
+    in, Phi out.  Split propagation: per GEMM pass its digit planes (V_z, 2 W M Mpad
+    bf16 per digit, or O) and the operand's (2 W N Mpad per digit), the FP64 pass
+    output (W N M complex) out; per slicing pass the output in, the FP64 Taylor sum
+    read and written, the next digits out; the transposed copy and first slicing of
+    Phi; Phi out."""
+    N = na + nb
+    Mpad = (M + 31) // 32 * 32
+    F = W * N * M * 16
+    if precision == "fp64":
+        if kernel == "vhs":
+            return X * (M * (M + 1) // 2) * 8 + W * X * 16 + W * M * M * 24
+        if kernel == "propagate":
+            return W * M * M * 24 + M * M * 8 + 2 * F
+        return None
+    if kernel != "propagate" or not digits:
+        return None
+    V, T, O = 2 * W * M * Mpad * 2, 2 * W * N * Mpad * 2, M * Mpad * 2
+    n = len(digits) - 2
+    total = 2 * F + F + digits[0] * T                    # transpose, Phi's digits
+    total += digits[0] * (O + T) + F                     # first half
+    total += 3 * F + digits[1] * T                       # its slicing pass
+    for k in range(1, n + 1):
+        total += digits[k] * (V + T) + F                 # Taylor pass
+        total += 3 * F + digits[k + 1] * T               # slicing pass
+    total += digits[-1] * (O + T) + 2 * F                # second half, Phi out
+    return total
 
 
 def fp64_peak() -> dict:
@@ -422,9 +463,14 @@ def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, worl
         avg_s = dom_ms / max(dom_n, 1) / 1e3
         out["step_flops"] = sum(flops.values())
         out["step_tflops"] = out["step_flops"] / (out["ms_per_step"] / 1e3) / 1e12
+        traffic = TRAFFIC.get(("fp64", name, dom)) if not walkers else None
+        algo = algorithmic_bytes("fp64", dom, W, X, M, na, nb)
         out["roofline"] = {"bound": "alu", "kernel": f"{dom} ({FP64_KERNELS[dom]})",
                            "achieved": per_launch / avg_s / 1e12, "unit": "TFLOP/s",
-                           "traffic": TRAFFIC.get(("fp64", name, dom)) if not walkers else None,
+                           "traffic": traffic, "algorithmic_bytes": algo,
+                           "traffic_over_algorithmic": (traffic / algo
+                                                        if traffic and algo else None),
+                           "dram_gbs": traffic / avg_s / 1e9 if traffic else None,
                            "flops_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3,
                            "per": "launch"}
     else:
@@ -434,10 +480,14 @@ def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, worl
         out["prop_digits"] = digits
         out["split_slices"] = S
         out["tensor_flops_per_step"] = sum(flops.values())
+        traffic = TRAFFIC.get(("split_bf16", name, dom)) if not walkers else None
+        algo = algorithmic_bytes("split_bf16", dom, W, X, M, na, nb, digits)
         out["roofline"] = {"bound": "tensor", "kernel": f"{dom} ({SPLIT_KERNELS[dom]})",
                            "achieved": per_step / dom_s / 1e12, "unit": "TFLOP/s",
-                           "traffic": (TRAFFIC.get(("split_bf16", name, dom))
-                                       if not walkers else None),
+                           "traffic": traffic, "algorithmic_bytes": algo,
+                           "traffic_over_algorithmic": (traffic / algo
+                                                        if traffic and algo else None),
+                           "dram_gbs": traffic / dom_s / 1e9 if traffic else None,
                            "flops_per_step": per_step, "ms_per_step": dom_s * 1e3,
                            "per": "step (every launch of the class, digit slicing included)",
                            "flops_note": "digit products (s + t <= S - 1 of S digits) x the "
@@ -449,7 +499,10 @@ def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, worl
 
 def attach_peak(roof: dict, peaks: dict, fp64: dict | None) -> dict:
     """Roofline denominators: measured BF16 (MEASURED_PEAKS.json, burst and sustained)
-    for tensor-bound classes, the DGEMM rate measured in this run for FP64 ones."""
+    for tensor-bound classes, the FP64 ALU peak for FP64 ones; the DRAM rate of the
+    captured traffic as a fraction of the measured HBM copy bandwidth beside them."""
+    if roof.get("dram_gbs"):
+        roof["dram_frac_of_hbm"] = roof["dram_gbs"] / peaks.get("hbm_gbs", 6400.0)
     if roof["bound"] == "tensor":
         burst = peaks.get("bf16_tflops", 1800.0)
         sust = peaks.get("bf16_tflops_sustained", 1400.0)
@@ -764,9 +817,10 @@ def run_leg(args) -> int:
     import torch
     torch.cuda.set_device(0)
     leg = args.profile_leg
-    if leg.startswith(("fp64", "split")):
+    if leg.startswith(("fp64", "split", "mixed")):
         prec, name = leg.split("-")
-        out = step_leg(name, "fp64" if prec == "fp64" else "split_bf16", args.steps,
+        steps = args.mixed_steps if prec == "mixed" and args.mixed_steps else args.steps
+        out = step_leg(name, "fp64" if prec == "fp64" else "split_bf16", steps,
                        args.warmup, 0, 1, 0, walkers=args.profile_walkers)
     elif leg.startswith("batched"):
         out = batched_leg(0, "fp64" if leg.endswith("fp64") else "split_bf16", 2)
@@ -820,7 +874,7 @@ def run_afq(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(WORKLOAD, args.cpu_seconds, 2)
-    if not args.no_extra:
+    if not (args.no_extra or args.no_mixed):
         split = step_leg(WORKLOAD, "split_bf16", args.split_steps, args.warmup, rank, 1, local,
                          e2e_steps=e2e_steps)
         attach_peak(split["roofline"], peaks, fp64)

@@ -240,6 +240,34 @@ def test_c2_full_size_sampled_walkers():
     assert rel(e[idx, 3], eref[:, 3]).max() <= TOL
 
 
+def test_c3_fp64_full_size_sampled_walkers():
+    """The benchmark's main line: 290 orbitals, 26 + 26 electrons, 1500 Cholesky
+    vectors, 640 walkers in FP64, autotuned as the benchmark runs it (the stored
+    exchange), device Philox fields, 5 steps ending with a QR, then the local energy;
+    3 walkers re-run by the oracle alone (walkers are independent, so a subset with its
+    own field rows gives the same values), each energy part, weight and walker element
+    within 1e-10."""
+    s, c = make_config("c3")
+    W, nsteps = c["W"], 5
+    ctx, _ = make_pair(s, W)
+    ctx.autotune()
+    assert ctx.exchange_algorithm() == "stored"
+    ctx.propagate(None, nsteps)
+    e, _ = ctx.local_energy()
+    idx = np.array([0, 333, 639])
+    from oracle.afqmc import Oracle
+    orc = Oracle(s.h1, s.L, s.e0, s.psi_a, s.psi_b, dt=0.005)
+    orc.init_walkers(trial_walkers(s, len(idx)))
+    orc.propagate([philox.gaussian_fields(k, W, s.X, 1)[idx] for k in range(nsteps)])
+    assert walker_rel(ctx.get_walkers()[idx], orc.phi).max() <= TOL
+    assert rel(ctx.get_weights()[idx], orc.w).max() <= TOL
+    eref, _ = orc.local_energy()
+    for k in range(4):
+        scale = np.maximum(np.abs(eref[:, k]), 1e-3 * np.abs(eref[:, 3]))
+        assert np.all(np.abs(e[idx, k] - eref[:, k]) <= TOL * scale), k
+    ctx.close()
+
+
 def test_recreated_contexts_on_reused_memory_are_identical():
     """Contexts destroyed and re-created while others stay alive reuse device memory
     that holds stale values (NaN bit patterns included); no kernel may read memory it
