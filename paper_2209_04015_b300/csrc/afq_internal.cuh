@@ -192,6 +192,17 @@ struct afq_ctx {
   int exv_BN = 0;
   CUtensorMap tm_exv_a[2], tm_exv_b;
 
+  // overlap product S = Psi^T Phi of the split-precision walker ensemble on the tensor
+  // cores (k_overlap_tc.cu): 7 exact digits of Psi^T (N x Mpad per digit) with row
+  // exponents, of Phi^T (2W N x Mpad per digit) with exponents per (z, j), and S itself
+  // (W x 2 x nmax x nmax complex)
+  __nv_bfloat16* ov_psi_sl = nullptr;
+  int* ov_ea = nullptr;
+  __nv_bfloat16* ov_phi_sl = nullptr;
+  int* ov_eb = nullptr;
+  double2* ov_S = nullptr;
+  CUtensorMap tm_ov_a, tm_ov_b;
+
   ChainTape chain;  // afq_chain_forward
   // half-rotated exchange tensor V_s[(j,p),(i,q)] = sum_g L~_g,s[j][q] L~_g,s[i][p] per
   // spin (alpha block, then beta block): built by afq_init_trial when the stored
@@ -316,6 +327,11 @@ int mixed_prop_init_trial(afq_ctx* ctx);
 int mixed_prop_init_walkers(afq_ctx* ctx);
 int launch_vhs_tc(afq_ctx* ctx);
 int launch_propagate_tc(afq_ctx* ctx);
+// S = Psi^T Phi on the tensor cores (k_overlap_tc.cu)
+int overlap_tc_init_trial(afq_ctx* ctx);
+int overlap_tc_init_walkers(afq_ctx* ctx);
+void overlap_tc_free(afq_ctx* ctx);
+int launch_overlap_s_tc(afq_ctx* ctx, WalkerSet& s);
 // the cluster kernel of every propagation pass (k_prop_fused.cu): AFQ_OK, an error,
 // or -1 when the shape cannot take it (nothing launched)
 int launch_propagate_fused(afq_ctx* ctx);

@@ -292,6 +292,7 @@ int mixed_exchange_tiles(int n, int* G, int* zb, int* BN) {
 
 void mixed_free(afq_ctx* ctx) {
   mixed_prop_free(ctx);
+  overlap_tc_free(ctx);
   if (ctx->Lt_sl) cudaFree(ctx->Lt_sl);
   if (ctx->th_sl) cudaFree(ctx->th_sl);
   if (ctx->fb_part) cudaFree(ctx->fb_part);
@@ -327,6 +328,7 @@ int mixed_init_trial(afq_ctx* ctx) {
   k_slice_lt_exact<<<warp_grid_rows(X), 256, 0, ctx->stream>>>(ctx->Lt, X, N, M, ctx->Mpad, S,
                                                                ctx->Lt_ex, ctx->e_fb);
   AFQ_LAUNCHED(ctx);
+  AFQ_TRY(overlap_tc_init_trial(ctx));
   if (!ctx->ex_stored) {
     AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->Lt_sl, plane * S * sizeof(__nv_bfloat16)));
     k_slice_rows_scaled<<<warp_grid_rows((long)X * N), 256, 0, ctx->stream>>>(
@@ -383,6 +385,7 @@ int mixed_init_walkers(afq_ctx* ctx) {
       return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (exchange) failed");
   }
   if (ctx->Vsl) AFQ_TRY(mixed_exchange_v_walkers(ctx));
+  AFQ_TRY(overlap_tc_init_walkers(ctx));
   return AFQ_OK;
 }
 

@@ -1,0 +1,282 @@
+// The overlap matrices S_z,s = Psi_s^T Phi_z,s (Sec. "Overlap") of a split-precision
+// walker set on the tensor cores, to FP64 quality.
+//
+// Overlaps, determinants and inverses stay FP64 in split precision; here only the
+// product S, which the overlap kernel otherwise forms with the FP64 pipe (half of
+// that kernel's time at 290 orbitals), runs as one GEMM on 7 exact digits per operand:
+// every row of Psi^T (one per orbital of the trial) and every row (z, j) of Phi^T is
+// scaled by a power of two and cut into 7 balanced 8-bit digits (55 bits, more than
+// FP64's 53), and the 28 digit products with s + t <= 6 accumulate in 7 TMEM diagonals
+// (tc_engine.cuh's exact-diagonal form).  The leading diagonal's sum is bounded by
+// 128^2 M < 2^24 for M <= 1024, so it is exact in FP32; the lower diagonals are
+// random-sign sums 2^-8 and more below it.  The epilogue recombines the diagonals in
+// two int64 halves (d <= 3 and d >= 4, each below 2^53) and adds them in FP64 once,
+// so S carries FP64-level rounding, and writes the two diagonal spin blocks per walker.
+//
+// GEMM: A = Psi^T digits (N rows, alpha then beta, one 128-row tile), B = Phi^T digits
+// (rows (z, re/im, j), K = p), D[i][(z, re/im, j)]; the off-diagonal spin blocks are
+// computed and dropped.
+#include "tc_engine.cuh"
+
+using namespace tce;
+
+namespace {
+
+constexpr int kOvDigits = 7;
+constexpr int kOvBN = 64;  // 7 accumulators x 64 columns fit the 512 TMEM columns
+
+// The exact digits of exact_digits for up to 7 digits (q[s] of weight 256^-s).
+__device__ __forceinline__ void exact_digits7(double x, int e, int S, int (&q)[kOvDigits]) {
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long v = 0;
+  if (E != 0) {
+    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = E - 1075 + 7 - e + 8 * (S - 1);  // value = mant 2^(E-1075)
+    if (sh >= 0)
+      v = sh < 10 ? mant << sh : 0;  // |x| <= 2^e: sh <= 2 + 8 (S - 1) - 53 + 1
+    else if (sh > -64)
+      v = (mant + (1LL << (-sh - 1))) >> (-sh);
+  }
+  const bool neg = bits < 0;
+#pragma unroll
+  for (int s = kOvDigits - 1; s >= 0; --s) {
+    q[s] = 0;
+    if (s >= S) continue;
+    int d = (int)(v & 255);
+    if (d > 128) d -= 256;
+    q[s] = neg ? -d : d;
+    v = (v - d) >> 8;
+  }
+}
+
+// Real rows of K doubles (row pitch ld) -> S digit planes of rows x Kp with one
+// exponent per row (one warp per row).
+__global__ void k_slice_rows7(const double* __restrict__ in, long ld, long rows, int K, int Kp,
+                              int S, __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const long plane = rows * Kp;
+  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
+       r += (long)gridDim.x * warps) {
+    const double* row = in + r * ld;
+    int m = 0;
+    for (int k = lane; k < K; k += 32) m = max(m, exp_field(row[k]));
+    const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
+    if (lane == 0) eout[r] = e;
+    for (int k = lane; k < Kp; k += 32) {
+      int q[kOvDigits];
+      exact_digits7(k < K ? row[k] : 0.0, e, S, q);
+#pragma unroll
+      for (int s = 0; s < kOvDigits; ++s)
+        if (s < S) out[s * plane + r * Kp + k] = __float2bfloat16_rn((float)q[s]);
+    }
+  }
+}
+
+// Phi (W x M x N complex) -> S digit planes [s][z][re/im][j][Kp] of Phi^T, one exponent
+// per complex row (z, j) shared by its real and imaginary parts (one warp per row; the
+// row's elements are N apart in Phi).
+__global__ void k_slice_phiT7(const double2* __restrict__ phi, int W, int M, int N, int Kp, int S,
+                              __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const long rows = (long)W * N, plane = 2L * rows * Kp;
+  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
+       r += (long)gridDim.x * warps) {
+    const long z = r / N;
+    const int j = (int)(r - z * N);
+    const double2* col = phi + z * (long)M * N + j;
+    int m = 0;
+    for (int p = lane; p < M; p += 32) {
+      const double2 v = col[(long)p * N];
+      m = max(m, max(exp_field(v.x), exp_field(v.y)));
+    }
+    const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
+    if (lane == 0) eout[r] = e;
+    __nv_bfloat16* ore = out + ((2 * z) * N + j) * (long)Kp;
+    __nv_bfloat16* oim = ore + (long)N * Kp;
+    for (int p = lane; p < Kp; p += 32) {
+      const double2 v = p < M ? col[(long)p * N] : make_double2(0.0, 0.0);
+      int qr[kOvDigits], qi[kOvDigits];
+      exact_digits7(v.x, e, S, qr);
+      exact_digits7(v.y, e, S, qi);
+#pragma unroll
+      for (int s = 0; s < kOvDigits; ++s)
+        if (s < S) {
+          ore[s * plane + p] = __float2bfloat16_rn((float)qr[s]);
+          oim[s * plane + p] = __float2bfloat16_rn((float)qi[s]);
+        }
+    }
+  }
+}
+
+// value = 2^scale_exp sum_d acc_d 256^-d for 7 diagonals, as two int64 halves
+// (d <= 3 and d >= 4, each exact in FP64) added once in FP64.
+__device__ __forceinline__ double combine7(const float (&acc)[kOvDigits], int scale_exp) {
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) hi += (long long)__float2int_rn(acc[d]) * (1LL << (8 * (3 - d)));
+#pragma unroll
+  for (int d = 4; d < kOvDigits; ++d)
+    lo += (long long)__float2int_rn(acc[d]) * (1LL << (8 * (6 - d)));
+  double h = 0.0, l = 0.0;
+  if (hi != 0)
+    h = __longlong_as_double(__double_as_longlong(__ll2double_rn(hi)) +
+                             ((long long)(scale_exp - 24) << 52));
+  if (lo != 0)
+    l = __longlong_as_double(__double_as_longlong(__ll2double_rn(lo)) +
+                             ((long long)(scale_exp - 48) << 52));
+  return h + l;
+}
+
+struct OvP {
+  struct Args {
+    TcCommon c;
+    int N, na, nb, nmax;
+    long rows_b;        // 2 W N
+    const int* ea;      // row exponents of Psi^T
+    const int* eb;      // exponents of Phi^T per complex row (z, j)
+    double2* S;         // W x 2 x nmax x nmax
+  };
+  struct Tile {
+    int r0, n0, kb0, kb1;
+  };
+  static constexpr int kUA = 1, kUB = 1;
+  template <int SS>
+  static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
+                               uint32_t bslot, bool first) {
+    issue_diagonals<SS>(tmem, (uint32_t)a.c.BN, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN),
+                        first);
+  }
+  static __device__ Tile tile(const Args& a) {
+    return Tile{0, (int)blockIdx.x * a.c.BN, 0, a.c.nkb};
+  }
+  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile&, int,
+                                int s, int kb, uint64_t* bar) {
+    tc::tma_load_3d(dst, tm, kb * kBK, 0, s, bar);
+  }
+  static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int,
+                                int s, int kb, uint64_t* bar) {
+    tc::tma_load_3d(dst, tm, kb * kBK, t.n0, s, bar);
+  }
+  template <int SS>
+  static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t*, int warp,
+                                  int lane) {
+    const int i = warp * 32 + lane;  // row of Psi^T: orbital i of the trial
+    const bool valid = i < a.N;
+    const int si = i < a.na ? 0 : 1, oi = si ? a.na : 0;
+    const int ei = valid ? a.ea[i] : 0;
+    const int N = a.N;
+    for (int c0 = 0; c0 < a.c.BN; c0 += 16) {
+      float f[kOvDigits][16];
+#pragma unroll
+      for (int d = 0; d < kOvDigits; ++d) tmem_row16(tmem + (uint32_t)(d * a.c.BN), warp, c0, f[d]);
+      if (!valid) continue;
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const long col = (long)t.n0 + c0 + jj;  // row of Phi^T: (z, re/im, j)
+        if (col >= a.rows_b) continue;
+        const long zp = col / N;
+        const int j = (int)(col - zp * N), part = (int)(zp & 1);
+        const long z = zp >> 1;
+        const int sj = j < a.na ? 0 : 1;
+        if (sj != si) continue;
+        float acc[kOvDigits];
+#pragma unroll
+        for (int d = 0; d < kOvDigits; ++d) acc[d] = f[d][jj];
+        const double v = combine7(acc, ei + a.eb[z * N + j] - 14);
+        double* dst = reinterpret_cast<double*>(
+            a.S + ((z * 2 + si) * a.nmax + (i - oi)) * a.nmax + (j - oi));
+        dst[part] = v;
+      }
+    }
+  }
+};
+
+int warp_grid7(long rows) {
+  long g = (rows + 7) / 8;
+  return (int)(g < 1 ? 1 : (g > 148 * 16 ? 148 * 16 : g));
+}
+
+}  // namespace
+
+// Once per trial: the 7 digits of Psi^T (N x M, rows alpha then beta) and their map.
+int overlap_tc_init_trial(afq_ctx* ctx) {
+  const int N = ctx->N, M = ctx->M, Mpad = ctx->Mpad;
+  if (ctx->ov_psi_sl) cudaFree(ctx->ov_psi_sl);
+  if (ctx->ov_ea) cudaFree(ctx->ov_ea);
+  ctx->ov_psi_sl = nullptr;
+  ctx->ov_ea = nullptr;
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_psi_sl, (size_t)kOvDigits * N * Mpad * 2));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_ea, (size_t)N * sizeof(int)));
+  k_slice_rows7<<<warp_grid7(N), 256, 0, ctx->stream>>>(ctx->psiT, M, N, M, Mpad, kOvDigits,
+                                                         ctx->ov_psi_sl, ctx->ov_ea);
+  AFQ_LAUNCHED(ctx);
+  const uint64_t da[3] = {(uint64_t)Mpad, (uint64_t)N, (uint64_t)kOvDigits};
+  const uint32_t ba[3] = {kBK, 128, 1};
+  if (!make_tmap(&ctx->tm_ov_a, ctx->ov_psi_sl, 3, da, ba))
+    return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (overlap) failed");
+  return AFQ_OK;
+}
+
+// Per walker set: Phi^T's digit planes, their exponents, the S buffer and the map.
+int overlap_tc_init_walkers(afq_ctx* ctx) {
+  const int N = ctx->N, W = ctx->ws.W, Mpad = ctx->Mpad;
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  for (void* p : {(void*)ctx->ov_phi_sl, (void*)ctx->ov_eb, (void*)ctx->ov_S})
+    if (p) cudaFree(p);
+  ctx->ov_phi_sl = nullptr;
+  ctx->ov_eb = nullptr;
+  ctx->ov_S = nullptr;
+  const long rows = 2L * W * N;
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_phi_sl, (size_t)kOvDigits * rows * Mpad * 2));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_eb, (size_t)W * N * sizeof(int)));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_S, (size_t)W * 2 * nmax * nmax * sizeof(double2)));
+  const uint64_t db[3] = {(uint64_t)Mpad, (uint64_t)rows, (uint64_t)kOvDigits};
+  const uint32_t bb[3] = {kBK, (uint32_t)kOvBN, 1};
+  if (!make_tmap(&ctx->tm_ov_b, ctx->ov_phi_sl, 3, db, bb))
+    return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (overlap) failed");
+  return AFQ_OK;
+}
+
+void overlap_tc_free(afq_ctx* ctx) {
+  for (void* p : {(void*)ctx->ov_psi_sl, (void*)ctx->ov_ea, (void*)ctx->ov_phi_sl,
+                  (void*)ctx->ov_eb, (void*)ctx->ov_S})
+    if (p) cudaFree(p);
+  ctx->ov_psi_sl = nullptr;
+  ctx->ov_ea = nullptr;
+  ctx->ov_phi_sl = nullptr;
+  ctx->ov_eb = nullptr;
+  ctx->ov_S = nullptr;
+}
+
+// S_z,s = Psi_s^T Phi_z,s for the walker set (its digits, then the GEMM) into ctx->ov_S.
+int launch_overlap_s_tc(afq_ctx* ctx, WalkerSet& s) {
+  const int N = ctx->N, M = ctx->M, Mpad = ctx->Mpad, W = s.W;
+  k_slice_phiT7<<<warp_grid7((long)W * N), 256, 0, ctx->stream>>>(s.phi, W, M, N, Mpad, kOvDigits,
+                                                                  ctx->ov_phi_sl, ctx->ov_eb);
+  AFQ_LAUNCHED(ctx);
+  OvP::Args a{};
+  a.c.nkb = Mpad / kBK;
+  a.c.BN = kOvBN;
+  a.c.tx_bytes = (uint32_t)kOvDigits * (kBK * 128 * 2 + kBK * kOvBN * 2);
+  a.c.tmem_cols = tmem_cols_for(kOvDigits * kOvBN);
+  a.c.err = ctx->flags + 2;
+  a.N = N;
+  a.na = ctx->na;
+  a.nb = ctx->nb;
+  a.nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  a.rows_b = 2L * W * N;
+  a.ea = ctx->ov_ea;
+  a.eb = ctx->ov_eb;
+  a.S = ctx->ov_S;
+  size_t smem = 0;
+  plan_smem(kOvDigits, 1, 1, kOvBN, 0, &a.c.stages, &smem);
+  if (a.c.stages < 1 || smem > kSmemLimit)
+    return afq_fail(ctx, AFQ_ERR_ARG, "overlap tile does not fit in shared memory");
+  dim3 grid((unsigned)((a.rows_b + kOvBN - 1) / kOvBN));
+  cudaError_t e = launch_tc<kOvDigits, OvP>(grid, smem, ctx->stream, ctx->tm_ov_a, ctx->tm_ov_b, a);
+  ctx->launches++;
+  if (e != cudaSuccess)
+    return afq_fail(ctx, AFQ_ERR_CUDA, std::string("overlap tc: ") + cudaGetErrorString(e));
+  return AFQ_OK;
+}

@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
                                                       const double2* __restrict__ phi,
                                                       double2* __restrict__ thetaT,
                                                       double2* __restrict__ det,
-                                                      double2* __restrict__ e1, int* flags) {
+                                                      double2* __restrict__ e1, int* flags,
+                                                      const double2* __restrict__ Spre,
+                                                      int nmax) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double2 red[OT / 32];
   __shared__ int s_piv;
@@ -122,11 +124,20 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
   double2* fac = reinterpret_cast<double2*>(cpsi + PC * ldn + (PC * ldn & 1));  // n
   const double2* phiz = phi + (long)z * M * N;
 
-  // 1. S_ij = sum_p Psi_pi Phi_pj
+  // 1. S_ij = sum_p Psi_pi Phi_pj (or, with Spre, the product formed on the tensor cores:
+  // W x 2 x nmax x nmax, to FP64 quality)
   double2 acc[MO];
 #pragma unroll
   for (int k = 0; k < MO; ++k) acc[k] = cmk(0.0, 0.0);
-  for (int p0 = 0; p0 < M; p0 += PC) {
+  if (Spre) {
+    const double2* Sz = Spre + ((long)z * 2 + s) * nmax * nmax;
+#pragma unroll
+    for (int k = 0; k < MO; ++k) {
+      const int o = tid + k * OT;
+      if (o < n * n) acc[k] = Sz[(o / n) * nmax + o % n];
+    }
+  }
+  for (int p0 = 0; p0 < M && !Spre; p0 += PC) {
     const int pc = min(PC, M - p0);
     for (int e = tid; e < PC * n; e += OT) {
       const int pp = e / n, j = e % n;
@@ -580,9 +591,15 @@ int launch_overlap_mo(afq_ctx* ctx, WalkerSet& s) {
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
   const size_t smem = overlap_smem(nmax);
   AFQ_CUDA(ctx, raise_smem_limit((const void*)k_overlap_theta<DF, MO>, smem));
+  // split-precision walker ensembles take S from the tensor cores (k_overlap_tc.cu)
+  const double2* Spre = nullptr;
+  if (DF && ctx->ov_S && &s == &ctx->ws) {
+    AFQ_TRY(launch_overlap_s_tc(ctx, s));
+    Spre = ctx->ov_S;
+  }
   k_overlap_theta<DF, MO><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
       ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
-      ctx->flags);
+      ctx->flags, Spre, nmax);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }
