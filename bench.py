@@ -89,6 +89,7 @@ def parse_args():
     ap.add_argument("--split-steps", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint leg")
     ap.add_argument("--profile-leg", choices=["fp64-c3", "split-c3", "fp64-c2", "split-c2",
+                                              "digits7-c3", "digits7-c2",
                                               "mixed-c3", "mixed-c2", "batched",
                                               "batched-fp64", "adjoint", "blocks"],
                     default=None, help="run one leg alone and print its JSON (for ncu); "
@@ -171,7 +172,7 @@ def step_flops(W, X, M, na, nb, order=6, exchange="direct"):
     }
 
 
-def split_flops(W, X, M, na, nb, algo, S, digits):
+def split_flops(W, X, M, na, nb, algo, S, digits, Sp=4):
     """Digit-product flops of the split-precision tensor-core GEMMs per step, by
     kernel class: each product of an S-digit operand pair with s + t <= S - 1 counts
     the GEMM's algorithmic flops (no padding counted, except the stored exchange's
@@ -180,7 +181,7 @@ def split_flops(W, X, M, na, nb, algo, S, digits):
     Mp = M * (M + 1) // 2
     prods = lambda d: d * (d + 1) // 2  # noqa: E731
     out = {"force_bias": prods(S) * 2 * X * N * M * 2 * W,
-           "vhs": prods(4) * 2 * Mp * X * 2 * W}
+           "vhs": prods(Sp) * 2 * Mp * X * 2 * W}
     if digits:
         Sp = max(digits)
         out["vhs"] = prods(Sp) * 2 * Mp * X * 2 * W
@@ -352,6 +353,10 @@ def cpu_baseline(name: str, seconds: float, walkers: int) -> dict:
 
 # ----------------------------------------------------------------------------- legs
 
+# split precision at FP64 quality: 7 exact digits per operand everywhere (55 bits)
+DIGITS7 = dict(split_slices=7, prop_slices=7)
+
+
 def new_context(s, W, precision, rank, stream, autotune=True, **kw):
     from paper_2209_04015_b300 import AfqContext
     ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, precision=precision,
@@ -365,7 +370,8 @@ def new_context(s, W, precision, rank, stream, autotune=True, **kw):
 
 
 def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, world: int,
-             local: int, walkers: int = 0, e2e_steps: int = 0, clocks: bool = False) -> dict:
+             local: int, walkers: int = 0, e2e_steps: int = 0, clocks: bool = False,
+             **ctx_kw) -> dict:
     """Device-timed steps (propagate + local energy of every walker) of one workload in
     one precision: W untimed warm-up steps, then `steps` steps, each between CUDA events
     on the context's stream with a 256 MB L2 flush before it (outside the events), the
@@ -378,7 +384,7 @@ def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, worl
     s, c = make_config(name, seed=1 + rank)
     W, X, M, na, nb = walkers or c["W"], s.X, s.M, s.na, s.nb
     stream = torch.cuda.current_stream()
-    ctx = new_context(s, W, precision, rank, stream)
+    ctx = new_context(s, W, precision, rank, stream, **ctx_kw)
     e_dev = torch.empty((W, 4, 2), dtype=torch.float64, device="cuda")
     emix_dev = torch.empty(1, dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -416,6 +422,7 @@ def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, worl
     tiles = ctx.get_tiles()
     digits = ctx.prop_digits()[0] if precision != "fp64" else None
     S = ctx.params.split_slices or 4
+    Sp = ctx.params.prop_slices or 4
     ctx.close()
     del flush
 
@@ -429,7 +436,7 @@ def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, worl
         host_fields.copy_(torch.from_numpy(
             np.random.default_rng(5 + rank).standard_normal((e2e_steps + 1, W, X))))
         hf = host_fields.numpy()
-        ectx = new_context(s, W, precision, rank, stream)
+        ectx = new_context(s, W, precision, rank, stream, **ctx_kw)
         ectx.propagate(hf[0], 1)
         ectx.local_energy()
         torch.cuda.synchronize()
@@ -474,7 +481,7 @@ def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, worl
                            "flops_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3,
                            "per": "launch"}
     else:
-        flops = split_flops(W, X, M, na, nb, algo, S, digits)
+        flops = split_flops(W, X, M, na, nb, algo, S, digits, Sp)
         per_step = flops[dom]
         dom_s = dom_ms / steps / 1e3
         out["prop_digits"] = digits
@@ -586,6 +593,51 @@ def mixed_errors(name: str, rank: int, long_steps: int = 100, check_walkers: int
                      "overlaps per walker; walkers: max element difference over the walker's "
                      "largest element; gradients max |d| / max |ref|, FP64 adjoint at the "
                      "split-propagated walkers, cotangent seeded)"}
+
+
+def digits7_errors(name: str, rank: int, steps: int = 20, check_walkers: int = 16) -> dict:
+    """The 7-digit (FP64-quality) split path against the FP64 path on the first walkers
+    after 1 and after `steps` steps of the same device Philox fields: max relative error
+    of every energy part, weight, overlap and walker element (walker: max element
+    difference over the walker's largest element)."""
+    import torch
+    from paper_2209_04015_b300 import AfqContext
+    from paper_2209_04015_b300.synthetic import make_config
+
+    s, c = make_config(name, seed=1 + rank)
+    stream = torch.cuda.current_stream()
+
+    def context(nw, **kw):
+        ctx = AfqContext(dt=0.005, qr_period=5, seed=1 + rank, stream=stream.cuda_stream, **kw)
+        ctx.init_hamiltonian(s.h1, s.L, s.e0)
+        ctx.init_trial(s.psi_a, s.psi_b)
+        ctx.init_walkers(nw)
+        return ctx
+
+    mix = context(c["W"], precision="split_bf16", **DIGITS7)
+    ref = context(check_walkers)
+    n, out = check_walkers, {}
+    for k in range(1, steps + 1):
+        mix.propagate(None, 1)
+        ref.propagate(None, 1)
+        if k in (1, steps):
+            em, _ = mix.local_energy()
+            er, _ = ref.local_energy()
+            r = {part: float(np.max(np.abs(em[:n, i] - er[:, i]) / np.abs(er[:, i])))
+                 for i, part in enumerate(("E1", "EJ", "EK", "E_L"))}
+            wm, wr = mix.get_weights()[:n], ref.get_weights()
+            r["w"] = float(np.max(np.abs(wm - wr) / np.abs(wr)))
+            om, orf = mix.get_overlaps()[:n], ref.get_overlaps()
+            r["overlap"] = float(np.max(np.abs(om - orf) / np.abs(orf)))
+            pm, pr = mix.get_walkers()[:n], ref.get_walkers()
+            r["phi"] = float(np.max(np.abs(pm - pr).reshape(n, -1).max(axis=1) /
+                                    np.abs(pr).reshape(n, -1).max(axis=1)))
+            out[f"after_{k}_steps"] = r
+    mix.close()
+    ref.close()
+    out["reference"] = (f"FP64 path (parity-checked against the FP64 oracle at 1e-10) on the "
+                        f"first {n} of {c['W']} walkers, same Philox fields; all max relative")
+    return out
 
 
 def block_leg(name: str, precision: str, rank: int, blocks: int = 4, block_steps: int = 25) -> dict:
@@ -817,11 +869,12 @@ def run_leg(args) -> int:
     import torch
     torch.cuda.set_device(0)
     leg = args.profile_leg
-    if leg.startswith(("fp64", "split", "mixed")):
+    if leg.startswith(("fp64", "split", "mixed", "digits7")):
         prec, name = leg.split("-")
         steps = args.mixed_steps if prec == "mixed" and args.mixed_steps else args.steps
         out = step_leg(name, "fp64" if prec == "fp64" else "split_bf16", steps,
-                       args.warmup, 0, 1, 0, walkers=args.profile_walkers)
+                       args.warmup, 0, 1, 0, walkers=args.profile_walkers,
+                       **(DIGITS7 if prec == "digits7" else {}))
     elif leg.startswith("batched"):
         out = batched_leg(0, "fp64" if leg.endswith("fp64") else "split_bf16", 2)
     elif leg == "blocks":
@@ -884,6 +937,15 @@ def run_afq(args):
             split["cpu_baseline"] = dict(line["cpu_baseline"],
                                          note="the FP64 oracle (the split path's reference)")
         line["split_bf16"] = split
+        d7 = step_leg(WORKLOAD, "split_bf16", args.steps, args.warmup, rank, 1, local,
+                      e2e_steps=e2e_steps, **DIGITS7)
+        attach_peak(d7["roofline"], peaks, fp64)
+        d7["speedup_vs_fp64"] = d7["value"] / head["value"] * world
+        d7["precision_note"] = ("split_bf16 with 7 exact 8-bit digits per operand (55 bits) in "
+                                "every tensor-core contraction: FP64 quality, held to the FP64 "
+                                "path's 1e-10 parity tests against the oracle")
+        d7["errors"] = digits7_errors(WORKLOAD, rank)
+        line["split_bf16_7digits"] = d7
         c2 = {}
         for prec in ("fp64", "split_bf16"):
             leg = step_leg("c2", prec, 5 * args.steps, args.warmup, rank, 1, local,

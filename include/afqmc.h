@@ -84,15 +84,20 @@ typedef struct afq_params {
   double fb_cap;       /* |xbar_g| cap; 0 = off                                  */
   int free_projection; /* 1: complex weights w <- w I (no phaseless cut)         */
   int split_slices;    /* AFQ_SPLIT_BF16: digits S per FP64 operand of the force bias
-                          and the exchange, 1..4; 0 = 4.  Force bias and stored
+                          and the exchange, 1..7; 0 = 4.  Force bias and stored
                           exchange: exact 8-bit digits, the products of digit
                           orders s + t <= S - 1 each in its own exact TMEM
-                          accumulator; direct exchange: the same digits stored at
-                          their weights, the leading product in an exact TMEM
-                          accumulator and the smaller ones in a second (FP32)   */
+                          accumulator; direct exchange (S <= 4 only; more digits
+                          take the stored exchange, AFQ_ERR_ARG at afq_init_trial
+                          when it is asked for or does not fit): the same digits
+                          stored at their weights, the leading product in an exact
+                          TMEM accumulator and the smaller ones in a second (FP32).
+                          7 digits (55 bits) with prop_slices = 7 give FP64
+                          quality (the FP64 path's 1e-10 parity with the oracle) */
   int prop_slices;     /* AFQ_SPLIT_BF16: exact 8-bit digits per FP64 operand of the
-                          VHS and propagator GEMMs, 1..4 (per-row power-of-two scale,
-                          one exact TMEM accumulator per digit order); 0 = 4     */
+                          VHS and propagator GEMMs, 1..7 (per-row power-of-two scale,
+                          one exact TMEM accumulator per digit order; the Taylor
+                          powers take fewer where their terms are small); 0 = 4  */
   int exchange;        /* an afq_exchange: algorithm of the exchange energy        */
   int prop_kernel;     /* AFQ_SPLIT_BF16 propagation: 0 = one launch per GEMM pass with
                           digit slicing launches between them (default); 1 = one

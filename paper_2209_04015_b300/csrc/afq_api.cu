@@ -275,8 +275,8 @@ int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
   if (!(ctx->p.dt > 0.0) || ctx->p.taylor_order < 1 || ctx->p.taylor_order > 32 ||
       ctx->p.qr_period < 0 ||
       (ctx->p.precision != AFQ_FP64 && ctx->p.precision != AFQ_SPLIT_BF16) ||
-      ctx->p.split_slices < 1 || ctx->p.split_slices > 4 || ctx->p.prop_slices < 1 ||
-      ctx->p.prop_slices > 4 || ctx->p.exchange < AFQ_EXCHANGE_AUTO ||
+      ctx->p.split_slices < 1 || ctx->p.split_slices > 7 || ctx->p.prop_slices < 1 ||
+      ctx->p.prop_slices > 7 || ctx->p.exchange < AFQ_EXCHANGE_AUTO ||
       ctx->p.exchange > AFQ_EXCHANGE_STORED || ctx->p.prop_kernel < 0 ||
       ctx->p.prop_kernel > 1) {
     delete ctx;
@@ -465,6 +465,16 @@ int afq_init_trial(afq_ctx* ctx, int na, int nb, const double* psi_a, const doub
     const double budget = std::fmin(0.25 * (double)fr, 16.0 * 1073741824.0);
     ctx->ex_stored = ctx->p.exchange == AFQ_EXCHANGE_STORED ||
                      (ctx->p.exchange == AFQ_EXCHANGE_AUTO && vbytes <= budget && M < 1.5 * X);
+    // the direct tensor-core exchange keeps a float tail accumulator (at most 4 digits);
+    // more digits (the FP64-quality setting) take the stored form when it fits at all
+    if (ctx->mixed && ctx->S > 4 && !ctx->ex_stored) {
+      if (ctx->p.exchange == AFQ_EXCHANGE_AUTO && vbytes <= 0.9 * (double)fr)
+        ctx->ex_stored = true;
+      else
+        return afq_fail(ctx, AFQ_ERR_ARG,
+                        "split_slices > 4 needs the stored exchange (the direct tensor-core "
+                        "exchange takes at most 4 digits)");
+    }
     if (ctx->ex_stored) {
       AFQ_TRY(build_exchange_v(ctx));
       const int slots = exchange_v_slots(ctx);

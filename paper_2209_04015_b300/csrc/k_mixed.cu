@@ -253,6 +253,8 @@ __global__ void k_slice_theta_exact(const double2* __restrict__ thetaT, int W, i
   }
 }
 
+constexpr int kFbKbExact = 32;  // K blocks per force-bias split beyond 4 digits
+
 int warp_grid_rows(long rows) {
   const long b = (rows + 7) / 8;  // 8 warps per 256-thread block
   return (int)(b < 1 ? 1 : (b > 148 * 64 ? 148 * 64 : b));
@@ -359,6 +361,9 @@ int mixed_init_walkers(afq_ctx* ctx) {
   const int nkb = N * Mp / kBK;
   const int tiles = ((X + 127) / 128) * ((W2 + ctx->fb_BN - 1) / ctx->fb_BN);
   int ks = (296 + tiles - 1) / tiles;
+  // beyond 4 digits (FP64 quality) each split covers at most 32 K blocks, K = 1024: the
+  // leading digit products' sum, at most 128^2 K = 2^24, stays exact in FP32
+  if (S > 4 && ks < (nkb + kFbKbExact - 1) / kFbKbExact) ks = (nkb + kFbKbExact - 1) / kFbKbExact;
   if (ks > nkb) ks = nkb;
   if (ks < 1) ks = 1;
   ctx->fb_kbper = (nkb + ks - 1) / ks;
@@ -432,7 +437,7 @@ int mixed_autotune(afq_ctx* ctx) {
   int best_kb = kb0;
   float best = 1e30f;
   for (int kb : {kb0, kb0 * 2, kb0 * 4, (kb0 + 1) / 2, (kb0 + 3) / 4}) {
-    if (kb < 1 || kb > nkb) continue;
+    if (kb < 1 || kb > nkb || (ctx->S > 4 && kb > kFbKbExact)) continue;
     const int ks = (nkb + kb - 1) / kb;
     if (ks > cap) continue;
     ctx->fb_kbper = kb;
@@ -495,7 +500,7 @@ int launch_force_bias_tc(afq_ctx* ctx, WalkerSet& s) {
 // ===========================================================================
 extern "C" int afq_gemm_split_bf16(int m, int n, int k, int slices, const double* A_dev,
                                    const double* B_dev, double* C_dev, void* cuda_stream) {
-  if (m < 1 || n < 1 || k < 1 || slices < 1 || slices > kMaxSlices || !A_dev || !B_dev || !C_dev)
+  if (m < 1 || n < 1 || k < 1 || slices < 1 || slices > 4 || !A_dev || !B_dev || !C_dev)
     return AFQ_ERR_ARG;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   const int Kp = round_up(k, kBK);

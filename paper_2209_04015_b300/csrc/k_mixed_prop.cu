@@ -135,14 +135,77 @@ struct PropArgs {
   int* err;
 };
 
+// TMEM load of CW (16 or 8) consecutive columns of this warp's lanes.
+template <int CW>
+__device__ __forceinline__ void prop_tmem_ld(uint32_t taddr, float (&v)[CW]) {
+  if constexpr (CW == 16) {
+    tc::tmem_ld16(taddr, v);
+  } else {
+    uint32_t r[8];
+    tc::tmem_ld8_nowait(taddr, r);
+    tc::tmem_wait_ld();
+    tc::tmem_regs_ready8(r);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  }
+}
+
 __device__ __forceinline__ void prop_epi_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kPropEpi * 32) : "memory");
+}
+
+// Epilogue of one group of CW columns (c0 .. c0 + CW - 1) of this thread's row p (the
+// form the kernel takes beyond 4 digits): real parts first (digits -> FP64), then
+// their imaginary partners, then the pass's output.
+template <int S, int CW>
+__device__ __forceinline__ void prop_epi_group(const PropArgs& a, uint32_t trow, int BN, int brows,
+                                               int c0, int z, int j0, int p, bool valid, int ep) {
+  const int M = a.M, N = a.N;
+  float f[S][CW];
+  double dre[CW];
+#pragma unroll
+  for (int d = 0; d < S; ++d) prop_tmem_ld<CW>(trow + (uint32_t)(d * BN + c0), f[d]);
+#pragma unroll
+  for (int jj = 0; jj < CW; ++jj) {
+    const int j = j0 + c0 + jj;
+    float ar[S];
+#pragma unroll
+    for (int d = 0; d < S; ++d) ar[d] = f[d][jj];
+    dre[jj] = (valid && j < N) ? combine_exact<S>(ar, ep + a.eb[(long)z * N + j] - 14) : 0.0;
+  }
+#pragma unroll
+  for (int d = 0; d < S; ++d) prop_tmem_ld<CW>(trow + (uint32_t)(d * BN + brows + c0), f[d]);
+  if (!valid) return;
+#pragma unroll
+  for (int jj = 0; jj < CW; ++jj) {
+    const int j = j0 + c0 + jj;
+    if (j >= N) continue;
+    float ai[S];
+#pragma unroll
+    for (int d = 0; d < S; ++d) ai[d] = f[d][jj];
+    const int sc = ep + a.eb[(long)z * N + j] - 14;
+    const double dr = dre[jj], di = combine_exact<S>(ai, sc);
+    const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
+    const long iphi = ((long)z * M + p) * N + j;  // [z][p][j]
+    if (a.mode == kModeFirst) {
+      // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
+      a.accT[ia] = make_double2(dr, di);
+    } else if (a.mode == kModeTerm) {
+      // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k to the
+      // FP64 Taylor sum
+      a.tout[ia] = make_double2(dr, di);
+    } else {
+      const double2 acc = a.accT[ia];
+      const double d = a.pdiag[p];
+      a.phi_out[iphi] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
+    }
+  }
 }
 
 template <int S, bool REAL>
 __global__ void __launch_bounds__(32 * kPropWarps, 1)
     k_prop_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const PropArgs a) {
+              const __grid_constant__ PropArgs a) {
   constexpr int kUA = REAL ? 1 : 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -281,44 +344,50 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
       const int ep = valid ? (REAL ? a.ea[p] : a.ea[(long)z * M + p]) : 0;
       const uint32_t trow = tmem + (uint32_t)(buf * S * BN) + ((uint32_t)(32 * lq) << 16);
       for (int c0 = 16 * part; c0 < brows; c0 += 32) {
-        // real parts of 16 columns first (digits -> FP64), then their imaginary partners
-        float f[S][16];
-        double dre[16];
+        if constexpr (S > 4) {
+          // more digits than registers for 16 columns at once: two groups of 8
+          prop_epi_group<S, 8>(a, trow, BN, brows, c0, z, j0, p, valid, ep);
+          prop_epi_group<S, 8>(a, trow, BN, brows, c0 + 8, z, j0, p, valid, ep);
+        } else {
+          // real parts of 16 columns first (digits -> FP64), then their imaginary partners
+          float f[S][16];
+          double dre[16];
 #pragma unroll
-        for (int d = 0; d < S; ++d) tc::tmem_ld16(trow + (uint32_t)(d * BN + c0), f[d]);
+          for (int d = 0; d < S; ++d) tc::tmem_ld16(trow + (uint32_t)(d * BN + c0), f[d]);
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int j = j0 + c0 + jj;
-          float ar[S];
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = j0 + c0 + jj;
+            float ar[S];
 #pragma unroll
-          for (int d = 0; d < S; ++d) ar[d] = f[d][jj];
-          dre[jj] = (valid && j < N) ? combine_exact<S>(ar, ep + a.eb[(long)z * N + j] - 14) : 0.0;
-        }
+            for (int d = 0; d < S; ++d) ar[d] = f[d][jj];
+            dre[jj] = (valid && j < N) ? combine_exact<S>(ar, ep + a.eb[(long)z * N + j] - 14) : 0.0;
+          }
 #pragma unroll
-        for (int d = 0; d < S; ++d) tc::tmem_ld16(trow + (uint32_t)(d * BN + brows + c0), f[d]);
-        if (!valid) continue;
+          for (int d = 0; d < S; ++d) tc::tmem_ld16(trow + (uint32_t)(d * BN + brows + c0), f[d]);
+          if (!valid) continue;
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int j = j0 + c0 + jj;
-          if (j >= N) continue;
-          float ai[S];
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = j0 + c0 + jj;
+            if (j >= N) continue;
+            float ai[S];
 #pragma unroll
-          for (int d = 0; d < S; ++d) ai[d] = f[d][jj];
-          const int sc = ep + a.eb[(long)z * N + j] - 14;
-          const double dr = dre[jj], di = combine_exact<S>(ai, sc);
-          const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
-          const long iphi = ((long)z * M + p) * N + j;  // [z][p][j]
-          if (a.mode == kModeFirst) {
-            // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
-            a.accT[ia] = make_double2(dr, di);
-          } else if (a.mode == kModeTerm) {
-            // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k to
-            // the FP64 Taylor sum
-            a.tout[ia] = make_double2(dr, di);
-          } else {
-            const double2 acc = a.accT[ia];
-            const double d = a.pdiag[p];
-            a.phi_out[iphi] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
+            for (int d = 0; d < S; ++d) ai[d] = f[d][jj];
+            const int sc = ep + a.eb[(long)z * N + j] - 14;
+            const double dr = dre[jj], di = combine_exact<S>(ai, sc);
+            const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
+            const long iphi = ((long)z * M + p) * N + j;  // [z][p][j]
+            if (a.mode == kModeFirst) {
+              // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
+              a.accT[ia] = make_double2(dr, di);
+            } else if (a.mode == kModeTerm) {
+              // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k to
+              // the FP64 Taylor sum
+              a.tout[ia] = make_double2(dr, di);
+            } else {
+              const double2 acc = a.accT[ia];
+              const double d = a.pdiag[p];
+              a.phi_out[iphi] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
+            }
           }
         }
       }
@@ -656,8 +725,9 @@ void mixed_prop_free(afq_ctx* ctx) {
 // Digits per pass.  A Taylor power u_k = V u_{k-1} enters the sum scaled by
 // g_k = dt^(k/2) / k!, so with x = sqrt(dt) |V|_2 the term is at most x^k / k! of Phi,
 // and cutting both its operands to S exact digits costs about 2^-(8S-1) of the term.
-// Each power gets the fewest digits that keep this below 2^-31 of Phi (the level of
-// the leading term with 4 digits); the P passes keep all Sp.  |V|_2 is estimated at
+// Each power gets the fewest digits that keep this below 2^-(8 Sp - 1) of Phi (the
+// level of the leading term with Sp digits: 2^-31 with 4, 2^-55 with 7); the P passes
+// keep all Sp.  |V|_2 is estimated at
 // set-up by power iteration on V = sum_g y_g L_g for four seeded N(0,1) field draws,
 // times 1.5 for the force-bias shift and the spread over walkers (a term whose x is
 // twice the estimate still stays near 2^-30).
@@ -733,7 +803,7 @@ int prop_digit_schedule(afq_ctx* ctx) {
     term *= x / k;
     int S = Sp;
     if (std::isfinite(term) && term > 0.0) {
-      S = (int)std::ceil((32.0 + std::log2(term)) / 8.0);
+      S = (int)std::ceil((8.0 * Sp + std::log2(term)) / 8.0);
       if (S < 1) S = 1;
       if (S > Sp) S = Sp;
     }
@@ -791,8 +861,12 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_a, (size_t)W * M * sizeof(int)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_t[0], (size_t)W * N * sizeof(int)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_t[1], (size_t)W * N * sizeof(int)));
-  ctx->vhs_BN = 2 * W >= 128 ? 128 : round_up(2 * W, 16);
+  // tiles whose S digit accumulators fit the 512 TMEM columns: the VHS's BN <= 512 / S,
+  // the propagation's 2 x prop_rows <= 512 / S (64 walker columns up to 4 digits)
+  const int vhs_cap = (512 / S) / 16 * 16, rows_cap = (256 / S) / 16 * 16;
+  ctx->vhs_BN = 2 * W >= vhs_cap ? (vhs_cap < 128 ? vhs_cap : 128) : round_up(2 * W, 16);
   ctx->prop_rows = N >= kPropRows ? kPropRows : round_up(N, 16);
+  if (ctx->prop_rows > rows_cap) ctx->prop_rows = rows_cap;
   if (S * ctx->vhs_BN > 512 || 2 * S * ctx->prop_rows > 512)
     return afq_fail(ctx, AFQ_ERR_ARG, "split propagation: too many slices for TMEM");
   const uint32_t brows = (uint32_t)ctx->prop_rows;
@@ -924,6 +998,9 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
     case 2: e = launch_prop_s<2, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
     case 3: e = launch_prop_s<3, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
     case 4: e = launch_prop_s<4, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
+    case 5: e = launch_prop_s<5, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
+    case 6: e = launch_prop_s<6, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
+    case 7: e = launch_prop_s<7, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
   }
   ctx->launches++;
   if (e != cudaSuccess)

@@ -29,7 +29,7 @@ constexpr int kThreads = 128;
 constexpr int kBK = 32;           // K elements per block: one 64-byte row
 constexpr int kASlot = 128 * 64;  // bytes of one 128-row A unit of one K block
 constexpr int kMaxStages = 4;
-constexpr int kMaxSlices = 4;
+constexpr int kMaxSlices = 7;  // 7 exact 8-bit digits: 55 bits, FP64 quality
 constexpr size_t kSmemLimit = 227 * 1024;
 
 struct TcCommon {
@@ -148,7 +148,7 @@ __device__ __forceinline__ void split_exact(double x, int e, int S, __nv_bfloat1
     const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
     const int sh = E - 1075 + 7 - e + 8 * (S - 1);  // value = mant 2^(E-1075)
     if (sh >= 0)
-      v = sh < 10 ? mant << sh : 0;  // cannot happen for |x| <= 2^e and S <= 4
+      v = sh < 10 ? mant << sh : 0;  // |x| <= 2^e: sh <= 8 S - 54 (v < 2^(8 S - 1))
     else if (sh > -64)
       v = (mant + (1LL << (-sh - 1))) >> (-sh);
   }
@@ -208,16 +208,32 @@ __device__ __forceinline__ void split_scaled(double x, int e, int S, __nv_bfloat
 }
 
 // Recombines the S exact diagonal accumulators of one element:
-// value = 2^scale_exp sum_d acc_d 256^-d, through one int64 and one conversion.
+// value = 2^scale_exp sum_d acc_d 256^-d, through one int64 and one conversion for
+// S <= 4; for more digits (whose weighted sum would overflow an int64) through two:
+// the leading S - 3 diagonals and the last 3, each exact in FP64, added once.
+__device__ __forceinline__ double ll_scaled(long long t, int e) {
+  if (t == 0) return 0.0;
+  return __longlong_as_double(__double_as_longlong(__ll2double_rn(t)) + ((long long)e << 52));
+}
 template <int S>
 __device__ __forceinline__ double combine_exact(const float (&acc)[S], int scale_exp) {
-  long long t = 0;
+  if constexpr (S <= 4) {
+    long long t = 0;
 #pragma unroll
-  for (int d = 0; d < S; ++d) t += (long long)__float2int_rn(acc[d]) * (1LL << (8 * (S - 1 - d)));
-  if (t == 0) return 0.0;
-  const double v = __ll2double_rn(t);
-  return __longlong_as_double(__double_as_longlong(v) +
-                              ((long long)(scale_exp - 8 * (S - 1)) << 52));
+    for (int d = 0; d < S; ++d) t += (long long)__float2int_rn(acc[d]) * (1LL << (8 * (S - 1 - d)));
+    if (t == 0) return 0.0;
+    const double v = __ll2double_rn(t);
+    return __longlong_as_double(__double_as_longlong(v) +
+                                ((long long)(scale_exp - 8 * (S - 1)) << 52));
+  } else {
+    constexpr int H = S - 3;
+    long long hi = 0, lo = 0;
+#pragma unroll
+    for (int d = 0; d < H; ++d) hi += (long long)__float2int_rn(acc[d]) * (1LL << (8 * (H - 1 - d)));
+#pragma unroll
+    for (int d = H; d < S; ++d) lo += (long long)__float2int_rn(acc[d]) * (1LL << (8 * (S - 1 - d)));
+    return ll_scaled(hi, scale_exp - 8 * (H - 1)) + ll_scaled(lo, scale_exp - 8 * (S - 1));
+  }
 }
 
 __device__ __forceinline__ void tmem_row16(uint32_t tmem, int warp, int c0, float (&v)[16]) {
@@ -436,6 +452,9 @@ cudaError_t launch_tc_s(int S, dim3 grid, size_t smem, cudaStream_t stream, cons
     case 2: return launch_tc<2, P>(grid, smem, stream, a, b, args);
     case 3: return launch_tc<3, P>(grid, smem, stream, a, b, args);
     case 4: return launch_tc<4, P>(grid, smem, stream, a, b, args);
+    case 5: return launch_tc<5, P>(grid, smem, stream, a, b, args);
+    case 6: return launch_tc<6, P>(grid, smem, stream, a, b, args);
+    case 7: return launch_tc<7, P>(grid, smem, stream, a, b, args);
   }
   return cudaErrorInvalidValue;
 }
