@@ -139,7 +139,8 @@ __global__ void k_slice_real(const double* __restrict__ in, long ld, long rows, 
 }
 
 // Rows of K doubles (row pitch ld) -> S planes of scaled digits (split_scaled) of
-// rows x Kp, zero for k >= K, with one exponent per row (one warp per row)
+// rows x Kp, zero for k >= K, with one exponent per row (one warp per row); for the
+// direct exchange, which takes at most 4 digits
 __global__ void k_slice_rows_scaled(const double* __restrict__ in, long ld, long rows, int K,
                                     int Kp, int S, __nv_bfloat16* __restrict__ out) {
   const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
@@ -150,7 +151,8 @@ __global__ void k_slice_rows_scaled(const double* __restrict__ in, long ld, long
     int m = 0;
     for (int k = lane; k < K; k += 32) m = max(m, exp_field(row[k]));
     const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
-    for (int k = lane; k < Kp; k += 32) split_scaled(k < K ? row[k] : 0.0, e, S, out + r * Kp + k, plane);
+    for (int k = lane; k < Kp; k += 32)
+      split_scaled<kFastSlices>(k < K ? row[k] : 0.0, e, S, out + r * Kp + k, plane);
   }
 }
 
@@ -166,8 +168,8 @@ __global__ void k_slice_theta_scaled(const double2* __restrict__ thetaT, int W, 
     const int j = (int)(r / Mpad), p = (int)(r % Mpad);
     const double2 v = p < M ? thetaT[(z * N + j) * M + p] : make_double2(0.0, 0.0);
     __nv_bfloat16* o = out + (2 * z) * NMp + r;
-    split_scaled(v.x, eb[2 * z], S, o, plane);
-    split_scaled(v.y, eb[2 * z + 1], S, o + NMp, plane);
+    split_scaled<kFastSlices>(v.x, eb[2 * z], S, o, plane);
+    split_scaled<kFastSlices>(v.y, eb[2 * z + 1], S, o + NMp, plane);
   }
 }
 
@@ -237,7 +239,8 @@ __global__ void __launch_bounds__(256) k_theta_exponents(const double2* __restri
 }
 
 // theta^T (W x N x M complex) -> integer digit planes [s][z][re/im][N Mpad] with the
-// exponents above (zero padding); one thread per (z, j, p < Mpad)
+// exponents above (zero padding); one thread per (z, j, p < Mpad); D >= S
+template <int D>
 __global__ void k_slice_theta_exact(const double2* __restrict__ thetaT, int W, int N, int M,
                                     int Mpad, int S, const int* __restrict__ eb,
                                     __nv_bfloat16* __restrict__ out) {
@@ -248,8 +251,8 @@ __global__ void k_slice_theta_exact(const double2* __restrict__ thetaT, int W, i
     const int j = (int)(r / Mpad), p = (int)(r % Mpad);
     const double2 v = p < M ? thetaT[(z * N + j) * M + p] : make_double2(0.0, 0.0);
     __nv_bfloat16* o = out + (2 * z) * NMp + r;
-    split_exact(v.x, eb[2 * z], S, o, plane);
-    split_exact(v.y, eb[2 * z + 1], S, o + NMp, plane);
+    split_exact<D>(v.x, eb[2 * z], S, o, plane);
+    split_exact<D>(v.y, eb[2 * z + 1], S, o + NMp, plane);
   }
 }
 
@@ -458,8 +461,9 @@ int mixed_autotune(afq_ctx* ctx) {
 int launch_slice_theta(afq_ctx* ctx, WalkerSet& s) {
   k_theta_exponents<<<s.W, 256, 0, ctx->stream>>>(s.thetaT, (long)ctx->N * ctx->M, ctx->exv_eb);
   AFQ_LAUNCHED(ctx);
-  k_slice_theta_exact<<<grid1d((long)s.W * ctx->N * ctx->Mpad), 256, 0, ctx->stream>>>(
-      s.thetaT, s.W, ctx->N, ctx->M, ctx->Mpad, ctx->S, ctx->exv_eb, ctx->exv_th);
+  (ctx->S <= kFastSlices ? k_slice_theta_exact<kFastSlices> : k_slice_theta_exact<kMaxSlices>)
+      <<<grid1d((long)s.W * ctx->N * ctx->Mpad), 256, 0, ctx->stream>>>(
+          s.thetaT, s.W, ctx->N, ctx->M, ctx->Mpad, ctx->S, ctx->exv_eb, ctx->exv_th);
   AFQ_LAUNCHED(ctx);
   if (ctx->th_sl) {
     const long total = (long)s.W * ctx->N * ctx->Mpad;

@@ -409,7 +409,8 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int warp_max_int(int v) { return __reduce_max_sync(0xffffffffu, v); }
 
-// y (W x X complex) -> rows (z, re/im) of K = X, padded to Xpad
+// y (W x X complex) -> rows (z, re/im) of K = X, padded to Xpad (D >= S: digit loop bound)
+template <int D>
 __global__ void k_slice_y(const double2* __restrict__ y, int W, int X, int Xpad, int S,
                           __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
   const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
@@ -424,12 +425,13 @@ __global__ void k_slice_y(const double2* __restrict__ y, int W, int X, int Xpad,
     const int e = row_exponent_field(warp_max_int(m));
     if (lane == 0) eout[r] = e;
     for (int g = lane; g < Xpad; g += 32)
-      split_exact(g < X ? row[2 * g] : 0.0, e, S, out + r * Xpad + g, plane);
+      split_exact<D>(g < X ? row[2 * g] : 0.0, e, S, out + r * Xpad + g, plane);
   }
 }
 
 // complex rows (z, i), i < R, K elements each -> planes [s][z][re/im][i][Kp]; one
 // exponent per complex row, shared by its real and imaginary parts
+template <int D>
 __global__ void k_slice_cplx(const double2* __restrict__ in, long rows, int R, int K, int Kp, int S,
                              __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
   const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
@@ -446,8 +448,8 @@ __global__ void k_slice_cplx(const double2* __restrict__ in, long rows, int R, i
     __nv_bfloat16* oim = ore + (long)R * Kp;
     for (int k = lane; k < Kp; k += 32) {
       const double2 v = k < K ? row[k] : make_double2(0.0, 0.0);
-      split_exact(v.x, e, S, ore + k, plane);
-      split_exact(v.y, e, S, oim + k, plane);
+      split_exact<D>(v.x, e, S, ore + k, plane);
+      split_exact<D>(v.y, e, S, oim + k, plane);
     }
   }
 }
@@ -457,7 +459,7 @@ int warp_grid(long rows);
 // One-pass form of k_slice_cplx for rows of K <= 64 NP: each lane holds NP pairs of
 // consecutive elements in registers (one read of the row), the warp takes the row
 // exponent, and every digit plane is written as bfloat16 pairs (128-byte warp stores).
-template <int NP>
+template <int NP, int D>
 __global__ void __launch_bounds__(256) k_slice_cplx1(const double2* __restrict__ in, long rows,
                                                      int R, int K, int Kp, int S,
                                                      __nv_bfloat16* __restrict__ out,
@@ -487,14 +489,14 @@ __global__ void __launch_bounds__(256) k_slice_cplx1(const double2* __restrict__
     for (int t = 0; t < NP; ++t) {
       const int k = 2 * lane + 64 * t;
       if (k >= Kp) continue;
-      int q0[kMaxSlices], q1[kMaxSlices];
+      int q0[D], q1[D];
 #pragma unroll
       for (int part = 0; part < 2; ++part) {
-        exact_digits(part ? v[t][0].y : v[t][0].x, e, S, q0);
-        exact_digits(part ? v[t][1].y : v[t][1].x, e, S, q1);
+        exact_digits<D>(part ? v[t][0].y : v[t][0].x, e, S, q0);
+        exact_digits<D>(part ? v[t][1].y : v[t][1].x, e, S, q1);
         __nv_bfloat16* o = (part ? oim : ore) + k;
 #pragma unroll
-        for (int s = 0; s < kMaxSlices; ++s)
+        for (int s = 0; s < D; ++s)
           if (s < S)
             *reinterpret_cast<__nv_bfloat162*>(o + s * plane) =
                 __floats2bfloat162_rn((float)q0[s], (float)q1[s]);
@@ -508,7 +510,7 @@ __global__ void __launch_bounds__(256) k_slice_cplx1(const double2* __restrict__
 // the last term (last != 0), the digits of the finished sum acc for the second
 // one-body half.  kmod = k mod 4 selects the rotation i^k; kscale (M values, or NULL)
 // scales element p of every row first (the diagonal of P in the first call).
-template <int NP>
+template <int NP, int D>
 __global__ void __launch_bounds__(256) k_taylor_slice(const double2* __restrict__ in,
                                                       double2* __restrict__ acc, long rows,
                                                       int R, int K, int Kp, int S, double gk,
@@ -561,14 +563,14 @@ __global__ void __launch_bounds__(256) k_taylor_slice(const double2* __restrict_
     for (int t = 0; t < NP; ++t) {
       const int k = 2 * lane + 64 * t;
       if (k >= Kp) continue;
-      int q0[kMaxSlices], q1[kMaxSlices];
+      int q0[D], q1[D];
 #pragma unroll
       for (int part = 0; part < 2; ++part) {
-        exact_digits(part ? v[t][0].y : v[t][0].x, e, S, q0);
-        exact_digits(part ? v[t][1].y : v[t][1].x, e, S, q1);
+        exact_digits<D>(part ? v[t][0].y : v[t][0].x, e, S, q0);
+        exact_digits<D>(part ? v[t][1].y : v[t][1].x, e, S, q1);
         __nv_bfloat16* o = (part ? oim : ore) + k;
 #pragma unroll
-        for (int s = 0; s < kMaxSlices; ++s)
+        for (int s = 0; s < D; ++s)
           if (s < S)
             *reinterpret_cast<__nv_bfloat162*>(o + s * plane) =
                 __floats2bfloat162_rn((float)q0[s], (float)q1[s]);
@@ -602,17 +604,26 @@ __global__ void k_taylor_acc(const double2* __restrict__ u, double2* __restrict_
 
 // Digits of complex rows (z, i) of K elements into planes [s][z][re/im][i][Kp]: the
 // one-pass kernel for K <= 1024, else the two-pass one.
-void slice_rows(const double2* in, long rows, int R, int K, int Kp, int S,
-                __nv_bfloat16* out, int* eout, cudaStream_t st) {
+template <int D>
+void slice_rows_d(const double2* in, long rows, int R, int K, int Kp, int S,
+                  __nv_bfloat16* out, int* eout, cudaStream_t st) {
   const int g = warp_grid(rows);
   if (Kp <= 128)
-    k_slice_cplx1<2><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+    k_slice_cplx1<2, D><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
   else if (Kp <= 256)
-    k_slice_cplx1<4><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+    k_slice_cplx1<4, D><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
   else if (Kp <= 512)
-    k_slice_cplx1<8><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+    k_slice_cplx1<8, D><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
   else
-    k_slice_cplx<<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+    k_slice_cplx<D><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+}
+
+void slice_rows(const double2* in, long rows, int R, int K, int Kp, int S,
+                __nv_bfloat16* out, int* eout, cudaStream_t st) {
+  if (S <= kFastSlices)
+    slice_rows_d<kFastSlices>(in, rows, R, K, Kp, S, out, eout, st);
+  else
+    slice_rows_d<kMaxSlices>(in, rows, R, K, Kp, S, out, eout, st);
 }
 
 // Phi (W x M x N) -> W x N x M (transposed copy, FP64)
@@ -910,8 +921,14 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
 // factor i sqrt(dt) of A_z = i sqrt(dt) V_z is applied by the Taylor epilogue.
 int launch_vhs_tc(afq_ctx* ctx) {
   const int W = ctx->ws.W, M = ctx->M, S = ctx->Sp;
-  k_slice_y<<<warp_grid(2L * W), 256, 0, ctx->stream>>>(ctx->y, W, ctx->X, ctx->Xpad, S,
-                                                       ctx->y_sl, ctx->e_y);
+  if (S <= kFastSlices)
+    k_slice_y<kFastSlices><<<warp_grid(2L * W), 256, 0, ctx->stream>>>(ctx->y, W, ctx->X,
+                                                                      ctx->Xpad, S, ctx->y_sl,
+                                                                      ctx->e_y);
+  else
+    k_slice_y<kMaxSlices><<<warp_grid(2L * W), 256, 0, ctx->stream>>>(ctx->y, W, ctx->X,
+                                                                     ctx->Xpad, S, ctx->y_sl,
+                                                                     ctx->e_y);
   AFQ_LAUNCHED(ctx);
   VhsP::Args a{};
   a.c.nkb = ctx->Xpad / kBK;
@@ -1015,15 +1032,16 @@ int taylor_slice(afq_ctx* ctx, int b, double gk, int kmod, int last, int S,
   const int W = ctx->ws.W, N = ctx->N, M = ctx->M, Kp = ctx->Mpad;
   const long rows = (long)W * N;
   const int g = warp_grid(rows);
+  const bool fast = S <= kFastSlices;
   if (Kp <= 128)
-    k_taylor_slice<2><<<g, 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows, N, M, Kp, S, gk,
-                                                  kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+    (fast ? k_taylor_slice<2, kFastSlices> : k_taylor_slice<2, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
   else if (Kp <= 256)
-    k_taylor_slice<4><<<g, 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows, N, M, Kp, S, gk,
-                                                  kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+    (fast ? k_taylor_slice<4, kFastSlices> : k_taylor_slice<4, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
   else if (Kp <= 512)
-    k_taylor_slice<8><<<g, 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows, N, M, Kp, S, gk,
-                                                  kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+    (fast ? k_taylor_slice<8, kFastSlices> : k_taylor_slice<8, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
   else {
     k_taylor_acc<<<grid1d(rows * M), 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows * M, M,
                                                             gk, kmod, kscale);

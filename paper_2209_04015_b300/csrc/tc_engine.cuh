@@ -30,6 +30,7 @@ constexpr int kBK = 32;           // K elements per block: one 64-byte row
 constexpr int kASlot = 128 * 64;  // bytes of one 128-row A unit of one K block
 constexpr int kMaxStages = 4;
 constexpr int kMaxSlices = 7;  // 7 exact 8-bit digits: 55 bits, FP64 quality
+constexpr int kFastSlices = 4;  // digit loop bound of the per-step slicing kernels when S <= 4
 constexpr size_t kSmemLimit = 227 * 1024;
 
 struct TcCommon {
@@ -138,7 +139,10 @@ __device__ __forceinline__ int row_exponent_field(int emax) { return emax ? emax
 // Integer digits of x relative to the row scale 2^e (|x| <= 2^e):
 // x ~ 2^(e-7) sum_s q_s 256^-s with balanced digits q_s in [-128, 128] (exact in
 // bfloat16), written S planes apart.  Rounds x 2^(7-e+8(S-1)) to the nearest
-// integer and cuts it into base-256 digits.
+// integer and cuts it into base-256 digits.  D >= S bounds the unrolled digit loops:
+// the per-step slicing kernels take D = kFastSlices when S <= 4, so that the digit
+// counts beyond 4 cost them neither registers nor instructions.
+template <int D = kMaxSlices>
 __device__ __forceinline__ void split_exact(double x, int e, int S, __nv_bfloat16* out,
                                             long plane) {
   const long long bits = __double_as_longlong(x);
@@ -153,9 +157,9 @@ __device__ __forceinline__ void split_exact(double x, int e, int S, __nv_bfloat1
       v = (mant + (1LL << (-sh - 1))) >> (-sh);
   }
   const bool neg = bits < 0;
-  int q[kMaxSlices];
+  int q[D];
 #pragma unroll
-  for (int s = kMaxSlices - 1; s >= 0; --s) {
+  for (int s = D - 1; s >= 0; --s) {
     if (s >= S) continue;
     int d = (int)(v & 255);
     if (d > 128) d -= 256;
@@ -163,12 +167,13 @@ __device__ __forceinline__ void split_exact(double x, int e, int S, __nv_bfloat1
     v = (v - d) >> 8;
   }
 #pragma unroll
-  for (int s = 0; s < kMaxSlices; ++s)
+  for (int s = 0; s < D; ++s)
     if (s < S) out[s * plane] = __float2bfloat16_rn((float)(neg ? -q[s] : q[s]));
 }
 
-// The same digits returned in q[0..S-1] (q[s] = digit of weight 256^-s).
-__device__ __forceinline__ void exact_digits(double x, int e, int S, int (&q)[kMaxSlices]) {
+// The same digits returned in q[0..S-1] (q[s] = digit of weight 256^-s; S <= D).
+template <int D>
+__device__ __forceinline__ void exact_digits(double x, int e, int S, int (&q)[D]) {
   const long long bits = __double_as_longlong(x);
   const int E = (int)((bits >> 52) & 0x7FF);
   long long v = 0;
@@ -182,7 +187,7 @@ __device__ __forceinline__ void exact_digits(double x, int e, int S, int (&q)[kM
   }
   const bool neg = bits < 0;
 #pragma unroll
-  for (int s = kMaxSlices - 1; s >= 0; --s) {
+  for (int s = D - 1; s >= 0; --s) {
     q[s] = 0;
     if (s >= S) continue;
     int d = (int)(v & 255);
@@ -198,12 +203,13 @@ __device__ __forceinline__ void exact_digits(double x, int e, int S, int (&q)[kM
 // them can keep the leading product (0, 0) -- a sum of integer multiples of one power
 // of two, exact in FP32 -- in one accumulator and every smaller product in another,
 // whose FP32 rounding then only touches digits ~2^-8 below the leading ones.
+template <int D = kMaxSlices>
 __device__ __forceinline__ void split_scaled(double x, int e, int S, __nv_bfloat16* out,
                                              long plane) {
-  int q[kMaxSlices];
-  exact_digits(x, e, S, q);
+  int q[D];
+  exact_digits<D>(x, e, S, q);
 #pragma unroll
-  for (int s = 0; s < kMaxSlices; ++s)
+  for (int s = 0; s < D; ++s)
     if (s < S) out[s * plane] = __float2bfloat16_rn(ldexpf((float)q[s], e - 7 - 8 * s));
 }
 
