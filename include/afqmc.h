@@ -352,6 +352,18 @@ typedef struct afq_batch afq_batch;
 int afq_batch_create(afq_batch** batch, int n, afq_ctx* const* ctxs);
 int afq_batch_destroy(afq_batch* batch);
 const char* afq_batch_last_error(const afq_batch* batch);
+/* Launch layout of the next afq_batch_capture (Eq. Bx and the Taylor walker update
+   of Sec. "Review of AFQMC", per system).  grouped = 0 (default): every system's
+   step is its own graph branch.  grouped = 1 (FP64 contexts only, else
+   AFQ_ERR_ARG): per step the fields of every system run on its branch, then ONE
+   persistent launch builds the VHS of all systems and ONE propagates all their
+   walkers -- CTAs take tiles of every system from a per-system descriptor table
+   (M, N, X, W, device pointers) in order of decreasing cost, the next tile from a
+   device counter -- and the rest of the step and the local energy run on the
+   branches.  Results are bit-identical to the per-system launches.  The tables
+   hold the contexts' current device buffers: re-capture after afq_init_walkers or
+   afq_set_state changes a walker count. */
+int afq_batch_set_grouped(afq_batch* batch, int grouped);
 /* Capture nsteps steps + local energies of every system (same rules as
    afq_graph_capture, for each context). */
 int afq_batch_capture(afq_batch* batch, int nsteps);

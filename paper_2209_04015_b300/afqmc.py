@@ -91,6 +91,7 @@ _SIGS = {
     "afq_batch_destroy": (ctypes.c_int, [_P]),
     "afq_batch_last_error": (ctypes.c_char_p, [_P]),
     "afq_batch_capture": (ctypes.c_int, [_P, ctypes.c_int]),
+    "afq_batch_set_grouped": (ctypes.c_int, [_P, ctypes.c_int]),
     "afq_batch_launch": (ctypes.c_int, [_P, ctypes.c_int]),
     "afq_batch_synchronize": (ctypes.c_int, [_P]),
     "afq_autotune": (ctypes.c_int, [_P]),
@@ -455,10 +456,12 @@ class AfqContext:
 
 
 class AfqBatch:
-    """Several contexts stepped by one CUDA graph, one concurrent branch per system
-    (wraps afq_batch*).  The contexts must outlive the batch."""
+    """Several contexts stepped by one CUDA graph (wraps afq_batch*): one concurrent
+    branch per system, or with grouped=True (FP64 contexts) one persistent launch
+    each for the VHS build and the propagation of all systems per step.  The
+    contexts must outlive the batch."""
 
-    def __init__(self, contexts: list[AfqContext]):
+    def __init__(self, contexts: list[AfqContext], grouped: bool = False):
         self.lib = load_library()
         self.contexts = list(contexts)
         arr = (_P * len(self.contexts))(*[c.h for c in self.contexts])
@@ -467,6 +470,13 @@ class AfqBatch:
         if rc != AFQ_OK:
             raise AfqError(rc, "afq_batch_create failed")
         self.h = h
+        if grouped:
+            self.set_grouped(True)
+
+    def set_grouped(self, grouped: bool) -> None:
+        """Launch layout of the next capture: per-system branches, or (FP64 contexts)
+        grouped VHS and propagation launches over all systems."""
+        self._check(self.lib.afq_batch_set_grouped(self.h, int(bool(grouped))))
 
     def _check(self, rc: int) -> None:
         if rc != AFQ_OK:

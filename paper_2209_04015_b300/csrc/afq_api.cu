@@ -220,9 +220,24 @@ bool symmetric(const double* a, int M, double* dev_out) {
 }
 
 // One hybrid-propagation step (Sec. "Review of AFQMC") on the context's stream.
-int one_step(afq_ctx* ctx, const double* xi_dev, const double* e_shift_dev = nullptr) {
+// A step in three parts: the fields, the VHS build and propagation (which a batch in
+// grouped mode launches for all its systems at once), and the rest.
+int step_fields(afq_ctx* ctx, const double* xi_dev) {
+  return timed(ctx, AFQ_K_FIELDS, [&] { return launch_fields(ctx, xi_dev); });
+}
+
+int step_finish(afq_ctx* ctx, const double* e_shift_dev) {
   const double log_const = -ctx->p.dt * (ctx->e0 - 0.5 * ctx->sum_vbar2 - ctx->e_shift);
-  AFQ_TRY(timed(ctx, AFQ_K_FIELDS, [&] { return launch_fields(ctx, xi_dev); }));
+  AFQ_TRY(green_and_bias(ctx, ctx->ws));
+  AFQ_TRY(timed(ctx, AFQ_K_WEIGHTS, [&] { return launch_weights(ctx, log_const, e_shift_dev); }));
+  ctx->step++;
+  if (ctx->p.qr_period > 0 && ctx->step % (uint64_t)ctx->p.qr_period == 0)
+    AFQ_TRY(timed(ctx, AFQ_K_QR, [&] { return launch_qr(ctx, ctx->ws, ctx->A); }));
+  return AFQ_OK;
+}
+
+int one_step(afq_ctx* ctx, const double* xi_dev, const double* e_shift_dev = nullptr) {
+  AFQ_TRY(step_fields(ctx, xi_dev));
   if (ctx->mixed) {
     AFQ_TRY(timed(ctx, AFQ_K_VHS, [&] { return launch_vhs_tc(ctx); }));
     AFQ_TRY(timed(ctx, AFQ_K_PROPAGATE, [&] { return launch_propagate_tc(ctx); }));
@@ -230,12 +245,7 @@ int one_step(afq_ctx* ctx, const double* xi_dev, const double* e_shift_dev = nul
     AFQ_TRY(timed(ctx, AFQ_K_VHS, [&] { return launch_vhs_fp64(ctx); }));
     AFQ_TRY(timed(ctx, AFQ_K_PROPAGATE, [&] { return launch_propagate_fp64(ctx); }));
   }
-  AFQ_TRY(green_and_bias(ctx, ctx->ws));
-  AFQ_TRY(timed(ctx, AFQ_K_WEIGHTS, [&] { return launch_weights(ctx, log_const, e_shift_dev); }));
-  ctx->step++;
-  if (ctx->p.qr_period > 0 && ctx->step % (uint64_t)ctx->p.qr_period == 0)
-    AFQ_TRY(timed(ctx, AFQ_K_QR, [&] { return launch_qr(ctx, ctx->ws, ctx->A); }));
-  return AFQ_OK;
+  return step_finish(ctx, e_shift_dev);
 }
 
 }  // namespace
@@ -890,6 +900,8 @@ struct afq_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int nsteps = 0;
+  int grouped = 0;              // 1: VHS and propagation as grouped launches (FP64)
+  GroupedStep* gs = nullptr;    // their descriptor tables (built at capture)
   std::string err;
 };
 
@@ -907,6 +919,58 @@ int record_steps(afq_ctx* ctx, int nsteps) {
   }
   ctx->capturing = false;
   ctx->step = step0;
+  return rc;
+}
+
+// Stage-major recording of a batch in grouped mode, on the batch's streams (being
+// captured from b->origin): per step, every system's fields on its own branch, the
+// grouped VHS build and propagation of all systems on the origin stream, then the
+// rest of every system's step and its local energy on the branches again.
+int record_grouped(afq_batch* b, int nsteps) {
+  const size_t n = b->ctx.size();
+  std::vector<cudaStream_t> own(n);
+  std::vector<uint64_t> step0(n);
+  for (size_t i = 0; i < n; ++i) {
+    own[i] = b->ctx[i]->stream;
+    step0[i] = b->ctx[i]->step;
+    b->ctx[i]->stream = b->streams[i];
+    b->ctx[i]->capturing = true;
+  }
+  auto fork = [&]() {
+    if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) return AFQ_ERR_CUDA;
+    for (size_t i = 0; i < n; ++i)
+      if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) return AFQ_ERR_CUDA;
+    return AFQ_OK;
+  };
+  auto join = [&]() {
+    for (size_t i = 0; i < n; ++i)
+      if (cudaEventRecord(b->events[i], b->streams[i]) != cudaSuccess ||
+          cudaStreamWaitEvent(b->origin, b->events[i], 0) != cudaSuccess)
+        return AFQ_ERR_CUDA;
+    return AFQ_OK;
+  };
+  int rc = AFQ_OK;
+  for (int k = 0; k < nsteps && rc == AFQ_OK; ++k) {
+    rc = fork();
+    for (size_t i = 0; i < n && rc == AFQ_OK; ++i) rc = step_fields(b->ctx[i], nullptr);
+    if (rc == AFQ_OK) rc = join();
+    if (rc == AFQ_OK && (grouped_step_vhs(b->gs, b->origin) != cudaSuccess ||
+                         grouped_step_propagate(b->gs, b->origin) != cudaSuccess))
+      rc = AFQ_ERR_CUDA;
+    if (rc == AFQ_OK) rc = fork();
+    for (size_t i = 0; i < n && rc == AFQ_OK; ++i) {
+      rc = step_finish(b->ctx[i], nullptr);
+      if (rc == AFQ_OK) rc = energy_impl(b->ctx[i]);
+      if (rc != AFQ_OK) b->err = b->ctx[i]->err;
+    }
+    if (rc == AFQ_OK) rc = join();
+  }
+  for (size_t i = 0; i < n; ++i) {
+    b->ctx[i]->stream = own[i];
+    b->ctx[i]->capturing = false;
+    b->ctx[i]->step = step0[i];
+  }
+  if (rc != AFQ_OK && b->err.empty()) b->err = "grouped capture failed";
   return rc;
 }
 
@@ -1032,6 +1096,7 @@ int afq_batch_destroy(afq_batch* b) {
   if (b->origin) cudaStreamSynchronize(b->origin);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  grouped_step_free(b->gs);
   for (auto s : b->streams)
     if (s) cudaStreamDestroy(s);
   for (auto e : b->events)
@@ -1043,6 +1108,18 @@ int afq_batch_destroy(afq_batch* b) {
 }
 
 const char* afq_batch_last_error(const afq_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int afq_batch_set_grouped(afq_batch* b, int grouped) {
+  if (!b || (grouped != 0 && grouped != 1)) return AFQ_ERR_ARG;
+  if (grouped)
+    for (auto* c : b->ctx)
+      if (c->mixed) {
+        b->err = "grouped launches take FP64 contexts";
+        return AFQ_ERR_ARG;
+      }
+  b->grouped = grouped;
+  return AFQ_OK;
+}
 
 int afq_batch_capture(afq_batch* b, int nsteps) {
   if (!b) return AFQ_ERR_ARG;
@@ -1058,13 +1135,20 @@ int afq_batch_capture(afq_batch* b, int nsteps) {
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
+  grouped_step_free(b->gs);
+  b->gs = nullptr;
+  if (b->grouped) {  // descriptor tables of the current walker buffers
+    const int rc = grouped_step_create(&b->gs, b->ctx.data(), (int)b->ctx.size(), &b->err);
+    if (rc != AFQ_OK) return rc;
+  }
   if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     b->err = "begin capture";
     return AFQ_ERR_CUDA;
   }
   int rc = cudaEventRecord(b->fork, b->origin) == cudaSuccess ? AFQ_OK : AFQ_ERR_CUDA;
+  if (rc == AFQ_OK && b->grouped) rc = record_grouped(b, nsteps);
   // one branch per system: its steps run concurrently with the other systems'
-  for (size_t i = 0; i < b->ctx.size() && rc == AFQ_OK; ++i) {
+  for (size_t i = 0; i < b->ctx.size() && rc == AFQ_OK && !b->grouped; ++i) {
     afq_ctx* c = b->ctx[i];
     cudaStream_t own = c->stream;
     c->stream = b->streams[i];

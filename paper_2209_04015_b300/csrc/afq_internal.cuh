@@ -288,6 +288,12 @@ int launch_fields(afq_ctx* ctx, const double* xi_dev);
 int launch_philox_fields(afq_ctx* ctx, uint64_t step, double* out, uint32_t* words);
 int launch_vhs_fp64(afq_ctx* ctx);
 int launch_propagate_fp64(afq_ctx* ctx);
+// grouped VHS and propagation of several FP64 systems (batches; k_step.cu)
+struct GroupedStep;
+int grouped_step_create(GroupedStep** out, afq_ctx* const* ctxs, int n, std::string* err);
+void grouped_step_free(GroupedStep* g);
+cudaError_t grouped_step_vhs(GroupedStep* g, cudaStream_t st);
+cudaError_t grouped_step_propagate(GroupedStep* g, cudaStream_t st);
 int launch_weights(afq_ctx* ctx, double log_const, const double* e_shift_dev = nullptr);
 int launch_emix(afq_ctx* ctx, WalkerSet& s, double* out);
 int comb_walkers(afq_ctx* ctx, double u, double w_cap);  // k_population.cu

@@ -1,6 +1,9 @@
 // Step kernels of libafqmc: auxiliary fields and force bias, the VHS build, the
 // Taylor propagator with the one-body halves, and the phaseless weight update
 // (Sec. "Review of AFQMC": hybrid propagation, Eqs. import, ovl, ph and theta).
+#include <algorithm>
+#include <vector>
+
 #include "afq_internal.cuh"
 
 namespace {
@@ -154,15 +157,15 @@ __global__ void k_philox_fields(int W, int X, uint64_t seed, uint64_t step, doub
 // written to both triangles of the dense symmetric W x M x M output.
 // ---------------------------------------------------------------------------
 constexpr int VZ = 8, VT = 64, VK = 32;
-__global__ void __launch_bounds__(256) k_vhs_fp64(int W, int X, int M, int Mp, double sdt,
-                                                  const double2* __restrict__ y,
-                                                  const double* __restrict__ Lpk,
-                                                  const int2* __restrict__ tpq,
-                                                  double2* __restrict__ A,
-                                                  double* __restrict__ Asum) {
+// One tile: packed rows t0 = bx VT .. + VT of walkers z0 = by VZ .. + VZ (256 threads).
+__device__ __forceinline__ void vhs_tile(int W, int X, int M, int Mp, double sdt,
+                                         const double2* __restrict__ y,
+                                         const double* __restrict__ Lpk,
+                                         const int2* __restrict__ tpq, double2* __restrict__ A,
+                                         double* __restrict__ Asum, int bx, int by) {
   __shared__ double2 Ys[VZ][VK];
   __shared__ double Ls[VK][VT];
-  const int t0 = blockIdx.x * VT, z0 = blockIdx.y * VZ;
+  const int t0 = bx * VT, z0 = by * VZ;
   const int tz = threadIdx.x / 32, tt = threadIdx.x % 32;
   double2 a0 = cmk(0.0, 0.0), a1 = cmk(0.0, 0.0);
   for (int k0 = 0; k0 < X; k0 += VK) {
@@ -205,6 +208,15 @@ __global__ void __launch_bounds__(256) k_vhs_fp64(int W, int X, int M, int Mp, d
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_vhs_fp64(int W, int X, int M, int Mp, double sdt,
+                                                  const double2* __restrict__ y,
+                                                  const double* __restrict__ Lpk,
+                                                  const int2* __restrict__ tpq,
+                                                  double2* __restrict__ A,
+                                                  double* __restrict__ Asum) {
+  vhs_tile(W, X, M, Mp, sdt, y, Lpk, tpq, A, Asum, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -323,30 +335,33 @@ __device__ __forceinline__ void sym_apply_cplx3(int M, int p, const double2* __r
   for (int c = 0; c < NCg; ++c) out[c] = cmk(p1[c] - p2[c], p3[c] - p1[c] - p2[c]);
 }
 
-// K5 (FP64): Phi <- P T_n(A) P Phi for NC walker columns of one walker per CTA, the
-// current Taylor term in shared memory.  G threads share each row p (each owns NC/G
-// of the columns), so that G M threads fill whole warps for M not a multiple of 32.
+// K5 (FP64): Phi <- P T_n(A) P Phi for NC walker columns c0 .. c0 + NC - 1 of walker
+// z, the current Taylor term in shared memory (sm: propagate_fp64_smem bytes).  G
+// threads share each row p (each owns NC/G of the columns), so that G M threads fill
+// whole warps for M not a multiple of 32.  The unit runs on nthr threads (thread t of
+// them); a unit that is not live only takes part in the CTA's barriers.
 template <int NC, int G>
-__global__ void k_propagate_fp64(int M, int N, int order, const double* __restrict__ P,
-                                 const double2* __restrict__ A, const double* __restrict__ Asum,
-                                 double2* __restrict__ phi) {
+__device__ __forceinline__ void prop_unit(int M, int N, int order, const double* __restrict__ P,
+                                          const double2* __restrict__ A,
+                                          const double* __restrict__ Asum,
+                                          double2* __restrict__ phi, int z, int c0, int t,
+                                          int nthr, unsigned char* sm, bool live) {
   constexpr int NCg = NC / G;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  double2* cur = reinterpret_cast<double2*>(smraw);  // M x NC
+  double2* cur = reinterpret_cast<double2*>(sm);  // M x NC
   double2* nxt = cur + M * NC;
   double2* acc = nxt + M * NC;
   double* curs = reinterpret_cast<double*>(acc + M * NC);  // Re + Im of cur (M x NC)
   double* nxts = curs + M * NC;
-  const int z = blockIdx.y, c0 = blockIdx.x * NC, t = threadIdx.x;
-  const bool act = t < G * M;
+  const bool act = live && t < G * M;
   const int p = act ? t % M : 0, cb = act ? (t / M) * NCg : 0;
   const double2* Az = A + (long)z * M * M;
   const double* Sz = Asum + (long)z * M * M;
   double2* phz = phi + (long)z * M * N;
-  for (int e = t; e < M * NC; e += blockDim.x) {
-    const int q = e / NC, c = e % NC;
-    cur[e] = c0 + c < N ? phz[(long)q * N + c0 + c] : cmk(0.0, 0.0);
-  }
+  if (live)
+    for (int e = t; e < M * NC; e += nthr) {
+      const int q = e / NC, c = e % NC;
+      cur[e] = c0 + c < N ? phz[(long)q * N + c0 + c] : cmk(0.0, 0.0);
+    }
   __syncthreads();
   double2 r[NCg];
   if (act) {
@@ -392,6 +407,101 @@ __global__ void k_propagate_fp64(int M, int N, int order, const double* __restri
 #pragma unroll
     for (int c = 0; c < NCg; ++c)
       if (c0 + cb + c < N) phz[(long)p * N + c0 + cb + c] = r[c];
+  }
+}
+
+// One CTA per (column chunk, walker).
+template <int NC, int G>
+__global__ void k_propagate_fp64(int M, int N, int order, const double* __restrict__ P,
+                                 const double2* __restrict__ A, const double* __restrict__ Asum,
+                                 double2* __restrict__ phi) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  prop_unit<NC, G>(M, N, order, P, A, Asum, phi, blockIdx.y, blockIdx.x * NC, threadIdx.x,
+                   blockDim.x, smraw, true);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped launches for batches of uneven systems: one persistent launch per stage
+// (the VHS build, the Taylor propagation) whose CTAs take tiles of every system from
+// a descriptor table, the next tile from a device counter.  A tile runs the same
+// device code as the system's own launch, so results are bit-identical to it.
+// ---------------------------------------------------------------------------
+struct VhsDesc {
+  int W, X, M, Mp;
+  double sdt;
+  const double2* y;
+  const double* Lpk;
+  const int2* tpq;
+  double2* A;
+  double* Asum;
+  int tx;     // packed-row tiles of VT rows
+  int tile0;  // first tile of this system in the launch
+};
+
+struct PropDesc {
+  int M, N, order, G;
+  int T;       // threads of one unit (one walker's column chunk): 32 ceil(G M / 32)
+  int U;       // units per CTA (U T <= the CTA's threads)
+  int chunks;  // column chunks per walker
+  int units;   // chunks x W
+  int tile0;   // first CTA tile of this system in the launch
+  int unit_smem;  // shared-memory bytes of one unit (a multiple of 16)
+  const double* P;
+  const double2* A;
+  const double* Asum;
+  double2* phi;
+};
+
+// The next tile of a persistent grouped launch (every thread gets the same value).
+__device__ __forceinline__ int next_tile(int* counter) {
+  __shared__ int tile;
+  __syncthreads();  // every thread has read the previous value
+  if (threadIdx.x == 0) tile = atomicAdd(counter, 1);
+  __syncthreads();
+  return tile;
+}
+
+__global__ void __launch_bounds__(256) k_vhs_fp64_grouped(const VhsDesc* __restrict__ d, int ns,
+                                                          int total, int* __restrict__ counter) {
+  for (;;) {
+    const int tile = next_tile(counter);
+    if (tile >= total) return;
+    int s = 0;
+    while (s + 1 < ns && tile >= d[s + 1].tile0) ++s;
+    const VhsDesc g = d[s];
+    const int local = tile - g.tile0;
+    vhs_tile(g.W, g.X, g.M, g.Mp, g.sdt, g.y, g.Lpk, g.tpq, g.A, g.Asum, local % g.tx,
+             local / g.tx);
+  }
+}
+
+// Each CTA tile holds U units of one system side by side (threads u T .. u T + T - 1
+// and shared memory u unit_smem .. of unit u); G is the system's threads per row.
+template <int NC>
+__global__ void __launch_bounds__(1024, 1)
+    k_propagate_fp64_grouped(const PropDesc* __restrict__ d, int ns, int total,
+                             int* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  for (;;) {
+    const int tile = next_tile(counter);
+    if (tile >= total) return;
+    int s = 0;
+    while (s + 1 < ns && tile >= d[s + 1].tile0) ++s;
+    const PropDesc g = d[s];
+    const int sub = (int)threadIdx.x / g.T;
+    const int unit = (tile - g.tile0) * g.U + sub;
+    const bool live = sub < g.U && unit < g.units;
+    const int z = live ? unit / g.chunks : 0, c0 = live ? (unit % g.chunks) * NC : 0;
+    const int t = (int)threadIdx.x - (sub < g.U ? sub : 0) * g.T;
+    unsigned char* sm = smraw + (size_t)(sub < g.U ? sub : 0) * g.unit_smem;
+    if (NC >= 4 && g.G == 4)
+      prop_unit<NC, (NC >= 4 ? 4 : 1)>(g.M, g.N, g.order, g.P, g.A, g.Asum, g.phi, z, c0, t, g.T,
+                                       sm, live);
+    else if (NC >= 2 && g.G == 2)
+      prop_unit<NC, (NC >= 2 ? 2 : 1)>(g.M, g.N, g.order, g.P, g.A, g.Asum, g.phi, z, c0, t, g.T,
+                                       sm, live);
+    else
+      prop_unit<NC, 1>(g.M, g.N, g.order, g.P, g.A, g.Asum, g.phi, z, c0, t, g.T, sm, live);
   }
 }
 
@@ -548,4 +658,175 @@ int launch_emix(afq_ctx* ctx, WalkerSet& s, double* out) {
   k_emix<<<1, 256, 0, ctx->stream>>>(s.W, ctx->p.free_projection, s.w, s.energy, out);
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Grouped launches: descriptor tables (host side)
+// ---------------------------------------------------------------------------
+struct GroupedStep {
+  int ns = 0, nc = 4, prop_threads = 0, vhs_total = 0, prop_total = 0;
+  int vhs_grid = 0, prop_grid = 0;
+  size_t prop_smem = 0;
+  VhsDesc* vd = nullptr;  // device tables
+  PropDesc* pd = nullptr;
+  int* counters = nullptr;  // [0] VHS, [1] propagation; zeroed before each VHS launch
+};
+
+namespace {
+
+template <int NC>
+const void* grouped_prop_kernel() {
+  return (const void*)k_propagate_fp64_grouped<NC>;
+}
+
+const void* grouped_prop_fn(int nc) {
+  return nc == 2 ? grouped_prop_kernel<2>() : grouped_prop_kernel<4>();
+}
+
+}  // namespace
+
+void grouped_step_free(GroupedStep* g) {
+  if (!g) return;
+  if (g->vd) cudaFree(g->vd);
+  if (g->pd) cudaFree(g->pd);
+  if (g->counters) cudaFree(g->counters);
+  delete g;
+}
+
+// Tiles of the systems in order of decreasing cost per tile (the dynamic tile counter
+// then hands the long tiles out first); one column chunk NC for all systems: 2 when
+// every system's autotuned chunk is 2, else 4 (8 columns would spill at the 64
+// registers a thread of a 1024-thread CTA has).  Each column's arithmetic does not
+// depend on NC, so the results are those of the systems' own launches.
+int grouped_step_create(GroupedStep** out, afq_ctx* const* ctxs, int n, std::string* err) {
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i] || ctxs[i]->mixed || !ctxs[i]->Asum || !ctxs[i]->have_walkers) {
+      *err = "grouped launches take FP64 contexts with walkers";
+      return AFQ_ERR_ARG;
+    }
+  int nc = 2;
+  for (int i = 0; i < n; ++i)
+    if (ctxs[i]->prop_nc != 2) nc = 4;
+  constexpr int kThreads = 1024;
+  constexpr size_t kSmem = 227 * 1024;
+  for (int i = 0; i < n; ++i)
+    while (nc > 2 && propagate_fp64_smem(ctxs[i]->M, nc) > kSmem) nc /= 2;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::vector<VhsDesc> vd(n);
+  std::vector<PropDesc> pd(n);
+  // VHS: a tile costs VZ walkers x VT packed rows x X
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return ctxs[a]->X > ctxs[b]->X; });
+  int tile = 0;
+  for (int k = 0; k < n; ++k) {
+    const afq_ctx* c = ctxs[order[k]];
+    VhsDesc& d = vd[k];
+    d.W = c->ws.W;
+    d.X = c->X;
+    d.M = c->M;
+    d.Mp = c->Mp;
+    d.sdt = sqrt(c->p.dt);
+    d.y = c->y;
+    d.Lpk = c->Lpk;
+    d.tpq = c->tpq;
+    d.A = c->A;
+    d.Asum = c->Asum;
+    d.tx = (c->Mp + VT - 1) / VT;
+    d.tile0 = tile;
+    tile += d.tx * ((c->ws.W + VZ - 1) / VZ);
+  }
+  const int vhs_total = tile;
+  // propagation: a CTA tile costs U units x order x M^2 NC
+  size_t smem = 0;
+  std::vector<double> cost(n);
+  std::vector<PropDesc> tmp(n);
+  for (int i = 0; i < n; ++i) {
+    const afq_ctx* c = ctxs[i];
+    PropDesc& d = tmp[i];
+    d.M = c->M;
+    d.N = c->N;
+    d.order = c->p.taylor_order;
+    d.G = propagate_rows_per_thread(c->M, nc);
+    d.T = 32 * ((d.G * c->M + 31) / 32);
+    if (d.T > kThreads) {
+      *err = "grouped propagation: too many orbitals";
+      return AFQ_ERR_ARG;
+    }
+    d.unit_smem = (int)((propagate_fp64_smem(c->M, nc) + 15) / 16 * 16);
+    d.U = kThreads / d.T;
+    while (d.U > 1 && (size_t)d.U * d.unit_smem > kSmem) --d.U;
+    d.chunks = (c->N + nc - 1) / nc;
+    d.units = d.chunks * c->ws.W;
+    d.P = c->P;
+    d.A = c->A;
+    d.Asum = c->Asum;
+    d.phi = c->ws.phi;
+    smem = std::max(smem, (size_t)d.U * d.unit_smem);
+    cost[i] = (double)d.U * d.order * c->M * c->M;
+  }
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  tile = 0;
+  for (int k = 0; k < n; ++k) {
+    pd[k] = tmp[order[k]];
+    pd[k].tile0 = tile;
+    tile += (pd[k].units + pd[k].U - 1) / pd[k].U;
+  }
+  const int prop_total = tile;
+
+  GroupedStep* g = new (std::nothrow) GroupedStep();
+  if (!g) return AFQ_ERR_NOMEM;
+  g->ns = n;
+  g->nc = nc;
+  g->prop_threads = kThreads;
+  g->prop_smem = smem;
+  g->vhs_total = vhs_total;
+  g->prop_total = prop_total;
+  int per_sm = 0;
+  bool ok = cudaMalloc((void**)&g->vd, n * sizeof(VhsDesc)) == cudaSuccess &&
+            cudaMalloc((void**)&g->pd, n * sizeof(PropDesc)) == cudaSuccess &&
+            cudaMalloc((void**)&g->counters, 2 * sizeof(int)) == cudaSuccess &&
+            cudaMemcpy(g->vd, vd.data(), n * sizeof(VhsDesc), cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
+            cudaMemcpy(g->pd, pd.data(), n * sizeof(PropDesc), cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
+            raise_smem_limit(grouped_prop_fn(nc), smem) == cudaSuccess;
+  int dev = 0, sms = 148;
+  ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
+       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+  ok = ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vhs_fp64_grouped, 256, 0) ==
+                 cudaSuccess;
+  g->vhs_grid = std::min(vhs_total, sms * std::max(per_sm, 1));
+  ok = ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grouped_prop_fn(nc), kThreads,
+                                                           smem) == cudaSuccess;
+  g->prop_grid = std::min(prop_total, sms * std::max(per_sm, 1));
+  if (!ok) {
+    cudaGetLastError();
+    grouped_step_free(g);
+    *err = "grouped launches: device tables";
+    return AFQ_ERR_CUDA;
+  }
+  *out = g;
+  return AFQ_OK;
+}
+
+// The grouped VHS build of every system (zeroes both tile counters first).
+cudaError_t grouped_step_vhs(GroupedStep* g, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(g->counters, 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_vhs_fp64_grouped<<<g->vhs_grid, 256, 0, st>>>(g->vd, g->ns, g->vhs_total, g->counters);
+  return cudaGetLastError();
+}
+
+// The grouped Taylor propagation of every system (after grouped_step_vhs).
+cudaError_t grouped_step_propagate(GroupedStep* g, cudaStream_t st) {
+  if (g->nc == 2)
+    k_propagate_fp64_grouped<2><<<g->prop_grid, g->prop_threads, g->prop_smem, st>>>(
+        g->pd, g->ns, g->prop_total, g->counters + 1);
+  else
+    k_propagate_fp64_grouped<4><<<g->prop_grid, g->prop_threads, g->prop_smem, st>>>(
+        g->pd, g->ns, g->prop_total, g->counters + 1);
+  return cudaGetLastError();
 }

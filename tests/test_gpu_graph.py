@@ -3,7 +3,7 @@
 A replayed graph runs the same kernels in the same order as eager stepping, so its
 walkers, weights and energies must be bit-identical; a batch of uneven systems in
 one graph must reproduce each system stepped on its own, and in FP64 match the
-oracle at 1e-10; autotuned tiles change only the order of floating-point sums
+oracle at 1e-10, with per-system branches and with grouped launches alike; autotuned tiles change only the order of floating-point sums
 (results within 1e-12 relative in FP64, and the FP64 path still matches the oracle
 at 1e-10).
 """
@@ -103,13 +103,16 @@ def test_c4_batch_in_split_precision_matches_individual():
     b.close()
 
 
-def test_c4_batch_in_fp64_matches_oracle():
+@pytest.mark.parametrize("grouped", [False, True])
+def test_c4_batch_in_fp64_matches_oracle(grouped):
     """The batched workload in FP64 (eight uneven systems: 48..220 orbitals, 0.2 M
     electrons per spin, X = 5 M, 512..32 walkers) stepped by one graph for one QR
     period with device Philox fields, against the oracle: two walkers of every system
     re-run by the oracle alone with the same counter-based field stream drawn by its
     own Philox (walkers are independent and the counters are keyed by walker index).
-    Walkers, overlaps, weights and every energy part within 1e-10 relative."""
+    Walkers, overlaps, weights and every energy part within 1e-10 relative.  grouped:
+    the VHS build and the propagation of all eight systems as one persistent launch
+    each per step."""
     from oracle.afqmc import Oracle
     from paper_2209_04015_b300 import AfqBatch
     systems = make_c4()
@@ -118,7 +121,7 @@ def test_c4_batch_in_fp64_matches_oracle():
     bctx = [new_ctx(s, W, phis[k], seed=7 + k) for k, (s, W) in enumerate(systems)]
     for c in bctx:
         c.autotune()
-    b = AfqBatch(bctx)
+    b = AfqBatch(bctx, grouped=grouped)
     b.capture(nsteps)
     b.launch(1)
     b.synchronize()
@@ -142,6 +145,60 @@ def test_c4_batch_in_fp64_matches_oracle():
             assert np.all(np.abs(e[idx, part] - eref[:, part]) <= 1e-10 * scale), (k, part)
     b.close()
     for c in bctx:
+        c.close()
+
+
+@pytest.mark.parametrize("workload", ["uneven", "c4"])
+def test_grouped_batch_is_bit_identical_to_per_system_launches(workload):
+    """Grouped launches (one persistent VHS build and one persistent propagation over
+    every system's tiles per step, tiles from a per-system descriptor table) against
+    the per-system graph branches, two QR periods: the same kernels' arithmetic per
+    tile, so walkers, weights, overlaps and energies are bit-identical.  The uneven set
+    has ragged column chunks, several units per CTA and a system with one walker;
+    the c4 set is the batched workload, autotuned (its per-system column chunks differ
+    from the grouped launch's)."""
+    from paper_2209_04015_b300 import AfqBatch
+    if workload == "uneven":
+        shapes = [(20, 4, 3, 50, 16), (37, 5, 3, 71, 13), (9, 2, 1, 12, 1), (64, 7, 7, 120, 5),
+                  (33, 2, 6, 40, 7)]
+        systems = [(make_system(M, na, nb, X, seed=40 + k, decay="geometric"), W)
+                   for k, (M, na, nb, X, W) in enumerate(shapes)]
+    else:
+        systems = make_c4()
+    phis = [perturbed_walkers(s, W, eps=0.3, seed=50 + k) for k, (s, W) in enumerate(systems)]
+    sets = []
+    for grouped in (False, True):
+        ctxs = [new_ctx(s, W, phis[k], seed=3 + k) for k, (s, W) in enumerate(systems)]
+        if workload == "c4":
+            for c in ctxs:
+                c.autotune()
+        b = AfqBatch(ctxs, grouped=grouped)
+        b.capture(5)
+        b.launch(2)
+        b.synchronize()
+        sets.append((b, ctxs))
+    (b0, per_system), (b1, grouped_ctxs) = sets
+    for a, g in zip(per_system, grouped_ctxs):
+        same(a, g)
+        ea, ma = a.get_energy()
+        eg, mg = g.get_energy()
+        assert np.array_equal(ea, eg) and ma == mg
+        assert a.get_step() == g.get_step() == 10
+    for b, ctxs in sets:
+        b.close()
+        for c in ctxs:
+            c.close()
+
+
+def test_grouped_batch_takes_fp64_contexts_only():
+    from paper_2209_04015_b300 import AfqBatch
+    from paper_2209_04015_b300.afqmc import AFQ_ERR_ARG, AfqError
+    s = make_system(37, 5, 3, 71, seed=4, decay="geometric")
+    ctxs = [new_ctx(s, 4), new_ctx(s, 4, precision="split_bf16")]
+    with pytest.raises(AfqError) as e:
+        AfqBatch(ctxs, grouped=True)
+    assert e.value.code == AFQ_ERR_ARG
+    for c in ctxs:
         c.close()
 
 
