@@ -460,7 +460,7 @@ int warp_grid(long rows);
 // consecutive elements in registers (one read of the row), the warp takes the row
 // exponent, and every digit plane is written as bfloat16 pairs (128-byte warp stores).
 template <int NP, int D>
-__global__ void __launch_bounds__(256) k_slice_cplx1(const double2* __restrict__ in, long rows,
+__global__ void __launch_bounds__(256, (NP <= 6 && D <= kFastSlices) ? 3 : 2) k_slice_cplx1(const double2* __restrict__ in, long rows,
                                                      int R, int K, int Kp, int S,
                                                      __nv_bfloat16* __restrict__ out,
                                                      int* __restrict__ eout) {
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(256) k_slice_cplx1(const double2* __restrict__
 // one-body half.  kmod = k mod 4 selects the rotation i^k; kscale (M values, or NULL)
 // scales element p of every row first (the diagonal of P in the first call).
 template <int NP, int D>
-__global__ void __launch_bounds__(256) k_taylor_slice(const double2* __restrict__ in,
+__global__ void __launch_bounds__(256, (NP <= 6 && D <= kFastSlices) ? 3 : 2) k_taylor_slice(const double2* __restrict__ in,
                                                       double2* __restrict__ acc, long rows,
                                                       int R, int K, int Kp, int S, double gk,
                                                       int kmod, int last,
@@ -612,6 +612,10 @@ void slice_rows_d(const double2* in, long rows, int R, int K, int Kp, int S,
     k_slice_cplx1<2, D><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
   else if (Kp <= 256)
     k_slice_cplx1<4, D><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+  else if (Kp <= 320)  // the row in as few registers as it needs: more warps per SM
+    k_slice_cplx1<5, D><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
+  else if (Kp <= 384)
+    k_slice_cplx1<6, D><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
   else if (Kp <= 512)
     k_slice_cplx1<8, D><<<g, 256, 0, st>>>(in, rows, R, K, Kp, S, out, eout);
   else
@@ -1038,6 +1042,12 @@ int taylor_slice(afq_ctx* ctx, int b, double gk, int kmod, int last, int S,
         ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
   else if (Kp <= 256)
     (fast ? k_taylor_slice<4, kFastSlices> : k_taylor_slice<4, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+  else if (Kp <= 320)  // the row in as few registers as it needs: more warps per SM
+    (fast ? k_taylor_slice<5, kFastSlices> : k_taylor_slice<5, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+  else if (Kp <= 384)
+    (fast ? k_taylor_slice<6, kFastSlices> : k_taylor_slice<6, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
         ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
   else if (Kp <= 512)
     (fast ? k_taylor_slice<8, kFastSlices> : k_taylor_slice<8, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
