@@ -100,13 +100,16 @@ typedef struct afq_params {
                           powers take fewer where their terms are small); 0 = 4  */
   int exchange;        /* an afq_exchange: algorithm of the exchange energy        */
   int prop_kernel;     /* AFQ_SPLIT_BF16 propagation: 0 = one launch per GEMM pass with
-                          digit slicing launches between them (default); 1 = one
-                          persistent kernel of thread-block clusters for all GEMM
-                          passes of a step (each walker's 128-row slabs form a
+                          digit slicing launches between them (default); passes of up
+                          to 4 digits issue one MMA per A digit over the concatenated
+                          B digits (32-column tiles, two TMEM accumulator sets);
+                          1 = one persistent kernel of thread-block clusters for all
+                          GEMM passes of a step (each walker's 128-row slabs form a
                           cluster that exchanges the digit exponents on chip; about
                           2x slower on this part, kept as an option), falling back
-                          to 0 where a shape cannot take it.  Both give the same
-                          bits.                                                    */
+                          to 0 where a shape cannot take it; 2 = the per-pass
+                          kernels with one MMA per digit pair (64-column complex
+                          tiles).  All give the same bits.                         */
 } afq_params;
 
 /* Fill *p with the defaults: dt 0.005, Taylor order 6, QR every 5 steps, seed 1,

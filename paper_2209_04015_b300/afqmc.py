@@ -20,7 +20,7 @@ AFQ_OK, AFQ_ERR_ARG, AFQ_ERR_CUDA, AFQ_ERR_SINGULAR, AFQ_ERR_NAN, AFQ_ERR_STATE,
 AFQ_STATIC_EXCHANGE_SLOTS = 262144  # complex partial-sum slots of the static scratch array
 PRECISIONS = {"fp64": 0, "split_bf16": 1, "split_tf32": 2}
 EXCHANGES = {"auto": 0, "direct": 1, "stored": 2}
-PROP_KERNELS = {"per_pass": 0, "fused": 1}
+PROP_KERNELS = {"per_pass": 0, "fused": 1, "per_pair": 2}
 STATUS_NAMES = {0: "AFQ_OK", 1: "AFQ_ERR_ARG", 2: "AFQ_ERR_CUDA", 3: "AFQ_ERR_SINGULAR",
                 4: "AFQ_ERR_NAN", 5: "AFQ_ERR_STATE", 6: "AFQ_ERR_NOMEM"}
 

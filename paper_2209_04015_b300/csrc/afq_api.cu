@@ -288,7 +288,7 @@ int afq_create(afq_ctx** out, const afq_params* params, void* cuda_stream) {
       ctx->p.split_slices < 1 || ctx->p.split_slices > 7 || ctx->p.prop_slices < 1 ||
       ctx->p.prop_slices > 7 || ctx->p.exchange < AFQ_EXCHANGE_AUTO ||
       ctx->p.exchange > AFQ_EXCHANGE_STORED || ctx->p.prop_kernel < 0 ||
-      ctx->p.prop_kernel > 1) {
+      ctx->p.prop_kernel > 2) {
     delete ctx;
     return AFQ_ERR_ARG;
   }

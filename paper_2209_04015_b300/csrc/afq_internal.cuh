@@ -176,7 +176,10 @@ struct afq_ctx {
   int *e_lt = nullptr, *e_pm = nullptr, *e_y = nullptr, *e_a = nullptr;  // row exponents
   int* e_t[2] = {nullptr, nullptr};
   CUtensorMap tm_vhs_a, tm_vhs_b, tm_pm, tm_az, tm_t[2];
-  CUtensorMap tm_t_real[2];  // the same operands in prop_rows_real-row boxes (P passes)
+  __nv_bfloat16* T_neg[2] = {nullptr, nullptr};  // S x W x N x Mpad: -Im of the operands (<= 4 digits)
+  CUtensorMap tm_t_real[2];  // the same operands in prop_rows_real-row boxes (P passes and
+                             // the column-concatenated complex passes)
+  CUtensorMap tm_tneg[2];    // T_neg in prop_rows_real-row boxes
   int prop_rows_real = 0;    // walker columns per tile of the real P passes
   CUtensorMap tm_t_fused[2]; // the same operands in prop_rows_fused-row boxes (cluster kernel)
   int prop_rows_fused = 0;   // walker columns per chain of the cluster kernel

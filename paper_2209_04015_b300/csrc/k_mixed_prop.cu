@@ -114,6 +114,15 @@ struct VhsP {
 // diagonals accumulate in S TMEM regions of BN columns; each epilogue thread
 // recombines a real column and its imaginary partner brows columns later and writes
 // whole complex FP64 values.
+// Column-concatenated form (CAT, up to 4 digits): the B digit slots t = 0 .. S - 1
+// lie one after another in shared memory, so A digit s times the first S - s slots
+// is ONE MMA of N = (S - s) BN columns whose column block t lands in accumulator s + t
+// (the accumulators are BN columns apart): S MMAs per K block and A unit instead of
+// S (S + 1) / 2, each reading its A digit from shared memory once.  The complex
+// product takes a second B region [-Im T; Re T] per slot (the negated digits come from
+// the slicing pass), so that Im A times it adds [-Im A Im T | Im A Re T] in the same
+// two MMAs per digit.  The sums per accumulator are the same exact integer sums, so
+// the results are bit-identical to the per-pair form.
 // Roles: warp 0 TMA, warp 1 MMA (and TMEM), warps 2-9 epilogue (two per TMEM lane
 // quarter, splitting the column chunks); the producer runs ahead across tiles while
 // the epilogue drains TMEM.
@@ -186,7 +195,6 @@ __device__ __forceinline__ void prop_epi_group(const PropArgs& a, uint32_t trow,
     const int sc = ep + a.eb[(long)z * N + j] - 14;
     const double dr = dre[jj], di = combine_exact<S>(ai, sc);
     const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
-    const long iphi = ((long)z * M + p) * N + j;  // [z][p][j]
     if (a.mode == kModeFirst) {
       // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
       a.accT[ia] = make_double2(dr, di);
@@ -197,16 +205,18 @@ __device__ __forceinline__ void prop_epi_group(const PropArgs& a, uint32_t trow,
     } else {
       const double2 acc = a.accT[ia];
       const double d = a.pdiag[p];
-      a.phi_out[iphi] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
+      a.phi_out[((long)z * M + p) * N + j] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
     }
   }
 }
 
-template <int S, bool REAL>
+template <int S, bool REAL, bool CAT>
 __global__ void __launch_bounds__(32 * kPropWarps, 1)
     k_prop_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              const __grid_constant__ PropArgs a) {
+              const __grid_constant__ CUtensorMap tmBn, const __grid_constant__ PropArgs a) {
   constexpr int kUA = REAL ? 1 : 2;
+  constexpr int kUB = (CAT && !REAL) ? 2 : 1;  // B regions per digit: [Re; Im] (+ [-Im; Re])
+  static_assert(!CAT || S <= 4, "the column-concatenated form takes up to 4 digits");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -223,7 +233,7 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nst = a.stages, BN = a.BN, brows = a.brows;
   const uint32_t bslot = (uint32_t)BN * 64u;
-  const uint32_t stage_bytes = S * (kUA * kASlot + bslot);
+  const uint32_t stage_bytes = S * (kUA * kASlot + kUB * bslot);
   int* err = a.err;
   if (threadIdx.x == 0) skip = *(const volatile int*)err;
   __syncthreads();
@@ -241,6 +251,7 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
     tc::fence_mbar_init();
     tc::prefetch_tmap(&tmA);
     tc::prefetch_tmap(&tmB);
+    if (kUB == 2) tc::prefetch_tmap(&tmBn);
   }
   if (warp == 1) {
     tc::tmem_alloc(&tmem_base, a.tmem_cols);
@@ -280,6 +291,12 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
             tc::tma_load_4d(sb + s * bslot, &tmB, kb * kBK, j0, 2 * z, s, &full[st]);
             tc::tma_load_4d(sb + s * bslot + brows * 64, &tmB, kb * kBK, j0, 2 * z + 1, s,
                             &full[st]);
+            if (kUB == 2) {  // the second region: [-Im T; Re T]
+              uint8_t* sb2 = sb + S * bslot;
+              tc::tma_load_4d(sb2 + s * bslot, &tmBn, kb * kBK, j0, z, s, &full[st]);
+              tc::tma_load_4d(sb2 + s * bslot + brows * 64, &tmB, kb * kBK, j0, 2 * z, s,
+                              &full[st]);
+            }
           }
         }
       }
@@ -311,12 +328,30 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
           const uint32_t sb = sa + S * kUA * kASlot;
-          issue_diagonals<S>(acc, (uint32_t)BN, sa, sb, bslot, 0, 0, id_full, kb == 0);
-          if (!REAL) {
-            issue_diagonals<S>(acc, (uint32_t)BN, sa, sb + (uint32_t)brows * 64u, bslot, 1, 0,
-                               id_half_neg, false);
-            issue_diagonals<S>(acc + (uint32_t)brows, (uint32_t)BN, sa, sb, bslot, 1, 0, id_half,
-                               false);
+          if constexpr (CAT) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+              const uint32_t idn = tc::idesc_bf16(128, (S - s) * BN);
+              const uint32_t d = acc + (uint32_t)(s * BN);
+#pragma unroll
+              for (int ks = 0; ks < 2; ++ks)
+                tc::mma_bf16(d, tc::sdesc_k64(a_unit(sa, S, 0, s) + ks * 32),
+                             tc::sdesc_k64(sb + ks * 32), idn, !(kb == 0 && s == 0 && ks == 0));
+              if (!REAL) {
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks)
+                  tc::mma_bf16(d, tc::sdesc_k64(a_unit(sa, S, 1, s) + ks * 32),
+                               tc::sdesc_k64(sb + S * bslot + ks * 32), idn, 1);
+              }
+            }
+          } else {
+            issue_diagonals<S>(acc, (uint32_t)BN, sa, sb, bslot, 0, 0, id_full, kb == 0);
+            if (!REAL) {
+              issue_diagonals<S>(acc, (uint32_t)BN, sa, sb + (uint32_t)brows * 64u, bslot, 1, 0,
+                                 id_half_neg, false);
+              issue_diagonals<S>(acc + (uint32_t)brows, (uint32_t)BN, sa, sb, bslot, 1, 0,
+                                 id_half, false);
+            }
           }
           tc::mma_commit(&empty[st]);
         }
@@ -375,8 +410,7 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
             const int sc = ep + a.eb[(long)z * N + j] - 14;
             const double dr = dre[jj], di = combine_exact<S>(ai, sc);
             const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
-            const long iphi = ((long)z * M + p) * N + j;  // [z][p][j]
-            if (a.mode == kModeFirst) {
+                    if (a.mode == kModeFirst) {
               // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
               a.accT[ia] = make_double2(dr, di);
             } else if (a.mode == kModeTerm) {
@@ -386,7 +420,7 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
             } else {
               const double2 acc = a.accT[ia];
               const double d = a.pdiag[p];
-              a.phi_out[iphi] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
+              a.phi_out[((long)z * M + p) * N + j] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
             }
           }
         }
@@ -517,9 +551,10 @@ __global__ void __launch_bounds__(256, (NP <= 6 && D <= kFastSlices) ? 3 : 2) k_
                                                       int kmod, int last,
                                                       const double* __restrict__ kscale,
                                                       __nv_bfloat16* __restrict__ out,
+                                                      __nv_bfloat16* __restrict__ nout,
                                                       int* __restrict__ eout) {
   const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
-  const long plane = 2L * rows * Kp;
+  const long plane = 2L * rows * Kp, nplane = rows * Kp;
   for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
        r += (long)gridDim.x * warps) {
     const double2* row = in + r * K;
@@ -574,6 +609,14 @@ __global__ void __launch_bounds__(256, (NP <= 6 && D <= kFastSlices) ? 3 : 2) k_
           if (s < S)
             *reinterpret_cast<__nv_bfloat162*>(o + s * plane) =
                 __floats2bfloat162_rn((float)q0[s], (float)q1[s]);
+        if (part && nout) {  // -Im digits [s][z][j][Kp] for the column-concatenated GEMM
+          __nv_bfloat16* on = nout + r * Kp + k;
+#pragma unroll
+          for (int s = 0; s < D; ++s)
+            if (s < S)
+              *reinterpret_cast<__nv_bfloat162*>(on + s * nplane) =
+                  __floats2bfloat162_rn((float)-q0[s], (float)-q1[s]);
+        }
       }
     }
   }
@@ -630,18 +673,27 @@ void slice_rows(const double2* in, long rows, int R, int K, int Kp, int S,
     slice_rows_d<kMaxSlices>(in, rows, R, K, Kp, S, out, eout, st);
 }
 
-// Phi (W x M x N) -> W x N x M (transposed copy, FP64)
-__global__ void k_transpose_phi(const double2* __restrict__ phi, int W, int M, int N,
-                                double2* __restrict__ out) {
-  const long total = (long)W * N * M;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
-    const int p = (int)(e % M);
-    const long zj = e / M;
-    const int j = (int)(zj % N);
-    const long z = zj / N;
-    out[e] = phi[(z * M + p) * N + j];
+// out[z] = in[z]^T for W complex R x C matrices (FP64; Phi -> Phi^T), through
+// 32 x 32 shared-memory tiles so that reads and writes are both coalesced.
+__global__ void __launch_bounds__(256) k_transpose_cplx(const double2* __restrict__ in, int W,
+                                                        int R, int C, double2* __restrict__ out) {
+  __shared__ double2 t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y;
+  for (int z = blockIdx.z; z < W; z += gridDim.z) {
+    const double2* src = in + (long)z * R * C;
+    double2* dst = out + (long)z * R * C;
+    for (int k = ty; k < 32; k += 8)
+      if (r0 + k < R && c0 + tx < C) t[k][tx] = src[(long)(r0 + k) * C + c0 + tx];
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8)
+      if (c0 + k < C && r0 + tx < R) dst[(long)(c0 + k) * R + r0 + tx] = t[tx][k];
+    __syncthreads();
   }
+}
+
+void transpose_cplx(const double2* in, int W, int R, int C, double2* out, cudaStream_t st) {
+  const dim3 grid((C + 31) / 32, (R + 31) / 32, W < 65535 ? W : 65535);
+  k_transpose_cplx<<<grid, dim3(32, 8), 0, st>>>(in, W, R, C, out);
 }
 
 // exponent of each (p, q) row of L^T: max over g of |L_g,pq|
@@ -717,7 +769,8 @@ int warp_grid(long rows) {
 // context integration
 // ===========================================================================
 void mixed_prop_free(afq_ctx* ctx) {
-  for (auto** p : {&ctx->LT_sl, &ctx->Pm_sl, &ctx->y_sl, &ctx->A_sl, &ctx->T_sl[0], &ctx->T_sl[1]})
+  for (auto** p : {&ctx->LT_sl, &ctx->Pm_sl, &ctx->y_sl, &ctx->A_sl, &ctx->T_sl[0], &ctx->T_sl[1],
+                   &ctx->T_neg[0], &ctx->T_neg[1]})
     if (*p) {
       cudaFree(*p);
       *p = nullptr;
@@ -851,7 +904,8 @@ int mixed_prop_init_trial(afq_ctx* ctx) {
 // Per walker set: operand buffers and tensor maps of the propagation.
 int mixed_prop_init_walkers(afq_ctx* ctx) {
   const int S = ctx->Sp, M = ctx->M, N = ctx->N, W = ctx->ws.W, Mp = ctx->Mpad;
-  for (auto** p : {&ctx->y_sl, &ctx->A_sl, &ctx->T_sl[0], &ctx->T_sl[1]})
+  for (auto** p : {&ctx->y_sl, &ctx->A_sl, &ctx->T_sl[0], &ctx->T_sl[1], &ctx->T_neg[0],
+                   &ctx->T_neg[1]})
     if (*p) {
       cudaFree(*p);
       *p = nullptr;
@@ -870,6 +924,10 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->A_sl, (size_t)S * 2 * W * M * Mp * 2));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_sl[0], tbytes));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_sl[1], tbytes));
+  if (S <= kFastSlices) {  // -Im digits of the operands (column-concatenated complex GEMMs)
+    AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_neg[0], tbytes / 2));
+    AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_neg[1], tbytes / 2));
+  }
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->accT, (size_t)W * N * M * sizeof(double2)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->tout, (size_t)W * N * M * sizeof(double2)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_y, (size_t)2 * W * sizeof(int)));
@@ -906,6 +964,7 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
     // of one tile overlaps the MMAs of the next)
     ctx->prop_rows_real = ctx->prop_rows > 32 ? 32 : ctx->prop_rows;
     const uint32_t btr[4] = {kBK, (uint32_t)ctx->prop_rows_real, 1, 1};
+    const uint64_t dtn[4] = {(uint64_t)Mp, (uint64_t)N, (uint64_t)W, (uint64_t)S};
     ctx->prop_rows_fused = fused_prop_rows(N);
     const uint32_t btf[4] = {kBK, (uint32_t)ctx->prop_rows_fused, 1, 1};
     ok = ok && make_tmap(&ctx->tm_pm, ctx->Pm_sl, 3, dp, bp) &&
@@ -916,6 +975,11 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
          make_tmap(&ctx->tm_t_real[1], ctx->T_sl[1], 4, dt, btr) &&
          make_tmap(&ctx->tm_t_fused[0], ctx->T_sl[0], 4, dt, btf) &&
          make_tmap(&ctx->tm_t_fused[1], ctx->T_sl[1], 4, dt, btf);
+    if (ctx->T_neg[0])
+      ok = ok && make_tmap(&ctx->tm_tneg[0], ctx->T_neg[0], 4, dtn, btr) &&
+           make_tmap(&ctx->tm_tneg[1], ctx->T_neg[1], 4, dtn, btr);
+    else
+      ctx->tm_tneg[0] = ctx->tm_tneg[1] = ctx->tm_t_real[0];  // unused
   }
   if (!ok) return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (propagation) failed");
   return AFQ_OK;
@@ -970,13 +1034,24 @@ int sm_count_prop() {
   return n;
 }
 
-template <int S, bool REAL>
+template <int S, bool REAL, bool CAT>
 cudaError_t launch_prop_s(int grid, size_t smem, cudaStream_t stream, const CUtensorMap& ta,
-                          const CUtensorMap& tb, const PropArgs& a) {
-  cudaError_t e = raise_smem_limit((const void*)k_prop_tc<S, REAL>, smem);
+                          const CUtensorMap& tb, const CUtensorMap& tbn, const PropArgs& a) {
+  cudaError_t e = raise_smem_limit((const void*)k_prop_tc<S, REAL, CAT>, smem);
   if (e != cudaSuccess) return e;
-  k_prop_tc<S, REAL><<<grid, 32 * kPropWarps, smem, stream>>>(ta, tb, a);
+  k_prop_tc<S, REAL, CAT><<<grid, 32 * kPropWarps, smem, stream>>>(ta, tb, tbn, a);
   return cudaGetLastError();
+}
+
+// Whether a pass of S digits takes the column-concatenated form (the default per-pass
+// kernel, up to 4 digits; complex passes also need the negated digits, written by the
+// one-pass slicing kernel for rows up to 512).  Complex passes of 1 or 2 digits keep
+// the per-pair form on 64-column tiles: their two accumulator sets fit there already,
+// and 32-column tiles would read the A digits twice (measured slower: 133 -> 183 us
+// per 2-digit pass at 290 orbitals; 3 digits 304 -> 238 us, 4 digits 400 -> 390 us).
+bool prop_cat(const afq_ctx* ctx, int S, bool real) {
+  return ctx->p.prop_kernel == 0 && S <= kFastSlices &&
+         (real || (S >= 3 && ctx->Mpad <= 512 && ctx->T_neg[0] != nullptr));
 }
 
 // One GEMM pass of the propagation (mode first / term / last) on operand buffer b.
@@ -988,40 +1063,51 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   a.N = N;
   a.W = ctx->ws.W;
   a.mode = mode;
-  a.brows = REAL ? ctx->prop_rows_real : ctx->prop_rows;
+  const bool cat = prop_cat(ctx, S, REAL);
+  a.brows = REAL || cat ? ctx->prop_rows_real : ctx->prop_rows;
   a.BN = 2 * a.brows;
   a.nkb = ctx->Mpad / kBK;
   a.npt = (ctx->M + 127) / 128;
   a.njt = (N + a.brows - 1) / a.brows;
   a.ntiles = a.W * a.njt * a.npt;
-  const int kUA = REAL ? 1 : 2;
-  a.tx_bytes = (uint32_t)S * (kUA * kBK * 128 * 2 + 2 * kBK * a.brows * 2);
+  const int kUA = REAL ? 1 : 2, kUB = cat && !REAL ? 2 : 1;
+  a.tx_bytes = (uint32_t)S * (kUA * kBK * 128 * 2 + kUB * 2 * kBK * a.brows * 2);
   a.nbuf = 2 * S * a.BN <= 512 ? 2 : 1;
   a.tmem_cols = tmem_cols_for(a.nbuf * S * a.BN);
   a.ea = ea;
   a.eb = ctx->e_t[b];
   a.accT = ctx->accT;
   a.pdiag = ctx->pdiag;
-  a.phi_out = ctx->ws.phi;
   a.tout = ctx->tout;
+  a.phi_out = ctx->ws.phi;
   a.err = ctx->flags + 2;
-  const size_t stage = (size_t)S * (kUA * (size_t)kASlot + (size_t)a.BN * 64);
+  const size_t stage = (size_t)S * (kUA * (size_t)kASlot + (size_t)kUB * a.BN * 64);
   int nst = (int)((kSmemLimit - 2048 - 1024) / stage);
   if (nst > kMaxStages) nst = kMaxStages;
   if (nst < 1 || S * a.BN > 512) return afq_fail(ctx, AFQ_ERR_ARG, "propagation tile does not fit");
   a.stages = nst;
   const size_t smem = stage * nst + 1024;
   const int grid = a.ntiles < sm_count_prop() ? a.ntiles : sm_count_prop();
-  const CUtensorMap& tb = REAL ? ctx->tm_t_real[b] : ctx->tm_t[b];
+  const CUtensorMap& tb = REAL || cat ? ctx->tm_t_real[b] : ctx->tm_t[b];
+  const CUtensorMap& tbn = ctx->tm_tneg[b];
   cudaError_t e = cudaErrorInvalidValue;
-  switch (S) {
-    case 1: e = launch_prop_s<1, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
-    case 2: e = launch_prop_s<2, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
-    case 3: e = launch_prop_s<3, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
-    case 4: e = launch_prop_s<4, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
-    case 5: e = launch_prop_s<5, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
-    case 6: e = launch_prop_s<6, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
-    case 7: e = launch_prop_s<7, REAL>(grid, smem, ctx->stream, ta, tb, a); break;
+  if (cat) {
+    switch (S) {
+      case 1: e = launch_prop_s<1, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 2: e = launch_prop_s<2, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 3: e = launch_prop_s<3, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 4: e = launch_prop_s<4, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+    }
+  } else {
+    switch (S) {
+      case 1: e = launch_prop_s<1, REAL, false>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 2: e = launch_prop_s<2, REAL, false>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 3: e = launch_prop_s<3, REAL, false>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 4: e = launch_prop_s<4, REAL, false>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 5: e = launch_prop_s<5, REAL, false>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 6: e = launch_prop_s<6, REAL, false>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 7: e = launch_prop_s<7, REAL, false>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+    }
   }
   ctx->launches++;
   if (e != cudaSuccess)
@@ -1032,26 +1118,27 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
 // acc += i^k g_k u_k and the digits of u_k (or of acc after the last term) into
 // operand buffer b; rows longer than 512 take the two-kernel form
 int taylor_slice(afq_ctx* ctx, int b, double gk, int kmod, int last, int S,
-                 const double* kscale = nullptr) {
+                 const double* kscale = nullptr, bool neg = false) {
+  __nv_bfloat16* nout = neg ? ctx->T_neg[b] : nullptr;
   const int W = ctx->ws.W, N = ctx->N, M = ctx->M, Kp = ctx->Mpad;
   const long rows = (long)W * N;
   const int g = warp_grid(rows);
   const bool fast = S <= kFastSlices;
   if (Kp <= 128)
     (fast ? k_taylor_slice<2, kFastSlices> : k_taylor_slice<2, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
-        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], nout, ctx->e_t[b]);
   else if (Kp <= 256)
     (fast ? k_taylor_slice<4, kFastSlices> : k_taylor_slice<4, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
-        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], nout, ctx->e_t[b]);
   else if (Kp <= 320)  // the row in as few registers as it needs: more warps per SM
     (fast ? k_taylor_slice<5, kFastSlices> : k_taylor_slice<5, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
-        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], nout, ctx->e_t[b]);
   else if (Kp <= 384)
     (fast ? k_taylor_slice<6, kFastSlices> : k_taylor_slice<6, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
-        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], nout, ctx->e_t[b]);
   else if (Kp <= 512)
     (fast ? k_taylor_slice<8, kFastSlices> : k_taylor_slice<8, kMaxSlices>)<<<g, 256, 0, ctx->stream>>>(
-        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], ctx->e_t[b]);
+        ctx->tout, ctx->accT, rows, N, M, Kp, S, gk, kmod, last, kscale, ctx->T_sl[b], nout, ctx->e_t[b]);
   else {
     k_taylor_acc<<<grid1d(rows * M), 256, 0, ctx->stream>>>(ctx->tout, ctx->accT, rows * M, M,
                                                             gk, kmod, kscale);
@@ -1084,8 +1171,7 @@ int launch_propagate_tc(afq_ctx* ctx) {
     if (rc != -1) return rc;
   }
   const int W = ctx->ws.W;
-  k_transpose_phi<<<grid1d((long)W * ctx->N * ctx->M), 256, 0, ctx->stream>>>(
-      ctx->ws.phi, W, ctx->M, ctx->N, ctx->tout);
+  transpose_cplx(ctx->ws.phi, W, ctx->M, ctx->N, ctx->tout, ctx->stream);  // Phi^T
   AFQ_LAUNCHED(ctx);
   int cur = 0, rc;
   const int n = ctx->p.taylor_order;
@@ -1096,7 +1182,10 @@ int launch_propagate_tc(afq_ctx* ctx) {
   rc = launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeFirst, dg[0]);
   if (rc != AFQ_OK) return rc;
   cur = 1 - cur;
-  if ((rc = taylor_slice(ctx, cur, 1.0, 0, 1, dg[n >= 1 ? 1 : n + 1], ctx->pdiag)) != AFQ_OK)
+  // u_0 (or, with no Taylor terms, the sum for the last pass); a complex pass of the
+  // column-concatenated form after it also takes the negated imaginary digits
+  if ((rc = taylor_slice(ctx, cur, 1.0, 0, 1, dg[n >= 1 ? 1 : n + 1], ctx->pdiag,
+                         n >= 1 && prop_cat(ctx, dg[1], false))) != AFQ_OK)
     return rc;
   double gk = 1.0;
   for (int k = 1; k <= n; ++k) {
@@ -1104,8 +1193,11 @@ int launch_propagate_tc(afq_ctx* ctx) {
     if (rc != AFQ_OK) return rc;
     cur = 1 - cur;
     gk *= sqrt(ctx->p.dt) / k;
-    if ((rc = taylor_slice(ctx, cur, gk, k & 3, k == n, dg[k + 1])) != AFQ_OK) return rc;
+    if ((rc = taylor_slice(ctx, cur, gk, k & 3, k == n, dg[k + 1], nullptr,
+                           k < n && prop_cat(ctx, dg[k + 1], false))) != AFQ_OK)
+      return rc;
   }
-  // Phi = P acc = diag(P) acc + O acc
+  // Phi = P acc = diag(P) acc + O acc (written in place: a Phi^T output with a tiled
+  // transpose after it measured 35 us slower per step at 290 orbitals)
   return launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeLast, dg[n + 1]);
 }

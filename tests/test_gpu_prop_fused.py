@@ -1,5 +1,7 @@
-"""The split-precision propagation as one cluster kernel (prop_kernel = 1) against the
-per-pass kernels (the default) (GPU).
+"""The split-precision propagation as one cluster kernel (prop_kernel = 1) and as
+per-pass kernels with one MMA per digit pair (prop_kernel = 2) against the default
+per-pass kernels, whose passes of up to 4 digits issue one MMA per A digit over the
+concatenated B digits (GPU).
 
 Both forms run the same arithmetic (the same digits, row exponents, digit products,
 recombination and FP64 updates in the same order), the cluster kernel with every GEMM
@@ -29,6 +31,7 @@ def ctx_for(s, W, phi, kernel, **kw):
     return ctx
 
 
+@pytest.mark.parametrize("other", ["fused", "per_pair"])
 @pytest.mark.parametrize("shape", [
     (37, 5, 3, 71, 13),      # one slab, 16-column tile
     (100, 10, 10, 400, 24),  # one slab, 32-column tile
@@ -37,12 +40,14 @@ def ctx_for(s, W, phi, kernel, **kw):
     (50, 7, 0, 66, 9),       # no beta electrons
     (1024, 64, 64, 5, 2),    # clusters of 8 slabs, two column tiles
 ])
-def test_cluster_kernel_is_bit_identical_to_per_pass(shape):
+def test_other_kernels_are_bit_identical_to_per_pass(shape, other):
+    """The same digits, row exponents and exact integer sums per TMEM accumulator in
+    every form, so the same bits after 6 steps with a QR."""
     need_gpu()
     M, na, nb, X, W = shape
     s = make_system(M, na, nb, X, seed=M + na, decay="geometric", e0=0.1)
     phi = perturbed_walkers(s, W, eps=0.3, seed=3)
-    fused = ctx_for(s, W, phi, "fused")
+    fused = ctx_for(s, W, phi, other)
     ref = ctx_for(s, W, phi, "per_pass")
     nsteps = 6  # a QR after the fifth
     fields = np.stack([gaussian_fields(W, s.X, seed=90 + k) for k in range(nsteps)])
