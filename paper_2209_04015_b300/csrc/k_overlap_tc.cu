@@ -13,9 +13,12 @@
 // two int64 halves (d <= 3 and d >= 4, each below 2^53) and adds them in FP64 once,
 // so S carries FP64-level rounding, and writes the two diagonal spin blocks per walker.
 //
-// GEMM: A = Psi^T digits (N rows, alpha then beta, one 128-row tile), B = Phi^T digits
-// (rows (z, re/im, j), K = p), D[i][(z, re/im, j)]; the off-diagonal spin blocks are
-// computed and dropped.
+// GEMM: A = Phi^T digits (128-row tiles of the rows (z, re/im, j), K = p), B = Psi^T
+// digits (N rows, alpha then beta, in 64-column tiles), D[(z, re/im, j)][i] = S^T;
+// the off-diagonal spin blocks are computed and dropped.  The B digit slots lie one
+// after another in shared memory, so A digit s times B digits 0 .. 6 - s is one MMA of
+// (7 - s) 64 columns (split at 256) into accumulators s .. 6: 10 MMAs per 16-wide K
+// step instead of the 28 digit pairs, each reading its A digit once.
 #include "tc_engine.cuh"
 
 using namespace tce;
@@ -23,7 +26,7 @@ using namespace tce;
 namespace {
 
 constexpr int kOvDigits = 7;
-constexpr int kOvBN = 64;  // 7 accumulators x 64 columns fit the 512 TMEM columns
+constexpr int kOvBN = 64;  // columns i per tile: 7 accumulators x 64 fit the 512 TMEM columns
 
 // The exact digits of exact_digits for up to 7 digits (q[s] of weight 256^-s).
 __device__ __forceinline__ void exact_digits7(double x, int e, int S, int (&q)[kOvDigits]) {
@@ -132,7 +135,7 @@ struct OvP {
   struct Args {
     TcCommon c;
     int N, na, nb, nmax;
-    long rows_b;        // 2 W N
+    long rows_a;        // 2 W N rows (z, re/im, j) of Phi^T
     const int* ea;      // row exponents of Psi^T
     const int* eb;      // exponents of Phi^T per complex row (z, j)
     double2* S;         // W x 2 x nmax x nmax
@@ -144,15 +147,27 @@ struct OvP {
   template <int SS>
   static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
                                uint32_t bslot, bool first) {
-    issue_diagonals<SS>(tmem, (uint32_t)a.c.BN, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN),
-                        first);
+    const uint32_t BN = (uint32_t)a.c.BN;
+#pragma unroll
+    for (int s = 0; s < SS; ++s)
+#pragma unroll
+      for (int t0 = 0; t0 < SS - s; t0 += 4) {
+        const int nt = SS - s - t0 < 4 ? SS - s - t0 : 4;
+        const uint32_t idesc = tc::idesc_bf16(128, nt * (int)BN);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+          tc::mma_bf16(tmem + (uint32_t)(s + t0) * BN,
+                       tc::sdesc_k64(a_unit(sa, SS, 0, s) + ks * 32),
+                       tc::sdesc_k64(b_unit(sb, bslot, SS, 0, t0) + ks * 32), idesc,
+                       !(first && s == 0 && ks == 0));
+      }
   }
   static __device__ Tile tile(const Args& a) {
-    return Tile{0, (int)blockIdx.x * a.c.BN, 0, a.c.nkb};
+    return Tile{(int)blockIdx.x * 128, (int)blockIdx.y * kOvBN, 0, a.c.nkb};
   }
-  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile&, int,
+  static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int,
                                 int s, int kb, uint64_t* bar) {
-    tc::tma_load_3d(dst, tm, kb * kBK, 0, s, bar);
+    tc::tma_load_3d(dst, tm, kb * kBK, t.r0, s, bar);
   }
   static __device__ void load_b(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int,
                                 int s, int kb, uint64_t* bar) {
@@ -161,32 +176,28 @@ struct OvP {
   template <int SS>
   static __device__ void epilogue(const Args& a, const Tile& t, uint32_t tmem, uint8_t*, int warp,
                                   int lane) {
-    const int i = warp * 32 + lane;  // row of Psi^T: orbital i of the trial
-    const bool valid = i < a.N;
-    const int si = i < a.na ? 0 : 1, oi = si ? a.na : 0;
-    const int ei = valid ? a.ea[i] : 0;
+    const long row = (long)t.r0 + warp * 32 + lane;  // row of Phi^T: (z, re/im, j)
+    const bool valid = row < a.rows_a;
     const int N = a.N;
+    const long zp = valid ? row / N : 0;
+    const int j = valid ? (int)(row - zp * N) : 0, part = (int)(zp & 1);
+    const long z = zp >> 1;
+    const int sj = j < a.na ? 0 : 1, oj = sj ? a.na : 0;
+    const int ej = valid ? a.eb[z * N + j] : 0;
+    double* dst = reinterpret_cast<double*>(a.S + (z * 2 + sj) * (long)a.nmax * a.nmax) + part;
     for (int c0 = 0; c0 < a.c.BN; c0 += 16) {
       float f[kOvDigits][16];
 #pragma unroll
       for (int d = 0; d < kOvDigits; ++d) tmem_row16(tmem + (uint32_t)(d * a.c.BN), warp, c0, f[d]);
       if (!valid) continue;
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        const long col = (long)t.n0 + c0 + jj;  // row of Phi^T: (z, re/im, j)
-        if (col >= a.rows_b) continue;
-        const long zp = col / N;
-        const int j = (int)(col - zp * N), part = (int)(zp & 1);
-        const long z = zp >> 1;
-        const int sj = j < a.na ? 0 : 1;
-        if (sj != si) continue;
+      for (int ii = 0; ii < 16; ++ii) {
+        const int i = t.n0 + c0 + ii;  // orbital i of the trial
+        if (i >= N || (i < a.na ? 0 : 1) != sj) continue;
         float acc[kOvDigits];
 #pragma unroll
-        for (int d = 0; d < kOvDigits; ++d) acc[d] = f[d][jj];
-        const double v = combine7(acc, ei + a.eb[z * N + j] - 14);
-        double* dst = reinterpret_cast<double*>(
-            a.S + ((z * 2 + si) * a.nmax + (i - oi)) * a.nmax + (j - oi));
-        dst[part] = v;
+        for (int d = 0; d < kOvDigits; ++d) acc[d] = f[d][ii];
+        dst[2 * ((long)(i - oj) * a.nmax + (j - oj))] = combine7(acc, a.ea[i] + ej - 14);
       }
     }
   }
@@ -212,7 +223,7 @@ int overlap_tc_init_trial(afq_ctx* ctx) {
                                                          ctx->ov_psi_sl, ctx->ov_ea);
   AFQ_LAUNCHED(ctx);
   const uint64_t da[3] = {(uint64_t)Mpad, (uint64_t)N, (uint64_t)kOvDigits};
-  const uint32_t ba[3] = {kBK, 128, 1};
+  const uint32_t ba[3] = {kBK, (uint32_t)kOvBN, 1};
   if (!make_tmap(&ctx->tm_ov_a, ctx->ov_psi_sl, 3, da, ba))
     return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (overlap) failed");
   return AFQ_OK;
@@ -232,7 +243,7 @@ int overlap_tc_init_walkers(afq_ctx* ctx) {
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_eb, (size_t)W * N * sizeof(int)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_S, (size_t)W * 2 * nmax * nmax * sizeof(double2)));
   const uint64_t db[3] = {(uint64_t)Mpad, (uint64_t)rows, (uint64_t)kOvDigits};
-  const uint32_t bb[3] = {kBK, (uint32_t)kOvBN, 1};
+  const uint32_t bb[3] = {kBK, 128, 1};
   if (!make_tmap(&ctx->tm_ov_b, ctx->ov_phi_sl, 3, db, bb))
     return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (overlap) failed");
   return AFQ_OK;
@@ -265,7 +276,7 @@ int launch_overlap_s_tc(afq_ctx* ctx, WalkerSet& s) {
   a.na = ctx->na;
   a.nb = ctx->nb;
   a.nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
-  a.rows_b = 2L * W * N;
+  a.rows_a = 2L * W * N;
   a.ea = ctx->ov_ea;
   a.eb = ctx->ov_eb;
   a.S = ctx->ov_S;
@@ -273,8 +284,8 @@ int launch_overlap_s_tc(afq_ctx* ctx, WalkerSet& s) {
   plan_smem(kOvDigits, 1, 1, kOvBN, 0, &a.c.stages, &smem);
   if (a.c.stages < 1 || smem > kSmemLimit)
     return afq_fail(ctx, AFQ_ERR_ARG, "overlap tile does not fit in shared memory");
-  dim3 grid((unsigned)((a.rows_b + kOvBN - 1) / kOvBN));
-  cudaError_t e = launch_tc<kOvDigits, OvP>(grid, smem, ctx->stream, ctx->tm_ov_a, ctx->tm_ov_b, a);
+  dim3 grid((unsigned)((a.rows_a + 127) / 128), (unsigned)((N + kOvBN - 1) / kOvBN));
+  cudaError_t e = launch_tc<kOvDigits, OvP>(grid, smem, ctx->stream, ctx->tm_ov_b, ctx->tm_ov_a, a);
   ctx->launches++;
   if (e != cudaSuccess)
     return afq_fail(ctx, AFQ_ERR_CUDA, std::string("overlap tc: ") + cudaGetErrorString(e));
