@@ -55,9 +55,9 @@ FP64_ALU_TFLOPS = 148 * 4 * 2.032e9 / 1e12
 # these exact workloads: per launch for the FP64 kernels, per step (every launch of
 # the class) for the split propagation; absent where no capture of the current
 # kernels exists.
-TRAFFIC = {("fp64", "c2", "propagate"): 34943232 + 16384,
-           ("fp64", "c3", "vhs"): 40627748352 + 1298133760,
-           ("split_bf16", "c3", "propagate"): 7590425344 + 2743548160}
+TRAFFIC = {("fp64", "c2", "propagate"): 34945792 + 0,
+           ("fp64", "c3", "vhs"): 40650807296 + 1304730112,
+           ("split_bf16", "c3", "propagate"): 7700683776 + 2990288128}
 FP64_KERNELS = {"propagate": "k_propagate_fp64", "exchange": "k_exchange_v / k_exchange_fp64",
                 "vhs": "k_vhs_fp64", "force_bias": "k_force_bias_fp64"}
 SPLIT_KERNELS = {"propagate": "k_prop_tc (8 GEMM passes) + k_taylor_slice / k_slice_cplx1",
@@ -487,7 +487,9 @@ def step_leg(name: str, precision: str, steps: int, warmup: int, rank: int, worl
         out["prop_digits"] = digits
         out["split_slices"] = S
         out["tensor_flops_per_step"] = sum(flops.values())
-        traffic = TRAFFIC.get(("split_bf16", name, dom)) if not walkers else None
+        # the captured split traffic is that of the default digits (4 and 4)
+        traffic = (TRAFFIC.get(("split_bf16", name, dom))
+                   if not walkers and S == 4 and Sp == 4 else None)
         algo = algorithmic_bytes("split_bf16", dom, W, X, M, na, nb, digits)
         out["roofline"] = {"bound": "tensor", "kernel": f"{dom} ({SPLIT_KERNELS[dom]})",
                            "achieved": per_step / dom_s / 1e12, "unit": "TFLOP/s",
