@@ -510,8 +510,9 @@ def attach_peak(roof: dict, peaks: dict, fp64: dict | None) -> dict:
     """Roofline denominators: measured BF16 (MEASURED_PEAKS.json, burst and sustained)
     for tensor-bound classes, the FP64 ALU peak for FP64 ones; the DRAM rate of the
     captured traffic as a fraction of the measured HBM copy bandwidth beside them."""
+    hbm = peaks.get("hbm_gbs", 6400.0)
     if roof.get("dram_gbs"):
-        roof["dram_frac_of_hbm"] = roof["dram_gbs"] / peaks.get("hbm_gbs", 6400.0)
+        roof["dram_frac_of_hbm"] = roof["dram_gbs"] / hbm
     if roof["bound"] == "tensor":
         burst = peaks.get("bf16_tflops", 1800.0)
         sust = peaks.get("bf16_tflops_sustained", 1400.0)
@@ -520,6 +521,30 @@ def attach_peak(roof: dict, peaks: dict, fp64: dict | None) -> dict:
                     peak_source="MEASURED_PEAKS.json bf16_tflops (burst, measured; "
                                 "bf16_tflops_sustained for frac_of_sustained)"
                     if "bf16_tflops" in peaks else "fallback 1.8 PFLOP/s bf16 burst")
+        algo, fl = roof.get("algorithmic_bytes"), roof.get("flops_per_step")
+        if algo and fl:
+            # the roofline model: below the ridge point the class is bound by HBM, and
+            # its roofline is the algorithmic bytes over the measured copy bandwidth
+            intensity = fl / algo
+            ridge = burst * 1e12 / (hbm * 1e9)
+            attainable = min(burst, intensity * hbm * 1e9 / 1e12)
+            tensor = {"achieved": roof["achieved"], "unit": "TFLOP/s", "peak": burst,
+                      "frac": roof["achieved"] / burst,
+                      "frac_of_sustained": roof["achieved"] / sust,
+                      "attainable": attainable,
+                      "frac_of_attainable": roof["achieved"] / attainable}
+            roof.update(intensity_flop_per_byte=intensity, ridge_flop_per_byte=ridge)
+            if intensity < ridge:
+                sec = roof["ms_per_step"] / 1e3
+                gbs = algo / sec / 1e9
+                for k in ("frac_of_sustained",):
+                    roof.pop(k, None)
+                roof.update(bound="hbm", achieved=gbs, unit="GB/s", peak=hbm, frac=gbs / hbm,
+                            peak_source="MEASURED_PEAKS.json hbm_gbs (copy bandwidth, "
+                                        "measured)" if "hbm_gbs" in peaks
+                            else "fallback 6.4 TB/s", tensor=tensor)
+            else:
+                roof["tensor"] = tensor
     else:
         p = fp64["tflops"]
         roof.update(peak=p, frac=roof["achieved"] / p,
