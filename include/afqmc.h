@@ -109,7 +109,10 @@ typedef struct afq_params {
                           2x slower on this part, kept as an option), falling back
                           to 0 where a shape cannot take it; 2 = the per-pass
                           kernels with one MMA per digit pair (64-column complex
-                          tiles).  All give the same bits.                         */
+                          tiles), and so every other split GEMM (force bias, VHS,
+                          stored exchange, overlap product), which otherwise issue
+                          one MMA per A digit over the concatenated B digits.  All
+                          give the same bits.                                      */
 } afq_params;
 
 /* Fill *p with the defaults: dt 0.005, Taylor order 6, QR every 5 steps, seed 1,

@@ -41,8 +41,7 @@ struct ExVP {
   template <int S>
   static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
                                uint32_t bslot, bool first) {
-    issue_diagonals<S>(tmem, (uint32_t)a.c.BN, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN),
-                       first);
+    issue_split<S>(a.c, tmem, sa, sb, bslot, first);
   }
   struct Tile {
     int r0, n0, kb0, kb1;  // r0: first row in the stacked V'; K blocks from the diagonal
@@ -256,6 +255,7 @@ int launch_exchange_tcv(afq_ctx* ctx, WalkerSet& s) {
   a.c.tx_bytes = (uint32_t)ctx->S * (kBK * 128 * 2 + kBK * ctx->exv_BN * 2);
   a.c.tmem_cols = tmem_cols_for(ctx->S * ctx->exv_BN);
   a.c.err = ctx->flags + 2;
+  a.c.per_pair = ctx->p.prop_kernel == 2;
   a.W2 = W2;
   a.ea = ctx->exv_ea;
   a.eb = ctx->exv_eb;

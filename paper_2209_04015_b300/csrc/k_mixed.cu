@@ -78,8 +78,7 @@ struct FbP {
   template <int S>
   static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
                                uint32_t bslot, bool first) {
-    issue_diagonals<S>(tmem, (uint32_t)a.c.BN, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN),
-                       first);
+    issue_split<S>(a.c, tmem, sa, sb, bslot, first);
   }
   struct Tile {
     int g0, n0, ks, kb0, kb1;
@@ -481,6 +480,7 @@ int launch_force_bias_tc(afq_ctx* ctx, WalkerSet& s) {
   a.c.tx_bytes = (uint32_t)ctx->S * (kBK * 128 * 2 + kBK * ctx->fb_BN * 2);
   a.c.tmem_cols = tmem_cols_for(ctx->S * ctx->fb_BN);
   a.c.err = ctx->flags + 2;
+  a.c.per_pair = ctx->p.prop_kernel == 2;
   a.X = ctx->X;
   a.W2 = 2 * s.W;
   a.kbper = ctx->fb_kbper;

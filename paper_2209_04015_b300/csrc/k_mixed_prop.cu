@@ -54,8 +54,7 @@ struct VhsP {
   template <int S>
   static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
                                uint32_t bslot, bool first) {
-    issue_diagonals<S>(tmem, (uint32_t)a.c.BN, sa, sb, bslot, 0, 0, tc::idesc_bf16(128, a.c.BN),
-                       first);
+    issue_split<S>(a.c, tmem, sa, sb, bslot, first);
   }
   static __device__ Tile tile(const Args& a) {
     return Tile{(int)blockIdx.y * 128, (int)blockIdx.x * a.c.BN, 0, a.c.nkb};
@@ -1004,6 +1003,7 @@ int launch_vhs_tc(afq_ctx* ctx) {
   a.c.tx_bytes = (uint32_t)S * (kBK * 128 * 2 + kBK * a.c.BN * 2);
   a.c.tmem_cols = tmem_cols_for(S * a.c.BN);
   a.c.err = ctx->flags + 2;
+  a.c.per_pair = ctx->p.prop_kernel == 2;
   a.M = M;
   a.W = W;
   a.Mp = ctx->Mp;

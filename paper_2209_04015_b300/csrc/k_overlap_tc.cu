@@ -147,20 +147,7 @@ struct OvP {
   template <int SS>
   static __device__ void issue(const Args& a, uint32_t tmem, uint32_t sa, uint32_t sb,
                                uint32_t bslot, bool first) {
-    const uint32_t BN = (uint32_t)a.c.BN;
-#pragma unroll
-    for (int s = 0; s < SS; ++s)
-#pragma unroll
-      for (int t0 = 0; t0 < SS - s; t0 += 4) {
-        const int nt = SS - s - t0 < 4 ? SS - s - t0 : 4;
-        const uint32_t idesc = tc::idesc_bf16(128, nt * (int)BN);
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks)
-          tc::mma_bf16(tmem + (uint32_t)(s + t0) * BN,
-                       tc::sdesc_k64(a_unit(sa, SS, 0, s) + ks * 32),
-                       tc::sdesc_k64(b_unit(sb, bslot, SS, 0, t0) + ks * 32), idesc,
-                       !(first && s == 0 && ks == 0));
-      }
+    issue_split<SS>(a.c, tmem, sa, sb, bslot, first);
   }
   static __device__ Tile tile(const Args& a) {
     return Tile{(int)blockIdx.x * 128, (int)blockIdx.y * kOvBN, 0, a.c.nkb};
@@ -272,6 +259,7 @@ int launch_overlap_s_tc(afq_ctx* ctx, WalkerSet& s) {
   a.c.tx_bytes = (uint32_t)kOvDigits * (kBK * 128 * 2 + kBK * kOvBN * 2);
   a.c.tmem_cols = tmem_cols_for(kOvDigits * kOvBN);
   a.c.err = ctx->flags + 2;
+  a.c.per_pair = ctx->p.prop_kernel == 2;
   a.N = N;
   a.na = ctx->na;
   a.nb = ctx->nb;
