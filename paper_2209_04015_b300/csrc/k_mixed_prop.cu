@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
               const __grid_constant__ CUtensorMap tmBn, const __grid_constant__ PropArgs a) {
   constexpr int kUA = REAL ? 1 : 2;
   constexpr int kUB = (CAT && !REAL) ? 2 : 1;  // B regions per digit: [Re; Im] (+ [-Im; Re])
-  static_assert(!CAT || S <= 4, "the column-concatenated form takes up to 4 digits");
+  static_assert(!CAT || S <= kMaxSlices, "digits");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -327,7 +327,8 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
           const uint32_t sb = sa + S * kUA * kASlot;
-          if constexpr (CAT) {
+          if constexpr (CAT && S <= 4) {
+            // S BN <= 256: A digit s takes all its B slots in one MMA
 #pragma unroll
             for (int s = 0; s < S; ++s) {
               const uint32_t idn = tc::idesc_bf16(128, (S - s) * BN);
@@ -343,6 +344,26 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
                                tc::sdesc_k64(sb + S * bslot + ks * 32), idn, 1);
               }
             }
+          } else if constexpr (CAT) {
+            const int tmax = 256 / BN;  // B slots per MMA (N <= 256)
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+              for (int t0 = 0; t0 < S - s; t0 += tmax) {
+                const int nt = S - s - t0 < tmax ? S - s - t0 : tmax;
+                const uint32_t idn = tc::idesc_bf16(128, nt * BN);
+                const uint32_t d = acc + (uint32_t)((s + t0) * BN);
+                const uint32_t b1 = sb + (uint32_t)t0 * bslot;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks)
+                  tc::mma_bf16(d, tc::sdesc_k64(a_unit(sa, S, 0, s) + ks * 32),
+                               tc::sdesc_k64(b1 + ks * 32), idn, !(kb == 0 && s == 0 && ks == 0));
+                if (!REAL) {
+#pragma unroll
+                  for (int ks = 0; ks < 2; ++ks)
+                    tc::mma_bf16(d, tc::sdesc_k64(a_unit(sa, S, 1, s) + ks * 32),
+                                 tc::sdesc_k64(b1 + S * bslot + ks * 32), idn, 1);
+                }
+              }
           } else {
             issue_diagonals<S>(acc, (uint32_t)BN, sa, sb, bslot, 0, 0, id_full, kb == 0);
             if (!REAL) {
@@ -923,10 +944,9 @@ int mixed_prop_init_walkers(afq_ctx* ctx) {
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->A_sl, (size_t)S * 2 * W * M * Mp * 2));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_sl[0], tbytes));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_sl[1], tbytes));
-  if (S <= kFastSlices) {  // -Im digits of the operands (column-concatenated complex GEMMs)
-    AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_neg[0], tbytes / 2));
-    AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_neg[1], tbytes / 2));
-  }
+  // -Im digits of the operands (column-concatenated complex GEMMs)
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_neg[0], tbytes / 2));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->T_neg[1], tbytes / 2));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->accT, (size_t)W * N * M * sizeof(double2)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->tout, (size_t)W * N * M * sizeof(double2)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->e_y, (size_t)2 * W * sizeof(int)));
@@ -1044,13 +1064,14 @@ cudaError_t launch_prop_s(int grid, size_t smem, cudaStream_t stream, const CUte
 }
 
 // Whether a pass of S digits takes the column-concatenated form (the default per-pass
-// kernel, up to 4 digits; complex passes also need the negated digits, written by the
-// one-pass slicing kernel for rows up to 512).  Complex passes of 1 or 2 digits keep
+// kernel, whose S accumulators of prop_rows_real-wide tiles fit TMEM; complex passes
+// also need the negated digits, written by the one-pass slicing kernel for rows up to
+// 512).  Complex passes of 1 or 2 digits keep
 // the per-pair form on 64-column tiles: their two accumulator sets fit there already,
 // and 32-column tiles would read the A digits twice (measured slower: 133 -> 183 us
 // per 2-digit pass at 290 orbitals; 3 digits 304 -> 238 us, 4 digits 400 -> 390 us).
 bool prop_cat(const afq_ctx* ctx, int S, bool real) {
-  return ctx->p.prop_kernel == 0 && S <= kFastSlices &&
+  return ctx->p.prop_kernel == 0 && 2 * S * ctx->prop_rows_real <= 512 &&
          (real || (S >= 3 && ctx->Mpad <= 512 && ctx->T_neg[0] != nullptr));
 }
 
@@ -1097,6 +1118,9 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
       case 2: e = launch_prop_s<2, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
       case 3: e = launch_prop_s<3, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
       case 4: e = launch_prop_s<4, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 5: e = launch_prop_s<5, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 6: e = launch_prop_s<6, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 7: e = launch_prop_s<7, REAL, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
     }
   } else {
     switch (S) {

@@ -1,4 +1,5 @@
-"""Split precision at FP64 quality (7 exact digits per operand) against the oracle (GPU).
+"""Split precision at FP64 quality (7 exact digits per operand) against the oracle, and
+its two MMA issue forms against each other (GPU).
 
 With split_slices = prop_slices = 7 every tensor-core contraction (force bias, VHS,
 Taylor powers and one-body halves, stored exchange, overlap product) takes 55-bit
@@ -70,3 +71,34 @@ def test_seven_digits_need_the_stored_exchange():
     with pytest.raises(AfqError) as e:
         ctx.init_trial(s.psi_a, s.psi_b)
     assert e.value.code == AFQ_ERR_ARG
+
+
+@pytest.mark.parametrize("shape", [(37, 5, 3, 71, 13), (96, 20, 20, 101, 7)])
+def test_seven_digit_mma_forms_are_bit_identical(shape):
+    """Every split GEMM at 7 digits with one MMA per A digit over the concatenated B
+    digits (the default) against one MMA per digit pair (prop_kernel 'per_pair'): the
+    same exact integer sums per TMEM accumulator, so the same bits after 6 steps with
+    a QR, and the same energies."""
+    from paper_2209_04015_b300 import AfqContext
+    M, na, nb, X, W = shape
+    s = make_system(M, na, nb, X, seed=M + 11, decay="geometric", e0=0.2)
+    phi = perturbed_walkers(s, W, eps=0.3, seed=5)
+    ctxs = []
+    for kernel in ("per_pass", "per_pair"):
+        ctx = AfqContext(dt=0.005, qr_period=5, prop_kernel=kernel, **DIGITS)
+        ctx.init_hamiltonian(s.h1, s.L, s.e0)
+        ctx.init_trial(s.psi_a, s.psi_b)
+        ctx.init_walkers(W, phi)
+        ctxs.append(ctx)
+    fields = np.stack([gaussian_fields(W, s.X, seed=40 + k) for k in range(6)])
+    for ctx in ctxs:
+        ctx.propagate(fields, 6)
+    a, b = ctxs
+    assert np.array_equal(a.get_walkers(), b.get_walkers())
+    assert np.array_equal(a.get_weights(), b.get_weights())
+    assert np.array_equal(a.get_overlaps(), b.get_overlaps())
+    ea, _ = a.local_energy()
+    eb, _ = b.local_energy()
+    assert np.array_equal(ea, eb)
+    for ctx in ctxs:
+        ctx.close()
