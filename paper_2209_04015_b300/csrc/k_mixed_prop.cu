@@ -133,6 +133,8 @@ struct PropArgs {
   int M, N, W, mode, brows, BN, nkb, stages, npt, njt, ntiles;
   int nbuf;               // TMEM accumulator sets (2 when 2 S BN <= 512: the epilogue of
                           // one tile overlaps the MMAs of the next)
+  int split;              // column-concatenated complex pass: each K block takes two ring
+                          // stages, [Re A digits | Re T; Im T] then [Im A digits | -Im T; Re T]
   uint32_t tx_bytes, tmem_cols;
   const int* ea;          // row exponents of A: O (P off the diagonal) per p, or V_z per (z, p)
   const double* pdiag;    // M: diagonal of P (mode last adds diag(P) acc in FP64)
@@ -209,6 +211,37 @@ __device__ __forceinline__ void prop_epi_group(const PropArgs& a, uint32_t trow,
   }
 }
 
+// Column-concatenated MMAs of one A unit (S digit slots of 128 rows at a0) against one
+// B region (S slots of BN rows at b0): A digit s times B slots t0 .. t0 + nt - 1 is one
+// MMA of nt BN columns (N <= 256) into accumulators s + t0 .. (BN columns apart).
+template <int S>
+__device__ __forceinline__ void prop_issue_cat(uint32_t acc, int BN, uint32_t a0, uint32_t b0,
+                                               uint32_t bslot, bool first) {
+  if constexpr (S <= 4) {  // S BN <= 256 (BN <= 64): one MMA per A digit
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const uint32_t idn = tc::idesc_bf16(128, (S - s) * BN);
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks)
+        tc::mma_bf16(acc + (uint32_t)(s * BN), tc::sdesc_k64(a0 + s * kASlot + ks * 32),
+                     tc::sdesc_k64(b0 + ks * 32), idn, !(first && s == 0 && ks == 0));
+    }
+  } else {
+    const int tmax = 256 / BN;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      for (int t0 = 0; t0 < S - s; t0 += tmax) {
+        const int nt = S - s - t0 < tmax ? S - s - t0 : tmax;
+        const uint32_t idn = tc::idesc_bf16(128, nt * BN);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+          tc::mma_bf16(acc + (uint32_t)((s + t0) * BN), tc::sdesc_k64(a0 + s * kASlot + ks * 32),
+                       tc::sdesc_k64(b0 + (uint32_t)t0 * bslot + ks * 32), idn,
+                       !(first && s == 0 && ks == 0));
+      }
+  }
+}
+
 template <int S, bool REAL, bool CAT>
 __global__ void __launch_bounds__(32 * kPropWarps, 1)
     k_prop_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -232,7 +265,8 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nst = a.stages, BN = a.BN, brows = a.brows;
   const uint32_t bslot = (uint32_t)BN * 64u;
-  const uint32_t stage_bytes = S * (kUA * kASlot + kUB * bslot);
+  const int nh = (kUB == 2 && a.split) ? 2 : 1;  // ring stages per K block
+  const uint32_t stage_bytes = nh == 2 ? S * (kASlot + bslot) : S * (kUA * kASlot + kUB * bslot);
   int* err = a.err;
   if (threadIdx.x == 0) skip = *(const volatile int*)err;
   __syncthreads();
@@ -269,7 +303,8 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
       for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
         const int z = tile / per_z, r = tile - z * per_z;
         const int p0 = (r % a.npt) * 128, j0 = (r / a.npt) * brows;
-        for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+        for (int hb = 0; hb < nh * a.nkb; ++hb, ++it) {
+          const int kb = hb / nh, h = hb - kb * nh;
           const int st = it % nst;
           if (it >= nst && !tc::mbar_wait(&empty[st], ((it / nst) - 1) & 1, err)) {
             atomicExch(err, 1);
@@ -278,6 +313,20 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
           }
           tc::mbar_arrive_expect_tx(&full[st], a.tx_bytes);
           uint8_t* sa = smem + st * stage_bytes;
+          if (nh == 2) {  // h = 0: Re A and [Re T; Im T]; h = 1: Im A and [-Im T; Re T]
+            uint8_t* sb = sa + S * kASlot;
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+              tc::tma_load_4d(sa + s * kASlot, &tmA, kb * kBK, p0, 2 * z + h, s, &full[st]);
+              if (h == 0)
+                tc::tma_load_4d(sb + s * bslot, &tmB, kb * kBK, j0, 2 * z, s, &full[st]);
+              else
+                tc::tma_load_4d(sb + s * bslot, &tmBn, kb * kBK, j0, z, s, &full[st]);
+              tc::tma_load_4d(sb + s * bslot + brows * 64, &tmB, kb * kBK, j0, 2 * z + 1 - h, s,
+                              &full[st]);
+            }
+            continue;
+          }
           uint8_t* sb = sa + S * kUA * kASlot;
 #pragma unroll
           for (int s = 0; s < S; ++s) {
@@ -317,7 +366,8 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
         }
         tc::fence_after_sync();
         const uint32_t acc = tmem + (uint32_t)(buf * S * BN);
-        for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+        for (int hb = 0; hb < nh * a.nkb; ++hb, ++it) {
+          const int kb = hb / nh, h = hb - kb * nh;
           const int st = it % nst;
           if (!tc::mbar_wait(&full[st], (it / nst) & 1, err)) {
             atomicExch(err, 1);
@@ -326,44 +376,17 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
           }
           tc::fence_after_sync();
           const uint32_t sa = tc::smem_u32(smem + st * stage_bytes);
+          if (nh == 2) {
+            // one A unit against one B region per stage: Re A [Re T; Im T] adds
+            // [Re A Re T | Re A Im T], Im A [-Im T; Re T] adds [-Im A Im T | Im A Re T]
+            if constexpr (CAT) prop_issue_cat<S>(acc, BN, sa, sa + S * kASlot, bslot, kb == 0 && h == 0);
+            tc::mma_commit(&empty[st]);
+            continue;
+          }
           const uint32_t sb = sa + S * kUA * kASlot;
-          if constexpr (CAT && S <= 4) {
-            // S BN <= 256: A digit s takes all its B slots in one MMA
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-              const uint32_t idn = tc::idesc_bf16(128, (S - s) * BN);
-              const uint32_t d = acc + (uint32_t)(s * BN);
-#pragma unroll
-              for (int ks = 0; ks < 2; ++ks)
-                tc::mma_bf16(d, tc::sdesc_k64(a_unit(sa, S, 0, s) + ks * 32),
-                             tc::sdesc_k64(sb + ks * 32), idn, !(kb == 0 && s == 0 && ks == 0));
-              if (!REAL) {
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks)
-                  tc::mma_bf16(d, tc::sdesc_k64(a_unit(sa, S, 1, s) + ks * 32),
-                               tc::sdesc_k64(sb + S * bslot + ks * 32), idn, 1);
-              }
-            }
-          } else if constexpr (CAT) {
-            const int tmax = 256 / BN;  // B slots per MMA (N <= 256)
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-              for (int t0 = 0; t0 < S - s; t0 += tmax) {
-                const int nt = S - s - t0 < tmax ? S - s - t0 : tmax;
-                const uint32_t idn = tc::idesc_bf16(128, nt * BN);
-                const uint32_t d = acc + (uint32_t)((s + t0) * BN);
-                const uint32_t b1 = sb + (uint32_t)t0 * bslot;
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks)
-                  tc::mma_bf16(d, tc::sdesc_k64(a_unit(sa, S, 0, s) + ks * 32),
-                               tc::sdesc_k64(b1 + ks * 32), idn, !(kb == 0 && s == 0 && ks == 0));
-                if (!REAL) {
-#pragma unroll
-                  for (int ks = 0; ks < 2; ++ks)
-                    tc::mma_bf16(d, tc::sdesc_k64(a_unit(sa, S, 1, s) + ks * 32),
-                                 tc::sdesc_k64(b1 + S * bslot + ks * 32), idn, 1);
-                }
-              }
+          if constexpr (CAT) {
+            prop_issue_cat<S>(acc, BN, sa, sb, bslot, kb == 0);
+            if (!REAL) prop_issue_cat<S>(acc, BN, sa + S * kASlot, sb + S * bslot, bslot, false);
           } else {
             issue_diagonals<S>(acc, (uint32_t)BN, sa, sb, bslot, 0, 0, id_full, kb == 0);
             if (!REAL) {
@@ -1092,7 +1115,14 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   a.njt = (N + a.brows - 1) / a.brows;
   a.ntiles = a.W * a.njt * a.npt;
   const int kUA = REAL ? 1 : 2, kUB = cat && !REAL ? 2 : 1;
-  a.tx_bytes = (uint32_t)S * (kUA * kBK * 128 * 2 + kUB * 2 * kBK * a.brows * 2);
+  // a complex pass in the concatenated form whose K block fills less than two ring
+  // stages takes two stages per K block (one A unit and one B region each): twice the
+  // ring depth for the same bytes (measured at 290 orbitals with 7 digits: propagation
+  // 8.64 -> 7.36 ms; at 4 digits, where two whole stages fit, 3.04 -> 3.09 ms, so not there)
+  const size_t whole = (size_t)S * (kUA * (size_t)kASlot + (size_t)kUB * a.BN * 64);
+  a.split = kUB == 2 && (kSmemLimit - 2048 - 1024) / whole < 2 ? 1 : 0;
+  a.tx_bytes = a.split ? (uint32_t)S * (kBK * 128 * 2 + 2 * kBK * a.brows * 2)
+                       : (uint32_t)S * (kUA * kBK * 128 * 2 + kUB * 2 * kBK * a.brows * 2);
   a.nbuf = 2 * S * a.BN <= 512 ? 2 : 1;
   a.tmem_cols = tmem_cols_for(a.nbuf * S * a.BN);
   a.ea = ea;
@@ -1102,7 +1132,8 @@ int launch_prop(afq_ctx* ctx, const CUtensorMap& ta, int b, const int* ea, int m
   a.tout = ctx->tout;
   a.phi_out = ctx->ws.phi;
   a.err = ctx->flags + 2;
-  const size_t stage = (size_t)S * (kUA * (size_t)kASlot + (size_t)kUB * a.BN * 64);
+  const size_t stage = a.split ? (size_t)S * ((size_t)kASlot + (size_t)a.BN * 64)
+                               : (size_t)S * (kUA * (size_t)kASlot + (size_t)kUB * a.BN * 64);
   int nst = (int)((kSmemLimit - 2048 - 1024) / stage);
   if (nst > kMaxStages) nst = kMaxStages;
   if (nst < 1 || S * a.BN > 512) return afq_fail(ctx, AFQ_ERR_ARG, "propagation tile does not fit");
