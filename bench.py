@@ -622,11 +622,12 @@ def mixed_errors(name: str, rank: int, long_steps: int = 100, check_walkers: int
                      "split-propagated walkers, cotangent seeded)"}
 
 
-def digits7_errors(name: str, rank: int, steps: int = 20, check_walkers: int = 16) -> dict:
-    """The 7-digit (FP64-quality) split path against the FP64 path on the first walkers
-    after 1 and after `steps` steps of the same device Philox fields: max relative error
-    of every energy part, weight, overlap and walker element (walker: max element
-    difference over the walker's largest element)."""
+def digits7_errors(name: str, rank: int, steps: int = 20, check_walkers: int = 16,
+                   digits: int = 7) -> dict:
+    """The split path with `digits` exact digits everywhere (7: FP64 quality) against
+    the FP64 path on the first walkers after 1 and after `steps` steps of the same
+    device Philox fields: max relative error of every energy part, weight, overlap and
+    walker element (walker: max element difference over the walker's largest element)."""
     import torch
     from paper_2209_04015_b300 import AfqContext
     from paper_2209_04015_b300.synthetic import make_config
@@ -641,7 +642,7 @@ def digits7_errors(name: str, rank: int, steps: int = 20, check_walkers: int = 1
         ctx.init_walkers(nw)
         return ctx
 
-    mix = context(c["W"], precision="split_bf16", **DIGITS7)
+    mix = context(c["W"], precision="split_bf16", split_slices=digits, prop_slices=digits)
     ref = context(check_walkers)
     n, out = check_walkers, {}
     for k in range(1, steps + 1):
@@ -994,6 +995,15 @@ def run_afq(args):
                                 "path's 1e-10 parity tests against the oracle")
         d7["errors"] = digits7_errors(WORKLOAD, rank)
         line["split_bf16_7digits"] = d7
+        d6 = step_leg(WORKLOAD, "split_bf16", args.steps, args.warmup, rank, 1, local,
+                      split_slices=6, prop_slices=6)
+        attach_peak(d6["roofline"], peaks, fp64)
+        d6["speedup_vs_fp64"] = d6["value"] / head["value"] * world
+        d6["precision_note"] = ("split_bf16 with 6 exact 8-bit digits per operand (47 bits): "
+                                "errors against the FP64 path at its own rounding level, held "
+                                "to the FP64 path's 1e-10 parity tests against the oracle")
+        d6["errors"] = digits7_errors(WORKLOAD, rank, digits=6)
+        line["split_bf16_6digits"] = d6
         c2 = {}
         for prec in ("fp64", "split_bf16"):
             leg = step_leg("c2", prec, 5 * args.steps, args.warmup, rank, 1, local,

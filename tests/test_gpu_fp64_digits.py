@@ -1,11 +1,12 @@
-"""Split precision at FP64 quality (7 exact digits per operand) against the oracle, and
-its two MMA issue forms against each other (GPU).
+"""Split precision at FP64 quality (7 exact digits per operand, and 6) against the
+oracle, and its two MMA issue forms against each other (GPU).
 
 With split_slices = prop_slices = 7 every tensor-core contraction (force bias, VHS,
 Taylor powers and one-body halves, stored exchange, overlap product) takes 55-bit
 digit expansions of both operands with exact integer accumulation, so the split path
 is held to the FP64 path's parity bar: walkers element by element, overlaps, weights
-and every energy part within 1e-10 relative of the oracle.
+and every energy part within 1e-10 relative of the oracle.  6 digits (47 bits) are
+held to the same bar.
 """
 import numpy as np
 import pytest
@@ -25,15 +26,19 @@ def _gpu():
     need_gpu()
 
 
+@pytest.mark.parametrize("nd", [7, 6])
 @pytest.mark.parametrize("shape", [(37, 5, 3, 71, 13), (50, 7, 0, 66, 9), (96, 20, 20, 101, 7)])
-def test_seven_digit_split_matches_oracle_at_fp64_tolerance(shape):
+def test_seven_digit_split_matches_oracle_at_fp64_tolerance(shape, nd):
+    """7 digits (55 bits), and 6 (47 bits, whose truncation lies at the FP64 path's own
+    rounding level on these workloads), held to the FP64 parity bar."""
     M, na, nb, X, W = shape
     s = make_system(M, na, nb, X, seed=M + 3, decay="geometric", e0=0.37)
     phi = perturbed_walkers(s, W, eps=0.3, seed=2)
-    ctx, orc = make_pair(s, W, phi=phi, **DIGITS)
+    ctx, orc = make_pair(s, W, phi=phi, precision="split_bf16", split_slices=nd,
+                         prop_slices=nd)
     assert ctx.exchange_algorithm() == "stored"
     digits, _ = ctx.prop_digits()
-    assert digits[0] == digits[-1] == 7
+    assert digits[0] == digits[-1] == nd
     fields = np.stack([gaussian_fields(W, s.X, seed=70 + k) for k in range(6)])
     ctx.propagate(fields, 6)  # a QR after the fifth step
     orc.propagate(list(fields))
