@@ -93,16 +93,19 @@ typedef struct afq_params {
                           stored at their weights, the leading product in an exact
                           TMEM accumulator and the smaller ones in a second (FP32).
                           7 digits (55 bits) with prop_slices = 7 give FP64
-                          quality (the FP64 path's 1e-10 parity with the oracle) */
+                          quality (the FP64 path's 1e-10 parity with the oracle);
+                          6 with 6 pass the same parity tests               */
   int prop_slices;     /* AFQ_SPLIT_BF16: exact 8-bit digits per FP64 operand of the
                           VHS and propagator GEMMs, 1..7 (per-row power-of-two scale,
                           one exact TMEM accumulator per digit order; the Taylor
                           powers take fewer where their terms are small); 0 = 4  */
   int exchange;        /* an afq_exchange: algorithm of the exchange energy        */
   int prop_kernel;     /* AFQ_SPLIT_BF16 propagation: 0 = one launch per GEMM pass with
-                          digit slicing launches between them (default); passes of up
-                          to 4 digits issue one MMA per A digit over the concatenated
-                          B digits (32-column tiles, two TMEM accumulator sets);
+                          digit slicing launches between them (default); the real
+                          passes and the complex passes of 3 or more digits issue one
+                          MMA per A digit over the concatenated B digits (32-column
+                          tiles; two TMEM accumulator sets up to 4 digits, two ring
+                          stages per K block from 5);
                           1 = one persistent kernel of thread-block clusters for all
                           GEMM passes of a step (each walker's 128-row slabs form a
                           cluster that exchanges the digit exponents on chip; about
