@@ -4,10 +4,12 @@ Usage: python -m paper_2209_04015_b300.build [--debug]
 """
 from __future__ import annotations
 
+import concurrent.futures
 import glob
 import os
 import subprocess
 import sys
+import tempfile
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -29,14 +31,26 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles every csrc/*.cu for sm_103a (one nvcc per file, in parallel) and links
+    them into libafqmc.so next to this file."""
     if not force and up_to_date():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *sources()]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+             "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+        flags.insert(0, "-Xptxas=-v")
+    with tempfile.TemporaryDirectory(prefix="afq_build_") as tmp:
+        objs = [os.path.join(tmp, os.path.basename(src) + ".o") for src in sources()]
+
+        def compile_one(src_obj):
+            src, obj = src_obj
+            subprocess.run([nvcc, *flags, "-c", src, "-o", obj], check=True)
+
+        jobs = max(1, min(len(objs), os.cpu_count() or 1))
+        with concurrent.futures.ThreadPoolExecutor(jobs) as pool:
+            list(pool.map(compile_one, zip(sources(), objs)))
+        subprocess.run([nvcc, *ARCH, "-shared", "-o", LIB + ".tmp", *objs], check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

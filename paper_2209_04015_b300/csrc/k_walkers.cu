@@ -92,6 +92,57 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
   sh = t;
 }
 
+// The same multiply-accumulate with every rounding spelled out (__fmul_rn / __fadd_rn
+// are never contracted into an FMA, so the two-sum sees the rounded head product),
+// and a renormalisation (two-sum of head and tail) for values that are stored and
+// updated again: the Gauss-Jordan elimination below updates each entry up to n times.
+__device__ __forceinline__ void df_mac_rn(float& sh, float& sl, float ah, float al, float bh,
+                                          float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = fmaf(ah, bh, -p);
+  const float c = fmaf(ah, bl, __fmul_rn(al, bh));
+  const float t = __fadd_rn(sh, p);
+  const float bv = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  sl = __fadd_rn(sl, __fadd_rn(err, __fadd_rn(e, c)));
+  sh = t;
+}
+__device__ __forceinline__ void df_renorm(float& h, float& l) {
+  const float s = __fadd_rn(h, l), bv = __fsub_rn(s, h);
+  l = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(l, bv));
+  h = s;
+}
+// acc - f a and a b for complex double-floats (renormalised)
+__device__ __forceinline__ DF2 df_cfms(const DF2& f, const DF2& a, const DF2& acc) {
+  float rh = acc.hi.x, rl = acc.lo.x, ih = acc.hi.y, il = acc.lo.y;
+  df_mac_rn(rh, rl, -f.hi.x, -f.lo.x, a.hi.x, a.lo.x);
+  df_mac_rn(rh, rl, f.hi.y, f.lo.y, a.hi.y, a.lo.y);
+  df_mac_rn(ih, il, -f.hi.x, -f.lo.x, a.hi.y, a.lo.y);
+  df_mac_rn(ih, il, -f.hi.y, -f.lo.y, a.hi.x, a.lo.x);
+  df_renorm(rh, rl);
+  df_renorm(ih, il);
+  return DF2{make_float2(rh, ih), make_float2(rl, il)};
+}
+__device__ __forceinline__ DF2 df_cmul(const DF2& a, const DF2& b) {
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  df_mac_rn(rh, rl, a.hi.x, a.lo.x, b.hi.x, b.lo.x);
+  df_mac_rn(rh, rl, -a.hi.y, -a.lo.y, b.hi.y, b.lo.y);
+  df_mac_rn(ih, il, a.hi.x, a.lo.x, b.hi.y, b.lo.y);
+  df_mac_rn(ih, il, a.hi.y, a.lo.y, b.hi.x, b.lo.x);
+  df_renorm(rh, rl);
+  df_renorm(ih, il);
+  return DF2{make_float2(rh, ih), make_float2(rl, il)};
+}
+__device__ __forceinline__ DF2 df_from(double2 v) {
+  DF2 d;
+  df_split(v.x, d.hi.x, d.lo.x);
+  df_split(v.y, d.hi.y, d.lo.y);
+  return d;
+}
+__device__ __forceinline__ double2 df_to_double(const DF2& v) {
+  return cmk(f2d_bits(v.hi.x) + f2d_bits(v.lo.x), f2d_bits(v.hi.y) + f2d_bits(v.lo.y));
+}
+
 // MO: S entries per thread (n^2 <= OT MO); the launch picks the smallest that fits,
 // so that the accumulators do not hold registers sized for 64 electrons.
 template <bool DF, int MO>
@@ -162,85 +213,149 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
     }
     __syncthreads();
   }
-#pragma unroll
-  for (int k = 0; k < MO; ++k) {
-    const int o = tid + k * OT;
-    if (o < n * n) {
-      const int i = o / n, j = o % n;
-      aug[i * n2 + j] = acc[k];
-      aug[i * n2 + n + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
-    }
-  }
-  if (tid == 0) s_det = cmk(1.0, 0.0);
-  __syncthreads();
-
-  // 2. Gauss-Jordan elimination with partial pivoting (ties -> lowest row).  Per pivot
-  // three barriers: warp 0 picks the pivot row and its reciprocal; all threads swap
-  // the pivot row into place scaled by the reciprocal and keep the column-kc factors
-  // of the other rows; then every other row is updated on the columns not yet reduced
-  // (left columns > kc and the whole right half), warps over rows, lanes over columns.
-  __shared__ double2 s_inv, s_old;
   const int wid = tid >> 5, lane = tid & 31;
-  for (int kc = 0; kc < n; ++kc) {
-    if (tid < 32) {
-      double best = -1.0;
-      int bi = kc;
-      for (int r = kc + tid; r < n; r += 32) {
-        const double v = cabs2(aug[r * n2 + kc]);
-        if (v > best) { best = v; bi = r; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (tid == 0) {
-        double2 pv = aug[bi * n2 + kc];
-        const bool bad = !(cabs2(pv) >= 1e-300);
-        if (bad) atomicAdd(&flags[0], 1);
-        const double2 d = cmul(s_det, pv);
-        s_det = bi != kc ? cmk(-d.x, -d.y) : d;
-        if (bad) pv = cmk(1.0, 0.0);
-        s_inv = cdiv(cmk(1.0, 0.0), pv);
-        s_old = aug[kc * n2 + kc];  // column kc of the row that moves to row bi
-        s_piv = bi;
+  if constexpr (!DF) {
+#pragma unroll
+    for (int k = 0; k < MO; ++k) {
+      const int o = tid + k * OT;
+      if (o < n * n) {
+        const int i = o / n, j = o % n;
+        aug[i * n2 + j] = acc[k];
+        aug[i * n2 + n + j] = cmk(i == j ? 1.0 : 0.0, 0.0);
       }
     }
+    if (tid == 0) s_det = cmk(1.0, 0.0);
     __syncthreads();
-    const int piv = s_piv;
-    const double2 inv = s_inv;
-    // factors of column kc for the rows after the swap (row piv receives old row kc;
-    // the swap below writes only rows kc and piv, so the other reads are unaffected)
-    for (int r = tid; r < n; r += OT)
-      if (r != kc) fac[r] = r == piv ? s_old : aug[r * n2 + kc];
-    for (int c = kc + tid; c < n2; c += OT) {
-      const double2 top = aug[piv * n2 + c];
-      if (piv != kc) aug[piv * n2 + c] = aug[kc * n2 + c];
-      aug[kc * n2 + c] = cmul(top, inv);
+
+    // 2. Gauss-Jordan elimination with partial pivoting (ties -> lowest row).  Per pivot
+    // three barriers: warp 0 picks the pivot row and its reciprocal; all threads swap
+    // the pivot row into place scaled by the reciprocal and keep the column-kc factors
+    // of the other rows; then every other row is updated on the columns not yet reduced
+    // (left columns > kc and the whole right half), warps over rows, lanes over columns.
+    __shared__ double2 s_inv, s_old;
+    for (int kc = 0; kc < n; ++kc) {
+      if (tid < 32) {
+        double best = -1.0;
+        int bi = kc;
+        for (int r = kc + tid; r < n; r += 32) {
+          const double v = cabs2(aug[r * n2 + kc]);
+          if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (tid == 0) {
+          double2 pv = aug[bi * n2 + kc];
+          const bool bad = !(cabs2(pv) >= 1e-300);
+          if (bad) atomicAdd(&flags[0], 1);
+          const double2 d = cmul(s_det, pv);
+          s_det = bi != kc ? cmk(-d.x, -d.y) : d;
+          if (bad) pv = cmk(1.0, 0.0);
+          s_inv = cdiv(cmk(1.0, 0.0), pv);
+          s_old = aug[kc * n2 + kc];  // column kc of the row that moves to row bi
+          s_piv = bi;
+        }
+      }
+      __syncthreads();
+      const int piv = s_piv;
+      const double2 inv = s_inv;
+      // factors of column kc for the rows after the swap (row piv receives old row kc;
+      // the swap below writes only rows kc and piv, so the other reads are unaffected)
+      for (int r = tid; r < n; r += OT)
+        if (r != kc) fac[r] = r == piv ? s_old : aug[r * n2 + kc];
+      for (int c = kc + tid; c < n2; c += OT) {
+        const double2 top = aug[piv * n2 + c];
+        if (piv != kc) aug[piv * n2 + c] = aug[kc * n2 + c];
+        aug[kc * n2 + c] = cmul(top, inv);
+      }
+      __syncthreads();
+      for (int r = wid; r < n; r += OT / 32) {
+        if (r == kc) continue;
+        const double2 f = fac[r];
+        for (int c = kc + 1 + lane; c < n2; c += 32)
+          aug[r * n2 + c] = cfms(f, aug[kc * n2 + c], aug[r * n2 + c]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int r = wid; r < n; r += OT / 32) {
-      if (r == kc) continue;
-      const double2 f = fac[r];
-      for (int c = kc + 1 + lane; c < n2; c += 32)
-        aug[r * n2 + c] = cfms(f, aug[kc * n2 + c], aug[r * n2 + c]);
+  } else {
+    // 2'. The same elimination on double-floats (split-precision walker ensembles):
+    // the FP64 pipe runs 2 lanes per clock on B300 and bound the FP64 form, while a
+    // double-float complex update costs ~50 FP32 operations on a 64x faster pipe.  The
+    // pivot search compares the FP32 heads; the pivot's reciprocal and the determinant
+    // are formed in FP64 by one thread.  Each update rounds at ~2^-47 of |f a|
+    // (FP64: 2^-53), so S^-1 and det S keep ~2^-44 relative for the overlap matrices of
+    // normalised walkers -- theta is formed in double-floats anyway.
+    DF2* adf = reinterpret_cast<DF2*>(aug);  // n x 2n  [S | I] -> [I | S^-1]
+    DF2* fdf = reinterpret_cast<DF2*>(fac);
+    __shared__ DF2 s_invd, s_oldd;
+    const DF2 dzero = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int k = 0; k < MO; ++k) {
+      const int o = tid + k * OT;
+      if (o < n * n) {
+        const int i = o / n, j = o % n;
+        adf[i * n2 + j] = df_from(acc[k]);
+        DF2 e = dzero;
+        if (i == j) e.hi.x = 1.f;
+        adf[i * n2 + n + j] = e;
+      }
     }
+    if (tid == 0) s_det = cmk(1.0, 0.0);
     __syncthreads();
+    for (int kc = 0; kc < n; ++kc) {
+      if (tid < 32) {
+        float best = -1.f;
+        int bi = kc;
+        for (int r = kc + tid; r < n; r += 32) {
+          const float2 h = adf[r * n2 + kc].hi;
+          const float v = h.x * h.x + h.y * h.y;
+          if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (tid == 0) {
+          double2 pv = df_to_double(adf[bi * n2 + kc]);
+          const bool bad = !(cabs2(pv) >= 1e-300);
+          if (bad) atomicAdd(&flags[0], 1);
+          const double2 d = cmul(s_det, pv);
+          s_det = bi != kc ? cmk(-d.x, -d.y) : d;
+          if (bad) pv = cmk(1.0, 0.0);
+          s_invd = df_from(cdiv(cmk(1.0, 0.0), pv));
+          s_oldd = adf[kc * n2 + kc];
+          s_piv = bi;
+        }
+      }
+      __syncthreads();
+      const int piv = s_piv;
+      const DF2 inv = s_invd;
+      for (int r = tid; r < n; r += OT)
+        if (r != kc) fdf[r] = r == piv ? s_oldd : adf[r * n2 + kc];
+      for (int c = kc + tid; c < n2; c += OT) {
+        const DF2 top = adf[piv * n2 + c];
+        if (piv != kc) adf[piv * n2 + c] = adf[kc * n2 + c];
+        adf[kc * n2 + c] = df_cmul(top, inv);
+      }
+      __syncthreads();
+      for (int r = wid; r < n; r += OT / 32) {
+        if (r == kc) continue;
+        const DF2 f = fdf[r];
+        for (int c = kc + 1 + lane; c < n2; c += 32)
+          adf[r * n2 + c] = df_cfms(f, adf[kc * n2 + c], adf[r * n2 + c]);
+      }
+      __syncthreads();
+    }
   }
 
   // 3. theta^T_jp = sum_k (S^-1)_kj Phi_pk and E1 = sum_jp h~_jp theta^T_jp
   double2 e1acc = cmk(0.0, 0.0);
   if (DF) {
-    // S^-1 as double-floats, over the (now unused) left half of aug
-    DF2* sdf = reinterpret_cast<DF2*>(aug);  // [k][j] at slot k * n2 + j
-    for (int e = tid; e < n * n; e += OT) {
-      const int k = e / n, j = e % n;
-      const double2 v = aug[k * n2 + n + j];
-      DF2 d;
-      df_split(v.x, d.hi.x, d.lo.x);
-      df_split(v.y, d.hi.y, d.lo.y);
-      sdf[k * n2 + j] = d;
-    }
+    // S^-1 as double-floats: the right half of the eliminated augmented matrix
+    const DF2* sdf = reinterpret_cast<const DF2*>(aug) + n;  // [k][j] at slot k * n2 + j
     DF2* pdf = reinterpret_cast<DF2*>(cphi);  // Phi chunk as double-floats
     for (int p0 = 0; p0 < M; p0 += PC) {
       const int pc = min(PC, M - p0);
