@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
                                                       double2* __restrict__ det,
                                                       double2* __restrict__ e1, int* flags,
                                                       const double2* __restrict__ Spre,
-                                                      int nmax) {
+                                                      int nmax, int pcr) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double2 red[OT / 32];
   __shared__ int s_piv;
@@ -357,21 +357,16 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
     // S^-1 as double-floats: the right half of the eliminated augmented matrix
     const DF2* sdf = reinterpret_cast<const DF2*>(aug) + n;  // [k][j] at slot k * n2 + j
     DF2* pdf = reinterpret_cast<DF2*>(cphi);  // Phi chunk as double-floats
-    for (int p0 = 0; p0 < M; p0 += PC) {
-      const int pc = min(PC, M - p0);
+    for (int p0 = 0; p0 < M; p0 += pcr) {
+      const int pc = min(pcr, M - p0);
       __syncthreads();
-      for (int e = tid; e < PC * n; e += OT) {
+      for (int e = tid; e < pc * n; e += OT) {
         const int pp = e / n, j = e % n;
-        const double2 v = pp < pc ? phiz[(long)(p0 + pp) * N + off + j] : cmk(0.0, 0.0);
-        DF2 d;
-        df_split(v.x, d.hi.x, d.lo.x);
-        df_split(v.y, d.hi.y, d.lo.y);
-        pdf[pp * ldn + j] = d;
+        pdf[pp * ldn + j] = df_from(phiz[(long)(p0 + pp) * N + off + j]);
       }
       __syncthreads();
-      for (int e = tid; e < n * PC; e += OT) {
-        const int j = e / PC, pp = e % PC;
-        if (pp >= pc) continue;
+      for (int e = tid; e < n * pc; e += OT) {
+        const int j = e / pc, pp = e % pc;
         float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
         for (int k = 0; k < n; ++k) {
           const DF2 a = sdf[k * n2 + j];
@@ -389,16 +384,16 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
       }
     }
   }
-  for (int p0 = 0; p0 < M && !DF; p0 += PC) {
-    const int pc = min(PC, M - p0);
-    for (int e = tid; e < PC * n; e += OT) {
+  for (int p0 = 0; p0 < M && !DF; p0 += pcr) {
+    const int pc = min(pcr, M - p0);
+    for (int e = tid; e < pc * n; e += OT) {
       const int pp = e / n, j = e % n;
-      cphi[pp * ldn + j] = pp < pc ? phiz[(long)(p0 + pp) * N + off + j] : cmk(0.0, 0.0);
+      cphi[pp * ldn + j] = phiz[(long)(p0 + pp) * N + off + j];
     }
     __syncthreads();
-    for (int e = tid; e < n * PC; e += OT) {
-      const int j = e / PC, pp = e % PC;
-      if (pp < pc) {
+    for (int e = tid; e < n * pc; e += OT) {
+      const int j = e / pc, pp = e % pc;
+      {
         double2 t = cmk(0.0, 0.0);
         for (int k = 0; k < n; ++k) {
           const double2 sv = aug[k * n2 + n + j];
@@ -675,6 +670,133 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
   if (tid == 0) detR[2 * z + s] = exp(logdet);
 }
 
+// The same Gram-Schmidt QR with reorthogonalisation on double-floats (the walker
+// ensembles of split-precision contexts).  B300 runs FP64 at 2 lanes per clock per SM,
+// which bound the FP64 form of this kernel (M n^2 complex multiply-adds per matrix);
+// double-float products and sums run on the 64x faster FP32 pipe at ~2^-44 relative,
+// far below the ~2^-31 that the split-precision propagation leaves in the walkers.
+// R's diagonal, its logarithms and the reorthogonalisation test are FP64.  Qw holds
+// the double-float columns (the same 16 bytes per complex entry as the FP64 form).
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+  const float s = __fadd_rn(h, bh), bv = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(bh, bv));
+  l = __fadd_rn(l, __fadd_rn(bl, e));
+  h = s;
+  df_renorm(h, l);
+}
+__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_down_sync(0xffffffffu, h, o);
+    const float bl = __shfl_down_sync(0xffffffffu, l, o);
+    df_add(h, l, bh, bl);
+  }
+}
+__global__ void __launch_bounds__(256) k_qr_df(int M, int N, int na, int nb,
+                                               double2* __restrict__ phi, DF2* __restrict__ Qw,
+                                               double* __restrict__ detR, int* flags) {
+  __shared__ DF2 rs[AFQ_NMAX + 1];
+  __shared__ float2 red[32];
+  __shared__ double2 redd[32];
+  __shared__ float s_inv_h, s_inv_l;
+  __shared__ int s_again;
+  __shared__ double rdiag[AFQ_NMAX];
+  const int z = blockIdx.x, s = blockIdx.y, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5, nt = blockDim.x, nw = nt >> 5;
+  const int n = s ? nb : na, off = s ? na : 0;
+  if (n == 0) {
+    if (tid == 0) detR[2 * z + s] = 1.0;
+    return;
+  }
+  double2* phz = phi + (long)z * M * N;
+  DF2* Q = Qw + ((long)z * N + off) * M;  // column j at Q + j * M
+  for (int e = tid; e < M * n; e += nt) {
+    const int p = e / n, j = e % n;
+    Q[(long)j * M + p] = df_from(phz[(long)p * N + off + j]);
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    DF2* v = Q + (long)j * M;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (j > 0) {
+        // r_i = q_i^H v for i < j; the first pass also takes |v|^2 as index j
+        const int last = pass == 0 ? j : j - 1;
+        for (int i = wid; i <= last; i += nw) {
+          const DF2* qi = i < j ? Q + (long)i * M : v;
+          float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+          for (int p = lane; p < M; p += 32) {
+            const DF2 a = qi[p], b = v[p];
+            df_mac_rn(rh, rl, a.hi.x, a.lo.x, b.hi.x, b.lo.x);
+            df_mac_rn(rh, rl, a.hi.y, a.lo.y, b.hi.y, b.lo.y);
+            df_mac_rn(ih, il, a.hi.x, a.lo.x, b.hi.y, b.lo.y);
+            df_mac_rn(ih, il, -a.hi.y, -a.lo.y, b.hi.x, b.lo.x);
+          }
+          df_renorm(rh, rl);
+          df_renorm(ih, il);
+          df_warp_sum(rh, rl);
+          df_warp_sum(ih, il);
+          if (lane == 0) rs[i] = DF2{make_float2(rh, ih), make_float2(rl, il)};
+        }
+        __syncthreads();
+        for (int p = tid; p < M; p += nt) {
+          DF2 t = v[p];
+          for (int i = 0; i < j; ++i) t = df_cfms(Q[(long)i * M + p], rs[i], t);
+          v[p] = t;
+        }
+        __syncthreads();
+      }
+      float nh = 0.f, nl = 0.f;
+      for (int p = tid; p < M; p += nt) {
+        const DF2 b = v[p];
+        df_mac_rn(nh, nl, b.hi.x, b.lo.x, b.hi.x, b.lo.x);
+        df_mac_rn(nh, nl, b.hi.y, b.lo.y, b.hi.y, b.lo.y);
+      }
+      df_renorm(nh, nl);
+      df_warp_sum(nh, nl);
+      if (lane == 0) red[wid] = make_float2(nh, nl);
+      __syncthreads();
+      if (tid == 0) {
+        float th = 0.f, tl = 0.f;
+        for (int w = 0; w < nw; ++w) df_add(th, tl, red[w].x, red[w].y);
+        const double nr = f2d_bits(th) + f2d_bits(tl);
+        const double before = f2d_bits(rs[j].hi.x) + f2d_bits(rs[j].lo.x);
+        const int again = pass == 0 && j > 0 && nr < 0.5 * before;
+        s_again = again;
+        if (!again) {
+          const double rjj = sqrt(nr);
+          if (!(rjj > 0.0)) atomicAdd(&flags[0], 1);
+          float ih2, il2;
+          df_split(rjj > 0.0 ? 1.0 / rjj : 1.0, ih2, il2);
+          s_inv_h = ih2;
+          s_inv_l = il2;
+          rdiag[j] = rjj > 0.0 ? rjj : 1.0;
+        }
+      }
+      __syncthreads();
+      if (!s_again) break;
+    }
+    const float ih = s_inv_h, il = s_inv_l;
+    for (int p = tid; p < M; p += nt) {
+      const DF2 b = v[p];
+      float rh = 0.f, rl = 0.f, qh = 0.f, ql = 0.f;
+      df_mac_rn(rh, rl, b.hi.x, b.lo.x, ih, il);
+      df_mac_rn(qh, ql, b.hi.y, b.lo.y, ih, il);
+      df_renorm(rh, rl);
+      df_renorm(qh, ql);
+      v[p] = DF2{make_float2(rh, qh), make_float2(rl, ql)};
+    }
+    __syncthreads();
+  }
+  // log det R = sum_j log R_jj, the logs in parallel off the column loop
+  double lg = 0.0;
+  for (int j = tid; j < n; j += nt) lg += log(rdiag[j]);
+  const double logdet = block_sum2(cmk(lg, 0.0), redd).x;
+  for (int e = tid; e < M * n; e += nt) {
+    const int p = e / n, j = e % n;
+    phz[(long)p * N + off + j] = df_to_double(Q[(long)j * M + p]);
+  }
+  if (tid == 0) detR[2 * z + s] = exp(logdet);
+}
+
 __global__ void k_qr_finish(int W, const double* __restrict__ detR, double2* __restrict__ ovlp) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   if (z < W) ovlp[z] = cscale(ovlp[z], 1.0 / (detR[2 * z] * detR[2 * z + 1]));
@@ -699,6 +821,23 @@ size_t exchange_smem(int G, int n) {
 
 int exchange_group_size(int nmax) { return nmax > 0 ? (64 / nmax > 1 ? 64 / nmax : 1) : 1; }
 
+// Rows of Phi per theta chunk (<= PC): each chunk's n x rows outputs are spread over
+// the OT threads, so the count minimising the number of thread passes over all chunks,
+// ceil(M / rows) ceil(n rows / OT), keeps every thread busy (290 orbitals and 26
+// electrons: 29 rows, 30 passes instead of 37 with 32 rows).  Larger rows win ties.
+int theta_chunk_rows(int M, int n) {
+  int best = PC;
+  long best_passes = -1;
+  for (int r = PC; r >= 1; --r) {
+    const long passes = (long)((M + r - 1) / r) * ((long)(n * r + OT - 1) / OT);
+    if (best_passes < 0 || passes < best_passes) {
+      best_passes = passes;
+      best = r;
+    }
+  }
+  return best;
+}
+
 // df: theta by double-float arithmetic (split-precision walker ensembles); S, its
 // determinant and inverse and the one-body energy stay FP64 either way.
 template <bool DF, int MO>
@@ -714,7 +853,7 @@ int launch_overlap_mo(afq_ctx* ctx, WalkerSet& s) {
   }
   k_overlap_theta<DF, MO><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
       ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
-      ctx->flags, Spre, nmax);
+      ctx->flags, Spre, nmax, theta_chunk_rows(ctx->M, nmax));
   AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }
@@ -814,8 +953,13 @@ int launch_qr(afq_ctx* ctx, WalkerSet& s, double2* Qw) {
   int nt = (ctx->M + 31) / 32 * 32;
   if (nt < 64) nt = 64;
   if (nt > 256) nt = 256;
-  k_qr<<<dim3(s.W, 2), nt, 0, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb, s.phi, Qw,
-                                              ctx->detR, ctx->flags);
+  if (ctx->mixed && &s == &ctx->ws)  // split-precision walkers: double-float QR
+    k_qr_df<<<dim3(s.W, 2), nt, 0, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb, s.phi,
+                                                   reinterpret_cast<DF2*>(Qw), ctx->detR,
+                                                   ctx->flags);
+  else
+    k_qr<<<dim3(s.W, 2), nt, 0, ctx->stream>>>(ctx->M, ctx->N, ctx->na, ctx->nb, s.phi, Qw,
+                                                ctx->detR, ctx->flags);
   AFQ_LAUNCHED(ctx);
   k_qr_finish<<<(s.W + 127) / 128, 128, 0, ctx->stream>>>(s.W, ctx->detR, s.ovlp);
   AFQ_LAUNCHED(ctx);
