@@ -566,17 +566,15 @@ __global__ void __launch_bounds__(256, (NP <= 6 && D <= kFastSlices) ? 3 : 2) k_
     for (int t = 0; t < NP; ++t) {
       const int k = 2 * lane + 64 * t;
       if (k >= Kp) continue;
-      int q0[D], q1[D];
+      float q0[D], q1[D];
 #pragma unroll
       for (int part = 0; part < 2; ++part) {
-        exact_digits<D>(part ? v[t][0].y : v[t][0].x, e, S, q0);
-        exact_digits<D>(part ? v[t][1].y : v[t][1].x, e, S, q1);
+        exact_digits_f<D>(part ? v[t][0].y : v[t][0].x, e, S, q0);
+        exact_digits_f<D>(part ? v[t][1].y : v[t][1].x, e, S, q1);
         __nv_bfloat16* o = (part ? oim : ore) + k;
 #pragma unroll
         for (int s = 0; s < D; ++s)
-          if (s < S)
-            *reinterpret_cast<__nv_bfloat162*>(o + s * plane) =
-                __floats2bfloat162_rn((float)q0[s], (float)q1[s]);
+          if (s < S) *reinterpret_cast<__nv_bfloat162*>(o + s * plane) = digit_bf16x2(q0[s], q1[s]);
       }
     }
   }
@@ -641,24 +639,21 @@ __global__ void __launch_bounds__(256, (NP <= 6 && D <= kFastSlices) ? 3 : 2) k_
     for (int t = 0; t < NP; ++t) {
       const int k = 2 * lane + 64 * t;
       if (k >= Kp) continue;
-      int q0[D], q1[D];
+      float q0[D], q1[D];
 #pragma unroll
       for (int part = 0; part < 2; ++part) {
-        exact_digits<D>(part ? v[t][0].y : v[t][0].x, e, S, q0);
-        exact_digits<D>(part ? v[t][1].y : v[t][1].x, e, S, q1);
+        exact_digits_f<D>(part ? v[t][0].y : v[t][0].x, e, S, q0);
+        exact_digits_f<D>(part ? v[t][1].y : v[t][1].x, e, S, q1);
         __nv_bfloat16* o = (part ? oim : ore) + k;
 #pragma unroll
         for (int s = 0; s < D; ++s)
-          if (s < S)
-            *reinterpret_cast<__nv_bfloat162*>(o + s * plane) =
-                __floats2bfloat162_rn((float)q0[s], (float)q1[s]);
+          if (s < S) *reinterpret_cast<__nv_bfloat162*>(o + s * plane) = digit_bf16x2(q0[s], q1[s]);
         if (part && nout) {  // -Im digits [s][z][j][Kp] for the column-concatenated GEMM
           __nv_bfloat16* on = nout + r * Kp + k;
 #pragma unroll
           for (int s = 0; s < D; ++s)
             if (s < S)
-              *reinterpret_cast<__nv_bfloat162*>(on + s * nplane) =
-                  __floats2bfloat162_rn((float)-q0[s], (float)-q1[s]);
+              *reinterpret_cast<__nv_bfloat162*>(on + s * nplane) = digit_bf16x2(-q0[s], -q1[s]);
         }
       }
     }

@@ -28,31 +28,6 @@ namespace {
 constexpr int kOvDigits = 7;
 constexpr int kOvBN = 64;  // columns i per tile: 7 accumulators x 64 fit the 512 TMEM columns
 
-// The exact digits of exact_digits for up to 7 digits (q[s] of weight 256^-s).
-__device__ __forceinline__ void exact_digits7(double x, int e, int S, int (&q)[kOvDigits]) {
-  const long long bits = __double_as_longlong(x);
-  const int E = (int)((bits >> 52) & 0x7FF);
-  long long v = 0;
-  if (E != 0) {
-    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-    const int sh = E - 1075 + 7 - e + 8 * (S - 1);  // value = mant 2^(E-1075)
-    if (sh >= 0)
-      v = sh < 10 ? mant << sh : 0;  // |x| <= 2^e: sh <= 2 + 8 (S - 1) - 53 + 1
-    else if (sh > -64)
-      v = (mant + (1LL << (-sh - 1))) >> (-sh);
-  }
-  const bool neg = bits < 0;
-#pragma unroll
-  for (int s = kOvDigits - 1; s >= 0; --s) {
-    q[s] = 0;
-    if (s >= S) continue;
-    int d = (int)(v & 255);
-    if (d > 128) d -= 256;
-    q[s] = neg ? -d : d;
-    v = (v - d) >> 8;
-  }
-}
-
 // Real rows of K doubles (row pitch ld) -> S digit planes of rows x Kp with one
 // exponent per row (one warp per row).
 __global__ void k_slice_rows7(const double* __restrict__ in, long ld, long rows, int K, int Kp,
@@ -67,11 +42,11 @@ __global__ void k_slice_rows7(const double* __restrict__ in, long ld, long rows,
     const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
     if (lane == 0) eout[r] = e;
     for (int k = lane; k < Kp; k += 32) {
-      int q[kOvDigits];
-      exact_digits7(k < K ? row[k] : 0.0, e, S, q);
+      float q[kOvDigits];
+      exact_digits_f<kOvDigits>(k < K ? row[k] : 0.0, e, S, q);
 #pragma unroll
       for (int s = 0; s < kOvDigits; ++s)
-        if (s < S) out[s * plane + r * Kp + k] = __float2bfloat16_rn((float)q[s]);
+        if (s < S) out[s * plane + r * Kp + k] = digit_bf16(q[s]);
     }
   }
 }
@@ -99,14 +74,14 @@ __global__ void k_slice_phiT7(const double2* __restrict__ phi, int W, int M, int
     __nv_bfloat16* oim = ore + (long)N * Kp;
     for (int p = lane; p < Kp; p += 32) {
       const double2 v = p < M ? col[(long)p * N] : make_double2(0.0, 0.0);
-      int qr[kOvDigits], qi[kOvDigits];
-      exact_digits7(v.x, e, S, qr);
-      exact_digits7(v.y, e, S, qi);
+      float qr[kOvDigits], qi[kOvDigits];
+      exact_digits_f<kOvDigits>(v.x, e, S, qr);
+      exact_digits_f<kOvDigits>(v.y, e, S, qi);
 #pragma unroll
       for (int s = 0; s < kOvDigits; ++s)
         if (s < S) {
-          ore[s * plane + p] = __float2bfloat16_rn((float)qr[s]);
-          oim[s * plane + p] = __float2bfloat16_rn((float)qi[s]);
+          ore[s * plane + p] = digit_bf16(qr[s]);
+          oim[s * plane + p] = digit_bf16(qi[s]);
         }
     }
   }

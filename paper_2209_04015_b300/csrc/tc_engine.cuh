@@ -178,40 +178,6 @@ __device__ __forceinline__ int exp_field(double x) {
 // Row exponent e with |x| <= 2^e for a row whose largest exponent field is emax.
 __device__ __forceinline__ int row_exponent_field(int emax) { return emax ? emax - 1022 : 0; }
 
-// Integer digits of x relative to the row scale 2^e (|x| <= 2^e):
-// x ~ 2^(e-7) sum_s q_s 256^-s with balanced digits q_s in [-128, 128] (exact in
-// bfloat16), written S planes apart.  Rounds x 2^(7-e+8(S-1)) to the nearest
-// integer and cuts it into base-256 digits.  D >= S bounds the unrolled digit loops:
-// the per-step slicing kernels take D = kFastSlices when S <= 4, so that the digit
-// counts beyond 4 cost them neither registers nor instructions.
-template <int D = kMaxSlices>
-__device__ __forceinline__ void split_exact(double x, int e, int S, __nv_bfloat16* out,
-                                            long plane) {
-  const long long bits = __double_as_longlong(x);
-  const int E = (int)((bits >> 52) & 0x7FF);
-  long long v = 0;
-  if (E != 0) {
-    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-    const int sh = E - 1075 + 7 - e + 8 * (S - 1);  // value = mant 2^(E-1075)
-    if (sh >= 0)
-      v = sh < 10 ? mant << sh : 0;  // |x| <= 2^e: sh <= 8 S - 54 (v < 2^(8 S - 1))
-    else if (sh > -64)
-      v = (mant + (1LL << (-sh - 1))) >> (-sh);
-  }
-  const bool neg = bits < 0;
-  int q[D];
-#pragma unroll
-  for (int s = D - 1; s >= 0; --s) {
-    if (s >= S) continue;
-    int d = (int)(v & 255);
-    if (d > 128) d -= 256;
-    q[s] = d;
-    v = (v - d) >> 8;
-  }
-#pragma unroll
-  for (int s = 0; s < D; ++s)
-    if (s < S) out[s * plane] = __float2bfloat16_rn((float)(neg ? -q[s] : q[s]));
-}
 
 // The same digits returned in q[0..S-1] (q[s] = digit of weight 256^-s; S <= D).
 template <int D>
@@ -237,6 +203,84 @@ __device__ __forceinline__ void exact_digits(double x, int e, int S, int (&q)[D]
     q[s] = neg ? -d : d;
     v = (v - d) >> 8;
   }
+}
+
+// The same digits returned as exact floats (q[s] = digit of weight 256^-s, S <= D),
+// cut without integer <-> float conversions and with 32-bit arithmetic when D <= 4:
+// v = round(|x| 2^(7 - e + 8 (S - 1))) as before; adding 127 to each of the S - 1 low
+// bytes of v (w = v + 0x7F...7F) turns the balanced digits in [-127, 128] into the
+// plain bytes of w (digit = byte - 127, the top digit = the top byte), and a byte
+// permute places byte k of w under the exponent of 2^23, so that one FMA gives
+// sign(x) (byte - 127).  The slicing passes that cut every walker's operands each step
+// were bound by the integer pipe with the shift-and-mask loop and the conversions.
+template <int D>
+__device__ __forceinline__ void exact_digits_f(double x, int e, int S, float (&q)[D]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(bits >> 32);
+  const int E = (int)((hi >> 20) & 0x7FF);
+  const int r = 1068 + e - 8 * (S - 1) - E;  // v = round(mant 2^-r), mant = 1.m 2^52
+  const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const float sg = (int)hi < 0 ? -1.f : 1.f;
+  const float ctop = -8388608.f * sg, clow = -8388735.f * sg;  // -(2^23) and -(2^23 + 127)
+  if constexpr (D <= 4) {
+    unsigned v = 0;  // |x| < 2^e: r >= 22, so v <= 2^31 (2^31 only by rounding up)
+    if (E != 0 && r > 0 && r < 54) {
+      const unsigned t = (unsigned)(mant >> (r - 1));  // v = (t + 1) / 2 without overflow
+      v = (t >> 1) + (t & 1u);
+    }
+    const unsigned w = v + (0x7F7F7Fu >> (8 * (4 - S)));
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+      q[s] = 0.f;
+      if (s >= S) continue;
+      const unsigned b = __byte_perm(w, 0x4B000000u, 0x7440u | (unsigned)(S - 1 - s));
+      q[s] = fmaf(__uint_as_float(b), sg, s == 0 ? ctop : clow);
+    }
+  } else {
+    unsigned long long v = 0;
+    if (E != 0) {
+      if (r <= 0)
+        v = r > -10 ? mant << (-r) : 0;
+      else if (r < 54)
+        v = ((mant >> (r - 1)) + 1ull) >> 1;
+    }
+    const unsigned long long w = v + (0x7F7F7F7F7F7F7Full >> (8 * (8 - S)));
+    const unsigned wl = (unsigned)w, wh = (unsigned)(w >> 32);
+#pragma unroll
+    for (int s = 0; s < D; ++s) {
+      q[s] = 0.f;
+      if (s >= S) continue;
+      const int k = S - 1 - s;
+      const unsigned b = __byte_perm(k < 4 ? wl : wh, 0x4B000000u, 0x7440u | (unsigned)(k & 3));
+      q[s] = fmaf(__uint_as_float(b), sg, s == 0 ? ctop : clow);
+    }
+  }
+}
+
+// bfloat16 of an exact digit float (at most 8 significant bits: its low 16 bits are
+// zero) and of a pair of them, by moving bits
+__device__ __forceinline__ __nv_bfloat16 digit_bf16(float f) {
+  return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
+}
+__device__ __forceinline__ __nv_bfloat162 digit_bf16x2(float lo, float hi) {
+  const unsigned u = __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+  return *reinterpret_cast<const __nv_bfloat162*>(&u);
+}
+
+// Integer digits of x relative to the row scale 2^e (|x| <= 2^e):
+// x ~ 2^(e-7) sum_s q_s 256^-s with balanced digits q_s in [-128, 128] (exact in
+// bfloat16), written S planes apart.  Rounds x 2^(7-e+8(S-1)) to the nearest
+// integer and cuts it into base-256 digits.  D >= S bounds the unrolled digit loops:
+// the per-step slicing kernels take D = kFastSlices when S <= 4, so that the digit
+// counts beyond 4 cost them neither registers nor instructions.
+template <int D = kMaxSlices>
+__device__ __forceinline__ void split_exact(double x, int e, int S, __nv_bfloat16* out,
+                                            long plane) {
+  float q[D];
+  exact_digits_f<D>(x, e, S, q);
+#pragma unroll
+  for (int s = 0; s < D; ++s)
+    if (s < S) out[s * plane] = digit_bf16(q[s]);
 }
 
 // Scaled digits: the same digits as exact_digits, each written as its value
