@@ -127,6 +127,7 @@ struct VhsP {
 // the epilogue drains TMEM.
 enum { kModeFirst = 0, kModeTerm = 1, kModeLast = 2 };
 constexpr int kPropWarps = 10;
+constexpr int kAccAhead = 4;  // FP64 Taylor sums loaded ahead of the last pass's stores
 constexpr int kPropEpi = 8;
 
 struct PropArgs {
@@ -186,27 +187,37 @@ __device__ __forceinline__ void prop_epi_group(const PropArgs& a, uint32_t trow,
 #pragma unroll
   for (int d = 0; d < S; ++d) prop_tmem_ld<CW>(trow + (uint32_t)(d * BN + brows + c0), f[d]);
   if (!valid) return;
+  const double pd = a.mode == kModeLast ? a.pdiag[p] : 0.0;
 #pragma unroll
-  for (int jj = 0; jj < CW; ++jj) {
-    const int j = j0 + c0 + jj;
-    if (j >= N) continue;
-    float ai[S];
+  for (int h = 0; h < CW; h += kAccAhead) {
+    double2 accv[kAccAhead];  // the last pass's Taylor sums, loaded ahead of the stores
+    if (a.mode == kModeLast) {
 #pragma unroll
-    for (int d = 0; d < S; ++d) ai[d] = f[d][jj];
-    const int sc = ep + a.eb[(long)z * N + j] - 14;
-    const double dr = dre[jj], di = combine_exact<S>(ai, sc);
-    const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
-    if (a.mode == kModeFirst) {
-      // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
-      a.accT[ia] = make_double2(dr, di);
-    } else if (a.mode == kModeTerm) {
-      // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k to the
-      // FP64 Taylor sum
-      a.tout[ia] = make_double2(dr, di);
-    } else {
-      const double2 acc = a.accT[ia];
-      const double d = a.pdiag[p];
-      a.phi_out[((long)z * M + p) * N + j] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
+      for (int jj = 0; jj < kAccAhead; ++jj) {
+        const int j = j0 + c0 + h + jj;
+        accv[jj] = j < N ? a.accT[((long)z * N + j) * M + p] : make_double2(0.0, 0.0);
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < kAccAhead; ++jj) {
+      const int j = j0 + c0 + h + jj;
+      if (j >= N) continue;
+      float ai[S];
+#pragma unroll
+      for (int d = 0; d < S; ++d) ai[d] = f[d][h + jj];
+      const double dr = dre[h + jj], di = combine_exact<S>(ai, ep + a.eb[(long)z * N + j] - 14);
+      const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
+      if (a.mode == kModeFirst) {
+        // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
+        a.accT[ia] = make_double2(dr, di);
+      } else if (a.mode == kModeTerm) {
+        // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k to the
+        // FP64 Taylor sum
+        a.tout[ia] = make_double2(dr, di);
+      } else {
+        a.phi_out[((long)z * M + p) * N + j] =
+            make_double2(fma(pd, accv[jj].x, dr), fma(pd, accv[jj].y, di));
+      }
     }
   }
 }
@@ -427,7 +438,10 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
           prop_epi_group<S, 8>(a, trow, BN, brows, c0, z, j0, p, valid, ep);
           prop_epi_group<S, 8>(a, trow, BN, brows, c0 + 8, z, j0, p, valid, ep);
         } else {
-          // real parts of 16 columns first (digits -> FP64), then their imaginary partners
+          // real parts of 16 columns first (digits -> FP64), then their imaginary partners.
+          // In the last pass the FP64 Taylor sums are loaded into registers kAccAhead
+          // columns ahead of the stores: the compiler cannot move a load across a store through
+          // another pointer, and one DRAM latency per column serialised the epilogue.
           float f[S][16];
           double dre[16];
 #pragma unroll
@@ -443,27 +457,38 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
 #pragma unroll
           for (int d = 0; d < S; ++d) tc::tmem_ld16(trow + (uint32_t)(d * BN + brows + c0), f[d]);
           if (!valid) continue;
+          const double pd = a.mode == kModeLast ? a.pdiag[p] : 0.0;
 #pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int j = j0 + c0 + jj;
-            if (j >= N) continue;
-            float ai[S];
+          for (int h = 0; h < 16; h += kAccAhead) {
+            double2 accv[kAccAhead];
+            if (a.mode == kModeLast) {
 #pragma unroll
-            for (int d = 0; d < S; ++d) ai[d] = f[d][jj];
-            const int sc = ep + a.eb[(long)z * N + j] - 14;
-            const double dr = dre[jj], di = combine_exact<S>(ai, sc);
-            const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
-                    if (a.mode == kModeFirst) {
-              // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
-              a.accT[ia] = make_double2(dr, di);
-            } else if (a.mode == kModeTerm) {
-              // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k to
-              // the FP64 Taylor sum
-              a.tout[ia] = make_double2(dr, di);
-            } else {
-              const double2 acc = a.accT[ia];
-              const double d = a.pdiag[p];
-              a.phi_out[((long)z * M + p) * N + j] = make_double2(fma(d, acc.x, dr), fma(d, acc.y, di));
+              for (int jj = 0; jj < kAccAhead; ++jj) {
+                const int j = j0 + c0 + h + jj;
+                accv[jj] = j < N ? a.accT[((long)z * N + j) * M + p] : make_double2(0.0, 0.0);
+              }
+            }
+#pragma unroll
+            for (int jj = 0; jj < kAccAhead; ++jj) {
+              const int j = j0 + c0 + h + jj;
+              if (j >= N) continue;
+              float ai[S];
+#pragma unroll
+              for (int d = 0; d < S; ++d) ai[d] = f[d][h + jj];
+              const double dr = dre[h + jj];
+              const double di = combine_exact<S>(ai, ep + a.eb[(long)z * N + j] - 14);
+              const long ia = ((long)z * N + j) * M + p;  // [z][j][p]
+              if (a.mode == kModeFirst) {
+                // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
+                a.accT[ia] = make_double2(dr, di);
+              } else if (a.mode == kModeTerm) {
+                // u_k = V u_{k-1}: the unscaled power; the slicing pass adds i^k g_k u_k
+                // to the FP64 Taylor sum
+                a.tout[ia] = make_double2(dr, di);
+              } else {
+                a.phi_out[((long)z * M + p) * N + j] =
+                    make_double2(fma(pd, accv[jj].x, dr), fma(pd, accv[jj].y, di));
+              }
             }
           }
         }
