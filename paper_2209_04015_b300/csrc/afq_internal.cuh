@@ -205,6 +205,18 @@ struct afq_ctx {
   int* ov_eb = nullptr;
   double2* ov_S = nullptr;
   CUtensorMap tm_ov_a, tm_ov_b;
+  // theta = Phi S^-1 of the split-precision walker ensemble on the tensor cores
+  // (k_mixed_prop.cu), per unit u = (z, spin): th_S exact digits of Phi's rows p over
+  // the spin's columns k (A: th_S x 2W x re/im x M x th_K) and of S^-1's columns j over
+  // k (B: th_S x 2W x re/im x nmax x th_K, and -Im: th_S x 2W x nmax x th_K), their
+  // exponents per (u, p) and (u, j), S^-1 itself in FP64 (2W x nmax x nmax, written by
+  // the overlap kernel) and the one-body energy's partial sums per GEMM tile and warp
+  int th_S = 0, th_K = 0, th_brows = 0;
+  __nv_bfloat16 *th_a_sl = nullptr, *th_b_sl = nullptr, *th_bn_sl = nullptr;
+  int *th_ea = nullptr, *th_eb = nullptr;
+  double2* th_sinv = nullptr;
+  double2* th_e1part = nullptr;
+  CUtensorMap tm_tha, tm_thb, tm_thbn;
 
   ChainTape chain;  // afq_chain_forward
   // half-rotated exchange tensor V_s[(j,p),(i,q)] = sum_g L~_g,s[j][q] L~_g,s[i][p] per
@@ -336,6 +348,10 @@ int mixed_prop_init_trial(afq_ctx* ctx);
 int mixed_prop_init_walkers(afq_ctx* ctx);
 int launch_vhs_tc(afq_ctx* ctx);
 int launch_propagate_tc(afq_ctx* ctx);
+// theta^T and E1 of the walker ensemble on the tensor cores from S^-1 in ctx->th_sinv
+int theta_tc_init_walkers(afq_ctx* ctx);
+void theta_tc_free(afq_ctx* ctx);
+int launch_theta_tc(afq_ctx* ctx, WalkerSet& s);
 // S = Psi^T Phi on the tensor cores (k_overlap_tc.cu)
 int overlap_tc_init_trial(afq_ctx* ctx);
 int overlap_tc_init_walkers(afq_ctx* ctx);

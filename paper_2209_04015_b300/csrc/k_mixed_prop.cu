@@ -125,7 +125,11 @@ struct VhsP {
 // Roles: warp 0 TMA, warp 1 MMA (and TMEM), warps 2-9 epilogue (two per TMEM lane
 // quarter, splitting the column chunks); the producer runs ahead across tiles while
 // the epilogue drains TMEM.
-enum { kModeFirst = 0, kModeTerm = 1, kModeLast = 2 };
+enum { kModeFirst = 0, kModeTerm = 1, kModeLast = 2, kModeTheta = 3 };
+// kModeTheta: the same kernel forms theta = Phi S^-1 per unit u = (z, spin) (A = the
+// digits of the unit's Phi rows over its K = n columns, B = those of S^-1; N = nmax),
+// writes theta^T into tout at the unit's rows of the W x (na + nb) x M layout and sums
+// E1 = sum_jp h~_jp theta_pj per tile and epilogue warp into e1part
 constexpr int kPropWarps = 10;
 constexpr int kAccAhead = 4;  // FP64 Taylor sums loaded ahead of the last pass's stores
 constexpr int kPropEpi = 8;
@@ -144,7 +148,23 @@ struct PropArgs {
   double2* phi_out;       // mode last: Phi (W x M x N)
   double2* tout;          // W x N x M FP64: the next operand (sliced by the next kernel)
   int* err;
+  int na, nb, Ntot;       // kModeTheta: electrons per spin and their sum
+  const double* ht;       // kModeTheta: h~ = Psi^T h1 (Ntot x M)
+  double2* e1part;        // kModeTheta: ntiles x kPropEpi partial sums of E1
 };
+
+// kModeTheta's output element: theta^T at the unit's rows, and this thread's share of E1
+__device__ __forceinline__ void prop_store_theta(const PropArgs& a, int z, int j, int p, double dr,
+                                                 double di, double2& e1) {
+  const int M = a.M, sg = z & 1, nsg = sg ? a.nb : a.na;
+  if (j < nsg) {
+    const long row = (long)(z >> 1) * a.Ntot + sg * a.na + j;
+    a.tout[row * M + p] = make_double2(dr, di);
+    const double h = a.ht[(long)(sg * a.na + j) * M + p];
+    e1.x = fma(h, dr, e1.x);
+    e1.y = fma(h, di, e1.y);
+  }
+}
 
 // TMEM load of CW (16 or 8) consecutive columns of this warp's lanes.
 template <int CW>
@@ -168,9 +188,10 @@ __device__ __forceinline__ void prop_epi_sync() {
 // Epilogue of one group of CW columns (c0 .. c0 + CW - 1) of this thread's row p (the
 // form the kernel takes beyond 4 digits): real parts first (digits -> FP64), then
 // their imaginary partners, then the pass's output.
-template <int S, int CW>
+template <int S, int CW, bool THETA>
 __device__ __forceinline__ void prop_epi_group(const PropArgs& a, uint32_t trow, int BN, int brows,
-                                               int c0, int z, int j0, int p, bool valid, int ep) {
+                                               int c0, int z, int j0, int p, bool valid, int ep,
+                                               double2& e1) {
   const int M = a.M, N = a.N;
   float f[S][CW];
   double dre[CW];
@@ -206,6 +227,10 @@ __device__ __forceinline__ void prop_epi_group(const PropArgs& a, uint32_t trow,
 #pragma unroll
       for (int d = 0; d < S; ++d) ai[d] = f[d][h + jj];
       const double dr = dre[h + jj], di = combine_exact<S>(ai, ep + a.eb[(long)z * N + j] - 14);
+      if constexpr (THETA) {
+        prop_store_theta(a, z, j, p, dr, di, e1);
+        continue;
+      }
       const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
       if (a.mode == kModeFirst) {
         // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
@@ -253,7 +278,7 @@ __device__ __forceinline__ void prop_issue_cat(uint32_t acc, int BN, uint32_t a0
   }
 }
 
-template <int S, bool REAL, bool CAT>
+template <int S, bool REAL, bool CAT, bool THETA = false>
 __global__ void __launch_bounds__(32 * kPropWarps, 1)
     k_prop_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmBn, const __grid_constant__ PropArgs a) {
@@ -432,11 +457,12 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
       const bool valid = p < M;
       const int ep = valid ? (REAL ? a.ea[p] : a.ea[(long)z * M + p]) : 0;
       const uint32_t trow = tmem + (uint32_t)(buf * S * BN) + ((uint32_t)(32 * lq) << 16);
+      double2 e1 = make_double2(0.0, 0.0);
       for (int c0 = 16 * part; c0 < brows; c0 += 32) {
         if constexpr (S > 4) {
           // more digits than registers for 16 columns at once: two groups of 8
-          prop_epi_group<S, 8>(a, trow, BN, brows, c0, z, j0, p, valid, ep);
-          prop_epi_group<S, 8>(a, trow, BN, brows, c0 + 8, z, j0, p, valid, ep);
+          prop_epi_group<S, 8, THETA>(a, trow, BN, brows, c0, z, j0, p, valid, ep, e1);
+          prop_epi_group<S, 8, THETA>(a, trow, BN, brows, c0 + 8, z, j0, p, valid, ep, e1);
         } else {
           // real parts of 16 columns first (digits -> FP64), then their imaginary partners.
           // In the last pass the FP64 Taylor sums are loaded into registers kAccAhead
@@ -477,6 +503,10 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
               for (int d = 0; d < S; ++d) ai[d] = f[d][h + jj];
               const double dr = dre[h + jj];
               const double di = combine_exact<S>(ai, ep + a.eb[(long)z * N + j] - 14);
+              if constexpr (THETA) {
+                prop_store_theta(a, z, j, p, dr, di, e1);
+                continue;
+              }
               const long ia = ((long)z * N + j) * M + p;  // [z][j][p]
               if (a.mode == kModeFirst) {
                 // O Phi; the slicing pass adds diag(P) Phi (FP64) and cuts u_0 = P Phi
@@ -492,6 +522,13 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
             }
           }
         }
+      }
+      if constexpr (THETA) {  // this warp's share of E1, summed in a fixed order
+        for (int o = 16; o > 0; o >>= 1) {
+          e1.x += __shfl_down_sync(0xffffffffu, e1.x, o);
+          e1.y += __shfl_down_sync(0xffffffffu, e1.y, o);
+        }
+        if (lane == 0) a.e1part[(long)tile * kPropEpi + q] = e1;
       }
       tc::fence_before_sync();
       if (lane == 0) tc::mbar_arrive(&tempty[buf]);
@@ -706,6 +743,111 @@ __global__ void k_taylor_acc(const double2* __restrict__ u, double2* __restrict_
     a.y = fma(gk, w.y, a.y);
     acc[e] = a;
   }
+}
+
+// Operands of theta = Phi S^-1 on the tensor cores, per unit u = (z, spin).
+// A: row (u, p) holds Phi[z][p][off + k] over the spin's n columns k, zero-padded to
+// Kt; one exponent per row shared by the real and imaginary parts; planes
+// [s][u][re/im][p][Kt].  One warp per row, lanes over k (Kt <= 64).
+template <int D>
+__global__ void k_slice_phi_theta(const double2* __restrict__ phi, int W, int M, int N, int na,
+                                  int nb, int Kt, int S, __nv_bfloat16* __restrict__ out,
+                                  int* __restrict__ eout) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const long rows = 2L * W * M, plane = 2L * rows * Kt;
+  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
+       r += (long)gridDim.x * warps) {
+    const long u = r / M;
+    const int p = (int)(r - u * M), sg = (int)(u & 1);
+    const int n = sg ? nb : na, off = sg ? na : 0;
+    const double2* row = phi + ((u >> 1) * M + p) * (long)N + off;
+    double2 v[2];
+    int m = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      v[h] = k < n ? row[k] : make_double2(0.0, 0.0);
+      m = max(m, max(exp_field(v[h].x), exp_field(v[h].y)));
+    }
+    const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
+    if (lane == 0) eout[r] = e;
+    __nv_bfloat16* ore = out + ((u * 2) * M + p) * (long)Kt;
+    __nv_bfloat16* oim = ore + (long)M * Kt;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      if (k >= Kt) continue;
+      float qr[D], qi[D];
+      exact_digits_f<D>(v[h].x, e, S, qr);
+      exact_digits_f<D>(v[h].y, e, S, qi);
+#pragma unroll
+      for (int s = 0; s < D; ++s)
+        if (s < S) {
+          ore[s * plane + k] = digit_bf16(qr[s]);
+          oim[s * plane + k] = digit_bf16(qi[s]);
+        }
+    }
+  }
+}
+
+// B: row (u, j) holds S^-1[k][j] over k < n (the unit's spin; S^-1 is u's nmax x nmax
+// block of sinv, [k][j]), zero-padded to Kt, rows j >= n zero; one exponent per row;
+// planes [s][u][re/im][j][Kt] and the negated imaginary digits [s][u][j][Kt] (the
+// second B region of the column-concatenated complex GEMM).
+template <int D>
+__global__ void k_slice_sinv(const double2* __restrict__ sinv, int W, int nmax, int na, int nb,
+                             int Kt, int S, __nv_bfloat16* __restrict__ out,
+                             __nv_bfloat16* __restrict__ nout, int* __restrict__ eout) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const long rows = 2L * W * nmax, plane = 2L * rows * Kt, nplane = rows * Kt;
+  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
+       r += (long)gridDim.x * warps) {
+    const long u = r / nmax;
+    const int j = (int)(r - u * nmax), n = (u & 1) ? nb : na;
+    const double2* blk = sinv + u * (long)nmax * nmax;
+    double2 v[2];
+    int m = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      v[h] = k < n && j < n ? blk[(long)k * nmax + j] : make_double2(0.0, 0.0);
+      m = max(m, max(exp_field(v[h].x), exp_field(v[h].y)));
+    }
+    const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
+    if (lane == 0) eout[r] = e;
+    __nv_bfloat16* ore = out + ((u * 2) * nmax + j) * (long)Kt;
+    __nv_bfloat16* oim = ore + (long)nmax * Kt;
+    __nv_bfloat16* onm = nout + r * Kt;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      if (k >= Kt) continue;
+      float qr[D], qi[D];
+      exact_digits_f<D>(v[h].x, e, S, qr);
+      exact_digits_f<D>(v[h].y, e, S, qi);
+#pragma unroll
+      for (int s = 0; s < D; ++s)
+        if (s < S) {
+          ore[s * plane + k] = digit_bf16(qr[s]);
+          oim[s * plane + k] = digit_bf16(qi[s]);
+          onm[s * nplane + k] = digit_bf16(-qi[s]);
+        }
+    }
+  }
+}
+
+// E1 per unit: the partial sums of its GEMM tiles and epilogue warps in a fixed order
+__global__ void k_e1_reduce(long units, int parts, const double2* __restrict__ part,
+                            double2* __restrict__ e1) {
+  const long u = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (u >= units) return;
+  double2 t = make_double2(0.0, 0.0);
+  for (int i = 0; i < parts; ++i) {
+    const double2 v = part[u * parts + i];
+    t.x += v.x;
+    t.y += v.y;
+  }
+  e1[u] = t;
 }
 
 // Digits of complex rows (z, i) of K elements into planes [s][z][re/im][i][Kp]: the
@@ -1097,12 +1239,12 @@ int sm_count_prop() {
   return n;
 }
 
-template <int S, bool REAL, bool CAT>
+template <int S, bool REAL, bool CAT, bool THETA = false>
 cudaError_t launch_prop_s(int grid, size_t smem, cudaStream_t stream, const CUtensorMap& ta,
                           const CUtensorMap& tb, const CUtensorMap& tbn, const PropArgs& a) {
-  cudaError_t e = raise_smem_limit((const void*)k_prop_tc<S, REAL, CAT>, smem);
+  cudaError_t e = raise_smem_limit((const void*)k_prop_tc<S, REAL, CAT, THETA>, smem);
   if (e != cudaSuccess) return e;
-  k_prop_tc<S, REAL, CAT><<<grid, 32 * kPropWarps, smem, stream>>>(ta, tb, tbn, a);
+  k_prop_tc<S, REAL, CAT, THETA><<<grid, 32 * kPropWarps, smem, stream>>>(ta, tb, tbn, a);
   return cudaGetLastError();
 }
 
@@ -1275,4 +1417,141 @@ int launch_propagate_tc(afq_ctx* ctx) {
   // Phi = P acc = diag(P) acc + O acc (written in place: a Phi^T output with a tiled
   // transpose after it measured 35 us slower per step at 290 orbitals)
   return launch_prop<true>(ctx, ctx->tm_pm, cur, ctx->e_pm, kModeLast, dg[n + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// theta = Phi S^-1 on the tensor cores (split-precision walker ensembles)
+// ---------------------------------------------------------------------------
+// theta_s = Phi_s S_s^-1 (Eq. halfgf) per unit u = (z, spin) is a complex product of
+// Phi's M x n rows and the n x n inverse: the propagation kernel's form with K = n
+// (one or two K blocks) and N = nmax columns, on exact digits of both operands (as
+// many as the force bias and the exchange take; up to 4).  The double-float form on
+// the FP32 pipe cost ~0.5 ms at 290 orbitals and 640 walkers.
+
+void theta_tc_free(afq_ctx* ctx) {
+  for (void* p : {(void*)ctx->th_a_sl, (void*)ctx->th_b_sl, (void*)ctx->th_bn_sl,
+                  (void*)ctx->th_ea, (void*)ctx->th_eb, (void*)ctx->th_sinv,
+                  (void*)ctx->th_e1part})
+    if (p) cudaFree(p);
+  ctx->th_a_sl = ctx->th_b_sl = ctx->th_bn_sl = nullptr;
+  ctx->th_ea = ctx->th_eb = nullptr;
+  ctx->th_sinv = ctx->th_e1part = nullptr;
+}
+
+int theta_tc_init_walkers(afq_ctx* ctx) {
+  theta_tc_free(ctx);
+  const int W = ctx->ws.W, M = ctx->M;
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  const int hi = ctx->S > ctx->Sp ? ctx->S : ctx->Sp;
+  // beyond 4 digits (FP64 quality) the double-float theta stays: the epilogue's int64
+  // recombination of 5 to 7 digit orders takes two FP64 conversions per element and
+  // one TMEM accumulator set, which measured slower at 290 orbitals (0.41 ms)
+  if (nmax < 1 || nmax > 64 || hi > kFastSlices) return AFQ_OK;
+  ctx->th_S = hi;
+  ctx->th_K = round_up(nmax, kBK);
+  ctx->th_brows = nmax >= 32 ? 32 : round_up(nmax, 16);
+  const int S = ctx->th_S, Kt = ctx->th_K, brows = ctx->th_brows;
+  const long units = 2L * W;
+  const int npt = (M + 127) / 128, njt = (nmax + brows - 1) / brows;
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_a_sl, (size_t)S * 2 * units * M * Kt * 2));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_b_sl, (size_t)S * 2 * units * nmax * Kt * 2));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_bn_sl, (size_t)S * units * nmax * Kt * 2));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_ea, (size_t)units * M * sizeof(int)));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_eb, (size_t)units * nmax * sizeof(int)));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_sinv, (size_t)units * nmax * nmax * sizeof(double2)));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_e1part,
+                           (size_t)units * npt * njt * kPropEpi * sizeof(double2)));
+  const uint64_t da[4] = {(uint64_t)Kt, (uint64_t)M, (uint64_t)(2 * units), (uint64_t)S};
+  const uint32_t ba[4] = {kBK, 128, 1, 1};
+  const uint64_t db[4] = {(uint64_t)Kt, (uint64_t)nmax, (uint64_t)(2 * units), (uint64_t)S};
+  const uint64_t dbn[4] = {(uint64_t)Kt, (uint64_t)nmax, (uint64_t)units, (uint64_t)S};
+  const uint32_t bb[4] = {kBK, (uint32_t)brows, 1, 1};
+  if (!make_tmap(&ctx->tm_tha, ctx->th_a_sl, 4, da, ba) ||
+      !make_tmap(&ctx->tm_thb, ctx->th_b_sl, 4, db, bb) ||
+      !make_tmap(&ctx->tm_thbn, ctx->th_bn_sl, 4, dbn, bb))
+    return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (theta) failed");
+  return AFQ_OK;
+}
+
+int launch_theta_tc(afq_ctx* ctx, WalkerSet& s) {
+  const int W = s.W, M = ctx->M, N = ctx->N, na = ctx->na, nb = ctx->nb;
+  const int nmax = na > nb ? na : nb, S = ctx->th_S, Kt = ctx->th_K;
+  const long units = 2L * W;
+  if (S < 1 || W != ctx->ws.W) return afq_fail(ctx, AFQ_ERR_STATE, "theta operands not set up");
+  // the digits of S^-1 (B) and of Phi (A)
+  if (S <= kFastSlices) {
+    k_slice_sinv<kFastSlices><<<warp_grid(units * nmax), 256, 0, ctx->stream>>>(
+        ctx->th_sinv, W, nmax, na, nb, Kt, S, ctx->th_b_sl, ctx->th_bn_sl, ctx->th_eb);
+    AFQ_LAUNCHED(ctx);
+    k_slice_phi_theta<kFastSlices><<<warp_grid(units * M), 256, 0, ctx->stream>>>(
+        s.phi, W, M, N, na, nb, Kt, S, ctx->th_a_sl, ctx->th_ea);
+  } else {
+    k_slice_sinv<kMaxSlices><<<warp_grid(units * nmax), 256, 0, ctx->stream>>>(
+        ctx->th_sinv, W, nmax, na, nb, Kt, S, ctx->th_b_sl, ctx->th_bn_sl, ctx->th_eb);
+    AFQ_LAUNCHED(ctx);
+    k_slice_phi_theta<kMaxSlices><<<warp_grid(units * M), 256, 0, ctx->stream>>>(
+        s.phi, W, M, N, na, nb, Kt, S, ctx->th_a_sl, ctx->th_ea);
+  }
+  AFQ_LAUNCHED(ctx);
+  PropArgs a{};
+  a.M = M;
+  a.N = nmax;
+  a.W = (int)units;
+  a.mode = kModeTheta;
+  const bool cat = ctx->p.prop_kernel != 2 && 2 * S * ctx->th_brows <= 512;
+  a.brows = ctx->th_brows;
+  a.BN = 2 * a.brows;
+  a.nkb = Kt / kBK;
+  a.npt = (M + 127) / 128;
+  a.njt = (nmax + a.brows - 1) / a.brows;
+  a.ntiles = a.W * a.njt * a.npt;
+  const int kUA = 2, kUB = cat ? 2 : 1;
+  const size_t whole = (size_t)S * (kUA * (size_t)kASlot + (size_t)kUB * a.BN * 64);
+  a.split = kUB == 2 && (kSmemLimit - 2048 - 1024) / whole < 2 ? 1 : 0;
+  a.tx_bytes = a.split ? (uint32_t)S * (kBK * 128 * 2 + 2 * kBK * a.brows * 2)
+                       : (uint32_t)S * (kUA * kBK * 128 * 2 + kUB * 2 * kBK * a.brows * 2);
+  a.nbuf = 2 * S * a.BN <= 512 ? 2 : 1;
+  a.tmem_cols = tmem_cols_for(a.nbuf * S * a.BN);
+  a.ea = ctx->th_ea;
+  a.eb = ctx->th_eb;
+  a.tout = s.thetaT;
+  a.err = ctx->flags + 2;
+  a.na = na;
+  a.nb = nb;
+  a.Ntot = N;
+  a.ht = ctx->ht;
+  a.e1part = ctx->th_e1part;
+  const size_t stage = a.split ? (size_t)S * ((size_t)kASlot + (size_t)a.BN * 64)
+                               : (size_t)S * (kUA * (size_t)kASlot + (size_t)kUB * a.BN * 64);
+  int nst = (int)((kSmemLimit - 2048 - 1024) / stage);
+  if (nst > kMaxStages) nst = kMaxStages;
+  if (nst < 1 || S * a.BN > 512) return afq_fail(ctx, AFQ_ERR_ARG, "theta tile does not fit");
+  a.stages = nst;
+  const size_t smem = stage * nst + 1024;
+  const int grid = a.ntiles < sm_count_prop() ? a.ntiles : sm_count_prop();
+  cudaError_t e = cudaErrorInvalidValue;
+  const CUtensorMap &ta = ctx->tm_tha, &tb = ctx->tm_thb, &tbn = ctx->tm_thbn;
+  if (cat) {
+    switch (S) {
+      case 1: e = launch_prop_s<1, false, true, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 2: e = launch_prop_s<2, false, true, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 3: e = launch_prop_s<3, false, true, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 4: e = launch_prop_s<4, false, true, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+    }
+  } else {
+    switch (S) {
+      case 1: e = launch_prop_s<1, false, false, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 2: e = launch_prop_s<2, false, false, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 3: e = launch_prop_s<3, false, false, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+      case 4: e = launch_prop_s<4, false, false, true>(grid, smem, ctx->stream, ta, tb, tbn, a); break;
+    }
+  }
+  ctx->launches++;
+  if (e != cudaSuccess)
+    return afq_fail(ctx, AFQ_ERR_CUDA, std::string("theta tc: ") + cudaGetErrorString(e));
+  const int parts = a.npt * a.njt * kPropEpi;
+  k_e1_reduce<<<(unsigned)((units + 127) / 128), 128, 0, ctx->stream>>>(units, parts,
+                                                                        ctx->th_e1part, s.e1);
+  AFQ_LAUNCHED(ctx);
+  return AFQ_OK;
 }

@@ -208,10 +208,11 @@ int overlap_tc_init_walkers(afq_ctx* ctx) {
   const uint32_t bb[3] = {kBK, 128, 1};
   if (!make_tmap(&ctx->tm_ov_b, ctx->ov_phi_sl, 3, db, bb))
     return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (overlap) failed");
-  return AFQ_OK;
+  return theta_tc_init_walkers(ctx);
 }
 
 void overlap_tc_free(afq_ctx* ctx) {
+  theta_tc_free(ctx);
   for (void* p : {(void*)ctx->ov_psi_sl, (void*)ctx->ov_ea, (void*)ctx->ov_phi_sl,
                   (void*)ctx->ov_eb, (void*)ctx->ov_S})
     if (p) cudaFree(p);

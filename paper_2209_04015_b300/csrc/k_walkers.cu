@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
                                                       double2* __restrict__ det,
                                                       double2* __restrict__ e1, int* flags,
                                                       const double2* __restrict__ Spre,
-                                                      int nmax, int pcr) {
+                                                      int nmax, int pcr,
+                                                      double2* __restrict__ sinv_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double2 red[OT / 32];
   __shared__ int s_piv;
@@ -351,9 +352,17 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
     }
   }
 
-  // 3. theta^T_jp = sum_k (S^-1)_kj Phi_pk and E1 = sum_jp h~_jp theta^T_jp
+  // 3. theta^T_jp = sum_k (S^-1)_kj Phi_pk and E1 = sum_jp h~_jp theta^T_jp -- or, for
+  // the tensor-core theta (sinv_out), S^-1 in FP64 for its digits
   double2 e1acc = cmk(0.0, 0.0);
-  if (DF) {
+  if (DF && sinv_out) {
+    const DF2* sdf = reinterpret_cast<const DF2*>(aug) + n;  // [k][j] at slot k * n2 + j
+    double2* so = sinv_out + (long)(2 * z + s) * nmax * nmax;
+    for (int e = tid; e < n * n; e += OT) {
+      const int k = e / n, j = e % n;
+      so[(long)k * nmax + j] = df_to_double(sdf[k * n2 + j]);
+    }
+  } else if (DF) {
     // S^-1 as double-floats: the right half of the eliminated augmented matrix
     const DF2* sdf = reinterpret_cast<const DF2*>(aug) + n;  // [k][j] at slot k * n2 + j
     DF2* pdf = reinterpret_cast<DF2*>(cphi);  // Phi chunk as double-floats
@@ -412,7 +421,7 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
   }
   const double2 tot = block_sum2(e1acc, red);
   if (tid == 0) {
-    e1[2 * z + s] = tot;
+    if (!sinv_out) e1[2 * z + s] = tot;
     det[2 * z + s] = s_det;
   }
 }
@@ -846,15 +855,20 @@ int launch_overlap_mo(afq_ctx* ctx, WalkerSet& s) {
   const size_t smem = overlap_smem(nmax);
   AFQ_CUDA(ctx, raise_smem_limit((const void*)k_overlap_theta<DF, MO>, smem));
   // split-precision walker ensembles take S from the tensor cores (k_overlap_tc.cu)
+  // and theta = Phi S^-1 with E1 (k_mixed_prop.cu), this kernel then giving det S and
+  // S^-1 only
   const double2* Spre = nullptr;
+  double2* sinv = nullptr;
   if (DF && ctx->ov_S && &s == &ctx->ws) {
     AFQ_TRY(launch_overlap_s_tc(ctx, s));
     Spre = ctx->ov_S;
+    sinv = ctx->th_sinv;
   }
   k_overlap_theta<DF, MO><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
       ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
-      ctx->flags, Spre, nmax, theta_chunk_rows(ctx->M, nmax));
+      ctx->flags, Spre, nmax, theta_chunk_rows(ctx->M, nmax), sinv);
   AFQ_LAUNCHED(ctx);
+  if (sinv) AFQ_TRY(launch_theta_tc(ctx, s));
   return AFQ_OK;
 }
 
