@@ -742,6 +742,9 @@ int afq_spin_squared(afq_ctx* ctx, double* s2_out, double* s2_mix) {
   if (!ctx) return AFQ_ERR_ARG;
   if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
   const size_t W = ctx->ws.W;
+  // split precision forms the step's theta at the force bias's digit count: the
+  // estimator takes it in double-floats
+  if (ctx->mixed && ctx->th_sinv) AFQ_TRY(launch_theta_precise(ctx));
   double* d = nullptr;  // W complex values, then the weighted estimate
   AFQ_TRY(dalloc(ctx, &d, 2 * W + 1));
   int rc = launch_spin_squared(ctx, ctx->ws, reinterpret_cast<double2*>(d), d + 2 * W);
@@ -762,6 +765,7 @@ int afq_one_rdm(afq_ctx* ctx, double* g_out) {
   if (!ctx || !g_out) return AFQ_ERR_ARG;
   if (!ctx->have_walkers) return afq_fail(ctx, AFQ_ERR_STATE, "afq_init_walkers first");
   const size_t NM = (size_t)ctx->N * ctx->M, MM2 = 2 * (size_t)ctx->M * ctx->M;
+  if (ctx->mixed && ctx->th_sinv) AFQ_TRY(launch_theta_precise(ctx));  // as for S^2
   double* d = nullptr;  // Thetabar (N x M complex), sum w, then the two matrices
   AFQ_TRY(dalloc(ctx, &d, 2 * (NM + 1 + MM2)));
   double2* work = reinterpret_cast<double2*>(d);

@@ -196,7 +196,7 @@ struct afq_ctx {
   CUtensorMap tm_exv_a[2], tm_exv_b;
 
   // overlap product S = Psi^T Phi of the split-precision walker ensemble on the tensor
-  // cores (k_overlap_tc.cu): 7 exact digits of Psi^T (N x Mpad per digit) with row
+  // cores (k_overlap_tc.cu): 7 exact digits of Psi^T and h~ (2N x Mpad per digit) with row
   // exponents, of Phi^T (2W N x Mpad per digit) with exponents per (z, j), and S itself
   // (W x 2 x nmax x nmax complex)
   __nv_bfloat16* ov_psi_sl = nullptr;
@@ -204,18 +204,18 @@ struct afq_ctx {
   __nv_bfloat16* ov_phi_sl = nullptr;
   int* ov_eb = nullptr;
   double2* ov_S = nullptr;
+  double2* ov_H = nullptr;  // h~ Phi per (z, spin), same layout: E1 = tr(S^-1 H)
   CUtensorMap tm_ov_a, tm_ov_b;
   // theta = Phi S^-1 of the split-precision walker ensemble on the tensor cores
   // (k_mixed_prop.cu), per unit u = (z, spin): th_S exact digits of Phi's rows p over
   // the spin's columns k (A: th_S x 2W x re/im x M x th_K) and of S^-1's columns j over
   // k (B: th_S x 2W x re/im x nmax x th_K, and -Im: th_S x 2W x nmax x th_K), their
-  // exponents per (u, p) and (u, j), S^-1 itself in FP64 (2W x nmax x nmax, written by
-  // the overlap kernel) and the one-body energy's partial sums per GEMM tile and warp
+  // exponents per (u, p) and (u, j), and S^-1 itself in FP64 (2W x nmax x nmax, written
+  // by the Gauss-Jordan kernel); E1 is summed by the pass that takes theta's exponents
   int th_S = 0, th_K = 0, th_brows = 0;
   __nv_bfloat16 *th_a_sl = nullptr, *th_b_sl = nullptr, *th_bn_sl = nullptr;
   int *th_ea = nullptr, *th_eb = nullptr;
   double2* th_sinv = nullptr;
-  double2* th_e1part = nullptr;
   CUtensorMap tm_tha, tm_thb, tm_thbn;
 
   ChainTape chain;  // afq_chain_forward
@@ -290,6 +290,7 @@ int launch_set_identity(afq_ctx* ctx, int M, double* out);
 
 // walker kernels (k_walkers.cu)
 int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s, bool df = false);
+int launch_theta_precise(afq_ctx* ctx);  // the walker ensemble's theta in double-floats
 int launch_force_bias_fp64(afq_ctx* ctx, WalkerSet& s);
 int launch_exchange_fp64(afq_ctx* ctx, WalkerSet& s);
 int launch_energy_assemble(afq_ctx* ctx, WalkerSet& s);
@@ -348,7 +349,7 @@ int mixed_prop_init_trial(afq_ctx* ctx);
 int mixed_prop_init_walkers(afq_ctx* ctx);
 int launch_vhs_tc(afq_ctx* ctx);
 int launch_propagate_tc(afq_ctx* ctx);
-// theta^T and E1 of the walker ensemble on the tensor cores from S^-1 in ctx->th_sinv
+// theta^T of the walker ensemble on the tensor cores from S^-1 in ctx->th_sinv
 int theta_tc_init_walkers(afq_ctx* ctx);
 void theta_tc_free(afq_ctx* ctx);
 int launch_theta_tc(afq_ctx* ctx, WalkerSet& s);

@@ -127,9 +127,8 @@ struct VhsP {
 // the epilogue drains TMEM.
 enum { kModeFirst = 0, kModeTerm = 1, kModeLast = 2, kModeTheta = 3 };
 // kModeTheta: the same kernel forms theta = Phi S^-1 per unit u = (z, spin) (A = the
-// digits of the unit's Phi rows over its K = n columns, B = those of S^-1; N = nmax),
-// writes theta^T into tout at the unit's rows of the W x (na + nb) x M layout and sums
-// E1 = sum_jp h~_jp theta_pj per tile and epilogue warp into e1part
+// digits of the unit's Phi rows over its K = n columns, B = those of S^-1; N = nmax)
+// and writes theta^T into tout at the unit's rows of the W x (na + nb) x M layout
 constexpr int kPropWarps = 10;
 constexpr int kAccAhead = 4;  // FP64 Taylor sums loaded ahead of the last pass's stores
 constexpr int kPropEpi = 8;
@@ -149,21 +148,35 @@ struct PropArgs {
   double2* tout;          // W x N x M FP64: the next operand (sliced by the next kernel)
   int* err;
   int na, nb, Ntot;       // kModeTheta: electrons per spin and their sum
-  const double* ht;       // kModeTheta: h~ = Psi^T h1 (Ntot x M)
-  double2* e1part;        // kModeTheta: ntiles x kPropEpi partial sums of E1
 };
 
-// kModeTheta's output element: theta^T at the unit's rows, and this thread's share of E1
+// kModeTheta's output element: theta^T at the unit's rows
 __device__ __forceinline__ void prop_store_theta(const PropArgs& a, int z, int j, int p, double dr,
-                                                 double di, double2& e1) {
-  const int M = a.M, sg = z & 1, nsg = sg ? a.nb : a.na;
-  if (j < nsg) {
-    const long row = (long)(z >> 1) * a.Ntot + sg * a.na + j;
-    a.tout[row * M + p] = make_double2(dr, di);
-    const double h = a.ht[(long)(sg * a.na + j) * M + p];
-    e1.x = fma(h, dr, e1.x);
-    e1.y = fma(h, di, e1.y);
-  }
+                                                 double di) {
+  const int sg = z & 1;
+  if (j < (sg ? a.nb : a.na))
+    a.tout[((long)(z >> 1) * a.Ntot + sg * a.na + j) * a.M + p] = make_double2(dr, di);
+}
+
+// The exact digit diagonals of a kModeTheta element (K <= 64, at most 4 digits: every
+// diagonal sum is an integer of magnitude at most (d + 1) 64 128^2 <= 2^22, and their
+// weighted int64 sum is below 2^47) recombined without the
+// FP64 pipe: float -> int by the 1.5 2^23 shift, int64 -> double by normalising the bits.
+template <int S>
+__device__ __forceinline__ double combine_theta(const float (&acc)[S], int scale_exp) {
+  long long t = 0;
+#pragma unroll
+  for (int d = 0; d < S; ++d)
+    t += (long long)(__float_as_int(__fadd_rn(acc[d], 12582912.0f)) - 0x4B400000) *
+         (1LL << (8 * (S - 1 - d)));
+  if (t == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)t & 0x8000000000000000ull;
+  const unsigned long long m = (unsigned long long)(t < 0 ? -t : t);
+  const int msb = 63 - __clzll((long long)m);  // <= 52
+  const unsigned long long bits = sgn |
+      ((unsigned long long)(msb + 1023 + scale_exp - 8 * (S - 1)) << 52) |
+      ((m << (52 - msb)) & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
 }
 
 // TMEM load of CW (16 or 8) consecutive columns of this warp's lanes.
@@ -190,8 +203,7 @@ __device__ __forceinline__ void prop_epi_sync() {
 // their imaginary partners, then the pass's output.
 template <int S, int CW, bool THETA>
 __device__ __forceinline__ void prop_epi_group(const PropArgs& a, uint32_t trow, int BN, int brows,
-                                               int c0, int z, int j0, int p, bool valid, int ep,
-                                               double2& e1) {
+                                               int c0, int z, int j0, int p, bool valid, int ep) {
   const int M = a.M, N = a.N;
   float f[S][CW];
   double dre[CW];
@@ -227,8 +239,7 @@ __device__ __forceinline__ void prop_epi_group(const PropArgs& a, uint32_t trow,
 #pragma unroll
       for (int d = 0; d < S; ++d) ai[d] = f[d][h + jj];
       const double dr = dre[h + jj], di = combine_exact<S>(ai, ep + a.eb[(long)z * N + j] - 14);
-      if constexpr (THETA) {
-        prop_store_theta(a, z, j, p, dr, di, e1);
+      if constexpr (THETA) {  // (theta runs at most 4 digits: the inline epilogue)
         continue;
       }
       const long ia = ((long)z * N + j) * M + p;    // [z][j][p]
@@ -457,12 +468,11 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
       const bool valid = p < M;
       const int ep = valid ? (REAL ? a.ea[p] : a.ea[(long)z * M + p]) : 0;
       const uint32_t trow = tmem + (uint32_t)(buf * S * BN) + ((uint32_t)(32 * lq) << 16);
-      double2 e1 = make_double2(0.0, 0.0);
       for (int c0 = 16 * part; c0 < brows; c0 += 32) {
         if constexpr (S > 4) {
           // more digits than registers for 16 columns at once: two groups of 8
-          prop_epi_group<S, 8, THETA>(a, trow, BN, brows, c0, z, j0, p, valid, ep, e1);
-          prop_epi_group<S, 8, THETA>(a, trow, BN, brows, c0 + 8, z, j0, p, valid, ep, e1);
+          prop_epi_group<S, 8, THETA>(a, trow, BN, brows, c0, z, j0, p, valid, ep);
+          prop_epi_group<S, 8, THETA>(a, trow, BN, brows, c0 + 8, z, j0, p, valid, ep);
         } else {
           // real parts of 16 columns first (digits -> FP64), then their imaginary partners.
           // In the last pass the FP64 Taylor sums are loaded into registers kAccAhead
@@ -478,7 +488,10 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
             float ar[S];
 #pragma unroll
             for (int d = 0; d < S; ++d) ar[d] = f[d][jj];
-            dre[jj] = (valid && j < N) ? combine_exact<S>(ar, ep + a.eb[(long)z * N + j] - 14) : 0.0;
+            if constexpr (THETA)
+              dre[jj] = (valid && j < N) ? combine_theta<S>(ar, ep + a.eb[(long)z * N + j] - 14) : 0.0;
+            else
+              dre[jj] = (valid && j < N) ? combine_exact<S>(ar, ep + a.eb[(long)z * N + j] - 14) : 0.0;
           }
 #pragma unroll
           for (int d = 0; d < S; ++d) tc::tmem_ld16(trow + (uint32_t)(d * BN + brows + c0), f[d]);
@@ -502,9 +515,10 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
 #pragma unroll
               for (int d = 0; d < S; ++d) ai[d] = f[d][h + jj];
               const double dr = dre[h + jj];
-              const double di = combine_exact<S>(ai, ep + a.eb[(long)z * N + j] - 14);
+              const double di = THETA ? combine_theta<S>(ai, ep + a.eb[(long)z * N + j] - 14)
+                                      : combine_exact<S>(ai, ep + a.eb[(long)z * N + j] - 14);
               if constexpr (THETA) {
-                prop_store_theta(a, z, j, p, dr, di, e1);
+                prop_store_theta(a, z, j, p, dr, di);
                 continue;
               }
               const long ia = ((long)z * N + j) * M + p;  // [z][j][p]
@@ -522,13 +536,6 @@ __global__ void __launch_bounds__(32 * kPropWarps, 1)
             }
           }
         }
-      }
-      if constexpr (THETA) {  // this warp's share of E1, summed in a fixed order
-        for (int o = 16; o > 0; o >>= 1) {
-          e1.x += __shfl_down_sync(0xffffffffu, e1.x, o);
-          e1.y += __shfl_down_sync(0xffffffffu, e1.y, o);
-        }
-        if (lane == 0) a.e1part[(long)tile * kPropEpi + q] = e1;
       }
       tc::fence_before_sync();
       if (lane == 0) tc::mbar_arrive(&tempty[buf]);
@@ -748,43 +755,52 @@ __global__ void k_taylor_acc(const double2* __restrict__ u, double2* __restrict_
 // Operands of theta = Phi S^-1 on the tensor cores, per unit u = (z, spin).
 // A: row (u, p) holds Phi[z][p][off + k] over the spin's n columns k, zero-padded to
 // Kt; one exponent per row shared by the real and imaginary parts; planes
-// [s][u][re/im][p][Kt].  One warp per row, lanes over k (Kt <= 64).
+// [s][u][re/im][p][Kt].  Each half-warp takes a row, two consecutive k per lane (Kt of
+// 32 or 64), so every digit plane is written as 64-byte bfloat16-pair runs.
 template <int D>
 __global__ void k_slice_phi_theta(const double2* __restrict__ phi, int W, int M, int N, int na,
                                   int nb, int Kt, int S, __nv_bfloat16* __restrict__ out,
                                   int* __restrict__ eout) {
-  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, hl = lane & 15;
+  const unsigned hmask = (lane < 16) ? 0x0000FFFFu : 0xFFFF0000u;
   const long rows = 2L * W * M, plane = 2L * rows * Kt;
-  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
-       r += (long)gridDim.x * warps) {
-    const long u = r / M;
-    const int p = (int)(r - u * M), sg = (int)(u & 1);
+  const long hw0 = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const long nhw = ((long)gridDim.x * blockDim.x) >> 4;
+  for (long r = hw0; r - (hw0 & 1) < rows; r += nhw) {  // both halves of a warp iterate alike
+    const bool live = r < rows;
+    const long rr = live ? r : rows - 1;
+    const long u = rr / M;
+    const int p = (int)(rr - u * M), sg = (int)(u & 1);
     const int n = sg ? nb : na, off = sg ? na : 0;
     const double2* row = phi + ((u >> 1) * M + p) * (long)N + off;
-    double2 v[2];
+    double2 v[2][2];
     int m = 0;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int k = lane + 32 * h;
-      v[h] = k < n ? row[k] : make_double2(0.0, 0.0);
-      m = max(m, max(exp_field(v[h].x), exp_field(v[h].y)));
-    }
-    const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
-    if (lane == 0) eout[r] = e;
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * hl + 32 * t + h;
+        v[t][h] = k < n ? row[k] : make_double2(0.0, 0.0);
+        m = max(m, max(exp_field(v[t][h].x), exp_field(v[t][h].y)));
+      }
+    const int e = row_exponent_field(__reduce_max_sync(hmask, m));
+    if (live && hl == 0) eout[rr] = e;
     __nv_bfloat16* ore = out + ((u * 2) * M + p) * (long)Kt;
     __nv_bfloat16* oim = ore + (long)M * Kt;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int k = lane + 32 * h;
-      if (k >= Kt) continue;
-      float qr[D], qi[D];
-      exact_digits_f<D>(v[h].x, e, S, qr);
-      exact_digits_f<D>(v[h].y, e, S, qi);
+    for (int t = 0; t < 2; ++t) {
+      const int k = 2 * hl + 32 * t;
+      if (!live || k >= Kt) continue;
+      float r0[D], r1[D], i0[D], i1[D];
+      exact_digits_f<D>(v[t][0].x, e, S, r0);
+      exact_digits_f<D>(v[t][1].x, e, S, r1);
+      exact_digits_f<D>(v[t][0].y, e, S, i0);
+      exact_digits_f<D>(v[t][1].y, e, S, i1);
 #pragma unroll
       for (int s = 0; s < D; ++s)
         if (s < S) {
-          ore[s * plane + k] = digit_bf16(qr[s]);
-          oim[s * plane + k] = digit_bf16(qi[s]);
+          *reinterpret_cast<__nv_bfloat162*>(ore + s * plane + k) = digit_bf16x2(r0[s], r1[s]);
+          *reinterpret_cast<__nv_bfloat162*>(oim + s * plane + k) = digit_bf16x2(i0[s], i1[s]);
         }
     }
   }
@@ -834,20 +850,6 @@ __global__ void k_slice_sinv(const double2* __restrict__ sinv, int W, int nmax, 
         }
     }
   }
-}
-
-// E1 per unit: the partial sums of its GEMM tiles and epilogue warps in a fixed order
-__global__ void k_e1_reduce(long units, int parts, const double2* __restrict__ part,
-                            double2* __restrict__ e1) {
-  const long u = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (u >= units) return;
-  double2 t = make_double2(0.0, 0.0);
-  for (int i = 0; i < parts; ++i) {
-    const double2 v = part[u * parts + i];
-    t.x += v.x;
-    t.y += v.y;
-  }
-  e1[u] = t;
 }
 
 // Digits of complex rows (z, i) of K elements into planes [s][z][re/im][i][Kp]: the
@@ -1430,12 +1432,11 @@ int launch_propagate_tc(afq_ctx* ctx) {
 
 void theta_tc_free(afq_ctx* ctx) {
   for (void* p : {(void*)ctx->th_a_sl, (void*)ctx->th_b_sl, (void*)ctx->th_bn_sl,
-                  (void*)ctx->th_ea, (void*)ctx->th_eb, (void*)ctx->th_sinv,
-                  (void*)ctx->th_e1part})
+                  (void*)ctx->th_ea, (void*)ctx->th_eb, (void*)ctx->th_sinv})
     if (p) cudaFree(p);
   ctx->th_a_sl = ctx->th_b_sl = ctx->th_bn_sl = nullptr;
   ctx->th_ea = ctx->th_eb = nullptr;
-  ctx->th_sinv = ctx->th_e1part = nullptr;
+  ctx->th_sinv = nullptr;
 }
 
 int theta_tc_init_walkers(afq_ctx* ctx) {
@@ -1452,15 +1453,12 @@ int theta_tc_init_walkers(afq_ctx* ctx) {
   ctx->th_brows = nmax >= 32 ? 32 : round_up(nmax, 16);
   const int S = ctx->th_S, Kt = ctx->th_K, brows = ctx->th_brows;
   const long units = 2L * W;
-  const int npt = (M + 127) / 128, njt = (nmax + brows - 1) / brows;
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_a_sl, (size_t)S * 2 * units * M * Kt * 2));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_b_sl, (size_t)S * 2 * units * nmax * Kt * 2));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_bn_sl, (size_t)S * units * nmax * Kt * 2));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_ea, (size_t)units * M * sizeof(int)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_eb, (size_t)units * nmax * sizeof(int)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_sinv, (size_t)units * nmax * nmax * sizeof(double2)));
-  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->th_e1part,
-                           (size_t)units * npt * njt * kPropEpi * sizeof(double2)));
   const uint64_t da[4] = {(uint64_t)Kt, (uint64_t)M, (uint64_t)(2 * units), (uint64_t)S};
   const uint32_t ba[4] = {kBK, 128, 1, 1};
   const uint64_t db[4] = {(uint64_t)Kt, (uint64_t)nmax, (uint64_t)(2 * units), (uint64_t)S};
@@ -1519,8 +1517,6 @@ int launch_theta_tc(afq_ctx* ctx, WalkerSet& s) {
   a.na = na;
   a.nb = nb;
   a.Ntot = N;
-  a.ht = ctx->ht;
-  a.e1part = ctx->th_e1part;
   const size_t stage = a.split ? (size_t)S * ((size_t)kASlot + (size_t)a.BN * 64)
                                : (size_t)S * (kUA * (size_t)kASlot + (size_t)kUB * a.BN * 64);
   int nst = (int)((kSmemLimit - 2048 - 1024) / stage);
@@ -1549,9 +1545,5 @@ int launch_theta_tc(afq_ctx* ctx, WalkerSet& s) {
   ctx->launches++;
   if (e != cudaSuccess)
     return afq_fail(ctx, AFQ_ERR_CUDA, std::string("theta tc: ") + cudaGetErrorString(e));
-  const int parts = a.npt * a.njt * kPropEpi;
-  k_e1_reduce<<<(unsigned)((units + 127) / 128), 128, 0, ctx->stream>>>(units, parts,
-                                                                        ctx->th_e1part, s.e1);
-  AFQ_LAUNCHED(ctx);
   return AFQ_OK;
 }

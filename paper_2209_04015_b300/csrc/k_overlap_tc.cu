@@ -28,15 +28,16 @@ namespace {
 constexpr int kOvDigits = 7;
 constexpr int kOvBN = 64;  // columns i per tile: 7 accumulators x 64 fit the 512 TMEM columns
 
-// Real rows of K doubles (row pitch ld) -> S digit planes of rows x Kp with one
-// exponent per row (one warp per row).
-__global__ void k_slice_rows7(const double* __restrict__ in, long ld, long rows, int K, int Kp,
-                              int S, __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
+// Real rows of K doubles (row pitch ld; rows from rows1 on come from in2) -> S digit
+// planes of rows x Kp with one exponent per row (one warp per row).
+__global__ void k_slice_rows7(const double* __restrict__ in, const double* __restrict__ in2,
+                              long rows1, long ld, long rows, int K, int Kp, int S,
+                              __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
   const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
   const long plane = rows * Kp;
   for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
        r += (long)gridDim.x * warps) {
-    const double* row = in + r * ld;
+    const double* row = r < rows1 ? in + r * ld : in2 + (r - rows1) * ld;
     int m = 0;
     for (int k = lane; k < K; k += 32) m = max(m, exp_field(row[k]));
     const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
@@ -114,6 +115,7 @@ struct OvP {
     const int* ea;      // row exponents of Psi^T
     const int* eb;      // exponents of Phi^T per complex row (z, j)
     double2* S;         // W x 2 x nmax x nmax
+    double2* H;         // W x 2 x nmax x nmax: h~ Phi (B rows N .. 2N - 1), or unused
   };
   struct Tile {
     int r0, n0, kb0, kb1;
@@ -147,6 +149,8 @@ struct OvP {
     const int sj = j < a.na ? 0 : 1, oj = sj ? a.na : 0;
     const int ej = valid ? a.eb[z * N + j] : 0;
     double* dst = reinterpret_cast<double*>(a.S + (z * 2 + sj) * (long)a.nmax * a.nmax) + part;
+    double* hdst = a.H ? reinterpret_cast<double*>(a.H + (z * 2 + sj) * (long)a.nmax * a.nmax) + part
+                       : nullptr;
     for (int c0 = 0; c0 < a.c.BN; c0 += 16) {
       float f[kOvDigits][16];
 #pragma unroll
@@ -154,12 +158,14 @@ struct OvP {
       if (!valid) continue;
 #pragma unroll
       for (int ii = 0; ii < 16; ++ii) {
-        const int i = t.n0 + c0 + ii;  // orbital i of the trial
-        if (i >= N || (i < a.na ? 0 : 1) != sj) continue;
+        const int ib = t.n0 + c0 + ii;  // B row: orbital i of Psi^T, or of h~ from N on
+        const int i = ib < N ? ib : ib - N;
+        if (ib >= (a.H ? 2 * N : N) || (i < a.na ? 0 : 1) != sj) continue;
         float acc[kOvDigits];
 #pragma unroll
         for (int d = 0; d < kOvDigits; ++d) acc[d] = f[d][ii];
-        dst[2 * ((long)(i - oj) * a.nmax + (j - oj))] = combine7(acc, a.ea[i] + ej - 14);
+        double* out = ib < N ? dst : hdst;
+        out[2 * ((long)(i - oj) * a.nmax + (j - oj))] = combine7(acc, a.ea[ib] + ej - 14);
       }
     }
   }
@@ -172,19 +178,23 @@ int warp_grid7(long rows) {
 
 }  // namespace
 
-// Once per trial: the 7 digits of Psi^T (N x M, rows alpha then beta) and their map.
+// Once per trial: the 7 digits of Psi^T and of h~ (N x M each, rows alpha then beta)
+// and their map.
 int overlap_tc_init_trial(afq_ctx* ctx) {
   const int N = ctx->N, M = ctx->M, Mpad = ctx->Mpad;
   if (ctx->ov_psi_sl) cudaFree(ctx->ov_psi_sl);
   if (ctx->ov_ea) cudaFree(ctx->ov_ea);
   ctx->ov_psi_sl = nullptr;
   ctx->ov_ea = nullptr;
-  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_psi_sl, (size_t)kOvDigits * N * Mpad * 2));
-  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_ea, (size_t)N * sizeof(int)));
-  k_slice_rows7<<<warp_grid7(N), 256, 0, ctx->stream>>>(ctx->psiT, M, N, M, Mpad, kOvDigits,
-                                                         ctx->ov_psi_sl, ctx->ov_ea);
+  // B rows: Psi^T (N), then h~ = Psi^T h1 (N), so that one GEMM also gives h~ Phi, from
+  // which E1 = tr(S^-1 h~ Phi) follows when theta itself is formed at 4 digits
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_psi_sl, (size_t)kOvDigits * 2 * N * Mpad * 2));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_ea, (size_t)2 * N * sizeof(int)));
+  k_slice_rows7<<<warp_grid7(2 * N), 256, 0, ctx->stream>>>(ctx->psiT, ctx->ht, N, M, 2 * N, M,
+                                                             Mpad, kOvDigits, ctx->ov_psi_sl,
+                                                             ctx->ov_ea);
   AFQ_LAUNCHED(ctx);
-  const uint64_t da[3] = {(uint64_t)Mpad, (uint64_t)N, (uint64_t)kOvDigits};
+  const uint64_t da[3] = {(uint64_t)Mpad, (uint64_t)(2 * N), (uint64_t)kOvDigits};
   const uint32_t ba[3] = {kBK, (uint32_t)kOvBN, 1};
   if (!make_tmap(&ctx->tm_ov_a, ctx->ov_psi_sl, 3, da, ba))
     return afq_fail(ctx, AFQ_ERR_CUDA, "cuTensorMapEncodeTiled (overlap) failed");
@@ -195,15 +205,17 @@ int overlap_tc_init_trial(afq_ctx* ctx) {
 int overlap_tc_init_walkers(afq_ctx* ctx) {
   const int N = ctx->N, W = ctx->ws.W, Mpad = ctx->Mpad;
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
-  for (void* p : {(void*)ctx->ov_phi_sl, (void*)ctx->ov_eb, (void*)ctx->ov_S})
+  for (void* p : {(void*)ctx->ov_phi_sl, (void*)ctx->ov_eb, (void*)ctx->ov_S, (void*)ctx->ov_H})
     if (p) cudaFree(p);
   ctx->ov_phi_sl = nullptr;
   ctx->ov_eb = nullptr;
   ctx->ov_S = nullptr;
+  ctx->ov_H = nullptr;
   const long rows = 2L * W * N;
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_phi_sl, (size_t)kOvDigits * rows * Mpad * 2));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_eb, (size_t)W * N * sizeof(int)));
   AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_S, (size_t)W * 2 * nmax * nmax * sizeof(double2)));
+  AFQ_CUDA(ctx, cudaMalloc((void**)&ctx->ov_H, (size_t)W * 2 * nmax * nmax * sizeof(double2)));
   const uint64_t db[3] = {(uint64_t)Mpad, (uint64_t)rows, (uint64_t)kOvDigits};
   const uint32_t bb[3] = {kBK, 128, 1};
   if (!make_tmap(&ctx->tm_ov_b, ctx->ov_phi_sl, 3, db, bb))
@@ -214,8 +226,9 @@ int overlap_tc_init_walkers(afq_ctx* ctx) {
 void overlap_tc_free(afq_ctx* ctx) {
   theta_tc_free(ctx);
   for (void* p : {(void*)ctx->ov_psi_sl, (void*)ctx->ov_ea, (void*)ctx->ov_phi_sl,
-                  (void*)ctx->ov_eb, (void*)ctx->ov_S})
+                  (void*)ctx->ov_eb, (void*)ctx->ov_S, (void*)ctx->ov_H})
     if (p) cudaFree(p);
+  ctx->ov_H = nullptr;
   ctx->ov_psi_sl = nullptr;
   ctx->ov_ea = nullptr;
   ctx->ov_phi_sl = nullptr;
@@ -223,7 +236,8 @@ void overlap_tc_free(afq_ctx* ctx) {
   ctx->ov_S = nullptr;
 }
 
-// S_z,s = Psi_s^T Phi_z,s for the walker set (its digits, then the GEMM) into ctx->ov_S.
+// S_z,s = Psi_s^T Phi_z,s for the walker set (its digits, then the GEMM) into ctx->ov_S,
+// and with the tensor-core theta also H_z,s = h~_s Phi_z,s into ctx->ov_H.
 int launch_overlap_s_tc(afq_ctx* ctx, WalkerSet& s) {
   const int N = ctx->N, M = ctx->M, Mpad = ctx->Mpad, W = s.W;
   k_slice_phiT7<<<warp_grid7((long)W * N), 256, 0, ctx->stream>>>(s.phi, W, M, N, Mpad, kOvDigits,
@@ -244,11 +258,14 @@ int launch_overlap_s_tc(afq_ctx* ctx, WalkerSet& s) {
   a.ea = ctx->ov_ea;
   a.eb = ctx->ov_eb;
   a.S = ctx->ov_S;
+  const bool with_h = ctx->th_sinv != nullptr && &s == &ctx->ws;  // E1 = tr(S^-1 H)
+  a.H = with_h ? ctx->ov_H : nullptr;
   size_t smem = 0;
   plan_smem(kOvDigits, 1, 1, kOvBN, 0, &a.c.stages, &smem);
   if (a.c.stages < 1 || smem > kSmemLimit)
     return afq_fail(ctx, AFQ_ERR_ARG, "overlap tile does not fit in shared memory");
-  dim3 grid((unsigned)((a.rows_a + 127) / 128), (unsigned)((N + kOvBN - 1) / kOvBN));
+  const int brows = with_h ? 2 * N : N;
+  dim3 grid((unsigned)((a.rows_a + 127) / 128), (unsigned)((brows + kOvBN - 1) / kOvBN));
   cudaError_t e = launch_tc<kOvDigits, OvP>(grid, smem, ctx->stream, ctx->tm_ov_b, ctx->tm_ov_a, a);
   ctx->launches++;
   if (e != cudaSuccess)

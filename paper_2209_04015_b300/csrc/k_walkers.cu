@@ -7,6 +7,7 @@
 // so every DFMA is fed without global-memory waits, and size grids in the
 // thousands of CTAs so all 148 SMs keep their FP64 pipes busy.
 #include "afq_internal.cuh"
+#include "df_arith.cuh"
 
 namespace {
 
@@ -40,107 +41,127 @@ __device__ double2 block_sum2(double2 v, double2* red) {
 // det S_s and S_s^-1, theta_s^T = S_s^-T Phi_s^T, and E1_s = sum h~ . theta.
 // One CTA per (walker, spin).
 // ---------------------------------------------------------------------------
-// Double-float (hi + lo FP32 pairs, Dekker / Knuth) arithmetic for theta in the
-// split-precision mode: x = hi + lo with |lo| <= ulp(hi) / 2, products with their
-// exact FMA error term and two-sum accumulation, ~2^-44 relative -- near FP64 for
-// one-body energies while running on the FP32 pipe (64x B300's FP64 rate).
-struct DF2 {
-  float2 hi, lo;  // complex: (re, im) of the high and the low parts
-};
-// x = h + l from the bits on the integer pipe (B300 runs double <-> float conversions
-// on its 2-lane FP64 pipe): h keeps the top 24 significant bits of x (truncated), l the
-// next 29 rounded to 24, so |x - h - l| <= 2^-48 |x|.  Zero, subnormal and
-// out-of-float-range inputs (not met by walkers or S^-1 of bounded condition) give
-// h = l = 0 or a saturated h.
-__device__ __forceinline__ void df_split(double x, float& h, float& l) {
-  const long long b = __double_as_longlong(x);
-  const int E = (int)((b >> 52) & 0x7FF);
-  const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
-  if (E < 897 || E > 1150) {  // outside the normal float range: zero or saturate
-    h = E < 897 ? 0.f : __int_as_float((int)(sign | 0x7F7FFFFFu));
-    l = 0.f;
+
+// det S and S^-1 of the split-precision walker ensemble when theta is formed on the
+// tensor cores: one warp per (walker, spin) matrix, in-place Gauss-Jordan elimination
+// with partial row pivoting (ties -> lowest row) on double-floats (n^3 complex updates
+// instead of the augmented form's ~1.5 n^3), lanes over columns, only warp-level
+// synchronisation; the row swaps are undone on the columns at the end.  det S is
+// accumulated in FP64 from the pivots; S^-1 is written in FP64 ([k][j], nmax apart);
+// E1 follows from S^-1 and H = h~ Phi (both exact to FP64 quality), not from theta.
+// A pivot with |p|^2 below 1e-36 (the double-float range) is flagged as singular.
+__global__ void k_gj_df(int units, int na, int nb, int nmax, const double2* __restrict__ Spre,
+                        const double2* __restrict__ H, double2* __restrict__ sinv,
+                        double2* __restrict__ det, double2* __restrict__ e1, int* flags) {
+  extern __shared__ __align__(16) unsigned char gjraw[];
+  const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long unit = (long)blockIdx.x * wpb + wid;
+  if (unit >= units) return;  // whole warps only: no block-wide synchronisation below
+  const int n = (unit & 1) ? nb : na;
+  if (n == 0) {
+    if (lane == 0) {
+      det[unit] = cmk(1.0, 0.0);
+      e1[unit] = cmk(0.0, 0.0);
+    }
     return;
   }
-  const long long m = b & 0xFFFFFFFFFFFFFLL;
-  h = __int_as_float((int)(sign | ((unsigned)(E - 896) << 23) | (unsigned)(m >> 29)));
-  const int low = (int)(m & 0x1FFFFFFF);  // the 29 bits below h: low 2^(E - 1075)
-  const int se = E - 1075 + 127;          // biased exponent of 2^(E - 1075)
-  const float scale = se > 0 ? __int_as_float(se << 23) : 0.f;
-  l = (float)low * scale;
-  if (sign) l = -l;
-}
-// float -> double from the bits (normal floats; zero and subnormals give 0)
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = (unsigned)__float_as_int(f);
-  const unsigned e = (u >> 23) & 0xFF;
-  if (e == 0) return 0.0;
-  const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
-                               ((unsigned long long)(e + 896) << 52) |
-                               ((unsigned long long)(u & 0x7FFFFF) << 29);
-  return __longlong_as_double((long long)b);
-}
-// (sh, sl) += a * b for real double-floats a = (ah, al), b = (bh, bl)
-__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh,
-                                       float bl) {
-  const float p = ah * bh;
-  const float e = fmaf(ah, bh, -p);             // exact error of the head product
-  const float c = fmaf(ah, bl, al * bh);        // cross terms (low order)
-  const float t = sh + p;                       // two-sum of the heads
-  const float bv = t - sh;
-  const float err = (sh - (t - bv)) + (p - bv);
-  sl += err + e + c;
-  sh = t;
-}
-
-// The same multiply-accumulate with every rounding spelled out (__fmul_rn / __fadd_rn
-// are never contracted into an FMA, so the two-sum sees the rounded head product),
-// and a renormalisation (two-sum of head and tail) for values that are stored and
-// updated again: the Gauss-Jordan elimination below updates each entry up to n times.
-__device__ __forceinline__ void df_mac_rn(float& sh, float& sl, float ah, float al, float bh,
-                                          float bl) {
-  const float p = __fmul_rn(ah, bh);
-  const float e = fmaf(ah, bh, -p);
-  const float c = fmaf(ah, bl, __fmul_rn(al, bh));
-  const float t = __fadd_rn(sh, p);
-  const float bv = __fsub_rn(t, sh);
-  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bv)), __fsub_rn(p, bv));
-  sl = __fadd_rn(sl, __fadd_rn(err, __fadd_rn(e, c)));
-  sh = t;
-}
-__device__ __forceinline__ void df_renorm(float& h, float& l) {
-  const float s = __fadd_rn(h, l), bv = __fsub_rn(s, h);
-  l = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(l, bv));
-  h = s;
-}
-// acc - f a and a b for complex double-floats (renormalised)
-__device__ __forceinline__ DF2 df_cfms(const DF2& f, const DF2& a, const DF2& acc) {
-  float rh = acc.hi.x, rl = acc.lo.x, ih = acc.hi.y, il = acc.lo.y;
-  df_mac_rn(rh, rl, -f.hi.x, -f.lo.x, a.hi.x, a.lo.x);
-  df_mac_rn(rh, rl, f.hi.y, f.lo.y, a.hi.y, a.lo.y);
-  df_mac_rn(ih, il, -f.hi.x, -f.lo.x, a.hi.y, a.lo.y);
-  df_mac_rn(ih, il, -f.hi.y, -f.lo.y, a.hi.x, a.lo.x);
-  df_renorm(rh, rl);
-  df_renorm(ih, il);
-  return DF2{make_float2(rh, ih), make_float2(rl, il)};
-}
-__device__ __forceinline__ DF2 df_cmul(const DF2& a, const DF2& b) {
+  DF2* a = reinterpret_cast<DF2*>(gjraw) + (long)wid * (nmax * nmax + nmax);  // n x n, then
+  DF2* fk = a + nmax * nmax;                                                  // column k
+  int* perm = reinterpret_cast<int*>(reinterpret_cast<DF2*>(gjraw) + (long)wpb * (nmax * nmax + nmax)) +
+              wid * nmax;
+  const double2* Sz = Spre + unit * nmax * nmax;
+  for (int i = 0; i < n; ++i)
+    for (int j = lane; j < n; j += 32) a[i * n + j] = df_from(Sz[(long)i * nmax + j]);
+  __syncwarp();
+  double2 dt = cmk(1.0, 0.0);
+  for (int k = 0; k < n; ++k) {
+    float best = -1.f;
+    int bi = k;
+    for (int i = k + lane; i < n; i += 32) {
+      const float2 h = a[i * n + k].hi;
+      const float v = h.x * h.x + h.y * h.y;
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (bi != k)
+      for (int j = lane; j < n; j += 32) {
+        const DF2 t = a[k * n + j];
+        a[k * n + j] = a[bi * n + j];
+        a[bi * n + j] = t;
+      }
+    if (lane == 0) perm[k] = bi;
+    __syncwarp();
+    DF2 pv = a[k * n + k];
+    const float m2 = pv.hi.x * pv.hi.x + pv.hi.y * pv.hi.y;
+    const bool bad = !(m2 >= 1e-36f);
+    if (bad) {
+      if (lane == 0) atomicAdd(&flags[0], 1);
+      pv = DF2{make_float2(1.f, 0.f), make_float2(0.f, 0.f)};
+    }
+    const double2 d = cmul(dt, df_to_double(pv));
+    dt = bi != k ? cmk(-d.x, -d.y) : d;
+    const DF2 inv = df_crecip(pv);
+    for (int j = lane; j < n; j += 32) a[k * n + j] = j == k ? inv : df_cmul(a[k * n + j], inv);
+    for (int i = lane; i < n; i += 32) fk[i] = a[i * n + k];
+    __syncwarp();
+    const DF2 zero = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int j = lane; j < n; j += 32) {
+      const DF2 akj = j == k ? inv : a[k * n + j];
+      // four rows at a time: independent double-float chains for the latency
+      for (int i0 = 0; i0 < n; i0 += 4) {
+        DF2 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u;
+          if (i < n && i != k) r[u] = df_cfms(fk[i], akj, j == k ? zero : a[i * n + j]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u;
+          if (i < n && i != k) a[i * n + j] = r[u];
+        }
+      }
+    }
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = lane; i < n; i += 32) {
+        const DF2 t = a[i * n + k];
+        a[i * n + k] = a[i * n + p];
+        a[i * n + p] = t;
+      }
+    __syncwarp();
+  }
+  double2* so = sinv + unit * nmax * nmax;
+  for (int i = 0; i < n; ++i)
+    for (int j = lane; j < n; j += 32) so[(long)i * nmax + j] = df_to_double(a[i * n + j]);
+  // E1 = sum_jp h~_jp theta_pj = tr(H S^-1) with H = h~ Phi (trial i x walker j, from the
+  // overlap GEMM): lanes over the walker index j, sum over i of H_ij (S^-1)_ji
+  const double2* Hz = H + unit * nmax * nmax;
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-  df_mac_rn(rh, rl, a.hi.x, a.lo.x, b.hi.x, b.lo.x);
-  df_mac_rn(rh, rl, -a.hi.y, -a.lo.y, b.hi.y, b.lo.y);
-  df_mac_rn(ih, il, a.hi.x, a.lo.x, b.hi.y, b.lo.y);
-  df_mac_rn(ih, il, a.hi.y, a.lo.y, b.hi.x, b.lo.x);
+  for (int j = lane; j < n; j += 32)
+    for (int i = 0; i < n; ++i) {
+      const DF2 h = df_from(Hz[(long)i * nmax + j]);
+      const DF2 b = a[j * n + i];
+      df_mac_rn(rh, rl, h.hi.x, h.lo.x, b.hi.x, b.lo.x);
+      df_mac_rn(rh, rl, -h.hi.y, -h.lo.y, b.hi.y, b.lo.y);
+      df_mac_rn(ih, il, h.hi.x, h.lo.x, b.hi.y, b.lo.y);
+      df_mac_rn(ih, il, h.hi.y, h.lo.y, b.hi.x, b.lo.x);
+    }
   df_renorm(rh, rl);
   df_renorm(ih, il);
-  return DF2{make_float2(rh, ih), make_float2(rl, il)};
-}
-__device__ __forceinline__ DF2 df_from(double2 v) {
-  DF2 d;
-  df_split(v.x, d.hi.x, d.lo.x);
-  df_split(v.y, d.hi.y, d.lo.y);
-  return d;
-}
-__device__ __forceinline__ double2 df_to_double(const DF2& v) {
-  return cmk(f2d_bits(v.hi.x) + f2d_bits(v.lo.x), f2d_bits(v.hi.y) + f2d_bits(v.lo.y));
+  df_warp_sum(rh, rl);
+  df_warp_sum(ih, il);
+  if (lane == 0) {
+    det[unit] = dt;
+    e1[unit] = cmk(f2d_bits(rh) + f2d_bits(rl), f2d_bits(ih) + f2d_bits(il));
+  }
 }
 
 // MO: S entries per thread (n^2 <= OT MO); the launch picks the smallest that fits,
@@ -154,8 +175,7 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
                                                       double2* __restrict__ det,
                                                       double2* __restrict__ e1, int* flags,
                                                       const double2* __restrict__ Spre,
-                                                      int nmax, int pcr,
-                                                      double2* __restrict__ sinv_out) {
+                                                      int nmax, int pcr) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double2 red[OT / 32];
   __shared__ int s_piv;
@@ -352,17 +372,9 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
     }
   }
 
-  // 3. theta^T_jp = sum_k (S^-1)_kj Phi_pk and E1 = sum_jp h~_jp theta^T_jp -- or, for
-  // the tensor-core theta (sinv_out), S^-1 in FP64 for its digits
+  // 3. theta^T_jp = sum_k (S^-1)_kj Phi_pk and E1 = sum_jp h~_jp theta^T_jp
   double2 e1acc = cmk(0.0, 0.0);
-  if (DF && sinv_out) {
-    const DF2* sdf = reinterpret_cast<const DF2*>(aug) + n;  // [k][j] at slot k * n2 + j
-    double2* so = sinv_out + (long)(2 * z + s) * nmax * nmax;
-    for (int e = tid; e < n * n; e += OT) {
-      const int k = e / n, j = e % n;
-      so[(long)k * nmax + j] = df_to_double(sdf[k * n2 + j]);
-    }
-  } else if (DF) {
+  if (DF) {
     // S^-1 as double-floats: the right half of the eliminated augmented matrix
     const DF2* sdf = reinterpret_cast<const DF2*>(aug) + n;  // [k][j] at slot k * n2 + j
     DF2* pdf = reinterpret_cast<DF2*>(cphi);  // Phi chunk as double-floats
@@ -421,7 +433,7 @@ __global__ void __launch_bounds__(OT) k_overlap_theta(int M, int N, int na, int 
   }
   const double2 tot = block_sum2(e1acc, red);
   if (tid == 0) {
-    if (!sinv_out) e1[2 * z + s] = tot;
+    e1[2 * z + s] = tot;
     det[2 * z + s] = s_det;
   }
 }
@@ -686,20 +698,6 @@ __global__ void __launch_bounds__(256) k_qr(int M, int N, int na, int nb,
 // far below the ~2^-31 that the split-precision propagation leaves in the walkers.
 // R's diagonal, its logarithms and the reorthogonalisation test are FP64.  Qw holds
 // the double-float columns (the same 16 bytes per complex entry as the FP64 form).
-__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
-  const float s = __fadd_rn(h, bh), bv = __fsub_rn(s, h);
-  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(bh, bv));
-  l = __fadd_rn(l, __fadd_rn(bl, e));
-  h = s;
-  df_renorm(h, l);
-}
-__device__ __forceinline__ void df_warp_sum(float& h, float& l) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const float bh = __shfl_down_sync(0xffffffffu, h, o);
-    const float bl = __shfl_down_sync(0xffffffffu, l, o);
-    df_add(h, l, bh, bl);
-  }
-}
 __global__ void __launch_bounds__(256) k_qr_df(int M, int N, int na, int nb,
                                                double2* __restrict__ phi, DF2* __restrict__ Qw,
                                                double* __restrict__ detR, int* flags) {
@@ -855,20 +853,15 @@ int launch_overlap_mo(afq_ctx* ctx, WalkerSet& s) {
   const size_t smem = overlap_smem(nmax);
   AFQ_CUDA(ctx, raise_smem_limit((const void*)k_overlap_theta<DF, MO>, smem));
   // split-precision walker ensembles take S from the tensor cores (k_overlap_tc.cu)
-  // and theta = Phi S^-1 with E1 (k_mixed_prop.cu), this kernel then giving det S and
-  // S^-1 only
   const double2* Spre = nullptr;
-  double2* sinv = nullptr;
   if (DF && ctx->ov_S && &s == &ctx->ws) {
     AFQ_TRY(launch_overlap_s_tc(ctx, s));
     Spre = ctx->ov_S;
-    sinv = ctx->th_sinv;
   }
   k_overlap_theta<DF, MO><<<dim3(s.W, 2), OT, smem, ctx->stream>>>(
       ctx->M, ctx->N, ctx->na, ctx->nb, ctx->psiT, ctx->ht, s.phi, s.thetaT, s.det, s.e1,
-      ctx->flags, Spre, nmax, theta_chunk_rows(ctx->M, nmax), sinv);
+      ctx->flags, Spre, nmax, theta_chunk_rows(ctx->M, nmax));
   AFQ_LAUNCHED(ctx);
-  if (sinv) AFQ_TRY(launch_theta_tc(ctx, s));
   return AFQ_OK;
 }
 
@@ -883,7 +876,32 @@ int launch_overlap_df(afq_ctx* ctx, WalkerSet& s) {
   return launch_overlap_mo<DF, MAXO1>(ctx, s);
 }
 
+// The split-precision walker ensemble with the tensor-core theta: S and H = h~ Phi on
+// the tensor cores (7 digits), det S, S^-1 and E1 by one warp per matrix, theta on the
+// tensor cores (the force bias's and the exchange's digit count).
+int launch_overlap_gj_tc(afq_ctx* ctx, WalkerSet& s) {
+  const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
+  AFQ_TRY(launch_overlap_s_tc(ctx, s));
+  const size_t per_warp = (size_t)(nmax * nmax + nmax) * sizeof(DF2) + (size_t)nmax * sizeof(int);
+  int wpb = (int)((200u * 1024u) / per_warp);
+  if (wpb > 4) wpb = 4;
+  if (wpb < 1) return afq_fail(ctx, AFQ_ERR_ARG, "overlap matrix too large for one warp");
+  const size_t smem = per_warp * wpb;
+  AFQ_CUDA(ctx, raise_smem_limit((const void*)k_gj_df, smem));
+  const long units = 2L * s.W;
+  k_gj_df<<<(unsigned)((units + wpb - 1) / wpb), 32 * wpb, smem, ctx->stream>>>(
+      (int)units, ctx->na, ctx->nb, nmax, ctx->ov_S, ctx->ov_H, ctx->th_sinv, s.det, s.e1,
+      ctx->flags);
+  AFQ_LAUNCHED(ctx);
+  return launch_theta_tc(ctx, s);
+}
+
+// theta of the walker ensemble to double-float precision (~2^-44) whichever form the
+// step used: the mixed estimators read theta itself, not only its digits
+int launch_theta_precise(afq_ctx* ctx) { return launch_overlap_df<true>(ctx, ctx->ws); }
+
 int launch_overlap_theta(afq_ctx* ctx, WalkerSet& s, bool df) {
+  if (df && ctx->ov_S && ctx->th_sinv && &s == &ctx->ws) return launch_overlap_gj_tc(ctx, s);
   return df ? launch_overlap_df<true>(ctx, s) : launch_overlap_df<false>(ctx, s);
 }
 
