@@ -57,7 +57,7 @@ FP64_ALU_TFLOPS = 148 * 4 * 2.032e9 / 1e12
 # kernels exists.
 TRAFFIC = {("fp64", "c2", "propagate"): 34945792 + 0,
            ("fp64", "c3", "vhs"): 40650807296 + 1304730112,
-           ("split_bf16", "c3", "propagate"): 7700683776 + 2990288128}
+           ("split_bf16", "c3", "propagate"): 7705380864 + 3032207616}
 FP64_KERNELS = {"propagate": "k_propagate_fp64", "exchange": "k_exchange_v / k_exchange_fp64",
                 "vhs": "k_vhs_fp64", "force_bias": "k_force_bias_fp64"}
 SPLIT_KERNELS = {"propagate": "k_prop_tc (8 GEMM passes) + k_taylor_slice / k_slice_cplx1",

@@ -48,8 +48,11 @@ typedef enum afq_precision {
   AFQ_FP64 = 0,       /* every contraction in float64                         */
   AFQ_SPLIT_BF16 = 1, /* force bias, exchange, VHS and propagator contractions as
                          bf16 tensor-core GEMMs (tcgen05) on exact 8-bit integer
-                         digits of their operands; theta by double-float
-                         arithmetic; overlaps, inverses, QR and weights float64 */
+                         digits of their operands; the overlap matrix S and
+                         h~ Phi on 7 digits (FP64 quality); det S, S^-1 and the QR
+                         in double-float arithmetic (~2^-44 relative); theta on
+                         the force bias's digits up to 4 (double-float beyond, and
+                         for afq_spin_squared / afq_one_rdm); weights float64 */
   AFQ_SPLIT_TF32 = 2  /* reserved: afq_create rejects it (AFQ_ERR_ARG)          */
 } afq_precision;
 
