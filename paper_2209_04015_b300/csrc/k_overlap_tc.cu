@@ -126,8 +126,10 @@ struct OvP {
                                uint32_t bslot, bool first) {
     issue_split<SS>(a.c, tmem, sa, sb, bslot, first);
   }
+  // column tiles fastest: the S and H tiles of a row tile run side by side, so the
+  // second reads the Phi^T digits from L2
   static __device__ Tile tile(const Args& a) {
-    return Tile{(int)blockIdx.x * 128, (int)blockIdx.y * kOvBN, 0, a.c.nkb};
+    return Tile{(int)blockIdx.y * 128, (int)blockIdx.x * kOvBN, 0, a.c.nkb};
   }
   static __device__ void load_a(const CUtensorMap* tm, void* dst, const Args&, const Tile& t, int,
                                 int s, int kb, uint64_t* bar) {
@@ -265,7 +267,7 @@ int launch_overlap_s_tc(afq_ctx* ctx, WalkerSet& s) {
   if (a.c.stages < 1 || smem > kSmemLimit)
     return afq_fail(ctx, AFQ_ERR_ARG, "overlap tile does not fit in shared memory");
   const int brows = with_h ? 2 * N : N;
-  dim3 grid((unsigned)((a.rows_a + 127) / 128), (unsigned)((brows + kOvBN - 1) / kOvBN));
+  dim3 grid((unsigned)((brows + kOvBN - 1) / kOvBN), (unsigned)((a.rows_a + 127) / 128));
   cudaError_t e = launch_tc<kOvDigits, OvP>(grid, smem, ctx->stream, ctx->tm_ov_b, ctx->tm_ov_a, a);
   ctx->launches++;
   if (e != cudaSuccess)
