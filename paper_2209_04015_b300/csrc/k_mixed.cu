@@ -238,20 +238,33 @@ __global__ void __launch_bounds__(256) k_theta_exponents(const double2* __restri
 }
 
 // theta^T (W x N x M complex) -> integer digit planes [s][z][re/im][N Mpad] with the
-// exponents above (zero padding); one thread per (z, j, p < Mpad); D >= S
+// exponents above (zero padding); one thread per pair of consecutive elements
+// (z, j, p, p + 1 < Mpad; Mpad is even), written as bfloat16 pairs; D >= S
 template <int D>
 __global__ void k_slice_theta_exact(const double2* __restrict__ thetaT, int W, int N, int M,
                                     int Mpad, int S, const int* __restrict__ eb,
                                     __nv_bfloat16* __restrict__ out) {
   const long NMp = (long)N * Mpad, total = (long)W * NMp, plane = 2 * total;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
-    const long z = e / NMp, r = e % NMp;
+  for (long e2 = blockIdx.x * (long)blockDim.x + threadIdx.x; e2 < total / 2;
+       e2 += (long)gridDim.x * blockDim.x) {
+    const long e = 2 * e2, z = e / NMp, r = e % NMp;
     const int j = (int)(r / Mpad), p = (int)(r % Mpad);
-    const double2 v = p < M ? thetaT[(z * N + j) * M + p] : make_double2(0.0, 0.0);
+    const double2* src = thetaT + (z * N + j) * M + p;
+    const double2 v0 = p < M ? src[0] : make_double2(0.0, 0.0);
+    const double2 v1 = p + 1 < M ? src[1] : make_double2(0.0, 0.0);
+    const int er = eb[2 * z], ei = eb[2 * z + 1];
+    float a0[D], a1[D], b0[D], b1[D];
+    exact_digits_f<D>(v0.x, er, S, a0);
+    exact_digits_f<D>(v1.x, er, S, a1);
+    exact_digits_f<D>(v0.y, ei, S, b0);
+    exact_digits_f<D>(v1.y, ei, S, b1);
     __nv_bfloat16* o = out + (2 * z) * NMp + r;
-    split_exact<D>(v.x, eb[2 * z], S, o, plane);
-    split_exact<D>(v.y, eb[2 * z + 1], S, o + NMp, plane);
+#pragma unroll
+    for (int s = 0; s < D; ++s)
+      if (s < S) {
+        *reinterpret_cast<__nv_bfloat162*>(o + s * plane) = digit_bf16x2(a0[s], a1[s]);
+        *reinterpret_cast<__nv_bfloat162*>(o + NMp + s * plane) = digit_bf16x2(b0[s], b1[s]);
+      }
   }
 }
 
@@ -461,7 +474,7 @@ int launch_slice_theta(afq_ctx* ctx, WalkerSet& s) {
   k_theta_exponents<<<s.W, 256, 0, ctx->stream>>>(s.thetaT, (long)ctx->N * ctx->M, ctx->exv_eb);
   AFQ_LAUNCHED(ctx);
   (ctx->S <= kFastSlices ? k_slice_theta_exact<kFastSlices> : k_slice_theta_exact<kMaxSlices>)
-      <<<grid1d((long)s.W * ctx->N * ctx->Mpad), 256, 0, ctx->stream>>>(
+      <<<grid1d((long)s.W * ctx->N * ctx->Mpad / 2), 256, 0, ctx->stream>>>(
           s.thetaT, s.W, ctx->N, ctx->M, ctx->Mpad, ctx->S, ctx->exv_eb, ctx->exv_th);
   AFQ_LAUNCHED(ctx);
   if (ctx->th_sl) {
