@@ -43,124 +43,138 @@ __device__ double2 block_sum2(double2 v, double2* red) {
 // ---------------------------------------------------------------------------
 
 // det S and S^-1 of the split-precision walker ensemble when theta is formed on the
-// tensor cores: one warp per (walker, spin) matrix, in-place Gauss-Jordan elimination
-// with partial row pivoting (ties -> lowest row) on double-floats (n^3 complex updates
-// instead of the augmented form's ~1.5 n^3), lanes over columns, only warp-level
-// synchronisation; the row swaps are undone on the columns at the end.  det S is
+// tensor cores: one block of kGjWarps warps per (walker, spin) matrix, in-place
+// Gauss-Jordan elimination with partial row pivoting (ties -> lowest row) on
+// double-floats (n^3 complex updates instead of the augmented form's ~1.5 n^3).  Per
+// pivot warp 0 finds the pivot, swaps the rows, forms the reciprocal (an FP32
+// reciprocal refined by a Newton step in double-floats) and scales the pivot row; then
+// every warp updates its share of the rows, lanes over columns, four rows at a time for
+// independent chains.  The row swaps are undone on the columns at the end.  det S is
 // accumulated in FP64 from the pivots; S^-1 is written in FP64 ([k][j], nmax apart);
 // E1 follows from S^-1 and H = h~ Phi (both exact to FP64 quality), not from theta.
 // A pivot with |p|^2 below 1e-36 (the double-float range) is flagged as singular.
-__global__ void k_gj_df(int units, int na, int nb, int nmax, const double2* __restrict__ Spre,
-                        const double2* __restrict__ H, double2* __restrict__ sinv,
-                        double2* __restrict__ det, double2* __restrict__ e1, int* flags) {
+constexpr int kGjWarps = 4;
+__global__ void __launch_bounds__(32 * kGjWarps) k_gj_df(int units, int na, int nb, int nmax,
+                                                         const double2* __restrict__ Spre,
+                                                         const double2* __restrict__ H,
+                                                         double2* __restrict__ sinv,
+                                                         double2* __restrict__ det,
+                                                         double2* __restrict__ e1, int* flags) {
   extern __shared__ __align__(16) unsigned char gjraw[];
-  const int wpb = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long unit = (long)blockIdx.x * wpb + wid;
-  if (unit >= units) return;  // whole warps only: no block-wide synchronisation below
+  __shared__ DF2 s_inv;
+  __shared__ int perm[AFQ_NMAX];
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const long unit = blockIdx.x;
+  if (unit >= units) return;
   const int n = (unit & 1) ? nb : na;
   if (n == 0) {
-    if (lane == 0) {
+    if (tid == 0) {
       det[unit] = cmk(1.0, 0.0);
       e1[unit] = cmk(0.0, 0.0);
     }
     return;
   }
-  DF2* a = reinterpret_cast<DF2*>(gjraw) + (long)wid * (nmax * nmax + nmax);  // n x n, then
-  DF2* fk = a + nmax * nmax;                                                  // column k
-  int* perm = reinterpret_cast<int*>(reinterpret_cast<DF2*>(gjraw) + (long)wpb * (nmax * nmax + nmax)) +
-              wid * nmax;
+  DF2* a = reinterpret_cast<DF2*>(gjraw);  // n x n
+  DF2* fk = a + nmax * nmax;               // column k
   const double2* Sz = Spre + unit * nmax * nmax;
-  for (int i = 0; i < n; ++i)
-    for (int j = lane; j < n; j += 32) a[i * n + j] = df_from(Sz[(long)i * nmax + j]);
-  __syncwarp();
-  double2 dt = cmk(1.0, 0.0);
+  for (int e = tid; e < n * n; e += 32 * kGjWarps) a[e] = df_from(Sz[(long)(e / n) * nmax + e % n]);
+  __syncthreads();
+  double2 dt = cmk(1.0, 0.0);  // thread 0
+  const DF2 zero = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   for (int k = 0; k < n; ++k) {
-    float best = -1.f;
-    int bi = k;
-    for (int i = k + lane; i < n; i += 32) {
-      const float2 h = a[i * n + k].hi;
-      const float v = h.x * h.x + h.y * h.y;
-      if (v > best) { best = v; bi = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if (bi != k)
-      for (int j = lane; j < n; j += 32) {
-        const DF2 t = a[k * n + j];
-        a[k * n + j] = a[bi * n + j];
-        a[bi * n + j] = t;
+    if (wid == 0) {
+      float best = -1.f;
+      int bi = k;
+      for (int i = k + lane; i < n; i += 32) {
+        const float2 h = a[i * n + k].hi;
+        const float v = h.x * h.x + h.y * h.y;
+        if (v > best) { best = v; bi = i; }
       }
-    if (lane == 0) perm[k] = bi;
-    __syncwarp();
-    DF2 pv = a[k * n + k];
-    const float m2 = pv.hi.x * pv.hi.x + pv.hi.y * pv.hi.y;
-    const bool bad = !(m2 >= 1e-36f);
-    if (bad) {
-      if (lane == 0) atomicAdd(&flags[0], 1);
-      pv = DF2{make_float2(1.f, 0.f), make_float2(0.f, 0.f)};
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (bi != k)
+        for (int j = lane; j < n; j += 32) {
+          const DF2 t = a[k * n + j];
+          a[k * n + j] = a[bi * n + j];
+          a[bi * n + j] = t;
+        }
+      __syncwarp();
+      DF2 pv = a[k * n + k];
+      const float m2 = pv.hi.x * pv.hi.x + pv.hi.y * pv.hi.y;
+      if (!(m2 >= 1e-36f)) {
+        if (lane == 0) atomicAdd(&flags[0], 1);
+        pv = DF2{make_float2(1.f, 0.f), make_float2(0.f, 0.f)};
+      }
+      if (lane == 0) {
+        perm[k] = bi;
+        const double2 d = cmul(dt, df_to_double(pv));
+        dt = bi != k ? cmk(-d.x, -d.y) : d;
+      }
+      const DF2 inv = df_crecip(pv);
+      for (int j = lane; j < n; j += 32) a[k * n + j] = j == k ? inv : df_cmul(a[k * n + j], inv);
+      for (int i = lane; i < n; i += 32) fk[i] = a[i * n + k];
+      if (lane == 0) s_inv = inv;
     }
-    const double2 d = cmul(dt, df_to_double(pv));
-    dt = bi != k ? cmk(-d.x, -d.y) : d;
-    const DF2 inv = df_crecip(pv);
-    for (int j = lane; j < n; j += 32) a[k * n + j] = j == k ? inv : df_cmul(a[k * n + j], inv);
-    for (int i = lane; i < n; i += 32) fk[i] = a[i * n + k];
-    __syncwarp();
-    const DF2 zero = DF2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    __syncthreads();
+    const DF2 inv = s_inv;
     for (int j = lane; j < n; j += 32) {
       const DF2 akj = j == k ? inv : a[k * n + j];
-      // four rows at a time: independent double-float chains for the latency
-      for (int i0 = 0; i0 < n; i0 += 4) {
+      // this warp's rows wid, wid + kGjWarps, ...: four at a time (independent chains)
+      for (int i0 = wid; i0 < n; i0 += 4 * kGjWarps) {
         DF2 r[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int i = i0 + u;
+          const int i = i0 + u * kGjWarps;
           if (i < n && i != k) r[u] = df_cfms(fk[i], akj, j == k ? zero : a[i * n + j]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int i = i0 + u;
+          const int i = i0 + u * kGjWarps;
           if (i < n && i != k) a[i * n + j] = r[u];
         }
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
-  for (int k = n - 1; k >= 0; --k) {
-    const int p = perm[k];
-    if (p != k)
-      for (int i = lane; i < n; i += 32) {
+  // undo the row swaps on the columns: each thread owns a row
+  for (int i = tid; i < n; i += 32 * kGjWarps)
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = perm[k];
+      if (p != k) {
         const DF2 t = a[i * n + k];
         a[i * n + k] = a[i * n + p];
         a[i * n + p] = t;
       }
-    __syncwarp();
-  }
-  double2* so = sinv + unit * nmax * nmax;
-  for (int i = 0; i < n; ++i)
-    for (int j = lane; j < n; j += 32) so[(long)i * nmax + j] = df_to_double(a[i * n + j]);
-  // E1 = sum_jp h~_jp theta_pj = tr(H S^-1) with H = h~ Phi (trial i x walker j, from the
-  // overlap GEMM): lanes over the walker index j, sum over i of H_ij (S^-1)_ji
-  const double2* Hz = H + unit * nmax * nmax;
-  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-  for (int j = lane; j < n; j += 32)
-    for (int i = 0; i < n; ++i) {
-      const DF2 h = df_from(Hz[(long)i * nmax + j]);
-      const DF2 b = a[j * n + i];
-      df_mac_rn(rh, rl, h.hi.x, h.lo.x, b.hi.x, b.lo.x);
-      df_mac_rn(rh, rl, -h.hi.y, -h.lo.y, b.hi.y, b.lo.y);
-      df_mac_rn(ih, il, h.hi.x, h.lo.x, b.hi.y, b.lo.y);
-      df_mac_rn(ih, il, h.hi.y, h.lo.y, b.hi.x, b.lo.x);
     }
-  df_renorm(rh, rl);
-  df_renorm(ih, il);
-  df_warp_sum(rh, rl);
-  df_warp_sum(ih, il);
-  if (lane == 0) {
-    det[unit] = dt;
-    e1[unit] = cmk(f2d_bits(rh) + f2d_bits(rl), f2d_bits(ih) + f2d_bits(il));
+  __syncthreads();
+  double2* so = sinv + unit * nmax * nmax;
+  for (int e = tid; e < n * n; e += 32 * kGjWarps)
+    so[(long)(e / n) * nmax + e % n] = df_to_double(a[e]);
+  if (wid == 0) {
+    // E1 = sum_jp h~_jp theta_pj = tr(H S^-1) with H = h~ Phi (trial i x walker j, from
+    // the overlap GEMM): lanes over the walker index j, sum over i of H_ij (S^-1)_ji
+    const double2* Hz = H + unit * nmax * nmax;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int j = lane; j < n; j += 32)
+      for (int i = 0; i < n; ++i) {
+        const DF2 h = df_from(Hz[(long)i * nmax + j]);
+        const DF2 b = a[j * n + i];
+        df_mac_rn(rh, rl, h.hi.x, h.lo.x, b.hi.x, b.lo.x);
+        df_mac_rn(rh, rl, -h.hi.y, -h.lo.y, b.hi.y, b.lo.y);
+        df_mac_rn(ih, il, h.hi.x, h.lo.x, b.hi.y, b.lo.y);
+        df_mac_rn(ih, il, h.hi.y, h.lo.y, b.hi.x, b.lo.x);
+      }
+    df_renorm(rh, rl);
+    df_renorm(ih, il);
+    df_warp_sum(rh, rl);
+    df_warp_sum(ih, il);
+    if (lane == 0) {
+      det[unit] = dt;
+      e1[unit] = cmk(f2d_bits(rh) + f2d_bits(rl), f2d_bits(ih) + f2d_bits(il));
+    }
   }
 }
 
@@ -877,19 +891,15 @@ int launch_overlap_df(afq_ctx* ctx, WalkerSet& s) {
 }
 
 // The split-precision walker ensemble with the tensor-core theta: S and H = h~ Phi on
-// the tensor cores (7 digits), det S, S^-1 and E1 by one warp per matrix, theta on the
+// the tensor cores (7 digits), det S, S^-1 and E1 by one block per matrix, theta on the
 // tensor cores (the force bias's and the exchange's digit count).
 int launch_overlap_gj_tc(afq_ctx* ctx, WalkerSet& s) {
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
   AFQ_TRY(launch_overlap_s_tc(ctx, s));
-  const size_t per_warp = (size_t)(nmax * nmax + nmax) * sizeof(DF2) + (size_t)nmax * sizeof(int);
-  int wpb = (int)((200u * 1024u) / per_warp);
-  if (wpb > 4) wpb = 4;
-  if (wpb < 1) return afq_fail(ctx, AFQ_ERR_ARG, "overlap matrix too large for one warp");
-  const size_t smem = per_warp * wpb;
+  const size_t smem = (size_t)(nmax * nmax + nmax) * sizeof(DF2);
   AFQ_CUDA(ctx, raise_smem_limit((const void*)k_gj_df, smem));
   const long units = 2L * s.W;
-  k_gj_df<<<(unsigned)((units + wpb - 1) / wpb), 32 * wpb, smem, ctx->stream>>>(
+  k_gj_df<<<(unsigned)units, 32 * kGjWarps, smem, ctx->stream>>>(
       (int)units, ctx->na, ctx->nb, nmax, ctx->ov_S, ctx->ov_H, ctx->th_sinv, s.det, s.e1,
       ctx->flags);
   AFQ_LAUNCHED(ctx);
