@@ -149,13 +149,24 @@ __global__ void __launch_bounds__(256) k_exv_dot(int Ka, int Kb, int na, int nb,
   const double* yr = y + (spin ? (long)W2 * Ka : 0) + (long)(2 * z) * Kp;
   const double* yi = yr + Kp;
   double2 acc = make_double2(0.0, 0.0);
-  for (int r = threadIdx.x; r < Kp; r += 256) {
-    const int j = r / Mpad, p = r % Mpad;
-    if (p >= M) continue;
-    const double2 x = thetaT[(long)z * NM + offM + (long)j * M + p];
-    const double a = yr[r], b = yi[r];
-    acc.x = fma(x.x, a, fma(-x.y, b, acc.x));
-    acc.y = fma(x.x, b, fma(x.y, a, acc.y));
+  // four consecutive elements of one row per thread (Mpad is a multiple of 32), their
+  // loads issued together ahead of the multiply-adds
+  for (int r0 = 4 * threadIdx.x; r0 < Kp; r0 += 4 * 256) {
+    const int j = r0 / Mpad, p0 = r0 - j * Mpad;
+    const double2* th = thetaT + (long)z * NM + offM + (long)j * M + p0;
+    double2 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = p0 + u < M ? th[u] : make_double2(0.0, 0.0);
+    const double2 a01 = *reinterpret_cast<const double2*>(yr + r0);
+    const double2 a23 = *reinterpret_cast<const double2*>(yr + r0 + 2);
+    const double2 b01 = *reinterpret_cast<const double2*>(yi + r0);
+    const double2 b23 = *reinterpret_cast<const double2*>(yi + r0 + 2);
+    const double av[4] = {a01.x, a01.y, a23.x, a23.y}, bv[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc.x = fma(x[u].x, av[u], fma(-x[u].y, bv[u], acc.x));
+      acc.y = fma(x[u].x, bv[u], fma(x[u].y, av[u], acc.y));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
