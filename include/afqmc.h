@@ -230,7 +230,9 @@ int afq_get_e_shift(afq_ctx* ctx, double* e_shift);
      <Psi_T|S^2|Phi_z> / <Psi_T|Phi_z> = N_beta + M_S (M_S + 1) - tr(G_alpha G_beta),
    M_S = (na - nb) / 2, G_s the walker's Green's function of spin s (the trace of
    the product, from Wick's theorem; the paper's printed sum drops the transpose,
-   which only agrees for symmetric G).  FP64 from the walkers' current theta.
+   which only agrees for symmetric G).  FP64 from the walkers' current theta (an
+   AFQ_SPLIT_BF16 context first recomputes theta in double-float arithmetic: its step
+   forms theta at the force bias's digit count).
    s2_out: W complex (host) or NULL; s2_mix: Re(sum w S2 / sum w) (host) or NULL.
    AFQ_ERR_STATE before afq_init_walkers. */
 int afq_spin_squared(afq_ctx* ctx, double* s2_out, double* s2_mix);
@@ -239,7 +241,8 @@ int afq_spin_squared(afq_ctx* ctx, double* s2_out, double* s2_mix);
    estimator, Sec. "Customized mixed estimators"):
      <G^s>_pq = sum_z w_z G^s_z,pq / sum_z w_z,   G_pq = <a+_p a_q> = sum_j Psi_pj theta_qj,
    formed as Psi_s (sum_z w_z theta_z,s)^T / sum_z w_z from the walkers' current theta
-   (FP64; complex weights in free projection).  g_out: host, 2 x M x M complex, the
+   (FP64; complex weights in free projection; double-float theta recomputed first in
+   AFQ_SPLIT_BF16 contexts, as for afq_spin_squared).  g_out: host, 2 x M x M complex, the
    alpha matrix first (AFQ_ERR_ARG if NULL); AFQ_ERR_STATE before afq_init_walkers. */
 int afq_one_rdm(afq_ctx* ctx, double* g_out);
 
