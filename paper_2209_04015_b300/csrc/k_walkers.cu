@@ -859,8 +859,9 @@ int theta_chunk_rows(int M, int n) {
   return best;
 }
 
-// df: theta by double-float arithmetic (split-precision walker ensembles); S, its
-// determinant and inverse and the one-body energy stay FP64 either way.
+// df: the elimination and theta in double-float arithmetic (split-precision walker
+// ensembles); S is FP64 (or the tensor cores' product to FP64 quality), det S and the
+// one-body energy accumulate in FP64 either way.
 template <bool DF, int MO>
 int launch_overlap_mo(afq_ctx* ctx, WalkerSet& s) {
   const int nmax = ctx->na > ctx->nb ? ctx->na : ctx->nb;
