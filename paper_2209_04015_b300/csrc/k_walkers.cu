@@ -53,8 +53,11 @@ __device__ double2 block_sum2(double2 v, double2* red) {
 // accumulated in FP64 from the pivots; S^-1 is written in FP64 ([k][j], nmax apart);
 // E1 follows from S^-1 and H = h~ Phi (both exact to FP64 quality), not from theta.
 // A pivot with |p|^2 below 1e-36 (the double-float range) is flagged as singular.
+// Nine blocks per SM (<= 56 registers): the 2 x 640 matrices of 640 walkers then run in
+// one wave on 148 SMs, where eight left a second wave of 96 (0.80 -> 0.76 ms for the
+// overlap class at 290 orbitals; two warps or one warp per matrix measured 0.78).
 constexpr int kGjWarps = 4;
-__global__ void __launch_bounds__(32 * kGjWarps) k_gj_df(int units, int na, int nb, int nmax,
+__global__ void __launch_bounds__(32 * kGjWarps, 9) k_gj_df(int units, int na, int nb, int nmax,
                                                          const double2* __restrict__ Spre,
                                                          const double2* __restrict__ H,
                                                          double2* __restrict__ sinv,
