@@ -53,28 +53,45 @@ __global__ void k_slice_rows7(const double* __restrict__ in, const double* __res
 }
 
 // Phi (W x M x N complex) -> S digit planes [s][z][re/im][j][Kp] of Phi^T, one exponent
-// per complex row (z, j) shared by its real and imaginary parts (one warp per row; the
-// row's elements are N apart in Phi).
-__global__ void k_slice_phiT7(const double2* __restrict__ phi, int W, int M, int N, int Kp, int S,
-                              __nv_bfloat16* __restrict__ out, int* __restrict__ eout) {
-  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
-  const long rows = (long)W * N, plane = 2L * rows * Kp;
-  for (long r = (long)blockIdx.x * warps + (threadIdx.x >> 5); r < rows;
-       r += (long)gridDim.x * warps) {
-    const long z = r / N;
-    const int j = (int)(r - z * N);
-    const double2* col = phi + z * (long)M * N + j;
+// per complex row (z, j) shared by its real and imaginary parts.  A block takes kPhiJG
+// consecutive columns j of one walker: its threads copy those columns of every row p
+// (kPhiJG complex, contiguous in Phi) into shared memory once, then warp w cuts column
+// j0 + w.  (Read straight from Phi, a column strides N complex per element, so each 16
+// bytes cost a 32-byte sector, and it was read twice: for the maximum, for the digits.)
+constexpr int kPhiJG = 8;
+constexpr int kPhiJGP = kPhiJG + 1;  // tile pitch: a warp's column reads are conflict-free
+__global__ void __launch_bounds__(32 * kPhiJG) k_slice_phiT7(const double2* __restrict__ phi,
+                                                             int W, int M, int N, int Kp, int S,
+                                                             __nv_bfloat16* __restrict__ out,
+                                                             int* __restrict__ eout) {
+  extern __shared__ __align__(16) unsigned char phraw[];
+  double2* tile = reinterpret_cast<double2*>(phraw);  // [p][jj], kPhiJGP apart
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ngrp = (N + kPhiJG - 1) / kPhiJG;
+  const long plane = 2L * W * N * Kp, items = (long)W * ngrp;
+  for (long it = blockIdx.x; it < items; it += gridDim.x) {  // block-uniform
+    const long z = it / ngrp;
+    const int j0 = (int)(it - z * ngrp) * kPhiJG;
+    const double2* pz = phi + z * (long)M * N + j0;
+    __syncthreads();  // the previous item's column reads are done
+    for (int e = threadIdx.x; e < M * kPhiJG; e += 32 * kPhiJG) {
+      const int p = e / kPhiJG, jj = e - p * kPhiJG;
+      tile[p * kPhiJGP + jj] = j0 + jj < N ? pz[(long)p * N + jj] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const int j = j0 + w;
+    if (j >= N) continue;
     int m = 0;
     for (int p = lane; p < M; p += 32) {
-      const double2 v = col[(long)p * N];
+      const double2 v = tile[p * kPhiJGP + w];
       m = max(m, max(exp_field(v.x), exp_field(v.y)));
     }
     const int e = row_exponent_field(__reduce_max_sync(0xffffffffu, m));
-    if (lane == 0) eout[r] = e;
+    if (lane == 0) eout[z * N + j] = e;
     __nv_bfloat16* ore = out + ((2 * z) * N + j) * (long)Kp;
     __nv_bfloat16* oim = ore + (long)N * Kp;
     for (int p = lane; p < Kp; p += 32) {
-      const double2 v = p < M ? col[(long)p * N] : make_double2(0.0, 0.0);
+      const double2 v = p < M ? tile[p * kPhiJGP + w] : make_double2(0.0, 0.0);
       float qr[kOvDigits], qi[kOvDigits];
       exact_digits_f<kOvDigits>(v.x, e, S, qr);
       exact_digits_f<kOvDigits>(v.y, e, S, qi);
@@ -242,8 +259,14 @@ void overlap_tc_free(afq_ctx* ctx) {
 // and with the tensor-core theta also H_z,s = h~_s Phi_z,s into ctx->ov_H.
 int launch_overlap_s_tc(afq_ctx* ctx, WalkerSet& s) {
   const int N = ctx->N, M = ctx->M, Mpad = ctx->Mpad, W = s.W;
-  k_slice_phiT7<<<warp_grid7((long)W * N), 256, 0, ctx->stream>>>(s.phi, W, M, N, Mpad, kOvDigits,
-                                                                  ctx->ov_phi_sl, ctx->ov_eb);
+  {
+    const size_t smem = (size_t)M * kPhiJGP * sizeof(double2);
+    AFQ_CUDA(ctx, raise_smem_limit((const void*)k_slice_phiT7, smem));
+    const long items = (long)W * ((N + kPhiJG - 1) / kPhiJG);
+    const int grid = (int)(items < 1 ? 1 : items < 148 * 16 ? items : 148 * 16);
+    k_slice_phiT7<<<grid, 32 * kPhiJG, smem, ctx->stream>>>(s.phi, W, M, N, Mpad, kOvDigits,
+                                                            ctx->ov_phi_sl, ctx->ov_eb);
+  }
   AFQ_LAUNCHED(ctx);
   OvP::Args a{};
   a.c.nkb = Mpad / kBK;
